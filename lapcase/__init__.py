@@ -1,0 +1,243 @@
+"""Seeded synthetic inputs for the laplacianFoam time step (shared by the CUDA path and the oracle).
+
+This module draws random numbers and writes down mesh *specifications*; it holds none of
+the finite-volume arithmetic (no volumes, face areas, distances, matrix coefficients or
+solver steps). Both consumers derive those independently from a :class:`RawCase`.
+
+A raw case is a rectilinear hexahedral box (the blockMesh-style meshes of the paper's
+evaluation, section "Evaluation", Table "Mesh dimensions") described by:
+
+* ``xs, ys, zs`` -- vertex coordinates along each axis (lengths nx+1, ny+1, nz+1);
+* ``perm`` -- optional relabelling of cells: natural cell id ``i + nx*(j + ny*k)`` gets label
+  ``perm[id]`` (None = identity);
+* diffusivity ``DT`` per geometric face: either the scalar ``DT_uniform`` or three arrays
+  ``DTx[k, j, i]`` (shape nz, ny, nx+1; i indexes x-normal face planes 0..nx, boundary planes
+  included), ``DTy[k, j, i]`` (nz, ny+1, nx) and ``DTz[k, j, i]`` (nz+1, ny, nx);
+* six patches in the fixed order x0, x1, y0, y1, z0, z1, each ``(type, value)`` with type
+  ``FIXED_VALUE`` or ``ZERO_GRADIENT``;
+* the initial field ``T0`` (scalar, or an array over natural cell ids), the time step ``dt``,
+  the number of steps and the PCG controls (tolerance, relTol, maxIter, minIter).
+
+Face conventions every consumer must follow (they define the order of the LDU arrays):
+
+* internal faces: one per pair of face-adjacent cells; owner = smaller label, neighbour =
+  larger label; faces sorted by (owner, neighbour) -- OpenFOAM's upper-triangular order
+  (section "OpenFOAM": every face has an owner, only internal faces a neighbour; the face
+  normal points from owner to neighbour);
+* boundary faces: grouped by patch in the order above; inside an x-patch faces run over
+  (k, j) with j fastest, inside a y-patch over (k, i) with i fastest, inside a z-patch over
+  (j, i) with i fastest.
+"""
+from __future__ import annotations
+
+import dataclasses
+import math
+from typing import List, Optional, Sequence, Tuple
+
+import numpy as np
+
+FIXED_VALUE = 0
+ZERO_GRADIENT = 1
+PATCH_NAMES = ("x0", "x1", "y0", "y1", "z0", "z1")
+
+FP64 = 0
+MIXED = 1
+
+
+@dataclasses.dataclass
+class RawCase:
+    xs: np.ndarray
+    ys: np.ndarray
+    zs: np.ndarray
+    perm: Optional[np.ndarray] = None
+    DT_uniform: float = 0.0
+    DTx: Optional[np.ndarray] = None
+    DTy: Optional[np.ndarray] = None
+    DTz: Optional[np.ndarray] = None
+    patches: Sequence[Tuple[int, float]] = ((FIXED_VALUE, 373.0), (FIXED_VALUE, 273.0),
+                                           (ZERO_GRADIENT, 0.0), (ZERO_GRADIENT, 0.0),
+                                           (ZERO_GRADIENT, 0.0), (ZERO_GRADIENT, 0.0))
+    T0: object = 273.0
+    dt: float = 0.005
+    n_steps: int = 20
+    tol: float = 1e-6
+    rel_tol: float = 0.0
+    max_iter: int = 1000
+    min_iter: int = 0
+    precision: int = FP64
+    name: str = "case"
+
+    @property
+    def nx(self) -> int:
+        return len(self.xs) - 1
+
+    @property
+    def ny(self) -> int:
+        return len(self.ys) - 1
+
+    @property
+    def nz(self) -> int:
+        return len(self.zs) - 1
+
+    @property
+    def n_cells(self) -> int:
+        return self.nx * self.ny * self.nz
+
+    @property
+    def n_internal_faces(self) -> int:
+        nx, ny, nz = self.nx, self.ny, self.nz
+        return (nx - 1) * ny * nz + nx * (ny - 1) * nz + nx * ny * (nz - 1)
+
+    @property
+    def n_boundary_faces(self) -> int:
+        nx, ny, nz = self.nx, self.ny, self.nz
+        return 2 * (ny * nz + nx * nz + nx * ny)
+
+    def T0_natural(self) -> np.ndarray:
+        """Initial field over natural cell ids (float64)."""
+        if np.isscalar(self.T0):
+            return np.full(self.n_cells, float(self.T0))
+        return np.ascontiguousarray(self.T0, dtype=np.float64).reshape(self.n_cells)
+
+    def with_(self, **kw) -> "RawCase":
+        return dataclasses.replace(self, **kw)
+
+
+def uniform_axis(n: int, length: float = 1.0) -> np.ndarray:
+    return np.linspace(0.0, length, n + 1)
+
+
+def graded_axis(n: int, ratio: float, length: float = 1.0) -> np.ndarray:
+    """Vertex coordinates with each cell ``ratio`` times wider than the previous one."""
+    widths = ratio ** np.arange(n, dtype=np.float64)
+    widths *= length / widths.sum()
+    xs = np.concatenate(([0.0], np.cumsum(widths)))
+    xs[-1] = length
+    return xs
+
+
+def _log_uniform(rng: np.random.Generator, lo: float, hi: float, size=None):
+    return np.exp(rng.uniform(math.log(lo), math.log(hi), size))
+
+
+def face_dt_arrays(nx: int, ny: int, nz: int, rng: np.random.Generator, lo: float, hi: float):
+    """Per-geometric-face diffusivity drawn log-uniform in [lo, hi] (boundary faces included)."""
+    DTx = _log_uniform(rng, lo, hi, (nz, ny, nx + 1))
+    DTy = _log_uniform(rng, lo, hi, (nz, ny + 1, nx))
+    DTz = _log_uniform(rng, lo, hi, (nz + 1, ny, nx))
+    return DTx, DTy, DTz
+
+
+# ---------------------------------------------------------------------------------------
+# The five workloads (20^3 plain, 100^3 permuted, 200^3 graded, a batch of 512, a serving
+# stream) and small variants of them for tests.
+# ---------------------------------------------------------------------------------------
+
+def plain_box(n: int = 20) -> RawCase:
+    """n^3 unit cube, natural numbering, DT=4e-5, dt=0.005, 20 steps, x0=373 K, x1=273 K
+    fixedValue, other faces zeroGradient, T0=273 K, tol 1e-6, relTol 0."""
+    ax = uniform_axis(n)
+    return RawCase(xs=ax, ys=ax.copy(), zs=ax.copy(), DT_uniform=4e-5, dt=0.005, n_steps=20,
+                   tol=1e-6, rel_tol=0.0, T0=273.0, name=f"plain{n}")
+
+
+def permuted_box(n: int = 100, seed_perm: int = 1, seed_dt: int = 2, n_steps: int = 50) -> RawCase:
+    """n^3 unit cube with a seeded random cell relabelling and per-face DT log-uniform in
+    [1e-6, 1e-4]; dt=0.01, tol 1e-8, boundary conditions and T0 as the plain box."""
+    ax = uniform_axis(n)
+    perm = np.random.default_rng(seed_perm).permutation(n ** 3).astype(np.int64)
+    DTx, DTy, DTz = face_dt_arrays(n, n, n, np.random.default_rng(seed_dt), 1e-6, 1e-4)
+    return RawCase(xs=ax, ys=ax.copy(), zs=ax.copy(), perm=perm, DTx=DTx, DTy=DTy, DTz=DTz,
+                   dt=0.01, n_steps=n_steps, tol=1e-8, rel_tol=0.0, T0=273.0,
+                   name=f"permuted{n}")
+
+
+def graded_box(n: int = 200, ratio: float = 1.02, n_steps: int = 100,
+               precision: int = FP64) -> RawCase:
+    """n^3 unit cube graded in x (each cell ``ratio`` times the previous), uniform in y and z,
+    boundary conditions and T0 as the plain box, DT=4e-5, dt=0.005, tol 1e-6."""
+    return RawCase(xs=graded_axis(n, ratio), ys=uniform_axis(n), zs=uniform_axis(n),
+                   DT_uniform=4e-5, dt=0.005, n_steps=n_steps, tol=1e-6, rel_tol=0.0,
+                   T0=273.0, precision=precision, name=f"graded{n}")
+
+
+def batch_cases(n_cases: int = 512, seed: int = 3, n_min: int = 16, n_max: int = 96,
+                n_steps: int = 10, precision: int = FP64) -> List[RawCase]:
+    """Independent cases: edge n log-uniform in [n_min, n_max], DT log-uniform in
+    [1e-6, 1e-4], dt log-uniform in [1e-3, 1e-1], fixedValue temperatures U(250, 400) on
+    x0 and x1 (drawn independently), zeroGradient elsewhere, T0 uniform = the x1 value."""
+    rng = np.random.default_rng(seed)
+    out = []
+    for c in range(n_cases):
+        n = int(round(math.exp(rng.uniform(math.log(n_min), math.log(n_max)))))
+        DT = float(_log_uniform(rng, 1e-6, 1e-4))
+        dt = float(_log_uniform(rng, 1e-3, 1e-1))
+        Ta, Tb = (float(v) for v in rng.uniform(250.0, 400.0, 2))
+        ax = uniform_axis(n)
+        patches = ((FIXED_VALUE, Ta), (FIXED_VALUE, Tb)) + ((ZERO_GRADIENT, 0.0),) * 4
+        out.append(RawCase(xs=ax, ys=ax.copy(), zs=ax.copy(), DT_uniform=DT, dt=dt,
+                           n_steps=n_steps, tol=1e-6, rel_tol=0.0, T0=Tb, patches=patches,
+                           precision=precision, name=f"batch{c}_n{n}"))
+    return out
+
+
+@dataclasses.dataclass
+class Request:
+    arrival_s: float
+    case: RawCase
+
+
+def serving_stream(n_requests: int = 2000, seed: int = 4, rate_per_s: float = 200.0,
+                   n_min: int = 32, n_max: int = 160, max_steps: int = 50) -> List[Request]:
+    """Poisson arrivals (exponential gaps, mean 1/rate) of solve requests: edge n
+    log-uniform in [n_min, n_max], steps uniform in 1..max_steps, precision FP64 or mixed
+    with probability 1/2, DT, dt and boundary values drawn as for :func:`batch_cases`."""
+    rng = np.random.default_rng(seed)
+    t = 0.0
+    out = []
+    for r in range(n_requests):
+        t += float(rng.exponential(1.0 / rate_per_s))
+        n = int(round(math.exp(rng.uniform(math.log(n_min), math.log(n_max)))))
+        steps = int(rng.integers(1, max_steps + 1))
+        precision = MIXED if rng.random() < 0.5 else FP64
+        DT = float(_log_uniform(rng, 1e-6, 1e-4))
+        dt = float(_log_uniform(rng, 1e-3, 1e-1))
+        Ta, Tb = (float(v) for v in rng.uniform(250.0, 400.0, 2))
+        ax = uniform_axis(n)
+        patches = ((FIXED_VALUE, Ta), (FIXED_VALUE, Tb)) + ((ZERO_GRADIENT, 0.0),) * 4
+        out.append(Request(t, RawCase(xs=ax, ys=ax.copy(), zs=ax.copy(), DT_uniform=DT, dt=dt,
+                                      n_steps=steps, tol=1e-6, rel_tol=0.0, T0=Tb,
+                                      patches=patches, precision=precision,
+                                      name=f"req{r}_n{n}")))
+    return out
+
+
+def random_small_case(seed: int, nx: int = 4, ny: int = 4, nz: int = 4, permute: bool = True,
+                      face_dt: bool = True, graded: bool = True,
+                      patch_types: Optional[Sequence[int]] = None) -> RawCase:
+    """A small randomised case for validation: optional permutation, per-face DT, grading
+    in all three axes, random patch values and a random initial field."""
+    rng = np.random.default_rng(seed)
+
+    def axis(n):
+        if not graded:
+            return uniform_axis(n)
+        w = rng.uniform(0.5, 1.5, n)
+        return np.concatenate(([0.0], np.cumsum(w / w.sum())))
+
+    xs, ys, zs = axis(nx), axis(ny), axis(nz)
+    N = nx * ny * nz
+    perm = rng.permutation(N).astype(np.int64) if permute else None
+    if face_dt:
+        DTx, DTy, DTz = face_dt_arrays(nx, ny, nz, rng, 1e-3, 1e-1)
+        DTu = 0.0
+    else:
+        DTx = DTy = DTz = None
+        DTu = float(_log_uniform(rng, 1e-3, 1e-1))
+    if patch_types is None:
+        patch_types = [FIXED_VALUE if rng.random() < 0.5 else ZERO_GRADIENT for _ in range(6)]
+    patches = tuple((int(t), float(rng.uniform(250, 400))) for t in patch_types)
+    T0 = rng.uniform(250, 400, N)
+    return RawCase(xs=xs, ys=ys, zs=zs, perm=perm, DT_uniform=DTu, DTx=DTx, DTy=DTy, DTz=DTz,
+                   patches=patches, T0=T0, dt=float(_log_uniform(rng, 1e-3, 1.0)), n_steps=3,
+                   tol=1e-12, rel_tol=0.0, name=f"small{seed}")
