@@ -1,0 +1,383 @@
+#!/usr/bin/env python
+"""Benchmark of the implicit laplacianFoam time step on GB300.
+
+Default workload: the 200^3 box graded 1.02x per cell in x (8,000,000 cells, 23,880,000
+internal faces), T=373 K / 273 K fixedValue on x0 / x1, zeroGradient elsewhere, T0=273 K,
+DT=4e-5, dt=0.005, diagonal PCG to tol 1e-6 (relTol 0), FP64, with the mixed-precision
+form run side by side. One bench step = one implicit time step (assembly, initial residual
+and normFactor, PCG to convergence). Inputs stay resident in HBM; the working set
+(~2 GB) is far larger than the 129 MB L2, so no L2 flush is needed between steps.
+
+Metric: PCG cell-iterations/s = sum over timed steps of n_cells * PCG iterations / time.
+
+  python bench.py [--gpus N] [--steps K] [--warmup W] [--impl ours|reference]
+
+N > 1 runs under torchrun: every rank advances its own replica (the step does not shard
+without a halo exchange; replicas are independent), time = max over ranks, value = all
+ranks' cell-iterations / that time.
+"""
+from __future__ import annotations
+
+import argparse
+import hashlib
+import json
+import os
+import statistics
+import subprocess
+import sys
+import tempfile
+import time
+
+import numpy as np
+
+ROOT = os.path.dirname(os.path.abspath(__file__))
+sys.path.insert(0, ROOT)
+
+import lapcase  # noqa: E402
+
+METRIC = "PCG cell-iterations/s and achieved HBM GB/s (FP64 vs mixed), p99 solve latency"
+UNIT = "cell-iterations/s"
+WORKLOAD = ("graded200: 200^3 unit box graded 1.02x per cell in x (8.0M cells, 23.88M internal "
+            "faces), DT=4e-5, dt=0.005, x0=373 K / x1=273 K fixedValue, zeroGradient elsewhere, "
+            "T0=273 K, diagonal PCG tol 1e-6 relTol 0")
+KERNEL_SOURCES = ["paper_2507_18268_gb300/csrc/lfm_step.cu", "paper_2507_18268_gb300/csrc/lfm_device.cuh",
+                  "paper_2507_18268_gb300/csrc/lfm_internal.h"]
+
+
+def kernel_hash() -> str:
+    h = hashlib.sha256()
+    for p in KERNEL_SOURCES:
+        with open(os.path.join(ROOT, p), "rb") as f:
+            h.update(f.read())
+    return h.hexdigest()[:16]
+
+
+def algorithmic_bytes(N: int, F: int, iters: int, steps: int, precision: int) -> float:
+    """Minimum DRAM bytes of `steps` steps with `iters` PCG iterations in total.
+
+    Per PCG iteration (every array touched once per pass, int32 addressing):
+      FP64  112 N + 16 F  (p update 32N; A p and p.q 24N + 16F; x, r updates and dots 56N)
+      mixed  56 N + 12 F  (the same passes on 4-byte values)
+    Per step: assembly 40 N + 16 F (reads V, T, the face coefficients and addressing; writes
+    diag, source, 1/diag and the off-diagonals) and the initial residual 48 N + 16 F.
+    """
+    if precision == 0:
+        per_iter = 112 * N + 16 * F
+    else:
+        per_iter = 56 * N + 12 * F
+    per_step = (40 * N + 16 * F) + (48 * N + 16 * F)
+    return float(iters) * per_iter + float(steps) * per_step
+
+
+def load_peaks():
+    p = os.path.join(ROOT, "MEASURED_PEAKS.json")
+    if os.path.exists(p):
+        with open(p) as f:
+            d = json.load(f)
+        return float(d["hbm_gbs"]), "measured"
+    return 6800.0, "fallback"
+
+
+def load_traffic_ratio(name: str):
+    """DRAM-traffic / algorithmic-bytes ratio from a committed ncu summary, if it was taken
+    on the current kernel source."""
+    p = os.path.join(ROOT, "profiles", f"traffic_{name}.json")
+    if not os.path.exists(p):
+        return None
+    with open(p) as f:
+        d = json.load(f)
+    if d.get("kernel_hash") != kernel_hash():
+        return None
+    return float(d["dram_bytes"]) / float(d["algorithmic_bytes"])
+
+
+class ClockSampler:
+    """nvidia-smi clock / throttle-reason samples during the timed region."""
+
+    FIELDS = ("index,clocks.sm,clocks.max.sm,power.draw,clocks_event_reasons.active,"
+              "clocks_event_reasons.hw_slowdown,clocks_event_reasons.hw_thermal_slowdown,"
+              "clocks_event_reasons.sw_thermal_slowdown,clocks_event_reasons.sw_power_cap")
+
+    def __init__(self, gpu: int):
+        self.gpu = gpu
+        self.proc = None
+        self.path = None
+
+    def start(self):
+        try:
+            fd, self.path = tempfile.mkstemp(suffix=".csv")
+            os.close(fd)
+            self.proc = subprocess.Popen(
+                ["nvidia-smi", "-i", str(self.gpu), f"--query-gpu={self.FIELDS}", "--format=csv,noheader,nounits",
+                 "-lms", "100", "-f", self.path], stdout=subprocess.DEVNULL, stderr=subprocess.DEVNULL)
+            time.sleep(0.3)
+        except (OSError, FileNotFoundError):
+            self.proc = None
+
+    def stop(self):
+        if self.proc is None:
+            return None
+        time.sleep(0.15)
+        self.proc.terminate()
+        try:
+            self.proc.wait(timeout=5)
+        except subprocess.TimeoutExpired:
+            self.proc.kill()
+        rows = []
+        try:
+            with open(self.path) as f:
+                for line in f:
+                    parts = [x.strip() for x in line.split(",")]
+                    if len(parts) >= 9:
+                        rows.append(parts)
+            os.unlink(self.path)
+        except OSError:
+            return None
+        if not rows:
+            return None
+        sm = [float(r[1]) for r in rows if r[1].replace(".", "").isdigit()]
+        mx = [float(r[2]) for r in rows if r[2].replace(".", "").isdigit()]
+        names = ["hw_slowdown", "hw_thermal_slowdown", "sw_thermal_slowdown", "sw_power_cap"]
+        reasons = sorted({names[i] for r in rows for i in range(4) if r[5 + i].lower() == "active"})
+        return {"sm_mhz": statistics.median(sm) if sm else None, "sm_max_mhz": max(mx) if mx else None,
+                "reasons": reasons, "samples": len(rows),
+                "power_w_max": max((float(r[3]) for r in rows if r[3].replace(".", "").isdigit()), default=None)}
+
+
+def dist_setup():
+    world = int(os.environ.get("WORLD_SIZE", "1"))
+    rank = int(os.environ.get("RANK", "0"))
+    local = int(os.environ.get("LOCAL_RANK", "0"))
+    if world > 1:
+        import torch
+        import torch.distributed as dist
+        backend = "nccl" if torch.cuda.is_available() else "gloo"
+        if backend == "nccl":
+            torch.cuda.set_device(local)
+        dist.init_process_group(backend)
+    return world, rank, local
+
+
+def barrier(world):
+    if world > 1:
+        import torch.distributed as dist
+        dist.barrier()
+
+
+def reduce_max(x: float, world: int) -> float:
+    if world == 1:
+        return x
+    import torch
+    import torch.distributed as dist
+    t = torch.tensor([x], dtype=torch.float64, device="cuda" if torch.cuda.is_available() else "cpu")
+    dist.all_reduce(t, op=dist.ReduceOp.MAX)
+    return float(t.item())
+
+
+def reduce_sum(x: float, world: int) -> float:
+    if world == 1:
+        return x
+    import torch
+    import torch.distributed as dist
+    t = torch.tensor([x], dtype=torch.float64, device="cuda" if torch.cuda.is_available() else "cpu")
+    dist.all_reduce(t, op=dist.ReduceOp.SUM)
+    return float(t.item())
+
+
+def reference_slab_case() -> lapcase.RawCase:
+    """A 200 x 200 x 25 slab of the graded 200^3 box (same cell sizes, same x grading and
+    boundary conditions, zeroGradient z faces): the same 1D-in-x physics per cell."""
+    full = lapcase.graded_box(200)
+    return full.with_(zs=lapcase.uniform_axis(200)[:26].copy(), name="graded200_slab25")
+
+
+def run_cpu_oracle(case, n_steps: int, warmup: int = 0):
+    import oracle
+    mesh = oracle.box_mesh(case)
+    T = oracle.initial_field(case)
+    if warmup:
+        T, _ = oracle.advance(case, n_steps=warmup, mesh=mesh, T=T)
+    t0 = time.perf_counter()
+    T, st = oracle.advance(case, n_steps=n_steps, mesh=mesh, T=T)
+    dt = time.perf_counter() - t0
+    iters = sum(s.iters for s in st)
+    return mesh.n_cells * iters / dt, dt, iters
+
+
+def main_reference(args, world, rank):
+    if rank != 0:
+        return
+    case = reference_slab_case()
+    value, secs, iters = run_cpu_oracle(case, args.steps, args.warmup)
+    sample = (f"oracle (serial FP64 C, scatter face loops) on a 200x200x25 slab of graded200 "
+              f"({case.n_cells} cells), {args.warmup} warm-up + {args.steps} timed steps, "
+              f"{iters} PCG iterations in {secs:.2f} s")
+    line = {"impl": "reference", "metric": METRIC, "value": value, "unit": UNIT, "n_gpus": args.gpus,
+            "steps": args.steps, "warmup": args.warmup, "ms_per_step": 1e3 * secs / max(args.steps, 1),
+            "higher_is_better": True, "scaling": "weak", "vs_baseline": None, "dtype": "f64",
+            "data": "synthetic", "config": {"workload": WORKLOAD, "sample": "200x200x25 slab"},
+            "cpu_baseline": {"value": value, "unit": UNIT, "cores": 1, "kind": "oracle", "sample": sample},
+            "e2e": {"value": value, "unit": UNIT, "h2d_bytes_per_step": 0, "d2h_bytes_per_step": 0}}
+    print(json.dumps(line), flush=True)
+
+
+def time_device_resident(solver, B, torch, stream, n_steps: int):
+    ev0, ev1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+    torch.cuda.synchronize()
+    ev0.record(stream)
+    B.lfm_advance_async(solver.ctx, n_steps)
+    ev1.record(stream)
+    stats = solver.finish(n_steps)
+    torch.cuda.synchronize()
+    return ev0.elapsed_time(ev1) * 1e-3, stats
+
+
+def main_ours(args, world, rank, local):
+    import torch
+
+    from paper_2507_18268_gb300 import Solver
+    from paper_2507_18268_gb300 import binding as B
+    from paper_2507_18268_gb300.mesh import box_mesh, field_by_label
+
+    torch.cuda.set_device(local)
+    case = lapcase.graded_box(200)
+    mesh = box_mesh(case)
+    N, F = mesh.n_cells, mesh.n_faces
+    stream = torch.cuda.Stream(device=local)
+    hbm_peak, peak_kind = load_peaks()
+    K, W = args.steps, args.warmup
+
+    # ---- FP64, device-resident --------------------------------------------------------
+    s64 = Solver.from_case(case, mesh=mesh, device=local, stream=stream)
+    s64.advance(W)
+    clocks = ClockSampler(local)
+    barrier(world)
+    torch.cuda.synchronize()
+    if rank == 0:
+        clocks.start()
+    secs, st = time_device_resident(s64, B, torch, stream, K)
+    barrier(world)
+    clk = clocks.stop() if rank == 0 else None
+    iters = sum(x["iters"] for x in st)
+    assert all(x["converged"] for x in st), "FP64 step did not converge"
+    secs_max = reduce_max(secs, world)
+    cell_iters_all = reduce_sum(float(N) * iters, world)
+    value = cell_iters_all / secs_max
+    alg = algorithmic_bytes(N, F, iters, K, 0)
+    achieved_gbs = alg / secs / 1e9
+    ratio = load_traffic_ratio("graded200_fp64")
+    T64 = s64.field()
+    launch = s64.launch()
+
+    # ---- mixed precision, device-resident ------------------------------------------
+    mixed = None
+    if not args.no_mixed:
+        smx = Solver.from_case(case.with_(precision=B.LFM_MIXED), mesh=mesh, device=local, stream=stream)
+        smx.advance(W)
+        barrier(world)
+        msecs, mst = time_device_resident(smx, B, torch, stream, K)
+        barrier(world)
+        miters = sum(x["iters"] for x in mst)
+        assert all(x["converged"] for x in mst), "mixed step did not converge"
+        msecs_max = reduce_max(msecs, world)
+        mvalue = reduce_sum(float(N) * miters, world) / msecs_max
+        malg = algorithmic_bytes(N, F, miters, K, 1)
+        Tm = smx.field()
+        mratio = load_traffic_ratio("graded200_mixed")
+        mixed = {"value": mvalue, "unit": UNIT, "ms_per_step": 1e3 * msecs_max / K,
+                 "iters_per_step": miters / K, "sweeps_per_step": sum(x["sweeps"] for x in mst) / K,
+                 "speedup_vs_fp64_cell_steps": (secs_max / msecs_max),
+                 "max_rel_diff_vs_fp64": float(np.max(np.abs(Tm - T64) / np.abs(T64))),
+                 "roofline": {"bound": "hbm", "achieved": malg / msecs / 1e9, "peak": hbm_peak, "unit": "GB/s",
+                              "frac": malg / msecs / 1e9 / hbm_peak,
+                              "traffic": (mratio * malg / K) if mratio else None,
+                              "per": "one step (one launch runs all timed steps)"}}
+        smx.close()
+
+    # ---- end to end through the public API with pinned host buffers ---------------
+    e2e = None
+    if not args.no_e2e:
+        T_host = torch.empty(N, dtype=torch.float64).pin_memory().numpy()
+        T_host[:] = field_by_label(case, mesh)
+        s64.set_field(T_host)
+        s64.advance(W)
+        T_host[:] = s64.field()
+        barrier(world)
+        torch.cuda.synchronize()
+        t0 = time.perf_counter()
+        eiters = 0
+        for _ in range(K):
+            B.lfm_set_field(s64.ctx, T_host)
+            est = B.lfm_advance(s64.ctx, 1)
+            B.lfm_get_field(s64.ctx, N, out=T_host)
+            eiters += est[0].iters
+        torch.cuda.synchronize()
+        esecs = time.perf_counter() - t0
+        barrier(world)
+        esecs_max = reduce_max(esecs, world)
+        e2e = {"value": reduce_sum(float(N) * eiters, world) / esecs_max, "unit": UNIT,
+               "h2d_bytes_per_step": 8 * N, "d2h_bytes_per_step": 8 * N + 40 + 4,
+               "ms_per_step": 1e3 * esecs_max / K}
+    s64.close()
+
+    # ---- CPU baseline: the oracle on a bounded sample -------------------------------
+    cpu = None
+    if rank == 0 and not args.no_cpu_baseline:
+        cb_case = reference_slab_case()
+        cb_steps = 20
+        cval, csecs, citers = run_cpu_oracle(cb_case, cb_steps)
+        cpu = {"value": cval, "unit": UNIT, "cores": 1, "kind": "oracle",
+               "sample": f"serial FP64 oracle, {cb_steps} steps of a 200x200x25 slab of graded200 "
+                         f"({cb_case.n_cells} cells, {citers} PCG iterations, {csecs:.1f} s)"}
+
+    if rank != 0:
+        return
+    line = {
+        "metric": METRIC, "value": value, "unit": UNIT, "n_gpus": world, "steps": K, "warmup": W,
+        "ms_per_step": 1e3 * secs_max / K, "higher_is_better": True, "scaling": "weak",
+        "vs_baseline": None, "dtype": "f64", "data": "synthetic",
+        "config": {"workload": WORKLOAD, "cells": N, "internal_faces": F, "precision": "fp64",
+                   "parallelism": f"replicas x{world}" if world > 1 else "single GPU",
+                   "l2": "inputs larger than L2 (~2 GB working set vs 129 MB L2); no flush",
+                   "launch": {"ctas": launch[0], "threads": launch[1]}},
+        "iters_per_step": iters / K,
+        "cell_steps_per_s": float(N) * K * world / secs_max,
+        "roofline": {"bound": "hbm", "achieved": achieved_gbs, "peak": hbm_peak, "unit": "GB/s",
+                     "frac": achieved_gbs / hbm_peak, "traffic": (ratio * alg / K) if ratio else None,
+                     "peak_kind": peak_kind, "kernel": "step_kernel_f64",
+                     "per": "one step (one launch runs all timed steps)"},
+        "gpu_launches": 1,
+        "clocks": clk,
+        "mixed": mixed,
+        "e2e": e2e,
+        "cpu_baseline": cpu,
+    }
+    print(json.dumps(line), flush=True)
+
+
+def main():
+    ap = argparse.ArgumentParser()
+    ap.add_argument("--gpus", type=int, default=1)
+    ap.add_argument("--steps", type=int, default=100)
+    ap.add_argument("--warmup", type=int, default=5)
+    ap.add_argument("--impl", default="ours", choices=["ours", "reference"])
+    ap.add_argument("--no-mixed", action="store_true")
+    ap.add_argument("--no-e2e", action="store_true")
+    ap.add_argument("--no-cpu-baseline", action="store_true")
+    args = ap.parse_args()
+    if args.warmup < 3:
+        ap.error("--warmup must be >= 3")
+    world, rank, local = dist_setup()
+    try:
+        if args.impl == "reference":
+            main_reference(args, world, rank)
+        else:
+            main_ours(args, world, rank, local)
+    finally:
+        if world > 1:
+            import torch.distributed as dist
+            dist.destroy_process_group()
+
+
+if __name__ == "__main__":
+    main()

@@ -1,0 +1,212 @@
+/*
+ * lapfoam.h -- C ABI of liblapfoam.so: one implicit-Euler time step of laplacianFoam
+ * (arXiv 2507.18268) on an NVIDIA GB300 (sm_103a).
+ *
+ * What a step computes (paper, section "The laplacianFoam application", Eq. (1) and the
+ * listing "laplacianFoam application"): the matrix of fvm::ddt(T) - fvm::laplacian(DT, T)
+ * is assembled in OpenFOAM's LDU face-addressed form (section "OpenFOAM": owner and
+ * neighbour per internal face, faces in upper-triangular order) and solved by the
+ * conjugate-gradient method with the diagonal preconditioner (section "Evaluation"),
+ * stopping on OpenFOAM's normFactor-scaled L1 residual.
+ *
+ * Conventions shared by every call:
+ *   - Every call returns an int status (LFM_OK = 0 or a negative LFM_E* code); no C++
+ *     exception crosses this boundary. lfm_last_error() gives a one-line reason.
+ *   - Host arrays passed in are read during the call only (deep copy); the caller keeps
+ *     ownership. Output arrays are caller-allocated host memory unless said otherwise.
+ *   - A context holds one case on one device and issues all its work on one CUDA stream
+ *     (the one passed to lfm_create; NULL = the legacy default stream). A context is not
+ *     thread-safe; distinct contexts may be used from distinct threads.
+ *   - Device memory is either a caller-bound workspace (lfm_bind_workspace, never freed by
+ *     the library) or allocated by the library at upload time and freed by lfm_destroy.
+ *   - Non-convergence within max_iter is reported in the step statistics, not as an error
+ *     (as OpenFOAM does). A singular search direction (|p.Ap| / normFactor < 1e-300) stops
+ *     the step and returns LFM_ESINGULAR; a non-finite residual returns LFM_ENONFINITE.
+ *   - Calls made out of order (advance before upload, ...) return LFM_ESTATE.
+ */
+#ifndef LAPFOAM_H
+#define LAPFOAM_H
+
+#include <stddef.h>
+#include <stdint.h>
+
+#ifdef __cplusplus
+extern "C" {
+#endif
+
+enum {
+  LFM_OK = 0,
+  LFM_EINVAL = -1,     /* bad argument or mesh (index out of range, owner >= neighbour, V <= 0, NaN) */
+  LFM_ENOMEM = -2,     /* workspace too small / device allocation failed / over budget */
+  LFM_ECUDA = -3,      /* a CUDA runtime call failed */
+  LFM_ESINGULAR = -4,  /* PCG met a singular search direction */
+  LFM_ENONFINITE = -5, /* residual became NaN/Inf */
+  LFM_ETIMEOUT = -6,   /* a device-side barrier wait gave up (kernel returned; context usable) */
+  LFM_ESTATE = -7      /* call out of order */
+};
+
+enum { LFM_FIXED_VALUE = 0, LFM_ZERO_GRADIENT = 1 };
+enum { LFM_FP64 = 0, LFM_MIXED = 1 };
+
+typedef struct lfm_ctx lfm_ctx;
+
+/*
+ * LDU mesh (section "OpenFOAM" of the paper: owner/neighbour face addressing).
+ *   owner[f] < neighbour[f] for every internal face f, faces sorted by (owner, neighbour)
+ *   (upper-triangular order). V[c] > 0 cell volumes, magSf[f] > 0 face areas,
+ *   deltaCoeffs[f] > 0 the inverse owner-to-neighbour centre distance.
+ *   Boundary faces are grouped in patches: patch p covers boundary faces
+ *   [patch_start[p], patch_start[p] + patch_size[p]) which must tile [0, n_bfaces) in order.
+ *   bface_cell[b] is the cell of boundary face b, bmagSf its area, bdeltaCoeffs the inverse
+ *   distance from the cell centre to the face centre.
+ * All arrays are host memory, int32 indices, float64 values.
+ */
+typedef struct {
+  int32_t n_cells, n_faces;
+  const int32_t *owner, *neighbour;
+  const double *V, *magSf, *deltaCoeffs;
+  int32_t n_patches;
+  const int32_t *patch_start, *patch_size;
+  int32_t n_bfaces;
+  const int32_t *bface_cell;
+  const double *bmagSf, *bdeltaCoeffs;
+} lfm_mesh;
+
+/* PCG controls. tol: stop when sum|r| / normFactor < tol; rel_tol > 0 also stops when the
+ * residual falls below rel_tol times the step's initial residual; max_iter caps and
+ * min_iter forces iterations (OpenFOAM defaults: 1000, 0). precision: LFM_FP64 or
+ * LFM_MIXED (FP32 matrix and vectors, FP64 dots / normFactor / convergence test / true
+ * residual, FP64 field updated by defect correction). */
+typedef struct {
+  double tol, rel_tol;
+  int32_t max_iter, min_iter, precision;
+} lfm_solver_opts;
+
+/* Per-step solver record. iters: PCG iterations (LFM_MIXED: inner FP32 iterations summed
+ * over the refinement sweeps); sweeps: LFM_MIXED refinement sweeps (LFM_FP64: 1, or 0 when
+ * the step needed no iteration); init_res / final_res: normFactor-scaled L1 residuals
+ * (LFM_MIXED: of the FP64 true residual b - A T). */
+typedef struct {
+  int32_t iters, converged, sweeps, status;
+  double init_res, final_res, norm_factor;
+} lfm_step_stats;
+
+/* Library version string. */
+const char *lfm_version(void);
+
+/* ---- host-only helpers (no device is touched) ------------------------------------- */
+
+/* Validates a mesh: index ranges, owner < neighbour, upper-triangular order, positive
+ * finite geometry, patches tiling the boundary faces. Returns LFM_OK or LFM_EINVAL with the
+ * reason in msg (msg may be NULL). */
+int lfm_mesh_check(const lfm_mesh *mesh, char *msg, size_t msg_len);
+
+/* Face-to-cell addressing of the paper's section "Code Porting" (lists of lists built once
+ * per mesh): for cell c, its owner-side faces are [own_start[c], own_start[c+1]) (faces are
+ * sorted by owner), and its neighbour-side faces are losort[lo_start[c] .. lo_start[c+1])
+ * in ascending face order. own_start, lo_start: n_cells+1 entries; losort: n_faces.
+ * Counting sort, O(n_cells + n_faces). Input must satisfy lfm_mesh_check. */
+int lfm_face_addressing(int32_t n_cells, int32_t n_faces, const int32_t *owner,
+                        const int32_t *neighbour, int32_t *own_start, int32_t *losort,
+                        int32_t *lo_start);
+
+/* ---- single-case context ----------------------------------------------------------- */
+
+/* Device bytes lfm_upload_mesh needs for this mesh: precision LFM_FP64 or LFM_MIXED for a
+ * workspace serving that precision only, any other value (e.g. -1) for one serving both.
+ * A library-owned workspace (no lfm_bind_workspace) always serves both. */
+size_t lfm_workspace_bytes(const lfm_mesh *mesh, int32_t precision);
+
+/* Creates a context on CUDA device `device`, issuing work on `cuda_stream` (a
+ * cudaStream_t; NULL = legacy default stream). */
+int lfm_create(lfm_ctx **out, int device, void *cuda_stream);
+
+/* Binds caller-owned device memory (at least lfm_workspace_bytes, 256-byte aligned) that
+ * upload carves all device arrays from. Must precede lfm_upload_mesh; never freed here. */
+int lfm_bind_workspace(lfm_ctx *ctx, void *dev_ptr, size_t bytes);
+
+/* Validates and uploads the mesh (deep copy), builds the face-to-cell addressing and the
+ * cell-side boundary-face lists. Resets DT to 0, every patch to zeroGradient, dt to 1,
+ * the solver to {1e-6, 0, 1000, 0, LFM_FP64} and T to 0. */
+int lfm_upload_mesh(lfm_ctx *ctx, const lfm_mesh *mesh);
+
+/* Diffusivity DT per internal face (DT_faces[n_faces]) and per boundary face
+ * (DT_bfaces[n_bfaces]); a NULL array takes the value `uniform`. Values must be finite
+ * and >= 0. */
+int lfm_set_diffusivity(lfm_ctx *ctx, double uniform, const double *DT_faces,
+                        const double *DT_bfaces);
+
+/* Patch type (LFM_FIXED_VALUE / LFM_ZERO_GRADIENT) and, for fixedValue, the boundary
+ * values: values[patch_size[patch]] or, when values is NULL, `uniform` on every face. */
+int lfm_set_patch(lfm_ctx *ctx, int32_t patch, int32_t type, const double *values,
+                  double uniform);
+
+/* Time step (finite, > 0). */
+int lfm_set_time_step(lfm_ctx *ctx, double dt);
+
+/* Solver controls (tol >= 0, rel_tol >= 0, max_iter >= 1, 0 <= min_iter <= max_iter). */
+int lfm_set_solver(lfm_ctx *ctx, const lfm_solver_opts *opts);
+
+/* Field T[n_cells] from host memory (stream-ordered copy; synchronises before return). */
+int lfm_set_field(lfm_ctx *ctx, const double *T);
+
+/* Field T from device memory of the same device (T_dev[n_cells], stream-ordered). */
+int lfm_set_field_device(lfm_ctx *ctx, const double *T_dev);
+
+/* Runs n_steps implicit steps on the device: per step assemble, initial residual and
+ * normFactor, PCG iterations, all inside device-side control flow; T_old <- T each step.
+ * Synchronises before return; out (host, n_steps records, may be NULL) receives the
+ * per-step statistics. */
+int lfm_advance(lfm_ctx *ctx, int32_t n_steps, lfm_step_stats *out);
+
+/* Enqueues n_steps like lfm_advance without waiting (statistics stay on the device until
+ * lfm_finish). At most one pending advance per context. */
+int lfm_advance_async(lfm_ctx *ctx, int32_t n_steps);
+
+/* 1 if the pending advance is still running, LFM_OK if done (or none pending). */
+int lfm_query(lfm_ctx *ctx);
+
+/* Waits for the pending advance, copies up to n records of statistics to out (may be
+ * NULL) and returns its status. */
+int lfm_finish(lfm_ctx *ctx, lfm_step_stats *out, int32_t n);
+
+/* Reads T[n_cells] to host memory and, when T_boundary is not NULL, the boundary-face
+ * values T_boundary[n_bfaces] (fixedValue: the set value; zeroGradient: the face cell's T),
+ * both computed on the device. Synchronises before return. */
+int lfm_get_field(lfm_ctx *ctx, double *T_out, double *T_boundary);
+
+/* Device pointer of the context's T[n_cells] (float64), valid until lfm_destroy. */
+int lfm_field_device_ptr(lfm_ctx *ctx, double **T_dev);
+
+/* Reads the assembled matrix of the current T (diag[n_cells], upper[n_faces],
+ * source[n_cells]) to host memory, running only the assembly. Diagnostic / test use. */
+int lfm_get_matrix(lfm_ctx *ctx, double *diag, double *upper, double *source);
+
+/* Launch configuration chosen by the tuner for this context: CTAs and threads per CTA. */
+int lfm_get_launch(lfm_ctx *ctx, int32_t *ctas, int32_t *threads);
+
+/* Overrides the launch configuration (ctas <= 0 or threads <= 0 restores the tuned one).
+ * ctas is clamped to what can be co-resident. */
+int lfm_set_launch(lfm_ctx *ctx, int32_t ctas, int32_t threads);
+
+/* Sets the device-side barrier wait limit in nanoseconds (default 2e9). When one wait
+ * runs out the kernel stops and the call returns LFM_ETIMEOUT; the context stays usable. */
+int lfm_set_barrier_timeout(lfm_ctx *ctx, uint64_t ns);
+
+/* Test hook: when cta >= 0, the next advance makes CTA `cta` leave the kernel before its
+ * first barrier arrival, so the other CTAs' waits run out and the advance returns
+ * LFM_ETIMEOUT (no fault, no hang: every wait is bounded). One-shot; needs >= 2 CTAs. */
+int lfm_debug_skip_arrival(lfm_ctx *ctx, int32_t cta);
+
+/* Destroys the context (frees library-owned device memory; never a bound workspace). */
+int lfm_destroy(lfm_ctx *ctx);
+
+/* Reason for the last non-OK return on this context (ctx may be NULL: the last error of
+ * a context-free call on this thread). */
+const char *lfm_last_error(const lfm_ctx *ctx);
+
+#ifdef __cplusplus
+}
+#endif
+
+#endif /* LAPFOAM_H */

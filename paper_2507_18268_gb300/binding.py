@@ -1,0 +1,312 @@
+"""ctypes binding of liblapfoam.so (include/lapfoam.h), same names as the C ABI.
+
+Argument marshalling only: every step of the time step runs in the CUDA library. Loading
+fails loudly when the library cannot be built or loaded; there is no fallback path.
+Functions raise :class:`LfmError` on a non-OK status (except where a status is the result,
+e.g. ``lfm_query``).
+"""
+from __future__ import annotations
+
+import ctypes
+from ctypes import POINTER, c_char_p, c_double, c_int, c_int32, c_size_t, c_uint64, c_void_p
+from typing import Optional, Sequence
+
+import numpy as np
+
+from . import _build
+
+LFM_OK, LFM_EINVAL, LFM_ENOMEM, LFM_ECUDA = 0, -1, -2, -3
+LFM_ESINGULAR, LFM_ENONFINITE, LFM_ETIMEOUT, LFM_ESTATE = -4, -5, -6, -7
+LFM_FIXED_VALUE, LFM_ZERO_GRADIENT = 0, 1
+LFM_FP64, LFM_MIXED = 0, 1
+LFM_BOTH = -1
+
+_NAMES = {0: "LFM_OK", -1: "LFM_EINVAL", -2: "LFM_ENOMEM", -3: "LFM_ECUDA", -4: "LFM_ESINGULAR",
+          -5: "LFM_ENONFINITE", -6: "LFM_ETIMEOUT", -7: "LFM_ESTATE"}
+
+
+class LfmError(RuntimeError):
+    def __init__(self, code: int, msg: str):
+        super().__init__(f"{_NAMES.get(code, code)}: {msg}")
+        self.code = code
+
+
+class lfm_mesh(ctypes.Structure):
+    _fields_ = [("n_cells", c_int32), ("n_faces", c_int32),
+                ("owner", POINTER(c_int32)), ("neighbour", POINTER(c_int32)),
+                ("V", POINTER(c_double)), ("magSf", POINTER(c_double)), ("deltaCoeffs", POINTER(c_double)),
+                ("n_patches", c_int32),
+                ("patch_start", POINTER(c_int32)), ("patch_size", POINTER(c_int32)),
+                ("n_bfaces", c_int32),
+                ("bface_cell", POINTER(c_int32)),
+                ("bmagSf", POINTER(c_double)), ("bdeltaCoeffs", POINTER(c_double))]
+
+
+class lfm_solver_opts(ctypes.Structure):
+    _fields_ = [("tol", c_double), ("rel_tol", c_double), ("max_iter", c_int32),
+                ("min_iter", c_int32), ("precision", c_int32)]
+
+
+class lfm_step_stats(ctypes.Structure):
+    _fields_ = [("iters", c_int32), ("converged", c_int32), ("sweeps", c_int32), ("status", c_int32),
+                ("init_res", c_double), ("final_res", c_double), ("norm_factor", c_double)]
+
+    def as_dict(self):
+        return {k: getattr(self, k) for k, _ in self._fields_}
+
+
+_ctx_p = c_void_p
+_SIGS = {
+    "lfm_version": ([], c_char_p),
+    "lfm_mesh_check": ([POINTER(lfm_mesh), c_char_p, c_size_t], c_int),
+    "lfm_face_addressing": ([c_int32, c_int32, POINTER(c_int32), POINTER(c_int32), POINTER(c_int32),
+                             POINTER(c_int32), POINTER(c_int32)], c_int),
+    "lfm_workspace_bytes": ([POINTER(lfm_mesh), c_int32], c_size_t),
+    "lfm_create": ([POINTER(_ctx_p), c_int, c_void_p], c_int),
+    "lfm_bind_workspace": ([_ctx_p, c_void_p, c_size_t], c_int),
+    "lfm_upload_mesh": ([_ctx_p, POINTER(lfm_mesh)], c_int),
+    "lfm_set_diffusivity": ([_ctx_p, c_double, POINTER(c_double), POINTER(c_double)], c_int),
+    "lfm_set_patch": ([_ctx_p, c_int32, c_int32, POINTER(c_double), c_double], c_int),
+    "lfm_set_time_step": ([_ctx_p, c_double], c_int),
+    "lfm_set_solver": ([_ctx_p, POINTER(lfm_solver_opts)], c_int),
+    "lfm_set_field": ([_ctx_p, POINTER(c_double)], c_int),
+    "lfm_set_field_device": ([_ctx_p, c_void_p], c_int),
+    "lfm_advance": ([_ctx_p, c_int32, POINTER(lfm_step_stats)], c_int),
+    "lfm_advance_async": ([_ctx_p, c_int32], c_int),
+    "lfm_query": ([_ctx_p], c_int),
+    "lfm_finish": ([_ctx_p, POINTER(lfm_step_stats), c_int32], c_int),
+    "lfm_get_field": ([_ctx_p, POINTER(c_double), POINTER(c_double)], c_int),
+    "lfm_field_device_ptr": ([_ctx_p, POINTER(c_void_p)], c_int),
+    "lfm_get_matrix": ([_ctx_p, POINTER(c_double), POINTER(c_double), POINTER(c_double)], c_int),
+    "lfm_get_launch": ([_ctx_p, POINTER(c_int32), POINTER(c_int32)], c_int),
+    "lfm_set_launch": ([_ctx_p, c_int32, c_int32], c_int),
+    "lfm_set_barrier_timeout": ([_ctx_p, c_uint64], c_int),
+    "lfm_debug_skip_arrival": ([_ctx_p, c_int32], c_int),
+    "lfm_destroy": ([_ctx_p], c_int),
+    "lfm_last_error": ([_ctx_p], c_char_p),
+}
+
+_lib = None
+
+
+def library_path() -> str:
+    return _build.LIB
+
+
+def load(build: bool = True) -> ctypes.CDLL:
+    """Loads liblapfoam.so (building it first when stale). Raises when that fails."""
+    global _lib
+    if _lib is None:
+        path = _build.build() if build else _build.LIB
+        lib = ctypes.CDLL(path)
+        for name, (args, res) in _SIGS.items():
+            fn = getattr(lib, name)
+            fn.argtypes = args
+            fn.restype = res
+        _lib = lib
+    return _lib
+
+
+def declared_symbols() -> Sequence[str]:
+    return list(_SIGS)
+
+
+def _err(ctx) -> str:
+    msg = load().lfm_last_error(ctx)
+    return msg.decode() if msg else ""
+
+
+def _check(rc: int, ctx=None) -> int:
+    if rc != LFM_OK:
+        raise LfmError(rc, _err(ctx))
+    return rc
+
+
+def _f64(a: Optional[np.ndarray]):
+    if a is None:
+        return None
+    a = np.ascontiguousarray(a, dtype=np.float64)
+    return a
+
+
+def _i32(a):
+    return np.ascontiguousarray(a, dtype=np.int32)
+
+
+def _ptr(a: Optional[np.ndarray], t):
+    if a is None:
+        return ctypes.cast(None, POINTER(t))
+    return a.ctypes.data_as(POINTER(t))
+
+
+class MeshArgs:
+    """Keeps the arrays of an ``lfm_mesh`` alive while the struct is in use."""
+
+    def __init__(self, m):
+        self.arrays = dict(owner=_i32(m.owner), neighbour=_i32(m.neighbour), V=_f64(m.V),
+                           magSf=_f64(m.magSf), deltaCoeffs=_f64(m.deltaCoeffs),
+                           patch_start=_i32(m.patch_start), patch_size=_i32(m.patch_size),
+                           bface_cell=_i32(m.bface_cell), bmagSf=_f64(m.bmagSf),
+                           bdeltaCoeffs=_f64(m.bdeltaCoeffs))
+        a = self.arrays
+        self.struct = lfm_mesh(int(m.n_cells), int(m.n_faces), _ptr(a["owner"], c_int32),
+                               _ptr(a["neighbour"], c_int32), _ptr(a["V"], c_double),
+                               _ptr(a["magSf"], c_double), _ptr(a["deltaCoeffs"], c_double),
+                               len(a["patch_start"]), _ptr(a["patch_start"], c_int32),
+                               _ptr(a["patch_size"], c_int32), int(m.n_bfaces),
+                               _ptr(a["bface_cell"], c_int32), _ptr(a["bmagSf"], c_double),
+                               _ptr(a["bdeltaCoeffs"], c_double))
+
+
+# ---- functions with the C names --------------------------------------------------------
+
+def lfm_version() -> str:
+    return load().lfm_version().decode()
+
+
+def lfm_mesh_check(mesh) -> str:
+    """'' when the mesh is valid, else the reason."""
+    args = MeshArgs(mesh)
+    buf = ctypes.create_string_buffer(512)
+    rc = load().lfm_mesh_check(ctypes.byref(args.struct), buf, 512)
+    return "" if rc == LFM_OK else buf.value.decode()
+
+
+def lfm_face_addressing(n_cells: int, owner, neighbour):
+    owner, neighbour = _i32(owner), _i32(neighbour)
+    F = len(owner)
+    own_start = np.empty(n_cells + 1, np.int32)
+    lo_start = np.empty(n_cells + 1, np.int32)
+    losort = np.empty(max(F, 1), np.int32)
+    _check(load().lfm_face_addressing(n_cells, F, _ptr(owner, c_int32), _ptr(neighbour, c_int32),
+                                      _ptr(own_start, c_int32), _ptr(losort, c_int32),
+                                      _ptr(lo_start, c_int32)))
+    return own_start, losort[:F], lo_start
+
+
+def lfm_workspace_bytes(mesh, precision: int = LFM_BOTH) -> int:
+    args = MeshArgs(mesh)
+    return int(load().lfm_workspace_bytes(ctypes.byref(args.struct), precision))
+
+
+def lfm_create(device: int = 0, stream: Optional[int] = None) -> c_void_p:
+    ctx = c_void_p()
+    _check(load().lfm_create(ctypes.byref(ctx), device, c_void_p(stream) if stream else None))
+    return ctx
+
+
+def lfm_bind_workspace(ctx, dev_ptr: int, nbytes: int):
+    _check(load().lfm_bind_workspace(ctx, c_void_p(dev_ptr), nbytes), ctx)
+
+
+def lfm_upload_mesh(ctx, mesh):
+    args = MeshArgs(mesh)
+    _check(load().lfm_upload_mesh(ctx, ctypes.byref(args.struct)), ctx)
+
+
+def lfm_set_diffusivity(ctx, uniform: float, DT_faces=None, DT_bfaces=None):
+    a, b = _f64(DT_faces), _f64(DT_bfaces)
+    _check(load().lfm_set_diffusivity(ctx, float(uniform), _ptr(a, c_double), _ptr(b, c_double)), ctx)
+
+
+def lfm_set_patch(ctx, patch: int, ptype: int, values=None, uniform: float = 0.0):
+    v = _f64(values)
+    _check(load().lfm_set_patch(ctx, patch, ptype, _ptr(v, c_double), float(uniform)), ctx)
+
+
+def lfm_set_time_step(ctx, dt: float):
+    _check(load().lfm_set_time_step(ctx, float(dt)), ctx)
+
+
+def lfm_set_solver(ctx, tol: float, rel_tol: float = 0.0, max_iter: int = 1000, min_iter: int = 0,
+                   precision: int = LFM_FP64):
+    o = lfm_solver_opts(float(tol), float(rel_tol), int(max_iter), int(min_iter), int(precision))
+    _check(load().lfm_set_solver(ctx, ctypes.byref(o)), ctx)
+
+
+def lfm_set_field(ctx, T: np.ndarray):
+    T = _f64(T)
+    _check(load().lfm_set_field(ctx, _ptr(T, c_double)), ctx)
+
+
+def lfm_set_field_device(ctx, dev_ptr: int):
+    _check(load().lfm_set_field_device(ctx, c_void_p(dev_ptr)), ctx)
+
+
+def lfm_advance(ctx, n_steps: int):
+    out = (lfm_step_stats * max(n_steps, 1))()
+    _check(load().lfm_advance(ctx, n_steps, out), ctx)
+    return [out[i] for i in range(n_steps)]
+
+
+def lfm_advance_async(ctx, n_steps: int):
+    _check(load().lfm_advance_async(ctx, n_steps), ctx)
+
+
+def lfm_query(ctx) -> int:
+    rc = load().lfm_query(ctx)
+    if rc < 0:
+        raise LfmError(rc, _err(ctx))
+    return rc
+
+
+def lfm_finish(ctx, n: int):
+    out = (lfm_step_stats * max(n, 1))()
+    rc = load().lfm_finish(ctx, out, n)
+    stats = [out[i] for i in range(n)]
+    if rc != LFM_OK:
+        raise LfmError(rc, _err(ctx))
+    return stats
+
+
+def lfm_finish_status(ctx, n: int):
+    """Like lfm_finish but returns (status, stats) instead of raising."""
+    out = (lfm_step_stats * max(n, 1))()
+    rc = load().lfm_finish(ctx, out, n)
+    return rc, [out[i] for i in range(n)]
+
+
+def lfm_get_field(ctx, n_cells: int, n_bfaces: int = 0, out: Optional[np.ndarray] = None,
+                  boundary: bool = False):
+    T = out if out is not None else np.empty(n_cells)
+    Tb = np.empty(n_bfaces) if boundary else None
+    _check(load().lfm_get_field(ctx, _ptr(T, c_double), _ptr(Tb, c_double)), ctx)
+    return (T, Tb) if boundary else T
+
+
+def lfm_field_device_ptr(ctx) -> int:
+    p = c_void_p()
+    _check(load().lfm_field_device_ptr(ctx, ctypes.byref(p)), ctx)
+    return int(p.value)
+
+
+def lfm_get_matrix(ctx, n_cells: int, n_faces: int):
+    d, u, s = np.empty(n_cells), np.empty(max(n_faces, 1)), np.empty(n_cells)
+    _check(load().lfm_get_matrix(ctx, _ptr(d, c_double), _ptr(u, c_double), _ptr(s, c_double)), ctx)
+    return d, u[:n_faces], s
+
+
+def lfm_get_launch(ctx):
+    a, b = c_int32(), c_int32()
+    _check(load().lfm_get_launch(ctx, ctypes.byref(a), ctypes.byref(b)), ctx)
+    return a.value, b.value
+
+
+def lfm_set_launch(ctx, ctas: int, threads: int):
+    _check(load().lfm_set_launch(ctx, int(ctas), int(threads)), ctx)
+
+
+def lfm_set_barrier_timeout(ctx, ns: int):
+    _check(load().lfm_set_barrier_timeout(ctx, int(ns)), ctx)
+
+
+def lfm_debug_skip_arrival(ctx, cta: int):
+    _check(load().lfm_debug_skip_arrival(ctx, int(cta)), ctx)
+
+
+def lfm_destroy(ctx):
+    load().lfm_destroy(ctx)
+
+
+def lfm_last_error(ctx=None) -> str:
+    return _err(ctx)

@@ -1,0 +1,757 @@
+// Host side of the C ABI declared in include/lapfoam.h: mesh validation, the face-to-cell
+// addressing, workspace layout, uploads and the advance calls.
+#include <cmath>
+#include <cstdarg>
+#include <cstdio>
+#include <cstring>
+#include <algorithm>
+#include <new>
+#include <string>
+#include <vector>
+
+#include <cuda_runtime.h>
+
+#include "lfm_internal.h"
+
+using namespace lfm;
+
+namespace {
+
+thread_local std::string g_last_error;
+
+int fail_free(int code, const char* fmt, ...) {
+  char buf[512];
+  va_list ap;
+  va_start(ap, fmt);
+  vsnprintf(buf, sizeof buf, fmt, ap);
+  va_end(ap);
+  g_last_error = buf;
+  return code;
+}
+
+size_t align_up(size_t v, size_t a) { return (v + a - 1) / a * a; }
+
+// Byte layout of a case's workspace. Offsets are relative to the workspace base.
+struct Layout {
+  size_t sync, partials, stats;
+  size_t nbr, own_start, losort, lo_start, lo_other, b_start, b_face, bcell, btype;
+  size_t V, magSf, delta, DT, bmagSf, bdelta, bDT, bval;
+  size_t diag, upper, src, rD, x, r, w, p, q, Tb;
+  size_t diag32, upper32, rD32, dx32, r32, w32, p32, q32;
+  size_t total;
+};
+
+// kind: LFM_FP64 (FP64 solver vectors), LFM_MIXED (FP32 matrix copy + FP32 vectors) or
+// kLayoutBoth (both sets, so that the precision may change after upload).
+constexpr int kLayoutBoth = -1;
+
+Layout make_layout(int64_t N, int64_t F, int64_t NB, int kind) {
+  Layout L{};
+  size_t o = 0;
+  auto take = [&](size_t bytes) {
+    size_t at = o;
+    o = align_up(o + (bytes ? bytes : 1), 256);
+    return at;
+  };
+  L.sync = take(sizeof(SyncWords));
+  L.partials = take(sizeof(double) * kMaxCtas * kMaxSums);
+  L.stats = take(sizeof(lfm_step_stats) * kStatsCap);
+  L.nbr = take(4 * F);
+  L.own_start = take(4 * (N + 1));
+  L.losort = take(4 * F);
+  L.lo_start = take(4 * (N + 1));
+  L.lo_other = take(4 * F);
+  L.b_start = take(4 * (N + 1));
+  L.b_face = take(4 * NB);
+  L.bcell = take(4 * NB);
+  L.btype = take(4 * NB);
+  L.V = take(8 * N);
+  L.magSf = take(8 * F);
+  L.delta = take(8 * F);
+  L.DT = take(8 * F);
+  L.bmagSf = take(8 * NB);
+  L.bdelta = take(8 * NB);
+  L.bDT = take(8 * NB);
+  L.bval = take(8 * NB);
+  L.diag = take(8 * N);
+  L.upper = take(8 * F);
+  L.src = take(8 * N);
+  L.rD = take(8 * N);
+  L.x = take(8 * N);
+  L.Tb = take(8 * NB);
+  L.r = L.w = L.p = L.q = 0;
+  L.diag32 = L.upper32 = L.rD32 = L.dx32 = L.r32 = L.w32 = L.p32 = L.q32 = 0;
+  if (kind == LFM_FP64 || kind == kLayoutBoth) {
+    L.r = take(8 * N);
+    L.w = take(8 * N);
+    L.p = take(8 * N);
+    L.q = take(8 * N);
+  }
+  if (kind == LFM_MIXED || kind == kLayoutBoth) {
+    L.diag32 = take(4 * N);
+    L.upper32 = take(4 * F);
+    L.rD32 = take(4 * N);
+    L.dx32 = take(4 * N);
+    L.r32 = take(4 * N);
+    L.w32 = take(4 * N);
+    L.p32 = take(4 * N);
+    L.q32 = take(4 * N);
+  }
+  L.total = o;
+  return L;
+}
+
+struct DeviceGuard {
+  int prev = -1;
+  explicit DeviceGuard(int dev) {
+    if (cudaGetDevice(&prev) != cudaSuccess) prev = -1;
+    if (prev != dev) cudaSetDevice(dev);
+  }
+  ~DeviceGuard() {
+    int cur = -1;
+    if (prev >= 0 && cudaGetDevice(&cur) == cudaSuccess && cur != prev) cudaSetDevice(prev);
+  }
+};
+
+}  // namespace
+
+struct lfm_ctx {
+  int device = 0;
+  cudaStream_t stream = nullptr;
+  std::string err;
+
+  // workspace
+  char* ws = nullptr;
+  size_t ws_bytes = 0;
+  bool ws_owned = false;
+  bool ws_bound = false;
+
+  // case
+  bool uploaded = false;
+  int32_t N = 0, F = 0, NB = 0;
+  int32_t n_patches = 0;
+  std::vector<int32_t> patch_start, patch_size, patch_type;
+  Layout lay{};
+  CaseDev cs{};
+
+  // controls
+  double dt = 1.0;
+  lfm_solver_opts opts{1e-6, 0.0, 1000, 0, LFM_FP64};
+  bool has64 = false, has32 = false;  // solver blocks present in the workspace
+
+  // launch
+  int tuned_ctas = 1, tuned_threads = 512;
+  int ctas = 0, threads = 0;  // overrides (0 = tuned)
+  uint64_t timeout_ns = 2000000000ull;
+  int skip_cta = -1;
+
+  // async state
+  lfm_step_stats* h_stats = nullptr;  // pinned, kStatsCap records
+  int32_t* h_status = nullptr;        // pinned
+  cudaEvent_t done = nullptr;
+  int pending_steps = 0;
+  int pending_remaining = 0;
+  std::vector<lfm_step_stats> stats_acc;
+};
+
+namespace {
+
+int fail(lfm_ctx* c, int code, const char* fmt, ...) {
+  char buf[512];
+  va_list ap;
+  va_start(ap, fmt);
+  vsnprintf(buf, sizeof buf, fmt, ap);
+  va_end(ap);
+  if (c) c->err = buf;
+  g_last_error = buf;
+  return code;
+}
+
+int cuda_fail(lfm_ctx* c, cudaError_t e, const char* what) {
+  return fail(c, LFM_ECUDA, "%s: %s", what, cudaGetErrorString(e));
+}
+
+#define CK(ctx, call)                                        \
+  do {                                                       \
+    cudaError_t e_ = (call);                                 \
+    if (e_ != cudaSuccess) return cuda_fail(ctx, e_, #call); \
+  } while (0)
+
+int set_why(std::string& why, const char* fmt, ...) {
+  char buf[256];
+  va_list ap;
+  va_start(ap, fmt);
+  vsnprintf(buf, sizeof buf, fmt, ap);
+  va_end(ap);
+  why = buf;
+  return LFM_EINVAL;
+}
+
+int check_mesh(const lfm_mesh* m, std::string& why) {
+  if (!m) return set_why(why, "mesh is NULL");
+  if (m->n_cells <= 0) return set_why(why, "n_cells must be > 0 (got %d)", m->n_cells);
+  if (m->n_faces < 0 || m->n_bfaces < 0 || m->n_patches < 0)
+    return set_why(why, "negative face or patch count (%d, %d, %d)", m->n_faces, m->n_bfaces, m->n_patches);
+  if (m->n_faces > 0 && (!m->owner || !m->neighbour || !m->magSf || !m->deltaCoeffs))
+    return set_why(why, "internal-face arrays missing");
+  if (!m->V) return set_why(why, "V missing");
+  if (m->n_bfaces > 0 && (!m->bface_cell || !m->bmagSf || !m->bdeltaCoeffs))
+    return set_why(why, "boundary-face arrays missing");
+  if (m->n_patches > 0 && (!m->patch_start || !m->patch_size)) return set_why(why, "patch arrays missing");
+  const int64_t N = m->n_cells;
+  for (int64_t c = 0; c < N; ++c)
+    if (!(std::isfinite(m->V[c]) && m->V[c] > 0)) return set_why(why, "V[%lld] not finite and > 0", (long long)c);
+  for (int64_t f = 0; f < m->n_faces; ++f) {
+    int32_t o = m->owner[f], n = m->neighbour[f];
+    if (o < 0 || o >= N || n < 0 || n >= N) return set_why(why, "face %lld: cell index out of range", (long long)f);
+    if (o >= n) return set_why(why, "face %lld: owner %d >= neighbour %d", (long long)f, o, n);
+    if (f > 0) {
+      int32_t po = m->owner[f - 1], pn = m->neighbour[f - 1];
+      if (po > o || (po == o && pn >= n)) return set_why(why, "face %lld breaks upper-triangular order", (long long)f);
+    }
+    if (!(std::isfinite(m->magSf[f]) && m->magSf[f] > 0)) return set_why(why, "magSf[%lld] not finite and > 0", (long long)f);
+    if (!(std::isfinite(m->deltaCoeffs[f]) && m->deltaCoeffs[f] > 0))
+      return set_why(why, "deltaCoeffs[%lld] not finite and > 0", (long long)f);
+  }
+  for (int64_t b = 0; b < m->n_bfaces; ++b) {
+    int32_t c = m->bface_cell[b];
+    if (c < 0 || c >= N) return set_why(why, "boundary face %lld: cell %d out of range", (long long)b, c);
+    if (!(std::isfinite(m->bmagSf[b]) && m->bmagSf[b] > 0)) return set_why(why, "bmagSf[%lld] not finite and > 0", (long long)b);
+    if (!(std::isfinite(m->bdeltaCoeffs[b]) && m->bdeltaCoeffs[b] > 0))
+      return set_why(why, "bdeltaCoeffs[%lld] not finite and > 0", (long long)b);
+  }
+  int64_t at = 0;
+  for (int32_t p = 0; p < m->n_patches; ++p) {
+    if (m->patch_start[p] != at || m->patch_size[p] < 0)
+      return set_why(why, "patch %d does not continue the boundary faces at %lld", p, (long long)at);
+    at += m->patch_size[p];
+  }
+  if (at != m->n_bfaces) return set_why(why, "patches cover %lld of %d boundary faces", (long long)at, m->n_bfaces);
+  return LFM_OK;
+}
+
+// Counting sort by key (stable): start[k] .. start[k+1] index the items with key k, in
+// ascending item order.
+void bucket(int32_t n_keys, int64_t n_items, const int32_t* key, int32_t* start, int32_t* order) {
+  std::fill(start, start + n_keys + 1, 0);
+  for (int64_t i = 0; i < n_items; ++i) ++start[key[i] + 1];
+  for (int32_t k = 0; k < n_keys; ++k) start[k + 1] += start[k];
+  std::vector<int32_t> fill(start, start + n_keys);
+  for (int64_t i = 0; i < n_items; ++i) order[fill[key[i]]++] = (int32_t)i;
+}
+
+template <class T>
+int h2d(lfm_ctx* c, size_t off, const T* src, size_t n) {
+  if (n == 0) return LFM_OK;
+  CK(c, cudaMemcpyAsync(c->ws + off, src, sizeof(T) * n, cudaMemcpyHostToDevice, c->stream));
+  return LFM_OK;
+}
+
+int choose_launch(lfm_ctx* c) {
+  const int threads = 512;
+  int maxc = max_coresident_ctas(c->opts.precision, threads, c->device);
+  if (maxc <= 0) return fail(c, LFM_ECUDA, "cannot size the cooperative launch");
+  int64_t want = ((int64_t)c->N + 4095) / 4096;
+  if (want < 1) want = 1;
+  if (want > maxc) want = maxc;
+  c->tuned_ctas = (int)want;
+  c->tuned_threads = threads;
+  return LFM_OK;
+}
+
+Launch current_launch(lfm_ctx* c, int& err) {
+  Launch L{};
+  L.threads = c->threads > 0 ? c->threads : c->tuned_threads;
+  int maxc = max_coresident_ctas(c->opts.precision, L.threads, c->device);
+  L.ctas = c->ctas > 0 ? c->ctas : c->tuned_ctas;
+  if (L.ctas > maxc) L.ctas = maxc;
+  err = L.ctas <= 0 ? 1 : 0;
+  L.timeout_ns = c->timeout_ns;
+  L.skip_cta = c->skip_cta;
+  return L;
+}
+
+void refresh_case(lfm_ctx* c) {
+  CaseDev& cs = c->cs;
+  cs.dt = c->dt;
+  cs.tol = c->opts.tol;
+  cs.rel_tol = c->opts.rel_tol;
+  cs.max_iter = c->opts.max_iter;
+  cs.min_iter = c->opts.min_iter;
+  cs.precision = c->opts.precision;
+}
+
+void bind_pointers(lfm_ctx* c) {
+  const Layout& L = c->lay;
+  char* b = c->ws;
+  CaseDev& cs = c->cs;
+  cs.N = c->N;
+  cs.F = c->F;
+  cs.NB = c->NB;
+  cs.sync = reinterpret_cast<SyncWords*>(b + L.sync);
+  cs.partials = reinterpret_cast<double*>(b + L.partials);
+  cs.stats = reinterpret_cast<lfm_step_stats*>(b + L.stats);
+  cs.nbr = reinterpret_cast<const int32_t*>(b + L.nbr);
+  cs.own_start = reinterpret_cast<const int32_t*>(b + L.own_start);
+  cs.losort = reinterpret_cast<const int32_t*>(b + L.losort);
+  cs.lo_start = reinterpret_cast<const int32_t*>(b + L.lo_start);
+  cs.lo_other = reinterpret_cast<const int32_t*>(b + L.lo_other);
+  cs.b_start = reinterpret_cast<const int32_t*>(b + L.b_start);
+  cs.b_face = reinterpret_cast<const int32_t*>(b + L.b_face);
+  cs.bcell = reinterpret_cast<const int32_t*>(b + L.bcell);
+  cs.btype = reinterpret_cast<const int32_t*>(b + L.btype);
+  cs.V = reinterpret_cast<const double*>(b + L.V);
+  cs.magSf = reinterpret_cast<const double*>(b + L.magSf);
+  cs.delta = reinterpret_cast<const double*>(b + L.delta);
+  cs.DT = reinterpret_cast<const double*>(b + L.DT);
+  cs.bmagSf = reinterpret_cast<const double*>(b + L.bmagSf);
+  cs.bdelta = reinterpret_cast<const double*>(b + L.bdelta);
+  cs.bDT = reinterpret_cast<const double*>(b + L.bDT);
+  cs.bval = reinterpret_cast<const double*>(b + L.bval);
+  cs.diag = reinterpret_cast<double*>(b + L.diag);
+  cs.upper = reinterpret_cast<double*>(b + L.upper);
+  cs.src = reinterpret_cast<double*>(b + L.src);
+  cs.rD = reinterpret_cast<double*>(b + L.rD);
+  cs.x = reinterpret_cast<double*>(b + L.x);
+  const bool d = c->has64, m = c->has32;
+  cs.r = d ? reinterpret_cast<double*>(b + L.r) : nullptr;
+  cs.w = d ? reinterpret_cast<double*>(b + L.w) : nullptr;
+  cs.p = d ? reinterpret_cast<double*>(b + L.p) : nullptr;
+  cs.q = d ? reinterpret_cast<double*>(b + L.q) : nullptr;
+  cs.diag32 = m ? reinterpret_cast<float*>(b + L.diag32) : nullptr;
+  cs.upper32 = m ? reinterpret_cast<float*>(b + L.upper32) : nullptr;
+  cs.rD32 = m ? reinterpret_cast<float*>(b + L.rD32) : nullptr;
+  cs.dx32 = m ? reinterpret_cast<float*>(b + L.dx32) : nullptr;
+  cs.r32 = m ? reinterpret_cast<float*>(b + L.r32) : nullptr;
+  cs.w32 = m ? reinterpret_cast<float*>(b + L.w32) : nullptr;
+  cs.p32 = m ? reinterpret_cast<float*>(b + L.p32) : nullptr;
+  cs.q32 = m ? reinterpret_cast<float*>(b + L.q32) : nullptr;
+}
+
+int need_uploaded(lfm_ctx* c) {
+  if (!c) return fail_free(LFM_EINVAL, "context is NULL");
+  if (!c->uploaded) return fail(c, LFM_ESTATE, "no mesh uploaded");
+  return LFM_OK;
+}
+
+// Enqueues one launch of `steps` steps (<= kStatsCap) and the copy-back of its statistics
+// and status into pinned host memory.
+int enqueue_chunk(lfm_ctx* c, int steps, int mode) {
+  refresh_case(c);
+  int e = 0;
+  Launch L = current_launch(c, e);
+  if (e) return fail(c, LFM_ECUDA, "no co-resident CTA fits the step kernel");
+  if (L.skip_cta >= 0 && L.ctas < 2) return fail(c, LFM_EINVAL, "the skip-arrival hook needs >= 2 CTAs");
+  CK(c, cudaMemsetAsync(c->cs.sync, 0, sizeof(SyncWords), c->stream));
+  CK(c, launch_steps(c->cs, L, steps, mode, c->stream));
+  c->skip_cta = -1;
+  if (steps > 0)
+    CK(c, cudaMemcpyAsync(c->h_stats, c->cs.stats, sizeof(lfm_step_stats) * steps, cudaMemcpyDeviceToHost,
+                          c->stream));
+  CK(c, cudaMemcpyAsync(c->h_status, &c->cs.sync->status, sizeof(int32_t), cudaMemcpyDeviceToHost, c->stream));
+  CK(c, cudaEventRecord(c->done, c->stream));
+  return LFM_OK;
+}
+
+// Waits for the enqueued chunk, appends its statistics, maps the device status.
+int collect_chunk(lfm_ctx* c, int steps) {
+  CK(c, cudaEventSynchronize(c->done));
+  for (int i = 0; i < steps; ++i) c->stats_acc.push_back(c->h_stats[i]);
+  int32_t st = *c->h_status;
+  if (st == LFM_ETIMEOUT) return fail(c, LFM_ETIMEOUT, "a device barrier wait ran out (kernel stopped)");
+  if (st == LFM_ESINGULAR) return fail(c, LFM_ESINGULAR, "PCG met a singular search direction");
+  if (st == LFM_ENONFINITE) return fail(c, LFM_ENONFINITE, "PCG residual became non-finite");
+  if (st != 0) return fail(c, LFM_ECUDA, "device status %d", (int)st);
+  return LFM_OK;
+}
+
+}  // namespace
+
+extern "C" {
+
+const char* lfm_version(void) { return "lapfoam-gb300 0.1 (sm_103a)"; }
+
+int lfm_mesh_check(const lfm_mesh* mesh, char* msg, size_t msg_len) {
+  std::string why;
+  int rc = check_mesh(mesh, why);
+  if (msg && msg_len) {
+    snprintf(msg, msg_len, "%s", rc == LFM_OK ? "" : why.c_str());
+  }
+  if (rc != LFM_OK) g_last_error = why;
+  return rc;
+}
+
+int lfm_face_addressing(int32_t n_cells, int32_t n_faces, const int32_t* owner, const int32_t* neighbour,
+                        int32_t* own_start, int32_t* losort, int32_t* lo_start) {
+  if (n_cells <= 0 || n_faces < 0 || (n_faces > 0 && (!owner || !neighbour)) || !own_start || !lo_start ||
+      (n_faces > 0 && !losort))
+    return fail_free(LFM_EINVAL, "lfm_face_addressing: bad arguments");
+  for (int32_t f = 0; f < n_faces; ++f) {
+    if (owner[f] < 0 || owner[f] >= n_cells || neighbour[f] <= owner[f] || neighbour[f] >= n_cells)
+      return fail_free(LFM_EINVAL, "lfm_face_addressing: face %d out of range or owner >= neighbour", f);
+    if (f > 0 && owner[f] < owner[f - 1])
+      return fail_free(LFM_EINVAL, "lfm_face_addressing: faces not sorted by owner at %d", f);
+  }
+  std::vector<int32_t> order(n_faces > 0 ? n_faces : 1);
+  bucket(n_cells, n_faces, owner, own_start, order.data());  // identity order: faces sorted by owner
+  bucket(n_cells, n_faces, neighbour, lo_start, losort);
+  return LFM_OK;
+}
+
+size_t lfm_workspace_bytes(const lfm_mesh* mesh, int32_t precision) {
+  if (!mesh || mesh->n_cells <= 0) return 0;
+  if (precision != LFM_FP64 && precision != LFM_MIXED) precision = kLayoutBoth;
+  return make_layout(mesh->n_cells, mesh->n_faces, mesh->n_bfaces, precision).total;
+}
+
+int lfm_create(lfm_ctx** out, int device, void* cuda_stream) {
+  if (!out) return fail_free(LFM_EINVAL, "lfm_create: out is NULL");
+  *out = nullptr;
+  int n = 0;
+  cudaError_t e = cudaGetDeviceCount(&n);
+  if (e != cudaSuccess || n == 0) return fail_free(LFM_ECUDA, "no CUDA device (%s)", cudaGetErrorString(e));
+  if (device < 0 || device >= n) return fail_free(LFM_EINVAL, "device %d out of range", device);
+  lfm_ctx* c = new (std::nothrow) lfm_ctx;
+  if (!c) return fail_free(LFM_ENOMEM, "out of host memory");
+  c->device = device;
+  c->stream = static_cast<cudaStream_t>(cuda_stream);
+  DeviceGuard g(device);
+  if (cudaMallocHost(&c->h_stats, sizeof(lfm_step_stats) * kStatsCap) != cudaSuccess ||
+      cudaMallocHost(&c->h_status, sizeof(int32_t)) != cudaSuccess ||
+      cudaEventCreateWithFlags(&c->done, cudaEventDisableTiming) != cudaSuccess) {
+    lfm_destroy(c);
+    return fail_free(LFM_ECUDA, "lfm_create: host staging or event allocation failed");
+  }
+  *out = c;
+  return LFM_OK;
+}
+
+int lfm_bind_workspace(lfm_ctx* c, void* dev_ptr, size_t bytes) {
+  if (!c) return fail_free(LFM_EINVAL, "context is NULL");
+  if (c->uploaded) return fail(c, LFM_ESTATE, "bind the workspace before uploading a mesh");
+  if (!dev_ptr || (reinterpret_cast<uintptr_t>(dev_ptr) & 255)) return fail(c, LFM_EINVAL, "workspace must be 256-byte aligned");
+  c->ws = static_cast<char*>(dev_ptr);
+  c->ws_bytes = bytes;
+  c->ws_bound = true;
+  c->ws_owned = false;
+  return LFM_OK;
+}
+
+int lfm_upload_mesh(lfm_ctx* c, const lfm_mesh* m) {
+  if (!c) return fail_free(LFM_EINVAL, "context is NULL");
+  std::string why;
+  if (check_mesh(m, why) != LFM_OK) return fail(c, LFM_EINVAL, "%s", why.c_str());
+  DeviceGuard g(c->device);
+  // A bound workspace gets the largest layout it holds (both solver blocks, else FP64,
+  // else mixed); a library-owned one holds both.
+  const Layout Lb = make_layout(m->n_cells, m->n_faces, m->n_bfaces, kLayoutBoth);
+  const Layout L64 = make_layout(m->n_cells, m->n_faces, m->n_bfaces, LFM_FP64);
+  const Layout L32 = make_layout(m->n_cells, m->n_faces, m->n_bfaces, LFM_MIXED);
+  Layout use = Lb;
+  bool has64 = true, has32 = true;
+  if (c->ws_bound) {
+    if (c->ws_bytes >= Lb.total) {
+    } else if (c->ws_bytes >= L64.total) {
+      use = L64;
+      has32 = false;
+    } else if (c->ws_bytes >= L32.total) {
+      use = L32;
+      has64 = false;
+    } else {
+      return fail(c, LFM_ENOMEM, "workspace has %zu bytes, needs %zu", c->ws_bytes, L32.total);
+    }
+  } else {
+    if (c->ws_owned && c->ws) {
+      cudaFree(c->ws);
+      c->ws = nullptr;
+    }
+    void* p = nullptr;
+    cudaError_t e = cudaMalloc(&p, use.total);
+    if (e != cudaSuccess) return fail(c, LFM_ENOMEM, "device allocation of %zu bytes failed: %s", use.total, cudaGetErrorString(e));
+    c->ws = static_cast<char*>(p);
+    c->ws_bytes = use.total;
+    c->ws_owned = true;
+  }
+  c->lay = use;
+  c->N = m->n_cells;
+  c->F = m->n_faces;
+  c->NB = m->n_bfaces;
+  c->has64 = has64;
+  c->has32 = has32;
+  c->n_patches = m->n_patches;
+  c->patch_start.assign(m->patch_start, m->patch_start + m->n_patches);
+  c->patch_size.assign(m->patch_size, m->patch_size + m->n_patches);
+  c->patch_type.assign(m->n_patches, LFM_ZERO_GRADIENT);
+  bind_pointers(c);
+
+  const int32_t N = c->N, F = c->F, NB = c->NB;
+  std::vector<int32_t> own_start(N + 1), lo_start(N + 1), losort(F > 0 ? F : 1), lo_other(F > 0 ? F : 1);
+  int rc = lfm_face_addressing(N, F, m->owner, m->neighbour, own_start.data(), losort.data(), lo_start.data());
+  if (rc != LFM_OK) return fail(c, rc, "%s", g_last_error.c_str());
+  for (int32_t i = 0; i < F; ++i) lo_other[i] = m->owner[losort[i]];
+  std::vector<int32_t> b_start(N + 1), b_face(NB > 0 ? NB : 1);
+  bucket(N, NB, m->bface_cell, b_start.data(), b_face.data());
+  std::vector<int32_t> btype(NB > 0 ? NB : 1, LFM_ZERO_GRADIENT);
+  std::vector<double> zeros_b(NB > 0 ? NB : 1, 0.0);
+
+  const Layout& Y = c->lay;
+  if ((rc = h2d(c, Y.nbr, m->neighbour, F)) || (rc = h2d(c, Y.own_start, own_start.data(), N + 1)) ||
+      (rc = h2d(c, Y.losort, losort.data(), F)) || (rc = h2d(c, Y.lo_start, lo_start.data(), N + 1)) ||
+      (rc = h2d(c, Y.lo_other, lo_other.data(), F)) || (rc = h2d(c, Y.b_start, b_start.data(), N + 1)) ||
+      (rc = h2d(c, Y.b_face, b_face.data(), NB)) || (rc = h2d(c, Y.bcell, m->bface_cell, NB)) ||
+      (rc = h2d(c, Y.btype, btype.data(), NB)) || (rc = h2d(c, Y.V, m->V, N)) ||
+      (rc = h2d(c, Y.magSf, m->magSf, F)) || (rc = h2d(c, Y.delta, m->deltaCoeffs, F)) ||
+      (rc = h2d(c, Y.bmagSf, m->bmagSf, NB)) || (rc = h2d(c, Y.bdelta, m->bdeltaCoeffs, NB)) ||
+      (rc = h2d(c, Y.bDT, zeros_b.data(), NB)) || (rc = h2d(c, Y.bval, zeros_b.data(), NB)))
+    return rc;
+  CK(c, cudaMemsetAsync(c->ws + Y.DT, 0, sizeof(double) * (F > 0 ? F : 1), c->stream));
+  CK(c, cudaMemsetAsync(c->ws + Y.x, 0, sizeof(double) * N, c->stream));
+  CK(c, cudaStreamSynchronize(c->stream));
+  c->dt = 1.0;
+  c->opts = lfm_solver_opts{1e-6, 0.0, 1000, 0, has64 ? LFM_FP64 : LFM_MIXED};
+  c->uploaded = true;
+  c->ctas = c->threads = 0;
+  return choose_launch(c);
+}
+
+int lfm_set_diffusivity(lfm_ctx* c, double uniform, const double* DT_faces, const double* DT_bfaces) {
+  int rc = need_uploaded(c);
+  if (rc) return rc;
+  if (!(std::isfinite(uniform) && uniform >= 0)) return fail(c, LFM_EINVAL, "uniform DT must be finite and >= 0");
+  for (int32_t f = 0; DT_faces && f < c->F; ++f)
+    if (!(std::isfinite(DT_faces[f]) && DT_faces[f] >= 0)) return fail(c, LFM_EINVAL, "DT_faces[%d] must be finite and >= 0", f);
+  for (int32_t b = 0; DT_bfaces && b < c->NB; ++b)
+    if (!(std::isfinite(DT_bfaces[b]) && DT_bfaces[b] >= 0)) return fail(c, LFM_EINVAL, "DT_bfaces[%d] must be finite and >= 0", b);
+  DeviceGuard g(c->device);
+  if (DT_faces) {
+    if ((rc = h2d(c, c->lay.DT, DT_faces, c->F))) return rc;
+  } else {
+    CK(c, launch_fill(const_cast<double*>(c->cs.DT), c->F, uniform, c->stream));
+  }
+  if (DT_bfaces) {
+    if ((rc = h2d(c, c->lay.bDT, DT_bfaces, c->NB))) return rc;
+  } else {
+    CK(c, launch_fill(const_cast<double*>(c->cs.bDT), c->NB, uniform, c->stream));
+  }
+  CK(c, cudaStreamSynchronize(c->stream));
+  return LFM_OK;
+}
+
+int lfm_set_patch(lfm_ctx* c, int32_t patch, int32_t type, const double* values, double uniform) {
+  int rc = need_uploaded(c);
+  if (rc) return rc;
+  if (patch < 0 || patch >= c->n_patches) return fail(c, LFM_EINVAL, "patch %d out of range", patch);
+  if (type != LFM_FIXED_VALUE && type != LFM_ZERO_GRADIENT) return fail(c, LFM_EINVAL, "unknown patch type %d", type);
+  const int32_t n = c->patch_size[patch], s = c->patch_start[patch];
+  std::vector<double> vals(n > 0 ? n : 1, uniform);
+  if (type == LFM_FIXED_VALUE) {
+    if (values) std::copy(values, values + n, vals.begin());
+    for (int32_t i = 0; i < n; ++i)
+      if (!std::isfinite(vals[i])) return fail(c, LFM_EINVAL, "patch %d value %d not finite", patch, i);
+  }
+  std::vector<int32_t> types(n > 0 ? n : 1, type);
+  DeviceGuard g(c->device);
+  if ((rc = h2d(c, c->lay.btype + 4 * (size_t)s, types.data(), n))) return rc;
+  if (type == LFM_FIXED_VALUE && (rc = h2d(c, c->lay.bval + 8 * (size_t)s, vals.data(), n))) return rc;
+  CK(c, cudaStreamSynchronize(c->stream));
+  c->patch_type[patch] = type;
+  return LFM_OK;
+}
+
+int lfm_set_time_step(lfm_ctx* c, double dt) {
+  int rc = need_uploaded(c);
+  if (rc) return rc;
+  if (!(std::isfinite(dt) && dt > 0)) return fail(c, LFM_EINVAL, "dt must be finite and > 0");
+  c->dt = dt;
+  return LFM_OK;
+}
+
+int lfm_set_solver(lfm_ctx* c, const lfm_solver_opts* o) {
+  int rc = need_uploaded(c);
+  if (rc) return rc;
+  if (!o) return fail(c, LFM_EINVAL, "opts is NULL");
+  if (!(std::isfinite(o->tol) && o->tol >= 0) || !(std::isfinite(o->rel_tol) && o->rel_tol >= 0) ||
+      o->max_iter < 1 || o->min_iter < 0 || o->min_iter > o->max_iter ||
+      (o->precision != LFM_FP64 && o->precision != LFM_MIXED))
+    return fail(c, LFM_EINVAL, "invalid solver options");
+  if ((o->precision == LFM_FP64 && !c->has64) || (o->precision == LFM_MIXED && !c->has32))
+    return fail(c, LFM_ENOMEM, "the workspace was laid out without the %s solver buffers",
+                o->precision == LFM_FP64 ? "FP64" : "mixed-precision");
+  const bool launch_changes = o->precision != c->opts.precision;
+  c->opts = *o;
+  if (launch_changes) return choose_launch(c);
+  return LFM_OK;
+}
+
+int lfm_set_field(lfm_ctx* c, const double* T) {
+  int rc = need_uploaded(c);
+  if (rc) return rc;
+  if (!T) return fail(c, LFM_EINVAL, "T is NULL");
+  DeviceGuard g(c->device);
+  CK(c, cudaMemcpyAsync(c->cs.x, T, sizeof(double) * c->N, cudaMemcpyHostToDevice, c->stream));
+  CK(c, cudaStreamSynchronize(c->stream));
+  return LFM_OK;
+}
+
+int lfm_set_field_device(lfm_ctx* c, const double* T_dev) {
+  int rc = need_uploaded(c);
+  if (rc) return rc;
+  if (!T_dev) return fail(c, LFM_EINVAL, "T_dev is NULL");
+  DeviceGuard g(c->device);
+  CK(c, cudaMemcpyAsync(c->cs.x, T_dev, sizeof(double) * c->N, cudaMemcpyDeviceToDevice, c->stream));
+  return LFM_OK;
+}
+
+int lfm_advance_async(lfm_ctx* c, int32_t n_steps) {
+  int rc = need_uploaded(c);
+  if (rc) return rc;
+  if (n_steps < 0) return fail(c, LFM_EINVAL, "n_steps must be >= 0");
+  if (c->pending_steps > 0) return fail(c, LFM_ESTATE, "an advance is already pending");
+  if (n_steps == 0) return LFM_OK;
+  DeviceGuard g(c->device);
+  c->stats_acc.clear();
+  const int first = n_steps < kStatsCap ? n_steps : kStatsCap;
+  if ((rc = enqueue_chunk(c, first, kModeSteps))) return rc;
+  c->pending_steps = first;
+  c->pending_remaining = n_steps - first;
+  return LFM_OK;
+}
+
+int lfm_query(lfm_ctx* c) {
+  if (!c) return fail_free(LFM_EINVAL, "context is NULL");
+  if (c->pending_steps == 0) return LFM_OK;
+  if (c->pending_remaining > 0) return 1;
+  DeviceGuard g(c->device);
+  cudaError_t e = cudaEventQuery(c->done);
+  if (e == cudaErrorNotReady) return 1;
+  if (e != cudaSuccess) return cuda_fail(c, e, "cudaEventQuery");
+  return LFM_OK;
+}
+
+int lfm_finish(lfm_ctx* c, lfm_step_stats* out, int32_t n) {
+  if (!c) return fail_free(LFM_EINVAL, "context is NULL");
+  DeviceGuard g(c->device);
+  int rc = LFM_OK;
+  while (c->pending_steps > 0) {
+    rc = collect_chunk(c, c->pending_steps);
+    c->pending_steps = 0;
+    if (rc != LFM_OK) {
+      c->pending_remaining = 0;
+      break;
+    }
+    if (c->pending_remaining > 0) {
+      const int next = c->pending_remaining < kStatsCap ? c->pending_remaining : kStatsCap;
+      if ((rc = enqueue_chunk(c, next, kModeSteps))) {
+        c->pending_remaining = 0;
+        break;
+      }
+      c->pending_steps = next;
+      c->pending_remaining -= next;
+    }
+  }
+  if (out) {
+    const int32_t m = (int32_t)c->stats_acc.size() < n ? (int32_t)c->stats_acc.size() : n;
+    for (int32_t i = 0; i < m; ++i) out[i] = c->stats_acc[i];
+  }
+  return rc;
+}
+
+int lfm_advance(lfm_ctx* c, int32_t n_steps, lfm_step_stats* out) {
+  int rc = lfm_advance_async(c, n_steps);
+  if (rc != LFM_OK) return rc;
+  return lfm_finish(c, out, n_steps);
+}
+
+int lfm_get_field(lfm_ctx* c, double* T_out, double* T_boundary) {
+  int rc = need_uploaded(c);
+  if (rc) return rc;
+  if (!T_out) return fail(c, LFM_EINVAL, "T_out is NULL");
+  DeviceGuard g(c->device);
+  CK(c, cudaMemcpyAsync(T_out, c->cs.x, sizeof(double) * c->N, cudaMemcpyDeviceToHost, c->stream));
+  if (T_boundary && c->NB > 0) {
+    double* Tb = reinterpret_cast<double*>(c->ws + c->lay.Tb);
+    CK(c, launch_boundary_values(c->cs, Tb, c->stream));
+    CK(c, cudaMemcpyAsync(T_boundary, Tb, sizeof(double) * c->NB, cudaMemcpyDeviceToHost, c->stream));
+  }
+  CK(c, cudaStreamSynchronize(c->stream));
+  return LFM_OK;
+}
+
+int lfm_field_device_ptr(lfm_ctx* c, double** T_dev) {
+  int rc = need_uploaded(c);
+  if (rc) return rc;
+  if (!T_dev) return fail(c, LFM_EINVAL, "T_dev is NULL");
+  *T_dev = c->cs.x;
+  return LFM_OK;
+}
+
+int lfm_get_matrix(lfm_ctx* c, double* diag, double* upper, double* source) {
+  int rc = need_uploaded(c);
+  if (rc) return rc;
+  if (!diag || !source || (c->F > 0 && !upper)) return fail(c, LFM_EINVAL, "output arrays missing");
+  if (c->pending_steps > 0) return fail(c, LFM_ESTATE, "an advance is pending");
+  DeviceGuard g(c->device);
+  if ((rc = enqueue_chunk(c, 1, kModeAssembleOnly))) return rc;
+  c->stats_acc.clear();
+  CK(c, cudaEventSynchronize(c->done));
+  if (*c->h_status != 0) return fail(c, LFM_ETIMEOUT, "assembly launch failed with device status %d", *c->h_status);
+  CK(c, cudaMemcpyAsync(diag, c->cs.diag, sizeof(double) * c->N, cudaMemcpyDeviceToHost, c->stream));
+  if (c->F > 0) CK(c, cudaMemcpyAsync(upper, c->cs.upper, sizeof(double) * c->F, cudaMemcpyDeviceToHost, c->stream));
+  CK(c, cudaMemcpyAsync(source, c->cs.src, sizeof(double) * c->N, cudaMemcpyDeviceToHost, c->stream));
+  CK(c, cudaStreamSynchronize(c->stream));
+  return LFM_OK;
+}
+
+int lfm_get_launch(lfm_ctx* c, int32_t* ctas, int32_t* threads) {
+  int rc = need_uploaded(c);
+  if (rc) return rc;
+  int e = 0;
+  Launch L = current_launch(c, e);
+  if (ctas) *ctas = L.ctas;
+  if (threads) *threads = L.threads;
+  return e ? fail(c, LFM_ECUDA, "no co-resident CTA fits") : LFM_OK;
+}
+
+int lfm_set_launch(lfm_ctx* c, int32_t ctas, int32_t threads) {
+  int rc = need_uploaded(c);
+  if (rc) return rc;
+  if (threads > 0 && threads != 256 && threads != 512 && threads != 1024)
+    return fail(c, LFM_EINVAL, "threads must be 256, 512 or 1024");
+  c->ctas = ctas > 0 ? ctas : 0;
+  c->threads = threads > 0 ? threads : 0;
+  return LFM_OK;
+}
+
+int lfm_set_barrier_timeout(lfm_ctx* c, uint64_t ns) {
+  if (!c) return fail_free(LFM_EINVAL, "context is NULL");
+  if (ns == 0) return fail(c, LFM_EINVAL, "timeout must be > 0");
+  c->timeout_ns = ns;
+  return LFM_OK;
+}
+
+int lfm_debug_skip_arrival(lfm_ctx* c, int32_t cta) {
+  if (!c) return fail_free(LFM_EINVAL, "context is NULL");
+  c->skip_cta = cta >= 0 ? cta : -1;
+  return LFM_OK;
+}
+
+int lfm_destroy(lfm_ctx* c) {
+  if (!c) return LFM_OK;
+  {
+    DeviceGuard g(c->device);
+    if (c->pending_steps > 0 && c->done) cudaEventSynchronize(c->done);
+    if (c->ws_owned && c->ws) cudaFree(c->ws);
+    if (c->h_stats) cudaFreeHost(c->h_stats);
+    if (c->h_status) cudaFreeHost(c->h_status);
+    if (c->done) cudaEventDestroy(c->done);
+  }
+  delete c;
+  return LFM_OK;
+}
+
+const char* lfm_last_error(const lfm_ctx* c) {
+  if (c) return c->err.c_str();
+  return g_last_error.c_str();
+}
+
+}  // extern "C"

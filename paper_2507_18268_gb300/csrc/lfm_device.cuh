@@ -1,0 +1,185 @@
+// Device primitives: bounded team barriers with deterministic reductions.
+//
+// A "team" is a set of co-resident CTAs (a cooperative launch guarantees co-residency)
+// working on one case. Each barrier may carry up to kMaxSums FP64 sums: every CTA reduces
+// its threads' values with a fixed warp-shuffle / shared-memory tree, writes the CTA total
+// to its slot of a partial table, and arrives on a counter. The last CTA to arrive adds the
+// slots in rank order (lane l takes ranks l, l+32, ...; then a fixed xor tree), publishes
+// the sums and releases the barrier by bumping a generation word. The result depends only
+// on the team size, never on arrival order, so repeated runs are bitwise identical.
+//
+// Every wait is bounded: a waiter that sees no release within the launch's time limit (or
+// sees another CTA's error) records an error status and the caller leaves the kernel.
+#pragma once
+
+#include <cstdint>
+
+#include "lfm_internal.h"
+
+namespace lfm {
+
+__device__ __forceinline__ uint64_t global_timer_ns() {
+  uint64_t t;
+  asm volatile("mov.u64 %0, %%globaltimer;" : "=l"(t));
+  return t;
+}
+
+__device__ __forceinline__ unsigned ld_acquire_u32(const unsigned* p) {
+  unsigned v;
+  asm volatile("ld.acquire.gpu.global.u32 %0, [%1];" : "=r"(v) : "l"(p) : "memory");
+  return v;
+}
+
+__device__ __forceinline__ void st_release_u32(unsigned* p, unsigned v) {
+  asm volatile("st.release.gpu.global.u32 [%0], %1;" ::"l"(p), "r"(v) : "memory");
+}
+
+__device__ __forceinline__ int ld_volatile_i32(const int32_t* p) {
+  return *reinterpret_cast<const volatile int32_t*>(p);
+}
+
+struct Team {
+  int size;
+  int rank;
+  SyncWords* sw;
+  double* partials;
+  uint64_t timeout_ns;
+};
+
+// Shared scratch a CTA needs for team_allreduce.
+struct TeamShared {
+  double red[32 * kMaxSums];
+  double out[kMaxSums];
+  int flag[4];
+};
+
+// Spins until *gen != g. False (with the error recorded) when the time limit runs out or
+// another CTA has recorded an error.
+__device__ __forceinline__ bool wait_generation(unsigned* gen, unsigned g, int32_t* status,
+                                                uint64_t timeout_ns) {
+  uint64_t t0 = global_timer_ns();
+  unsigned spins = 0;
+  while (ld_acquire_u32(gen) == g) {
+    ++spins;
+    if (spins > 16) __nanosleep(32);
+    if ((spins & 31u) == 0) {
+      if (ld_volatile_i32(status) != 0) return false;
+      if (global_timer_ns() - t0 > timeout_ns) {
+        atomicCAS(status, 0, (int32_t)LFM_ETIMEOUT);
+        return false;
+      }
+    }
+  }
+  return true;
+}
+
+// Fixed-pattern reduction of NS values over the CTA. Totals land in sh.out (visible after
+// the caller's next __syncthreads).
+template <int NS>
+__device__ __forceinline__ void block_reduce(double* v, TeamShared& sh) {
+  const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5, nw = blockDim.x >> 5;
+#pragma unroll
+  for (int k = 0; k < NS; ++k) {
+#pragma unroll
+    for (int o = 16; o > 0; o >>= 1) v[k] += __shfl_xor_sync(0xffffffffu, v[k], o);
+  }
+  if (lane == 0) {
+#pragma unroll
+    for (int k = 0; k < NS; ++k) sh.red[warp * NS + k] = v[k];
+  }
+  __syncthreads();
+  if (warp == 0) {
+#pragma unroll
+    for (int k = 0; k < NS; ++k) {
+      double t = lane < nw ? sh.red[lane * NS + k] : 0.0;
+#pragma unroll
+      for (int o = 16; o > 0; o >>= 1) t += __shfl_xor_sync(0xffffffffu, t, o);
+      if (lane == 0) sh.out[k] = t;
+    }
+  }
+}
+
+// Team-wide barrier carrying NS sums. On return (true) v[k] holds the team totals in every
+// thread. False: a wait ran out or another CTA failed; the caller must leave the kernel.
+template <int NS>
+__device__ bool team_allreduce(const Team& tm, double* v, TeamShared& sh) {
+  if constexpr (NS > 0) block_reduce<NS>(v, sh);
+  if (tm.size == 1) {
+    __syncthreads();
+    if constexpr (NS > 0) {
+#pragma unroll
+      for (int k = 0; k < NS; ++k) v[k] = sh.out[k];
+    }
+    return true;
+  }
+  if (threadIdx.x == 0) {
+    if constexpr (NS > 0) {
+#pragma unroll
+      for (int k = 0; k < NS; ++k) __stcg(&tm.partials[tm.rank * kMaxSums + k], sh.out[k]);
+    }
+    unsigned g = *reinterpret_cast<volatile unsigned*>(&tm.sw->gen);
+    __threadfence();
+    unsigned prev = atomicAdd(&tm.sw->count, 1u);
+    int last = prev == (unsigned)(tm.size - 1);
+    int ok = 1;
+    if (last) {
+      __threadfence();
+    } else {
+      ok = wait_generation(&tm.sw->gen, g, &tm.sw->status, tm.timeout_ns);
+      if (ok) {
+        __threadfence();
+        if constexpr (NS > 0) {
+#pragma unroll
+          for (int k = 0; k < NS; ++k) sh.out[k] = __ldcg(&tm.sw->scalars[k]);
+        }
+      }
+    }
+    sh.flag[0] = last;
+    sh.flag[1] = ok;
+    sh.flag[2] = (int)g;
+  }
+  __syncthreads();
+  if (!sh.flag[1]) return false;
+  if (sh.flag[0]) {
+    if (threadIdx.x < 32) {
+      const int lane = threadIdx.x;
+      if constexpr (NS > 0) {
+#pragma unroll
+        for (int k = 0; k < NS; ++k) {
+          double t = 0.0;
+          for (int r = lane; r < tm.size; r += 32) t += __ldcg(&tm.partials[r * kMaxSums + k]);
+#pragma unroll
+          for (int o = 16; o > 0; o >>= 1) t += __shfl_xor_sync(0xffffffffu, t, o);
+          if (lane == 0) {
+            sh.out[k] = t;
+            __stcg(&tm.sw->scalars[k], t);
+          }
+        }
+      }
+      __syncwarp();
+      if (lane == 0) {
+        __threadfence();
+        atomicExch(&tm.sw->count, 0u);
+        st_release_u32(&tm.sw->gen, (unsigned)sh.flag[2] + 1u);
+      }
+    }
+    __syncthreads();
+  }
+  if constexpr (NS > 0) {
+#pragma unroll
+    for (int k = 0; k < NS; ++k) v[k] = sh.out[k];
+  }
+  return true;
+}
+
+// Team-wide barrier without sums.
+__device__ __forceinline__ bool team_barrier(const Team& tm, TeamShared& sh) {
+  return team_allreduce<0>(tm, nullptr, sh);
+}
+
+// Records an error status for the launch (first error wins).
+__device__ __forceinline__ void set_status(SyncWords* sw, int32_t code) {
+  atomicCAS(&sw->status, 0, code);
+}
+
+}  // namespace lfm

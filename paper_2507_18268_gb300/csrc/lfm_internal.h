@@ -1,0 +1,106 @@
+// Internal structures shared by the host-side C ABI (lfm_api.cu) and the kernels
+// (lfm_step.cu). Nothing here is part of the public ABI.
+#pragma once
+
+#include <cstddef>
+#include <cstdint>
+
+#include <cuda_runtime.h>
+
+#include "../../include/lapfoam.h"
+
+namespace lfm {
+
+constexpr int kMaxSums = 4;          // scalars reduced per team barrier
+constexpr int kMaxCtas = 8192;       // capacity of the per-CTA partial-sum table
+constexpr int kStatsCap = 1024;      // per-launch statistics records
+constexpr int kMaxSweeps = 5;        // mixed precision: defect-correction sweeps per step
+
+// Barrier words of one team of CTAs; each field sits on its own 128-byte line.
+struct alignas(128) SyncWords {
+  unsigned int count;                // arrivals at the current barrier
+  unsigned int pad0[31];
+  unsigned int gen;                  // barrier generation (released by the last arrival)
+  unsigned int pad1[31];
+  double scalars[kMaxSums];          // reduced values published by the last arrival
+  double pad2[16 - kMaxSums];
+  int32_t status;                    // first error of the launch (0 = none)
+  int32_t pad3[31];
+};
+
+// Device view of one case: every pointer is device memory of the case's workspace.
+struct CaseDev {
+  int32_t N, F, NB;
+  int32_t precision;
+  double dt;
+  double tol, rel_tol;
+  int32_t max_iter, min_iter;
+
+  // face-to-cell addressing (constant for a mesh)
+  const int32_t* nbr;        // [F]   neighbour of face f (the other cell for its owner)
+  const int32_t* own_start;  // [N+1] faces owned by c: [own_start[c], own_start[c+1])
+  const int32_t* losort;     // [F]   faces sorted by neighbour, ascending face id per cell
+  const int32_t* lo_start;   // [N+1] neighbour-side faces of c: losort[lo_start[c] ..)
+  const int32_t* lo_other;   // [F]   owner of face losort[i]
+  const int32_t* b_start;    // [N+1] boundary faces of c: b_face[b_start[c] ..)
+  const int32_t* b_face;     // [NB]  boundary faces sorted by cell, ascending id per cell
+  const int32_t* bcell;      // [NB]  cell of boundary face b
+
+  // geometry and properties
+  const double* V;           // [N]
+  const double* magSf;       // [F]
+  const double* delta;       // [F]
+  const double* DT;          // [F]
+  const double* bmagSf;      // [NB]
+  const double* bdelta;      // [NB]
+  const double* bDT;         // [NB]
+  const double* bval;        // [NB]  fixedValue values
+  const int32_t* btype;      // [NB]  LFM_FIXED_VALUE / LFM_ZERO_GRADIENT
+
+  // assembled matrix (FP64)
+  double* diag;              // [N]
+  double* upper;             // [F]  (lower == upper)
+  double* src;               // [N]
+  double* rD;                // [N]  1/diag
+
+  // FP64 solver vectors; x is the field T (updated in place)
+  double* x;
+  double* r;
+  double* w;
+  double* p;
+  double* q;
+
+  // mixed precision: FP32 matrix copy and inner-solve vectors
+  float* diag32;
+  float* upper32;
+  float* rD32;
+  float* dx32;
+  float* r32;
+  float* w32;
+  float* p32;
+  float* q32;
+
+  // team state
+  SyncWords* sync;
+  double* partials;          // [kMaxCtas * kMaxSums]
+  lfm_step_stats* stats;     // [kStatsCap]
+};
+
+struct Launch {
+  int ctas;
+  int threads;
+  uint64_t timeout_ns;
+  int skip_cta;              // test hook: CTA that leaves before its first arrival (-1: none)
+};
+
+enum Mode { kModeSteps = 0, kModeAssembleOnly = 1 };
+
+// Kernel launchers (lfm_step.cu). Return a cudaError_t.
+cudaError_t launch_steps(const CaseDev& cs, const Launch& L, int n_steps, int mode,
+                         cudaStream_t stream);
+// Largest co-resident CTA count for the step kernel at `threads` per CTA.
+int max_coresident_ctas(int precision, int threads, int device);
+cudaError_t launch_boundary_values(const CaseDev& cs, double* Tb, cudaStream_t stream);
+cudaError_t launch_fill(double* a, size_t n, double v, cudaStream_t stream);
+
+}  // namespace lfm

@@ -1,0 +1,437 @@
+// Persistent cooperative kernels running whole implicit-Euler time steps of laplacianFoam
+// (arXiv 2507.18268, Eq. (1) and the listing "laplacianFoam application": per step one
+// solve of fvm::ddt(T) - fvm::laplacian(DT, T)).
+//
+// One launch runs n steps. Each CTA of the team owns a contiguous range of cells and, in
+// every phase, computes whole matrix rows by gathering over the face-to-cell lists (the
+// paper's atomic-free rewrite of the face loop, listing "First cycle gradient in
+// parallel"): no atomics touch data and every reduction has a fixed order.
+//
+// FP64 step (phases separated by team barriers):
+//   A  assembly        diag, upper (owner-side faces), source, rD; sum x for xRef
+//   I  initial state   A x, r = b - A x, row sums -> normFactor, sum|r|, w = rD r, rho;
+//                      p = w (first search direction)
+//   loop (diagonal-preconditioned CG, convergence on sum|r| / normFactor):
+//   P  p = w + beta p  (skipped on the first iteration)
+//   M  q = A p, sigma = p.q                   -> alpha = rho / sigma
+//   U  x += alpha p, r -= alpha q, w = rD r, sum|r|, rho' = w.r -> beta = rho'/rho
+//
+// Mixed step (defect correction, FP64 field x): the matrix is assembled in FP64 and copied
+// to FP32; each sweep computes the FP64 true residual r = b - A x, solves A dx = r by the
+// same CG recurrence on FP32 vectors with FP32 row sums, and adds dx to x in FP64. Dot
+// products, sum|r|, normFactor and every convergence test accumulate in FP64.
+#include <cuda_runtime.h>
+
+#include "lfm_device.cuh"
+#include "lfm_internal.h"
+
+namespace lfm {
+namespace {
+
+constexpr double kSmall = 1e-20;    // added to normFactor
+constexpr double kVSmall = 1e-300;  // singularity threshold on |p.Ap| / normFactor
+constexpr double kInnerRel = 1e-6;  // mixed: inner solve stops at this fraction of the sweep's start residual
+
+__device__ __forceinline__ bool converged(double res, double init_res, double tol, double rel_tol) {
+  return res < tol || (rel_tol > 0.0 && res < rel_tol * init_res);
+}
+
+// Contiguous cell range [c0, c1) of this CTA.
+__device__ __forceinline__ void cta_range(int N, int size, int rank, int& c0, int& c1) {
+  int chunk = (N + size - 1) / size;
+  chunk = (chunk + 31) & ~31;
+  long long a = (long long)rank * chunk;
+  c0 = (int)(a < N ? a : N);
+  long long b = a + chunk;
+  c1 = (int)(b < N ? b : N);
+}
+
+// ---- assembly: one row of fvm::ddt(T) - fvm::laplacian(DT, T) -------------------------
+// The row's diagonal is summed in ascending face order (neighbour-side faces first: their
+// owners are smaller labels, so they precede the cell's own faces in upper-triangular
+// order), then boundary faces, then V/dt, each product rounded separately (no FMA).
+template <bool kMixed>
+__device__ __forceinline__ double assemble_row(const CaseDev& cs, int c) {
+  double d = 0.0, s = 0.0;
+  const int lo0 = __ldg(cs.lo_start + c), lo1 = __ldg(cs.lo_start + c + 1);
+  for (int i = lo0; i < lo1; ++i) {
+    const int f = __ldg(cs.losort + i);
+    const double g = __dmul_rn(__dmul_rn(__ldg(cs.DT + f), __ldg(cs.magSf + f)), __ldg(cs.delta + f));
+    d = __dadd_rn(d, g);
+  }
+  const int f0 = __ldg(cs.own_start + c), f1 = __ldg(cs.own_start + c + 1);
+  for (int f = f0; f < f1; ++f) {
+    const double g = __dmul_rn(__dmul_rn(__ldg(cs.DT + f), __ldg(cs.magSf + f)), __ldg(cs.delta + f));
+    cs.upper[f] = -g;
+    if (kMixed) cs.upper32[f] = (float)(-g);
+    d = __dadd_rn(d, g);
+  }
+  const int b0 = __ldg(cs.b_start + c), b1 = __ldg(cs.b_start + c + 1);
+  for (int k = b0; k < b1; ++k) {
+    const int bf = __ldg(cs.b_face + k);
+    if (__ldg(cs.btype + bf) == LFM_FIXED_VALUE) {
+      const double gb = __dmul_rn(__dmul_rn(__ldg(cs.bDT + bf), __ldg(cs.bmagSf + bf)), __ldg(cs.bdelta + bf));
+      d = __dadd_rn(d, gb);
+      s = __dadd_rn(s, __dmul_rn(gb, __ldg(cs.bval + bf)));
+    }
+  }
+  const double vdt = __ldg(cs.V + c) / cs.dt;
+  const double xc = cs.x[c];
+  d = __dadd_rn(d, vdt);
+  s = __dadd_rn(s, __dmul_rn(vdt, xc));
+  const double rd = 1.0 / d;
+  cs.diag[c] = d;
+  cs.src[c] = s;
+  cs.rD[c] = rd;
+  if (kMixed) {
+    cs.diag32[c] = (float)d;
+    cs.rD32[c] = (float)rd;
+  }
+  return xc;
+}
+
+// ---- FP64 row of A v (gather over the face-to-cell lists) ----------------------------
+template <bool kRowSum>
+__device__ __forceinline__ double row_f64(const CaseDev& cs, int c, const double* __restrict__ v,
+                                          double d, double vc, double& rowsum) {
+  double acc = d * vc;
+  double rs = d;
+  const int lo0 = __ldg(cs.lo_start + c), lo1 = __ldg(cs.lo_start + c + 1);
+  for (int i = lo0; i < lo1; ++i) {
+    const double u = cs.upper[__ldg(cs.losort + i)];
+    acc = fma(u, v[__ldg(cs.lo_other + i)], acc);
+    if (kRowSum) rs += u;
+  }
+  const int f0 = __ldg(cs.own_start + c), f1 = __ldg(cs.own_start + c + 1);
+  for (int f = f0; f < f1; ++f) {
+    const double u = cs.upper[f];
+    acc = fma(u, v[__ldg(cs.nbr + f)], acc);
+    if (kRowSum) rs += u;
+  }
+  if (kRowSum) rowsum = rs;
+  return acc;
+}
+
+// ---- FP32 row of A v ------------------------------------------------------------------
+__device__ __forceinline__ float row_f32(const CaseDev& cs, int c, const float* __restrict__ v,
+                                         float d, float vc) {
+  float acc = d * vc;
+  const int lo0 = __ldg(cs.lo_start + c), lo1 = __ldg(cs.lo_start + c + 1);
+  for (int i = lo0; i < lo1; ++i)
+    acc = fmaf(cs.upper32[__ldg(cs.losort + i)], v[__ldg(cs.lo_other + i)], acc);
+  const int f0 = __ldg(cs.own_start + c), f1 = __ldg(cs.own_start + c + 1);
+  for (int f = f0; f < f1; ++f) acc = fmaf(cs.upper32[f], v[__ldg(cs.nbr + f)], acc);
+  return acc;
+}
+
+__device__ __forceinline__ void write_stats(const CaseDev& cs, const Team& tm, int slot, int iters,
+                                            int conv, int sweeps, int status, double init_res,
+                                            double final_res, double nf) {
+  if (tm.rank == 0 && threadIdx.x == 0) {
+    lfm_step_stats st;
+    st.iters = iters;
+    st.converged = conv;
+    st.sweeps = sweeps;
+    st.status = status;
+    st.init_res = init_res;
+    st.final_res = final_res;
+    st.norm_factor = nf;
+    cs.stats[slot] = st;
+  }
+}
+
+// =======================================================================================
+// FP64 step kernel
+// =======================================================================================
+template <int B>
+__global__ void __launch_bounds__(B) step_kernel_f64(CaseDev cs, Launch L, int n_steps, int mode) {
+  __shared__ TeamShared sh;
+  if ((int)blockIdx.x == L.skip_cta) return;  // test hook: never arrive
+  const Team tm{(int)gridDim.x, (int)blockIdx.x, cs.sync, cs.partials, L.timeout_ns};
+  int c0, c1;
+  cta_range(cs.N, tm.size, tm.rank, c0, c1);
+  const int tid = threadIdx.x;
+  double* __restrict__ x = cs.x;
+  double* __restrict__ r = cs.r;
+  double* __restrict__ w = cs.w;
+  double* __restrict__ p = cs.p;
+  double* __restrict__ q = cs.q;
+
+  for (int step = 0; step < n_steps; ++step) {
+    // ---- A: assembly -------------------------------------------------------------------
+    {
+      double v[1] = {0.0};
+      for (int c = c0 + tid; c < c1; c += B) v[0] += assemble_row<false>(cs, c);
+      if (!team_allreduce<1>(tm, v, sh)) return;
+      if (mode == kModeAssembleOnly) return;
+      // ---- I: initial residual, normFactor, first direction ---------------------------
+      const double xRef = v[0] / (double)cs.N;
+      double u[3] = {0.0, 0.0, 0.0};  // normFactor sum, sum|r|, rho
+      for (int c = c0 + tid; c < c1; c += B) {
+        const double d = cs.diag[c], xc = x[c], b = cs.src[c];
+        double rs;
+        const double ax = row_f64<true>(cs, c, x, d, xc, rs);
+        const double rc = b - ax;
+        const double pA = rs * xRef;
+        u[0] += fabs(ax - pA) + fabs(b - pA);
+        u[1] += fabs(rc);
+        const double wc = cs.rD[c] * rc;
+        u[2] = fma(wc, rc, u[2]);
+        r[c] = rc;
+        p[c] = wc;
+      }
+      if (!team_allreduce<3>(tm, u, sh)) return;
+      const double nf = u[0] + kSmall;
+      const double init_res = u[1] / nf;
+      double res = init_res, rho = u[2], beta = 0.0;
+      int iters = 0, status = 0;
+      bool conv = converged(res, init_res, cs.tol, cs.rel_tol);
+      if (cs.min_iter > 0 || !conv) {
+        for (;;) {
+          if (iters > 0) {
+            // ---- P: search direction ------------------------------------------------
+            for (int c = c0 + tid; c < c1; c += B) p[c] = fma(beta, p[c], w[c]);
+            if (!team_barrier(tm, sh)) return;
+          }
+          // ---- M: q = A p, sigma = p.q ---------------------------------------------
+          double s1[1] = {0.0};
+          for (int c = c0 + tid; c < c1; c += B) {
+            const double pc = p[c];
+            double unused;
+            const double qc = row_f64<false>(cs, c, p, cs.diag[c], pc, unused);
+            q[c] = qc;
+            s1[0] = fma(qc, pc, s1[0]);
+          }
+          if (!team_allreduce<1>(tm, s1, sh)) return;
+          const double sigma = s1[0];
+          if (fabs(sigma) / nf < kVSmall) {
+            status = LFM_ESINGULAR;
+            break;
+          }
+          const double alpha = rho / sigma;
+          // ---- U: update, residual, preconditioned residual, next rho ---------------
+          double s2[2] = {0.0, 0.0};
+          for (int c = c0 + tid; c < c1; c += B) {
+            const double pc = p[c], qc = q[c];
+            const double xc = fma(alpha, pc, x[c]);
+            const double rc = fma(-alpha, qc, r[c]);
+            const double wc = cs.rD[c] * rc;
+            x[c] = xc;
+            r[c] = rc;
+            w[c] = wc;
+            s2[0] += fabs(rc);
+            s2[1] = fma(wc, rc, s2[1]);
+          }
+          if (!team_allreduce<2>(tm, s2, sh)) return;
+          res = s2[0] / nf;
+          beta = s2[1] / rho;
+          rho = s2[1];
+          ++iters;
+          if (!isfinite(res)) {
+            status = LFM_ENONFINITE;
+            break;
+          }
+          conv = converged(res, init_res, cs.tol, cs.rel_tol);
+          if (!((iters < cs.max_iter && !conv) || iters < cs.min_iter)) break;
+        }
+      }
+      conv = converged(res, init_res, cs.tol, cs.rel_tol);
+      write_stats(cs, tm, step, iters, conv ? 1 : 0, iters > 0 ? 1 : 0, status, init_res, res, nf);
+      if (status != 0) {
+        if (tm.rank == 0 && tid == 0) set_status(cs.sync, status);
+        return;
+      }
+    }
+  }
+}
+
+// =======================================================================================
+// Mixed-precision step kernel (FP32 inner CG inside FP64 defect correction)
+// =======================================================================================
+template <int B>
+__global__ void __launch_bounds__(B) step_kernel_mixed(CaseDev cs, Launch L, int n_steps, int mode) {
+  __shared__ TeamShared sh;
+  if ((int)blockIdx.x == L.skip_cta) return;
+  const Team tm{(int)gridDim.x, (int)blockIdx.x, cs.sync, cs.partials, L.timeout_ns};
+  int c0, c1;
+  cta_range(cs.N, tm.size, tm.rank, c0, c1);
+  const int tid = threadIdx.x;
+  double* __restrict__ x = cs.x;
+  float* __restrict__ dx = cs.dx32;
+  float* __restrict__ r = cs.r32;
+  float* __restrict__ w = cs.w32;
+  float* __restrict__ p = cs.p32;
+  float* __restrict__ q = cs.q32;
+
+  for (int step = 0; step < n_steps; ++step) {
+    double v[1] = {0.0};
+    for (int c = c0 + tid; c < c1; c += B) v[0] += assemble_row<true>(cs, c);
+    if (!team_allreduce<1>(tm, v, sh)) return;
+    if (mode == kModeAssembleOnly) return;
+    const double xRef = v[0] / (double)cs.N;
+
+    double nf = 0.0, init_res = 0.0, res = 0.0;
+    int iters = 0, sweeps = 0, status = 0;
+    for (;;) {
+      // ---- T: FP64 true residual r = b - A x, seeded into the FP32 inner solve --------
+      double u[3] = {0.0, 0.0, 0.0};  // normFactor sum (first sweep), sum|r|, rho
+      for (int c = c0 + tid; c < c1; c += B) {
+        const double d = cs.diag[c], xc = x[c], b = cs.src[c];
+        double rs;
+        const double ax = row_f64<true>(cs, c, x, d, xc, rs);
+        const double rc = b - ax;
+        if (sweeps == 0) {
+          const double pA = rs * xRef;
+          u[0] += fabs(ax - pA) + fabs(b - pA);
+        }
+        u[1] += fabs(rc);
+        const float r32 = (float)rc;
+        const float w32 = cs.rD32[c] * r32;
+        u[2] = fma((double)w32, (double)r32, u[2]);
+        r[c] = r32;
+        w[c] = w32;
+        p[c] = w32;
+        dx[c] = 0.0f;
+      }
+      if (!team_allreduce<3>(tm, u, sh)) return;
+      if (sweeps == 0) {
+        nf = u[0] + kSmall;
+        init_res = u[1] / nf;
+      }
+      res = u[1] / nf;
+      if (!isfinite(res)) {
+        status = LFM_ENONFINITE;
+        break;
+      }
+      const bool conv = converged(res, init_res, cs.tol, cs.rel_tol);
+      if ((conv && !(sweeps == 0 && cs.min_iter > 0)) || sweeps == kMaxSweeps || iters >= cs.max_iter) break;
+
+      // ---- inner FP32 CG on A dx = r --------------------------------------------------
+      const double sweep_res = res;
+      const double inner_tol = fmax(cs.tol, kInnerRel * sweep_res);
+      const int min_inner = sweeps == 0 ? cs.min_iter : 0;
+      double rho = u[2], beta = 0.0;
+      int k = 0;
+      for (;;) {
+        if (k > 0) {
+          const float b32 = (float)beta;
+          for (int c = c0 + tid; c < c1; c += B) p[c] = fmaf(b32, p[c], w[c]);
+          if (!team_barrier(tm, sh)) return;
+        }
+        double s1[1] = {0.0};
+        for (int c = c0 + tid; c < c1; c += B) {
+          const float pc = p[c];
+          const float qc = row_f32(cs, c, p, cs.diag32[c], pc);
+          q[c] = qc;
+          s1[0] = fma((double)qc, (double)pc, s1[0]);
+        }
+        if (!team_allreduce<1>(tm, s1, sh)) return;
+        const double sigma = s1[0];
+        if (fabs(sigma) / nf < kVSmall) {
+          status = LFM_ESINGULAR;
+          break;
+        }
+        const float a32 = (float)(rho / sigma);
+        double s2[2] = {0.0, 0.0};
+        for (int c = c0 + tid; c < c1; c += B) {
+          const float pc = p[c], qc = q[c];
+          const float rc = fmaf(-a32, qc, r[c]);
+          const float wc = cs.rD32[c] * rc;
+          dx[c] = fmaf(a32, pc, dx[c]);
+          r[c] = rc;
+          w[c] = wc;
+          s2[0] += fabs((double)rc);
+          s2[1] = fma((double)wc, (double)rc, s2[1]);
+        }
+        if (!team_allreduce<2>(tm, s2, sh)) return;
+        const double inner_res = s2[0] / nf;
+        beta = s2[1] / rho;
+        rho = s2[1];
+        ++k;
+        ++iters;
+        if (!isfinite(inner_res)) {
+          status = LFM_ENONFINITE;
+          break;
+        }
+        const bool inner_conv = inner_res < inner_tol;
+        if (!((iters < cs.max_iter && !inner_conv) || k < min_inner)) break;
+      }
+      if (status != 0) break;
+      // ---- x += dx (FP64) ------------------------------------------------------------
+      for (int c = c0 + tid; c < c1; c += B) x[c] += (double)dx[c];
+      if (!team_barrier(tm, sh)) return;
+      ++sweeps;
+    }
+    const bool conv = converged(res, init_res, cs.tol, cs.rel_tol);
+    write_stats(cs, tm, step, iters, conv ? 1 : 0, sweeps, status, init_res, res, nf);
+    if (status != 0) {
+      if (tm.rank == 0 && tid == 0) set_status(cs.sync, status);
+      return;
+    }
+  }
+}
+
+// ---- small helpers -------------------------------------------------------------------
+__global__ void boundary_values_kernel(CaseDev cs, double* Tb) {
+  const int b = blockIdx.x * blockDim.x + threadIdx.x;
+  if (b < cs.NB) Tb[b] = cs.btype[b] == LFM_FIXED_VALUE ? cs.bval[b] : cs.x[cs.bcell[b]];
+}
+
+__global__ void fill_kernel(double* a, size_t n, double v) {
+  size_t i = blockIdx.x * (size_t)blockDim.x + threadIdx.x;
+  const size_t stride = (size_t)gridDim.x * blockDim.x;
+  for (; i < n; i += stride) a[i] = v;
+}
+
+template <int B>
+void* step_fn(int precision) {
+  return precision == LFM_MIXED ? (void*)step_kernel_mixed<B> : (void*)step_kernel_f64<B>;
+}
+
+void* step_fn_for(int precision, int threads) {
+  switch (threads) {
+    case 256: return step_fn<256>(precision);
+    case 512: return step_fn<512>(precision);
+    case 1024: return step_fn<1024>(precision);
+    default: return nullptr;
+  }
+}
+
+}  // namespace
+
+int max_coresident_ctas(int precision, int threads, int device) {
+  void* fn = step_fn_for(precision, threads);
+  if (!fn) return 0;
+  int per_sm = 0, sms = 0;
+  if (cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, fn, threads, 0) != cudaSuccess) return 0;
+  if (cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, device) != cudaSuccess) return 0;
+  int n = per_sm * sms;
+  return n < kMaxCtas ? n : kMaxCtas;
+}
+
+cudaError_t launch_steps(const CaseDev& cs, const Launch& L, int n_steps, int mode,
+                         cudaStream_t stream) {
+  void* fn = step_fn_for(cs.precision, L.threads);
+  if (!fn) return cudaErrorInvalidValue;
+  CaseDev a0 = cs;
+  Launch a1 = L;
+  int a2 = n_steps, a3 = mode;
+  void* args[] = {&a0, &a1, &a2, &a3};
+  return cudaLaunchCooperativeKernel(fn, dim3(L.ctas), dim3(L.threads), args, 0, stream);
+}
+
+cudaError_t launch_boundary_values(const CaseDev& cs, double* Tb, cudaStream_t stream) {
+  if (cs.NB == 0) return cudaSuccess;
+  boundary_values_kernel<<<(cs.NB + 255) / 256, 256, 0, stream>>>(cs, Tb);
+  return cudaGetLastError();
+}
+
+cudaError_t launch_fill(double* a, size_t n, double v, cudaStream_t stream) {
+  if (n == 0) return cudaSuccess;
+  size_t blocks = (n + 255) / 256;
+  if (blocks > 4096) blocks = 4096;
+  fill_kernel<<<(unsigned)blocks, 256, 0, stream>>>(a, n, v);
+  return cudaGetLastError();
+}
+
+}  // namespace lfm

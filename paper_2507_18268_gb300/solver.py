@@ -1,0 +1,122 @@
+"""A case on the GPU: one ``lfm_ctx`` with its mesh, properties, controls and field.
+
+PyTorch supplies device memory (the workspace tensor) and the CUDA stream; the library does
+all the work.
+"""
+from __future__ import annotations
+
+from typing import List, Optional
+
+import numpy as np
+
+import lapcase
+
+from . import binding as B
+from .mesh import LduMesh, box_mesh, field_by_label
+
+
+def _stream_handle(stream) -> Optional[int]:
+    if stream is None:
+        return None
+    if isinstance(stream, int):
+        return stream
+    return int(stream.cuda_stream)  # torch.cuda.Stream
+
+
+class Solver:
+    def __init__(self, mesh: LduMesh, device: int = 0, stream=None, workspace: str = "torch",
+                 layout: int = B.LFM_BOTH):
+        self.mesh = mesh
+        self.device = device
+        self.stream = stream
+        self._ws = None
+        self.ctx = B.lfm_create(device, _stream_handle(stream))
+        try:
+            if workspace == "torch":
+                import torch
+
+                nbytes = B.lfm_workspace_bytes(mesh, layout)
+                self._ws = torch.empty(nbytes, dtype=torch.uint8, device=f"cuda:{device}")
+                B.lfm_bind_workspace(self.ctx, self._ws.data_ptr(), nbytes)
+            B.lfm_upload_mesh(self.ctx, mesh)
+        except Exception:
+            B.lfm_destroy(self.ctx)
+            self.ctx = None
+            raise
+
+    # ---- configuration ---------------------------------------------------------------
+    @classmethod
+    def from_case(cls, case: lapcase.RawCase, mesh: Optional[LduMesh] = None, **kw) -> "Solver":
+        mesh = mesh or box_mesh(case)
+        s = cls(mesh, **kw)
+        s.configure(case)
+        return s
+
+    def configure(self, case: lapcase.RawCase, field: bool = True):
+        m = self.mesh
+        B.lfm_set_diffusivity(self.ctx, 0.0, m.DT_faces, m.DT_bfaces)
+        for p, (ptype, value) in enumerate(case.patches):
+            B.lfm_set_patch(self.ctx, p, int(ptype), None, float(value))
+        B.lfm_set_time_step(self.ctx, case.dt)
+        B.lfm_set_solver(self.ctx, case.tol, case.rel_tol, case.max_iter, case.min_iter, case.precision)
+        if field:
+            B.lfm_set_field(self.ctx, field_by_label(case, m))
+
+    def set_solver(self, tol, rel_tol=0.0, max_iter=1000, min_iter=0, precision=B.LFM_FP64):
+        B.lfm_set_solver(self.ctx, tol, rel_tol, max_iter, min_iter, precision)
+
+    def set_field(self, T: np.ndarray):
+        B.lfm_set_field(self.ctx, T)
+
+    def set_field_device(self, ptr: int):
+        B.lfm_set_field_device(self.ctx, ptr)
+
+    # ---- running ---------------------------------------------------------------------
+    def advance(self, n_steps: int) -> List[dict]:
+        return [s.as_dict() for s in B.lfm_advance(self.ctx, n_steps)]
+
+    def advance_async(self, n_steps: int):
+        B.lfm_advance_async(self.ctx, n_steps)
+
+    def done(self) -> bool:
+        return B.lfm_query(self.ctx) == B.LFM_OK
+
+    def finish(self, n: int) -> List[dict]:
+        return [s.as_dict() for s in B.lfm_finish(self.ctx, n)]
+
+    # ---- results ---------------------------------------------------------------------
+    def field(self, out: Optional[np.ndarray] = None) -> np.ndarray:
+        return B.lfm_get_field(self.ctx, self.mesh.n_cells, out=out)
+
+    def fields(self):
+        return B.lfm_get_field(self.ctx, self.mesh.n_cells, self.mesh.n_bfaces, boundary=True)
+
+    def field_device_ptr(self) -> int:
+        return B.lfm_field_device_ptr(self.ctx)
+
+    def matrix(self):
+        return B.lfm_get_matrix(self.ctx, self.mesh.n_cells, self.mesh.n_faces)
+
+    def launch(self):
+        return B.lfm_get_launch(self.ctx)
+
+    def set_launch(self, ctas: int, threads: int):
+        B.lfm_set_launch(self.ctx, ctas, threads)
+
+    def close(self):
+        if self.ctx is not None:
+            B.lfm_destroy(self.ctx)
+            self.ctx = None
+        self._ws = None
+
+    def __enter__(self):
+        return self
+
+    def __exit__(self, *exc):
+        self.close()
+
+    def __del__(self):
+        try:
+            self.close()
+        except Exception:
+            pass
