@@ -121,9 +121,12 @@ size_t lfm_workspace_bytes(const lfm_mesh *mesh, int32_t precision);
  * cudaStream_t; NULL = legacy default stream). */
 int lfm_create(lfm_ctx **out, int device, void *cuda_stream);
 
-/* Binds caller-owned device memory (at least lfm_workspace_bytes, 256-byte aligned) that
- * upload carves all device arrays from. Must precede lfm_upload_mesh; never freed here. */
-int lfm_bind_workspace(lfm_ctx *ctx, void *dev_ptr, size_t bytes);
+/* Binds caller-owned device memory that upload carves all device arrays from: at least
+ * lfm_workspace_bytes(mesh, precision) bytes, 256-byte aligned; `precision` (LFM_FP64,
+ * LFM_MIXED, or -1 for both) selects which solver buffers it holds, and lfm_set_solver
+ * refuses a precision it does not hold (LFM_ENOMEM). Must precede lfm_upload_mesh; the
+ * library never frees it. */
+int lfm_bind_workspace(lfm_ctx *ctx, void *dev_ptr, size_t bytes, int32_t precision);
 
 /* Validates and uploads the mesh (deep copy), builds the face-to-cell addressing and the
  * cell-side boundary-face lists. Resets DT to 0, every patch to zeroGradient, dt to 1,

@@ -63,7 +63,7 @@ _SIGS = {
                              POINTER(c_int32), POINTER(c_int32)], c_int),
     "lfm_workspace_bytes": ([POINTER(lfm_mesh), c_int32], c_size_t),
     "lfm_create": ([POINTER(_ctx_p), c_int, c_void_p], c_int),
-    "lfm_bind_workspace": ([_ctx_p, c_void_p, c_size_t], c_int),
+    "lfm_bind_workspace": ([_ctx_p, c_void_p, c_size_t, c_int32], c_int),
     "lfm_upload_mesh": ([_ctx_p, POINTER(lfm_mesh)], c_int),
     "lfm_set_diffusivity": ([_ctx_p, c_double, POINTER(c_double), POINTER(c_double)], c_int),
     "lfm_set_patch": ([_ctx_p, c_int32, c_int32, POINTER(c_double), c_double], c_int),
@@ -195,8 +195,8 @@ def lfm_create(device: int = 0, stream: Optional[int] = None) -> c_void_p:
     return ctx
 
 
-def lfm_bind_workspace(ctx, dev_ptr: int, nbytes: int):
-    _check(load().lfm_bind_workspace(ctx, c_void_p(dev_ptr), nbytes), ctx)
+def lfm_bind_workspace(ctx, dev_ptr: int, nbytes: int, precision: int = LFM_BOTH):
+    _check(load().lfm_bind_workspace(ctx, c_void_p(dev_ptr), nbytes, precision), ctx)
 
 
 def lfm_upload_mesh(ctx, mesh):

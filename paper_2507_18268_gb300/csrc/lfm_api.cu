@@ -34,10 +34,10 @@ size_t align_up(size_t v, size_t a) { return (v + a - 1) / a * a; }
 // Byte layout of a case's workspace. Offsets are relative to the workspace base.
 struct Layout {
   size_t sync, partials, stats;
-  size_t nbr, own_start, losort, lo_start, lo_other, b_start, b_face, bcell, btype;
+  size_t slot_other, slot_face, b_start, b_face, bcell, btype;
   size_t V, magSf, delta, DT, bmagSf, bdelta, bDT, bval;
-  size_t diag, upper, src, rD, x, r, w, p, q, Tb;
-  size_t diag32, upper32, rD32, dx32, r32, w32, p32, q32;
+  size_t diag, upper, slot_coef, src, rD, x, r, w, p, q, Tb;
+  size_t diag32, slot_coef32, rD32, dx32, r32, w32, p32, q32;
   size_t total;
 };
 
@@ -45,7 +45,7 @@ struct Layout {
 // kLayoutBoth (both sets, so that the precision may change after upload).
 constexpr int kLayoutBoth = -1;
 
-Layout make_layout(int64_t N, int64_t F, int64_t NB, int kind) {
+Layout make_layout(int64_t N, int64_t F, int64_t NB, int64_t W, int kind) {
   Layout L{};
   size_t o = 0;
   auto take = [&](size_t bytes) {
@@ -56,11 +56,8 @@ Layout make_layout(int64_t N, int64_t F, int64_t NB, int kind) {
   L.sync = take(sizeof(SyncWords));
   L.partials = take(sizeof(double) * kMaxCtas * kMaxSums);
   L.stats = take(sizeof(lfm_step_stats) * kStatsCap);
-  L.nbr = take(4 * F);
-  L.own_start = take(4 * (N + 1));
-  L.losort = take(4 * F);
-  L.lo_start = take(4 * (N + 1));
-  L.lo_other = take(4 * F);
+  L.slot_other = take(4 * W * N);
+  L.slot_face = take(4 * W * N);
   L.b_start = take(4 * (N + 1));
   L.b_face = take(4 * NB);
   L.bcell = take(4 * NB);
@@ -75,12 +72,13 @@ Layout make_layout(int64_t N, int64_t F, int64_t NB, int kind) {
   L.bval = take(8 * NB);
   L.diag = take(8 * N);
   L.upper = take(8 * F);
+  L.slot_coef = take(8 * W * N);
   L.src = take(8 * N);
   L.rD = take(8 * N);
   L.x = take(8 * N);
   L.Tb = take(8 * NB);
   L.r = L.w = L.p = L.q = 0;
-  L.diag32 = L.upper32 = L.rD32 = L.dx32 = L.r32 = L.w32 = L.p32 = L.q32 = 0;
+  L.diag32 = L.slot_coef32 = L.rD32 = L.dx32 = L.r32 = L.w32 = L.p32 = L.q32 = 0;
   if (kind == LFM_FP64 || kind == kLayoutBoth) {
     L.r = take(8 * N);
     L.w = take(8 * N);
@@ -89,7 +87,7 @@ Layout make_layout(int64_t N, int64_t F, int64_t NB, int kind) {
   }
   if (kind == LFM_MIXED || kind == kLayoutBoth) {
     L.diag32 = take(4 * N);
-    L.upper32 = take(4 * F);
+    L.slot_coef32 = take(4 * W * N);
     L.rD32 = take(4 * N);
     L.dx32 = take(4 * N);
     L.r32 = take(4 * N);
@@ -125,10 +123,11 @@ struct lfm_ctx {
   size_t ws_bytes = 0;
   bool ws_owned = false;
   bool ws_bound = false;
+  int ws_kind = -1;                   // solver buffers a bound workspace holds
 
   // case
   bool uploaded = false;
-  int32_t N = 0, F = 0, NB = 0;
+  int32_t N = 0, F = 0, NB = 0, W = 0;
   int32_t n_patches = 0;
   std::vector<int32_t> patch_start, patch_size, patch_type;
   Layout lay{};
@@ -240,6 +239,18 @@ void bucket(int32_t n_keys, int64_t n_items, const int32_t* key, int32_t* start,
   for (int64_t i = 0; i < n_items; ++i) order[fill[key[i]]++] = (int32_t)i;
 }
 
+// Largest number of internal faces of any cell (the slot width of the layout).
+int32_t slot_width(const lfm_mesh* m) {
+  std::vector<int32_t> deg(m->n_cells, 0);
+  for (int32_t f = 0; f < m->n_faces; ++f) {
+    ++deg[m->owner[f]];
+    ++deg[m->neighbour[f]];
+  }
+  int32_t W = 0;
+  for (int32_t v : deg) W = v > W ? v : W;
+  return W;
+}
+
 template <class T>
 int h2d(lfm_ctx* c, size_t off, const T* src, size_t n) {
   if (n == 0) return LFM_OK;
@@ -249,7 +260,7 @@ int h2d(lfm_ctx* c, size_t off, const T* src, size_t n) {
 
 int choose_launch(lfm_ctx* c) {
   const int threads = 512;
-  int maxc = max_coresident_ctas(c->opts.precision, threads, c->device);
+  int maxc = max_coresident_ctas(c->opts.precision, threads, c->W, c->device);
   if (maxc <= 0) return fail(c, LFM_ECUDA, "cannot size the cooperative launch");
   int64_t want = ((int64_t)c->N + 4095) / 4096;
   if (want < 1) want = 1;
@@ -262,7 +273,7 @@ int choose_launch(lfm_ctx* c) {
 Launch current_launch(lfm_ctx* c, int& err) {
   Launch L{};
   L.threads = c->threads > 0 ? c->threads : c->tuned_threads;
-  int maxc = max_coresident_ctas(c->opts.precision, L.threads, c->device);
+  int maxc = max_coresident_ctas(c->opts.precision, L.threads, c->W, c->device);
   L.ctas = c->ctas > 0 ? c->ctas : c->tuned_ctas;
   if (L.ctas > maxc) L.ctas = maxc;
   err = L.ctas <= 0 ? 1 : 0;
@@ -291,11 +302,9 @@ void bind_pointers(lfm_ctx* c) {
   cs.sync = reinterpret_cast<SyncWords*>(b + L.sync);
   cs.partials = reinterpret_cast<double*>(b + L.partials);
   cs.stats = reinterpret_cast<lfm_step_stats*>(b + L.stats);
-  cs.nbr = reinterpret_cast<const int32_t*>(b + L.nbr);
-  cs.own_start = reinterpret_cast<const int32_t*>(b + L.own_start);
-  cs.losort = reinterpret_cast<const int32_t*>(b + L.losort);
-  cs.lo_start = reinterpret_cast<const int32_t*>(b + L.lo_start);
-  cs.lo_other = reinterpret_cast<const int32_t*>(b + L.lo_other);
+  cs.W = c->W;
+  cs.slot_other = reinterpret_cast<const int32_t*>(b + L.slot_other);
+  cs.slot_face = reinterpret_cast<const int32_t*>(b + L.slot_face);
   cs.b_start = reinterpret_cast<const int32_t*>(b + L.b_start);
   cs.b_face = reinterpret_cast<const int32_t*>(b + L.b_face);
   cs.bcell = reinterpret_cast<const int32_t*>(b + L.bcell);
@@ -310,6 +319,7 @@ void bind_pointers(lfm_ctx* c) {
   cs.bval = reinterpret_cast<const double*>(b + L.bval);
   cs.diag = reinterpret_cast<double*>(b + L.diag);
   cs.upper = reinterpret_cast<double*>(b + L.upper);
+  cs.slot_coef = reinterpret_cast<double*>(b + L.slot_coef);
   cs.src = reinterpret_cast<double*>(b + L.src);
   cs.rD = reinterpret_cast<double*>(b + L.rD);
   cs.x = reinterpret_cast<double*>(b + L.x);
@@ -319,7 +329,7 @@ void bind_pointers(lfm_ctx* c) {
   cs.p = d ? reinterpret_cast<double*>(b + L.p) : nullptr;
   cs.q = d ? reinterpret_cast<double*>(b + L.q) : nullptr;
   cs.diag32 = m ? reinterpret_cast<float*>(b + L.diag32) : nullptr;
-  cs.upper32 = m ? reinterpret_cast<float*>(b + L.upper32) : nullptr;
+  cs.slot_coef32 = m ? reinterpret_cast<float*>(b + L.slot_coef32) : nullptr;
   cs.rD32 = m ? reinterpret_cast<float*>(b + L.rD32) : nullptr;
   cs.dx32 = m ? reinterpret_cast<float*>(b + L.dx32) : nullptr;
   cs.r32 = m ? reinterpret_cast<float*>(b + L.r32) : nullptr;
@@ -399,9 +409,13 @@ int lfm_face_addressing(int32_t n_cells, int32_t n_faces, const int32_t* owner, 
 }
 
 size_t lfm_workspace_bytes(const lfm_mesh* mesh, int32_t precision) {
-  if (!mesh || mesh->n_cells <= 0) return 0;
+  std::string why;
+  if (check_mesh(mesh, why) != LFM_OK) {
+    g_last_error = why;
+    return 0;
+  }
   if (precision != LFM_FP64 && precision != LFM_MIXED) precision = kLayoutBoth;
-  return make_layout(mesh->n_cells, mesh->n_faces, mesh->n_bfaces, precision).total;
+  return make_layout(mesh->n_cells, mesh->n_faces, mesh->n_bfaces, slot_width(mesh), precision).total;
 }
 
 int lfm_create(lfm_ctx** out, int device, void* cuda_stream) {
@@ -426,7 +440,7 @@ int lfm_create(lfm_ctx** out, int device, void* cuda_stream) {
   return LFM_OK;
 }
 
-int lfm_bind_workspace(lfm_ctx* c, void* dev_ptr, size_t bytes) {
+int lfm_bind_workspace(lfm_ctx* c, void* dev_ptr, size_t bytes, int32_t precision) {
   if (!c) return fail_free(LFM_EINVAL, "context is NULL");
   if (c->uploaded) return fail(c, LFM_ESTATE, "bind the workspace before uploading a mesh");
   if (!dev_ptr || (reinterpret_cast<uintptr_t>(dev_ptr) & 255)) return fail(c, LFM_EINVAL, "workspace must be 256-byte aligned");
@@ -434,6 +448,7 @@ int lfm_bind_workspace(lfm_ctx* c, void* dev_ptr, size_t bytes) {
   c->ws_bytes = bytes;
   c->ws_bound = true;
   c->ws_owned = false;
+  c->ws_kind = (precision == LFM_FP64 || precision == LFM_MIXED) ? precision : kLayoutBoth;
   return LFM_OK;
 }
 
@@ -442,24 +457,13 @@ int lfm_upload_mesh(lfm_ctx* c, const lfm_mesh* m) {
   std::string why;
   if (check_mesh(m, why) != LFM_OK) return fail(c, LFM_EINVAL, "%s", why.c_str());
   DeviceGuard g(c->device);
-  // A bound workspace gets the largest layout it holds (both solver blocks, else FP64,
-  // else mixed); a library-owned one holds both.
-  const Layout Lb = make_layout(m->n_cells, m->n_faces, m->n_bfaces, kLayoutBoth);
-  const Layout L64 = make_layout(m->n_cells, m->n_faces, m->n_bfaces, LFM_FP64);
-  const Layout L32 = make_layout(m->n_cells, m->n_faces, m->n_bfaces, LFM_MIXED);
-  Layout use = Lb;
-  bool has64 = true, has32 = true;
+  const int32_t W = slot_width(m);
+  if (W > kMaxSlots) return fail(c, LFM_EINVAL, "a cell has %d internal faces (at most %d supported)", W, kMaxSlots);
+  const int kind = c->ws_bound ? c->ws_kind : kLayoutBoth;
+  const Layout use = make_layout(m->n_cells, m->n_faces, m->n_bfaces, W, kind);
+  const bool has64 = kind != LFM_MIXED, has32 = kind != LFM_FP64;
   if (c->ws_bound) {
-    if (c->ws_bytes >= Lb.total) {
-    } else if (c->ws_bytes >= L64.total) {
-      use = L64;
-      has32 = false;
-    } else if (c->ws_bytes >= L32.total) {
-      use = L32;
-      has64 = false;
-    } else {
-      return fail(c, LFM_ENOMEM, "workspace has %zu bytes, needs %zu", c->ws_bytes, L32.total);
-    }
+    if (c->ws_bytes < use.total) return fail(c, LFM_ENOMEM, "workspace has %zu bytes, needs %zu", c->ws_bytes, use.total);
   } else {
     if (c->ws_owned && c->ws) {
       cudaFree(c->ws);
@@ -476,6 +480,7 @@ int lfm_upload_mesh(lfm_ctx* c, const lfm_mesh* m) {
   c->N = m->n_cells;
   c->F = m->n_faces;
   c->NB = m->n_bfaces;
+  c->W = W;
   c->has64 = has64;
   c->has32 = has32;
   c->n_patches = m->n_patches;
@@ -485,25 +490,45 @@ int lfm_upload_mesh(lfm_ctx* c, const lfm_mesh* m) {
   bind_pointers(c);
 
   const int32_t N = c->N, F = c->F, NB = c->NB;
-  std::vector<int32_t> own_start(N + 1), lo_start(N + 1), losort(F > 0 ? F : 1), lo_other(F > 0 ? F : 1);
+  std::vector<int32_t> own_start(N + 1), lo_start(N + 1), losort(F > 0 ? F : 1);
   int rc = lfm_face_addressing(N, F, m->owner, m->neighbour, own_start.data(), losort.data(), lo_start.data());
   if (rc != LFM_OK) return fail(c, rc, "%s", g_last_error.c_str());
-  for (int32_t i = 0; i < F; ++i) lo_other[i] = m->owner[losort[i]];
+  // Slot-major copy of the face-to-cell lists: neighbour-side faces, owned faces, padding.
+  std::vector<int32_t> slot_other((size_t)W * N), slot_face((size_t)W * N);
+  for (int32_t cell = 0; cell < N; ++cell) {
+    int k = 0;
+    for (int32_t i = lo_start[cell]; i < lo_start[cell + 1]; ++i, ++k) {
+      slot_other[(size_t)k * N + cell] = m->owner[losort[i]];
+      slot_face[(size_t)k * N + cell] = losort[i];
+    }
+    for (int32_t f = own_start[cell]; f < own_start[cell + 1]; ++f, ++k) {
+      slot_other[(size_t)k * N + cell] = m->neighbour[f];
+      slot_face[(size_t)k * N + cell] = f;
+    }
+    for (; k < W; ++k) {
+      slot_other[(size_t)k * N + cell] = cell;
+      slot_face[(size_t)k * N + cell] = -1;
+    }
+  }
   std::vector<int32_t> b_start(N + 1), b_face(NB > 0 ? NB : 1);
   bucket(N, NB, m->bface_cell, b_start.data(), b_face.data());
   std::vector<int32_t> btype(NB > 0 ? NB : 1, LFM_ZERO_GRADIENT);
   std::vector<double> zeros_b(NB > 0 ? NB : 1, 0.0);
 
   const Layout& Y = c->lay;
-  if ((rc = h2d(c, Y.nbr, m->neighbour, F)) || (rc = h2d(c, Y.own_start, own_start.data(), N + 1)) ||
-      (rc = h2d(c, Y.losort, losort.data(), F)) || (rc = h2d(c, Y.lo_start, lo_start.data(), N + 1)) ||
-      (rc = h2d(c, Y.lo_other, lo_other.data(), F)) || (rc = h2d(c, Y.b_start, b_start.data(), N + 1)) ||
+  const size_t WN = (size_t)W * N;
+  if ((rc = h2d(c, Y.slot_other, slot_other.data(), WN)) || (rc = h2d(c, Y.slot_face, slot_face.data(), WN)) ||
+      (rc = h2d(c, Y.b_start, b_start.data(), N + 1)) ||
       (rc = h2d(c, Y.b_face, b_face.data(), NB)) || (rc = h2d(c, Y.bcell, m->bface_cell, NB)) ||
       (rc = h2d(c, Y.btype, btype.data(), NB)) || (rc = h2d(c, Y.V, m->V, N)) ||
       (rc = h2d(c, Y.magSf, m->magSf, F)) || (rc = h2d(c, Y.delta, m->deltaCoeffs, F)) ||
       (rc = h2d(c, Y.bmagSf, m->bmagSf, NB)) || (rc = h2d(c, Y.bdelta, m->bdeltaCoeffs, NB)) ||
       (rc = h2d(c, Y.bDT, zeros_b.data(), NB)) || (rc = h2d(c, Y.bval, zeros_b.data(), NB)))
     return rc;
+  if (WN > 0) {
+    CK(c, cudaMemsetAsync(c->ws + Y.slot_coef, 0, sizeof(double) * WN, c->stream));
+    if (has32) CK(c, cudaMemsetAsync(c->ws + Y.slot_coef32, 0, sizeof(float) * WN, c->stream));
+  }
   CK(c, cudaMemsetAsync(c->ws + Y.DT, 0, sizeof(double) * (F > 0 ? F : 1), c->stream));
   CK(c, cudaMemsetAsync(c->ws + Y.x, 0, sizeof(double) * N, c->stream));
   CK(c, cudaStreamSynchronize(c->stream));

@@ -15,6 +15,7 @@ constexpr int kMaxSums = 4;          // scalars reduced per team barrier
 constexpr int kMaxCtas = 8192;       // capacity of the per-CTA partial-sum table
 constexpr int kStatsCap = 1024;      // per-launch statistics records
 constexpr int kMaxSweeps = 5;        // mixed precision: defect-correction sweeps per step
+constexpr int kMaxSlots = 32;        // largest number of internal faces per cell
 
 // Barrier words of one team of CTAs; each field sits on its own 128-byte line.
 struct alignas(128) SyncWords {
@@ -36,12 +37,12 @@ struct CaseDev {
   double tol, rel_tol;
   int32_t max_iter, min_iter;
 
-  // face-to-cell addressing (constant for a mesh)
-  const int32_t* nbr;        // [F]   neighbour of face f (the other cell for its owner)
-  const int32_t* own_start;  // [N+1] faces owned by c: [own_start[c], own_start[c+1])
-  const int32_t* losort;     // [F]   faces sorted by neighbour, ascending face id per cell
-  const int32_t* lo_start;   // [N+1] neighbour-side faces of c: losort[lo_start[c] ..)
-  const int32_t* lo_other;   // [F]   owner of face losort[i]
+  // face-to-cell addressing, slot-major ("ELL"): each cell has W slots, slot k of cell c at
+  // index k*N + c. Slots hold the cell's neighbour-side faces (ascending face id), then its
+  // owned faces (ascending), then padding (other = c, face = -1, coefficient 0).
+  int32_t W;
+  const int32_t* slot_other; // [W*N] the other cell of the slot's face
+  const int32_t* slot_face;  // [W*N] face id, -1 for padding
   const int32_t* b_start;    // [N+1] boundary faces of c: b_face[b_start[c] ..)
   const int32_t* b_face;     // [NB]  boundary faces sorted by cell, ascending id per cell
   const int32_t* bcell;      // [NB]  cell of boundary face b
@@ -57,9 +58,10 @@ struct CaseDev {
   const double* bval;        // [NB]  fixedValue values
   const int32_t* btype;      // [NB]  LFM_FIXED_VALUE / LFM_ZERO_GRADIENT
 
-  // assembled matrix (FP64)
+  // assembled matrix (FP64): LDU (diag, upper) plus the per-slot copy of the off-diagonals
   double* diag;              // [N]
   double* upper;             // [F]  (lower == upper)
+  double* slot_coef;         // [W*N]
   double* src;               // [N]
   double* rD;                // [N]  1/diag
 
@@ -72,7 +74,7 @@ struct CaseDev {
 
   // mixed precision: FP32 matrix copy and inner-solve vectors
   float* diag32;
-  float* upper32;
+  float* slot_coef32;        // [W*N]
   float* rD32;
   float* dx32;
   float* r32;
@@ -99,7 +101,7 @@ enum Mode { kModeSteps = 0, kModeAssembleOnly = 1 };
 cudaError_t launch_steps(const CaseDev& cs, const Launch& L, int n_steps, int mode,
                          cudaStream_t stream);
 // Largest co-resident CTA count for the step kernel at `threads` per CTA.
-int max_coresident_ctas(int precision, int threads, int device);
+int max_coresident_ctas(int precision, int threads, int W, int device);
 cudaError_t launch_boundary_values(const CaseDev& cs, double* Tb, cudaStream_t stream);
 cudaError_t launch_fill(double* a, size_t n, double v, cudaStream_t stream);
 

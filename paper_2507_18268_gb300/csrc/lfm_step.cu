@@ -3,12 +3,15 @@
 // solve of fvm::ddt(T) - fvm::laplacian(DT, T)).
 //
 // One launch runs n steps. Each CTA of the team owns a contiguous range of cells and, in
-// every phase, computes whole matrix rows by gathering over the face-to-cell lists (the
+// every phase, computes whole matrix rows by gathering over the face-to-cell slots (the
 // paper's atomic-free rewrite of the face loop, listing "First cycle gradient in
-// parallel"): no atomics touch data and every reduction has a fixed order.
+// parallel"): no atomics touch data and every reduction has a fixed order. A thread takes
+// two cells per loop trip and issues all their loads before using any, so that each thread
+// keeps a dozen independent memory requests in flight.
 //
 // FP64 step (phases separated by team barriers):
-//   A  assembly        diag, upper (owner-side faces), source, rD; sum x for xRef
+//   A  assembly        per slot g = DT |Sf| deltaCoeff; diag, upper (LDU), slot copy,
+//                      source, rD = 1/diag; sum x for xRef
 //   I  initial state   A x, r = b - A x, row sums -> normFactor, sum|r|, w = rD r, rho;
 //                      p = w (first search direction)
 //   loop (diagonal-preconditioned CG, convergence on sum|r| / normFactor):
@@ -46,25 +49,33 @@ __device__ __forceinline__ void cta_range(int N, int size, int rank, int& c0, in
   c1 = (int)(b < N ? b : N);
 }
 
+// Slot count: the compile-time width when the kernel is specialised, else the case's.
+template <int W>
+__device__ __forceinline__ int nslots(const CaseDev& cs) {
+  return W > 0 ? W : cs.W;
+}
+
 // ---- assembly: one row of fvm::ddt(T) - fvm::laplacian(DT, T) -------------------------
-// The row's diagonal is summed in ascending face order (neighbour-side faces first: their
-// owners are smaller labels, so they precede the cell's own faces in upper-triangular
-// order), then boundary faces, then V/dt, each product rounded separately (no FMA).
-template <bool kMixed>
+// The diagonal is summed in slot order, i.e. ascending face order (neighbour-side faces
+// have smaller owners, so they precede the cell's own faces in upper-triangular order),
+// then the boundary faces, then V/dt; every product and sum is rounded separately (no FMA).
+template <int W, bool kMixed>
 __device__ __forceinline__ double assemble_row(const CaseDev& cs, int c) {
+  const size_t N = (size_t)cs.N;
+  const int ns = nslots<W>(cs);
   double d = 0.0, s = 0.0;
-  const int lo0 = __ldg(cs.lo_start + c), lo1 = __ldg(cs.lo_start + c + 1);
-  for (int i = lo0; i < lo1; ++i) {
-    const int f = __ldg(cs.losort + i);
-    const double g = __dmul_rn(__dmul_rn(__ldg(cs.DT + f), __ldg(cs.magSf + f)), __ldg(cs.delta + f));
-    d = __dadd_rn(d, g);
-  }
-  const int f0 = __ldg(cs.own_start + c), f1 = __ldg(cs.own_start + c + 1);
-  for (int f = f0; f < f1; ++f) {
-    const double g = __dmul_rn(__dmul_rn(__ldg(cs.DT + f), __ldg(cs.magSf + f)), __ldg(cs.delta + f));
-    cs.upper[f] = -g;
-    if (kMixed) cs.upper32[f] = (float)(-g);
-    d = __dadd_rn(d, g);
+#pragma unroll
+  for (int k = 0; k < (W > 0 ? W : kMaxSlots); ++k) {
+    if (W == 0 && k >= ns) break;
+    const size_t at = (size_t)k * N + c;
+    const int f = __ldg(cs.slot_face + at);
+    if (f >= 0) {
+      const double g = __dmul_rn(__dmul_rn(__ldg(cs.DT + f), __ldg(cs.magSf + f)), __ldg(cs.delta + f));
+      cs.slot_coef[at] = -g;
+      if (kMixed) cs.slot_coef32[at] = (float)(-g);
+      if (__ldg(cs.slot_other + at) > c) cs.upper[f] = -g;
+      d = __dadd_rn(d, g);
+    }
   }
   const int b0 = __ldg(cs.b_start + c), b1 = __ldg(cs.b_start + c + 1);
   for (int k = b0; k < b1; ++k) {
@@ -90,37 +101,125 @@ __device__ __forceinline__ double assemble_row(const CaseDev& cs, int c) {
   return xc;
 }
 
-// ---- FP64 row of A v (gather over the face-to-cell lists) ----------------------------
-template <bool kRowSum>
-__device__ __forceinline__ double row_f64(const CaseDev& cs, int c, const double* __restrict__ v,
-                                          double d, double vc, double& rowsum) {
-  double acc = d * vc;
+// ---- FP64 row of A v, products and sums rounded separately in slot order ---------------
+// Reproduces a serial face loop's rounding exactly; also returns the row sum of A.
+template <int W>
+__device__ __forceinline__ double row_exact(const CaseDev& cs, int c, const double* __restrict__ v,
+                                            double d, double vc, double& rowsum) {
+  const size_t N = (size_t)cs.N;
+  const int ns = nslots<W>(cs);
+  double acc = __dmul_rn(d, vc);
   double rs = d;
-  const int lo0 = __ldg(cs.lo_start + c), lo1 = __ldg(cs.lo_start + c + 1);
-  for (int i = lo0; i < lo1; ++i) {
-    const double u = cs.upper[__ldg(cs.losort + i)];
-    acc = fma(u, v[__ldg(cs.lo_other + i)], acc);
-    if (kRowSum) rs += u;
+#pragma unroll
+  for (int k = 0; k < (W > 0 ? W : kMaxSlots); ++k) {
+    if (W == 0 && k >= ns) break;
+    const size_t at = (size_t)k * N + c;
+    const double u = cs.slot_coef[at];
+    const double vo = v[__ldg(cs.slot_other + at)];
+    acc = __dadd_rn(acc, __dmul_rn(u, vo));
+    rs = __dadd_rn(rs, u);
   }
-  const int f0 = __ldg(cs.own_start + c), f1 = __ldg(cs.own_start + c + 1);
-  for (int f = f0; f < f1; ++f) {
-    const double u = cs.upper[f];
-    acc = fma(u, v[__ldg(cs.nbr + f)], acc);
-    if (kRowSum) rs += u;
-  }
-  if (kRowSum) rowsum = rs;
+  rowsum = rs;
   return acc;
 }
 
-// ---- FP32 row of A v ------------------------------------------------------------------
-__device__ __forceinline__ float row_f32(const CaseDev& cs, int c, const float* __restrict__ v,
-                                         float d, float vc) {
-  float acc = d * vc;
-  const int lo0 = __ldg(cs.lo_start + c), lo1 = __ldg(cs.lo_start + c + 1);
-  for (int i = lo0; i < lo1; ++i)
-    acc = fmaf(cs.upper32[__ldg(cs.losort + i)], v[__ldg(cs.lo_other + i)], acc);
-  const int f0 = __ldg(cs.own_start + c), f1 = __ldg(cs.own_start + c + 1);
-  for (int f = f0; f < f1; ++f) acc = fmaf(cs.upper32[f], v[__ldg(cs.nbr + f)], acc);
+// ---- FP64 A v for two rows at once (FMA accumulation) ----------------------------------
+template <int W>
+__device__ __forceinline__ void rows2_f64(const CaseDev& cs, int c, int c2, const double* __restrict__ v,
+                                          double& y, double& y2, double& vc, double& vc2) {
+  const size_t N = (size_t)cs.N;
+  vc = v[c];
+  vc2 = v[c2];
+  double acc = cs.diag[c] * vc, acc2 = cs.diag[c2] * vc2;
+  if constexpr (W > 0) {
+    int o[W], o2[W];
+    double u[W], u2[W];
+#pragma unroll
+    for (int k = 0; k < W; ++k) {
+      o[k] = __ldg(cs.slot_other + (size_t)k * N + c);
+      o2[k] = __ldg(cs.slot_other + (size_t)k * N + c2);
+      u[k] = cs.slot_coef[(size_t)k * N + c];
+      u2[k] = cs.slot_coef[(size_t)k * N + c2];
+    }
+#pragma unroll
+    for (int k = 0; k < W; ++k) {
+      acc = fma(u[k], v[o[k]], acc);
+      acc2 = fma(u2[k], v[o2[k]], acc2);
+    }
+  } else {
+    const int ns = cs.W;
+    for (int k = 0; k < ns; ++k) {
+      const size_t at = (size_t)k * N;
+      acc = fma(cs.slot_coef[at + c], v[__ldg(cs.slot_other + at + c)], acc);
+      acc2 = fma(cs.slot_coef[at + c2], v[__ldg(cs.slot_other + at + c2)], acc2);
+    }
+  }
+  y = acc;
+  y2 = acc2;
+}
+
+template <int W>
+__device__ __forceinline__ double row_f64(const CaseDev& cs, int c, const double* __restrict__ v, double& vc) {
+  const size_t N = (size_t)cs.N;
+  const int ns = nslots<W>(cs);
+  vc = v[c];
+  double acc = cs.diag[c] * vc;
+#pragma unroll
+  for (int k = 0; k < (W > 0 ? W : kMaxSlots); ++k) {
+    if (W == 0 && k >= ns) break;
+    const size_t at = (size_t)k * N + c;
+    acc = fma(cs.slot_coef[at], v[__ldg(cs.slot_other + at)], acc);
+  }
+  return acc;
+}
+
+// ---- FP32 A v --------------------------------------------------------------------------
+template <int W>
+__device__ __forceinline__ void rows2_f32(const CaseDev& cs, int c, int c2, const float* __restrict__ v,
+                                          float& y, float& y2, float& vc, float& vc2) {
+  const size_t N = (size_t)cs.N;
+  vc = v[c];
+  vc2 = v[c2];
+  float acc = cs.diag32[c] * vc, acc2 = cs.diag32[c2] * vc2;
+  if constexpr (W > 0) {
+    int o[W], o2[W];
+    float u[W], u2[W];
+#pragma unroll
+    for (int k = 0; k < W; ++k) {
+      o[k] = __ldg(cs.slot_other + (size_t)k * N + c);
+      o2[k] = __ldg(cs.slot_other + (size_t)k * N + c2);
+      u[k] = cs.slot_coef32[(size_t)k * N + c];
+      u2[k] = cs.slot_coef32[(size_t)k * N + c2];
+    }
+#pragma unroll
+    for (int k = 0; k < W; ++k) {
+      acc = fmaf(u[k], v[o[k]], acc);
+      acc2 = fmaf(u2[k], v[o2[k]], acc2);
+    }
+  } else {
+    const int ns = cs.W;
+    for (int k = 0; k < ns; ++k) {
+      const size_t at = (size_t)k * N;
+      acc = fmaf(cs.slot_coef32[at + c], v[__ldg(cs.slot_other + at + c)], acc);
+      acc2 = fmaf(cs.slot_coef32[at + c2], v[__ldg(cs.slot_other + at + c2)], acc2);
+    }
+  }
+  y = acc;
+  y2 = acc2;
+}
+
+template <int W>
+__device__ __forceinline__ float row_f32(const CaseDev& cs, int c, const float* __restrict__ v, float& vc) {
+  const size_t N = (size_t)cs.N;
+  const int ns = nslots<W>(cs);
+  vc = v[c];
+  float acc = cs.diag32[c] * vc;
+#pragma unroll
+  for (int k = 0; k < (W > 0 ? W : kMaxSlots); ++k) {
+    if (W == 0 && k >= ns) break;
+    const size_t at = (size_t)k * N + c;
+    acc = fmaf(cs.slot_coef32[at], v[__ldg(cs.slot_other + at)], acc);
+  }
   return acc;
 }
 
@@ -141,13 +240,10 @@ __device__ __forceinline__ void write_stats(const CaseDev& cs, const Team& tm, i
 }
 
 // =======================================================================================
-// FP64 step kernel
+// FP64 steps
 // =======================================================================================
-template <int B>
-__global__ void __launch_bounds__(B) step_kernel_f64(CaseDev cs, Launch L, int n_steps, int mode) {
-  __shared__ TeamShared sh;
-  if ((int)blockIdx.x == L.skip_cta) return;  // test hook: never arrive
-  const Team tm{(int)gridDim.x, (int)blockIdx.x, cs.sync, cs.partials, L.timeout_ns};
+template <int B, int W>
+__device__ void run_steps_f64(const CaseDev& cs, const Team& tm, int n_steps, int mode, TeamShared& sh) {
   int c0, c1;
   cta_range(cs.N, tm.size, tm.rank, c0, c1);
   const int tid = threadIdx.x;
@@ -156,103 +252,133 @@ __global__ void __launch_bounds__(B) step_kernel_f64(CaseDev cs, Launch L, int n
   double* __restrict__ w = cs.w;
   double* __restrict__ p = cs.p;
   double* __restrict__ q = cs.q;
+  const double* __restrict__ rD = cs.rD;
 
   for (int step = 0; step < n_steps; ++step) {
-    // ---- A: assembly -------------------------------------------------------------------
-    {
-      double v[1] = {0.0};
-      for (int c = c0 + tid; c < c1; c += B) v[0] += assemble_row<false>(cs, c);
-      if (!team_allreduce<1>(tm, v, sh)) return;
-      if (mode == kModeAssembleOnly) return;
-      // ---- I: initial residual, normFactor, first direction ---------------------------
-      const double xRef = v[0] / (double)cs.N;
-      double u[3] = {0.0, 0.0, 0.0};  // normFactor sum, sum|r|, rho
-      for (int c = c0 + tid; c < c1; c += B) {
-        const double d = cs.diag[c], xc = x[c], b = cs.src[c];
-        double rs;
-        const double ax = row_f64<true>(cs, c, x, d, xc, rs);
-        const double rc = b - ax;
-        const double pA = rs * xRef;
-        u[0] += fabs(ax - pA) + fabs(b - pA);
-        u[1] += fabs(rc);
-        const double wc = cs.rD[c] * rc;
-        u[2] = fma(wc, rc, u[2]);
-        r[c] = rc;
-        p[c] = wc;
-      }
-      if (!team_allreduce<3>(tm, u, sh)) return;
-      const double nf = u[0] + kSmall;
-      const double init_res = u[1] / nf;
-      double res = init_res, rho = u[2], beta = 0.0;
-      int iters = 0, status = 0;
-      bool conv = converged(res, init_res, cs.tol, cs.rel_tol);
-      if (cs.min_iter > 0 || !conv) {
-        for (;;) {
-          if (iters > 0) {
-            // ---- P: search direction ------------------------------------------------
-            for (int c = c0 + tid; c < c1; c += B) p[c] = fma(beta, p[c], w[c]);
-            if (!team_barrier(tm, sh)) return;
+    // ---- A: assembly ---------------------------------------------------------------------
+    double v[1] = {0.0};
+    for (int c = c0 + tid; c < c1; c += B) v[0] += assemble_row<W, false>(cs, c);
+    if (!team_allreduce<1>(tm, v, sh)) return;
+    if (mode == kModeAssembleOnly) return;
+    // ---- I: initial residual, normFactor, first direction -----------------------------
+    const double xRef = v[0] / (double)cs.N;
+    double u[3] = {0.0, 0.0, 0.0};  // normFactor sum, sum|r|, rho
+    for (int c = c0 + tid; c < c1; c += B) {
+      const double d = cs.diag[c], xc = x[c], b = cs.src[c];
+      double rs;
+      const double ax = row_exact<W>(cs, c, x, d, xc, rs);
+      const double rc = b - ax;
+      const double pA = rs * xRef;
+      u[0] += fabs(ax - pA) + fabs(b - pA);
+      u[1] += fabs(rc);
+      const double wc = rD[c] * rc;
+      u[2] = fma(wc, rc, u[2]);
+      r[c] = rc;
+      p[c] = wc;
+    }
+    if (!team_allreduce<3>(tm, u, sh)) return;
+    const double nf = u[0] + kSmall;
+    const double init_res = u[1] / nf;
+    double res = init_res, rho = u[2], beta = 0.0;
+    int iters = 0, status = 0;
+    bool conv = converged(res, init_res, cs.tol, cs.rel_tol);
+    if (cs.min_iter > 0 || !conv) {
+      for (;;) {
+        if (iters > 0) {
+          // ---- P: search direction -------------------------------------------------
+          int c = c0 + tid;
+          for (; c + B < c1; c += 2 * B) {
+            const double p1 = p[c], p2 = p[c + B], w1 = w[c], w2 = w[c + B];
+            p[c] = fma(beta, p1, w1);
+            p[c + B] = fma(beta, p2, w2);
           }
-          // ---- M: q = A p, sigma = p.q ---------------------------------------------
-          double s1[1] = {0.0};
-          for (int c = c0 + tid; c < c1; c += B) {
-            const double pc = p[c];
-            double unused;
-            const double qc = row_f64<false>(cs, c, p, cs.diag[c], pc, unused);
-            q[c] = qc;
-            s1[0] = fma(qc, pc, s1[0]);
-          }
-          if (!team_allreduce<1>(tm, s1, sh)) return;
-          const double sigma = s1[0];
-          if (fabs(sigma) / nf < kVSmall) {
-            status = LFM_ESINGULAR;
-            break;
-          }
-          const double alpha = rho / sigma;
-          // ---- U: update, residual, preconditioned residual, next rho ---------------
-          double s2[2] = {0.0, 0.0};
-          for (int c = c0 + tid; c < c1; c += B) {
-            const double pc = p[c], qc = q[c];
-            const double xc = fma(alpha, pc, x[c]);
-            const double rc = fma(-alpha, qc, r[c]);
-            const double wc = cs.rD[c] * rc;
-            x[c] = xc;
-            r[c] = rc;
-            w[c] = wc;
-            s2[0] += fabs(rc);
-            s2[1] = fma(wc, rc, s2[1]);
-          }
-          if (!team_allreduce<2>(tm, s2, sh)) return;
-          res = s2[0] / nf;
-          beta = s2[1] / rho;
-          rho = s2[1];
-          ++iters;
-          if (!isfinite(res)) {
-            status = LFM_ENONFINITE;
-            break;
-          }
-          conv = converged(res, init_res, cs.tol, cs.rel_tol);
-          if (!((iters < cs.max_iter && !conv) || iters < cs.min_iter)) break;
+          if (c < c1) p[c] = fma(beta, p[c], w[c]);
+          if (!team_barrier(tm, sh)) return;
         }
+        // ---- M: q = A p, sigma = p.q ----------------------------------------------
+        double s1[1] = {0.0};
+        {
+          int c = c0 + tid;
+          for (; c + B < c1; c += 2 * B) {
+            double y1, y2, pc1, pc2;
+            rows2_f64<W>(cs, c, c + B, p, y1, y2, pc1, pc2);
+            q[c] = y1;
+            q[c + B] = y2;
+            s1[0] = fma(y1, pc1, s1[0]);
+            s1[0] = fma(y2, pc2, s1[0]);
+          }
+          if (c < c1) {
+            double pc;
+            const double y = row_f64<W>(cs, c, p, pc);
+            q[c] = y;
+            s1[0] = fma(y, pc, s1[0]);
+          }
+        }
+        if (!team_allreduce<1>(tm, s1, sh)) return;
+        const double sigma = s1[0];
+        if (fabs(sigma) / nf < kVSmall) {
+          status = LFM_ESINGULAR;
+          break;
+        }
+        const double alpha = rho / sigma;
+        // ---- U: update, residual, preconditioned residual, next rho ----------------
+        double s2[2] = {0.0, 0.0};
+        {
+          int c = c0 + tid;
+          for (; c + B < c1; c += 2 * B) {
+            const int e = c + B;
+            const double pa = p[c], pb = p[e], qa = q[c], qb = q[e];
+            const double xa = x[c], xb = x[e], ra = r[c], rb = r[e], da = rD[c], db = rD[e];
+            const double rna = fma(-alpha, qa, ra), rnb = fma(-alpha, qb, rb);
+            const double wa = da * rna, wb = db * rnb;
+            x[c] = fma(alpha, pa, xa);
+            x[e] = fma(alpha, pb, xb);
+            r[c] = rna;
+            r[e] = rnb;
+            w[c] = wa;
+            w[e] = wb;
+            s2[0] += fabs(rna);
+            s2[0] += fabs(rnb);
+            s2[1] = fma(wa, rna, s2[1]);
+            s2[1] = fma(wb, rnb, s2[1]);
+          }
+          if (c < c1) {
+            const double rn = fma(-alpha, q[c], r[c]);
+            const double wn = rD[c] * rn;
+            x[c] = fma(alpha, p[c], x[c]);
+            r[c] = rn;
+            w[c] = wn;
+            s2[0] += fabs(rn);
+            s2[1] = fma(wn, rn, s2[1]);
+          }
+        }
+        if (!team_allreduce<2>(tm, s2, sh)) return;
+        res = s2[0] / nf;
+        beta = s2[1] / rho;
+        rho = s2[1];
+        ++iters;
+        if (!isfinite(res)) {
+          status = LFM_ENONFINITE;
+          break;
+        }
+        conv = converged(res, init_res, cs.tol, cs.rel_tol);
+        if (!((iters < cs.max_iter && !conv) || iters < cs.min_iter)) break;
       }
-      conv = converged(res, init_res, cs.tol, cs.rel_tol);
-      write_stats(cs, tm, step, iters, conv ? 1 : 0, iters > 0 ? 1 : 0, status, init_res, res, nf);
-      if (status != 0) {
-        if (tm.rank == 0 && tid == 0) set_status(cs.sync, status);
-        return;
-      }
+    }
+    conv = converged(res, init_res, cs.tol, cs.rel_tol);
+    write_stats(cs, tm, step, iters, conv ? 1 : 0, iters > 0 ? 1 : 0, status, init_res, res, nf);
+    if (status != 0) {
+      if (tm.rank == 0 && tid == 0) set_status(cs.sync, status);
+      return;
     }
   }
 }
 
 // =======================================================================================
-// Mixed-precision step kernel (FP32 inner CG inside FP64 defect correction)
+// Mixed-precision steps (FP32 inner CG inside FP64 defect correction)
 // =======================================================================================
-template <int B>
-__global__ void __launch_bounds__(B) step_kernel_mixed(CaseDev cs, Launch L, int n_steps, int mode) {
-  __shared__ TeamShared sh;
-  if ((int)blockIdx.x == L.skip_cta) return;
-  const Team tm{(int)gridDim.x, (int)blockIdx.x, cs.sync, cs.partials, L.timeout_ns};
+template <int B, int W>
+__device__ void run_steps_mixed(const CaseDev& cs, const Team& tm, int n_steps, int mode, TeamShared& sh) {
   int c0, c1;
   cta_range(cs.N, tm.size, tm.rank, c0, c1);
   const int tid = threadIdx.x;
@@ -262,10 +388,11 @@ __global__ void __launch_bounds__(B) step_kernel_mixed(CaseDev cs, Launch L, int
   float* __restrict__ w = cs.w32;
   float* __restrict__ p = cs.p32;
   float* __restrict__ q = cs.q32;
+  const float* __restrict__ rD = cs.rD32;
 
   for (int step = 0; step < n_steps; ++step) {
     double v[1] = {0.0};
-    for (int c = c0 + tid; c < c1; c += B) v[0] += assemble_row<true>(cs, c);
+    for (int c = c0 + tid; c < c1; c += B) v[0] += assemble_row<W, true>(cs, c);
     if (!team_allreduce<1>(tm, v, sh)) return;
     if (mode == kModeAssembleOnly) return;
     const double xRef = v[0] / (double)cs.N;
@@ -278,7 +405,7 @@ __global__ void __launch_bounds__(B) step_kernel_mixed(CaseDev cs, Launch L, int
       for (int c = c0 + tid; c < c1; c += B) {
         const double d = cs.diag[c], xc = x[c], b = cs.src[c];
         double rs;
-        const double ax = row_f64<true>(cs, c, x, d, xc, rs);
+        const double ax = row_exact<W>(cs, c, x, d, xc, rs);
         const double rc = b - ax;
         if (sweeps == 0) {
           const double pA = rs * xRef;
@@ -286,7 +413,7 @@ __global__ void __launch_bounds__(B) step_kernel_mixed(CaseDev cs, Launch L, int
         }
         u[1] += fabs(rc);
         const float r32 = (float)rc;
-        const float w32 = cs.rD32[c] * r32;
+        const float w32 = rD[c] * r32;
         u[2] = fma((double)w32, (double)r32, u[2]);
         r[c] = r32;
         w[c] = w32;
@@ -307,23 +434,39 @@ __global__ void __launch_bounds__(B) step_kernel_mixed(CaseDev cs, Launch L, int
       if ((conv && !(sweeps == 0 && cs.min_iter > 0)) || sweeps == kMaxSweeps || iters >= cs.max_iter) break;
 
       // ---- inner FP32 CG on A dx = r --------------------------------------------------
-      const double sweep_res = res;
-      const double inner_tol = fmax(cs.tol, kInnerRel * sweep_res);
+      const double inner_tol = fmax(cs.tol, kInnerRel * res);
       const int min_inner = sweeps == 0 ? cs.min_iter : 0;
       double rho = u[2], beta = 0.0;
       int k = 0;
       for (;;) {
         if (k > 0) {
           const float b32 = (float)beta;
-          for (int c = c0 + tid; c < c1; c += B) p[c] = fmaf(b32, p[c], w[c]);
+          int c = c0 + tid;
+          for (; c + B < c1; c += 2 * B) {
+            const float p1 = p[c], p2 = p[c + B], w1 = w[c], w2 = w[c + B];
+            p[c] = fmaf(b32, p1, w1);
+            p[c + B] = fmaf(b32, p2, w2);
+          }
+          if (c < c1) p[c] = fmaf(b32, p[c], w[c]);
           if (!team_barrier(tm, sh)) return;
         }
         double s1[1] = {0.0};
-        for (int c = c0 + tid; c < c1; c += B) {
-          const float pc = p[c];
-          const float qc = row_f32(cs, c, p, cs.diag32[c], pc);
-          q[c] = qc;
-          s1[0] = fma((double)qc, (double)pc, s1[0]);
+        {
+          int c = c0 + tid;
+          for (; c + B < c1; c += 2 * B) {
+            float y1, y2, pc1, pc2;
+            rows2_f32<W>(cs, c, c + B, p, y1, y2, pc1, pc2);
+            q[c] = y1;
+            q[c + B] = y2;
+            s1[0] = fma((double)y1, (double)pc1, s1[0]);
+            s1[0] = fma((double)y2, (double)pc2, s1[0]);
+          }
+          if (c < c1) {
+            float pc;
+            const float y = row_f32<W>(cs, c, p, pc);
+            q[c] = y;
+            s1[0] = fma((double)y, (double)pc, s1[0]);
+          }
         }
         if (!team_allreduce<1>(tm, s1, sh)) return;
         const double sigma = s1[0];
@@ -333,15 +476,34 @@ __global__ void __launch_bounds__(B) step_kernel_mixed(CaseDev cs, Launch L, int
         }
         const float a32 = (float)(rho / sigma);
         double s2[2] = {0.0, 0.0};
-        for (int c = c0 + tid; c < c1; c += B) {
-          const float pc = p[c], qc = q[c];
-          const float rc = fmaf(-a32, qc, r[c]);
-          const float wc = cs.rD32[c] * rc;
-          dx[c] = fmaf(a32, pc, dx[c]);
-          r[c] = rc;
-          w[c] = wc;
-          s2[0] += fabs((double)rc);
-          s2[1] = fma((double)wc, (double)rc, s2[1]);
+        {
+          int c = c0 + tid;
+          for (; c + B < c1; c += 2 * B) {
+            const int e = c + B;
+            const float pa = p[c], pb = p[e], qa = q[c], qb = q[e];
+            const float xa = dx[c], xb = dx[e], ra = r[c], rb = r[e], da = rD[c], db = rD[e];
+            const float rna = fmaf(-a32, qa, ra), rnb = fmaf(-a32, qb, rb);
+            const float wa = da * rna, wb = db * rnb;
+            dx[c] = fmaf(a32, pa, xa);
+            dx[e] = fmaf(a32, pb, xb);
+            r[c] = rna;
+            r[e] = rnb;
+            w[c] = wa;
+            w[e] = wb;
+            s2[0] += fabs((double)rna);
+            s2[0] += fabs((double)rnb);
+            s2[1] = fma((double)wa, (double)rna, s2[1]);
+            s2[1] = fma((double)wb, (double)rnb, s2[1]);
+          }
+          if (c < c1) {
+            const float rn = fmaf(-a32, q[c], r[c]);
+            const float wn = rD[c] * rn;
+            dx[c] = fmaf(a32, p[c], dx[c]);
+            r[c] = rn;
+            w[c] = wn;
+            s2[0] += fabs((double)rn);
+            s2[1] = fma((double)wn, (double)rn, s2[1]);
+          }
         }
         if (!team_allreduce<2>(tm, s2, sh)) return;
         const double inner_res = s2[0] / nf;
@@ -371,7 +533,23 @@ __global__ void __launch_bounds__(B) step_kernel_mixed(CaseDev cs, Launch L, int
   }
 }
 
-// ---- small helpers -------------------------------------------------------------------
+// ---- kernels ---------------------------------------------------------------------------
+template <int B, int W>
+__global__ void __launch_bounds__(B) step_kernel_f64(CaseDev cs, Launch L, int n_steps, int mode) {
+  __shared__ TeamShared sh;
+  if ((int)blockIdx.x == L.skip_cta) return;  // test hook: never arrive
+  const Team tm{(int)gridDim.x, (int)blockIdx.x, cs.sync, cs.partials, L.timeout_ns};
+  run_steps_f64<B, W>(cs, tm, n_steps, mode, sh);
+}
+
+template <int B, int W>
+__global__ void __launch_bounds__(B) step_kernel_mixed(CaseDev cs, Launch L, int n_steps, int mode) {
+  __shared__ TeamShared sh;
+  if ((int)blockIdx.x == L.skip_cta) return;
+  const Team tm{(int)gridDim.x, (int)blockIdx.x, cs.sync, cs.partials, L.timeout_ns};
+  run_steps_mixed<B, W>(cs, tm, n_steps, mode, sh);
+}
+
 __global__ void boundary_values_kernel(CaseDev cs, double* Tb) {
   const int b = blockIdx.x * blockDim.x + threadIdx.x;
   if (b < cs.NB) Tb[b] = cs.btype[b] == LFM_FIXED_VALUE ? cs.bval[b] : cs.x[cs.bcell[b]];
@@ -384,23 +562,24 @@ __global__ void fill_kernel(double* a, size_t n, double v) {
 }
 
 template <int B>
-void* step_fn(int precision) {
-  return precision == LFM_MIXED ? (void*)step_kernel_mixed<B> : (void*)step_kernel_f64<B>;
+void* step_fn_w(int precision, int W) {
+  if (W == 6) return precision == LFM_MIXED ? (void*)step_kernel_mixed<B, 6> : (void*)step_kernel_f64<B, 6>;
+  return precision == LFM_MIXED ? (void*)step_kernel_mixed<B, 0> : (void*)step_kernel_f64<B, 0>;
 }
 
-void* step_fn_for(int precision, int threads) {
+void* step_fn_for(int precision, int threads, int W) {
   switch (threads) {
-    case 256: return step_fn<256>(precision);
-    case 512: return step_fn<512>(precision);
-    case 1024: return step_fn<1024>(precision);
+    case 256: return step_fn_w<256>(precision, W);
+    case 512: return step_fn_w<512>(precision, W);
+    case 1024: return step_fn_w<1024>(precision, W);
     default: return nullptr;
   }
 }
 
 }  // namespace
 
-int max_coresident_ctas(int precision, int threads, int device) {
-  void* fn = step_fn_for(precision, threads);
+int max_coresident_ctas(int precision, int threads, int W, int device) {
+  void* fn = step_fn_for(precision, threads, W);
   if (!fn) return 0;
   int per_sm = 0, sms = 0;
   if (cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, fn, threads, 0) != cudaSuccess) return 0;
@@ -411,7 +590,7 @@ int max_coresident_ctas(int precision, int threads, int device) {
 
 cudaError_t launch_steps(const CaseDev& cs, const Launch& L, int n_steps, int mode,
                          cudaStream_t stream) {
-  void* fn = step_fn_for(cs.precision, L.threads);
+  void* fn = step_fn_for(cs.precision, L.threads, cs.W);
   if (!fn) return cudaErrorInvalidValue;
   CaseDev a0 = cs;
   Launch a1 = L;

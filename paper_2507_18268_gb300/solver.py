@@ -37,7 +37,7 @@ class Solver:
 
                 nbytes = B.lfm_workspace_bytes(mesh, layout)
                 self._ws = torch.empty(nbytes, dtype=torch.uint8, device=f"cuda:{device}")
-                B.lfm_bind_workspace(self.ctx, self._ws.data_ptr(), nbytes)
+                B.lfm_bind_workspace(self.ctx, self._ws.data_ptr(), nbytes, layout)
             B.lfm_upload_mesh(self.ctx, mesh)
         except Exception:
             B.lfm_destroy(self.ctx)

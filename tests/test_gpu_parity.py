@@ -77,8 +77,11 @@ def assert_parity(name, T, st, n_steps=None):
         assert g["iters"] == o.iters, (k, g, o)
         assert bool(g["converged"]) == o.converged
         assert g["status"] == 0
-        assert abs(g["norm_factor"] - o.norm_factor) <= 1e-12 * o.norm_factor
-        assert abs(g["init_res"] - o.init_res) <= 1e-9 * max(o.init_res, 1e-300) + 1e-300
+        # normFactor adds |Ax - s xRef| terms that nearly cancel where T is uniform; the mean
+        # xRef is summed in another order, so each term carries ~eps*|b| of roundoff and the
+        # total up to ~N*eps*|b|/normFactor ~ 1e-10 relative on these cases.
+        assert abs(g["norm_factor"] - o.norm_factor) <= 1e-8 * o.norm_factor
+        assert abs(g["init_res"] - o.init_res) <= 1e-8 * o.init_res + 1e-300
     assert relerr(T, To) <= RTOL64
 
 
@@ -142,7 +145,6 @@ def test_checkpoint_resume_bitwise():
     case = CASES["permuted20"]()
     with Solver.from_case(case) as a:
         a.advance(10)
-        T_full_ref = None
         a.advance(10)
         T_full_ref = a.field()
     with Solver.from_case(case) as b:
@@ -178,10 +180,10 @@ def test_min_and_max_iter():
     To, so = oracle.advance(case)
     assert [s["iters"] for s in st] == [s.iters for s in so] and all(s["iters"] >= 5 for s in st)
     assert relerr(T, To) <= RTOL64
-    case = CASES["graded40"]().with_(max_iter=3, n_steps=2)
+    case = CASES["permuted20"]().with_(tol=1e-14, max_iter=3, n_steps=2)
     T, st, _ = gpu_run(case)
     To, so = oracle.advance(case)
-    assert [s["iters"] for s in st] == [3, 3] and not st[0]["converged"]
+    assert [s["iters"] for s in st] == [3, 3] == [s.iters for s in so] and not st[0]["converged"]
     assert relerr(T, To) <= RTOL64
 
 
@@ -240,7 +242,7 @@ def test_bound_workspace_too_small():
     ws = torch.empty(need - 4096, dtype=torch.uint8, device="cuda")
     ctx = B.lfm_create(0, None)
     try:
-        B.lfm_bind_workspace(ctx, ws.data_ptr(), need - 4096)
+        B.lfm_bind_workspace(ctx, ws.data_ptr(), need - 4096, B.LFM_MIXED)
         with pytest.raises(B.LfmError) as e:
             B.lfm_upload_mesh(ctx, m)
         assert e.value.code == B.LFM_ENOMEM
@@ -267,11 +269,9 @@ def test_mixed_workspace_only_layout():
     m = box_mesh(case)
     need = B.lfm_workspace_bytes(m, B.LFM_MIXED)
     ws = torch.empty(need, dtype=torch.uint8, device="cuda")
-    with Solver(m, workspace="none") as s:
-        pass
     ctx = B.lfm_create(0, None)
     try:
-        B.lfm_bind_workspace(ctx, ws.data_ptr(), need)
+        B.lfm_bind_workspace(ctx, ws.data_ptr(), need, B.LFM_MIXED)
         B.lfm_upload_mesh(ctx, m)
         with pytest.raises(B.LfmError) as e:
             B.lfm_set_solver(ctx, 1e-6, 0, 1000, 0, B.LFM_FP64)
