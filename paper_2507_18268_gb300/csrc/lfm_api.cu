@@ -36,7 +36,7 @@ struct Layout {
   size_t sync, partials, stats;
   size_t slot_other, slot_face, b_start, b_face, bcell, btype;
   size_t V, magSf, delta, DT, bmagSf, bdelta, bDT, bval;
-  size_t diag, upper, slot_coef, src, rD, x, r, w, p, q, Tb;
+  size_t diag, upper, slot_coef, src, rD, sumA, x, r, w, p, q, Tb;
   size_t diag32, slot_coef32, rD32, dx32, r32, w32, p32, q32;
   size_t total;
 };
@@ -75,6 +75,7 @@ Layout make_layout(int64_t N, int64_t F, int64_t NB, int64_t W, int kind) {
   L.slot_coef = take(8 * W * N);
   L.src = take(8 * N);
   L.rD = take(8 * N);
+  L.sumA = take(8 * N);
   L.x = take(8 * N);
   L.Tb = take(8 * NB);
   L.r = L.w = L.p = L.q = 0;
@@ -322,6 +323,7 @@ void bind_pointers(lfm_ctx* c) {
   cs.slot_coef = reinterpret_cast<double*>(b + L.slot_coef);
   cs.src = reinterpret_cast<double*>(b + L.src);
   cs.rD = reinterpret_cast<double*>(b + L.rD);
+  cs.sumA = reinterpret_cast<double*>(b + L.sumA);
   cs.x = reinterpret_cast<double*>(b + L.x);
   const bool d = c->has64, m = c->has32;
   cs.r = d ? reinterpret_cast<double*>(b + L.r) : nullptr;

@@ -64,6 +64,7 @@ struct CaseDev {
   double* slot_coef;         // [W*N]
   double* src;               // [N]
   double* rD;                // [N]  1/diag
+  double* sumA;              // [N]  row sums of A (V/dt + boundary conductance)
 
   // FP64 solver vectors; x is the field T (updated in place)
   double* x;

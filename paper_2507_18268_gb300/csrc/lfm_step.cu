@@ -22,7 +22,9 @@
 // Mixed step (defect correction, FP64 field x): the matrix is assembled in FP64 and copied
 // to FP32; each sweep computes the FP64 true residual r = b - A x, solves A dx = r by the
 // same CG recurrence on FP32 vectors with FP32 row sums, and adds dx to x in FP64. Dot
-// products, sum|r|, normFactor and every convergence test accumulate in FP64.
+// products, sum|r|, normFactor and every convergence test are FP64-accurate: FP64 for the
+// FP64 quantities; for FP32 terms, exact products summed as unevaluated FP32 pairs per
+// thread and FP64 across threads (see Acc2f).
 #include <cuda_runtime.h>
 
 #include "lfm_device.cuh"
@@ -55,6 +57,31 @@ __device__ __forceinline__ int nslots(const CaseDev& cs) {
   return W > 0 ? W : cs.W;
 }
 
+// ---- FP64-accurate accumulation of FP32 terms without FP64 instructions -----------------
+// A running sum kept as an unevaluated pair hi + lo of FP32 numbers: each product of two
+// FP32 values is split exactly into p + e (e = fma(a, b, -p)), p enters hi through Knuth's
+// TwoSum (whose rounding error is exact), and the error terms collect in lo. Over the tens
+// of terms one thread adds per pass, hi + lo carries ~2^-44 relative error; each thread
+// converts it to FP64 once, and the block and team reductions run in FP64. (The FP64 pipe
+// is the scarce unit on GB300: converting every term would cost two FP64 issues each.)
+struct Acc2f {
+  float hi = 0.0f, lo = 0.0f;
+  __device__ __forceinline__ void add(float v) {
+    const float s = __fadd_rn(hi, v);
+    const float bp = __fsub_rn(s, hi);
+    const float e = __fadd_rn(__fsub_rn(hi, __fsub_rn(s, bp)), __fsub_rn(v, bp));
+    hi = s;
+    lo = __fadd_rn(lo, e);
+  }
+  __device__ __forceinline__ void add_prod(float a, float b) {
+    const float p = __fmul_rn(a, b);
+    const float e = __fmaf_rn(a, b, -p);
+    add(p);
+    lo = __fadd_rn(lo, e);
+  }
+  __device__ __forceinline__ double value() const { return (double)hi + (double)lo; }
+};
+
 // ---- assembly: one row of fvm::ddt(T) - fvm::laplacian(DT, T) -------------------------
 // The diagonal is summed in slot order, i.e. ascending face order (neighbour-side faces
 // have smaller owners, so they precede the cell's own faces in upper-triangular order),
@@ -77,6 +104,7 @@ __device__ __forceinline__ double assemble_row(const CaseDev& cs, int c) {
       d = __dadd_rn(d, g);
     }
   }
+  double gsum = 0.0;  // boundary conductance of the row
   const int b0 = __ldg(cs.b_start + c), b1 = __ldg(cs.b_start + c + 1);
   for (int k = b0; k < b1; ++k) {
     const int bf = __ldg(cs.b_face + k);
@@ -84,6 +112,7 @@ __device__ __forceinline__ double assemble_row(const CaseDev& cs, int c) {
       const double gb = __dmul_rn(__dmul_rn(__ldg(cs.bDT + bf), __ldg(cs.bmagSf + bf)), __ldg(cs.bdelta + bf));
       d = __dadd_rn(d, gb);
       s = __dadd_rn(s, __dmul_rn(gb, __ldg(cs.bval + bf)));
+      gsum = __dadd_rn(gsum, gb);
     }
   }
   const double vdt = __ldg(cs.V + c) / cs.dt;
@@ -94,6 +123,9 @@ __device__ __forceinline__ double assemble_row(const CaseDev& cs, int c) {
   cs.diag[c] = d;
   cs.src[c] = s;
   cs.rD[c] = rd;
+  // Row sum of A: the off-diagonals cancel the face conductances in the diagonal exactly in
+  // real arithmetic, leaving V/dt plus the boundary conductance.
+  cs.sumA[c] = gsum + vdt;
   if (kMixed) {
     cs.diag32[c] = (float)d;
     cs.rD32[c] = (float)rd;
@@ -102,24 +134,19 @@ __device__ __forceinline__ double assemble_row(const CaseDev& cs, int c) {
 }
 
 // ---- FP64 row of A v, products and sums rounded separately in slot order ---------------
-// Reproduces a serial face loop's rounding exactly; also returns the row sum of A.
+// Reproduces a serial face loop's rounding exactly.
 template <int W>
 __device__ __forceinline__ double row_exact(const CaseDev& cs, int c, const double* __restrict__ v,
-                                            double d, double vc, double& rowsum) {
+                                            double d, double vc) {
   const size_t N = (size_t)cs.N;
   const int ns = nslots<W>(cs);
   double acc = __dmul_rn(d, vc);
-  double rs = d;
 #pragma unroll
   for (int k = 0; k < (W > 0 ? W : kMaxSlots); ++k) {
     if (W == 0 && k >= ns) break;
     const size_t at = (size_t)k * N + c;
-    const double u = cs.slot_coef[at];
-    const double vo = v[__ldg(cs.slot_other + at)];
-    acc = __dadd_rn(acc, __dmul_rn(u, vo));
-    rs = __dadd_rn(rs, u);
+    acc = __dadd_rn(acc, __dmul_rn(cs.slot_coef[at], v[__ldg(cs.slot_other + at)]));
   }
-  rowsum = rs;
   return acc;
 }
 
@@ -265,10 +292,9 @@ __device__ void run_steps_f64(const CaseDev& cs, const Team& tm, int n_steps, in
     double u[3] = {0.0, 0.0, 0.0};  // normFactor sum, sum|r|, rho
     for (int c = c0 + tid; c < c1; c += B) {
       const double d = cs.diag[c], xc = x[c], b = cs.src[c];
-      double rs;
-      const double ax = row_exact<W>(cs, c, x, d, xc, rs);
+      const double ax = row_exact<W>(cs, c, x, d, xc);
       const double rc = b - ax;
-      const double pA = rs * xRef;
+      const double pA = cs.sumA[c] * xRef;
       u[0] += fabs(ax - pA) + fabs(b - pA);
       u[1] += fabs(rc);
       const double wc = rD[c] * rc;
@@ -402,24 +428,26 @@ __device__ void run_steps_mixed(const CaseDev& cs, const Team& tm, int n_steps, 
     for (;;) {
       // ---- T: FP64 true residual r = b - A x, seeded into the FP32 inner solve --------
       double u[3] = {0.0, 0.0, 0.0};  // normFactor sum (first sweep), sum|r|, rho
+      Acc2f rho_acc;
       for (int c = c0 + tid; c < c1; c += B) {
-        const double d = cs.diag[c], xc = x[c], b = cs.src[c];
-        double rs;
-        const double ax = row_exact<W>(cs, c, x, d, xc, rs);
+        const double b = cs.src[c];
+        double xc;
+        const double ax = row_f64<W>(cs, c, x, xc);
         const double rc = b - ax;
         if (sweeps == 0) {
-          const double pA = rs * xRef;
+          const double pA = cs.sumA[c] * xRef;
           u[0] += fabs(ax - pA) + fabs(b - pA);
         }
         u[1] += fabs(rc);
         const float r32 = (float)rc;
         const float w32 = rD[c] * r32;
-        u[2] = fma((double)w32, (double)r32, u[2]);
+        rho_acc.add_prod(w32, r32);
         r[c] = r32;
         w[c] = w32;
         p[c] = w32;
         dx[c] = 0.0f;
       }
+      u[2] = rho_acc.value();
       if (!team_allreduce<3>(tm, u, sh)) return;
       if (sweeps == 0) {
         nf = u[0] + kSmall;
@@ -450,23 +478,25 @@ __device__ void run_steps_mixed(const CaseDev& cs, const Team& tm, int n_steps, 
           if (c < c1) p[c] = fmaf(b32, p[c], w[c]);
           if (!team_barrier(tm, sh)) return;
         }
-        double s1[1] = {0.0};
+        double s1[1];
         {
+          Acc2f sig;
           int c = c0 + tid;
           for (; c + B < c1; c += 2 * B) {
             float y1, y2, pc1, pc2;
             rows2_f32<W>(cs, c, c + B, p, y1, y2, pc1, pc2);
             q[c] = y1;
             q[c + B] = y2;
-            s1[0] = fma((double)y1, (double)pc1, s1[0]);
-            s1[0] = fma((double)y2, (double)pc2, s1[0]);
+            sig.add_prod(y1, pc1);
+            sig.add_prod(y2, pc2);
           }
           if (c < c1) {
             float pc;
             const float y = row_f32<W>(cs, c, p, pc);
             q[c] = y;
-            s1[0] = fma((double)y, (double)pc, s1[0]);
+            sig.add_prod(y, pc);
           }
+          s1[0] = sig.value();
         }
         if (!team_allreduce<1>(tm, s1, sh)) return;
         const double sigma = s1[0];
@@ -475,8 +505,9 @@ __device__ void run_steps_mixed(const CaseDev& cs, const Team& tm, int n_steps, 
           break;
         }
         const float a32 = (float)(rho / sigma);
-        double s2[2] = {0.0, 0.0};
+        double s2[2];
         {
+          Acc2f rsum, rho_n;
           int c = c0 + tid;
           for (; c + B < c1; c += 2 * B) {
             const int e = c + B;
@@ -490,10 +521,10 @@ __device__ void run_steps_mixed(const CaseDev& cs, const Team& tm, int n_steps, 
             r[e] = rnb;
             w[c] = wa;
             w[e] = wb;
-            s2[0] += fabs((double)rna);
-            s2[0] += fabs((double)rnb);
-            s2[1] = fma((double)wa, (double)rna, s2[1]);
-            s2[1] = fma((double)wb, (double)rnb, s2[1]);
+            rsum.add(fabsf(rna));
+            rsum.add(fabsf(rnb));
+            rho_n.add_prod(wa, rna);
+            rho_n.add_prod(wb, rnb);
           }
           if (c < c1) {
             const float rn = fmaf(-a32, q[c], r[c]);
@@ -501,9 +532,11 @@ __device__ void run_steps_mixed(const CaseDev& cs, const Team& tm, int n_steps, 
             dx[c] = fmaf(a32, p[c], dx[c]);
             r[c] = rn;
             w[c] = wn;
-            s2[0] += fabs((double)rn);
-            s2[1] = fma((double)wn, (double)rn, s2[1]);
+            rsum.add(fabsf(rn));
+            rho_n.add_prod(wn, rn);
           }
+          s2[0] = rsum.value();
+          s2[1] = rho_n.value();
         }
         if (!team_allreduce<2>(tm, s2, sh)) return;
         const double inner_res = s2[0] / nf;
