@@ -247,6 +247,9 @@ def main_ours(args, world, rank, local):
     hbm_peak, peak_kind = load_peaks()
     K, W = args.steps, args.warmup
 
+    if args.only == "mixed":
+        return main_mixed_only(args, world, rank, local, case, mesh, stream)
+
     # ---- FP64, device-resident --------------------------------------------------------
     s64 = Solver.from_case(case, mesh=mesh, device=local, stream=stream)
     s64.advance(W)
@@ -355,6 +358,25 @@ def main_ours(args, world, rank, local):
     print(json.dumps(line), flush=True)
 
 
+def main_mixed_only(args, world, rank, local, case, mesh, stream):
+    """Profiling mode: the mixed form alone (one warm-up launch, one timed launch)."""
+    import torch
+
+    from paper_2507_18268_gb300 import Solver
+    from paper_2507_18268_gb300 import binding as B
+
+    K, W = args.steps, args.warmup
+    smx = Solver.from_case(case.with_(precision=B.LFM_MIXED), mesh=mesh, device=local, stream=stream)
+    smx.advance(W)
+    secs, st = time_device_resident(smx, B, torch, stream, K)
+    iters = sum(x["iters"] for x in st)
+    smx.close()
+    if rank == 0:
+        print(json.dumps({"metric": METRIC, "value": mesh.n_cells * iters / secs, "unit": UNIT,
+                          "mode": "mixed only (profiling)", "steps": K, "warmup": W,
+                          "ms_per_step": 1e3 * secs / K, "iters_per_step": iters / K}), flush=True)
+
+
 def main():
     ap = argparse.ArgumentParser()
     ap.add_argument("--gpus", type=int, default=1)
@@ -364,9 +386,14 @@ def main():
     ap.add_argument("--no-mixed", action="store_true")
     ap.add_argument("--no-e2e", action="store_true")
     ap.add_argument("--no-cpu-baseline", action="store_true")
+    ap.add_argument("--only", choices=["fp64", "mixed"], default=None,
+                    help="profiling: run only this precision, device-resident, no e2e or CPU baseline")
     args = ap.parse_args()
     if args.warmup < 3:
         ap.error("--warmup must be >= 3")
+    if args.only:
+        args.no_e2e = args.no_cpu_baseline = True
+        args.no_mixed = args.only == "fp64"
     world, rank, local = dist_setup()
     try:
         if args.impl == "reference":
