@@ -201,6 +201,28 @@ int lfm_set_barrier_timeout(lfm_ctx *ctx, uint64_t ns);
  * LFM_ETIMEOUT (no fault, no hang: every wait is bounded). One-shot; needs >= 2 CTAs. */
 int lfm_debug_skip_arrival(lfm_ctx *ctx, int32_t cta);
 
+/* Allocation-free solve, for callers that cannot allocate device memory (a plug-in inside a
+ * host code whose memory manager owns every device buffer, a real-time loop that must not
+ * call an allocator once running). The paper has no counterpart to this call.
+ * Solves A x = source with the same diagonal-preconditioned CG and normFactor residual as
+ * lfm_advance, FP64 only (opts->precision must be LFM_FP64), where A is given in LDU form
+ * in device memory the caller owns: owner/neighbour[n_faces] (owner < neighbour, sorted by
+ * owner), diag[n_cells], upper[n_faces] (lower == upper), source[n_cells]; x[n_cells]
+ * (device) holds the initial guess and receives the solution. stats (host, may be NULL)
+ * receives the solve record. Runs on cuda_stream and synchronises before return.
+ * Limits: n_cells <= 65536 and n_faces <= 262144, else LFM_EINVAL before any device work;
+ * an invalid owner/neighbour array is reported as LFM_EINVAL by the kernel.
+ * Working memory: one fixed device array of about 4.8 MB inside the library, present on
+ * every GPU that loads it until the process exits; no call allocates, frees or calls an
+ * allocating library routine. All calls share that array (each call re-initialises what it
+ * needs), so calls whose kernels overlap on one GPU race: order them on one stream. The
+ * first call on a device looks up the array's device address (cudaGetSymbolAddress) with
+ * that device current; make that first call before any stream capture. */
+int lfm_pcg_solve_static(int32_t n_cells, int32_t n_faces, const int32_t *owner,
+                         const int32_t *neighbour, const double *diag, const double *upper,
+                         const double *source, double *x, const lfm_solver_opts *opts,
+                         lfm_step_stats *stats, void *cuda_stream);
+
 /* Destroys the context (frees library-owned device memory; never a bound workspace). */
 int lfm_destroy(lfm_ctx *ctx);
 

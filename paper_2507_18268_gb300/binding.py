@@ -82,6 +82,8 @@ _SIGS = {
     "lfm_set_launch": ([_ctx_p, c_int32, c_int32], c_int),
     "lfm_set_barrier_timeout": ([_ctx_p, c_uint64], c_int),
     "lfm_debug_skip_arrival": ([_ctx_p, c_int32], c_int),
+    "lfm_pcg_solve_static": ([c_int32, c_int32, c_void_p, c_void_p, c_void_p, c_void_p, c_void_p, c_void_p,
+                              POINTER(lfm_solver_opts), POINTER(lfm_step_stats), c_void_p], c_int),
     "lfm_destroy": ([_ctx_p], c_int),
     "lfm_last_error": ([_ctx_p], c_char_p),
 }
@@ -302,6 +304,20 @@ def lfm_set_barrier_timeout(ctx, ns: int):
 
 def lfm_debug_skip_arrival(ctx, cta: int):
     _check(load().lfm_debug_skip_arrival(ctx, int(cta)), ctx)
+
+
+def lfm_pcg_solve_static(n_cells: int, n_faces: int, owner_ptr: int, neighbour_ptr: int, diag_ptr: int,
+                         upper_ptr: int, source_ptr: int, x_ptr: int, tol: float, rel_tol: float = 0.0,
+                         max_iter: int = 1000, min_iter: int = 0, stream: Optional[int] = None):
+    """Allocation-free FP64 solve of a device-resident LDU system (pointers are device
+    addresses). Returns (status, stats); does not raise on a solver status."""
+    o = lfm_solver_opts(float(tol), float(rel_tol), int(max_iter), int(min_iter), LFM_FP64)
+    st = lfm_step_stats()
+    rc = load().lfm_pcg_solve_static(int(n_cells), int(n_faces), c_void_p(owner_ptr), c_void_p(neighbour_ptr),
+                                     c_void_p(diag_ptr), c_void_p(upper_ptr), c_void_p(source_ptr),
+                                     c_void_p(x_ptr), ctypes.byref(o), ctypes.byref(st),
+                                     c_void_p(stream) if stream else None)
+    return rc, st
 
 
 def lfm_destroy(ctx):

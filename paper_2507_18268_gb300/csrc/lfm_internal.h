@@ -16,6 +16,8 @@ constexpr int kMaxCtas = 8192;       // capacity of the per-CTA partial-sum tabl
 constexpr int kStatsCap = 1024;      // per-launch statistics records
 constexpr int kMaxSweeps = 5;        // mixed precision: defect-correction sweeps per step
 constexpr int kMaxSlots = 32;        // largest number of internal faces per cell
+constexpr int kStaticMaxCells = 1 << 16;   // allocation-free solve: largest system
+constexpr int kStaticMaxFaces = 1 << 18;
 
 // Barrier words of one team of CTAs; each field sits on its own 128-byte line.
 struct alignas(128) SyncWords {
