@@ -230,6 +230,64 @@ int lfm_destroy(lfm_ctx *ctx);
  * a context-free call on this thread). */
 const char *lfm_last_error(const lfm_ctx *ctx);
 
+/* ---- batched form ------------------------------------------------------------------
+ * A batch runs many independent cases (uploaded, configured contexts on one device) in one
+ * persistent cooperative launch. Each case becomes a job needing a team of
+ * k = ceil(n_cells / (threads * cells_per_thread[class])) CTAs (class 0: < 32768 cells,
+ * 1: < 262144, 2: larger); jobs are served longest-first from a device work queue, each
+ * with its case's own barriers and reductions, so a case's arithmetic is the same as when
+ * it runs alone (up to the summation order that its team size sets). Results (T,
+ * statistics) stay in each member context. While a batch advance is pending the member
+ * contexts must not be used directly. */
+typedef struct lfm_batch lfm_batch;
+
+/* Creates an empty batch on `device`, issuing work on `cuda_stream` (NULL = default). */
+int lfm_batch_create(lfm_batch **out, int device, void *cuda_stream);
+
+/* Adds an uploaded context (same device, no pending advance, in no other batch); its case
+ * id is written to case_id. The context stays owned by the caller and cannot be destroyed
+ * while it is a member. */
+int lfm_batch_add(lfm_batch *b, lfm_ctx *ctx, int32_t *case_id);
+
+/* Removes a case (its id may be reused by a later add). */
+int lfm_batch_remove(lfm_batch *b, int32_t case_id);
+
+/* Number of member cases. */
+int lfm_batch_size(const lfm_batch *b);
+
+/* Launch shape: threads per CTA (256 or 512) and cells per thread for the three size
+ * classes (NULL keeps the current ones; defaults 512 and {4, 8, 16}). */
+int lfm_batch_set_launch(lfm_batch *b, int32_t threads, const int32_t *cells_per_thread);
+
+/* Current launch shape (ctas = CTAs of the persistent launch). */
+int lfm_batch_get_launch(lfm_batch *b, int32_t *ctas, int32_t *threads, int32_t *cells_per_thread);
+
+/* Device-side barrier wait limit for batch launches (default 10 s). */
+int lfm_batch_set_barrier_timeout(lfm_batch *b, uint64_t ns);
+
+/* Enqueues n_steps (<= 1024) steps of every member case. use_graph != 0: one step is
+ * captured once into a CUDA graph (ticket reset + persistent kernel) and the graph is
+ * launched n_steps times; use_graph == 0: one launch runs all n_steps. */
+int lfm_batch_advance_async(lfm_batch *b, int32_t n_steps, int32_t use_graph);
+
+/* 1 while the pending advance runs, LFM_OK when done or none pending. */
+int lfm_batch_query(lfm_batch *b);
+
+/* Waits for the pending advance; returns LFM_OK or the first failing case's status. */
+int lfm_batch_finish(lfm_batch *b);
+
+/* Status of one case in the last finished advance. */
+int lfm_batch_case_status(lfm_batch *b, int32_t case_id);
+
+/* Copies the first n per-step records of one case's last advance to host memory. */
+int lfm_batch_case_stats(lfm_batch *b, int32_t case_id, lfm_step_stats *out, int32_t n);
+
+/* Destroys the batch (the member contexts are released, not destroyed). */
+int lfm_batch_destroy(lfm_batch *b);
+
+/* Reason for the batch's last non-OK return (b may be NULL). */
+const char *lfm_batch_last_error(const lfm_batch *b);
+
 #ifdef __cplusplus
 }
 #endif

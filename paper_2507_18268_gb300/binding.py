@@ -85,6 +85,20 @@ _SIGS = {
     "lfm_pcg_solve_static": ([c_int32, c_int32, c_void_p, c_void_p, c_void_p, c_void_p, c_void_p, c_void_p,
                               POINTER(lfm_solver_opts), POINTER(lfm_step_stats), c_void_p], c_int),
     "lfm_destroy": ([_ctx_p], c_int),
+    "lfm_batch_create": ([POINTER(c_void_p), c_int, c_void_p], c_int),
+    "lfm_batch_add": ([c_void_p, _ctx_p, POINTER(c_int32)], c_int),
+    "lfm_batch_remove": ([c_void_p, c_int32], c_int),
+    "lfm_batch_size": ([c_void_p], c_int),
+    "lfm_batch_set_launch": ([c_void_p, c_int32, POINTER(c_int32)], c_int),
+    "lfm_batch_get_launch": ([c_void_p, POINTER(c_int32), POINTER(c_int32), POINTER(c_int32)], c_int),
+    "lfm_batch_set_barrier_timeout": ([c_void_p, c_uint64], c_int),
+    "lfm_batch_advance_async": ([c_void_p, c_int32, c_int32], c_int),
+    "lfm_batch_query": ([c_void_p], c_int),
+    "lfm_batch_finish": ([c_void_p], c_int),
+    "lfm_batch_case_status": ([c_void_p, c_int32], c_int),
+    "lfm_batch_case_stats": ([c_void_p, c_int32, POINTER(lfm_step_stats), c_int32], c_int),
+    "lfm_batch_destroy": ([c_void_p], c_int),
+    "lfm_batch_last_error": ([c_void_p], c_char_p),
     "lfm_last_error": ([_ctx_p], c_char_p),
 }
 
@@ -326,3 +340,88 @@ def lfm_destroy(ctx):
 
 def lfm_last_error(ctx=None) -> str:
     return _err(ctx)
+
+
+# ---- batched form ------------------------------------------------------------------------
+
+def _berr(b) -> str:
+    msg = load().lfm_batch_last_error(b)
+    return msg.decode() if msg else ""
+
+
+def _bcheck(rc: int, b=None) -> int:
+    if rc != LFM_OK:
+        raise LfmError(rc, _berr(b))
+    return rc
+
+
+def lfm_batch_create(device: int = 0, stream: Optional[int] = None) -> c_void_p:
+    b = c_void_p()
+    _bcheck(load().lfm_batch_create(ctypes.byref(b), device, c_void_p(stream) if stream else None))
+    return b
+
+
+def lfm_batch_add(b, ctx) -> int:
+    cid = c_int32()
+    _bcheck(load().lfm_batch_add(b, ctx, ctypes.byref(cid)), b)
+    return cid.value
+
+
+def lfm_batch_remove(b, case_id: int):
+    _bcheck(load().lfm_batch_remove(b, int(case_id)), b)
+
+
+def lfm_batch_size(b) -> int:
+    return int(load().lfm_batch_size(b))
+
+
+def lfm_batch_set_launch(b, threads: int, cells_per_thread=None):
+    arr = None if cells_per_thread is None else (c_int32 * 3)(*[int(v) for v in cells_per_thread])
+    _bcheck(load().lfm_batch_set_launch(b, int(threads), arr), b)
+
+
+def lfm_batch_get_launch(b):
+    ctas, thr, cpt = c_int32(), c_int32(), (c_int32 * 3)()
+    _bcheck(load().lfm_batch_get_launch(b, ctypes.byref(ctas), ctypes.byref(thr), cpt), b)
+    return ctas.value, thr.value, list(cpt)
+
+
+def lfm_batch_set_barrier_timeout(b, ns: int):
+    _bcheck(load().lfm_batch_set_barrier_timeout(b, int(ns)), b)
+
+
+def lfm_batch_advance_async(b, n_steps: int, use_graph: bool = True):
+    _bcheck(load().lfm_batch_advance_async(b, int(n_steps), 1 if use_graph else 0), b)
+
+
+def lfm_batch_query(b) -> int:
+    rc = load().lfm_batch_query(b)
+    if rc < 0:
+        raise LfmError(rc, _berr(b))
+    return rc
+
+
+def lfm_batch_finish(b) -> int:
+    """Waits; returns LFM_OK or the first failing case's status (does not raise on those)."""
+    rc = load().lfm_batch_finish(b)
+    if rc == LFM_ECUDA:
+        raise LfmError(rc, _berr(b))
+    return rc
+
+
+def lfm_batch_case_status(b, case_id: int) -> int:
+    return int(load().lfm_batch_case_status(b, int(case_id)))
+
+
+def lfm_batch_case_stats(b, case_id: int, n: int):
+    out = (lfm_step_stats * max(n, 1))()
+    _bcheck(load().lfm_batch_case_stats(b, int(case_id), out, int(n)), b)
+    return [out[i] for i in range(n)]
+
+
+def lfm_batch_destroy(b):
+    load().lfm_batch_destroy(b)
+
+
+def lfm_batch_last_error(b=None) -> str:
+    return _berr(b)

@@ -114,6 +114,8 @@ struct DeviceGuard {
 
 }  // namespace
 
+struct lfm_batch;
+
 struct lfm_ctx {
   int device = 0;
   cudaStream_t stream = nullptr;
@@ -152,6 +154,7 @@ struct lfm_ctx {
   int pending_steps = 0;
   int pending_remaining = 0;
   std::vector<lfm_step_stats> stats_acc;
+  lfm_batch* batch = nullptr;         // batch this context belongs to, if any
 };
 
 namespace {
@@ -764,6 +767,7 @@ int lfm_debug_skip_arrival(lfm_ctx* c, int32_t cta) {
 
 int lfm_destroy(lfm_ctx* c) {
   if (!c) return LFM_OK;
+  if (c->batch) return fail(c, LFM_ESTATE, "remove the context from its batch first");
   {
     DeviceGuard g(c->device);
     if (c->pending_steps > 0 && c->done) cudaEventSynchronize(c->done);
@@ -779,6 +783,383 @@ int lfm_destroy(lfm_ctx* c) {
 const char* lfm_last_error(const lfm_ctx* c) {
   if (c) return c->err.c_str();
   return g_last_error.c_str();
+}
+
+
+}  // extern "C"
+
+// ======================================================================================
+// Batched form
+// ======================================================================================
+
+struct lfm_batch {
+  int device = 0;
+  cudaStream_t stream = nullptr;
+  cudaStream_t capture_stream = nullptr;
+  std::string err;
+  std::vector<lfm_ctx*> slots;      // case id -> member (nullptr once removed)
+  std::vector<double> est_iters;    // per case id: PCG iterations of its last step
+  std::vector<int32_t> status;      // per case id: status of the last advance
+  std::vector<int32_t> order;       // compact index of the last advance -> case id
+  int threads = 512;
+  int cpt[3] = {4, 8, 16};          // cells per thread by size class
+  uint64_t timeout_ns = 10000000000ull;
+  // device buffers, library-owned
+  int cap = 0;
+  CaseDev* d_cases = nullptr;
+  int32_t* d_job_case = nullptr;
+  int32_t* d_job_start = nullptr;
+  BatchHeader* d_hdr = nullptr;
+  int32_t* d_case_step = nullptr;
+  int32_t* d_status = nullptr;
+  int32_t* d_iters = nullptr;
+  // pinned staging
+  CaseDev* h_cases = nullptr;
+  int32_t* h_job_case = nullptr;
+  int32_t* h_job_start = nullptr;
+  BatchHeader* h_hdr = nullptr;
+  int32_t* h_status = nullptr;
+  int32_t* h_iters = nullptr;
+  cudaEvent_t done = nullptr;
+  int pending = 0;
+  int n_active = 0;
+  // captured one-step graph
+  cudaGraphExec_t gexec = nullptr;
+  int g_threads = 0, g_W = -1, g_ctas = 0;
+  int last_ctas = 0, last_W = 6;
+};
+
+namespace {
+
+thread_local std::string g_batch_error;
+
+int bfail(lfm_batch* b, int code, const char* fmt, ...) {
+  char buf[512];
+  va_list ap;
+  va_start(ap, fmt);
+  vsnprintf(buf, sizeof buf, fmt, ap);
+  va_end(ap);
+  if (b) b->err = buf;
+  g_batch_error = buf;
+  return code;
+}
+
+#define BCK(b, call)                                                                     \
+  do {                                                                                   \
+    cudaError_t e_ = (call);                                                             \
+    if (e_ != cudaSuccess) return bfail(b, LFM_ECUDA, "%s: %s", #call, cudaGetErrorString(e_)); \
+  } while (0)
+
+int size_class(int32_t N) { return N < 32768 ? 0 : (N < 262144 ? 1 : 2); }
+
+void free_buffers(lfm_batch* b) {
+  cudaFree(b->d_cases);
+  cudaFree(b->d_job_case);
+  cudaFree(b->d_job_start);
+  cudaFree(b->d_hdr);
+  cudaFree(b->d_case_step);
+  cudaFree(b->d_status);
+  cudaFree(b->d_iters);
+  cudaFreeHost(b->h_cases);
+  cudaFreeHost(b->h_job_case);
+  cudaFreeHost(b->h_job_start);
+  cudaFreeHost(b->h_hdr);
+  cudaFreeHost(b->h_status);
+  cudaFreeHost(b->h_iters);
+  b->d_cases = nullptr;
+  b->d_job_case = b->d_job_start = b->d_case_step = b->d_status = b->d_iters = nullptr;
+  b->d_hdr = nullptr;
+  b->h_cases = nullptr;
+  b->h_job_case = b->h_job_start = b->h_status = b->h_iters = nullptr;
+  b->h_hdr = nullptr;
+  if (b->gexec) cudaGraphExecDestroy(b->gexec);
+  b->gexec = nullptr;
+  b->cap = 0;
+}
+
+int ensure_capacity(lfm_batch* b, int n) {
+  if (n <= b->cap) return LFM_OK;
+  int cap = b->cap ? b->cap : 64;
+  while (cap < n) cap *= 2;
+  free_buffers(b);
+  BCK(b, cudaMalloc(&b->d_cases, sizeof(CaseDev) * cap));
+  BCK(b, cudaMalloc(&b->d_job_case, sizeof(int32_t) * cap));
+  BCK(b, cudaMalloc(&b->d_job_start, sizeof(int32_t) * (cap + 1)));
+  BCK(b, cudaMalloc(&b->d_hdr, sizeof(BatchHeader)));
+  BCK(b, cudaMalloc(&b->d_case_step, sizeof(int32_t) * cap));
+  BCK(b, cudaMalloc(&b->d_status, sizeof(int32_t) * cap));
+  BCK(b, cudaMalloc(&b->d_iters, sizeof(int32_t) * cap));
+  BCK(b, cudaMallocHost(&b->h_cases, sizeof(CaseDev) * cap));
+  BCK(b, cudaMallocHost(&b->h_job_case, sizeof(int32_t) * cap));
+  BCK(b, cudaMallocHost(&b->h_job_start, sizeof(int32_t) * (cap + 1)));
+  BCK(b, cudaMallocHost(&b->h_hdr, sizeof(BatchHeader)));
+  BCK(b, cudaMallocHost(&b->h_status, sizeof(int32_t) * cap));
+  BCK(b, cudaMallocHost(&b->h_iters, sizeof(int32_t) * cap));
+  b->cap = cap;
+  return LFM_OK;
+}
+
+}  // namespace
+
+extern "C" {
+
+int lfm_batch_create(lfm_batch** out, int device, void* cuda_stream) {
+  if (!out) return bfail(nullptr, LFM_EINVAL, "out is NULL");
+  *out = nullptr;
+  int n = 0;
+  if (cudaGetDeviceCount(&n) != cudaSuccess || n == 0) return bfail(nullptr, LFM_ECUDA, "no CUDA device");
+  if (device < 0 || device >= n) return bfail(nullptr, LFM_EINVAL, "device %d out of range", device);
+  lfm_batch* b = new (std::nothrow) lfm_batch;
+  if (!b) return bfail(nullptr, LFM_ENOMEM, "out of host memory");
+  b->device = device;
+  b->stream = static_cast<cudaStream_t>(cuda_stream);
+  DeviceGuard g(device);
+  if (cudaEventCreateWithFlags(&b->done, cudaEventDisableTiming) != cudaSuccess ||
+      cudaStreamCreateWithFlags(&b->capture_stream, cudaStreamNonBlocking) != cudaSuccess) {
+    lfm_batch_destroy(b);
+    return bfail(nullptr, LFM_ECUDA, "event or stream creation failed");
+  }
+  *out = b;
+  return LFM_OK;
+}
+
+int lfm_batch_add(lfm_batch* b, lfm_ctx* c, int32_t* case_id) {
+  if (!b || !c) return bfail(b, LFM_EINVAL, "batch or context is NULL");
+  if (b->pending) return bfail(b, LFM_ESTATE, "an advance is pending");
+  if (!c->uploaded) return bfail(b, LFM_ESTATE, "the context has no mesh");
+  if (c->batch) return bfail(b, LFM_ESTATE, "the context already belongs to a batch");
+  if (c->device != b->device) return bfail(b, LFM_EINVAL, "the context lives on device %d, the batch on %d", c->device, b->device);
+  if (c->pending_steps) return bfail(b, LFM_ESTATE, "the context has a pending advance");
+  int32_t id = -1;
+  for (size_t i = 0; i < b->slots.size(); ++i)
+    if (!b->slots[i]) {
+      id = (int32_t)i;
+      break;
+    }
+  if (id < 0) {
+    id = (int32_t)b->slots.size();
+    b->slots.push_back(nullptr);
+    b->est_iters.push_back(5.0);
+    b->status.push_back(0);
+  }
+  b->slots[id] = c;
+  b->est_iters[id] = 5.0;
+  b->status[id] = 0;
+  c->batch = b;
+  if (case_id) *case_id = id;
+  return LFM_OK;
+}
+
+int lfm_batch_remove(lfm_batch* b, int32_t id) {
+  if (!b) return bfail(nullptr, LFM_EINVAL, "batch is NULL");
+  if (b->pending) return bfail(b, LFM_ESTATE, "an advance is pending");
+  if (id < 0 || id >= (int32_t)b->slots.size() || !b->slots[id]) return bfail(b, LFM_EINVAL, "no case %d", id);
+  b->slots[id]->batch = nullptr;
+  b->slots[id] = nullptr;
+  return LFM_OK;
+}
+
+int lfm_batch_size(const lfm_batch* b) {
+  if (!b) return 0;
+  int n = 0;
+  for (lfm_ctx* c : b->slots) n += c != nullptr;
+  return n;
+}
+
+int lfm_batch_set_launch(lfm_batch* b, int32_t threads, const int32_t* cells_per_thread) {
+  if (!b) return bfail(nullptr, LFM_EINVAL, "batch is NULL");
+  if (threads != 256 && threads != 512) return bfail(b, LFM_EINVAL, "threads must be 256 or 512");
+  if (cells_per_thread)
+    for (int k = 0; k < 3; ++k)
+      if (cells_per_thread[k] < 1 || cells_per_thread[k] > (1 << 20)) return bfail(b, LFM_EINVAL, "cells per thread out of range");
+  b->threads = threads;
+  if (cells_per_thread)
+    for (int k = 0; k < 3; ++k) b->cpt[k] = cells_per_thread[k];
+  return LFM_OK;
+}
+
+int lfm_batch_get_launch(lfm_batch* b, int32_t* ctas, int32_t* threads, int32_t* cells_per_thread) {
+  if (!b) return bfail(nullptr, LFM_EINVAL, "batch is NULL");
+  DeviceGuard g(b->device);
+  if (ctas) *ctas = max_coresident_batch_ctas(b->threads, b->last_W, b->device);
+  if (threads) *threads = b->threads;
+  if (cells_per_thread)
+    for (int k = 0; k < 3; ++k) cells_per_thread[k] = b->cpt[k];
+  return LFM_OK;
+}
+
+int lfm_batch_set_barrier_timeout(lfm_batch* b, uint64_t ns) {
+  if (!b || ns == 0) return bfail(b, LFM_EINVAL, "bad timeout");
+  b->timeout_ns = ns;
+  if (b->gexec) cudaGraphExecDestroy(b->gexec);
+  b->gexec = nullptr;
+  return LFM_OK;
+}
+
+int lfm_batch_advance_async(lfm_batch* b, int32_t n_steps, int32_t use_graph) {
+  if (!b) return bfail(nullptr, LFM_EINVAL, "batch is NULL");
+  if (b->pending) return bfail(b, LFM_ESTATE, "an advance is pending");
+  if (n_steps < 0 || n_steps > kStatsCap) return bfail(b, LFM_EINVAL, "n_steps must be in [0, %d]", kStatsCap);
+  DeviceGuard g(b->device);
+  b->order.clear();
+  for (size_t i = 0; i < b->slots.size(); ++i)
+    if (b->slots[i]) b->order.push_back((int32_t)i);
+  const int n = (int)b->order.size();
+  b->n_active = n;
+  if (n == 0 || n_steps == 0) return LFM_OK;
+  int rc = ensure_capacity(b, n);
+  if (rc) return rc;
+  int W = 6;
+  for (int i = 0; i < n; ++i) {
+    lfm_ctx* c = b->slots[b->order[i]];
+    if (c->pending_steps) return bfail(b, LFM_ESTATE, "case %d has a pending advance of its own", b->order[i]);
+    refresh_case(c);
+    if ((c->opts.precision == LFM_FP64 && !c->has64) || (c->opts.precision == LFM_MIXED && !c->has32))
+      return bfail(b, LFM_ENOMEM, "case %d has no buffers for its precision", b->order[i]);
+    b->h_cases[i] = c->cs;
+    if (c->W != 6) W = 0;
+  }
+  const int ctas = max_coresident_batch_ctas(b->threads, W, b->device);
+  if (ctas <= 0) return bfail(b, LFM_ECUDA, "no co-resident CTA fits the batch kernel");
+  // jobs: team sizes from the size classes, longest (estimated) job first
+  std::vector<int> k(n), idx(n);
+  std::vector<double> t(n);
+  for (int i = 0; i < n; ++i) {
+    const int32_t N = b->h_cases[i].N;
+    const int64_t per_cta = (int64_t)b->threads * b->cpt[size_class(N)];
+    int64_t kk = (N + per_cta - 1) / per_cta;
+    if (kk < 1) kk = 1;
+    if (kk > ctas) kk = ctas;
+    k[i] = (int)kk;
+    t[i] = (double)N * (b->est_iters[b->order[i]] + 2.0) / (double)kk;
+    idx[i] = i;
+  }
+  std::stable_sort(idx.begin(), idx.end(), [&](int a, int c) { return t[a] > t[c]; });
+  int32_t tickets = 0;
+  for (int j = 0; j < n; ++j) {
+    b->h_job_case[j] = idx[j];
+    b->h_job_start[j] = tickets;
+    tickets += k[idx[j]];
+  }
+  b->h_job_start[n] = tickets;
+  b->h_hdr->n_jobs = n;
+  b->h_hdr->n_tickets = tickets;
+  b->h_hdr->ticket = 0;
+  b->h_hdr->pad = 0;
+  BCK(b, cudaMemcpyAsync(b->d_cases, b->h_cases, sizeof(CaseDev) * n, cudaMemcpyHostToDevice, b->stream));
+  BCK(b, cudaMemcpyAsync(b->d_job_case, b->h_job_case, sizeof(int32_t) * n, cudaMemcpyHostToDevice, b->stream));
+  BCK(b, cudaMemcpyAsync(b->d_job_start, b->h_job_start, sizeof(int32_t) * (n + 1), cudaMemcpyHostToDevice, b->stream));
+  BCK(b, cudaMemcpyAsync(b->d_hdr, b->h_hdr, sizeof(BatchHeader), cudaMemcpyHostToDevice, b->stream));
+  BCK(b, launch_batch_prepare(b->d_cases, n, b->d_case_step, b->stream));
+
+  BatchLaunch bl{};
+  bl.cases = b->d_cases;
+  bl.job_case = b->d_job_case;
+  bl.job_start = b->d_job_start;
+  bl.hdr = b->d_hdr;
+  bl.case_step = b->d_case_step;
+  bl.launch.ctas = ctas;
+  bl.launch.threads = b->threads;
+  bl.launch.timeout_ns = b->timeout_ns;
+  bl.launch.skip_cta = -1;
+  bl.W = W;
+  b->last_ctas = ctas;
+  b->last_W = W;
+  if (use_graph) {
+    if (!b->gexec || b->g_threads != b->threads || b->g_W != W || b->g_ctas != ctas) {
+      if (b->gexec) cudaGraphExecDestroy(b->gexec);
+      b->gexec = nullptr;
+      cudaGraph_t graph = nullptr;
+      BCK(b, cudaStreamBeginCapture(b->capture_stream, cudaStreamCaptureModeThreadLocal));
+      cudaError_t le = launch_batch_steps(bl, 1, b->capture_stream);
+      cudaError_t ce = cudaStreamEndCapture(b->capture_stream, &graph);
+      if (le != cudaSuccess || ce != cudaSuccess) {
+        if (graph) cudaGraphDestroy(graph);
+        return bfail(b, LFM_ECUDA, "capturing the batch step failed: %s / %s", cudaGetErrorString(le),
+                     cudaGetErrorString(ce));
+      }
+      cudaError_t ie = cudaGraphInstantiate(&b->gexec, graph, 0);
+      cudaGraphDestroy(graph);
+      if (ie != cudaSuccess) return bfail(b, LFM_ECUDA, "instantiating the batch step graph failed: %s", cudaGetErrorString(ie));
+      b->g_threads = b->threads;
+      b->g_W = W;
+      b->g_ctas = ctas;
+    }
+    for (int s = 0; s < n_steps; ++s) BCK(b, cudaGraphLaunch(b->gexec, b->stream));
+  } else {
+    BCK(b, launch_batch_steps(bl, n_steps, b->stream));
+  }
+  BCK(b, launch_batch_collect(b->d_cases, n, b->d_case_step, b->d_status, b->d_iters, b->stream));
+  BCK(b, cudaMemcpyAsync(b->h_status, b->d_status, sizeof(int32_t) * n, cudaMemcpyDeviceToHost, b->stream));
+  BCK(b, cudaMemcpyAsync(b->h_iters, b->d_iters, sizeof(int32_t) * n, cudaMemcpyDeviceToHost, b->stream));
+  BCK(b, cudaEventRecord(b->done, b->stream));
+  b->pending = n_steps;
+  return LFM_OK;
+}
+
+int lfm_batch_query(lfm_batch* b) {
+  if (!b) return bfail(nullptr, LFM_EINVAL, "batch is NULL");
+  if (!b->pending) return LFM_OK;
+  DeviceGuard g(b->device);
+  cudaError_t e = cudaEventQuery(b->done);
+  if (e == cudaErrorNotReady) return 1;
+  if (e != cudaSuccess) return bfail(b, LFM_ECUDA, "cudaEventQuery: %s", cudaGetErrorString(e));
+  return LFM_OK;
+}
+
+int lfm_batch_finish(lfm_batch* b) {
+  if (!b) return bfail(nullptr, LFM_EINVAL, "batch is NULL");
+  if (!b->pending) return LFM_OK;
+  DeviceGuard g(b->device);
+  b->pending = 0;
+  BCK(b, cudaEventSynchronize(b->done));
+  int first = LFM_OK;
+  for (int i = 0; i < b->n_active; ++i) {
+    const int32_t id = b->order[i];
+    b->status[id] = b->h_status[i];
+    if (b->h_iters[i] >= 0) b->est_iters[id] = b->h_iters[i];
+    if (b->h_status[i] != 0 && first == LFM_OK) first = b->h_status[i];
+  }
+  if (first != LFM_OK) return bfail(b, first, "at least one case failed (first status %d)", first);
+  return LFM_OK;
+}
+
+int lfm_batch_case_status(lfm_batch* b, int32_t id) {
+  if (!b || id < 0 || id >= (int32_t)b->slots.size()) return LFM_EINVAL;
+  return b->status[id];
+}
+
+int lfm_batch_case_stats(lfm_batch* b, int32_t id, lfm_step_stats* out, int32_t n) {
+  if (!b) return bfail(nullptr, LFM_EINVAL, "batch is NULL");
+  if (id < 0 || id >= (int32_t)b->slots.size() || !b->slots[id]) return bfail(b, LFM_EINVAL, "no case %d", id);
+  if (b->pending) return bfail(b, LFM_ESTATE, "an advance is pending");
+  if (n < 0 || n > kStatsCap) return bfail(b, LFM_EINVAL, "n out of range");
+  if (n == 0 || !out) return LFM_OK;
+  DeviceGuard g(b->device);
+  lfm_ctx* c = b->slots[id];
+  BCK(b, cudaMemcpyAsync(out, c->cs.stats, sizeof(lfm_step_stats) * n, cudaMemcpyDeviceToHost, b->stream));
+  BCK(b, cudaStreamSynchronize(b->stream));
+  return LFM_OK;
+}
+
+int lfm_batch_destroy(lfm_batch* b) {
+  if (!b) return LFM_OK;
+  {
+    DeviceGuard g(b->device);
+    if (b->pending && b->done) cudaEventSynchronize(b->done);
+    for (lfm_ctx* c : b->slots)
+      if (c) c->batch = nullptr;
+    free_buffers(b);
+    if (b->done) cudaEventDestroy(b->done);
+    if (b->capture_stream) cudaStreamDestroy(b->capture_stream);
+  }
+  delete b;
+  return LFM_OK;
+}
+
+const char* lfm_batch_last_error(const lfm_batch* b) {
+  if (b) return b->err.c_str();
+  return g_batch_error.c_str();
 }
 
 }  // extern "C"

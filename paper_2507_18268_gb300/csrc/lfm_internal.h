@@ -100,12 +100,37 @@ struct Launch {
 
 enum Mode { kModeSteps = 0, kModeAssembleOnly = 1 };
 
+// Batched form: job table header in device memory (rewritten before each advance).
+struct BatchHeader {
+  int32_t n_jobs;
+  int32_t n_tickets;
+  int32_t ticket;            // next ticket; reset to 0 before every launch
+  int32_t pad;
+};
+
+struct BatchLaunch {
+  const CaseDev* cases;      // [n_cases] descriptors of the member cases
+  const int32_t* job_case;   // [n_jobs] case of job j
+  const int32_t* job_start;  // [n_jobs + 1] first ticket of job j
+  BatchHeader* hdr;
+  int32_t* case_step;        // [n_cases] steps done in the current advance
+  Launch launch;
+  int W;
+};
+
 // Kernel launchers (lfm_step.cu). Return a cudaError_t.
 cudaError_t launch_steps(const CaseDev& cs, const Launch& L, int n_steps, int mode,
                          cudaStream_t stream);
 // Largest co-resident CTA count for the step kernel at `threads` per CTA.
 int max_coresident_ctas(int precision, int threads, int W, int device);
 cudaError_t launch_boundary_values(const CaseDev& cs, double* Tb, cudaStream_t stream);
+
+// Batched launchers (lfm_batch.cu).
+int max_coresident_batch_ctas(int threads, int W, int device);
+cudaError_t launch_batch_prepare(const CaseDev* cases, int n_cases, int32_t* case_step, cudaStream_t s);
+cudaError_t launch_batch_collect(const CaseDev* cases, int n_cases, const int32_t* case_step, int32_t* status,
+                                 int32_t* iters, cudaStream_t s);
+cudaError_t launch_batch_steps(const BatchLaunch& bl, int n_steps, cudaStream_t s);
 cudaError_t launch_fill(double* a, size_t n, double v, cudaStream_t stream);
 
 }  // namespace lfm
