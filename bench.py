@@ -377,6 +377,140 @@ def main_mixed_only(args, world, rank, local, case, mesh, stream):
                           "ms_per_step": 1e3 * secs / K, "iters_per_step": iters / K}), flush=True)
 
 
+def _cases_with_meshes(cases):
+    """Box meshes depend only on the edge length here (uniform DT): build each once."""
+    from paper_2507_18268_gb300.mesh import box_mesh
+    cache = {}
+    out = []
+    for c in cases:
+        key = (c.nx, c.ny, c.nz)
+        if key not in cache:
+            cache[key] = box_mesh(c)
+        out.append((c, cache[key]))
+    return out
+
+
+def main_batch(args, world, rank, local):
+    """batch512: 512 independent cases (edge log-uniform 16..96), 10 steps each, in one
+    persistent launch per step (graph replay), FP64 and mixed, against the plain FP64
+    single-case path run case after case."""
+    import torch
+
+    from paper_2507_18268_gb300 import binding as B
+    from paper_2507_18268_gb300.batch import Batch
+
+    torch.cuda.set_device(local)
+    n_cases = args.batch_cases
+    steps = args.steps if args.steps_given else 10
+    base_cases = lapcase.batch_cases(n_cases=n_cases, seed=3 + 1000 * rank, n_steps=steps)
+    total_cells = sum(c.n_cells for c in base_cases)
+    stream = torch.cuda.Stream(device=local)
+    results = {}
+    fields = {}
+    for prec, name in ((B.LFM_FP64, "fp64"), (B.LFM_MIXED, "mixed")):
+        cases = [c.with_(precision=prec) for c in base_cases]
+        bt = Batch(device=local, stream=stream)
+        ids = [bt.add_case(c, mesh=m) for c, m in _cases_with_meshes(cases)]
+        tune = bt.autotune()
+        T0 = {cid: bt.field(cid).copy() for cid in ids}
+        # warm-up: W batch steps, then restore the initial fields
+        bt.advance(args.warmup)
+        for cid in ids:
+            bt.cases[cid].set_field(T0[cid])
+        torch.cuda.synchronize()
+        ev0, ev1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+        ev0.record(stream)
+        bt.advance_async(steps, use_graph=True)
+        ev1.record(stream)
+        rc = bt.finish()
+        torch.cuda.synchronize()
+        assert rc == B.LFM_OK, B.lfm_batch_last_error(bt.handle)
+        secs = ev0.elapsed_time(ev1) * 1e-3
+        cell_iters = 0
+        conv = True
+        for cid in ids:
+            st = bt.stats(cid, steps)
+            cell_iters += bt.cases[cid].mesh.n_cells * sum(x["iters"] for x in st)
+            conv = conv and all(x["converged"] for x in st)
+        fields[name] = {cid: bt.field(cid) for cid in ids}
+        results[name] = {"value": cell_iters / secs, "ms_total": 1e3 * secs, "converged": conv,
+                         "cell_steps_per_s": total_cells * steps / secs,
+                         "launch": {"threads": tune["threads"], "cells_per_thread": tune["cells_per_thread"],
+                                    "ctas": B.lfm_batch_get_launch(bt.handle)[0]}}
+        if prec == B.LFM_FP64:
+            # plain FP64: the same cases, one after another, each with the single-case path
+            for cid in ids:
+                bt.cases[cid].set_field(T0[cid])
+            solvers = [bt.remove(cid, close=False) for cid in ids]
+            torch.cuda.synchronize()
+            t0 = time.perf_counter()
+            plain_iters = 0
+            for s in solvers:
+                st = s.advance(steps)
+                plain_iters += s.mesh.n_cells * sum(x["iters"] for x in st)
+            torch.cuda.synchronize()
+            psecs = time.perf_counter() - t0
+            diff = max(float(np.max(np.abs(s.field() - fields["fp64"][cid]) / np.abs(fields["fp64"][cid])))
+                       for cid, s in zip(ids, solvers))
+            results["plain_fp64_sequential"] = {"value": plain_iters / psecs, "ms_total": 1e3 * psecs,
+                                                "max_rel_diff_batched_vs_alone": diff}
+            for s in solvers:
+                s.close()
+        else:
+            ref = fields["fp64"]
+            results[name]["max_rel_diff_vs_fp64_batch"] = max(
+                float(np.max(np.abs(fields[name][cid] - ref[cid]) / np.abs(ref[cid]))) for cid in ids)
+        bt.close()
+    if rank != 0:
+        return
+    line = {"metric": METRIC, "value": results["fp64"]["value"], "unit": UNIT, "n_gpus": world, "steps": steps,
+            "warmup": args.warmup, "ms_per_step": results["fp64"]["ms_total"] / steps, "higher_is_better": True,
+            "scaling": "weak", "vs_baseline": None, "dtype": "f64", "data": "synthetic",
+            "config": {"workload": f"batch{n_cases}: {n_cases} cases, edge log-uniform 16..96 (seed 3), "
+                                   f"{total_cells} cells in total, {steps} steps each, graph-replayed step",
+                       "parallelism": "single GPU"},
+            "batched_fp64": results["fp64"], "batched_mixed": results["mixed"],
+            "plain_fp64_sequential": results["plain_fp64_sequential"],
+            "speedup_batched_fp64_vs_plain": results["fp64"]["value"] / results["plain_fp64_sequential"]["value"],
+            "speedup_batched_mixed_vs_plain": results["mixed"]["value"] / results["plain_fp64_sequential"]["value"]}
+    print(json.dumps(line), flush=True)
+
+
+def main_serve(args, world, rank, local):
+    """serve: Poisson arrivals (200/s, seed 4) of requests with edge log-uniform 32..160,
+    1..50 steps, FP64 or mixed with probability 1/2, under a 120 GB HBM budget; continuous
+    batching against the same requests solved alone one after another in FP64."""
+    import torch
+
+    from paper_2507_18268_gb300.serve import Server, serve_serial_fp64
+
+    torch.cuda.set_device(local)
+    reqs = lapcase.serving_stream(n_requests=args.requests, seed=4 + 1000 * rank)
+    warm = lapcase.serving_stream(n_requests=8, seed=99, n_min=16, n_max=24, max_steps=2)
+    srv = Server(device=local, budget_bytes=120e9)
+    srv.run(warm)
+    rep = srv.run(reqs)
+    srv.close()
+    serial = serve_serial_fp64(reqs, device=local)
+    if rank != 0:
+        return
+    keys = ("requests", "makespan_s", "throughput_req_s", "cell_iterations_per_s", "cell_steps_per_s",
+            "p50_latency_s", "p99_latency_s", "mean_latency_s")
+    served = {k: rep[k] for k in keys}
+    served.update(ticks=rep["ticks"], gpu_busy_s=rep["gpu_busy_s"], peak_hbm_bytes=rep["peak_hbm_bytes"],
+                  failed=rep["failed"])
+    line = {"metric": METRIC, "value": rep["cell_iterations_per_s"], "unit": UNIT, "n_gpus": world,
+            "steps": args.requests, "warmup": 1, "ms_per_step": 1e3 * rep["makespan_s"] / max(args.requests, 1),
+            "higher_is_better": True, "scaling": "weak", "vs_baseline": None, "dtype": "f64+mixed",
+            "data": "synthetic",
+            "config": {"workload": f"serve: {args.requests} requests, Poisson 200/s (seed 4), edge log-uniform "
+                                   "32..160, 1..50 steps, FP64/mixed 50/50, 120 GB HBM budget, one step per tick"},
+            "served": served, "serial_plain_fp64": {k: serial[k] for k in keys},
+            "p99_latency_ratio_serial_over_served": serial["p99_latency_s"] / rep["p99_latency_s"],
+            "throughput_ratio_served_over_serial": rep["throughput_req_s"] / serial["throughput_req_s"]}
+    print(json.dumps(line), flush=True)
+
+
 def main():
     ap = argparse.ArgumentParser()
     ap.add_argument("--gpus", type=int, default=1)
@@ -386,9 +520,13 @@ def main():
     ap.add_argument("--no-mixed", action="store_true")
     ap.add_argument("--no-e2e", action="store_true")
     ap.add_argument("--no-cpu-baseline", action="store_true")
+    ap.add_argument("--workload", choices=["graded200", "batch512", "serve"], default="graded200")
+    ap.add_argument("--batch-cases", type=int, default=512)
+    ap.add_argument("--requests", type=int, default=1000)
     ap.add_argument("--only", choices=["fp64", "mixed"], default=None,
                     help="profiling: run only this precision, device-resident, no e2e or CPU baseline")
     args = ap.parse_args()
+    args.steps_given = any(a.startswith("--steps") for a in sys.argv[1:])
     if args.warmup < 3:
         ap.error("--warmup must be >= 3")
     if args.only:
@@ -398,6 +536,10 @@ def main():
     try:
         if args.impl == "reference":
             main_reference(args, world, rank)
+        elif args.workload == "batch512":
+            main_batch(args, world, rank, local)
+        elif args.workload == "serve":
+            main_serve(args, world, rank, local)
         else:
             main_ours(args, world, rank, local)
     finally:

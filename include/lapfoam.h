@@ -110,6 +110,22 @@ int lfm_face_addressing(int32_t n_cells, int32_t n_faces, const int32_t *owner,
                         const int32_t *neighbour, int32_t *own_start, int32_t *losort,
                         int32_t *lo_start);
 
+/* Box meshes (rectilinear hexahedra, natural numbering c = i + nx (j + ny k), vertex
+ * coordinates xs[nx+1], ys[ny+1], zs[nz+1] strictly increasing; patches x0, x1, y0, y1,
+ * z0, z1 with x-patch faces ordered by (k, j), y-patch by (k, i), z-patch by (j, i)).
+ * Counts of such a mesh: cells, internal faces, boundary faces, slots per cell. */
+int lfm_box_counts(int32_t nx, int32_t ny, int32_t nz, int32_t *n_cells, int32_t *n_faces,
+                   int32_t *n_bfaces, int32_t *slot_width);
+
+/* Host replica of the device box builder (same per-cell routine): fills the slot-major
+ * face-to-cell arrays (slot_other, slot_face [W*N]), V [N], magSf, deltaCoeffs [F],
+ * the cell-side boundary lists (b_start [N+1], b_face [NB]) and bface_cell, bmagSf,
+ * bdeltaCoeffs [NB]. For validation of the closed forms; no device is touched. */
+int lfm_box_layout(int32_t nx, int32_t ny, int32_t nz, const double *xs, const double *ys,
+                   const double *zs, int32_t *slot_other, int32_t *slot_face, double *V,
+                   double *magSf, double *deltaCoeffs, int32_t *b_start, int32_t *b_face,
+                   int32_t *bface_cell, double *bmagSf, double *bdeltaCoeffs);
+
 /* ---- single-case context ----------------------------------------------------------- */
 
 /* Device bytes lfm_upload_mesh needs for this mesh: precision LFM_FP64 or LFM_MIXED for a
@@ -132,6 +148,28 @@ int lfm_bind_workspace(lfm_ctx *ctx, void *dev_ptr, size_t bytes, int32_t precis
  * cell-side boundary-face lists. Resets DT to 0, every patch to zeroGradient, dt to 1,
  * the solver to {1e-6, 0, 1000, 0, LFM_FP64} and T to 0. */
 int lfm_upload_mesh(lfm_ctx *ctx, const lfm_mesh *mesh);
+
+/* Builds a box mesh (see lfm_box_counts) directly on the device -- the same arrays as
+ * uploading the equivalent LDU mesh with lfm_upload_mesh, from closed forms, one thread
+ * per cell -- and resets properties and controls like lfm_upload_mesh. */
+int lfm_upload_box(lfm_ctx *ctx, int32_t nx, int32_t ny, int32_t nz, const double *xs,
+                   const double *ys, const double *zs);
+
+/* Workspace bytes for lfm_upload_box (precision as in lfm_workspace_bytes). */
+size_t lfm_workspace_bytes_box(int32_t nx, int32_t ny, int32_t nz, int32_t precision);
+
+/* Mesh sharing (for many cases on one mesh, e.g. a server): the context uses the mesh
+ * arrays (face-to-cell slots, boundary lists, geometry) uploaded by `src` instead of its
+ * own copy, and owns only its per-case arrays (properties, boundary values, matrix,
+ * field, solver vectors). `src` must stay alive (lfm_destroy refuses it while sharers
+ * exist). Resets properties and controls like lfm_upload_mesh. */
+int lfm_upload_mesh_shared(lfm_ctx *ctx, lfm_ctx *src);
+
+/* Workspace bytes of a context sharing src's mesh (precision as in lfm_workspace_bytes). */
+size_t lfm_workspace_bytes_shared(const lfm_ctx *src, int32_t precision);
+
+/* Sets every cell of T to `value` on the device. */
+int lfm_fill_field(lfm_ctx *ctx, double value);
 
 /* Diffusivity DT per internal face (DT_faces[n_faces]) and per boundary face
  * (DT_bfaces[n_bfaces]); a NULL array takes the value `uniform`. Values must be finite
@@ -278,6 +316,9 @@ int lfm_batch_finish(lfm_batch *b);
 
 /* Status of one case in the last finished advance. */
 int lfm_batch_case_status(lfm_batch *b, int32_t case_id);
+
+/* PCG iterations of one case's last step in the last finished advance (-1: none). */
+int lfm_batch_case_iters(lfm_batch *b, int32_t case_id);
 
 /* Copies the first n per-step records of one case's last advance to host memory. */
 int lfm_batch_case_stats(lfm_batch *b, int32_t case_id, lfm_step_stats *out, int32_t n);

@@ -89,6 +89,9 @@ class Batch:
     def status(self, cid: int) -> int:
         return B.lfm_batch_case_status(self.handle, cid)
 
+    def last_iters(self, cid: int) -> int:
+        return B.lfm_batch_case_iters(self.handle, cid)
+
     def field(self, cid: int) -> np.ndarray:
         return self.cases[cid].field()
 

@@ -65,6 +65,18 @@ _SIGS = {
     "lfm_create": ([POINTER(_ctx_p), c_int, c_void_p], c_int),
     "lfm_bind_workspace": ([_ctx_p, c_void_p, c_size_t, c_int32], c_int),
     "lfm_upload_mesh": ([_ctx_p, POINTER(lfm_mesh)], c_int),
+    "lfm_box_counts": ([c_int32, c_int32, c_int32, POINTER(c_int32), POINTER(c_int32), POINTER(c_int32),
+                        POINTER(c_int32)], c_int),
+    "lfm_box_layout": ([c_int32, c_int32, c_int32, POINTER(c_double), POINTER(c_double), POINTER(c_double),
+                        POINTER(c_int32), POINTER(c_int32), POINTER(c_double), POINTER(c_double), POINTER(c_double),
+                        POINTER(c_int32), POINTER(c_int32), POINTER(c_int32), POINTER(c_double),
+                        POINTER(c_double)], c_int),
+    "lfm_upload_box": ([_ctx_p, c_int32, c_int32, c_int32, POINTER(c_double), POINTER(c_double),
+                        POINTER(c_double)], c_int),
+    "lfm_workspace_bytes_box": ([c_int32, c_int32, c_int32, c_int32], c_size_t),
+    "lfm_upload_mesh_shared": ([_ctx_p, _ctx_p], c_int),
+    "lfm_workspace_bytes_shared": ([_ctx_p, c_int32], c_size_t),
+    "lfm_fill_field": ([_ctx_p, c_double], c_int),
     "lfm_set_diffusivity": ([_ctx_p, c_double, POINTER(c_double), POINTER(c_double)], c_int),
     "lfm_set_patch": ([_ctx_p, c_int32, c_int32, POINTER(c_double), c_double], c_int),
     "lfm_set_time_step": ([_ctx_p, c_double], c_int),
@@ -96,6 +108,7 @@ _SIGS = {
     "lfm_batch_query": ([c_void_p], c_int),
     "lfm_batch_finish": ([c_void_p], c_int),
     "lfm_batch_case_status": ([c_void_p, c_int32], c_int),
+    "lfm_batch_case_iters": ([c_void_p, c_int32], c_int),
     "lfm_batch_case_stats": ([c_void_p, c_int32, POINTER(lfm_step_stats), c_int32], c_int),
     "lfm_batch_destroy": ([c_void_p], c_int),
     "lfm_batch_last_error": ([c_void_p], c_char_p),
@@ -218,6 +231,53 @@ def lfm_bind_workspace(ctx, dev_ptr: int, nbytes: int, precision: int = LFM_BOTH
 def lfm_upload_mesh(ctx, mesh):
     args = MeshArgs(mesh)
     _check(load().lfm_upload_mesh(ctx, ctypes.byref(args.struct)), ctx)
+
+
+def lfm_box_counts(nx: int, ny: int, nz: int):
+    n, f, nb, w = c_int32(), c_int32(), c_int32(), c_int32()
+    _check(load().lfm_box_counts(nx, ny, nz, ctypes.byref(n), ctypes.byref(f), ctypes.byref(nb), ctypes.byref(w)))
+    return n.value, f.value, nb.value, w.value
+
+
+def lfm_box_layout(xs, ys, zs):
+    """Host replica of the device box builder; returns a dict of arrays."""
+    xs, ys, zs = _f64(xs), _f64(ys), _f64(zs)
+    nx, ny, nz = len(xs) - 1, len(ys) - 1, len(zs) - 1
+    N, F, NB, W = lfm_box_counts(nx, ny, nz)
+    out = dict(slot_other=np.empty(max(W * N, 1), np.int32), slot_face=np.empty(max(W * N, 1), np.int32),
+               V=np.empty(N), magSf=np.empty(max(F, 1)), deltaCoeffs=np.empty(max(F, 1)),
+               b_start=np.empty(N + 1, np.int32), b_face=np.empty(NB, np.int32), bface_cell=np.empty(NB, np.int32),
+               bmagSf=np.empty(NB), bdeltaCoeffs=np.empty(NB))
+    _check(load().lfm_box_layout(nx, ny, nz, _ptr(xs, c_double), _ptr(ys, c_double), _ptr(zs, c_double),
+                                 *[_ptr(out[k], c_int32 if out[k].dtype == np.int32 else c_double)
+                                   for k in ("slot_other", "slot_face", "V", "magSf", "deltaCoeffs", "b_start",
+                                             "b_face", "bface_cell", "bmagSf", "bdeltaCoeffs")]))
+    out["slot_other"], out["slot_face"] = out["slot_other"][:W * N], out["slot_face"][:W * N]
+    out["magSf"], out["deltaCoeffs"] = out["magSf"][:F], out["deltaCoeffs"][:F]
+    out.update(n_cells=N, n_faces=F, n_bfaces=NB, W=W)
+    return out
+
+
+def lfm_upload_box(ctx, xs, ys, zs):
+    xs, ys, zs = _f64(xs), _f64(ys), _f64(zs)
+    _check(load().lfm_upload_box(ctx, len(xs) - 1, len(ys) - 1, len(zs) - 1, _ptr(xs, c_double),
+                                 _ptr(ys, c_double), _ptr(zs, c_double)), ctx)
+
+
+def lfm_workspace_bytes_box(nx: int, ny: int, nz: int, precision: int = LFM_BOTH) -> int:
+    return int(load().lfm_workspace_bytes_box(nx, ny, nz, precision))
+
+
+def lfm_upload_mesh_shared(ctx, src_ctx):
+    _check(load().lfm_upload_mesh_shared(ctx, src_ctx), ctx)
+
+
+def lfm_workspace_bytes_shared(src_ctx, precision: int = LFM_BOTH) -> int:
+    return int(load().lfm_workspace_bytes_shared(src_ctx, precision))
+
+
+def lfm_fill_field(ctx, value: float):
+    _check(load().lfm_fill_field(ctx, float(value)), ctx)
 
 
 def lfm_set_diffusivity(ctx, uniform: float, DT_faces=None, DT_bfaces=None):
@@ -411,6 +471,10 @@ def lfm_batch_finish(b) -> int:
 
 def lfm_batch_case_status(b, case_id: int) -> int:
     return int(load().lfm_batch_case_status(b, int(case_id)))
+
+
+def lfm_batch_case_iters(b, case_id: int) -> int:
+    return int(load().lfm_batch_case_iters(b, int(case_id)))
 
 
 def lfm_batch_case_stats(b, case_id: int, n: int):

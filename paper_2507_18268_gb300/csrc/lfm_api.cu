@@ -45,7 +45,8 @@ struct Layout {
 // kLayoutBoth (both sets, so that the precision may change after upload).
 constexpr int kLayoutBoth = -1;
 
-Layout make_layout(int64_t N, int64_t F, int64_t NB, int64_t W, int kind) {
+// shared_mesh: the mesh arrays (slots, boundary lists, geometry) live in another context.
+Layout make_layout(int64_t N, int64_t F, int64_t NB, int64_t W, int kind, bool shared_mesh = false) {
   Layout L{};
   size_t o = 0;
   auto take = [&](size_t bytes) {
@@ -56,18 +57,20 @@ Layout make_layout(int64_t N, int64_t F, int64_t NB, int64_t W, int kind) {
   L.sync = take(sizeof(SyncWords));
   L.partials = take(sizeof(double) * kMaxCtas * kMaxSums);
   L.stats = take(sizeof(lfm_step_stats) * kStatsCap);
-  L.slot_other = take(4 * W * N);
-  L.slot_face = take(4 * W * N);
-  L.b_start = take(4 * (N + 1));
-  L.b_face = take(4 * NB);
-  L.bcell = take(4 * NB);
+  if (!shared_mesh) {
+    L.slot_other = take(4 * W * N);
+    L.slot_face = take(4 * W * N);
+    L.b_start = take(4 * (N + 1));
+    L.b_face = take(4 * NB);
+    L.bcell = take(4 * NB);
+    L.V = take(8 * N);
+    L.magSf = take(8 * F);
+    L.delta = take(8 * F);
+    L.bmagSf = take(8 * NB);
+    L.bdelta = take(8 * NB);
+  }
   L.btype = take(4 * NB);
-  L.V = take(8 * N);
-  L.magSf = take(8 * F);
-  L.delta = take(8 * F);
   L.DT = take(8 * F);
-  L.bmagSf = take(8 * NB);
-  L.bdelta = take(8 * NB);
   L.bDT = take(8 * NB);
   L.bval = take(8 * NB);
   L.diag = take(8 * N);
@@ -155,6 +158,8 @@ struct lfm_ctx {
   int pending_remaining = 0;
   std::vector<lfm_step_stats> stats_acc;
   lfm_batch* batch = nullptr;         // batch this context belongs to, if any
+  lfm_ctx* mesh_src = nullptr;        // context whose mesh arrays this one uses
+  int n_sharers = 0;                  // contexts using this one's mesh arrays
 };
 
 namespace {
@@ -307,20 +312,34 @@ void bind_pointers(lfm_ctx* c) {
   cs.partials = reinterpret_cast<double*>(b + L.partials);
   cs.stats = reinterpret_cast<lfm_step_stats*>(b + L.stats);
   cs.W = c->W;
-  cs.slot_other = reinterpret_cast<const int32_t*>(b + L.slot_other);
-  cs.slot_face = reinterpret_cast<const int32_t*>(b + L.slot_face);
-  cs.b_start = reinterpret_cast<const int32_t*>(b + L.b_start);
-  cs.b_face = reinterpret_cast<const int32_t*>(b + L.b_face);
-  cs.bcell = reinterpret_cast<const int32_t*>(b + L.bcell);
   cs.btype = reinterpret_cast<const int32_t*>(b + L.btype);
-  cs.V = reinterpret_cast<const double*>(b + L.V);
-  cs.magSf = reinterpret_cast<const double*>(b + L.magSf);
-  cs.delta = reinterpret_cast<const double*>(b + L.delta);
   cs.DT = reinterpret_cast<const double*>(b + L.DT);
-  cs.bmagSf = reinterpret_cast<const double*>(b + L.bmagSf);
-  cs.bdelta = reinterpret_cast<const double*>(b + L.bdelta);
   cs.bDT = reinterpret_cast<const double*>(b + L.bDT);
   cs.bval = reinterpret_cast<const double*>(b + L.bval);
+  if (c->mesh_src) {
+    const CaseDev& m = c->mesh_src->cs;
+    cs.slot_other = m.slot_other;
+    cs.slot_face = m.slot_face;
+    cs.b_start = m.b_start;
+    cs.b_face = m.b_face;
+    cs.bcell = m.bcell;
+    cs.V = m.V;
+    cs.magSf = m.magSf;
+    cs.delta = m.delta;
+    cs.bmagSf = m.bmagSf;
+    cs.bdelta = m.bdelta;
+  } else {
+    cs.slot_other = reinterpret_cast<const int32_t*>(b + L.slot_other);
+    cs.slot_face = reinterpret_cast<const int32_t*>(b + L.slot_face);
+    cs.b_start = reinterpret_cast<const int32_t*>(b + L.b_start);
+    cs.b_face = reinterpret_cast<const int32_t*>(b + L.b_face);
+    cs.bcell = reinterpret_cast<const int32_t*>(b + L.bcell);
+    cs.V = reinterpret_cast<const double*>(b + L.V);
+    cs.magSf = reinterpret_cast<const double*>(b + L.magSf);
+    cs.delta = reinterpret_cast<const double*>(b + L.delta);
+    cs.bmagSf = reinterpret_cast<const double*>(b + L.bmagSf);
+    cs.bdelta = reinterpret_cast<const double*>(b + L.bdelta);
+  }
   cs.diag = reinterpret_cast<double*>(b + L.diag);
   cs.upper = reinterpret_cast<double*>(b + L.upper);
   cs.slot_coef = reinterpret_cast<double*>(b + L.slot_coef);
@@ -459,6 +478,7 @@ int lfm_bind_workspace(lfm_ctx* c, void* dev_ptr, size_t bytes, int32_t precisio
 
 int lfm_upload_mesh(lfm_ctx* c, const lfm_mesh* m) {
   if (!c) return fail_free(LFM_EINVAL, "context is NULL");
+  if (c->n_sharers > 0 || c->mesh_src) return fail(c, LFM_ESTATE, "the context shares a mesh");
   std::string why;
   if (check_mesh(m, why) != LFM_OK) return fail(c, LFM_EINVAL, "%s", why.c_str());
   DeviceGuard g(c->device);
@@ -542,6 +562,194 @@ int lfm_upload_mesh(lfm_ctx* c, const lfm_mesh* m) {
   c->uploaded = true;
   c->ctas = c->threads = 0;
   return choose_launch(c);
+}
+
+namespace {
+int check_box(int32_t nx, int32_t ny, int32_t nz, const double* xs, const double* ys, const double* zs,
+              std::string& why) {
+  if (nx < 1 || ny < 1 || nz < 1) return set_why(why, "box dimensions must be >= 1");
+  if (!xs || !ys || !zs) return set_why(why, "vertex coordinates missing");
+  const long long N = (long long)nx * ny * nz;
+  const long long F = (long long)(nx - 1) * ny * nz + (long long)nx * (ny - 1) * nz + (long long)nx * ny * (nz - 1);
+  if (N > 0x7fffffffLL || F > 0x7fffffffLL) return set_why(why, "box too large for 32-bit indices");
+  if ((long long)nx + ny + nz + 3 > (long long)kMaxCtas * kMaxSums) return set_why(why, "too many vertex planes");
+  const double* ax[3] = {xs, ys, zs};
+  const int32_t n[3] = {nx, ny, nz};
+  for (int a = 0; a < 3; ++a)
+    for (int32_t i = 0; i <= n[a]; ++i) {
+      if (!std::isfinite(ax[a][i])) return set_why(why, "vertex coordinate not finite");
+      if (i > 0 && !(ax[a][i] > ax[a][i - 1])) return set_why(why, "vertex coordinates must increase strictly");
+    }
+  return LFM_OK;
+}
+}  // namespace
+
+int lfm_box_counts(int32_t nx, int32_t ny, int32_t nz, int32_t* n_cells, int32_t* n_faces, int32_t* n_bfaces,
+                   int32_t* slot_width) {
+  if (nx < 1 || ny < 1 || nz < 1) return fail_free(LFM_EINVAL, "box dimensions must be >= 1");
+  const long long N = (long long)nx * ny * nz;
+  const long long F = (long long)(nx - 1) * ny * nz + (long long)nx * (ny - 1) * nz + (long long)nx * ny * (nz - 1);
+  if (N > 0x7fffffffLL || F > 0x7fffffffLL) return fail_free(LFM_EINVAL, "box too large for 32-bit indices");
+  if (n_cells) *n_cells = (int32_t)N;
+  if (n_faces) *n_faces = (int32_t)F;
+  if (n_bfaces) *n_bfaces = (int32_t)(2 * ((long long)ny * nz + (long long)nx * nz + (long long)nx * ny));
+  if (slot_width) *slot_width = box_slot_width(nx, ny, nz);
+  return LFM_OK;
+}
+
+int lfm_box_layout(int32_t nx, int32_t ny, int32_t nz, const double* xs, const double* ys, const double* zs,
+                   int32_t* slot_other, int32_t* slot_face, double* V, double* magSf, double* delta,
+                   int32_t* b_start, int32_t* b_face, int32_t* bcell, double* bmagSf, double* bdelta) {
+  std::string why;
+  if (check_box(nx, ny, nz, xs, ys, zs, why) != LFM_OK) return fail_free(LFM_EINVAL, "%s", why.c_str());
+  if (!slot_other || !slot_face || !V || !magSf || !delta || !b_start || !b_face || !bcell || !bmagSf || !bdelta)
+    return fail_free(LFM_EINVAL, "output arrays missing");
+  box_layout_host(nx, ny, nz, box_slot_width(nx, ny, nz), xs, ys, zs, slot_other, slot_face, V, magSf, delta,
+                  b_start, b_face, bcell, bmagSf, bdelta);
+  return LFM_OK;
+}
+
+int lfm_upload_box(lfm_ctx* c, int32_t nx, int32_t ny, int32_t nz, const double* xs, const double* ys,
+                   const double* zs) {
+  if (!c) return fail_free(LFM_EINVAL, "context is NULL");
+  if (c->uploaded || c->n_sharers > 0 || c->mesh_src) return fail(c, LFM_ESTATE, "the context already has a mesh");
+  std::string why;
+  if (check_box(nx, ny, nz, xs, ys, zs, why) != LFM_OK) return fail(c, LFM_EINVAL, "%s", why.c_str());
+  DeviceGuard g(c->device);
+  int32_t N, F, NB, W;
+  lfm_box_counts(nx, ny, nz, &N, &F, &NB, &W);
+  const int kind = c->ws_bound ? c->ws_kind : kLayoutBoth;
+  const Layout use = make_layout(N, F, NB, W, kind);
+  const bool has64 = kind != LFM_MIXED, has32 = kind != LFM_FP64;
+  if (c->ws_bound) {
+    if (c->ws_bytes < use.total) return fail(c, LFM_ENOMEM, "workspace has %zu bytes, needs %zu", c->ws_bytes, use.total);
+  } else {
+    void* p = nullptr;
+    cudaError_t e = cudaMalloc(&p, use.total);
+    if (e != cudaSuccess) return fail(c, LFM_ENOMEM, "device allocation of %zu bytes failed: %s", use.total, cudaGetErrorString(e));
+    c->ws = static_cast<char*>(p);
+    c->ws_bytes = use.total;
+    c->ws_owned = true;
+  }
+  c->lay = use;
+  c->N = N;
+  c->F = F;
+  c->NB = NB;
+  c->W = W;
+  c->has64 = has64;
+  c->has32 = has32;
+  c->n_patches = 6;
+  const int32_t sizes[6] = {ny * nz, ny * nz, nx * nz, nx * nz, nx * ny, nx * ny};
+  c->patch_start.assign(6, 0);
+  c->patch_size.assign(sizes, sizes + 6);
+  for (int p = 1; p < 6; ++p) c->patch_start[p] = c->patch_start[p - 1] + sizes[p - 1];
+  c->patch_type.assign(6, LFM_ZERO_GRADIENT);
+  bind_pointers(c);
+  // vertex coordinates staged in the (not yet used) partial-sum table
+  double* coords = c->cs.partials;
+  const Layout& Y = c->lay;
+  CK(c, cudaMemcpyAsync(coords, xs, sizeof(double) * (nx + 1), cudaMemcpyHostToDevice, c->stream));
+  CK(c, cudaMemcpyAsync(coords + nx + 1, ys, sizeof(double) * (ny + 1), cudaMemcpyHostToDevice, c->stream));
+  CK(c, cudaMemcpyAsync(coords + nx + ny + 2, zs, sizeof(double) * (nz + 1), cudaMemcpyHostToDevice, c->stream));
+  CK(c, launch_box(nx, ny, nz, W, coords, coords + nx + 1, coords + nx + ny + 2, c->cs, c->stream));
+  std::vector<int32_t> btype(NB, LFM_ZERO_GRADIENT);
+  int rc;
+  if ((rc = h2d(c, Y.btype, btype.data(), NB))) return rc;
+  CK(c, cudaMemsetAsync(c->ws + Y.bDT, 0, sizeof(double) * NB, c->stream));
+  CK(c, cudaMemsetAsync(c->ws + Y.bval, 0, sizeof(double) * NB, c->stream));
+  const size_t WN = (size_t)W * N;
+  if (WN > 0) {
+    CK(c, cudaMemsetAsync(c->ws + Y.slot_coef, 0, sizeof(double) * WN, c->stream));
+    if (has32) CK(c, cudaMemsetAsync(c->ws + Y.slot_coef32, 0, sizeof(float) * WN, c->stream));
+  }
+  CK(c, cudaMemsetAsync(c->ws + Y.DT, 0, sizeof(double) * (F > 0 ? F : 1), c->stream));
+  CK(c, cudaMemsetAsync(c->ws + Y.x, 0, sizeof(double) * N, c->stream));
+  CK(c, cudaStreamSynchronize(c->stream));
+  c->dt = 1.0;
+  c->opts = lfm_solver_opts{1e-6, 0.0, 1000, 0, has64 ? LFM_FP64 : LFM_MIXED};
+  c->uploaded = true;
+  c->ctas = c->threads = 0;
+  return choose_launch(c);
+}
+
+size_t lfm_workspace_bytes_box(int32_t nx, int32_t ny, int32_t nz, int32_t precision) {
+  int32_t N, F, NB, W;
+  if (lfm_box_counts(nx, ny, nz, &N, &F, &NB, &W) != LFM_OK) return 0;
+  if (precision != LFM_FP64 && precision != LFM_MIXED) precision = kLayoutBoth;
+  return make_layout(N, F, NB, W, precision).total;
+}
+
+size_t lfm_workspace_bytes_shared(const lfm_ctx* src, int32_t precision) {
+  if (!src || !src->uploaded) return 0;
+  if (precision != LFM_FP64 && precision != LFM_MIXED) precision = kLayoutBoth;
+  return make_layout(src->N, src->F, src->NB, src->W, precision, true).total;
+}
+
+int lfm_upload_mesh_shared(lfm_ctx* c, lfm_ctx* src) {
+  if (!c || !src) return fail_free(LFM_EINVAL, "context is NULL");
+  if (c == src) return fail(c, LFM_EINVAL, "a context cannot share its own mesh");
+  if (c->uploaded || c->n_sharers > 0) return fail(c, LFM_ESTATE, "the context already has a mesh");
+  if (!src->uploaded) return fail(c, LFM_ESTATE, "the source context has no mesh");
+  if (src->device != c->device) return fail(c, LFM_EINVAL, "the source context lives on another device");
+  lfm_ctx* root = src->mesh_src ? src->mesh_src : src;
+  DeviceGuard g(c->device);
+  const int kind = c->ws_bound ? c->ws_kind : kLayoutBoth;
+  const Layout use = make_layout(root->N, root->F, root->NB, root->W, kind, true);
+  const bool has64 = kind != LFM_MIXED, has32 = kind != LFM_FP64;
+  if (c->ws_bound) {
+    if (c->ws_bytes < use.total) return fail(c, LFM_ENOMEM, "workspace has %zu bytes, needs %zu", c->ws_bytes, use.total);
+  } else {
+    void* p = nullptr;
+    cudaError_t e = cudaMalloc(&p, use.total);
+    if (e != cudaSuccess) return fail(c, LFM_ENOMEM, "device allocation of %zu bytes failed: %s", use.total, cudaGetErrorString(e));
+    c->ws = static_cast<char*>(p);
+    c->ws_bytes = use.total;
+    c->ws_owned = true;
+  }
+  c->mesh_src = root;
+  root->n_sharers++;
+  c->lay = use;
+  c->N = root->N;
+  c->F = root->F;
+  c->NB = root->NB;
+  c->W = root->W;
+  c->has64 = has64;
+  c->has32 = has32;
+  c->n_patches = root->n_patches;
+  c->patch_start = root->patch_start;
+  c->patch_size = root->patch_size;
+  c->patch_type.assign(root->n_patches, LFM_ZERO_GRADIENT);
+  bind_pointers(c);
+  const int32_t N = c->N, F = c->F, NB = c->NB;
+  const Layout& Y = c->lay;
+  const size_t WN = (size_t)c->W * N;
+  std::vector<int32_t> btype(NB > 0 ? NB : 1, LFM_ZERO_GRADIENT);
+  int rc;
+  if ((rc = h2d(c, Y.btype, btype.data(), NB))) return rc;
+  CK(c, cudaMemsetAsync(c->ws + Y.bDT, 0, sizeof(double) * (NB > 0 ? NB : 1), c->stream));
+  CK(c, cudaMemsetAsync(c->ws + Y.bval, 0, sizeof(double) * (NB > 0 ? NB : 1), c->stream));
+  if (WN > 0) {
+    CK(c, cudaMemsetAsync(c->ws + Y.slot_coef, 0, sizeof(double) * WN, c->stream));
+    if (has32) CK(c, cudaMemsetAsync(c->ws + Y.slot_coef32, 0, sizeof(float) * WN, c->stream));
+  }
+  CK(c, cudaMemsetAsync(c->ws + Y.DT, 0, sizeof(double) * (F > 0 ? F : 1), c->stream));
+  CK(c, cudaMemsetAsync(c->ws + Y.x, 0, sizeof(double) * N, c->stream));
+  CK(c, cudaStreamSynchronize(c->stream));
+  c->dt = 1.0;
+  c->opts = lfm_solver_opts{1e-6, 0.0, 1000, 0, has64 ? LFM_FP64 : LFM_MIXED};
+  c->uploaded = true;
+  c->ctas = c->threads = 0;
+  return choose_launch(c);
+}
+
+int lfm_fill_field(lfm_ctx* c, double value) {
+  int rc = need_uploaded(c);
+  if (rc) return rc;
+  if (!std::isfinite(value)) return fail(c, LFM_EINVAL, "value must be finite");
+  DeviceGuard g(c->device);
+  CK(c, launch_fill(c->cs.x, c->N, value, c->stream));
+  CK(c, cudaStreamSynchronize(c->stream));
+  return LFM_OK;
 }
 
 int lfm_set_diffusivity(lfm_ctx* c, double uniform, const double* DT_faces, const double* DT_bfaces) {
@@ -768,6 +976,8 @@ int lfm_debug_skip_arrival(lfm_ctx* c, int32_t cta) {
 int lfm_destroy(lfm_ctx* c) {
   if (!c) return LFM_OK;
   if (c->batch) return fail(c, LFM_ESTATE, "remove the context from its batch first");
+  if (c->n_sharers > 0) return fail(c, LFM_ESTATE, "%d contexts still use this context's mesh", c->n_sharers);
+  if (c->mesh_src) c->mesh_src->n_sharers--;
   {
     DeviceGuard g(c->device);
     if (c->pending_steps > 0 && c->done) cudaEventSynchronize(c->done);
@@ -800,6 +1010,7 @@ struct lfm_batch {
   std::vector<lfm_ctx*> slots;      // case id -> member (nullptr once removed)
   std::vector<double> est_iters;    // per case id: PCG iterations of its last step
   std::vector<int32_t> status;      // per case id: status of the last advance
+  std::vector<int32_t> last_iters;  // per case id: PCG iterations of its last step (-1: none)
   std::vector<int32_t> order;       // compact index of the last advance -> case id
   int threads = 512;
   int cpt[3] = {4, 8, 16};          // cells per thread by size class
@@ -941,10 +1152,12 @@ int lfm_batch_add(lfm_batch* b, lfm_ctx* c, int32_t* case_id) {
     b->slots.push_back(nullptr);
     b->est_iters.push_back(5.0);
     b->status.push_back(0);
+    b->last_iters.push_back(-1);
   }
   b->slots[id] = c;
   b->est_iters[id] = 5.0;
   b->status[id] = 0;
+  b->last_iters[id] = -1;
   c->batch = b;
   if (case_id) *case_id = id;
   return LFM_OK;
@@ -1117,6 +1330,7 @@ int lfm_batch_finish(lfm_batch* b) {
   for (int i = 0; i < b->n_active; ++i) {
     const int32_t id = b->order[i];
     b->status[id] = b->h_status[i];
+    b->last_iters[id] = b->h_iters[i];
     if (b->h_iters[i] >= 0) b->est_iters[id] = b->h_iters[i];
     if (b->h_status[i] != 0 && first == LFM_OK) first = b->h_status[i];
   }
@@ -1127,6 +1341,11 @@ int lfm_batch_finish(lfm_batch* b) {
 int lfm_batch_case_status(lfm_batch* b, int32_t id) {
   if (!b || id < 0 || id >= (int32_t)b->slots.size()) return LFM_EINVAL;
   return b->status[id];
+}
+
+int lfm_batch_case_iters(lfm_batch* b, int32_t id) {
+  if (!b || id < 0 || id >= (int32_t)b->slots.size()) return -1;
+  return b->last_iters[id];
 }
 
 int lfm_batch_case_stats(lfm_batch* b, int32_t id, lfm_step_stats* out, int32_t n) {

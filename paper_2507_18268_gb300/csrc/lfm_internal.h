@@ -125,6 +125,15 @@ cudaError_t launch_steps(const CaseDev& cs, const Launch& L, int n_steps, int mo
 int max_coresident_ctas(int precision, int threads, int W, int device);
 cudaError_t launch_boundary_values(const CaseDev& cs, double* Tb, cudaStream_t stream);
 
+// Box meshes built from closed forms (lfm_box.cu).
+int box_slot_width(long long nx, long long ny, long long nz);
+cudaError_t launch_box(long long nx, long long ny, long long nz, int W, const double* xs, const double* ys,
+                       const double* zs, const CaseDev& cs, cudaStream_t stream);
+void box_layout_host(long long nx, long long ny, long long nz, int W, const double* xs, const double* ys,
+                     const double* zs, int32_t* slot_other, int32_t* slot_face, double* V, double* magSf,
+                     double* delta, int32_t* b_start, int32_t* b_face, int32_t* bcell, double* bmagSf,
+                     double* bdelta);
+
 // Batched launchers (lfm_batch.cu).
 int max_coresident_batch_ctas(int threads, int W, int device);
 cudaError_t launch_batch_prepare(const CaseDev* cases, int n_cases, int32_t* case_step, cudaStream_t s);

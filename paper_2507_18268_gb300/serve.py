@@ -1,0 +1,216 @@
+"""Serving form: continuous batching of heat-diffusion solve requests on one GPU.
+
+Requests (a box case and a number of implicit steps, FP64 or mixed precision) arrive over
+time. The server keeps every admitted case resident on the device (matrix, PCG state and
+field live in its workspace) and advances all of them together: each scheduling tick is
+one batched launch that moves every admitted case forward one time step, so requests that
+arrive while others run join at the next tick and their work overlaps on the device.
+Admission is first-come first-served against an HBM budget (the workspaces of admitted
+cases plus the shared meshes); a finished case's field is read back, its workspace is
+released, and the next waiting request takes the space.
+
+Cases with the same box share one mesh built on the device (``lfm_upload_box`` once per
+size, then ``lfm_upload_mesh_shared`` per request), so admitting a request costs a
+workspace allocation and a few small uploads, not a host mesh build.
+"""
+from __future__ import annotations
+
+import collections
+import dataclasses
+import time
+from typing import Dict, List, Optional
+
+import numpy as np
+
+import lapcase
+
+from . import binding as B
+from .batch import Batch
+from .solver import Solver
+
+
+@dataclasses.dataclass
+class Done:
+    index: int
+    n_cells: int
+    steps: int
+    precision: int
+    arrival_s: float
+    admitted_s: float
+    finished_s: float
+    cell_iterations: int
+    status: int
+    field: Optional[np.ndarray] = None
+
+    @property
+    def latency_s(self) -> float:
+        return self.finished_s - self.arrival_s
+
+
+def percentile(xs, q):
+    return float(np.percentile(np.asarray(xs, dtype=float), q)) if len(xs) else float("nan")
+
+
+class Server:
+    def __init__(self, device: int = 0, budget_bytes: float = 120e9, use_graph: bool = True,
+                 launch: Optional[tuple] = None):
+        import torch
+
+        self.device = device
+        self.budget = float(budget_bytes)
+        self.use_graph = use_graph
+        self.stream = torch.cuda.Stream(device=device)
+        self.batch = Batch(device=device, stream=self.stream)
+        if launch:
+            self.batch.set_launch(*launch)
+        self.meshes: Dict[tuple, Solver] = collections.OrderedDict()
+        self.mesh_users: Dict[tuple, int] = collections.defaultdict(int)
+        self.used = 0.0
+        self.peak_used = 0.0
+
+    # ---- resources -----------------------------------------------------------------------
+    def _key(self, case: lapcase.RawCase):
+        return (case.nx, case.ny, case.nz, case.xs.tobytes(), case.ys.tobytes(), case.zs.tobytes())
+
+    def _mesh_for(self, case: lapcase.RawCase) -> Solver:
+        key = self._key(case)
+        if key in self.meshes:
+            self.meshes.move_to_end(key)
+            return self.meshes[key]
+        owner = Solver(box=(case.xs, case.ys, case.zs), device=self.device, layout=B.LFM_FP64)
+        self.meshes[key] = owner
+        self.used += owner.workspace_bytes
+        return owner
+
+    def _evict_idle_meshes(self, need: float):
+        for key in list(self.meshes):
+            if self.used + need <= self.budget:
+                return
+            if self.mesh_users[key] == 0:
+                owner = self.meshes.pop(key)
+                self.used -= owner.workspace_bytes
+                owner.close()
+
+    def _need(self, case: lapcase.RawCase) -> float:
+        N, F, NB, W = B.lfm_box_counts(case.nx, case.ny, case.nz)
+        per_case = B.lfm_workspace_bytes_box(case.nx, case.ny, case.nz, case.precision)
+        mesh = 0 if self._key(case) in self.meshes else B.lfm_workspace_bytes_box(case.nx, case.ny, case.nz,
+                                                                                   B.LFM_FP64)
+        # a sharer's workspace is smaller than a full one; this bound is conservative
+        return float(per_case + mesh)
+
+    # ---- the loop ------------------------------------------------------------------------
+    def run(self, requests: List[lapcase.Request], keep_fields: bool = False, time_scale: float = 1.0) -> dict:
+        """Serves the requests (arrival times scaled by time_scale) and returns a report."""
+        pending = collections.deque()
+        active: Dict[int, dict] = {}
+        done: List[Done] = []
+        nxt = 0
+        ticks = 0
+        busy = 0.0
+        t0 = time.perf_counter()
+        clock = lambda: time.perf_counter() - t0  # noqa: E731
+        while nxt < len(requests) or pending or active:
+            now = clock()
+            while nxt < len(requests) and requests[nxt].arrival_s * time_scale <= now:
+                pending.append(nxt)
+                nxt += 1
+            # admission: first come, first served, while the budget allows
+            while pending:
+                r = requests[pending[0]]
+                need = self._need(r.case)
+                if self.used + need > self.budget:
+                    self._evict_idle_meshes(need)
+                if self.used + need > self.budget and active:
+                    break
+                owner = self._mesh_for(r.case)
+                s = Solver.sharing(owner, r.case, device=self.device, layout=r.case.precision)
+                self.mesh_users[self._key(r.case)] += 1
+                self.used += s.workspace_bytes
+                self.peak_used = max(self.peak_used, self.used)
+                cid = self.batch.add(s)
+                active[cid] = {"req": pending.popleft(), "left": r.case.n_steps, "admitted": clock(),
+                               "cell_iters": 0, "solver": s}
+            if not active:
+                if nxt < len(requests):
+                    time.sleep(max(0.0, requests[nxt].arrival_s * time_scale - clock()))
+                continue
+            tb = time.perf_counter()
+            self.batch.advance_async(1, self.use_graph)
+            self.batch.finish()
+            busy += time.perf_counter() - tb
+            ticks += 1
+            now = clock()
+            for cid in list(active):
+                a = active[cid]
+                a["left"] -= 1
+                st = self.batch.status(cid)
+                a["cell_iters"] += a["solver"].mesh.n_cells * max(self.batch.last_iters(cid), 0)
+                if a["left"] == 0 or st != 0:
+                    r = requests[a["req"]]
+                    s = self.batch.remove(cid, close=False)
+                    field = s.field() if keep_fields else None
+                    done.append(Done(a["req"], s.mesh.n_cells, r.case.n_steps, r.case.precision,
+                                     r.arrival_s * time_scale, a["admitted"], now, a["cell_iters"], st, field))
+                    self.used -= s.workspace_bytes
+                    self.mesh_users[self._key(r.case)] -= 1
+                    s.close()
+                    del active[cid]
+        makespan = clock()
+        lat = [d.latency_s for d in done]
+        cells_steps = sum(d.n_cells * d.steps for d in done)
+        cell_iters = sum(d.cell_iterations for d in done)
+        return {"requests": len(done), "makespan_s": makespan, "throughput_req_s": len(done) / makespan,
+                "cell_steps_per_s": cells_steps / makespan, "cell_iterations_per_s": cell_iters / makespan,
+                "p50_latency_s": percentile(lat, 50),
+                "p99_latency_s": percentile(lat, 99), "mean_latency_s": float(np.mean(lat)) if lat else float("nan"),
+                "ticks": ticks, "gpu_busy_s": busy, "peak_hbm_bytes": self.peak_used,
+                "failed": sum(1 for d in done if d.status != 0), "done": done}
+
+    def close(self):
+        self.batch.close()
+        for owner in self.meshes.values():
+            owner.close()
+        self.meshes.clear()
+
+
+def serve_serial_fp64(requests: List[lapcase.Request], device: int = 0, keep_fields: bool = False,
+                      time_scale: float = 1.0) -> dict:
+    """Baseline: every request solved alone in FP64 with the single-case path, one after
+    another in arrival order (meshes built on the device and shared, as in the server).
+    Latency follows the queue: a request starts when it has arrived and the previous one
+    has finished."""
+    import torch
+
+    meshes: Dict[tuple, Solver] = {}
+    finish_prev = 0.0
+    lat, done = [], []
+    t_first = requests[0].arrival_s * time_scale if requests else 0.0
+    cells_steps = 0
+    cell_iters = 0
+    for i, r in enumerate(requests):
+        case = r.case.with_(precision=B.LFM_FP64)
+        key = (case.nx, case.ny, case.nz)
+        if key not in meshes:
+            meshes[key] = Solver(box=(case.xs, case.ys, case.zs), device=device, layout=B.LFM_FP64)
+        torch.cuda.synchronize()
+        t0 = time.perf_counter()
+        s = Solver.sharing(meshes[key], case, device=device, layout=B.LFM_FP64)
+        st = s.advance(case.n_steps)
+        field = s.field()
+        cell_iters += s.mesh.n_cells * sum(x["iters"] for x in st)
+        s.close()
+        dt = time.perf_counter() - t0
+        start = max(r.arrival_s * time_scale, finish_prev)
+        finish_prev = start + dt
+        lat.append(finish_prev - r.arrival_s * time_scale)
+        cells_steps += s.mesh.n_cells * case.n_steps
+        if keep_fields:
+            done.append(field)
+    for m in meshes.values():
+        m.close()
+    makespan = finish_prev - t_first
+    return {"requests": len(requests), "makespan_s": makespan, "throughput_req_s": len(requests) / makespan,
+            "cell_steps_per_s": cells_steps / makespan, "cell_iterations_per_s": cell_iters / makespan,
+            "p50_latency_s": percentile(lat, 50), "p99_latency_s": percentile(lat, 99),
+            "mean_latency_s": float(np.mean(lat)), "fields": done if keep_fields else None}

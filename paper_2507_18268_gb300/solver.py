@@ -23,22 +23,52 @@ def _stream_handle(stream) -> Optional[int]:
     return int(stream.cuda_stream)  # torch.cuda.Stream
 
 
+class BoxInfo:
+    """Sizes of a mesh that was built on the device or is shared (no host arrays)."""
+
+    def __init__(self, n_cells: int, n_faces: int, n_bfaces: int):
+        self.n_cells, self.n_faces, self.n_bfaces = n_cells, n_faces, n_bfaces
+        self.DT_faces = self.DT_bfaces = None
+        self.cell_of_label = None
+
+
 class Solver:
-    def __init__(self, mesh: LduMesh, device: int = 0, stream=None, workspace: str = "torch",
-                 layout: int = B.LFM_BOTH):
-        self.mesh = mesh
+    """One case: exactly one of ``mesh`` (host LDU arrays, uploaded), ``box`` ((xs, ys, zs)
+    vertex coordinates of a naturally numbered box, built on the device) or ``share``
+    (another Solver whose uploaded mesh this one uses) gives the mesh."""
+
+    def __init__(self, mesh: Optional[LduMesh] = None, device: int = 0, stream=None, workspace: str = "torch",
+                 layout: int = B.LFM_BOTH, box=None, share: Optional["Solver"] = None):
+        assert (mesh is not None) + (box is not None) + (share is not None) == 1
         self.device = device
         self.stream = stream
         self._ws = None
+        self._share = share
         self.ctx = B.lfm_create(device, _stream_handle(stream))
         try:
+            if mesh is not None:
+                self.mesh = mesh
+                nbytes = B.lfm_workspace_bytes(mesh, layout)
+            elif box is not None:
+                xs, ys, zs = box
+                n, f, nb, _ = B.lfm_box_counts(len(xs) - 1, len(ys) - 1, len(zs) - 1)
+                self.mesh = BoxInfo(n, f, nb)
+                nbytes = B.lfm_workspace_bytes_box(len(xs) - 1, len(ys) - 1, len(zs) - 1, layout)
+            else:
+                self.mesh = BoxInfo(share.mesh.n_cells, share.mesh.n_faces, share.mesh.n_bfaces)
+                nbytes = B.lfm_workspace_bytes_shared(share.ctx, layout)
+            self.workspace_bytes = nbytes
             if workspace == "torch":
                 import torch
 
-                nbytes = B.lfm_workspace_bytes(mesh, layout)
                 self._ws = torch.empty(nbytes, dtype=torch.uint8, device=f"cuda:{device}")
                 B.lfm_bind_workspace(self.ctx, self._ws.data_ptr(), nbytes, layout)
-            B.lfm_upload_mesh(self.ctx, mesh)
+            if mesh is not None:
+                B.lfm_upload_mesh(self.ctx, mesh)
+            elif box is not None:
+                B.lfm_upload_box(self.ctx, *box)
+            else:
+                B.lfm_upload_mesh_shared(self.ctx, share.ctx)
         except Exception:
             B.lfm_destroy(self.ctx)
             self.ctx = None
@@ -52,15 +82,40 @@ class Solver:
         s.configure(case)
         return s
 
+    @classmethod
+    def from_box_case(cls, case: lapcase.RawCase, **kw) -> "Solver":
+        """A naturally numbered box case with its mesh built on the device."""
+        assert case.perm is None
+        s = cls(box=(case.xs, case.ys, case.zs), **kw)
+        s.configure(case)
+        return s
+
+    @classmethod
+    def sharing(cls, src: "Solver", case: lapcase.RawCase, **kw) -> "Solver":
+        """A case on the mesh already uploaded by ``src``."""
+        s = cls(share=src, **kw)
+        s.configure(case)
+        return s
+
     def configure(self, case: lapcase.RawCase, field: bool = True):
         m = self.mesh
-        B.lfm_set_diffusivity(self.ctx, 0.0, m.DT_faces, m.DT_bfaces)
+        if m.DT_faces is None:
+            if not (case.DTx is None and case.DTy is None and case.DTz is None):
+                raise ValueError("per-face DT needs a host mesh (Solver(mesh=...))")
+            B.lfm_set_diffusivity(self.ctx, float(case.DT_uniform), None, None)
+        else:
+            B.lfm_set_diffusivity(self.ctx, 0.0, m.DT_faces, m.DT_bfaces)
         for p, (ptype, value) in enumerate(case.patches):
             B.lfm_set_patch(self.ctx, p, int(ptype), None, float(value))
         B.lfm_set_time_step(self.ctx, case.dt)
         B.lfm_set_solver(self.ctx, case.tol, case.rel_tol, case.max_iter, case.min_iter, case.precision)
         if field:
-            B.lfm_set_field(self.ctx, field_by_label(case, m))
+            if np.isscalar(case.T0):
+                B.lfm_fill_field(self.ctx, float(case.T0))
+            elif m.cell_of_label is None:
+                B.lfm_set_field(self.ctx, case.T0_natural())
+            else:
+                B.lfm_set_field(self.ctx, field_by_label(case, m))
 
     def set_solver(self, tol, rel_tol=0.0, max_iter=1000, min_iter=0, precision=B.LFM_FP64):
         B.lfm_set_solver(self.ctx, tol, rel_tol, max_iter, min_iter, precision)
@@ -108,6 +163,7 @@ class Solver:
             B.lfm_destroy(self.ctx)
             self.ctx = None
         self._ws = None
+        self._share = None
 
     def __enter__(self):
         return self
