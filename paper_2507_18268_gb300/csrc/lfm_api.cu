@@ -555,6 +555,8 @@ int lfm_upload_mesh(lfm_ctx* c, const lfm_mesh* m) {
     if (has32) CK(c, cudaMemsetAsync(c->ws + Y.slot_coef32, 0, sizeof(float) * WN, c->stream));
   }
   CK(c, cudaMemsetAsync(c->ws + Y.DT, 0, sizeof(double) * (F > 0 ? F : 1), c->stream));
+  c->cs.DT_is_uniform = 1;
+  c->cs.DT_uniform = 0.0;
   CK(c, cudaMemsetAsync(c->ws + Y.x, 0, sizeof(double) * N, c->stream));
   CK(c, cudaStreamSynchronize(c->stream));
   c->dt = 1.0;
@@ -663,6 +665,8 @@ int lfm_upload_box(lfm_ctx* c, int32_t nx, int32_t ny, int32_t nz, const double*
     if (has32) CK(c, cudaMemsetAsync(c->ws + Y.slot_coef32, 0, sizeof(float) * WN, c->stream));
   }
   CK(c, cudaMemsetAsync(c->ws + Y.DT, 0, sizeof(double) * (F > 0 ? F : 1), c->stream));
+  c->cs.DT_is_uniform = 1;
+  c->cs.DT_uniform = 0.0;
   CK(c, cudaMemsetAsync(c->ws + Y.x, 0, sizeof(double) * N, c->stream));
   CK(c, cudaStreamSynchronize(c->stream));
   c->dt = 1.0;
@@ -733,6 +737,8 @@ int lfm_upload_mesh_shared(lfm_ctx* c, lfm_ctx* src) {
     if (has32) CK(c, cudaMemsetAsync(c->ws + Y.slot_coef32, 0, sizeof(float) * WN, c->stream));
   }
   CK(c, cudaMemsetAsync(c->ws + Y.DT, 0, sizeof(double) * (F > 0 ? F : 1), c->stream));
+  c->cs.DT_is_uniform = 1;
+  c->cs.DT_uniform = 0.0;
   CK(c, cudaMemsetAsync(c->ws + Y.x, 0, sizeof(double) * N, c->stream));
   CK(c, cudaStreamSynchronize(c->stream));
   c->dt = 1.0;
@@ -763,8 +769,11 @@ int lfm_set_diffusivity(lfm_ctx* c, double uniform, const double* DT_faces, cons
   DeviceGuard g(c->device);
   if (DT_faces) {
     if ((rc = h2d(c, c->lay.DT, DT_faces, c->F))) return rc;
+    c->cs.DT_is_uniform = 0;
   } else {
     CK(c, launch_fill(const_cast<double*>(c->cs.DT), c->F, uniform, c->stream));
+    c->cs.DT_is_uniform = 1;
+    c->cs.DT_uniform = uniform;
   }
   if (DT_bfaces) {
     if ((rc = h2d(c, c->lay.bDT, DT_bfaces, c->NB))) return rc;

@@ -54,6 +54,8 @@ struct CaseDev {
   const double* magSf;       // [F]
   const double* delta;       // [F]
   const double* DT;          // [F]
+  double DT_uniform;         // the value of every DT[f] when DT_is_uniform
+  int32_t DT_is_uniform;
   const double* bmagSf;      // [NB]
   const double* bdelta;      // [NB]
   const double* bDT;         // [NB]

@@ -13,8 +13,10 @@
 // keeps a dozen independent memory requests in flight.
 //
 // FP64 step (phases separated by team barriers):
-//   A  assembly        per slot g = DT |Sf| deltaCoeff; diag, upper (LDU), slot copy,
-//                      source, rD = 1/diag; sum x for xRef
+//   A  assembly        per slot g = DT |Sf| deltaCoeff; diag, the per-slot off-diagonals
+//                      (each face's coefficient at both of its cells; the face-indexed
+//                      LDU `upper` is written only for matrix read-back), source,
+//                      rD = 1/diag, row sums; sum x for xRef
 //   I  initial state   A x, r = b - A x, row sums -> normFactor, sum|r|, w = rD r, rho;
 //                      p = w (first search direction)
 //   loop (diagonal-preconditioned CG, convergence on sum|r| / normFactor):
@@ -92,7 +94,7 @@ struct Acc2f {
 // have smaller owners, so they precede the cell's own faces in upper-triangular order),
 // then the boundary faces, then V/dt; every product and sum is rounded separately (no FMA).
 template <int W, bool kMixed>
-__device__ __forceinline__ double assemble_row(const CaseDev& cs, int c) {
+__device__ __forceinline__ double assemble_row(const CaseDev& cs, int c, bool write_upper) {
   const size_t N = (size_t)cs.N;
   const int ns = nslots<W>(cs);
   double d = 0.0, s = 0.0;
@@ -102,10 +104,12 @@ __device__ __forceinline__ double assemble_row(const CaseDev& cs, int c) {
     const size_t at = (size_t)k * N + c;
     const int f = __ldg(cs.slot_face + at);
     if (f >= 0) {
-      const double g = __dmul_rn(__dmul_rn(__ldg(cs.DT + f), __ldg(cs.magSf + f)), __ldg(cs.delta + f));
+      const double DTf = cs.DT_is_uniform ? cs.DT_uniform : __ldg(cs.DT + f);
+      const double g = __dmul_rn(__dmul_rn(DTf, __ldg(cs.magSf + f)), __ldg(cs.delta + f));
       cs.slot_coef[at] = -g;
       if (kMixed) cs.slot_coef32[at] = (float)(-g);
-      if (__ldg(cs.slot_other + at) > c) cs.upper[f] = -g;
+      // the face-indexed LDU copy, written by the face's owner, only when asked for
+      if (write_upper && __ldg(cs.slot_other + at) > c) cs.upper[f] = -g;
       d = __dadd_rn(d, g);
     }
   }
@@ -290,7 +294,7 @@ __device__ void run_steps_f64(const CaseDev& cs, const Team& tm, int n_steps, in
   for (int step = 0; step < n_steps; ++step) {
     // ---- A: assembly ---------------------------------------------------------------------
     double v[1] = {0.0};
-    for (int c = c0 + tid; c < c1; c += B) v[0] += assemble_row<W, false>(cs, c);
+    for (int c = c0 + tid; c < c1; c += B) v[0] += assemble_row<W, false>(cs, c, mode == kModeAssembleOnly);
     if (!team_allreduce<1>(tm, v, sh)) return;
     if (mode == kModeAssembleOnly) return;
     // ---- I: initial residual, normFactor, first direction -----------------------------
@@ -425,7 +429,7 @@ __device__ void run_steps_mixed(const CaseDev& cs, const Team& tm, int n_steps, 
 
   for (int step = 0; step < n_steps; ++step) {
     double v[1] = {0.0};
-    for (int c = c0 + tid; c < c1; c += B) v[0] += assemble_row<W, true>(cs, c);
+    for (int c = c0 + tid; c < c1; c += B) v[0] += assemble_row<W, true>(cs, c, mode == kModeAssembleOnly);
     if (!team_allreduce<1>(tm, v, sh)) return;
     if (mode == kModeAssembleOnly) return;
     const double xRef = v[0] / (double)cs.N;
