@@ -263,6 +263,7 @@ def main_ours(args, world, rank, local):
     clk = clocks.stop() if rank == 0 else None
     iters = sum(x["iters"] for x in st)
     assert all(x["converged"] for x in st), "FP64 step did not converge"
+    phases = {k: v / K for k, v in s64.phase_times().items()}
     secs_max = reduce_max(secs, world)
     cell_iters_all = reduce_sum(float(N) * iters, world)
     value = cell_iters_all / secs_max
@@ -281,6 +282,7 @@ def main_ours(args, world, rank, local):
         msecs, mst = time_device_resident(smx, B, torch, stream, K)
         barrier(world)
         miters = sum(x["iters"] for x in mst)
+        mphases = {k: v / K for k, v in smx.phase_times().items()}
         assert all(x["converged"] for x in mst), "mixed step did not converge"
         msecs_max = reduce_max(msecs, world)
         mvalue = reduce_sum(float(N) * miters, world) / msecs_max
@@ -291,6 +293,7 @@ def main_ours(args, world, rank, local):
                  "iters_per_step": miters / K, "sweeps_per_step": sum(x["sweeps"] for x in mst) / K,
                  "speedup_vs_fp64_cell_steps": (secs_max / msecs_max),
                  "max_rel_diff_vs_fp64": float(np.max(np.abs(Tm - T64) / np.abs(T64))),
+                 "phases_ms_per_step": mphases,
                  "roofline": {"bound": "hbm", "achieved": malg / msecs / 1e9, "peak": hbm_peak, "unit": "GB/s",
                               "frac": malg / msecs / 1e9 / hbm_peak,
                               "traffic": (mratio * malg / K) if mratio else None,
@@ -345,6 +348,9 @@ def main_ours(args, world, rank, local):
                    "launch": {"ctas": launch[0], "threads": launch[1]}},
         "iters_per_step": iters / K,
         "cell_steps_per_s": float(N) * K * world / secs_max,
+        "phases_ms_per_step": phases,
+        "assembly_ms_per_step": phases["assembly"],
+        "solver_ms_per_step": sum(v for k, v in phases.items() if k != "assembly"),
         "roofline": {"bound": "hbm", "achieved": achieved_gbs, "peak": hbm_peak, "unit": "GB/s",
                      "frac": achieved_gbs / hbm_peak, "traffic": (ratio * alg / K) if ratio else None,
                      "peak_kind": peak_kind, "kernel": "step_kernel_f64",

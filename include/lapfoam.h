@@ -223,6 +223,13 @@ int lfm_field_device_ptr(lfm_ctx *ctx, double **T_dev);
  * source[n_cells]) to host memory, running only the assembly. Diagnostic / test use. */
 int lfm_get_matrix(lfm_ctx *ctx, double *diag, double *upper, double *source);
 
+/* Device time of the last advance by phase kind, in milliseconds (ms[8]): 0 assembly,
+ * 1 initial residual / normFactor (mixed: FP64 true residuals), 2 search-direction update,
+ * 3 matrix-vector product and p.Ap, 4 solution/residual update and dots, 5 (mixed) FP64
+ * correction, 6-7 unused. Measured by one CTA between barrier exits, so each phase
+ * includes its barrier wait; the sum is the kernel's wall time. */
+int lfm_get_phase_times(lfm_ctx *ctx, double *ms);
+
 /* Launch configuration chosen by the tuner for this context: CTAs and threads per CTA. */
 int lfm_get_launch(lfm_ctx *ctx, int32_t *ctas, int32_t *threads);
 

@@ -91,6 +91,7 @@ _SIGS = {
     "lfm_field_device_ptr": ([_ctx_p, POINTER(c_void_p)], c_int),
     "lfm_get_matrix": ([_ctx_p, POINTER(c_double), POINTER(c_double), POINTER(c_double)], c_int),
     "lfm_get_launch": ([_ctx_p, POINTER(c_int32), POINTER(c_int32)], c_int),
+    "lfm_get_phase_times": ([_ctx_p, POINTER(c_double)], c_int),
     "lfm_set_launch": ([_ctx_p, c_int32, c_int32], c_int),
     "lfm_set_barrier_timeout": ([_ctx_p, c_uint64], c_int),
     "lfm_debug_skip_arrival": ([_ctx_p, c_int32], c_int),
@@ -360,6 +361,15 @@ def lfm_get_matrix(ctx, n_cells: int, n_faces: int):
     d, u, s = np.empty(n_cells), np.empty(max(n_faces, 1)), np.empty(n_cells)
     _check(load().lfm_get_matrix(ctx, _ptr(d, c_double), _ptr(u, c_double), _ptr(s, c_double)), ctx)
     return d, u[:n_faces], s
+
+
+PHASES = ("assembly", "initial_residual", "p_update", "amul_dot", "update_dots", "fp64_correction")
+
+
+def lfm_get_phase_times(ctx) -> dict:
+    ms = (c_double * 8)()
+    _check(load().lfm_get_phase_times(ctx, ms), ctx)
+    return {name: ms[i] for i, name in enumerate(PHASES)}
 
 
 def lfm_get_launch(ctx):

@@ -36,7 +36,7 @@ struct Layout {
   size_t sync, partials, stats;
   size_t slot_other, slot_face, b_start, b_face, bcell, btype;
   size_t V, magSf, delta, DT, bmagSf, bdelta, bDT, bval;
-  size_t diag, upper, slot_coef, src, rD, sumA, x, r, w, p, q, Tb;
+  size_t diag, upper, slot_coef, src, rD, sumA, vdt, x, r, w, p, q, Tb;
   size_t diag32, slot_coef32, rD32, dx32, r32, w32, p32, q32;
   size_t total;
 };
@@ -79,6 +79,7 @@ Layout make_layout(int64_t N, int64_t F, int64_t NB, int64_t W, int kind, bool s
   L.src = take(8 * N);
   L.rD = take(8 * N);
   L.sumA = take(8 * N);
+  L.vdt = take(8 * N);
   L.x = take(8 * N);
   L.Tb = take(8 * NB);
   L.r = L.w = L.p = L.q = 0;
@@ -153,6 +154,8 @@ struct lfm_ctx {
   // async state
   lfm_step_stats* h_stats = nullptr;  // pinned, kStatsCap records
   int32_t* h_status = nullptr;        // pinned
+  unsigned long long* h_phase = nullptr;  // pinned, kPhases
+  double phase_ms[kPhases] = {};      // per phase kind, summed over the last advance
   cudaEvent_t done = nullptr;
   int pending_steps = 0;
   int pending_remaining = 0;
@@ -346,6 +349,7 @@ void bind_pointers(lfm_ctx* c) {
   cs.src = reinterpret_cast<double*>(b + L.src);
   cs.rD = reinterpret_cast<double*>(b + L.rD);
   cs.sumA = reinterpret_cast<double*>(b + L.sumA);
+  cs.vdt = reinterpret_cast<const double*>(b + L.vdt);
   cs.x = reinterpret_cast<double*>(b + L.x);
   const bool d = c->has64, m = c->has32;
   cs.r = d ? reinterpret_cast<double*>(b + L.r) : nullptr;
@@ -360,6 +364,15 @@ void bind_pointers(lfm_ctx* c) {
   cs.w32 = m ? reinterpret_cast<float*>(b + L.w32) : nullptr;
   cs.p32 = m ? reinterpret_cast<float*>(b + L.p32) : nullptr;
   cs.q32 = m ? reinterpret_cast<float*>(b + L.q32) : nullptr;
+}
+
+// V/dt per cell, recomputed when dt or the mesh changes (the assembly reads it every step).
+bool ctx_batch_pending(const lfm_ctx* c);
+
+int refresh_vdt(lfm_ctx* c) {
+  CK(c, launch_vdt(c->cs.V, c->dt, const_cast<double*>(c->cs.vdt), c->N, c->stream));
+  CK(c, cudaStreamSynchronize(c->stream));
+  return LFM_OK;
 }
 
 int need_uploaded(lfm_ctx* c) {
@@ -383,6 +396,8 @@ int enqueue_chunk(lfm_ctx* c, int steps, int mode) {
     CK(c, cudaMemcpyAsync(c->h_stats, c->cs.stats, sizeof(lfm_step_stats) * steps, cudaMemcpyDeviceToHost,
                           c->stream));
   CK(c, cudaMemcpyAsync(c->h_status, &c->cs.sync->status, sizeof(int32_t), cudaMemcpyDeviceToHost, c->stream));
+  CK(c, cudaMemcpyAsync(c->h_phase, c->cs.sync->phase_ns, sizeof(unsigned long long) * kPhases,
+                        cudaMemcpyDeviceToHost, c->stream));
   CK(c, cudaEventRecord(c->done, c->stream));
   return LFM_OK;
 }
@@ -391,6 +406,7 @@ int enqueue_chunk(lfm_ctx* c, int steps, int mode) {
 int collect_chunk(lfm_ctx* c, int steps) {
   CK(c, cudaEventSynchronize(c->done));
   for (int i = 0; i < steps; ++i) c->stats_acc.push_back(c->h_stats[i]);
+  for (int k = 0; k < kPhases; ++k) c->phase_ms[k] += 1e-6 * (double)c->h_phase[k];
   int32_t st = *c->h_status;
   if (st == LFM_ETIMEOUT) return fail(c, LFM_ETIMEOUT, "a device barrier wait ran out (kernel stopped)");
   if (st == LFM_ESINGULAR) return fail(c, LFM_ESINGULAR, "PCG met a singular search direction");
@@ -456,6 +472,7 @@ int lfm_create(lfm_ctx** out, int device, void* cuda_stream) {
   DeviceGuard g(device);
   if (cudaMallocHost(&c->h_stats, sizeof(lfm_step_stats) * kStatsCap) != cudaSuccess ||
       cudaMallocHost(&c->h_status, sizeof(int32_t)) != cudaSuccess ||
+      cudaMallocHost(&c->h_phase, sizeof(unsigned long long) * kPhases) != cudaSuccess ||
       cudaEventCreateWithFlags(&c->done, cudaEventDisableTiming) != cudaSuccess) {
     lfm_destroy(c);
     return fail_free(LFM_ECUDA, "lfm_create: host staging or event allocation failed");
@@ -561,6 +578,7 @@ int lfm_upload_mesh(lfm_ctx* c, const lfm_mesh* m) {
   CK(c, cudaStreamSynchronize(c->stream));
   c->dt = 1.0;
   c->opts = lfm_solver_opts{1e-6, 0.0, 1000, 0, has64 ? LFM_FP64 : LFM_MIXED};
+  if ((rc = refresh_vdt(c))) return rc;
   c->uploaded = true;
   c->ctas = c->threads = 0;
   return choose_launch(c);
@@ -671,6 +689,7 @@ int lfm_upload_box(lfm_ctx* c, int32_t nx, int32_t ny, int32_t nz, const double*
   CK(c, cudaStreamSynchronize(c->stream));
   c->dt = 1.0;
   c->opts = lfm_solver_opts{1e-6, 0.0, 1000, 0, has64 ? LFM_FP64 : LFM_MIXED};
+  if ((rc = refresh_vdt(c))) return rc;
   c->uploaded = true;
   c->ctas = c->threads = 0;
   return choose_launch(c);
@@ -743,6 +762,7 @@ int lfm_upload_mesh_shared(lfm_ctx* c, lfm_ctx* src) {
   CK(c, cudaStreamSynchronize(c->stream));
   c->dt = 1.0;
   c->opts = lfm_solver_opts{1e-6, 0.0, 1000, 0, has64 ? LFM_FP64 : LFM_MIXED};
+  if ((rc = refresh_vdt(c))) return rc;
   c->uploaded = true;
   c->ctas = c->threads = 0;
   return choose_launch(c);
@@ -809,8 +829,10 @@ int lfm_set_time_step(lfm_ctx* c, double dt) {
   int rc = need_uploaded(c);
   if (rc) return rc;
   if (!(std::isfinite(dt) && dt > 0)) return fail(c, LFM_EINVAL, "dt must be finite and > 0");
+  if (c->pending_steps > 0 || ctx_batch_pending(c)) return fail(c, LFM_ESTATE, "an advance is pending");
   c->dt = dt;
-  return LFM_OK;
+  DeviceGuard g(c->device);
+  return refresh_vdt(c);
 }
 
 int lfm_set_solver(lfm_ctx* c, const lfm_solver_opts* o) {
@@ -857,6 +879,7 @@ int lfm_advance_async(lfm_ctx* c, int32_t n_steps) {
   if (n_steps == 0) return LFM_OK;
   DeviceGuard g(c->device);
   c->stats_acc.clear();
+  for (int k = 0; k < kPhases; ++k) c->phase_ms[k] = 0.0;
   const int first = n_steps < kStatsCap ? n_steps : kStatsCap;
   if ((rc = enqueue_chunk(c, first, kModeSteps))) return rc;
   c->pending_steps = first;
@@ -949,6 +972,14 @@ int lfm_get_matrix(lfm_ctx* c, double* diag, double* upper, double* source) {
   return LFM_OK;
 }
 
+int lfm_get_phase_times(lfm_ctx* c, double* ms) {
+  int rc = need_uploaded(c);
+  if (rc) return rc;
+  if (!ms) return fail(c, LFM_EINVAL, "ms is NULL");
+  for (int k = 0; k < kPhases; ++k) ms[k] = c->phase_ms[k];
+  return LFM_OK;
+}
+
 int lfm_get_launch(lfm_ctx* c, int32_t* ctas, int32_t* threads) {
   int rc = need_uploaded(c);
   if (rc) return rc;
@@ -993,6 +1024,7 @@ int lfm_destroy(lfm_ctx* c) {
     if (c->ws_owned && c->ws) cudaFree(c->ws);
     if (c->h_stats) cudaFreeHost(c->h_stats);
     if (c->h_status) cudaFreeHost(c->h_status);
+    if (c->h_phase) cudaFreeHost(c->h_phase);
     if (c->done) cudaEventDestroy(c->done);
   }
   delete c;
@@ -1052,6 +1084,12 @@ struct lfm_batch {
 namespace {
 
 thread_local std::string g_batch_error;
+
+}  // namespace
+
+namespace {
+bool ctx_batch_pending(const lfm_ctx* c) { return c->batch && c->batch->pending; }
+
 
 int bfail(lfm_batch* b, int code, const char* fmt, ...) {
   char buf[512];

@@ -29,7 +29,12 @@ struct alignas(128) SyncWords {
   double pad2[16 - kMaxSums];
   int32_t status;                    // first error of the launch (0 = none)
   int32_t pad3[31];
+  unsigned long long phase_ns[8];    // time per phase kind, accumulated by the team's rank 0
+  unsigned long long pad4[8];
 };
+
+// Phase kinds of the step (indices of SyncWords::phase_ns).
+enum Phase { kPhAssembly = 0, kPhInit = 1, kPhP = 2, kPhM = 3, kPhU = 4, kPhCorrect = 5, kPhases = 8 };
 
 // Device view of one case: every pointer is device memory of the case's workspace.
 struct CaseDev {
@@ -51,6 +56,7 @@ struct CaseDev {
 
   // geometry and properties
   const double* V;           // [N]
+  const double* vdt;         // [N]  V/dt, recomputed whenever dt or the mesh changes
   const double* magSf;       // [F]
   const double* delta;       // [F]
   const double* DT;          // [F]
@@ -143,5 +149,6 @@ cudaError_t launch_batch_collect(const CaseDev* cases, int n_cases, const int32_
                                  int32_t* iters, cudaStream_t s);
 cudaError_t launch_batch_steps(const BatchLaunch& bl, int n_steps, cudaStream_t s);
 cudaError_t launch_fill(double* a, size_t n, double v, cudaStream_t stream);
+cudaError_t launch_vdt(const double* V, double dt, double* vdt, int n, cudaStream_t stream);
 
 }  // namespace lfm

@@ -124,7 +124,7 @@ __device__ __forceinline__ double assemble_row(const CaseDev& cs, int c, bool wr
       gsum = __dadd_rn(gsum, gb);
     }
   }
-  const double vdt = __ldg(cs.V + c) / cs.dt;
+  const double vdt = cs.vdt[c];  // V/dt, hoisted out of the time loop (same IEEE quotient)
   const double xc = cs.x[c];
   d = __dadd_rn(d, vdt);
   s = __dadd_rn(s, __dmul_rn(vdt, xc));
@@ -259,6 +259,25 @@ __device__ __forceinline__ float row_f32(const CaseDev& cs, int c, const float* 
   return acc;
 }
 
+// Wall time per phase kind, measured by the team's rank-0 thread between barrier exits
+// (so each phase's share includes its barrier wait: the team's critical path).
+struct PhaseClock {
+  bool on;
+  unsigned long long t;
+  unsigned long long* acc;
+  __device__ __forceinline__ PhaseClock(const CaseDev& cs, const Team& tm)
+      : on(tm.rank == 0 && threadIdx.x == 0), t(0), acc(cs.sync->phase_ns) {
+    if (on) t = global_timer_ns();
+  }
+  __device__ __forceinline__ void lap(int phase) {
+    if (on) {
+      const unsigned long long now = global_timer_ns();
+      acc[phase] += now - t;
+      t = now;
+    }
+  }
+};
+
 __device__ __forceinline__ void write_stats(const CaseDev& cs, const Team& tm, int slot, int iters,
                                             int conv, int sweeps, int status, double init_res,
                                             double final_res, double nf) {
@@ -291,11 +310,13 @@ __device__ void run_steps_f64(const CaseDev& cs, const Team& tm, int n_steps, in
   double* __restrict__ q = cs.q;
   const double* __restrict__ rD = cs.rD;
 
+  PhaseClock clk(cs, tm);
   for (int step = 0; step < n_steps; ++step) {
     // ---- A: assembly ---------------------------------------------------------------------
     double v[1] = {0.0};
     for (int c = c0 + tid; c < c1; c += B) v[0] += assemble_row<W, false>(cs, c, mode == kModeAssembleOnly);
     if (!team_allreduce<1>(tm, v, sh)) return;
+    clk.lap(kPhAssembly);
     if (mode == kModeAssembleOnly) return;
     // ---- I: initial residual, normFactor, first direction -----------------------------
     const double xRef = v[0] / (double)cs.N;
@@ -313,6 +334,7 @@ __device__ void run_steps_f64(const CaseDev& cs, const Team& tm, int n_steps, in
       p[c] = wc;
     }
     if (!team_allreduce<3>(tm, u, sh)) return;
+    clk.lap(kPhInit);
     const double nf = u[0] + kSmall;
     const double init_res = u[1] / nf;
     double res = init_res, rho = u[2], beta = 0.0;
@@ -330,6 +352,7 @@ __device__ void run_steps_f64(const CaseDev& cs, const Team& tm, int n_steps, in
           }
           if (c < c1) p[c] = fma(beta, p[c], w[c]);
           if (!team_barrier(tm, sh)) return;
+          clk.lap(kPhP);
         }
         // ---- M: q = A p, sigma = p.q ----------------------------------------------
         double s1[1] = {0.0};
@@ -351,6 +374,7 @@ __device__ void run_steps_f64(const CaseDev& cs, const Team& tm, int n_steps, in
           }
         }
         if (!team_allreduce<1>(tm, s1, sh)) return;
+        clk.lap(kPhM);
         const double sigma = s1[0];
         if (fabs(sigma) / nf < kVSmall) {
           status = LFM_ESINGULAR;
@@ -389,6 +413,7 @@ __device__ void run_steps_f64(const CaseDev& cs, const Team& tm, int n_steps, in
           }
         }
         if (!team_allreduce<2>(tm, s2, sh)) return;
+        clk.lap(kPhU);
         res = s2[0] / nf;
         beta = s2[1] / rho;
         rho = s2[1];
@@ -427,10 +452,12 @@ __device__ void run_steps_mixed(const CaseDev& cs, const Team& tm, int n_steps, 
   float* __restrict__ q = cs.q32;
   const float* __restrict__ rD = cs.rD32;
 
+  PhaseClock clk(cs, tm);
   for (int step = 0; step < n_steps; ++step) {
     double v[1] = {0.0};
     for (int c = c0 + tid; c < c1; c += B) v[0] += assemble_row<W, true>(cs, c, mode == kModeAssembleOnly);
     if (!team_allreduce<1>(tm, v, sh)) return;
+    clk.lap(kPhAssembly);
     if (mode == kModeAssembleOnly) return;
     const double xRef = v[0] / (double)cs.N;
 
@@ -460,6 +487,7 @@ __device__ void run_steps_mixed(const CaseDev& cs, const Team& tm, int n_steps, 
       }
       u[2] = rho_acc.value();
       if (!team_allreduce<3>(tm, u, sh)) return;
+      clk.lap(kPhInit);
       if (sweeps == 0) {
         nf = u[0] + kSmall;
         init_res = u[1] / nf;
@@ -488,6 +516,7 @@ __device__ void run_steps_mixed(const CaseDev& cs, const Team& tm, int n_steps, 
           }
           if (c < c1) p[c] = fmaf(b32, p[c], w[c]);
           if (!team_barrier(tm, sh)) return;
+          clk.lap(kPhP);
         }
         double s1[1];
         {
@@ -510,6 +539,7 @@ __device__ void run_steps_mixed(const CaseDev& cs, const Team& tm, int n_steps, 
           s1[0] = sig.value();
         }
         if (!team_allreduce<1>(tm, s1, sh)) return;
+        clk.lap(kPhM);
         const double sigma = s1[0];
         if (fabs(sigma) / nf < kVSmall) {
           status = LFM_ESINGULAR;
@@ -550,6 +580,7 @@ __device__ void run_steps_mixed(const CaseDev& cs, const Team& tm, int n_steps, 
           s2[1] = rho_n.value();
         }
         if (!team_allreduce<2>(tm, s2, sh)) return;
+        clk.lap(kPhU);
         const double inner_res = s2[0] / nf;
         beta = s2[1] / rho;
         rho = s2[1];
@@ -566,6 +597,7 @@ __device__ void run_steps_mixed(const CaseDev& cs, const Team& tm, int n_steps, 
       // ---- x += dx (FP64) ------------------------------------------------------------
       for (int c = c0 + tid; c < c1; c += B) x[c] += (double)dx[c];
       if (!team_barrier(tm, sh)) return;
+      clk.lap(kPhCorrect);
       ++sweeps;
     }
     const bool conv = converged(res, init_res, cs.tol, cs.rel_tol);

@@ -31,6 +31,11 @@ __global__ void boundary_values_kernel(CaseDev cs, double* Tb) {
   if (b < cs.NB) Tb[b] = cs.btype[b] == LFM_FIXED_VALUE ? cs.bval[b] : cs.x[cs.bcell[b]];
 }
 
+__global__ void vdt_kernel(const double* __restrict__ V, double dt, double* __restrict__ vdt, int n) {
+  const int c = blockIdx.x * blockDim.x + threadIdx.x;
+  if (c < n) vdt[c] = V[c] / dt;
+}
+
 __global__ void fill_kernel(double* a, size_t n, double v) {
   size_t i = blockIdx.x * (size_t)blockDim.x + threadIdx.x;
   const size_t stride = (size_t)gridDim.x * blockDim.x;
@@ -78,6 +83,12 @@ cudaError_t launch_steps(const CaseDev& cs, const Launch& L, int n_steps, int mo
 cudaError_t launch_boundary_values(const CaseDev& cs, double* Tb, cudaStream_t stream) {
   if (cs.NB == 0) return cudaSuccess;
   boundary_values_kernel<<<(cs.NB + 255) / 256, 256, 0, stream>>>(cs, Tb);
+  return cudaGetLastError();
+}
+
+cudaError_t launch_vdt(const double* V, double dt, double* vdt, int n, cudaStream_t stream) {
+  if (n <= 0) return cudaSuccess;
+  vdt_kernel<<<(n + 255) / 256, 256, 0, stream>>>(V, dt, vdt, n);
   return cudaGetLastError();
 }
 

@@ -155,6 +155,10 @@ class Solver:
     def launch(self):
         return B.lfm_get_launch(self.ctx)
 
+    def phase_times(self) -> dict:
+        """Device milliseconds per phase kind of the last advance."""
+        return B.lfm_get_phase_times(self.ctx)
+
     def set_launch(self, ctas: int, threads: int):
         B.lfm_set_launch(self.ctx, ctas, threads)
 
