@@ -118,12 +118,14 @@ int lfm_box_counts(int32_t nx, int32_t ny, int32_t nz, int32_t *n_cells, int32_t
                    int32_t *n_bfaces, int32_t *slot_width);
 
 /* Host replica of the device box builder (same per-cell routine): fills the slot-major
- * face-to-cell arrays (slot_other, slot_face [W*N]), V [N], magSf, deltaCoeffs [F],
+ * face-to-cell arrays (slot_other, slot_face [W*N]; slot_mate [W*N]: for an owned face
+ * the slot index it occupies in its neighbour's row, -1 otherwise), V [N], magSf,
+ * deltaCoeffs [F],
  * the cell-side boundary lists (b_start [N+1], b_face [NB]) and bface_cell, bmagSf,
  * bdeltaCoeffs [NB]. For validation of the closed forms; no device is touched. */
 int lfm_box_layout(int32_t nx, int32_t ny, int32_t nz, const double *xs, const double *ys,
-                   const double *zs, int32_t *slot_other, int32_t *slot_face, double *V,
-                   double *magSf, double *deltaCoeffs, int32_t *b_start, int32_t *b_face,
+                   const double *zs, int32_t *slot_other, int32_t *slot_face, int8_t *slot_mate,
+                   double *V, double *magSf, double *deltaCoeffs, int32_t *b_start, int32_t *b_face,
                    int32_t *bface_cell, double *bmagSf, double *bdeltaCoeffs);
 
 /* ---- single-case context ----------------------------------------------------------- */

@@ -34,7 +34,7 @@ size_t align_up(size_t v, size_t a) { return (v + a - 1) / a * a; }
 // Byte layout of a case's workspace. Offsets are relative to the workspace base.
 struct Layout {
   size_t sync, partials, stats;
-  size_t slot_other, slot_face, b_start, b_face, bcell, btype;
+  size_t slot_other, slot_face, slot_mate, b_start, b_face, bcell, btype;
   size_t V, magSf, delta, DT, bmagSf, bdelta, bDT, bval;
   size_t diag, upper, slot_coef, src, rD, sumA, vdt, x, r, w, p, q, Tb;
   size_t diag32, slot_coef32, rD32, dx32, r32, w32, p32, q32;
@@ -60,6 +60,7 @@ Layout make_layout(int64_t N, int64_t F, int64_t NB, int64_t W, int kind, bool s
   if (!shared_mesh) {
     L.slot_other = take(4 * W * N);
     L.slot_face = take(4 * W * N);
+    L.slot_mate = take(W * N);
     L.b_start = take(4 * (N + 1));
     L.b_face = take(4 * NB);
     L.bcell = take(4 * NB);
@@ -270,11 +271,15 @@ int h2d(lfm_ctx* c, size_t off, const T* src, size_t n) {
   return LFM_OK;
 }
 
+// Default launch: one team of co-resident CTAs, about 4096 cells per CTA at least; 512
+// threads per CTA for FP64, 1024 for the mixed form (its FP32 passes need more threads in
+// flight per SM), chosen from launch-shape sweeps on graded200.
 int choose_launch(lfm_ctx* c) {
-  const int threads = 512;
+  const int threads = c->opts.precision == LFM_MIXED ? 1024 : 512;
   int maxc = max_coresident_ctas(c->opts.precision, threads, c->W, c->device);
   if (maxc <= 0) return fail(c, LFM_ECUDA, "cannot size the cooperative launch");
   int64_t want = ((int64_t)c->N + 4095) / 4096;
+  if (threads == 1024) want = ((int64_t)c->N + 8191) / 8192;
   if (want < 1) want = 1;
   if (want > maxc) want = maxc;
   c->tuned_ctas = (int)want;
@@ -323,6 +328,7 @@ void bind_pointers(lfm_ctx* c) {
     const CaseDev& m = c->mesh_src->cs;
     cs.slot_other = m.slot_other;
     cs.slot_face = m.slot_face;
+    cs.slot_mate = m.slot_mate;
     cs.b_start = m.b_start;
     cs.b_face = m.b_face;
     cs.bcell = m.bcell;
@@ -334,6 +340,7 @@ void bind_pointers(lfm_ctx* c) {
   } else {
     cs.slot_other = reinterpret_cast<const int32_t*>(b + L.slot_other);
     cs.slot_face = reinterpret_cast<const int32_t*>(b + L.slot_face);
+    cs.slot_mate = reinterpret_cast<const int8_t*>(b + L.slot_mate);
     cs.b_start = reinterpret_cast<const int32_t*>(b + L.b_start);
     cs.b_face = reinterpret_cast<const int32_t*>(b + L.b_face);
     cs.bcell = reinterpret_cast<const int32_t*>(b + L.bcell);
@@ -537,6 +544,7 @@ int lfm_upload_mesh(lfm_ctx* c, const lfm_mesh* m) {
   if (rc != LFM_OK) return fail(c, rc, "%s", g_last_error.c_str());
   // Slot-major copy of the face-to-cell lists: neighbour-side faces, owned faces, padding.
   std::vector<int32_t> slot_other((size_t)W * N), slot_face((size_t)W * N);
+  std::vector<int8_t> slot_mate((size_t)W * N, (int8_t)-1);
   for (int32_t cell = 0; cell < N; ++cell) {
     int k = 0;
     for (int32_t i = lo_start[cell]; i < lo_start[cell + 1]; ++i, ++k) {
@@ -552,6 +560,15 @@ int lfm_upload_mesh(lfm_ctx* c, const lfm_mesh* m) {
       slot_face[(size_t)k * N + cell] = -1;
     }
   }
+  // mate of an owned face: its position among the neighbour's neighbour-side faces
+  for (int32_t cell = 0; cell < N; ++cell) {
+    const int lo_n = lo_start[cell + 1] - lo_start[cell];
+    for (int32_t f = own_start[cell], k = lo_n; f < own_start[cell + 1]; ++f, ++k) {
+      const int32_t n = m->neighbour[f];
+      for (int32_t i = lo_start[n]; i < lo_start[n + 1]; ++i)
+        if (losort[i] == f) slot_mate[(size_t)k * N + cell] = (int8_t)(i - lo_start[n]);
+    }
+  }
   std::vector<int32_t> b_start(N + 1), b_face(NB > 0 ? NB : 1);
   bucket(N, NB, m->bface_cell, b_start.data(), b_face.data());
   std::vector<int32_t> btype(NB > 0 ? NB : 1, LFM_ZERO_GRADIENT);
@@ -560,6 +577,7 @@ int lfm_upload_mesh(lfm_ctx* c, const lfm_mesh* m) {
   const Layout& Y = c->lay;
   const size_t WN = (size_t)W * N;
   if ((rc = h2d(c, Y.slot_other, slot_other.data(), WN)) || (rc = h2d(c, Y.slot_face, slot_face.data(), WN)) ||
+      (rc = h2d(c, Y.slot_mate, slot_mate.data(), WN)) ||
       (rc = h2d(c, Y.b_start, b_start.data(), N + 1)) ||
       (rc = h2d(c, Y.b_face, b_face.data(), NB)) || (rc = h2d(c, Y.bcell, m->bface_cell, NB)) ||
       (rc = h2d(c, Y.btype, btype.data(), NB)) || (rc = h2d(c, Y.V, m->V, N)) ||
@@ -618,13 +636,16 @@ int lfm_box_counts(int32_t nx, int32_t ny, int32_t nz, int32_t* n_cells, int32_t
 }
 
 int lfm_box_layout(int32_t nx, int32_t ny, int32_t nz, const double* xs, const double* ys, const double* zs,
-                   int32_t* slot_other, int32_t* slot_face, double* V, double* magSf, double* delta,
+                   int32_t* slot_other, int32_t* slot_face, int8_t* slot_mate, double* V, double* magSf,
+                   double* delta,
                    int32_t* b_start, int32_t* b_face, int32_t* bcell, double* bmagSf, double* bdelta) {
   std::string why;
   if (check_box(nx, ny, nz, xs, ys, zs, why) != LFM_OK) return fail_free(LFM_EINVAL, "%s", why.c_str());
-  if (!slot_other || !slot_face || !V || !magSf || !delta || !b_start || !b_face || !bcell || !bmagSf || !bdelta)
+  if (!slot_other || !slot_face || !slot_mate || !V || !magSf || !delta || !b_start || !b_face || !bcell ||
+      !bmagSf || !bdelta)
     return fail_free(LFM_EINVAL, "output arrays missing");
-  box_layout_host(nx, ny, nz, box_slot_width(nx, ny, nz), xs, ys, zs, slot_other, slot_face, V, magSf, delta,
+  box_layout_host(nx, ny, nz, box_slot_width(nx, ny, nz), xs, ys, zs, slot_other, slot_face, slot_mate, V, magSf,
+                  delta,
                   b_start, b_face, bcell, bmagSf, bdelta);
   return LFM_OK;
 }

@@ -103,7 +103,13 @@ __device__ __forceinline__ void block_reduce(double* v, TeamShared& sh) {
 // thread. False: a wait ran out or another CTA failed; the caller must leave the kernel.
 template <int NS>
 __device__ bool team_allreduce(const Team& tm, double* v, TeamShared& sh) {
-  if constexpr (NS > 0) block_reduce<NS>(v, sh);
+  // Every thread's global writes of the phase must be ordered before thread 0 signals
+  // arrival: block_reduce synchronises the CTA itself; a barrier without sums needs its own.
+  if constexpr (NS > 0) {
+    block_reduce<NS>(v, sh);
+  } else {
+    __syncthreads();
+  }
   if (tm.size == 1) {
     __syncthreads();
     if constexpr (NS > 0) {

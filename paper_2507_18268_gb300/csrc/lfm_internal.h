@@ -50,6 +50,8 @@ struct CaseDev {
   int32_t W;
   const int32_t* slot_other; // [W*N] the other cell of the slot's face
   const int32_t* slot_face;  // [W*N] face id, -1 for padding
+  const int8_t* slot_mate;   // [W*N] for an owned face: the slot holding it in the neighbour's
+                             // row; -1 for neighbour-side faces and padding
   const int32_t* b_start;    // [N+1] boundary faces of c: b_face[b_start[c] ..)
   const int32_t* b_face;     // [NB]  boundary faces sorted by cell, ascending id per cell
   const int32_t* bcell;      // [NB]  cell of boundary face b
@@ -138,7 +140,8 @@ int box_slot_width(long long nx, long long ny, long long nz);
 cudaError_t launch_box(long long nx, long long ny, long long nz, int W, const double* xs, const double* ys,
                        const double* zs, const CaseDev& cs, cudaStream_t stream);
 void box_layout_host(long long nx, long long ny, long long nz, int W, const double* xs, const double* ys,
-                     const double* zs, int32_t* slot_other, int32_t* slot_face, double* V, double* magSf,
+                     const double* zs, int32_t* slot_other, int32_t* slot_face, int8_t* slot_mate,
+                     double* V, double* magSf,
                      double* delta, int32_t* b_start, int32_t* b_face, int32_t* bcell, double* bmagSf,
                      double* bdelta);
 

@@ -89,29 +89,45 @@ struct Acc2f {
   __device__ __forceinline__ double value() const { return (double)hi + (double)lo; }
 };
 
-// ---- assembly: one row of fvm::ddt(T) - fvm::laplacian(DT, T) -------------------------
-// The diagonal is summed in slot order, i.e. ascending face order (neighbour-side faces
-// have smaller owners, so they precede the cell's own faces in upper-triangular order),
-// then the boundary faces, then V/dt; every product and sum is rounded separately (no FMA).
+// ---- assembly of fvm::ddt(T) - fvm::laplacian(DT, T), two passes ---------------------
+// Pass 1 (per cell, its owned faces): g = (DT |Sf|) deltaCoeff, computed once per face and
+// stored as -g in the cell's slot and in the neighbour's matching slot (slot_mate).
+template <bool kMixed>
+__device__ __forceinline__ void assemble_faces(const CaseDev& cs, int c, int ns, bool write_upper) {
+  const size_t N = (size_t)cs.N;
+  for (int k = 0; k < ns; ++k) {
+    const size_t at = (size_t)k * N + c;
+    const int mate = __ldg(cs.slot_mate + at);
+    if (mate >= 0) {
+      const int f = __ldg(cs.slot_face + at);
+      const int n = __ldg(cs.slot_other + at);
+      const double DTf = cs.DT_is_uniform ? cs.DT_uniform : __ldg(cs.DT + f);
+      const double g = __dmul_rn(__dmul_rn(DTf, __ldg(cs.magSf + f)), __ldg(cs.delta + f));
+      const size_t at_n = (size_t)mate * N + n;
+      cs.slot_coef[at] = -g;
+      cs.slot_coef[at_n] = -g;
+      if (kMixed) {
+        cs.slot_coef32[at] = (float)(-g);
+        cs.slot_coef32[at_n] = (float)(-g);
+      }
+      if (write_upper) cs.upper[f] = -g;  // the face-indexed LDU copy, for read-back only
+    }
+  }
+}
+
+// Pass 2 (per cell): the diagonal summed in slot order, i.e. ascending face order
+// (neighbour-side faces have smaller owners, so they precede the cell's own faces in
+// upper-triangular order), then the boundary faces, then V/dt; every product and sum rounded
+// separately (no FMA); source, 1/diag and the row sum. Returns the cell's T.
 template <int W, bool kMixed>
-__device__ __forceinline__ double assemble_row(const CaseDev& cs, int c, bool write_upper) {
+__device__ __forceinline__ double assemble_diag(const CaseDev& cs, int c) {
   const size_t N = (size_t)cs.N;
   const int ns = nslots<W>(cs);
   double d = 0.0, s = 0.0;
 #pragma unroll
   for (int k = 0; k < (W > 0 ? W : kMaxSlots); ++k) {
     if (W == 0 && k >= ns) break;
-    const size_t at = (size_t)k * N + c;
-    const int f = __ldg(cs.slot_face + at);
-    if (f >= 0) {
-      const double DTf = cs.DT_is_uniform ? cs.DT_uniform : __ldg(cs.DT + f);
-      const double g = __dmul_rn(__dmul_rn(DTf, __ldg(cs.magSf + f)), __ldg(cs.delta + f));
-      cs.slot_coef[at] = -g;
-      if (kMixed) cs.slot_coef32[at] = (float)(-g);
-      // the face-indexed LDU copy, written by the face's owner, only when asked for
-      if (write_upper && __ldg(cs.slot_other + at) > c) cs.upper[f] = -g;
-      d = __dadd_rn(d, g);
-    }
+    d = __dadd_rn(d, -cs.slot_coef[(size_t)k * N + c]);  // padding slots hold 0
   }
   double gsum = 0.0;  // boundary conductance of the row
   const int b0 = __ldg(cs.b_start + c), b1 = __ldg(cs.b_start + c + 1);
@@ -128,7 +144,7 @@ __device__ __forceinline__ double assemble_row(const CaseDev& cs, int c, bool wr
   const double xc = cs.x[c];
   d = __dadd_rn(d, vdt);
   s = __dadd_rn(s, __dmul_rn(vdt, xc));
-  const double rd = 1.0 / d;
+  const double rd = __drcp_rn(d);  // IEEE round-to-nearest reciprocal, as 1.0 / d
   cs.diag[c] = d;
   cs.src[c] = s;
   cs.rD[c] = rd;
@@ -142,21 +158,18 @@ __device__ __forceinline__ double assemble_row(const CaseDev& cs, int c, bool wr
   return xc;
 }
 
-// ---- FP64 row of A v, products and sums rounded separately in slot order ---------------
-// Reproduces a serial face loop's rounding exactly.
-template <int W>
-__device__ __forceinline__ double row_exact(const CaseDev& cs, int c, const double* __restrict__ v,
-                                            double d, double vc) {
-  const size_t N = (size_t)cs.N;
+// Both passes for this CTA's cells, with the team barrier between them. v0 receives the
+// CTA threads' sum of T (for xRef); false when a barrier failed.
+template <int B, int W, bool kMixed>
+__device__ __forceinline__ bool assemble(const CaseDev& cs, const Team& tm, int c0, int c1, bool write_upper,
+                                         double& sum_x, TeamShared& sh) {
   const int ns = nslots<W>(cs);
-  double acc = __dmul_rn(d, vc);
-#pragma unroll
-  for (int k = 0; k < (W > 0 ? W : kMaxSlots); ++k) {
-    if (W == 0 && k >= ns) break;
-    const size_t at = (size_t)k * N + c;
-    acc = __dadd_rn(acc, __dmul_rn(cs.slot_coef[at], v[__ldg(cs.slot_other + at)]));
-  }
-  return acc;
+  for (int c = c0 + (int)threadIdx.x; c < c1; c += B) assemble_faces<kMixed>(cs, c, ns, write_upper);
+  if (!team_barrier(tm, sh)) return false;
+  double v = 0.0;
+  for (int c = c0 + (int)threadIdx.x; c < c1; c += B) v += assemble_diag<W, kMixed>(cs, c);
+  sum_x = v;
+  return true;
 }
 
 // ---- FP64 A v for two rows at once (FMA accumulation) ----------------------------------
@@ -314,7 +327,7 @@ __device__ void run_steps_f64(const CaseDev& cs, const Team& tm, int n_steps, in
   for (int step = 0; step < n_steps; ++step) {
     // ---- A: assembly ---------------------------------------------------------------------
     double v[1] = {0.0};
-    for (int c = c0 + tid; c < c1; c += B) v[0] += assemble_row<W, false>(cs, c, mode == kModeAssembleOnly);
+    if (!assemble<B, W, false>(cs, tm, c0, c1, mode == kModeAssembleOnly, v[0], sh)) return;
     if (!team_allreduce<1>(tm, v, sh)) return;
     clk.lap(kPhAssembly);
     if (mode == kModeAssembleOnly) return;
@@ -322,8 +335,9 @@ __device__ void run_steps_f64(const CaseDev& cs, const Team& tm, int n_steps, in
     const double xRef = v[0] / (double)cs.N;
     double u[3] = {0.0, 0.0, 0.0};  // normFactor sum, sum|r|, rho
     for (int c = c0 + tid; c < c1; c += B) {
-      const double d = cs.diag[c], xc = x[c], b = cs.src[c];
-      const double ax = row_exact<W>(cs, c, x, d, xc);
+      const double b = cs.src[c];
+      double xc;
+      const double ax = row_f64<W>(cs, c, x, xc);
       const double rc = b - ax;
       const double pA = cs.sumA[c] * xRef;
       u[0] += fabs(ax - pA) + fabs(b - pA);
@@ -455,7 +469,7 @@ __device__ void run_steps_mixed(const CaseDev& cs, const Team& tm, int n_steps, 
   PhaseClock clk(cs, tm);
   for (int step = 0; step < n_steps; ++step) {
     double v[1] = {0.0};
-    for (int c = c0 + tid; c < c1; c += B) v[0] += assemble_row<W, true>(cs, c, mode == kModeAssembleOnly);
+    if (!assemble<B, W, true>(cs, tm, c0, c1, mode == kModeAssembleOnly, v[0], sh)) return;
     if (!team_allreduce<1>(tm, v, sh)) return;
     clk.lap(kPhAssembly);
     if (mode == kModeAssembleOnly) return;

@@ -22,16 +22,20 @@ def general_path(case):
     W = int(deg.max()) if N else 0
     so = np.empty(W * N, np.int32)
     sf = np.empty(W * N, np.int32)
+    sm = np.full(W * N, -1, np.int8)
     for c in range(N):
-        slots = [(int(m.owner[f]), int(f)) for f in losort[lo_start[c]:lo_start[c + 1]]]
-        slots += [(int(m.neighbour[f]), f) for f in range(own_start[c], own_start[c + 1])]
-        slots += [(c, -1)] * (W - len(slots))
-        for k, (o, f) in enumerate(slots):
-            so[k * N + c], sf[k * N + c] = o, f
+        slots = [(int(m.owner[f]), int(f), -1) for f in losort[lo_start[c]:lo_start[c + 1]]]
+        for f in range(own_start[c], own_start[c + 1]):
+            n = int(m.neighbour[f])
+            mate = list(losort[lo_start[n]:lo_start[n + 1]]).index(f)
+            slots.append((n, f, mate))
+        slots += [(c, -1, -1)] * (W - len(slots))
+        for k, (o, f, mt) in enumerate(slots):
+            so[k * N + c], sf[k * N + c], sm[k * N + c] = o, f, mt
     counts = np.bincount(m.bface_cell, minlength=N)
     b_start = np.concatenate(([0], np.cumsum(counts))).astype(np.int32)
     b_face = np.argsort(m.bface_cell, kind="stable").astype(np.int32)
-    return dict(slot_other=so, slot_face=sf, V=m.V, magSf=m.magSf, deltaCoeffs=m.deltaCoeffs, b_start=b_start,
+    return dict(slot_other=so, slot_face=sf, slot_mate=sm, V=m.V, magSf=m.magSf, deltaCoeffs=m.deltaCoeffs, b_start=b_start,
                 b_face=b_face, bface_cell=m.bface_cell, bmagSf=m.bmagSf, bdeltaCoeffs=m.bdeltaCoeffs, W=W)
 
 
@@ -55,7 +59,7 @@ def test_box_layout_matches_general_path(shape, graded):
     ref = general_path(case)
     got = B.lfm_box_layout(case.xs, case.ys, case.zs)
     assert got["W"] == ref["W"]
-    for key in ("slot_other", "slot_face", "V", "magSf", "deltaCoeffs", "b_start", "b_face", "bface_cell",
+    for key in ("slot_other", "slot_face", "slot_mate", "V", "magSf", "deltaCoeffs", "b_start", "b_face", "bface_cell",
                 "bmagSf", "bdeltaCoeffs"):
         assert np.array_equal(got[key], ref[key]), key
 

@@ -125,3 +125,29 @@ def test_autotune_restores_state(tmp_path):
         # cached on the second call
         res2 = bt.autotune(cache=str(tmp_path / "tune.json"))
         assert res2["threads"] == res["threads"]
+
+
+def test_batch_multi_cta_teams_match_oracle():
+    # many cases, each split over several CTAs (small cells-per-thread), so team barriers
+    # carry cross-CTA data every phase; every result must match the oracle to 1e-10
+    cases = lapcase.batch_cases(n_cases=24, seed=21, n_min=20, n_max=36, n_steps=3)
+    with Batch() as bt:
+        ids = [bt.add_case(c) for c in cases]
+        bt.set_launch(256, (2, 2, 2))
+        for _ in range(2):
+            for cid, c in zip(ids, cases):
+                bt.cases[cid].set_field(oracle.initial_field(c))
+            assert bt.advance(3) == B.LFM_OK
+            for cid, c in zip(ids, cases):
+                To, so = oracle_cached(c)
+                assert relerr(bt.field(cid), To) <= 1e-10
+
+
+_ORACLE = {}
+
+
+def oracle_cached(c):
+    key = (c.name, c.nx, c.DT_uniform, c.dt)
+    if key not in _ORACLE:
+        _ORACLE[key] = oracle.advance(c)
+    return _ORACLE[key]
