@@ -271,15 +271,13 @@ int h2d(lfm_ctx* c, size_t off, const T* src, size_t n) {
   return LFM_OK;
 }
 
-// Default launch: one team of co-resident CTAs, about 4096 cells per CTA at least; 512
-// threads per CTA for FP64, 1024 for the mixed form (its FP32 passes need more threads in
-// flight per SM), chosen from launch-shape sweeps on graded200.
+// Default launch: one team of co-resident CTAs of 512 threads, at least about 4096 cells
+// per CTA (the best shape in launch-shape sweeps on the 200^3 graded box).
 int choose_launch(lfm_ctx* c) {
-  const int threads = c->opts.precision == LFM_MIXED ? 1024 : 512;
+  const int threads = 512;
   int maxc = max_coresident_ctas(c->opts.precision, threads, c->W, c->device);
   if (maxc <= 0) return fail(c, LFM_ECUDA, "cannot size the cooperative launch");
   int64_t want = ((int64_t)c->N + 4095) / 4096;
-  if (threads == 1024) want = ((int64_t)c->N + 8191) / 8192;
   if (want < 1) want = 1;
   if (want > maxc) want = maxc;
   c->tuned_ctas = (int)want;
