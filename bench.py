@@ -40,8 +40,8 @@ UNIT = "cell-iterations/s"
 WORKLOAD = ("graded200: 200^3 unit box graded 1.02x per cell in x (8.0M cells, 23.88M internal "
             "faces), DT=4e-5, dt=0.005, x0=373 K / x1=273 K fixedValue, zeroGradient elsewhere, "
             "T0=273 K, diagonal PCG tol 1e-6 relTol 0")
-KERNEL_SOURCES = ["paper_2507_18268_gb300/csrc/lfm_step.cu", "paper_2507_18268_gb300/csrc/lfm_device.cuh",
-                  "paper_2507_18268_gb300/csrc/lfm_internal.h"]
+KERNEL_SOURCES = ["paper_2507_18268_gb300/csrc/lfm_step.cu", "paper_2507_18268_gb300/csrc/lfm_solve.cuh",
+                  "paper_2507_18268_gb300/csrc/lfm_device.cuh", "paper_2507_18268_gb300/csrc/lfm_internal.h"]
 
 
 def kernel_hash() -> str:
