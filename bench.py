@@ -69,6 +69,17 @@ def algorithmic_bytes(N: int, F: int, iters: int, steps: int, precision: int) ->
     return float(iters) * per_iter + float(steps) * per_step
 
 
+def algorithmic_flops(N: int, F: int, iters: int, steps: int) -> float:
+    """Minimum FP64 floating-point operations (an FMA counts 2) of `steps` FP64 steps with
+    `iters` PCG iterations: per iteration 13 N + 4 F (p update 2N; A p 1N + 4F and p.Ap 2N;
+    x, r updates, w = rD r, w.r and sum|r| 8N); per step the assembly 5 N + 4 F and the
+    initial residual / normFactor 11 N + 4 F."""
+    return float(iters) * (13 * N + 4 * F) + float(steps) * (16 * N + 8 * F)
+
+
+FP64_NOMINAL_TFLOPS = 1.25  # GB300 dense FP64, nominal
+
+
 def load_peaks():
     p = os.path.join(ROOT, "MEASURED_PEAKS.json")
     if os.path.exists(p):
@@ -355,6 +366,11 @@ def main_ours(args, world, rank, local):
                      "frac": achieved_gbs / hbm_peak, "traffic": (ratio * alg / K) if ratio else None,
                      "peak_kind": peak_kind, "kernel": "step_kernel_f64",
                      "per": "one step (one launch runs all timed steps)"},
+        "roofline_fp64_pipe": {"bound": "alu", "achieved": algorithmic_flops(N, F, iters, K) / secs / 1e12,
+                               "peak": FP64_NOMINAL_TFLOPS, "unit": "TFLOP/s",
+                               "frac": algorithmic_flops(N, F, iters, K) / secs / 1e12 / FP64_NOMINAL_TFLOPS,
+                               "peak_kind": "nominal (1.25 TFLOP/s dense FP64)",
+                               "note": "ncu: FP64 pipe 70% busy, DRAM 65% (profiles/step_kernel_f64_graded200.md)"},
         "gpu_launches": 1,
         "clocks": clk,
         "mixed": mixed,
