@@ -118,13 +118,14 @@ int lfm_box_counts(int32_t nx, int32_t ny, int32_t nz, int32_t *n_cells, int32_t
                    int32_t *n_bfaces, int32_t *slot_width);
 
 /* Host replica of the device box builder (same per-cell routine): fills the slot-major
- * face-to-cell arrays (slot_other, slot_face [W*N]; slot_mate [W*N]: for an owned face
- * the slot index it occupies in its neighbour's row, -1 otherwise), V [N], magSf,
- * deltaCoeffs [F],
- * the cell-side boundary lists (b_start [N+1], b_face [NB]) and bface_cell, bmagSf,
- * bdeltaCoeffs [NB]. For validation of the closed forms; no device is touched. */
+ * face-to-cell arrays (slot_other, slot_face [W*N]: slot k of cell c at k*N + c), the
+ * per-face slot positions (face_slots [2F]: face f sits at slot face_slots[2f] of its
+ * owner's row and at face_slots[2f+1] of its neighbour's row), V [N], magSf,
+ * deltaCoeffs [F], the cell-side boundary lists (b_start [N+1], b_face [NB]) and
+ * bface_cell, bmagSf, bdeltaCoeffs [NB]. For validation of the closed forms; no device is
+ * touched. Boxes with W*N >= 2^32 are rejected (LFM_EINVAL). */
 int lfm_box_layout(int32_t nx, int32_t ny, int32_t nz, const double *xs, const double *ys,
-                   const double *zs, int32_t *slot_other, int32_t *slot_face, int8_t *slot_mate,
+                   const double *zs, int32_t *slot_other, int32_t *slot_face, uint32_t *face_slots,
                    double *V, double *magSf, double *deltaCoeffs, int32_t *b_start, int32_t *b_face,
                    int32_t *bface_cell, double *bmagSf, double *bdeltaCoeffs);
 
@@ -148,7 +149,8 @@ int lfm_bind_workspace(lfm_ctx *ctx, void *dev_ptr, size_t bytes, int32_t precis
 
 /* Validates and uploads the mesh (deep copy), builds the face-to-cell addressing and the
  * cell-side boundary-face lists. Resets DT to 0, every patch to zeroGradient, dt to 1,
- * the solver to {1e-6, 0, 1000, 0, LFM_FP64} and T to 0. */
+ * the solver to {1e-6, 0, 1000, 0, LFM_FP64} and T to 0. LFM_EINVAL also when a cell has
+ * more than 32 internal faces or (largest internal faces of a cell) x n_cells >= 2^32. */
 int lfm_upload_mesh(lfm_ctx *ctx, const lfm_mesh *mesh);
 
 /* Builds a box mesh (see lfm_box_counts) directly on the device -- the same arrays as
@@ -225,8 +227,9 @@ int lfm_field_device_ptr(lfm_ctx *ctx, double **T_dev);
  * source[n_cells]) to host memory, running only the assembly. Diagnostic / test use. */
 int lfm_get_matrix(lfm_ctx *ctx, double *diag, double *upper, double *source);
 
-/* Device time of the last advance by phase kind, in milliseconds (ms[8]): 0 assembly,
- * 1 initial residual / normFactor (mixed: FP64 true residuals), 2 search-direction update,
+/* Device time of the last advance by phase kind, in milliseconds (ms[8]): 0 assembly pass
+ * over faces (coefficients, sum of T), 1 assembly pass over rows together with the initial
+ * residual / normFactor (mixed: also the later FP64 true residuals), 2 search-direction update,
  * 3 matrix-vector product and p.Ap, 4 solution/residual update and dots, 5 (mixed) FP64
  * correction, 6-7 unused. Measured by one CTA between barrier exits, so each phase
  * includes its barrier wait; the sum is the kernel's wall time. */

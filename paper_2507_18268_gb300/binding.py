@@ -68,7 +68,7 @@ _SIGS = {
     "lfm_box_counts": ([c_int32, c_int32, c_int32, POINTER(c_int32), POINTER(c_int32), POINTER(c_int32),
                         POINTER(c_int32)], c_int),
     "lfm_box_layout": ([c_int32, c_int32, c_int32, POINTER(c_double), POINTER(c_double), POINTER(c_double),
-                        POINTER(c_int32), POINTER(c_int32), POINTER(ctypes.c_int8), POINTER(c_double),
+                        POINTER(c_int32), POINTER(c_int32), POINTER(ctypes.c_uint32), POINTER(c_double),
                         POINTER(c_double), POINTER(c_double),
                         POINTER(c_int32), POINTER(c_int32), POINTER(c_int32), POINTER(c_double),
                         POINTER(c_double)], c_int),
@@ -247,18 +247,18 @@ def lfm_box_layout(xs, ys, zs):
     nx, ny, nz = len(xs) - 1, len(ys) - 1, len(zs) - 1
     N, F, NB, W = lfm_box_counts(nx, ny, nz)
     out = dict(slot_other=np.empty(max(W * N, 1), np.int32), slot_face=np.empty(max(W * N, 1), np.int32),
-               slot_mate=np.empty(max(W * N, 1), np.int8),
+               face_slots=np.empty(max(2 * F, 2), np.uint32),
                V=np.empty(N), magSf=np.empty(max(F, 1)), deltaCoeffs=np.empty(max(F, 1)),
                b_start=np.empty(N + 1, np.int32), b_face=np.empty(NB, np.int32), bface_cell=np.empty(NB, np.int32),
                bmagSf=np.empty(NB), bdeltaCoeffs=np.empty(NB))
     _check(load().lfm_box_layout(nx, ny, nz, _ptr(xs, c_double), _ptr(ys, c_double), _ptr(zs, c_double),
-                                 *[_ptr(out[k], {np.dtype(np.int32): c_int32, np.dtype(np.int8): ctypes.c_int8,
+                                 *[_ptr(out[k], {np.dtype(np.int32): c_int32, np.dtype(np.uint32): ctypes.c_uint32,
                                                  np.dtype(np.float64): c_double}[out[k].dtype])
-                                   for k in ("slot_other", "slot_face", "slot_mate", "V", "magSf", "deltaCoeffs",
+                                   for k in ("slot_other", "slot_face", "face_slots", "V", "magSf", "deltaCoeffs",
                                              "b_start",
                                              "b_face", "bface_cell", "bmagSf", "bdeltaCoeffs")]))
     out["slot_other"], out["slot_face"] = out["slot_other"][:W * N], out["slot_face"][:W * N]
-    out["slot_mate"] = out["slot_mate"][:W * N]
+    out["face_slots"] = out["face_slots"][:2 * F]
     out["magSf"], out["deltaCoeffs"] = out["magSf"][:F], out["deltaCoeffs"][:F]
     out.update(n_cells=N, n_faces=F, n_bfaces=NB, W=W)
     return out
@@ -368,7 +368,7 @@ def lfm_get_matrix(ctx, n_cells: int, n_faces: int):
     return d, u[:n_faces], s
 
 
-PHASES = ("assembly", "initial_residual", "p_update", "amul_dot", "update_dots", "fp64_correction")
+PHASES = ("assembly_faces", "rows_initial_residual", "p_update", "amul_dot", "update_dots", "fp64_correction")
 
 
 def lfm_get_phase_times(ctx) -> dict:

@@ -34,9 +34,9 @@ size_t align_up(size_t v, size_t a) { return (v + a - 1) / a * a; }
 // Byte layout of a case's workspace. Offsets are relative to the workspace base.
 struct Layout {
   size_t sync, partials, stats;
-  size_t slot_other, slot_face, slot_mate, b_start, b_face, bcell, btype;
+  size_t slot_other, slot_face, face_slots, b_start, b_face, bcell, btype;
   size_t V, magSf, delta, DT, bmagSf, bdelta, bDT, bval;
-  size_t diag, upper, slot_coef, src, rD, sumA, vdt, x, r, w, p, q, Tb;
+  size_t diag, upper, slot_coef, src, rD, vdt, x, r, w, p, q, Tb;
   size_t diag32, slot_coef32, rD32, dx32, r32, w32, p32, q32;
   size_t total;
 };
@@ -60,7 +60,7 @@ Layout make_layout(int64_t N, int64_t F, int64_t NB, int64_t W, int kind, bool s
   if (!shared_mesh) {
     L.slot_other = take(4 * W * N);
     L.slot_face = take(4 * W * N);
-    L.slot_mate = take(W * N);
+    L.face_slots = take(8 * F);
     L.b_start = take(4 * (N + 1));
     L.b_face = take(4 * NB);
     L.bcell = take(4 * NB);
@@ -79,7 +79,6 @@ Layout make_layout(int64_t N, int64_t F, int64_t NB, int64_t W, int kind, bool s
   L.slot_coef = take(8 * W * N);
   L.src = take(8 * N);
   L.rD = take(8 * N);
-  L.sumA = take(8 * N);
   L.vdt = take(8 * N);
   L.x = take(8 * N);
   L.Tb = take(8 * NB);
@@ -326,7 +325,7 @@ void bind_pointers(lfm_ctx* c) {
     const CaseDev& m = c->mesh_src->cs;
     cs.slot_other = m.slot_other;
     cs.slot_face = m.slot_face;
-    cs.slot_mate = m.slot_mate;
+    cs.face_slots = m.face_slots;
     cs.b_start = m.b_start;
     cs.b_face = m.b_face;
     cs.bcell = m.bcell;
@@ -338,7 +337,7 @@ void bind_pointers(lfm_ctx* c) {
   } else {
     cs.slot_other = reinterpret_cast<const int32_t*>(b + L.slot_other);
     cs.slot_face = reinterpret_cast<const int32_t*>(b + L.slot_face);
-    cs.slot_mate = reinterpret_cast<const int8_t*>(b + L.slot_mate);
+    cs.face_slots = reinterpret_cast<const uint32_t*>(b + L.face_slots);
     cs.b_start = reinterpret_cast<const int32_t*>(b + L.b_start);
     cs.b_face = reinterpret_cast<const int32_t*>(b + L.b_face);
     cs.bcell = reinterpret_cast<const int32_t*>(b + L.bcell);
@@ -353,7 +352,6 @@ void bind_pointers(lfm_ctx* c) {
   cs.slot_coef = reinterpret_cast<double*>(b + L.slot_coef);
   cs.src = reinterpret_cast<double*>(b + L.src);
   cs.rD = reinterpret_cast<double*>(b + L.rD);
-  cs.sumA = reinterpret_cast<double*>(b + L.sumA);
   cs.vdt = reinterpret_cast<const double*>(b + L.vdt);
   cs.x = reinterpret_cast<double*>(b + L.x);
   const bool d = c->has64, m = c->has32;
@@ -506,6 +504,9 @@ int lfm_upload_mesh(lfm_ctx* c, const lfm_mesh* m) {
   DeviceGuard g(c->device);
   const int32_t W = slot_width(m);
   if (W > kMaxSlots) return fail(c, LFM_EINVAL, "a cell has %d internal faces (at most %d supported)", W, kMaxSlots);
+  if ((uint64_t)W * (uint64_t)m->n_cells > 0xffffffffull)
+    return fail(c, LFM_EINVAL, "slot width x cells = %llu exceeds 2^32 - 1",
+                (unsigned long long)W * (unsigned long long)m->n_cells);
   const int kind = c->ws_bound ? c->ws_kind : kLayoutBoth;
   const Layout use = make_layout(m->n_cells, m->n_faces, m->n_bfaces, W, kind);
   const bool has64 = kind != LFM_MIXED, has32 = kind != LFM_FP64;
@@ -540,31 +541,27 @@ int lfm_upload_mesh(lfm_ctx* c, const lfm_mesh* m) {
   std::vector<int32_t> own_start(N + 1), lo_start(N + 1), losort(F > 0 ? F : 1);
   int rc = lfm_face_addressing(N, F, m->owner, m->neighbour, own_start.data(), losort.data(), lo_start.data());
   if (rc != LFM_OK) return fail(c, rc, "%s", g_last_error.c_str());
-  // Slot-major copy of the face-to-cell lists: neighbour-side faces, owned faces, padding.
+  // Slot-major copy of the face-to-cell lists: neighbour-side faces, owned faces, padding;
+  // and, per face, the slot it occupies in its owner's row and in its neighbour's row.
   std::vector<int32_t> slot_other((size_t)W * N), slot_face((size_t)W * N);
-  std::vector<int8_t> slot_mate((size_t)W * N, (int8_t)-1);
+  std::vector<uint32_t> face_slots(F > 0 ? 2 * (size_t)F : 2);
   for (int32_t cell = 0; cell < N; ++cell) {
     int k = 0;
     for (int32_t i = lo_start[cell]; i < lo_start[cell + 1]; ++i, ++k) {
-      slot_other[(size_t)k * N + cell] = m->owner[losort[i]];
-      slot_face[(size_t)k * N + cell] = losort[i];
+      const size_t at = (size_t)k * N + cell;
+      slot_other[at] = m->owner[losort[i]];
+      slot_face[at] = losort[i];
+      face_slots[2 * (size_t)losort[i] + 1] = (uint32_t)at;
     }
     for (int32_t f = own_start[cell]; f < own_start[cell + 1]; ++f, ++k) {
-      slot_other[(size_t)k * N + cell] = m->neighbour[f];
-      slot_face[(size_t)k * N + cell] = f;
+      const size_t at = (size_t)k * N + cell;
+      slot_other[at] = m->neighbour[f];
+      slot_face[at] = f;
+      face_slots[2 * (size_t)f] = (uint32_t)at;
     }
     for (; k < W; ++k) {
       slot_other[(size_t)k * N + cell] = cell;
       slot_face[(size_t)k * N + cell] = -1;
-    }
-  }
-  // mate of an owned face: its position among the neighbour's neighbour-side faces
-  for (int32_t cell = 0; cell < N; ++cell) {
-    const int lo_n = lo_start[cell + 1] - lo_start[cell];
-    for (int32_t f = own_start[cell], k = lo_n; f < own_start[cell + 1]; ++f, ++k) {
-      const int32_t n = m->neighbour[f];
-      for (int32_t i = lo_start[n]; i < lo_start[n + 1]; ++i)
-        if (losort[i] == f) slot_mate[(size_t)k * N + cell] = (int8_t)(i - lo_start[n]);
     }
   }
   std::vector<int32_t> b_start(N + 1), b_face(NB > 0 ? NB : 1);
@@ -575,7 +572,7 @@ int lfm_upload_mesh(lfm_ctx* c, const lfm_mesh* m) {
   const Layout& Y = c->lay;
   const size_t WN = (size_t)W * N;
   if ((rc = h2d(c, Y.slot_other, slot_other.data(), WN)) || (rc = h2d(c, Y.slot_face, slot_face.data(), WN)) ||
-      (rc = h2d(c, Y.slot_mate, slot_mate.data(), WN)) ||
+      (rc = h2d(c, Y.face_slots, face_slots.data(), 2 * (size_t)F)) ||
       (rc = h2d(c, Y.b_start, b_start.data(), N + 1)) ||
       (rc = h2d(c, Y.b_face, b_face.data(), NB)) || (rc = h2d(c, Y.bcell, m->bface_cell, NB)) ||
       (rc = h2d(c, Y.btype, btype.data(), NB)) || (rc = h2d(c, Y.V, m->V, N)) ||
@@ -608,6 +605,7 @@ int check_box(int32_t nx, int32_t ny, int32_t nz, const double* xs, const double
   const long long N = (long long)nx * ny * nz;
   const long long F = (long long)(nx - 1) * ny * nz + (long long)nx * (ny - 1) * nz + (long long)nx * ny * (nz - 1);
   if (N > 0x7fffffffLL || F > 0x7fffffffLL) return set_why(why, "box too large for 32-bit indices");
+  if ((long long)box_slot_width(nx, ny, nz) * N > 0xffffffffLL) return set_why(why, "slot width x cells exceeds 2^32 - 1");
   if ((long long)nx + ny + nz + 3 > (long long)kMaxCtas * kMaxSums) return set_why(why, "too many vertex planes");
   const double* ax[3] = {xs, ys, zs};
   const int32_t n[3] = {nx, ny, nz};
@@ -626,6 +624,8 @@ int lfm_box_counts(int32_t nx, int32_t ny, int32_t nz, int32_t* n_cells, int32_t
   const long long N = (long long)nx * ny * nz;
   const long long F = (long long)(nx - 1) * ny * nz + (long long)nx * (ny - 1) * nz + (long long)nx * ny * (nz - 1);
   if (N > 0x7fffffffLL || F > 0x7fffffffLL) return fail_free(LFM_EINVAL, "box too large for 32-bit indices");
+  if ((long long)box_slot_width(nx, ny, nz) * N > 0xffffffffLL)
+    return fail_free(LFM_EINVAL, "slot width x cells exceeds 2^32 - 1");
   if (n_cells) *n_cells = (int32_t)N;
   if (n_faces) *n_faces = (int32_t)F;
   if (n_bfaces) *n_bfaces = (int32_t)(2 * ((long long)ny * nz + (long long)nx * nz + (long long)nx * ny));
@@ -634,15 +634,15 @@ int lfm_box_counts(int32_t nx, int32_t ny, int32_t nz, int32_t* n_cells, int32_t
 }
 
 int lfm_box_layout(int32_t nx, int32_t ny, int32_t nz, const double* xs, const double* ys, const double* zs,
-                   int32_t* slot_other, int32_t* slot_face, int8_t* slot_mate, double* V, double* magSf,
+                   int32_t* slot_other, int32_t* slot_face, uint32_t* face_slots, double* V, double* magSf,
                    double* delta,
                    int32_t* b_start, int32_t* b_face, int32_t* bcell, double* bmagSf, double* bdelta) {
   std::string why;
   if (check_box(nx, ny, nz, xs, ys, zs, why) != LFM_OK) return fail_free(LFM_EINVAL, "%s", why.c_str());
-  if (!slot_other || !slot_face || !slot_mate || !V || !magSf || !delta || !b_start || !b_face || !bcell ||
+  if (!slot_other || !slot_face || !face_slots || !V || !magSf || !delta || !b_start || !b_face || !bcell ||
       !bmagSf || !bdelta)
     return fail_free(LFM_EINVAL, "output arrays missing");
-  box_layout_host(nx, ny, nz, box_slot_width(nx, ny, nz), xs, ys, zs, slot_other, slot_face, slot_mate, V, magSf,
+  box_layout_host(nx, ny, nz, box_slot_width(nx, ny, nz), xs, ys, zs, slot_other, slot_face, face_slots, V, magSf,
                   delta,
                   b_start, b_face, bcell, bmagSf, bdelta);
   return LFM_OK;

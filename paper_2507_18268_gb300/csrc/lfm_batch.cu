@@ -57,9 +57,9 @@ __global__ void __launch_bounds__(B, 1024 / B) batch_kernel(const CaseDev* __res
     const Team tm{s_job[2], s_job[1], s_cs.sync, s_cs.partials, L.timeout_ns};
     const int base = case_step[c];
     if (s_cs.precision == LFM_MIXED)
-      run_steps_mixed<B, W>(s_cs, tm, n_steps, kModeSteps, sh, base);
+      run_steps_mixed<B, W>(s_cs, s_cs, tm, n_steps, kModeSteps, sh, base);
     else
-      run_steps_f64<B, W>(s_cs, tm, n_steps, kModeSteps, sh, base);
+      run_steps_f64<B, W>(s_cs, s_cs, tm, n_steps, kModeSteps, sh, base);
     __syncthreads();
     if (tm.rank == 0 && threadIdx.x == 0) case_step[c] = base + n_steps;
     __syncthreads();

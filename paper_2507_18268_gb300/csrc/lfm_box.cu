@@ -33,7 +33,7 @@ struct BoxDims {
 
 struct BoxOut {
   int32_t *slot_other, *slot_face;
-  int8_t* slot_mate;
+  uint32_t* face_slots;
   double *V, *magSf, *delta;
   int32_t *b_start, *b_face, *bcell;
   double *bmagSf, *bdelta;
@@ -82,53 +82,55 @@ __host__ __device__ inline void box_cell(const BoxDims& d, long long c, const Bo
   if (k > 0) {
     o.slot_other[(size_t)s * N + c] = (int32_t)(c - nx * ny);
     o.slot_face[(size_t)s * N + c] = (int32_t)(box_own_start(d, i, j, k - 1) + (i < nx - 1) + (j < ny - 1));
-    o.slot_mate[(size_t)s * N + c] = -1;
     ++s;
   }
   if (j > 0) {
     o.slot_other[(size_t)s * N + c] = (int32_t)(c - nx);
     o.slot_face[(size_t)s * N + c] = (int32_t)(box_own_start(d, i, j - 1, k) + (i < nx - 1));
-    o.slot_mate[(size_t)s * N + c] = -1;
     ++s;
   }
   if (i > 0) {
     o.slot_other[(size_t)s * N + c] = (int32_t)(c - 1);
     o.slot_face[(size_t)s * N + c] = (int32_t)box_own_start(d, i - 1, j, k);
-    o.slot_mate[(size_t)s * N + c] = -1;
     ++s;
   }
   // an owned face sits in the neighbour's row after the neighbour's lower-ordered faces:
   // +x: after its z- and y-faces, +y: after its z-face, +z: first
-  const int mate_x = (k > 0) + (j > 0), mate_y = (k > 0), mate_z = 0;
+  const long long mate_x = (k > 0) + (j > 0), mate_y = (k > 0), mate_z = 0;
   long long f = box_own_start(d, i, j, k);
   if (i < nx - 1) {
     o.magSf[f] = hy * hz;
     o.delta[f] = 1.0 / (box_centre(d.xs, i + 1) - box_centre(d.xs, i));
     o.slot_other[(size_t)s * N + c] = (int32_t)(c + 1);
-    o.slot_face[(size_t)s * N + c] = (int32_t)f++;
-    o.slot_mate[(size_t)s * N + c] = (int8_t)mate_x;
+    o.slot_face[(size_t)s * N + c] = (int32_t)f;
+    o.face_slots[2 * f] = (uint32_t)(s * N + c);
+    o.face_slots[2 * f + 1] = (uint32_t)(mate_x * N + c + 1);
+    ++f;
     ++s;
   }
   if (j < ny - 1) {
     o.magSf[f] = hx * hz;
     o.delta[f] = 1.0 / (box_centre(d.ys, j + 1) - box_centre(d.ys, j));
     o.slot_other[(size_t)s * N + c] = (int32_t)(c + nx);
-    o.slot_face[(size_t)s * N + c] = (int32_t)f++;
-    o.slot_mate[(size_t)s * N + c] = (int8_t)mate_y;
+    o.slot_face[(size_t)s * N + c] = (int32_t)f;
+    o.face_slots[2 * f] = (uint32_t)(s * N + c);
+    o.face_slots[2 * f + 1] = (uint32_t)(mate_y * N + c + nx);
+    ++f;
     ++s;
   }
   if (k < nz - 1) {
     o.magSf[f] = hx * hy;
     o.delta[f] = 1.0 / (box_centre(d.zs, k + 1) - box_centre(d.zs, k));
     o.slot_other[(size_t)s * N + c] = (int32_t)(c + nx * ny);
-    o.slot_face[(size_t)s * N + c] = (int32_t)f++;
-    o.slot_mate[(size_t)s * N + c] = (int8_t)mate_z;
+    o.slot_face[(size_t)s * N + c] = (int32_t)f;
+    o.face_slots[2 * f] = (uint32_t)(s * N + c);
+    o.face_slots[2 * f + 1] = (uint32_t)(mate_z * N + c + nx * ny);
+    ++f;
     ++s;
   }
   for (; s < d.W; ++s) {
     o.slot_other[(size_t)s * N + c] = (int32_t)c;
     o.slot_face[(size_t)s * N + c] = -1;
-    o.slot_mate[(size_t)s * N + c] = -1;
   }
 
   long long at = box_bstart(d, i, j, k);
@@ -169,7 +171,7 @@ cudaError_t launch_box(long long nx, long long ny, long long nz, int W, const do
                        const double* zs, const CaseDev& cs, cudaStream_t stream) {
   BoxDims d{nx, ny, nz, W, xs, ys, zs};
   BoxOut o{const_cast<int32_t*>(cs.slot_other), const_cast<int32_t*>(cs.slot_face),
-           const_cast<int8_t*>(cs.slot_mate), const_cast<double*>(cs.V),
+           const_cast<uint32_t*>(cs.face_slots), const_cast<double*>(cs.V),
            const_cast<double*>(cs.magSf), const_cast<double*>(cs.delta), const_cast<int32_t*>(cs.b_start),
            const_cast<int32_t*>(cs.b_face), const_cast<int32_t*>(cs.bcell), const_cast<double*>(cs.bmagSf),
            const_cast<double*>(cs.bdelta)};
@@ -179,11 +181,11 @@ cudaError_t launch_box(long long nx, long long ny, long long nz, int W, const do
 }
 
 void box_layout_host(long long nx, long long ny, long long nz, int W, const double* xs, const double* ys,
-                     const double* zs, int32_t* slot_other, int32_t* slot_face, int8_t* slot_mate, double* V,
+                     const double* zs, int32_t* slot_other, int32_t* slot_face, uint32_t* face_slots, double* V,
                      double* magSf, double* delta, int32_t* b_start, int32_t* b_face, int32_t* bcell,
                      double* bmagSf, double* bdelta) {
   BoxDims d{nx, ny, nz, W, xs, ys, zs};
-  BoxOut o{slot_other, slot_face, slot_mate, V, magSf, delta, b_start, b_face, bcell, bmagSf, bdelta};
+  BoxOut o{slot_other, slot_face, face_slots, V, magSf, delta, b_start, b_face, bcell, bmagSf, bdelta};
   const long long N = nx * ny * nz;
   for (long long c = 0; c <= N; ++c) box_cell(d, c, o);
 }

@@ -50,8 +50,8 @@ struct CaseDev {
   int32_t W;
   const int32_t* slot_other; // [W*N] the other cell of the slot's face
   const int32_t* slot_face;  // [W*N] face id, -1 for padding
-  const int8_t* slot_mate;   // [W*N] for an owned face: the slot holding it in the neighbour's
-                             // row; -1 for neighbour-side faces and padding
+  const uint32_t* face_slots; // [2F] face f sits at slot face_slots[2f] (= k*N + owner) of
+                              // its owner's row and at face_slots[2f+1] of its neighbour's
   const int32_t* b_start;    // [N+1] boundary faces of c: b_face[b_start[c] ..)
   const int32_t* b_face;     // [NB]  boundary faces sorted by cell, ascending id per cell
   const int32_t* bcell;      // [NB]  cell of boundary face b
@@ -74,9 +74,8 @@ struct CaseDev {
   double* diag;              // [N]
   double* upper;             // [F]  (lower == upper)
   double* slot_coef;         // [W*N]
-  double* src;               // [N]
+  double* src;               // [N]  (FP64 steps write it only for matrix read-back)
   double* rD;                // [N]  1/diag
-  double* sumA;              // [N]  row sums of A (V/dt + boundary conductance)
 
   // FP64 solver vectors; x is the field T (updated in place)
   double* x;
@@ -140,7 +139,7 @@ int box_slot_width(long long nx, long long ny, long long nz);
 cudaError_t launch_box(long long nx, long long ny, long long nz, int W, const double* xs, const double* ys,
                        const double* zs, const CaseDev& cs, cudaStream_t stream);
 void box_layout_host(long long nx, long long ny, long long nz, int W, const double* xs, const double* ys,
-                     const double* zs, int32_t* slot_other, int32_t* slot_face, int8_t* slot_mate,
+                     const double* zs, int32_t* slot_other, int32_t* slot_face, uint32_t* face_slots,
                      double* V, double* magSf,
                      double* delta, int32_t* b_start, int32_t* b_face, int32_t* bcell, double* bmagSf,
                      double* bdelta);

@@ -13,19 +13,21 @@
 // keeps a dozen independent memory requests in flight.
 //
 // FP64 step (phases separated by team barriers):
-//   A  assembly        per slot g = DT |Sf| deltaCoeff; diag, the per-slot off-diagonals
-//                      (each face's coefficient at both of its cells; the face-indexed
-//                      LDU `upper` is written only for matrix read-back), source,
-//                      rD = 1/diag, row sums; sum x for xRef
-//   I  initial state   A x, r = b - A x, row sums -> normFactor, sum|r|, w = rD r, rho;
-//                      p = w (first search direction)
+//   A1 faces           per owned face g = DT |Sf| deltaCoeff, stored at both of its cells'
+//                      slots (the face-indexed LDU `upper` is written only for matrix
+//                      read-back); sum x for xRef
+//   A2+I rows          diag, source, rD = 1/diag, row sum; from the same loaded row
+//                      A x, r = b - A x, normFactor, sum|r|, w = rD r, rho; p = w (first
+//                      search direction). The source is needed by no later phase of an
+//                      FP64 step and is stored only for read-back.
 //   loop (diagonal-preconditioned CG, convergence on sum|r| / normFactor):
 //   P  p = w + beta p  (skipped on the first iteration)
 //   M  q = A p, sigma = p.q                   -> alpha = rho / sigma
 //   U  x += alpha p, r -= alpha q, w = rD r, sum|r|, rho' = w.r -> beta = rho'/rho
 //
 // Mixed step (defect correction, FP64 field x): the matrix is assembled in FP64 and copied
-// to FP32; each sweep computes the FP64 true residual r = b - A x, solves A dx = r by the
+// to FP32; each sweep computes the FP64 true residual r = b - A x (the first one in the
+// assembly's row pass), solves A dx = r by the
 // same CG recurrence on FP32 vectors with FP32 row sums, and adds dx to x in FP64. Dot
 // products, sum|r|, normFactor and every convergence test are FP64-accurate: FP64 for the
 // FP64 quantities; for FP32 terms, exact products summed as unevaluated FP32 pairs per
@@ -90,186 +92,413 @@ struct Acc2f {
 };
 
 // ---- assembly of fvm::ddt(T) - fvm::laplacian(DT, T), two passes ---------------------
-// Pass 1 (per cell, its owned faces): g = (DT |Sf|) deltaCoeff, computed once per face and
-// stored as -g in the cell's slot and in the neighbour's matching slot (slot_mate).
+// Pass 1 (per face, in face order): g = (DT |Sf|) deltaCoeff, computed once per face and
+// stored as -g at the face's slot in its owner's row and in its neighbour's row. Faces are
+// read and the face-indexed LDU copy written with unit stride; two faces per loop trip.
 template <bool kMixed>
-__device__ __forceinline__ void assemble_faces(const CaseDev& cs, int c, int ns, bool write_upper) {
-  const size_t N = (size_t)cs.N;
-  for (int k = 0; k < ns; ++k) {
-    const size_t at = (size_t)k * N + c;
-    const int mate = __ldg(cs.slot_mate + at);
-    if (mate >= 0) {
-      const int f = __ldg(cs.slot_face + at);
-      const int n = __ldg(cs.slot_other + at);
-      const double DTf = cs.DT_is_uniform ? cs.DT_uniform : __ldg(cs.DT + f);
-      const double g = __dmul_rn(__dmul_rn(DTf, __ldg(cs.magSf + f)), __ldg(cs.delta + f));
-      const size_t at_n = (size_t)mate * N + n;
-      cs.slot_coef[at] = -g;
-      cs.slot_coef[at_n] = -g;
-      if (kMixed) {
-        cs.slot_coef32[at] = (float)(-g);
-        cs.slot_coef32[at_n] = (float)(-g);
-      }
-      if (write_upper) cs.upper[f] = -g;  // the face-indexed LDU copy, for read-back only
-    }
+__device__ __forceinline__ void assemble_face(const CaseDev& cs, int f, bool write_upper) {
+  const uint2 at = __ldg(reinterpret_cast<const uint2*>(cs.face_slots) + f);
+  const double DTf = cs.DT_is_uniform ? cs.DT_uniform : __ldg(cs.DT + f);
+  const double g = __dmul_rn(__dmul_rn(DTf, __ldg(cs.magSf + f)), __ldg(cs.delta + f));
+  cs.slot_coef[at.x] = -g;
+  cs.slot_coef[at.y] = -g;
+  if (kMixed) {
+    cs.slot_coef32[at.x] = (float)(-g);
+    cs.slot_coef32[at.y] = (float)(-g);
   }
+  if (write_upper) cs.upper[f] = -g;  // the face-indexed LDU copy, for read-back only
 }
 
-// Pass 2 (per cell): the diagonal summed in slot order, i.e. ascending face order
+// Pass 2 (per cell): the row's diagonal summed in slot order, i.e. ascending face order
 // (neighbour-side faces have smaller owners, so they precede the cell's own faces in
-// upper-triangular order), then the boundary faces, then V/dt; every product and sum rounded
-// separately (no FMA); source, 1/diag and the row sum. Returns the cell's T.
-template <int W, bool kMixed>
-__device__ __forceinline__ double assemble_diag(const CaseDev& cs, int c) {
-  const size_t N = (size_t)cs.N;
-  const int ns = nslots<W>(cs);
-  double d = 0.0, s = 0.0;
-#pragma unroll
-  for (int k = 0; k < (W > 0 ? W : kMaxSlots); ++k) {
-    if (W == 0 && k >= ns) break;
-    d = __dadd_rn(d, -cs.slot_coef[(size_t)k * N + c]);  // padding slots hold 0
-  }
-  double gsum = 0.0;  // boundary conductance of the row
+// upper-triangular order), then the boundary faces, then V/dt, every product and sum rounded
+// separately (no FMA); the source; the row sum of A (the off-diagonals cancel the face
+// conductances in the diagonal exactly in real arithmetic, leaving V/dt plus the boundary
+// conductance). The row's A x is formed from the same loaded coefficients (the off-diagonal
+// products fused in slot order, then diag * x_c), so the initial residual needs no second
+// pass over the matrix.
+struct Row {
+  double d, s, sa, ax, xc;
+};
+
+// Clears the sign of a zero (0.0 + v would, at the cost of an FP64 add).
+__device__ __forceinline__ double plus_zero(double v) {
+  const long long bits = __double_as_longlong(v);
+  return (bits << 1) == 0 ? 0.0 : v;
+}
+
+__device__ __forceinline__ void row_boundary(const CaseDev& cs, int c, Row& o) {
   const int b0 = __ldg(cs.b_start + c), b1 = __ldg(cs.b_start + c + 1);
+  const double vdt = cs.vdt[c];  // V/dt, formed once per (mesh, dt): the same IEEE quotient
+  const double sv = __dmul_rn(vdt, o.xc);
+  if (b0 == b1) {  // no boundary face: the sums below start from zero
+    o.d = __dadd_rn(o.d, vdt);
+    o.s = plus_zero(sv);
+    o.sa = vdt;
+    return;
+  }
+  double s = 0.0, gsum = 0.0;  // source, boundary conductance of the row
   for (int k = b0; k < b1; ++k) {
     const int bf = __ldg(cs.b_face + k);
     if (__ldg(cs.btype + bf) == LFM_FIXED_VALUE) {
       const double gb = __dmul_rn(__dmul_rn(__ldg(cs.bDT + bf), __ldg(cs.bmagSf + bf)), __ldg(cs.bdelta + bf));
-      d = __dadd_rn(d, gb);
+      o.d = __dadd_rn(o.d, gb);
       s = __dadd_rn(s, __dmul_rn(gb, __ldg(cs.bval + bf)));
       gsum = __dadd_rn(gsum, gb);
     }
   }
-  const double vdt = cs.vdt[c];  // V/dt, hoisted out of the time loop (same IEEE quotient)
-  const double xc = cs.x[c];
-  d = __dadd_rn(d, vdt);
-  s = __dadd_rn(s, __dmul_rn(vdt, xc));
-  const double rd = __drcp_rn(d);  // IEEE round-to-nearest reciprocal, as 1.0 / d
-  cs.diag[c] = d;
-  cs.src[c] = s;
+  o.d = __dadd_rn(o.d, vdt);
+  o.s = __dadd_rn(s, sv);
+  o.sa = gsum + vdt;
+}
+
+template <int W>
+__device__ __forceinline__ Row assemble_row(const CaseDev& cs, int c, const double* __restrict__ x) {
+  const size_t N = (size_t)cs.N;
+  Row o;
+  o.xc = x[c];
+  o.d = 0.0;
+  double off = 0.0;  // sum of the off-diagonal products, slot order
+  if constexpr (W > 0) {
+    int oc[W];
+    double u[W];
+#pragma unroll
+    for (int k = 0; k < W; ++k) {
+      oc[k] = __ldg(cs.slot_other + (size_t)k * N + c);
+      u[k] = cs.slot_coef[(size_t)k * N + c];
+    }
+    // 0 + g_0 = g_0 exactly; the sign of a zero cannot reach d, which ends above V/dt > 0
+    o.d = -u[0];
+#pragma unroll
+    for (int k = 1; k < W; ++k) o.d = __dadd_rn(o.d, -u[k]);  // padding slots hold 0
+#pragma unroll
+    for (int k = 0; k < W; ++k) off = fma(u[k], x[oc[k]], off);
+  } else {
+    const int ns = cs.W;
+    for (int k = 0; k < ns; ++k) {
+      const size_t at = (size_t)k * N + c;
+      const double u = cs.slot_coef[at];
+      o.d = __dadd_rn(o.d, -u);
+      off = fma(u, x[__ldg(cs.slot_other + at)], off);
+    }
+  }
+  row_boundary(cs, c, o);
+  o.ax = fma(o.d, o.xc, off);
+  return o;
+}
+
+// Writes the assembled row (diag, source, 1/diag and the FP32 copies). Returns 1/diag.
+template <bool kMixed>
+__device__ __forceinline__ double store_row(const CaseDev& cs, int c, const Row& o, bool keep_src) {
+  const double rd = __drcp_rn(o.d);  // IEEE round-to-nearest reciprocal, as 1.0 / d
+  cs.diag[c] = o.d;
   cs.rD[c] = rd;
-  // Row sum of A: the off-diagonals cancel the face conductances in the diagonal exactly in
-  // real arithmetic, leaving V/dt plus the boundary conductance.
-  cs.sumA[c] = gsum + vdt;
+  if (keep_src) cs.src[c] = o.s;
   if (kMixed) {
-    cs.diag32[c] = (float)d;
+    cs.diag32[c] = (float)o.d;
     cs.rD32[c] = (float)rd;
   }
-  return xc;
+  return rd;
 }
 
-// Both passes for this CTA's cells, with the team barrier between them. v0 receives the
-// CTA threads' sum of T (for xRef); false when a barrier failed.
-template <int B, int W, bool kMixed>
-__device__ __forceinline__ bool assemble(const CaseDev& cs, const Team& tm, int c0, int c1, bool write_upper,
-                                         double& sum_x, TeamShared& sh) {
-  const int ns = nslots<W>(cs);
-  for (int c = c0 + (int)threadIdx.x; c < c1; c += B) assemble_faces<kMixed>(cs, c, ns, write_upper);
-  if (!team_barrier(tm, sh)) return false;
+// The per-step passes (faces, rows + initial residual, true residual) are compiled as
+// functions of their own (__noinline__, taking an addressable copy of the case descriptor):
+// their register demand then does not shape the allocation of the iteration passes.
+
+// Pass 1 over the faces [f0, f1) of this CTA; returns this thread's sum of T over the cells
+// [c0, c1) (for xRef).
+template <int B, bool kMixed>
+__device__ __noinline__ double pass_faces(const CaseDev& cs, int f0, int f1, int c0, int c1, bool write_upper) {
+  for (int f = f0 + (int)threadIdx.x; f < f1; f += B) assemble_face<kMixed>(cs, f, write_upper);
+  const double* __restrict__ x = cs.x;
   double v = 0.0;
-  for (int c = c0 + (int)threadIdx.x; c < c1; c += B) v += assemble_diag<W, kMixed>(cs, c);
-  sum_x = v;
-  return true;
+  for (int c = c0 + (int)threadIdx.x; c < c1; c += B) v += x[c];
+  return v;
 }
 
-// ---- FP64 A v for two rows at once (FMA accumulation) ----------------------------------
-template <int W>
-__device__ __forceinline__ void rows2_f64(const CaseDev& cs, int c, int c2, const double* __restrict__ v,
-                                          double& y, double& y2, double& vc, double& vc2) {
-  const size_t N = (size_t)cs.N;
+// Pass 2 alone, for matrix read-back (every array of the assembled system written).
+template <int B, int W, bool kMixed>
+__device__ __noinline__ void pass_rows_only(const CaseDev& cs, int c0, int c1) {
+  for (int c = c0 + (int)threadIdx.x; c < c1; c += B) store_row<kMixed>(cs, c, assemble_row<W>(cs, c, cs.x), true);
+}
+
+// ---- A v over the slot-major matrix (FP64 or FP32 copy) --------------------------------
+template <typename T>
+struct Slots {
+  int N, W;
+  const int32_t* other;  // [W*N] neighbour cell per slot (padding: the cell itself)
+  const T* coef;         // [W*N] off-diagonal per slot (padding: 0)
+  const T* diag;         // [N]
+};
+
+__device__ __forceinline__ Slots<double> slots64(const CaseDev& cs) {
+  return Slots<double>{cs.N, cs.W, cs.slot_other, cs.slot_coef, cs.diag};
+}
+__device__ __forceinline__ Slots<float> slots32(const CaseDev& cs) {
+  return Slots<float>{cs.N, cs.W, cs.slot_other, cs.slot_coef32, cs.diag32};
+}
+
+__device__ __forceinline__ double fmadd(double a, double b, double c) { return fma(a, b, c); }
+__device__ __forceinline__ float fmadd(float a, float b, float c) { return fmaf(a, b, c); }
+
+// Rows c and c2 of A v (diag * v_c, then the slots in order, fused multiply-adds), all loads
+// of both rows issued before any is used.
+template <int W, typename T>
+__device__ __forceinline__ void rows2(const Slots<T>& A, int c, int c2, const T* __restrict__ v, T& y, T& y2,
+                                      T& vc, T& vc2) {
+  const size_t N = (size_t)A.N;
   vc = v[c];
   vc2 = v[c2];
-  double acc = cs.diag[c] * vc, acc2 = cs.diag[c2] * vc2;
+  T acc = A.diag[c] * vc, acc2 = A.diag[c2] * vc2;
   if constexpr (W > 0) {
     int o[W], o2[W];
-    double u[W], u2[W];
+    T u[W], u2[W];
 #pragma unroll
     for (int k = 0; k < W; ++k) {
-      o[k] = __ldg(cs.slot_other + (size_t)k * N + c);
-      o2[k] = __ldg(cs.slot_other + (size_t)k * N + c2);
-      u[k] = cs.slot_coef[(size_t)k * N + c];
-      u2[k] = cs.slot_coef[(size_t)k * N + c2];
+      o[k] = __ldg(A.other + (size_t)k * N + c);
+      o2[k] = __ldg(A.other + (size_t)k * N + c2);
+      u[k] = A.coef[(size_t)k * N + c];
+      u2[k] = A.coef[(size_t)k * N + c2];
     }
 #pragma unroll
     for (int k = 0; k < W; ++k) {
-      acc = fma(u[k], v[o[k]], acc);
-      acc2 = fma(u2[k], v[o2[k]], acc2);
+      acc = fmadd(u[k], v[o[k]], acc);
+      acc2 = fmadd(u2[k], v[o2[k]], acc2);
     }
   } else {
-    const int ns = cs.W;
-    for (int k = 0; k < ns; ++k) {
+    for (int k = 0; k < A.W; ++k) {
       const size_t at = (size_t)k * N;
-      acc = fma(cs.slot_coef[at + c], v[__ldg(cs.slot_other + at + c)], acc);
-      acc2 = fma(cs.slot_coef[at + c2], v[__ldg(cs.slot_other + at + c2)], acc2);
+      acc = fmadd(A.coef[at + c], v[__ldg(A.other + at + c)], acc);
+      acc2 = fmadd(A.coef[at + c2], v[__ldg(A.other + at + c2)], acc2);
     }
   }
   y = acc;
   y2 = acc2;
 }
 
-template <int W>
-__device__ __forceinline__ double row_f64(const CaseDev& cs, int c, const double* __restrict__ v, double& vc) {
-  const size_t N = (size_t)cs.N;
-  const int ns = nslots<W>(cs);
+template <int W, typename T>
+__device__ __forceinline__ T row1(const Slots<T>& A, int c, const T* __restrict__ v, T& vc) {
+  const size_t N = (size_t)A.N;
+  const int ns = W > 0 ? W : A.W;
   vc = v[c];
-  double acc = cs.diag[c] * vc;
+  T acc = A.diag[c] * vc;
 #pragma unroll
   for (int k = 0; k < (W > 0 ? W : kMaxSlots); ++k) {
     if (W == 0 && k >= ns) break;
     const size_t at = (size_t)k * N + c;
-    acc = fma(cs.slot_coef[at], v[__ldg(cs.slot_other + at)], acc);
+    acc = fmadd(A.coef[at], v[__ldg(A.other + at)], acc);
   }
   return acc;
 }
 
-// ---- FP32 A v --------------------------------------------------------------------------
-template <int W>
-__device__ __forceinline__ void rows2_f32(const CaseDev& cs, int c, int c2, const float* __restrict__ v,
-                                          float& y, float& y2, float& vc, float& vc2) {
-  const size_t N = (size_t)cs.N;
-  vc = v[c];
-  vc2 = v[c2];
-  float acc = cs.diag32[c] * vc, acc2 = cs.diag32[c2] * vc2;
-  if constexpr (W > 0) {
-    int o[W], o2[W];
-    float u[W], u2[W];
-#pragma unroll
-    for (int k = 0; k < W; ++k) {
-      o[k] = __ldg(cs.slot_other + (size_t)k * N + c);
-      o2[k] = __ldg(cs.slot_other + (size_t)k * N + c2);
-      u[k] = cs.slot_coef32[(size_t)k * N + c];
-      u2[k] = cs.slot_coef32[(size_t)k * N + c2];
-    }
-#pragma unroll
-    for (int k = 0; k < W; ++k) {
-      acc = fmaf(u[k], v[o[k]], acc);
-      acc2 = fmaf(u2[k], v[o2[k]], acc2);
-    }
-  } else {
-    const int ns = cs.W;
-    for (int k = 0; k < ns; ++k) {
-      const size_t at = (size_t)k * N;
-      acc = fmaf(cs.slot_coef32[at + c], v[__ldg(cs.slot_other + at + c)], acc);
-      acc2 = fmaf(cs.slot_coef32[at + c2], v[__ldg(cs.slot_other + at + c2)], acc2);
-    }
+// ---- PCG iteration passes over the cells [c0, c1) of this CTA ---------------------------
+// Inlined into the step loop, where the array bases can stay kernel-parameter operands
+// (fewer registers held for addresses, more loads in flight). A thread takes cells c and
+// c + B per loop trip.
+
+// P: p = w + beta p.
+template <int B, typename T>
+__device__ __forceinline__ void pass_direction(int c0, int c1, T beta, T* __restrict__ p, const T* __restrict__ w) {
+  int c = c0 + (int)threadIdx.x;
+  for (; c + B < c1; c += 2 * B) {
+    const T p1 = p[c], p2 = p[c + B], w1 = w[c], w2 = w[c + B];
+    p[c] = fmadd(beta, p1, w1);
+    p[c + B] = fmadd(beta, p2, w2);
   }
-  y = acc;
-  y2 = acc2;
+  if (c < c1) p[c] = fmadd(beta, p[c], w[c]);
 }
 
-template <int W>
-__device__ __forceinline__ float row_f32(const CaseDev& cs, int c, const float* __restrict__ v, float& vc) {
-  const size_t N = (size_t)cs.N;
-  const int ns = nslots<W>(cs);
-  vc = v[c];
-  float acc = cs.diag32[c] * vc;
-#pragma unroll
-  for (int k = 0; k < (W > 0 ? W : kMaxSlots); ++k) {
-    if (W == 0 && k >= ns) break;
-    const size_t at = (size_t)k * N + c;
-    acc = fmaf(cs.slot_coef32[at], v[__ldg(cs.slot_other + at)], acc);
+// M (FP64): q = A p; returns this thread's share of p.q.
+template <int B, int W>
+__device__ __forceinline__ double pass_amul_dot_f64(Slots<double> A, int c0, int c1, const double* __restrict__ p,
+                                                 double* __restrict__ q) {
+  double s = 0.0;
+  int c = c0 + (int)threadIdx.x;
+  for (; c + B < c1; c += 2 * B) {
+    double y1, y2, pc1, pc2;
+    rows2<W>(A, c, c + B, p, y1, y2, pc1, pc2);
+    q[c] = y1;
+    q[c + B] = y2;
+    s = fma(y1, pc1, s);
+    s = fma(y2, pc2, s);
   }
-  return acc;
+  if (c < c1) {
+    double pc;
+    const double y = row1<W>(A, c, p, pc);
+    q[c] = y;
+    s = fma(y, pc, s);
+  }
+  return s;
+}
+
+// M (FP32): q = A p; returns this thread's share of p.q, accumulated exactly as FP32 pairs.
+template <int B, int W>
+__device__ __forceinline__ double pass_amul_dot_f32(Slots<float> A, int c0, int c1, const float* __restrict__ p,
+                                                 float* __restrict__ q) {
+  Acc2f sig;
+  int c = c0 + (int)threadIdx.x;
+  for (; c + B < c1; c += 2 * B) {
+    float y1, y2, pc1, pc2;
+    rows2<W>(A, c, c + B, p, y1, y2, pc1, pc2);
+    q[c] = y1;
+    q[c + B] = y2;
+    sig.add_prod(y1, pc1);
+    sig.add_prod(y2, pc2);
+  }
+  if (c < c1) {
+    float pc;
+    const float y = row1<W>(A, c, p, pc);
+    q[c] = y;
+    sig.add_prod(y, pc);
+  }
+  return sig.value();
+}
+
+// U (FP64): x += alpha p, r -= alpha q, w = rD r; returns this thread's sum|r| and w.r.
+template <int B>
+__device__ __forceinline__ double2 pass_update_f64(int c0, int c1, double alpha, double* __restrict__ x,
+                                                double* __restrict__ r, double* __restrict__ w,
+                                                const double* __restrict__ p, const double* __restrict__ q,
+                                                const double* __restrict__ rD) {
+  double sa = 0.0, sr = 0.0;
+  int c = c0 + (int)threadIdx.x;
+  for (; c + B < c1; c += 2 * B) {
+    const int e = c + B;
+    const double pa = p[c], pb = p[e], qa = q[c], qb = q[e];
+    const double xa = x[c], xb = x[e], ra = r[c], rb = r[e], da = rD[c], db = rD[e];
+    const double rna = fma(-alpha, qa, ra), rnb = fma(-alpha, qb, rb);
+    const double wa = da * rna, wb = db * rnb;
+    x[c] = fma(alpha, pa, xa);
+    x[e] = fma(alpha, pb, xb);
+    r[c] = rna;
+    r[e] = rnb;
+    w[c] = wa;
+    w[e] = wb;
+    sa += fabs(rna);
+    sa += fabs(rnb);
+    sr = fma(wa, rna, sr);
+    sr = fma(wb, rnb, sr);
+  }
+  if (c < c1) {
+    const double rn = fma(-alpha, q[c], r[c]);
+    const double wn = rD[c] * rn;
+    x[c] = fma(alpha, p[c], x[c]);
+    r[c] = rn;
+    w[c] = wn;
+    sa += fabs(rn);
+    sr = fma(wn, rn, sr);
+  }
+  return make_double2(sa, sr);
+}
+
+// U (FP32 inner solve): dx += a p, r -= a q, w = rD r; returns sum|r| and w.r, each
+// accumulated exactly as FP32 pairs.
+template <int B>
+__device__ __forceinline__ double2 pass_update_f32(int c0, int c1, float a32, float* __restrict__ dx,
+                                                float* __restrict__ r, float* __restrict__ w,
+                                                const float* __restrict__ p, const float* __restrict__ q,
+                                                const float* __restrict__ rD) {
+  Acc2f rsum, rho_n;
+  int c = c0 + (int)threadIdx.x;
+  for (; c + B < c1; c += 2 * B) {
+    const int e = c + B;
+    const float pa = p[c], pb = p[e], qa = q[c], qb = q[e];
+    const float xa = dx[c], xb = dx[e], ra = r[c], rb = r[e], da = rD[c], db = rD[e];
+    const float rna = fmaf(-a32, qa, ra), rnb = fmaf(-a32, qb, rb);
+    const float wa = da * rna, wb = db * rnb;
+    dx[c] = fmaf(a32, pa, xa);
+    dx[e] = fmaf(a32, pb, xb);
+    r[c] = rna;
+    r[e] = rnb;
+    w[c] = wa;
+    w[e] = wb;
+    rsum.add(fabsf(rna));
+    rsum.add(fabsf(rnb));
+    rho_n.add_prod(wa, rna);
+    rho_n.add_prod(wb, rnb);
+  }
+  if (c < c1) {
+    const float rn = fmaf(-a32, q[c], r[c]);
+    const float wn = rD[c] * rn;
+    dx[c] = fmaf(a32, p[c], dx[c]);
+    r[c] = rn;
+    w[c] = wn;
+    rsum.add(fabsf(rn));
+    rho_n.add_prod(wn, rn);
+  }
+  return make_double2(rsum.value(), rho_n.value());
+}
+
+// Three partial sums of a pass, per thread.
+struct Sums3 {
+  double a, b, c;
+};
+
+// A2 + I (FP64 step): the rows of the matrix and, from the same loaded row, r = b - A x,
+// the normFactor terms, sum|r|, w = rD r and rho; p = w. Returns this thread's normFactor
+// sum, sum|r| and rho.
+template <int B, int W>
+__device__ __noinline__ Sums3 pass_rows_init_f64(const CaseDev& cs, int c0, int c1, double xRef) {
+  double* __restrict__ r = cs.r;
+  double* __restrict__ p = cs.p;
+  const double* __restrict__ x = cs.x;
+  double u0 = 0.0, u1 = 0.0, u2 = 0.0;
+  for (int c = c0 + (int)threadIdx.x; c < c1; c += B) {
+    const Row o = assemble_row<W>(cs, c, x);
+    const double rd = store_row<false>(cs, c, o, false);
+    const double rc = o.s - o.ax;
+    u0 += fabs(fma(-o.sa, xRef, o.ax)) + fabs(fma(-o.sa, xRef, o.s));
+    u1 += fabs(rc);
+    const double wc = rd * rc;
+    u2 = fma(wc, rc, u2);
+    r[c] = rc;
+    p[c] = wc;
+  }
+  return Sums3{u0, u1, u2};
+}
+
+// T (mixed step): the FP64 true residual r = b - A x, rounded to FP32 to seed the inner
+// solve (r, w = rD r, p = w, dx = 0). With kFirst it is computed together with the rows of
+// the matrix (A2) and the normFactor terms. Returns this thread's normFactor sum (kFirst),
+// sum|r| and rho (FP32 terms accumulated exactly as FP32 pairs).
+template <int B, int W, bool kFirst>
+__device__ __noinline__ Sums3 pass_true_residual(const CaseDev& cs, int c0, int c1, double xRef) {
+  float* __restrict__ r = cs.r32;
+  float* __restrict__ w = cs.w32;
+  float* __restrict__ p = cs.p32;
+  float* __restrict__ dx = cs.dx32;
+  const double* __restrict__ x = cs.x;
+  double u0 = 0.0, u1 = 0.0;
+  Acc2f rho_acc;
+  for (int c = c0 + (int)threadIdx.x; c < c1; c += B) {
+    double rc;
+    float rd32;
+    if (kFirst) {
+      const Row o = assemble_row<W>(cs, c, x);
+      rd32 = (float)store_row<true>(cs, c, o, true);
+      u0 += fabs(fma(-o.sa, xRef, o.ax)) + fabs(fma(-o.sa, xRef, o.s));
+      rc = o.s - o.ax;
+    } else {
+      double xc;
+      rc = cs.src[c] - row1<W>(slots64(cs), c, x, xc);
+      rd32 = cs.rD32[c];
+    }
+    u1 += fabs(rc);
+    const float r32 = (float)rc;
+    const float w32 = rd32 * r32;
+    rho_acc.add_prod(w32, r32);
+    r[c] = r32;
+    w[c] = w32;
+    p[c] = w32;
+    dx[c] = 0.0f;
+  }
+  return Sums3{u0, u1, rho_acc.value()};
+}
+
+// x += dx (mixed step, FP64).
+template <int B>
+__device__ __forceinline__ void pass_correct(int c0, int c1, double* __restrict__ x, const float* __restrict__ dx) {
+  for (int c = c0 + (int)threadIdx.x; c < c1; c += B) x[c] += (double)dx[c];
 }
 
 // Wall time per phase kind, measured by the team's rank-0 thread between barrier exits
@@ -311,10 +540,12 @@ __device__ __forceinline__ void write_stats(const CaseDev& cs, const Team& tm, i
 // FP64 steps
 // =======================================================================================
 template <int B, int W>
-__device__ void run_steps_f64(const CaseDev& cs, const Team& tm, int n_steps, int mode, TeamShared& sh,
+__device__ void run_steps_f64(const CaseDev& cs, const CaseDev& cref, const Team& tm, int n_steps, int mode,
+                              TeamShared& sh,
                               int stats_base = 0) {
-  int c0, c1;
+  int c0, c1, f0, f1;
   cta_range(cs.N, tm.size, tm.rank, c0, c1);
+  cta_range(cs.F, tm.size, tm.rank, f0, f1);
   const int tid = threadIdx.x;
   double* __restrict__ x = cs.x;
   double* __restrict__ r = cs.r;
@@ -325,28 +556,17 @@ __device__ void run_steps_f64(const CaseDev& cs, const Team& tm, int n_steps, in
 
   PhaseClock clk(cs, tm);
   for (int step = 0; step < n_steps; ++step) {
-    // ---- A: assembly ---------------------------------------------------------------------
-    double v[1] = {0.0};
-    if (!assemble<B, W, false>(cs, tm, c0, c1, mode == kModeAssembleOnly, v[0], sh)) return;
+    // ---- A1: face coefficients, sum of T -------------------------------------------------
+    double v[1] = {pass_faces<B, false>(cref, f0, f1, c0, c1, mode == kModeAssembleOnly)};
     if (!team_allreduce<1>(tm, v, sh)) return;
     clk.lap(kPhAssembly);
-    if (mode == kModeAssembleOnly) return;
-    // ---- I: initial residual, normFactor, first direction -----------------------------
-    const double xRef = v[0] / (double)cs.N;
-    double u[3] = {0.0, 0.0, 0.0};  // normFactor sum, sum|r|, rho
-    for (int c = c0 + tid; c < c1; c += B) {
-      const double b = cs.src[c];
-      double xc;
-      const double ax = row_f64<W>(cs, c, x, xc);
-      const double rc = b - ax;
-      const double pA = cs.sumA[c] * xRef;
-      u[0] += fabs(ax - pA) + fabs(b - pA);
-      u[1] += fabs(rc);
-      const double wc = rD[c] * rc;
-      u[2] = fma(wc, rc, u[2]);
-      r[c] = rc;
-      p[c] = wc;
+    if (mode == kModeAssembleOnly) {
+      pass_rows_only<B, W, false>(cref, c0, c1);
+      return;
     }
+    // ---- A2 + I: rows of the matrix, initial residual, normFactor, first direction -------
+    const Sums3 ui = pass_rows_init_f64<B, W>(cref, c0, c1, v[0] / (double)cs.N);
+    double u[3] = {ui.a, ui.b, ui.c};  // normFactor sum, sum|r|, rho
     if (!team_allreduce<3>(tm, u, sh)) return;
     clk.lap(kPhInit);
     const double nf = u[0] + kSmall;
@@ -358,35 +578,12 @@ __device__ void run_steps_f64(const CaseDev& cs, const Team& tm, int n_steps, in
       for (;;) {
         if (iters > 0) {
           // ---- P: search direction -------------------------------------------------
-          int c = c0 + tid;
-          for (; c + B < c1; c += 2 * B) {
-            const double p1 = p[c], p2 = p[c + B], w1 = w[c], w2 = w[c + B];
-            p[c] = fma(beta, p1, w1);
-            p[c + B] = fma(beta, p2, w2);
-          }
-          if (c < c1) p[c] = fma(beta, p[c], w[c]);
+          pass_direction<B, double>(c0, c1, beta, p, w);
           if (!team_barrier(tm, sh)) return;
           clk.lap(kPhP);
         }
         // ---- M: q = A p, sigma = p.q ----------------------------------------------
-        double s1[1] = {0.0};
-        {
-          int c = c0 + tid;
-          for (; c + B < c1; c += 2 * B) {
-            double y1, y2, pc1, pc2;
-            rows2_f64<W>(cs, c, c + B, p, y1, y2, pc1, pc2);
-            q[c] = y1;
-            q[c + B] = y2;
-            s1[0] = fma(y1, pc1, s1[0]);
-            s1[0] = fma(y2, pc2, s1[0]);
-          }
-          if (c < c1) {
-            double pc;
-            const double y = row_f64<W>(cs, c, p, pc);
-            q[c] = y;
-            s1[0] = fma(y, pc, s1[0]);
-          }
-        }
+        double s1[1] = {pass_amul_dot_f64<B, W>(slots64(cs), c0, c1, p, q)};
         if (!team_allreduce<1>(tm, s1, sh)) return;
         clk.lap(kPhM);
         const double sigma = s1[0];
@@ -396,36 +593,8 @@ __device__ void run_steps_f64(const CaseDev& cs, const Team& tm, int n_steps, in
         }
         const double alpha = rho / sigma;
         // ---- U: update, residual, preconditioned residual, next rho ----------------
-        double s2[2] = {0.0, 0.0};
-        {
-          int c = c0 + tid;
-          for (; c + B < c1; c += 2 * B) {
-            const int e = c + B;
-            const double pa = p[c], pb = p[e], qa = q[c], qb = q[e];
-            const double xa = x[c], xb = x[e], ra = r[c], rb = r[e], da = rD[c], db = rD[e];
-            const double rna = fma(-alpha, qa, ra), rnb = fma(-alpha, qb, rb);
-            const double wa = da * rna, wb = db * rnb;
-            x[c] = fma(alpha, pa, xa);
-            x[e] = fma(alpha, pb, xb);
-            r[c] = rna;
-            r[e] = rnb;
-            w[c] = wa;
-            w[e] = wb;
-            s2[0] += fabs(rna);
-            s2[0] += fabs(rnb);
-            s2[1] = fma(wa, rna, s2[1]);
-            s2[1] = fma(wb, rnb, s2[1]);
-          }
-          if (c < c1) {
-            const double rn = fma(-alpha, q[c], r[c]);
-            const double wn = rD[c] * rn;
-            x[c] = fma(alpha, p[c], x[c]);
-            r[c] = rn;
-            w[c] = wn;
-            s2[0] += fabs(rn);
-            s2[1] = fma(wn, rn, s2[1]);
-          }
-        }
+        const double2 su = pass_update_f64<B>(c0, c1, alpha, x, r, w, p, q, rD);
+        double s2[2] = {su.x, su.y};
         if (!team_allreduce<2>(tm, s2, sh)) return;
         clk.lap(kPhU);
         res = s2[0] / nf;
@@ -453,10 +622,12 @@ __device__ void run_steps_f64(const CaseDev& cs, const Team& tm, int n_steps, in
 // Mixed-precision steps (FP32 inner CG inside FP64 defect correction)
 // =======================================================================================
 template <int B, int W>
-__device__ void run_steps_mixed(const CaseDev& cs, const Team& tm, int n_steps, int mode, TeamShared& sh,
+__device__ void run_steps_mixed(const CaseDev& cs, const CaseDev& cref, const Team& tm, int n_steps, int mode,
+                              TeamShared& sh,
                                 int stats_base = 0) {
-  int c0, c1;
+  int c0, c1, f0, f1;
   cta_range(cs.N, tm.size, tm.rank, c0, c1);
+  cta_range(cs.F, tm.size, tm.rank, f0, f1);
   const int tid = threadIdx.x;
   double* __restrict__ x = cs.x;
   float* __restrict__ dx = cs.dx32;
@@ -468,38 +639,23 @@ __device__ void run_steps_mixed(const CaseDev& cs, const Team& tm, int n_steps, 
 
   PhaseClock clk(cs, tm);
   for (int step = 0; step < n_steps; ++step) {
-    double v[1] = {0.0};
-    if (!assemble<B, W, true>(cs, tm, c0, c1, mode == kModeAssembleOnly, v[0], sh)) return;
+    double v[1] = {pass_faces<B, true>(cref, f0, f1, c0, c1, mode == kModeAssembleOnly)};
     if (!team_allreduce<1>(tm, v, sh)) return;
     clk.lap(kPhAssembly);
-    if (mode == kModeAssembleOnly) return;
+    if (mode == kModeAssembleOnly) {
+      pass_rows_only<B, W, true>(cref, c0, c1);
+      return;
+    }
     const double xRef = v[0] / (double)cs.N;
 
     double nf = 0.0, init_res = 0.0, res = 0.0;
     int iters = 0, sweeps = 0, status = 0;
     for (;;) {
-      // ---- T: FP64 true residual r = b - A x, seeded into the FP32 inner solve --------
-      double u[3] = {0.0, 0.0, 0.0};  // normFactor sum (first sweep), sum|r|, rho
-      Acc2f rho_acc;
-      for (int c = c0 + tid; c < c1; c += B) {
-        const double b = cs.src[c];
-        double xc;
-        const double ax = row_f64<W>(cs, c, x, xc);
-        const double rc = b - ax;
-        if (sweeps == 0) {
-          const double pA = cs.sumA[c] * xRef;
-          u[0] += fabs(ax - pA) + fabs(b - pA);
-        }
-        u[1] += fabs(rc);
-        const float r32 = (float)rc;
-        const float w32 = rD[c] * r32;
-        rho_acc.add_prod(w32, r32);
-        r[c] = r32;
-        w[c] = w32;
-        p[c] = w32;
-        dx[c] = 0.0f;
-      }
-      u[2] = rho_acc.value();
+      // ---- T: FP64 true residual r = b - A x, seeded into the FP32 inner solve; on the
+      //      first sweep computed together with pass 2 of the assembly and normFactor -----
+      const Sums3 ui = sweeps == 0 ? pass_true_residual<B, W, true>(cref, c0, c1, xRef)
+                                   : pass_true_residual<B, W, false>(cref, c0, c1, xRef);
+      double u[3] = {ui.a, ui.b, ui.c};  // normFactor sum (first sweep), sum|r|, rho
       if (!team_allreduce<3>(tm, u, sh)) return;
       clk.lap(kPhInit);
       if (sweeps == 0) {
@@ -521,37 +677,11 @@ __device__ void run_steps_mixed(const CaseDev& cs, const Team& tm, int n_steps, 
       int k = 0;
       for (;;) {
         if (k > 0) {
-          const float b32 = (float)beta;
-          int c = c0 + tid;
-          for (; c + B < c1; c += 2 * B) {
-            const float p1 = p[c], p2 = p[c + B], w1 = w[c], w2 = w[c + B];
-            p[c] = fmaf(b32, p1, w1);
-            p[c + B] = fmaf(b32, p2, w2);
-          }
-          if (c < c1) p[c] = fmaf(b32, p[c], w[c]);
+          pass_direction<B, float>(c0, c1, (float)beta, p, w);
           if (!team_barrier(tm, sh)) return;
           clk.lap(kPhP);
         }
-        double s1[1];
-        {
-          Acc2f sig;
-          int c = c0 + tid;
-          for (; c + B < c1; c += 2 * B) {
-            float y1, y2, pc1, pc2;
-            rows2_f32<W>(cs, c, c + B, p, y1, y2, pc1, pc2);
-            q[c] = y1;
-            q[c + B] = y2;
-            sig.add_prod(y1, pc1);
-            sig.add_prod(y2, pc2);
-          }
-          if (c < c1) {
-            float pc;
-            const float y = row_f32<W>(cs, c, p, pc);
-            q[c] = y;
-            sig.add_prod(y, pc);
-          }
-          s1[0] = sig.value();
-        }
+        double s1[1] = {pass_amul_dot_f32<B, W>(slots32(cs), c0, c1, p, q)};
         if (!team_allreduce<1>(tm, s1, sh)) return;
         clk.lap(kPhM);
         const double sigma = s1[0];
@@ -559,40 +689,8 @@ __device__ void run_steps_mixed(const CaseDev& cs, const Team& tm, int n_steps, 
           status = LFM_ESINGULAR;
           break;
         }
-        const float a32 = (float)(rho / sigma);
-        double s2[2];
-        {
-          Acc2f rsum, rho_n;
-          int c = c0 + tid;
-          for (; c + B < c1; c += 2 * B) {
-            const int e = c + B;
-            const float pa = p[c], pb = p[e], qa = q[c], qb = q[e];
-            const float xa = dx[c], xb = dx[e], ra = r[c], rb = r[e], da = rD[c], db = rD[e];
-            const float rna = fmaf(-a32, qa, ra), rnb = fmaf(-a32, qb, rb);
-            const float wa = da * rna, wb = db * rnb;
-            dx[c] = fmaf(a32, pa, xa);
-            dx[e] = fmaf(a32, pb, xb);
-            r[c] = rna;
-            r[e] = rnb;
-            w[c] = wa;
-            w[e] = wb;
-            rsum.add(fabsf(rna));
-            rsum.add(fabsf(rnb));
-            rho_n.add_prod(wa, rna);
-            rho_n.add_prod(wb, rnb);
-          }
-          if (c < c1) {
-            const float rn = fmaf(-a32, q[c], r[c]);
-            const float wn = rD[c] * rn;
-            dx[c] = fmaf(a32, p[c], dx[c]);
-            r[c] = rn;
-            w[c] = wn;
-            rsum.add(fabsf(rn));
-            rho_n.add_prod(wn, rn);
-          }
-          s2[0] = rsum.value();
-          s2[1] = rho_n.value();
-        }
+        const double2 su = pass_update_f32<B>(c0, c1, (float)(rho / sigma), dx, r, w, p, q, rD);
+        double s2[2] = {su.x, su.y};
         if (!team_allreduce<2>(tm, s2, sh)) return;
         clk.lap(kPhU);
         const double inner_res = s2[0] / nf;
@@ -609,7 +707,7 @@ __device__ void run_steps_mixed(const CaseDev& cs, const Team& tm, int n_steps, 
       }
       if (status != 0) break;
       // ---- x += dx (FP64) ------------------------------------------------------------
-      for (int c = c0 + tid; c < c1; c += B) x[c] += (double)dx[c];
+      pass_correct<B>(c0, c1, x, dx);
       if (!team_barrier(tm, sh)) return;
       clk.lap(kPhCorrect);
       ++sweeps;

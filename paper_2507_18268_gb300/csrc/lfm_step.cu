@@ -11,19 +11,25 @@ namespace {
 
 // ---- kernels ---------------------------------------------------------------------------
 template <int B, int W>
-__global__ void __launch_bounds__(B) step_kernel_f64(CaseDev cs, Launch L, int n_steps, int mode) {
+__global__ void __launch_bounds__(B, 1024 / B) step_kernel_f64(CaseDev cs, Launch L, int n_steps, int mode) {
   __shared__ TeamShared sh;
+  __shared__ CaseDev s_cs;  // addressable copy for the per-step passes
   if ((int)blockIdx.x == L.skip_cta) return;  // test hook: never arrive
+  if (threadIdx.x == 0) s_cs = cs;
+  __syncthreads();
   const Team tm{(int)gridDim.x, (int)blockIdx.x, cs.sync, cs.partials, L.timeout_ns};
-  run_steps_f64<B, W>(cs, tm, n_steps, mode, sh);
+  run_steps_f64<B, W>(cs, s_cs, tm, n_steps, mode, sh);
 }
 
 template <int B, int W>
-__global__ void __launch_bounds__(B) step_kernel_mixed(CaseDev cs, Launch L, int n_steps, int mode) {
+__global__ void __launch_bounds__(B, 1024 / B) step_kernel_mixed(CaseDev cs, Launch L, int n_steps, int mode) {
   __shared__ TeamShared sh;
+  __shared__ CaseDev s_cs;  // addressable copy for the per-step passes
   if ((int)blockIdx.x == L.skip_cta) return;
+  if (threadIdx.x == 0) s_cs = cs;
+  __syncthreads();
   const Team tm{(int)gridDim.x, (int)blockIdx.x, cs.sync, cs.partials, L.timeout_ns};
-  run_steps_mixed<B, W>(cs, tm, n_steps, mode, sh);
+  run_steps_mixed<B, W>(cs, s_cs, tm, n_steps, mode, sh);
 }
 
 __global__ void boundary_values_kernel(CaseDev cs, double* Tb) {

@@ -53,14 +53,16 @@ def percentile(xs, q):
 
 class Server:
     def __init__(self, device: int = 0, budget_bytes: float = 120e9, use_graph: bool = True,
-                 launch: Optional[tuple] = None):
-        import torch
-
+                 launch: Optional[tuple] = None, batch: Optional[Batch] = None):
         self.device = device
         self.budget = float(budget_bytes)
         self.use_graph = use_graph
-        self.stream = torch.cuda.Stream(device=device)
-        self.batch = Batch(device=device, stream=self.stream)
+        if batch is None:
+            import torch
+
+            self.stream = torch.cuda.Stream(device=device)
+            batch = Batch(device=device, stream=self.stream)
+        self.batch = batch
         if launch:
             self.batch.set_launch(*launch)
         self.meshes: Dict[tuple, Solver] = collections.OrderedDict()
@@ -82,11 +84,14 @@ class Server:
         self.used += owner.workspace_bytes
         return owner
 
-    def _evict_idle_meshes(self, need: float):
+    def _evict_idle_meshes(self, need: float, keep=None):
+        """Releases least recently used meshes that no admitted case shares (never `keep`,
+        the mesh of the request being admitted, which `need` assumes present) until `need`
+        more bytes fit."""
         for key in list(self.meshes):
             if self.used + need <= self.budget:
                 return
-            if self.mesh_users[key] == 0:
+            if self.mesh_users[key] == 0 and key != keep:
                 owner = self.meshes.pop(key)
                 self.used -= owner.workspace_bytes
                 owner.close()
@@ -120,7 +125,7 @@ class Server:
                 r = requests[pending[0]]
                 need = self._need(r.case)
                 if self.used + need > self.budget:
-                    self._evict_idle_meshes(need)
+                    self._evict_idle_meshes(need, keep=self._key(r.case))
                 if self.used + need > self.budget and active:
                     break
                 owner = self._mesh_for(r.case)

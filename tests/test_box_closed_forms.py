@@ -3,8 +3,9 @@
 ``lfm_box_layout`` runs the same per-cell routine as the device kernel behind
 ``lfm_upload_box``; its arrays must equal, bit for bit, what the general path produces for
 the same box: the numpy mesh builder, the counting-sort face addressing, the slot layout
-(neighbour-side faces ascending, owned faces ascending, padding) and the cell-side
-boundary lists. This also proves every index the kernel writes is in range.
+(neighbour-side faces ascending, owned faces ascending, padding), each face's slot in its
+owner's and its neighbour's row, and the cell-side boundary lists. This also proves every
+index the kernel writes is in range.
 """
 import numpy as np
 import pytest
@@ -22,20 +23,19 @@ def general_path(case):
     W = int(deg.max()) if N else 0
     so = np.empty(W * N, np.int32)
     sf = np.empty(W * N, np.int32)
-    sm = np.full(W * N, -1, np.int8)
+    fs = np.full(2 * F, 0xffffffff, np.uint32)
     for c in range(N):
-        slots = [(int(m.owner[f]), int(f), -1) for f in losort[lo_start[c]:lo_start[c + 1]]]
-        for f in range(own_start[c], own_start[c + 1]):
-            n = int(m.neighbour[f])
-            mate = list(losort[lo_start[n]:lo_start[n + 1]]).index(f)
-            slots.append((n, f, mate))
+        slots = [(int(m.owner[f]), int(f), 1) for f in losort[lo_start[c]:lo_start[c + 1]]]
+        slots += [(int(m.neighbour[f]), int(f), 0) for f in range(own_start[c], own_start[c + 1])]
         slots += [(c, -1, -1)] * (W - len(slots))
-        for k, (o, f, mt) in enumerate(slots):
-            so[k * N + c], sf[k * N + c], sm[k * N + c] = o, f, mt
+        for k, (o, f, side) in enumerate(slots):
+            so[k * N + c], sf[k * N + c] = o, f
+            if side >= 0:
+                fs[2 * f + side] = k * N + c
     counts = np.bincount(m.bface_cell, minlength=N)
     b_start = np.concatenate(([0], np.cumsum(counts))).astype(np.int32)
     b_face = np.argsort(m.bface_cell, kind="stable").astype(np.int32)
-    return dict(slot_other=so, slot_face=sf, slot_mate=sm, V=m.V, magSf=m.magSf, deltaCoeffs=m.deltaCoeffs, b_start=b_start,
+    return dict(slot_other=so, slot_face=sf, face_slots=fs, V=m.V, magSf=m.magSf, deltaCoeffs=m.deltaCoeffs, b_start=b_start,
                 b_face=b_face, bface_cell=m.bface_cell, bmagSf=m.bmagSf, bdeltaCoeffs=m.bdeltaCoeffs, W=W)
 
 
@@ -59,7 +59,7 @@ def test_box_layout_matches_general_path(shape, graded):
     ref = general_path(case)
     got = B.lfm_box_layout(case.xs, case.ys, case.zs)
     assert got["W"] == ref["W"]
-    for key in ("slot_other", "slot_face", "slot_mate", "V", "magSf", "deltaCoeffs", "b_start", "b_face", "bface_cell",
+    for key in ("slot_other", "slot_face", "face_slots", "V", "magSf", "deltaCoeffs", "b_start", "b_face", "bface_cell",
                 "bmagSf", "bdeltaCoeffs"):
         assert np.array_equal(got[key], ref[key]), key
 
