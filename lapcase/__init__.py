@@ -27,6 +27,20 @@ Face conventions every consumer must follow (they define the order of the LDU ar
 * boundary faces: grouped by patch in the order above; inside an x-patch faces run over
   (k, j) with j fastest, inside a y-patch over (k, i) with i fastest, inside a z-patch over
   (j, i) with i fastest.
+
+General (non-orthogonal) hexahedral boxes add ``points`` -- vertex coordinates of shape
+(nz+1, ny+1, nx+1, 3), vertex (i, j, k) at ``points[k, j, i]`` -- which replace the
+rectilinear geometry (xs, ys, zs then only give the cell counts), and ``n_nonorth_corr``,
+the number of extra non-orthogonal corrector passes per time step (OpenFOAM's
+nNonOrthogonalCorrectors). Such cases use natural numbering (no ``perm``). Face point order
+(it fixes each face's orientation): the +x face of cell (i, j, k) -- shared with (i+1, j, k)
+-- has the points at i+1 in the order (j, k), (j+1, k), (j+1, k+1), (j, k+1); the +y face
+the points at j+1 in the order (i, k), (i, k+1), (i+1, k+1), (i+1, k); the +z face the
+points at k+1 in the order (i, j), (i+1, j), (i+1, j+1), (i, j+1). A boundary face on a
+"1" patch (x1, y1, z1) uses the same order as the internal face in its direction; on a "0"
+patch the reverse cycle starting from the same first point (x0: (j, k), (j, k+1),
+(j+1, k+1), (j+1, k); y0: (i, k), (i+1, k), (i+1, k+1), (i, k+1); z0: (i, j), (i, j+1),
+(i+1, j+1), (i+1, j)), so that boundary normals point out of the domain.
 """
 from __future__ import annotations
 
@@ -66,6 +80,8 @@ class RawCase:
     min_iter: int = 0
     precision: int = FP64
     name: str = "case"
+    points: Optional[np.ndarray] = None
+    n_nonorth_corr: int = 0
 
     @property
     def nx(self) -> int:
@@ -241,3 +257,51 @@ def random_small_case(seed: int, nx: int = 4, ny: int = 4, nz: int = 4, permute:
     return RawCase(xs=xs, ys=ys, zs=zs, perm=perm, DT_uniform=DTu, DTx=DTx, DTy=DTy, DTz=DTz,
                    patches=patches, T0=T0, dt=float(_log_uniform(rng, 1e-3, 1.0)), n_steps=3,
                    tol=1e-12, rel_tol=0.0, name=f"small{seed}")
+
+
+# ---------------------------------------------------------------------------------------
+# General (non-orthogonal) hexahedral boxes
+# ---------------------------------------------------------------------------------------
+
+def box_points(xs: np.ndarray, ys: np.ndarray, zs: np.ndarray) -> np.ndarray:
+    """Vertex array (nz+1, ny+1, nx+1, 3) of the rectilinear box on the given axes."""
+    Z, Y, X = np.meshgrid(zs, ys, xs, indexing="ij")
+    return np.ascontiguousarray(np.stack([X, Y, Z], axis=-1), dtype=np.float64)
+
+
+def mapped_box(case: RawCase, M, shift=(0.0, 0.0, 0.0), n_nonorth_corr: int = 1) -> RawCase:
+    """The case's box mapped by the affine map p -> M p + shift (faces stay planar; cells
+    are parallelepipeds when M is not diagonal)."""
+    P = box_points(case.xs, case.ys, case.zs)
+    P = P @ np.asarray(M, dtype=np.float64).T + np.asarray(shift, dtype=np.float64)
+    return case.with_(points=np.ascontiguousarray(P), n_nonorth_corr=n_nonorth_corr, perm=None,
+                      name=case.name + "_mapped")
+
+
+def perturbed_box(case: RawCase, amp: float = 0.2, seed: int = 5, n_nonorth_corr: int = 1) -> RawCase:
+    """The case's box with every interior vertex moved along each axis by up to ``amp``
+    times the smaller adjacent cell width (seeded, uniform); boundary vertices stay, so the
+    faces inside the domain become warped quadrilaterals. amp < 0.5 keeps cells valid."""
+    rng = np.random.default_rng(seed)
+    P = box_points(case.xs, case.ys, case.zs)
+    shape = P.shape[:3]
+    interior = np.zeros(shape, dtype=bool)
+    interior[1:-1, 1:-1, 1:-1] = True
+    for a, v in enumerate((case.xs, case.ys, case.zs)):
+        w = np.zeros(len(v))
+        if len(v) > 2:
+            w[1:-1] = np.minimum(np.diff(v)[:-1], np.diff(v)[1:])
+        bshape = [1, 1, 1]
+        bshape[2 - a] = len(v)
+        P[..., a] += np.where(interior, amp * rng.uniform(-1.0, 1.0, shape) * w.reshape(bshape), 0.0)
+    return case.with_(points=np.ascontiguousarray(P), n_nonorth_corr=n_nonorth_corr, perm=None,
+                      name=case.name + "_perturbed")
+
+
+def skewed_box(n: int = 200, n_steps: int = 100, precision: int = FP64) -> RawCase:
+    """The graded n^3 box (graded200 for n=200) sheared by x' = x + 0.25 y + 0.15 z, with one
+    non-orthogonal corrector per step; DT, dt, boundary conditions and tolerances as the
+    graded box."""
+    base = graded_box(n, n_steps=n_steps, precision=precision)
+    M = [[1.0, 0.25, 0.15], [0.0, 1.0, 0.0], [0.0, 0.0, 1.0]]
+    return mapped_box(base, M, n_nonorth_corr=1).with_(name=f"skewed{n}")

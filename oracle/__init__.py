@@ -8,8 +8,10 @@ it shares nothing with the CUDA path except the seeded raw-case description from
 Paper passages followed (arXiv 2507.18268): Eq. (1) and the laplacianFoam listing (one
 ``fvm::ddt(T) - fvm::laplacian(DT, T)`` solve per step), the face addressing of section
 "OpenFOAM", the face-loop pattern of the listing "First cycle in the gradf routine", and the
-PCG + diagonal preconditioner named in section "Evaluation". The formulae the paper does
-not print are listed in ``oracle.c``'s header.
+PCG + diagonal preconditioner named in section "Evaluation"; for general hexahedral meshes
+the gradient passes of section "Code Porting" (listings "weights", "dotInterpolate", the
+two gradf cycles, the field division and correctBoundaryConditions) and the corrected
+laplacian. The formulae the paper does not print are listed in ``oracle.c``.
 """
 from __future__ import annotations
 
@@ -38,6 +40,10 @@ class _Box(ctypes.Structure):
     _fields_ = [("nx", ctypes.c_int32), ("ny", ctypes.c_int32), ("nz", ctypes.c_int32),
                 ("xs", _f64p), ("ys", _f64p), ("zs", _f64p), ("perm", _i64p),
                 ("DT_uniform", ctypes.c_double), ("DTx", _f64p), ("DTy", _f64p), ("DTz", _f64p)]
+
+
+class _Hex(ctypes.Structure):
+    _fields_ = [("nx", ctypes.c_int32), ("ny", ctypes.c_int32), ("nz", ctypes.c_int32), ("pts", _f64p)]
 
 
 class _Stats(ctypes.Structure):
@@ -93,6 +99,24 @@ def _load():
                                     ctypes.c_int32, ctypes.c_int32, _f64p, ctypes.POINTER(_Stats)]
         lib.ora_advance.restype = ctypes.c_int
         lib.ora_boundary_values.argtypes = [ctypes.c_int64, _i32p, _i32p, _f64p, _f64p, _f64p]
+        lib.ora_hex_counts.argtypes = [ctypes.POINTER(_Hex), _i64p, _i64p, _i64p]
+        lib.ora_hex_mesh.argtypes = [ctypes.POINTER(_Hex), _i32p, _i32p, _f64p, _f64p, _i32p, _i32p, _f64p,
+                                     _f64p, _f64p, _f64p]
+        lib.ora_hex_mesh.restype = ctypes.c_int
+        lib.ora_hex_coeffs.argtypes = [ctypes.c_int64, ctypes.c_int64, _i32p, _i32p, _f64p, _f64p, _f64p, _i32p,
+                                       _f64p, _f64p, _f64p, _f64p, _f64p, _f64p, _f64p, _f64p]
+        lib.ora_gauss_grad.argtypes = [ctypes.c_int64, ctypes.c_int64, ctypes.c_int64, _i32p, _i32p, _f64p,
+                                       _f64p, _f64p, _i32p, _f64p, _f64p, _f64p, _f64p]
+        lib.ora_gauss_grad.restype = ctypes.c_int
+        lib.ora_grad_boundary.argtypes = [ctypes.c_int64, _i32p, _f64p, _f64p, _i32p, _f64p, _f64p, _f64p,
+                                          _f64p]
+        lib.ora_advance_corrected.argtypes = [ctypes.c_int64, ctypes.c_int64, _i32p, _i32p, _f64p, _f64p,
+                                              _f64p, _f64p, _f64p, _f64p, _f64p, ctypes.c_int64, _i32p, _i32p,
+                                              _f64p, _f64p, _f64p, _f64p, _f64p, ctypes.c_double,
+                                              ctypes.c_int32, ctypes.c_int32, ctypes.c_double,
+                                              ctypes.c_double, ctypes.c_int32, ctypes.c_int32, _f64p,
+                                              ctypes.POINTER(_Stats)]
+        lib.ora_advance_corrected.restype = ctypes.c_int
         _lib = lib
     return _lib
 
@@ -120,6 +144,15 @@ class Mesh:
     bmagSf: np.ndarray
     bdelta: np.ndarray
     DTb: np.ndarray
+    # general hexahedral geometry (None for the rectilinear box); ``delta`` then holds the
+    # nonOrthDeltaCoeffs used by the implicit laplacian
+    Sf: Optional[np.ndarray] = None      # [F, 3] owner -> neighbour
+    Cf: Optional[np.ndarray] = None      # [F, 3]
+    C: Optional[np.ndarray] = None       # [N, 3]
+    w: Optional[np.ndarray] = None       # [F] interpolation weight of the owner value
+    corr: Optional[np.ndarray] = None    # [F, 3] non-orthogonal correction vectors
+    bSf: Optional[np.ndarray] = None     # [NB, 3] outward
+    bCf: Optional[np.ndarray] = None     # [NB, 3]
 
 
 def box_mesh(case: lapcase.RawCase) -> Mesh:
@@ -151,6 +184,78 @@ def box_mesh(case: lapcase.RawCase) -> Mesh:
     if rc != 0:
         raise MemoryError("oracle mesh build ran out of memory")
     return m
+
+
+def hex_mesh(case: lapcase.RawCase) -> Mesh:
+    """General hexahedral mesh of a case with ``points``: topology and per-face DT from the
+    box description (natural numbering), geometry and discretisation coefficients from the
+    vertex positions."""
+    if case.points is None:
+        raise ValueError("case has no vertex array")
+    if case.perm is not None:
+        raise ValueError("general hexahedral cases use natural numbering")
+    lib = _load()
+    base = box_mesh(case)  # topology, patches and per-face DT (its rectilinear geometry is unused)
+    pts = np.ascontiguousarray(case.points, dtype=np.float64)
+    if pts.shape != (case.nz + 1, case.ny + 1, case.nx + 1, 3):
+        raise ValueError("points must have shape (nz+1, ny+1, nx+1, 3)")
+    h = _Hex(case.nx, case.ny, case.nz, _p(pts, _f64p))
+    N, F, NB = base.n_cells, base.n_faces, base.n_bfaces
+    owner, neighbour = np.empty(F, np.int32), np.empty(F, np.int32)
+    Sf, Cf, bSf, bCf = np.empty((F, 3)), np.empty((F, 3)), np.empty((NB, 3)), np.empty((NB, 3))
+    bcell, bpatch = np.empty(NB, np.int32), np.empty(NB, np.int32)
+    V, C = np.empty(N), np.empty((N, 3))
+    rc = lib.ora_hex_mesh(ctypes.byref(h), _p(owner, _i32p), _p(neighbour, _i32p), _p(Sf, _f64p), _p(Cf, _f64p),
+                          _p(bcell, _i32p), _p(bpatch, _i32p), _p(bSf, _f64p), _p(bCf, _f64p), _p(V, _f64p),
+                          _p(C, _f64p))
+    if rc != 0:
+        raise MemoryError("oracle hex mesh ran out of memory")
+    assert np.array_equal(owner, base.owner) and np.array_equal(neighbour, base.neighbour)
+    assert np.array_equal(bcell, base.bcell) and np.array_equal(bpatch, base.bpatch)
+    w, magSf, nod, corr = np.empty(F), np.empty(F), np.empty(F), np.empty((F, 3))
+    bmagSf, bdelta = np.empty(NB), np.empty(NB)
+    lib.ora_hex_coeffs(F, NB, _p(owner, _i32p), _p(neighbour, _i32p), _p(Sf, _f64p), _p(Cf, _f64p), _p(C, _f64p),
+                       _p(bcell, _i32p), _p(bSf, _f64p), _p(bCf, _f64p), _p(w, _f64p), _p(magSf, _f64p),
+                       _p(nod, _f64p), _p(corr, _f64p), _p(bmagSf, _f64p), _p(bdelta, _f64p))
+    return Mesh(N, F, NB, owner, neighbour, V, magSf, nod, base.DTf, bcell, bpatch, bmagSf, bdelta, base.DTb,
+                Sf=Sf, Cf=Cf, C=C, w=w, corr=corr, bSf=bSf, bCf=bCf)
+
+
+def mesh_of(case: lapcase.RawCase) -> Mesh:
+    return hex_mesh(case) if case.points is not None else box_mesh(case)
+
+
+def gauss_grad(mesh: Mesh, T: np.ndarray, Tb: np.ndarray) -> np.ndarray:
+    """Gauss linear gradient [N, 3] of the cell field T with boundary-face values Tb."""
+    lib = _load()
+    T = np.ascontiguousarray(T, dtype=np.float64)
+    Tb = np.ascontiguousarray(Tb, dtype=np.float64)
+    G = np.empty((mesh.n_cells, 3))
+    rc = lib.ora_gauss_grad(mesh.n_cells, mesh.n_faces, mesh.n_bfaces, _p(mesh.owner, _i32p),
+                            _p(mesh.neighbour, _i32p), _p(mesh.Sf, _f64p), _p(mesh.w, _f64p), _p(mesh.V, _f64p),
+                            _p(mesh.bcell, _i32p), _p(mesh.bSf, _f64p), _p(Tb, _f64p), _p(T, _f64p), _p(G, _f64p))
+    if rc != 0:
+        raise MemoryError("oracle gradient ran out of memory")
+    return G
+
+
+def grad_boundary(mesh: Mesh, btype: np.ndarray, bvalue: np.ndarray, T: np.ndarray, G: np.ndarray) -> np.ndarray:
+    """Boundary-face values [NB, 3] of the gradient after correctBoundaryConditions."""
+    lib = _load()
+    T = np.ascontiguousarray(T, dtype=np.float64)
+    G = np.ascontiguousarray(G, dtype=np.float64)
+    Gb = np.empty((mesh.n_bfaces, 3))
+    lib.ora_grad_boundary(mesh.n_bfaces, _p(mesh.bcell, _i32p), _p(mesh.bSf, _f64p), _p(mesh.bdelta, _f64p),
+                          _p(btype, _i32p), _p(bvalue, _f64p), _p(T, _f64p), _p(G, _f64p), _p(Gb, _f64p))
+    return Gb
+
+
+def grad(case: lapcase.RawCase, mesh: Mesh, T: np.ndarray):
+    """Gauss linear gradient of T with the case's boundary conditions: (cells [N, 3],
+    boundary faces [NB, 3])."""
+    btype, bvalue = boundary_types_values(case, mesh)
+    G = gauss_grad(mesh, T, boundary_values(case, mesh, T))
+    return G, grad_boundary(mesh, btype, bvalue, T, G)
 
 
 def boundary_types_values(case: lapcase.RawCase, mesh: Mesh):
@@ -223,11 +328,22 @@ def advance(case: lapcase.RawCase, n_steps: Optional[int] = None, mesh: Optional
             T: Optional[np.ndarray] = None):
     """Runs ``n_steps`` (default: the case's) implicit steps. Returns (T by label, [Stats])."""
     lib = _load()
-    mesh = mesh or box_mesh(case)
+    mesh = mesh or mesh_of(case)
     n_steps = case.n_steps if n_steps is None else n_steps
     btype, bvalue = boundary_types_values(case, mesh)
     T = initial_field(case) if T is None else np.array(T, dtype=np.float64, copy=True)
     stats = (_Stats * max(n_steps, 1))()
+    if mesh.Sf is not None:
+        rc = lib.ora_advance_corrected(
+            mesh.n_cells, mesh.n_faces, _p(mesh.owner, _i32p), _p(mesh.neighbour, _i32p), _p(mesh.V, _f64p),
+            _p(mesh.magSf, _f64p), _p(mesh.delta, _f64p), _p(mesh.DTf, _f64p), _p(mesh.Sf, _f64p),
+            _p(mesh.w, _f64p), _p(mesh.corr, _f64p), mesh.n_bfaces, _p(mesh.bcell, _i32p), _p(btype, _i32p),
+            _p(bvalue, _f64p), _p(mesh.bmagSf, _f64p), _p(mesh.bdelta, _f64p), _p(mesh.DTb, _f64p),
+            _p(mesh.bSf, _f64p), float(case.dt), int(n_steps), int(case.n_nonorth_corr), float(case.tol),
+            float(case.rel_tol), int(case.max_iter), int(case.min_iter), _p(T, _f64p), stats)
+        if rc != 0:
+            raise MemoryError("oracle advance ran out of memory")
+        return T, [_stats(stats[i]) for i in range(n_steps)]
     rc = lib.ora_advance(mesh.n_cells, mesh.n_faces, _p(mesh.owner, _i32p), _p(mesh.neighbour, _i32p),
                          _p(mesh.V, _f64p), _p(mesh.magSf, _f64p), _p(mesh.delta, _f64p),
                          _p(mesh.DTf, _f64p), mesh.n_bfaces, _p(mesh.bcell, _i32p), _p(btype, _i32p),
