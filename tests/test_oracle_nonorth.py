@@ -209,3 +209,13 @@ def test_correction_reduces_the_steady_state_error_on_a_perturbed_mesh():
     err_corr = np.max(np.abs(T_corr - exact))
     err_plain = np.max(np.abs(T_plain - exact))
     assert err_corr < 0.5 * err_plain
+
+
+def test_correction_vectors_are_tangential_to_the_faces():
+    # the over-relaxed split Sf = |Sf| (d / (n.d) + k): the implicit part runs along d and
+    # the explicit correction vector k lies in the face plane
+    case = lapcase.perturbed_box(graded_case(4, 5, 3, seed=9), amp=0.3)
+    m = oracle.hex_mesh(case)
+    n = m.Sf / m.magSf[:, None]
+    assert np.max(np.abs(np.einsum("fi,fi->f", m.corr, n))) < 1e-12
+    assert np.max(np.linalg.norm(m.corr, axis=1)) > 1e-2
