@@ -204,7 +204,7 @@ def reference_slab_case() -> lapcase.RawCase:
 
 def run_cpu_oracle(case, n_steps: int, warmup: int = 0):
     import oracle
-    mesh = oracle.box_mesh(case)
+    mesh = oracle.mesh_of(case)
     T = oracle.initial_field(case)
     if warmup:
         T, _ = oracle.advance(case, n_steps=warmup, mesh=mesh, T=T)
@@ -380,6 +380,96 @@ def main_ours(args, world, rank, local):
     print(json.dumps(line), flush=True)
 
 
+SKEWED = ("skewed200: graded200 sheared by x' = x + 0.25 y + 0.15 z (8.0M parallelepiped cells, 23.88M "
+          "internal faces, up to 16 degrees non-orthogonal), corrected laplacian with 1 non-orthogonal "
+          "corrector per step (2 assemble-and-solve passes), DT, dt, BCs and PCG controls as graded200")
+
+
+def algorithmic_bytes_corrected(N: int, F: int, iters: int, passes: int) -> float:
+    """Minimum DRAM bytes of the corrected FP64 step: per PCG iteration as the orthogonal
+    step (112 N + 16 F); per assemble-and-solve pass the orthogonal assembly and initial
+    residual (88 N + 32 F) plus the Gauss gradient (T, Sf, w in; G out: 32 N + 32 F) and the
+    correction flux (G, k, w, |Sf| in; flux out, read back by the rows: 24 N + 56 F)."""
+    return float(iters) * (112 * N + 16 * F) + float(passes) * ((88 + 32 + 24) * N + (32 + 32 + 56) * F)
+
+
+def main_skewed(args, world, rank, local):
+    """The non-orthogonal workload: device-resident FP64 and mixed, the oracle on a slab."""
+    import torch
+
+    from paper_2507_18268_gb300 import Solver
+    from paper_2507_18268_gb300 import binding as B
+    from paper_2507_18268_gb300.mesh import hex_mesh
+
+    torch.cuda.set_device(local)
+    K = args.steps if args.steps_given else 20
+    W = args.warmup
+    case = lapcase.skewed_box(200)
+    mesh, geo = hex_mesh(case)
+    N, F = mesh.n_cells, mesh.n_faces
+    stream = torch.cuda.Stream(device=local)
+    hbm_peak, peak_kind = load_peaks()
+    s64 = Solver.from_case(case, mesh=mesh, geometry=geo, device=local, stream=stream)
+    s64.advance(W)
+    clocks = ClockSampler(local)
+    barrier(world)
+    torch.cuda.synchronize()
+    if rank == 0:
+        clocks.start()
+    secs, st = time_device_resident(s64, B, torch, stream, K)
+    barrier(world)
+    clk = clocks.stop() if rank == 0 else None
+    assert all(x["converged"] for x in st), "corrected FP64 step did not converge"
+    iters = sum(x["iters"] for x in st)
+    passes = K * (1 + case.n_nonorth_corr)
+    phases = {k: v / K for k, v in s64.phase_times().items()}
+    secs_max = reduce_max(secs, world)
+    value = reduce_sum(float(N) * iters, world) / secs_max
+    alg = algorithmic_bytes_corrected(N, F, iters, passes)
+    T64 = s64.field()
+    launch = s64.launch()
+    s64.close()
+    mixed = None
+    if not args.no_mixed:
+        smx = Solver.from_case(case.with_(precision=B.LFM_MIXED), mesh=mesh, geometry=geo, device=local,
+                               stream=stream)
+        smx.advance(W)
+        msecs, mst = time_device_resident(smx, B, torch, stream, K)
+        miters = sum(x["iters"] for x in mst)
+        Tm = smx.field()
+        smx.close()
+        msecs_max = reduce_max(msecs, world)
+        mixed = {"value": reduce_sum(float(N) * miters, world) / msecs_max, "unit": UNIT,
+                 "ms_per_step": 1e3 * msecs_max / K, "iters_per_step": miters / K,
+                 "converged": all(x["converged"] for x in mst),
+                 "max_rel_diff_vs_fp64": float(np.max(np.abs(Tm - T64) / np.abs(T64)))}
+    cpu = None
+    if rank == 0 and not args.no_cpu_baseline:
+        slab = case.with_(zs=lapcase.uniform_axis(200)[:26].copy(),
+                          points=np.ascontiguousarray(case.points[:26]), name="skewed200_slab25")
+        cval, csecs, citers = run_cpu_oracle(slab, 10)
+        cpu = {"value": cval, "unit": UNIT, "cores": 1, "kind": "oracle",
+               "sample": f"serial FP64 oracle, 10 steps (20 corrected passes) of a 200x200x25 slab of skewed200 "
+                         f"({slab.n_cells} cells, {citers} PCG iterations, {csecs:.1f} s)"}
+    if rank != 0:
+        return
+    print(json.dumps({
+        "metric": METRIC, "value": value, "unit": UNIT, "n_gpus": world, "steps": K, "warmup": W,
+        "ms_per_step": 1e3 * secs_max / K, "higher_is_better": True, "scaling": "weak", "vs_baseline": None,
+        "dtype": "f64", "data": "synthetic",
+        "config": {"workload": SKEWED, "cells": N, "internal_faces": F, "precision": "fp64",
+                   "parallelism": f"replicas x{world}" if world > 1 else "single GPU",
+                   "l2": "inputs larger than L2; no flush", "launch": {"ctas": launch[0], "threads": launch[1]}},
+        "iters_per_step": iters / K, "passes_per_step": 1 + case.n_nonorth_corr,
+        "phases_ms_per_step": phases,
+        "roofline": {"bound": "hbm", "achieved": alg / secs / 1e9, "peak": hbm_peak, "unit": "GB/s",
+                     "frac": alg / secs / 1e9 / hbm_peak, "traffic": None, "peak_kind": peak_kind,
+                     "kernel": "step_kernel_f64", "per": "one step (one launch runs all timed steps)"},
+        "gpu_launches": 1, "clocks": clk, "mixed": mixed, "cpu_baseline": cpu,
+        "e2e": None,
+    }), flush=True)
+
+
 def main_mixed_only(args, world, rank, local, case, mesh, stream):
     """Profiling mode: the mixed form alone (one warm-up launch, one timed launch)."""
     import torch
@@ -542,7 +632,7 @@ def main():
     ap.add_argument("--no-mixed", action="store_true")
     ap.add_argument("--no-e2e", action="store_true")
     ap.add_argument("--no-cpu-baseline", action="store_true")
-    ap.add_argument("--workload", choices=["graded200", "batch512", "serve"], default="graded200")
+    ap.add_argument("--workload", choices=["graded200", "batch512", "serve", "skewed200"], default="graded200")
     ap.add_argument("--batch-cases", type=int, default=512)
     ap.add_argument("--requests", type=int, default=1000)
     ap.add_argument("--only", choices=["fp64", "mixed"], default=None,
@@ -562,6 +652,8 @@ def main():
             main_batch(args, world, rank, local)
         elif args.workload == "serve":
             main_serve(args, world, rank, local)
+        elif args.workload == "skewed200":
+            main_skewed(args, world, rank, local)
         else:
             main_ours(args, world, rank, local)
     finally:

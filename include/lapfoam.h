@@ -72,6 +72,28 @@ typedef struct {
   const double *bmagSf, *bdeltaCoeffs;
 } lfm_mesh;
 
+/*
+ * Geometry of a general (non-orthogonal) hexahedral or polyhedral mesh, for the corrected
+ * laplacian and the Gauss linear gradient (section "Code Porting" of the paper: the
+ * interpolation weights, dotInterpolate, the two gradf cycles, the division by the cell
+ * volume and correctBoundaryConditions).
+ *   Sf[3*n_faces]        internal face area vectors (x, y, z per face), owner -> neighbour;
+ *                        |Sf| must equal the mesh's magSf (relative 1e-9);
+ *   weights[n_faces]     linear-interpolation weight of the owner value, in [0, 1]: the
+ *                        face value is w (T_P - T_N) + T_N;
+ *   corr_vec[3*n_faces]  non-orthogonal correction vectors k = Sf/|Sf| - d * deltaCoeffs
+ *                        (d = C_N - C_P);
+ *   bSf[3*n_bfaces]      boundary face area vectors, pointing out of the domain.
+ * With it the mesh's deltaCoeffs are the implicit (non-orthogonal) coefficients
+ * 1 / max(n.d, 0.05 |d|) and bdeltaCoeffs the inverse patch-normal distances. The laplacian
+ * of every assembly then adds the explicit flux DT |Sf| k . (w (G_P - G_N) + G_N), G the
+ * Gauss gradient of the current T, to the source (boundary faces carry no correction).
+ * Host memory, float64; copied at upload.
+ */
+typedef struct {
+  const double *Sf, *weights, *corr_vec, *bSf;
+} lfm_geometry;
+
 /* PCG controls. tol: stop when sum|r| / normFactor < tol; rel_tol > 0 also stops when the
  * residual falls below rel_tol times the step's initial residual; max_iter caps and
  * min_iter forces iterations (OpenFOAM defaults: 1000, 0). precision: LFM_FP64 or
@@ -85,7 +107,10 @@ typedef struct {
 /* Per-step solver record. iters: PCG iterations (LFM_MIXED: inner FP32 iterations summed
  * over the refinement sweeps); sweeps: LFM_MIXED refinement sweeps (LFM_FP64: 1, or 0 when
  * the step needed no iteration); init_res / final_res: normFactor-scaled L1 residuals
- * (LFM_MIXED: of the FP64 true residual b - A T). */
+ * (LFM_MIXED: of the FP64 true residual b - A T). With non-orthogonal correctors (see
+ * lfm_set_nonorth_correctors) a step runs several assemble-and-solve passes: iters and
+ * sweeps are summed over them, init_res and norm_factor are the first pass's, final_res
+ * and converged the last pass's. */
 typedef struct {
   int32_t iters, converged, sweeps, status;
   double init_res, final_res, norm_factor;
@@ -147,11 +172,35 @@ int lfm_create(lfm_ctx **out, int device, void *cuda_stream);
  * library never frees it. */
 int lfm_bind_workspace(lfm_ctx *ctx, void *dev_ptr, size_t bytes, int32_t precision);
 
+/* Device bytes lfm_upload_mesh_geometry needs (the general-geometry arrays, and per case
+ * the gradient [3N] and correction flux [F]); precision as for lfm_workspace_bytes. */
+size_t lfm_workspace_bytes_geometry(const lfm_mesh *mesh, int32_t precision);
+
 /* Validates and uploads the mesh (deep copy), builds the face-to-cell addressing and the
  * cell-side boundary-face lists. Resets DT to 0, every patch to zeroGradient, dt to 1,
  * the solver to {1e-6, 0, 1000, 0, LFM_FP64} and T to 0. LFM_EINVAL also when a cell has
  * more than 32 internal faces or (largest internal faces of a cell) x n_cells >= 2^32. */
 int lfm_upload_mesh(lfm_ctx *ctx, const lfm_mesh *mesh);
+
+/* As lfm_upload_mesh, for a general (non-orthogonal) mesh: also uploads `geometry` and
+ * switches the laplacian to its corrected form. LFM_EINVAL when the geometry is
+ * inconsistent with the mesh (see lfm_geometry). */
+int lfm_upload_mesh_geometry(lfm_ctx *ctx, const lfm_mesh *mesh, const lfm_geometry *geometry);
+
+/* Number of extra non-orthogonal corrector passes per time step (OpenFOAM's
+ * nNonOrthogonalCorrectors; laplacianFoam's listing loops over them): every step assembles
+ * and solves 1 + n_corr times, each pass with the explicit correction from the latest T and
+ * the ddt source from T at the start of the step. 0 after upload; 0..64. Allowed on any
+ * mesh (on an orthogonal one the correction is zero and the extra passes re-solve). */
+int lfm_set_nonorth_correctors(lfm_ctx *ctx, int32_t n_corr);
+
+/* Gauss linear gradient of the current T (section "Code Porting": face values by linear
+ * interpolation or the boundary values, the Gauss sum over internal and boundary faces,
+ * division by V): grad[3*n_cells] (x, y, z per cell) to host memory; bgrad[3*n_bfaces]
+ * (may be NULL) receives the boundary values after correctBoundaryConditions (the cell's
+ * gradient with its normal component replaced by the patch snGrad). LFM_ESTATE without
+ * general geometry or with an advance pending. */
+int lfm_grad(lfm_ctx *ctx, double *grad, double *bgrad);
 
 /* Builds a box mesh (see lfm_box_counts) directly on the device -- the same arrays as
  * uploading the equivalent LDU mesh with lfm_upload_mesh, from closed forms, one thread

@@ -42,6 +42,11 @@ class lfm_mesh(ctypes.Structure):
                 ("bmagSf", POINTER(c_double)), ("bdeltaCoeffs", POINTER(c_double))]
 
 
+class lfm_geometry(ctypes.Structure):
+    _fields_ = [("Sf", POINTER(c_double)), ("weights", POINTER(c_double)), ("corr_vec", POINTER(c_double)),
+                ("bSf", POINTER(c_double))]
+
+
 class lfm_solver_opts(ctypes.Structure):
     _fields_ = [("tol", c_double), ("rel_tol", c_double), ("max_iter", c_int32),
                 ("min_iter", c_int32), ("precision", c_int32)]
@@ -62,6 +67,10 @@ _SIGS = {
     "lfm_face_addressing": ([c_int32, c_int32, POINTER(c_int32), POINTER(c_int32), POINTER(c_int32),
                              POINTER(c_int32), POINTER(c_int32)], c_int),
     "lfm_workspace_bytes": ([POINTER(lfm_mesh), c_int32], c_size_t),
+    "lfm_workspace_bytes_geometry": ([POINTER(lfm_mesh), c_int32], c_size_t),
+    "lfm_upload_mesh_geometry": ([_ctx_p, POINTER(lfm_mesh), POINTER(lfm_geometry)], c_int),
+    "lfm_set_nonorth_correctors": ([_ctx_p, c_int32], c_int),
+    "lfm_grad": ([_ctx_p, POINTER(c_double), POINTER(c_double)], c_int),
     "lfm_create": ([POINTER(_ctx_p), c_int, c_void_p], c_int),
     "lfm_bind_workspace": ([_ctx_p, c_void_p, c_size_t, c_int32], c_int),
     "lfm_upload_mesh": ([_ctx_p, POINTER(lfm_mesh)], c_int),
@@ -233,6 +242,40 @@ def lfm_bind_workspace(ctx, dev_ptr: int, nbytes: int, precision: int = LFM_BOTH
 def lfm_upload_mesh(ctx, mesh):
     args = MeshArgs(mesh)
     _check(load().lfm_upload_mesh(ctx, ctypes.byref(args.struct)), ctx)
+
+
+class GeometryArgs:
+    """Keeps the arrays of an ``lfm_geometry`` alive while the struct is in use."""
+
+    def __init__(self, g):
+        self.arrays = dict(Sf=_f64(g.Sf), weights=_f64(g.weights), corr_vec=_f64(g.corr_vec), bSf=_f64(g.bSf))
+        a = self.arrays
+        self.struct = lfm_geometry(_ptr(a["Sf"], c_double), _ptr(a["weights"], c_double),
+                                   _ptr(a["corr_vec"], c_double), _ptr(a["bSf"], c_double))
+
+
+def lfm_workspace_bytes_geometry(mesh, precision: int = LFM_BOTH) -> int:
+    args = MeshArgs(mesh)
+    return int(load().lfm_workspace_bytes_geometry(ctypes.byref(args.struct), precision))
+
+
+def lfm_upload_mesh_geometry(ctx, mesh, geometry):
+    """``geometry``: an object with Sf [F, 3], weights [F], corr_vec [F, 3], bSf [NB, 3]."""
+    args = MeshArgs(mesh)
+    gargs = GeometryArgs(geometry)
+    _check(load().lfm_upload_mesh_geometry(ctx, ctypes.byref(args.struct), ctypes.byref(gargs.struct)), ctx)
+
+
+def lfm_set_nonorth_correctors(ctx, n_corr: int):
+    _check(load().lfm_set_nonorth_correctors(ctx, int(n_corr)), ctx)
+
+
+def lfm_grad(ctx, n_cells: int, n_bfaces: int, boundary: bool = True):
+    """Gauss gradient of the current T: (cells [N, 3], boundary faces [NB, 3] or None)."""
+    G = np.empty((n_cells, 3))
+    Gb = np.empty((max(n_bfaces, 1), 3)) if boundary else None
+    _check(load().lfm_grad(ctx, _ptr(G, c_double), _ptr(Gb, c_double) if boundary else None), ctx)
+    return G, (Gb[:n_bfaces] if boundary else None)
 
 
 def lfm_box_counts(nx: int, ny: int, nz: int):

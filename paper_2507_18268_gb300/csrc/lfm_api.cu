@@ -36,7 +36,8 @@ struct Layout {
   size_t sync, partials, stats;
   size_t slot_other, slot_face, face_slots, b_start, b_face, bcell, btype;
   size_t V, magSf, delta, DT, bmagSf, bdelta, bDT, bval;
-  size_t diag, upper, slot_coef, src, rD, vdt, x, r, w, p, q, Tb;
+  size_t diag, upper, slot_coef, src, rD, vdt, x, x_old, r, w, p, q, Tb;
+  size_t Sf, fw, corr, bSf, grad, cflux;  // general geometry (0 when absent)
   size_t diag32, slot_coef32, rD32, dx32, r32, w32, p32, q32;
   size_t total;
 };
@@ -46,7 +47,9 @@ struct Layout {
 constexpr int kLayoutBoth = -1;
 
 // shared_mesh: the mesh arrays (slots, boundary lists, geometry) live in another context.
-Layout make_layout(int64_t N, int64_t F, int64_t NB, int64_t W, int kind, bool shared_mesh = false) {
+// geom: general (non-orthogonal) geometry arrays and the per-case gradient / correction flux.
+Layout make_layout(int64_t N, int64_t F, int64_t NB, int64_t W, int kind, bool shared_mesh = false,
+                   bool geom = false) {
   Layout L{};
   size_t o = 0;
   auto take = [&](size_t bytes) {
@@ -69,6 +72,16 @@ Layout make_layout(int64_t N, int64_t F, int64_t NB, int64_t W, int kind, bool s
     L.delta = take(8 * F);
     L.bmagSf = take(8 * NB);
     L.bdelta = take(8 * NB);
+    if (geom) {
+      L.Sf = take(24 * F);
+      L.fw = take(8 * F);
+      L.corr = take(24 * F);
+      L.bSf = take(24 * NB);
+    }
+  }
+  if (geom) {
+    L.grad = take(24 * N);
+    L.cflux = take(8 * F);
   }
   L.btype = take(4 * NB);
   L.DT = take(8 * F);
@@ -81,6 +94,7 @@ Layout make_layout(int64_t N, int64_t F, int64_t NB, int64_t W, int kind, bool s
   L.rD = take(8 * N);
   L.vdt = take(8 * N);
   L.x = take(8 * N);
+  L.x_old = take(8 * N);
   L.Tb = take(8 * NB);
   L.r = L.w = L.p = L.q = 0;
   L.diag32 = L.slot_coef32 = L.rD32 = L.dx32 = L.r32 = L.w32 = L.p32 = L.q32 = 0;
@@ -144,6 +158,8 @@ struct lfm_ctx {
   double dt = 1.0;
   lfm_solver_opts opts{1e-6, 0.0, 1000, 0, LFM_FP64};
   bool has64 = false, has32 = false;  // solver blocks present in the workspace
+  bool has_geom = false;              // general geometry uploaded (corrected laplacian)
+  int32_t n_corr = 0;                 // non-orthogonal corrector passes per step
 
   // launch
   int tuned_ctas = 1, tuned_threads = 512;
@@ -241,6 +257,32 @@ int check_mesh(const lfm_mesh* m, std::string& why) {
   return LFM_OK;
 }
 
+// Geometry of a general mesh: finite values, weights in [0, 1], |Sf| consistent with magSf.
+int check_geometry(const lfm_mesh* m, const lfm_geometry* g, std::string& why) {
+  if ((m->n_faces > 0 && (!g->Sf || !g->weights || !g->corr_vec)) || (m->n_bfaces > 0 && !g->bSf))
+    return set_why(why, "geometry arrays missing");
+  for (int64_t f = 0; f < m->n_faces; ++f) {
+    const double* s = g->Sf + 3 * f;
+    const double* k = g->corr_vec + 3 * f;
+    const double w = g->weights[f];
+    if (!(std::isfinite(w) && w >= 0.0 && w <= 1.0)) return set_why(why, "weights[%lld] not in [0, 1]", (long long)f);
+    for (int d = 0; d < 3; ++d)
+      if (!std::isfinite(s[d]) || !std::isfinite(k[d])) return set_why(why, "face %lld: Sf or corr_vec not finite", (long long)f);
+    const double mag = std::sqrt(s[0] * s[0] + s[1] * s[1] + s[2] * s[2]);
+    if (!(std::fabs(mag - m->magSf[f]) <= 1e-9 * m->magSf[f]))
+      return set_why(why, "face %lld: |Sf| = %g differs from magSf = %g", (long long)f, mag, m->magSf[f]);
+  }
+  for (int64_t b = 0; b < m->n_bfaces; ++b) {
+    const double* s = g->bSf + 3 * b;
+    for (int d = 0; d < 3; ++d)
+      if (!std::isfinite(s[d])) return set_why(why, "boundary face %lld: bSf not finite", (long long)b);
+    const double mag = std::sqrt(s[0] * s[0] + s[1] * s[1] + s[2] * s[2]);
+    if (!(std::fabs(mag - m->bmagSf[b]) <= 1e-9 * m->bmagSf[b]))
+      return set_why(why, "boundary face %lld: |bSf| differs from bmagSf", (long long)b);
+  }
+  return LFM_OK;
+}
+
 // Counting sort by key (stable): start[k] .. start[k+1] index the items with key k, in
 // ascending item order.
 void bucket(int32_t n_keys, int64_t n_items, const int32_t* key, int32_t* start, int32_t* order) {
@@ -304,6 +346,7 @@ void refresh_case(lfm_ctx* c) {
   cs.max_iter = c->opts.max_iter;
   cs.min_iter = c->opts.min_iter;
   cs.precision = c->opts.precision;
+  cs.n_corr = c->n_corr;
 }
 
 void bind_pointers(lfm_ctx* c) {
@@ -334,6 +377,10 @@ void bind_pointers(lfm_ctx* c) {
     cs.delta = m.delta;
     cs.bmagSf = m.bmagSf;
     cs.bdelta = m.bdelta;
+    cs.Sf = m.Sf;
+    cs.fw = m.fw;
+    cs.corr = m.corr;
+    cs.bSf = m.bSf;
   } else {
     cs.slot_other = reinterpret_cast<const int32_t*>(b + L.slot_other);
     cs.slot_face = reinterpret_cast<const int32_t*>(b + L.slot_face);
@@ -346,7 +393,15 @@ void bind_pointers(lfm_ctx* c) {
     cs.delta = reinterpret_cast<const double*>(b + L.delta);
     cs.bmagSf = reinterpret_cast<const double*>(b + L.bmagSf);
     cs.bdelta = reinterpret_cast<const double*>(b + L.bdelta);
+    const bool g = c->has_geom;
+    cs.Sf = g ? reinterpret_cast<const double*>(b + L.Sf) : nullptr;
+    cs.fw = g ? reinterpret_cast<const double*>(b + L.fw) : nullptr;
+    cs.corr = g ? reinterpret_cast<const double*>(b + L.corr) : nullptr;
+    cs.bSf = g ? reinterpret_cast<const double*>(b + L.bSf) : nullptr;
   }
+  cs.grad = c->has_geom ? reinterpret_cast<double*>(b + L.grad) : nullptr;
+  cs.cflux = c->has_geom ? reinterpret_cast<double*>(b + L.cflux) : nullptr;
+  cs.x_old = reinterpret_cast<double*>(b + L.x_old);
   cs.diag = reinterpret_cast<double*>(b + L.diag);
   cs.upper = reinterpret_cast<double*>(b + L.upper);
   cs.slot_coef = reinterpret_cast<double*>(b + L.slot_coef);
@@ -496,11 +551,12 @@ int lfm_bind_workspace(lfm_ctx* c, void* dev_ptr, size_t bytes, int32_t precisio
   return LFM_OK;
 }
 
-int lfm_upload_mesh(lfm_ctx* c, const lfm_mesh* m) {
+static int upload_mesh_impl(lfm_ctx* c, const lfm_mesh* m, const lfm_geometry* geo) {
   if (!c) return fail_free(LFM_EINVAL, "context is NULL");
   if (c->n_sharers > 0 || c->mesh_src) return fail(c, LFM_ESTATE, "the context shares a mesh");
   std::string why;
   if (check_mesh(m, why) != LFM_OK) return fail(c, LFM_EINVAL, "%s", why.c_str());
+  if (geo && check_geometry(m, geo, why) != LFM_OK) return fail(c, LFM_EINVAL, "%s", why.c_str());
   DeviceGuard g(c->device);
   const int32_t W = slot_width(m);
   if (W > kMaxSlots) return fail(c, LFM_EINVAL, "a cell has %d internal faces (at most %d supported)", W, kMaxSlots);
@@ -508,7 +564,7 @@ int lfm_upload_mesh(lfm_ctx* c, const lfm_mesh* m) {
     return fail(c, LFM_EINVAL, "slot width x cells = %llu exceeds 2^32 - 1",
                 (unsigned long long)W * (unsigned long long)m->n_cells);
   const int kind = c->ws_bound ? c->ws_kind : kLayoutBoth;
-  const Layout use = make_layout(m->n_cells, m->n_faces, m->n_bfaces, W, kind);
+  const Layout use = make_layout(m->n_cells, m->n_faces, m->n_bfaces, W, kind, false, geo != nullptr);
   const bool has64 = kind != LFM_MIXED, has32 = kind != LFM_FP64;
   if (c->ws_bound) {
     if (c->ws_bytes < use.total) return fail(c, LFM_ENOMEM, "workspace has %zu bytes, needs %zu", c->ws_bytes, use.total);
@@ -531,6 +587,8 @@ int lfm_upload_mesh(lfm_ctx* c, const lfm_mesh* m) {
   c->W = W;
   c->has64 = has64;
   c->has32 = has32;
+  c->has_geom = geo != nullptr;
+  c->n_corr = 0;
   c->n_patches = m->n_patches;
   c->patch_start.assign(m->patch_start, m->patch_start + m->n_patches);
   c->patch_size.assign(m->patch_size, m->patch_size + m->n_patches);
@@ -580,6 +638,9 @@ int lfm_upload_mesh(lfm_ctx* c, const lfm_mesh* m) {
       (rc = h2d(c, Y.bmagSf, m->bmagSf, NB)) || (rc = h2d(c, Y.bdelta, m->bdeltaCoeffs, NB)) ||
       (rc = h2d(c, Y.bDT, zeros_b.data(), NB)) || (rc = h2d(c, Y.bval, zeros_b.data(), NB)))
     return rc;
+  if (geo && ((rc = h2d(c, Y.Sf, geo->Sf, 3 * (size_t)F)) || (rc = h2d(c, Y.fw, geo->weights, F)) ||
+              (rc = h2d(c, Y.corr, geo->corr_vec, 3 * (size_t)F)) || (rc = h2d(c, Y.bSf, geo->bSf, 3 * (size_t)NB))))
+    return rc;
   if (WN > 0) {
     CK(c, cudaMemsetAsync(c->ws + Y.slot_coef, 0, sizeof(double) * WN, c->stream));
     if (has32) CK(c, cudaMemsetAsync(c->ws + Y.slot_coef32, 0, sizeof(float) * WN, c->stream));
@@ -595,6 +656,23 @@ int lfm_upload_mesh(lfm_ctx* c, const lfm_mesh* m) {
   c->uploaded = true;
   c->ctas = c->threads = 0;
   return choose_launch(c);
+}
+
+int lfm_upload_mesh(lfm_ctx* c, const lfm_mesh* m) { return upload_mesh_impl(c, m, nullptr); }
+
+int lfm_upload_mesh_geometry(lfm_ctx* c, const lfm_mesh* m, const lfm_geometry* geometry) {
+  if (!geometry) return fail(c, LFM_EINVAL, "geometry is NULL");
+  return upload_mesh_impl(c, m, geometry);
+}
+
+size_t lfm_workspace_bytes_geometry(const lfm_mesh* mesh, int32_t precision) {
+  std::string why;
+  if (check_mesh(mesh, why) != LFM_OK) {
+    g_last_error = why;
+    return 0;
+  }
+  if (precision != LFM_FP64 && precision != LFM_MIXED) precision = kLayoutBoth;
+  return make_layout(mesh->n_cells, mesh->n_faces, mesh->n_bfaces, slot_width(mesh), precision, false, true).total;
 }
 
 namespace {
@@ -677,6 +755,8 @@ int lfm_upload_box(lfm_ctx* c, int32_t nx, int32_t ny, int32_t nz, const double*
   c->W = W;
   c->has64 = has64;
   c->has32 = has32;
+  c->has_geom = false;
+  c->n_corr = 0;
   c->n_patches = 6;
   const int32_t sizes[6] = {ny * nz, ny * nz, nx * nz, nx * nz, nx * ny, nx * ny};
   c->patch_start.assign(6, 0);
@@ -724,7 +804,8 @@ size_t lfm_workspace_bytes_box(int32_t nx, int32_t ny, int32_t nz, int32_t preci
 size_t lfm_workspace_bytes_shared(const lfm_ctx* src, int32_t precision) {
   if (!src || !src->uploaded) return 0;
   if (precision != LFM_FP64 && precision != LFM_MIXED) precision = kLayoutBoth;
-  return make_layout(src->N, src->F, src->NB, src->W, precision, true).total;
+  const lfm_ctx* root = src->mesh_src ? src->mesh_src : src;
+  return make_layout(src->N, src->F, src->NB, src->W, precision, true, root->has_geom).total;
 }
 
 int lfm_upload_mesh_shared(lfm_ctx* c, lfm_ctx* src) {
@@ -736,7 +817,7 @@ int lfm_upload_mesh_shared(lfm_ctx* c, lfm_ctx* src) {
   lfm_ctx* root = src->mesh_src ? src->mesh_src : src;
   DeviceGuard g(c->device);
   const int kind = c->ws_bound ? c->ws_kind : kLayoutBoth;
-  const Layout use = make_layout(root->N, root->F, root->NB, root->W, kind, true);
+  const Layout use = make_layout(root->N, root->F, root->NB, root->W, kind, true, root->has_geom);
   const bool has64 = kind != LFM_MIXED, has32 = kind != LFM_FP64;
   if (c->ws_bound) {
     if (c->ws_bytes < use.total) return fail(c, LFM_ENOMEM, "workspace has %zu bytes, needs %zu", c->ws_bytes, use.total);
@@ -757,6 +838,8 @@ int lfm_upload_mesh_shared(lfm_ctx* c, lfm_ctx* src) {
   c->W = root->W;
   c->has64 = has64;
   c->has32 = has32;
+  c->has_geom = root->has_geom;
+  c->n_corr = 0;
   c->n_patches = root->n_patches;
   c->patch_start = root->patch_start;
   c->patch_size = root->patch_size;
@@ -868,6 +951,39 @@ int lfm_set_solver(lfm_ctx* c, const lfm_solver_opts* o) {
   const bool launch_changes = o->precision != c->opts.precision;
   c->opts = *o;
   if (launch_changes) return choose_launch(c);
+  return LFM_OK;
+}
+
+int lfm_set_nonorth_correctors(lfm_ctx* c, int32_t n_corr) {
+  int rc = need_uploaded(c);
+  if (rc) return rc;
+  if (n_corr < 0 || n_corr > 64) return fail(c, LFM_EINVAL, "n_corr must be in [0, 64] (got %d)", n_corr);
+  if (c->pending_steps > 0) return fail(c, LFM_ESTATE, "an advance is pending");
+  c->n_corr = n_corr;
+  return LFM_OK;
+}
+
+int lfm_grad(lfm_ctx* c, double* grad, double* bgrad) {
+  int rc = need_uploaded(c);
+  if (rc) return rc;
+  if (!c->has_geom) return fail(c, LFM_ESTATE, "the mesh was uploaded without general geometry");
+  if (!grad) return fail(c, LFM_EINVAL, "grad is NULL");
+  if (c->pending_steps > 0) return fail(c, LFM_ESTATE, "an advance is pending");
+  DeviceGuard g(c->device);
+  refresh_case(c);
+  double* bdev = nullptr;
+  if (bgrad && c->NB > 0) {
+    cudaError_t e = cudaMalloc(&bdev, sizeof(double) * 3 * (size_t)c->NB);
+    if (e != cudaSuccess) return fail(c, LFM_ENOMEM, "boundary gradient buffer: %s", cudaGetErrorString(e));
+  }
+  cudaError_t e = launch_grad(c->cs, bdev, c->stream);
+  if (e == cudaSuccess)
+    e = cudaMemcpyAsync(grad, c->cs.grad, sizeof(double) * 3 * (size_t)c->N, cudaMemcpyDeviceToHost, c->stream);
+  if (e == cudaSuccess && bdev)
+    e = cudaMemcpyAsync(bgrad, bdev, sizeof(double) * 3 * (size_t)c->NB, cudaMemcpyDeviceToHost, c->stream);
+  if (e == cudaSuccess) e = cudaStreamSynchronize(c->stream);
+  if (bdev) cudaFree(bdev);
+  if (e != cudaSuccess) return cuda_fail(c, e, "lfm_grad");
   return LFM_OK;
 }
 

@@ -70,6 +70,18 @@ struct CaseDev {
   const double* bval;        // [NB]  fixedValue values
   const int32_t* btype;      // [NB]  LFM_FIXED_VALUE / LFM_ZERO_GRADIENT
 
+  // general (non-orthogonal) geometry; null for orthogonal meshes. With it, delta holds the
+  // implicit (nonOrthDeltaCoeffs) coefficients and the corrected laplacian adds an explicit
+  // flux DT |Sf| k_f . (w_f (G_P - G_N) + G_N) from the Gauss gradient G of the current T.
+  const double* Sf;          // [3F] internal face area vectors, owner -> neighbour
+  const double* fw;          // [F]  interpolation weight of the owner value
+  const double* corr;        // [3F] correction vectors k_f
+  const double* bSf;         // [3NB] boundary face area vectors, outward
+  double* grad;              // [3N] Gauss gradient of T (per assembly)
+  double* cflux;             // [F]  explicit correction flux (per assembly)
+  double* x_old;             // [N]  T at the start of the step (non-orthogonal correctors)
+  int32_t n_corr;            // extra corrector passes per step (nNonOrthogonalCorrectors)
+
   // assembled matrix (FP64): LDU (diag, upper) plus the per-slot copy of the off-diagonals
   double* diag;              // [N]
   double* upper;             // [F]  (lower == upper)
@@ -133,6 +145,9 @@ cudaError_t launch_steps(const CaseDev& cs, const Launch& L, int n_steps, int mo
 // Largest co-resident CTA count for the step kernel at `threads` per CTA.
 int max_coresident_ctas(int precision, int threads, int W, int device);
 cudaError_t launch_boundary_values(const CaseDev& cs, double* Tb, cudaStream_t stream);
+// Gauss linear gradient of the current T: cells into cs.grad, and (bgrad non-null) the
+// corrected boundary values [3NB].
+cudaError_t launch_grad(const CaseDev& cs, double* bgrad, cudaStream_t stream);
 
 // Box meshes built from closed forms (lfm_box.cu).
 int box_slot_width(long long nx, long long ny, long long nz);

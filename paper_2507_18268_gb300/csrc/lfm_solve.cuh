@@ -127,10 +127,11 @@ __device__ __forceinline__ double plus_zero(double v) {
   return (bits << 1) == 0 ? 0.0 : v;
 }
 
-__device__ __forceinline__ void row_boundary(const CaseDev& cs, int c, Row& o) {
+// xo: T of the cell at the start of the step (the ddt source).
+__device__ __forceinline__ void row_boundary(const CaseDev& cs, int c, double xo, Row& o) {
   const int b0 = __ldg(cs.b_start + c), b1 = __ldg(cs.b_start + c + 1);
   const double vdt = cs.vdt[c];  // V/dt, formed once per (mesh, dt): the same IEEE quotient
-  const double sv = __dmul_rn(vdt, o.xc);
+  const double sv = __dmul_rn(vdt, xo);
   if (b0 == b1) {  // no boundary face: the sums below start from zero
     o.d = __dadd_rn(o.d, vdt);
     o.s = plus_zero(sv);
@@ -152,7 +153,93 @@ __device__ __forceinline__ void row_boundary(const CaseDev& cs, int c, Row& o) {
   o.sa = gsum + vdt;
 }
 
-template <int W>
+// ---- general geometry: Gauss gradient and the explicit non-orthogonal correction ---------
+// Sum over the cell's faces of the correction flux, + for faces it owns and - for the
+// others, in slot order (the same order as a scatter over faces in face order).
+__device__ __forceinline__ double corr_source(const CaseDev& cs, int c) {
+  const size_t N = (size_t)cs.N;
+  double v = 0.0;
+  for (int k = 0; k < cs.W; ++k) {
+    const size_t at = (size_t)k * N + c;
+    const int f = __ldg(cs.slot_face + at);
+    if (f < 0) break;  // padding comes last
+    const double fl = cs.cflux[f];
+    v = __ldg(cs.slot_other + at) > c ? __dadd_rn(v, fl) : __dsub_rn(v, fl);
+  }
+  return v;
+}
+
+// Gauss linear gradient of x at cell c (section "Code Porting": face values
+// w (x_P - x_N) + x_N, the Gauss sum Sf x_f over the cell's faces -- + where it owns the
+// face, - where it is the neighbour -- and its boundary faces, divided by V). Faces are
+// taken in slot order, which is face order, as in a scatter over faces; the division is a
+// multiplication by the rounded reciprocal of V.
+__device__ __forceinline__ void cell_grad(const CaseDev& cs, int c, const double* __restrict__ x, double* g) {
+  const size_t N = (size_t)cs.N;
+  const double xc = x[c];
+  double gx = 0.0, gy = 0.0, gz = 0.0;
+  for (int k = 0; k < cs.W; ++k) {
+    const size_t at = (size_t)k * N + c;
+    const int f = __ldg(cs.slot_face + at);
+    if (f < 0) break;
+    const int o = __ldg(cs.slot_other + at);
+    const bool own = o > c;
+    const double xo = x[o];
+    const double xP = own ? xc : xo, xN = own ? xo : xc;
+    const double xf = __dadd_rn(__dmul_rn(__ldg(cs.fw + f), __dsub_rn(xP, xN)), xN);
+    const double vx = __dmul_rn(__ldg(cs.Sf + 3 * (size_t)f), xf);
+    const double vy = __dmul_rn(__ldg(cs.Sf + 3 * (size_t)f + 1), xf);
+    const double vz = __dmul_rn(__ldg(cs.Sf + 3 * (size_t)f + 2), xf);
+    if (own) {
+      gx = __dadd_rn(gx, vx);
+      gy = __dadd_rn(gy, vy);
+      gz = __dadd_rn(gz, vz);
+    } else {
+      gx = __dsub_rn(gx, vx);
+      gy = __dsub_rn(gy, vy);
+      gz = __dsub_rn(gz, vz);
+    }
+  }
+  const int b0 = __ldg(cs.b_start + c), b1 = __ldg(cs.b_start + c + 1);
+  for (int k = b0; k < b1; ++k) {
+    const int bf = __ldg(cs.b_face + k);
+    const double xb = __ldg(cs.btype + bf) == LFM_FIXED_VALUE ? __ldg(cs.bval + bf) : xc;
+    gx = __dadd_rn(gx, __dmul_rn(__ldg(cs.bSf + 3 * (size_t)bf), xb));
+    gy = __dadd_rn(gy, __dmul_rn(__ldg(cs.bSf + 3 * (size_t)bf + 1), xb));
+    gz = __dadd_rn(gz, __dmul_rn(__ldg(cs.bSf + 3 * (size_t)bf + 2), xb));
+  }
+  const double rv = __drcp_rn(__ldg(cs.V + c));
+  g[0] = gx * rv;
+  g[1] = gy * rv;
+  g[2] = gz * rv;
+}
+
+// Explicit correction flux of face f: DT |Sf| k . (w (G_P - G_N) + G_N), the face value of
+// the gradient by the same linear interpolation (dotInterpolate of the correction vectors),
+// products and sums rounded separately. Owner and neighbour come from the face's two slots.
+__device__ __forceinline__ double face_corr_flux(const CaseDev& cs, int f) {
+  const uint2 at = __ldg(reinterpret_cast<const uint2*>(cs.face_slots) + f);
+  const int P = __ldg(cs.slot_other + at.y), Q = __ldg(cs.slot_other + at.x);
+  const double w = __ldg(cs.fw + f);
+  const double* gP = cs.grad + 3 * (size_t)P;
+  const double* gQ = cs.grad + 3 * (size_t)Q;
+  const double* k = cs.corr + 3 * (size_t)f;
+  double dot = 0.0;
+#pragma unroll
+  for (int d = 0; d < 3; ++d) {
+    const double gq = gQ[d];
+    const double gf = __dadd_rn(__dmul_rn(w, __dsub_rn(gP[d], gq)), gq);
+    const double t = __dmul_rn(__ldg(k + d), gf);
+    dot = d == 0 ? t : __dadd_rn(dot, t);
+  }
+  const double DTf = cs.DT_is_uniform ? cs.DT_uniform : __ldg(cs.DT + f);
+  return __dmul_rn(__dmul_rn(DTf, __ldg(cs.magSf + f)), dot);
+}
+
+// kCorr: the step has non-orthogonal corrector passes or general geometry: the ddt source
+// comes from x_old, and the explicit correction fluxes of the row's faces (owner +,
+// neighbour -, slot order = face order) are added to the source.
+template <int W, bool kCorr = false>
 __device__ __forceinline__ Row assemble_row(const CaseDev& cs, int c, const double* __restrict__ x) {
   const size_t N = (size_t)cs.N;
   Row o;
@@ -182,7 +269,8 @@ __device__ __forceinline__ Row assemble_row(const CaseDev& cs, int c, const doub
       off = fma(u, x[__ldg(cs.slot_other + at)], off);
     }
   }
-  row_boundary(cs, c, o);
+  row_boundary(cs, c, kCorr && cs.n_corr > 0 ? cs.x_old[c] : o.xc, o);
+  if (kCorr && cs.cflux) o.s = __dadd_rn(o.s, corr_source(cs, c));
   o.ax = fma(o.d, o.xc, off);
   return o;
 }
@@ -207,19 +295,52 @@ __device__ __forceinline__ double store_row(const CaseDev& cs, int c, const Row&
 
 // Pass 1 over the faces [f0, f1) of this CTA; returns this thread's sum of T over the cells
 // [c0, c1) (for xRef).
+// save_old: also keep T as the step's starting field (x_old) for the corrector passes.
 template <int B, bool kMixed>
-__device__ __noinline__ double pass_faces(const CaseDev& cs, int f0, int f1, int c0, int c1, bool write_upper) {
+__device__ __noinline__ double pass_faces(const CaseDev& cs, int f0, int f1, int c0, int c1, bool write_upper,
+                                          bool save_old) {
   for (int f = f0 + (int)threadIdx.x; f < f1; f += B) assemble_face<kMixed>(cs, f, write_upper);
   const double* __restrict__ x = cs.x;
   double v = 0.0;
-  for (int c = c0 + (int)threadIdx.x; c < c1; c += B) v += x[c];
+  if (save_old) {
+    double* __restrict__ xo = cs.x_old;
+    for (int c = c0 + (int)threadIdx.x; c < c1; c += B) {
+      const double xc = x[c];
+      xo[c] = xc;
+      v += xc;
+    }
+  } else {
+    for (int c = c0 + (int)threadIdx.x; c < c1; c += B) v += x[c];
+  }
   return v;
+}
+
+// Gauss gradient of T over the cells [c0, c1) into cs.grad (same phase as the face pass:
+// it reads only T and the geometry).
+template <int B>
+__device__ __noinline__ void pass_grad(const CaseDev& cs, int c0, int c1) {
+  double* __restrict__ G = cs.grad;
+  for (int c = c0 + (int)threadIdx.x; c < c1; c += B) {
+    double g[3];
+    cell_grad(cs, c, cs.x, g);
+    G[3 * (size_t)c] = g[0];
+    G[3 * (size_t)c + 1] = g[1];
+    G[3 * (size_t)c + 2] = g[2];
+  }
+}
+
+// Correction fluxes of the faces [f0, f1) into cs.cflux (after the gradient's barrier).
+template <int B>
+__device__ __noinline__ void pass_corr_flux(const CaseDev& cs, int f0, int f1) {
+  double* __restrict__ out = cs.cflux;
+  for (int f = f0 + (int)threadIdx.x; f < f1; f += B) out[f] = face_corr_flux(cs, f);
 }
 
 // Pass 2 alone, for matrix read-back (every array of the assembled system written).
 template <int B, int W, bool kMixed>
 __device__ __noinline__ void pass_rows_only(const CaseDev& cs, int c0, int c1) {
-  for (int c = c0 + (int)threadIdx.x; c < c1; c += B) store_row<kMixed>(cs, c, assemble_row<W>(cs, c, cs.x), true);
+  for (int c = c0 + (int)threadIdx.x; c < c1; c += B)
+    store_row<kMixed>(cs, c, assemble_row<W, true>(cs, c, cs.x), true);
 }
 
 // ---- A v over the slot-major matrix (FP64 or FP32 copy) --------------------------------
@@ -437,14 +558,14 @@ struct Sums3 {
 // A2 + I (FP64 step): the rows of the matrix and, from the same loaded row, r = b - A x,
 // the normFactor terms, sum|r|, w = rD r and rho; p = w. Returns this thread's normFactor
 // sum, sum|r| and rho.
-template <int B, int W>
+template <int B, int W, bool kCorr>
 __device__ __noinline__ Sums3 pass_rows_init_f64(const CaseDev& cs, int c0, int c1, double xRef) {
   double* __restrict__ r = cs.r;
   double* __restrict__ p = cs.p;
   const double* __restrict__ x = cs.x;
   double u0 = 0.0, u1 = 0.0, u2 = 0.0;
   for (int c = c0 + (int)threadIdx.x; c < c1; c += B) {
-    const Row o = assemble_row<W>(cs, c, x);
+    const Row o = assemble_row<W, kCorr>(cs, c, x);
     const double rd = store_row<false>(cs, c, o, false);
     const double rc = o.s - o.ax;
     u0 += fabs(fma(-o.sa, xRef, o.ax)) + fabs(fma(-o.sa, xRef, o.s));
@@ -461,7 +582,7 @@ __device__ __noinline__ Sums3 pass_rows_init_f64(const CaseDev& cs, int c0, int 
 // solve (r, w = rD r, p = w, dx = 0). With kFirst it is computed together with the rows of
 // the matrix (A2) and the normFactor terms. Returns this thread's normFactor sum (kFirst),
 // sum|r| and rho (FP32 terms accumulated exactly as FP32 pairs).
-template <int B, int W, bool kFirst>
+template <int B, int W, bool kFirst, bool kCorr>
 __device__ __noinline__ Sums3 pass_true_residual(const CaseDev& cs, int c0, int c1, double xRef) {
   float* __restrict__ r = cs.r32;
   float* __restrict__ w = cs.w32;
@@ -474,7 +595,7 @@ __device__ __noinline__ Sums3 pass_true_residual(const CaseDev& cs, int c0, int 
     double rc;
     float rd32;
     if (kFirst) {
-      const Row o = assemble_row<W>(cs, c, x);
+      const Row o = assemble_row<W, kCorr>(cs, c, x);
       rd32 = (float)store_row<true>(cs, c, o, true);
       u0 += fabs(fma(-o.sa, xRef, o.ax)) + fabs(fma(-o.sa, xRef, o.s));
       rc = o.s - o.ax;
@@ -536,8 +657,28 @@ __device__ __forceinline__ void write_stats(const CaseDev& cs, const Team& tm, i
   }
 }
 
+// Start of an assembly: the face pass (with the copy of T at the start of the step when
+// save_old, and with general geometry the Gauss gradient in the same phase), the team sum
+// of T for xRef, then with general geometry the correction-flux pass. False when a barrier
+// failed (the caller leaves the kernel).
+template <int B, bool kMixed>
+__device__ __forceinline__ bool assemble_prologue(const CaseDev& cs, const CaseDev& cref, const Team& tm, int c0,
+                                                  int c1, int f0, int f1, bool write_upper, bool save_old,
+                                                  double& sum_x, TeamShared& sh) {
+  double v[1] = {pass_faces<B, kMixed>(cref, f0, f1, c0, c1, write_upper, save_old)};
+  const bool geom = cs.Sf != nullptr;
+  if (geom) pass_grad<B>(cref, c0, c1);
+  if (!team_allreduce<1>(tm, v, sh)) return false;
+  if (geom) {
+    pass_corr_flux<B>(cref, f0, f1);
+    if (!team_barrier(tm, sh)) return false;
+  }
+  sum_x = v[0];
+  return true;
+}
+
 // =======================================================================================
-// FP64 steps
+// FP64 steps (1 + n_corr assemble-and-solve passes per step)
 // =======================================================================================
 template <int B, int W>
 __device__ void run_steps_f64(const CaseDev& cs, const CaseDev& cref, const Team& tm, int n_steps, int mode,
@@ -555,62 +696,80 @@ __device__ void run_steps_f64(const CaseDev& cs, const CaseDev& cref, const Team
   const double* __restrict__ rD = cs.rD;
 
   PhaseClock clk(cs, tm);
+  const bool corr_mode = cs.n_corr > 0 || cs.Sf != nullptr;
   for (int step = 0; step < n_steps; ++step) {
-    // ---- A1: face coefficients, sum of T -------------------------------------------------
-    double v[1] = {pass_faces<B, false>(cref, f0, f1, c0, c1, mode == kModeAssembleOnly)};
-    if (!team_allreduce<1>(tm, v, sh)) return;
-    clk.lap(kPhAssembly);
-    if (mode == kModeAssembleOnly) {
-      pass_rows_only<B, W, false>(cref, c0, c1);
-      return;
-    }
-    // ---- A2 + I: rows of the matrix, initial residual, normFactor, first direction -------
-    const Sums3 ui = pass_rows_init_f64<B, W>(cref, c0, c1, v[0] / (double)cs.N);
-    double u[3] = {ui.a, ui.b, ui.c};  // normFactor sum, sum|r|, rho
-    if (!team_allreduce<3>(tm, u, sh)) return;
-    clk.lap(kPhInit);
-    const double nf = u[0] + kSmall;
-    const double init_res = u[1] / nf;
-    double res = init_res, rho = u[2], beta = 0.0;
-    int iters = 0, status = 0;
-    bool conv = converged(res, init_res, cs.tol, cs.rel_tol);
-    if (cs.min_iter > 0 || !conv) {
-      for (;;) {
-        if (iters > 0) {
-          // ---- P: search direction -------------------------------------------------
-          pass_direction<B, double>(c0, c1, beta, p, w);
-          if (!team_barrier(tm, sh)) return;
-          clk.lap(kPhP);
-        }
-        // ---- M: q = A p, sigma = p.q ----------------------------------------------
-        double s1[1] = {pass_amul_dot_f64<B, W>(slots64(cs), c0, c1, p, q)};
-        if (!team_allreduce<1>(tm, s1, sh)) return;
-        clk.lap(kPhM);
-        const double sigma = s1[0];
-        if (fabs(sigma) / nf < kVSmall) {
-          status = LFM_ESINGULAR;
-          break;
-        }
-        const double alpha = rho / sigma;
-        // ---- U: update, residual, preconditioned residual, next rho ----------------
-        const double2 su = pass_update_f64<B>(c0, c1, alpha, x, r, w, p, q, rD);
-        double s2[2] = {su.x, su.y};
-        if (!team_allreduce<2>(tm, s2, sh)) return;
-        clk.lap(kPhU);
-        res = s2[0] / nf;
-        beta = s2[1] / rho;
-        rho = s2[1];
-        ++iters;
-        if (!isfinite(res)) {
-          status = LFM_ENONFINITE;
-          break;
-        }
-        conv = converged(res, init_res, cs.tol, cs.rel_tol);
-        if (!((iters < cs.max_iter && !conv) || iters < cs.min_iter)) break;
+    int iters_tot = 0, solves = 0, status = 0;
+    double nf0 = 0.0, init0 = 0.0, res = 0.0;
+    bool conv = false;
+    for (int pass = 0; pass <= cs.n_corr; ++pass) {
+      // ---- A1: face coefficients, sum of T (and the gradient / correction fluxes) --------
+      double sum_x = 0.0;
+      if (!assemble_prologue<B, false>(cs, cref, tm, c0, c1, f0, f1, mode == kModeAssembleOnly,
+                                       pass == 0 && cs.n_corr > 0, sum_x, sh))
+        return;
+      clk.lap(kPhAssembly);
+      if (mode == kModeAssembleOnly) {
+        pass_rows_only<B, W, false>(cref, c0, c1);
+        return;
       }
+      // ---- A2 + I: rows of the matrix, initial residual, normFactor, first direction -----
+      const double xRef = sum_x / (double)cs.N;
+      const Sums3 ui = corr_mode ? pass_rows_init_f64<B, W, true>(cref, c0, c1, xRef)
+                                 : pass_rows_init_f64<B, W, false>(cref, c0, c1, xRef);
+      double u[3] = {ui.a, ui.b, ui.c};  // normFactor sum, sum|r|, rho
+      if (!team_allreduce<3>(tm, u, sh)) return;
+      clk.lap(kPhInit);
+      const double nf = u[0] + kSmall;
+      const double init_res = u[1] / nf;
+      res = init_res;
+      double rho = u[2], beta = 0.0;
+      int iters = 0;
+      conv = converged(res, init_res, cs.tol, cs.rel_tol);
+      if (cs.min_iter > 0 || !conv) {
+        for (;;) {
+          if (iters > 0) {
+            // ---- P: search direction -----------------------------------------------
+            pass_direction<B, double>(c0, c1, beta, p, w);
+            if (!team_barrier(tm, sh)) return;
+            clk.lap(kPhP);
+          }
+          // ---- M: q = A p, sigma = p.q --------------------------------------------
+          double s1[1] = {pass_amul_dot_f64<B, W>(slots64(cs), c0, c1, p, q)};
+          if (!team_allreduce<1>(tm, s1, sh)) return;
+          clk.lap(kPhM);
+          const double sigma = s1[0];
+          if (fabs(sigma) / nf < kVSmall) {
+            status = LFM_ESINGULAR;
+            break;
+          }
+          const double alpha = rho / sigma;
+          // ---- U: update, residual, preconditioned residual, next rho --------------
+          const double2 su = pass_update_f64<B>(c0, c1, alpha, x, r, w, p, q, rD);
+          double s2[2] = {su.x, su.y};
+          if (!team_allreduce<2>(tm, s2, sh)) return;
+          clk.lap(kPhU);
+          res = s2[0] / nf;
+          beta = s2[1] / rho;
+          rho = s2[1];
+          ++iters;
+          if (!isfinite(res)) {
+            status = LFM_ENONFINITE;
+            break;
+          }
+          conv = converged(res, init_res, cs.tol, cs.rel_tol);
+          if (!((iters < cs.max_iter && !conv) || iters < cs.min_iter)) break;
+        }
+      }
+      conv = converged(res, init_res, cs.tol, cs.rel_tol);
+      if (pass == 0) {
+        nf0 = nf;
+        init0 = init_res;
+      }
+      iters_tot += iters;
+      solves += iters > 0 ? 1 : 0;
+      if (status != 0) break;
     }
-    conv = converged(res, init_res, cs.tol, cs.rel_tol);
-    write_stats(cs, tm, stats_base + step, iters, conv ? 1 : 0, iters > 0 ? 1 : 0, status, init_res, res, nf);
+    write_stats(cs, tm, stats_base + step, iters_tot, conv ? 1 : 0, solves, status, init0, res, nf0);
     if (status != 0) {
       if (tm.rank == 0 && tid == 0) set_status(cs.sync, status);
       return;
@@ -638,82 +797,102 @@ __device__ void run_steps_mixed(const CaseDev& cs, const CaseDev& cref, const Te
   const float* __restrict__ rD = cs.rD32;
 
   PhaseClock clk(cs, tm);
+  const bool corr_mode = cs.n_corr > 0 || cs.Sf != nullptr;
   for (int step = 0; step < n_steps; ++step) {
-    double v[1] = {pass_faces<B, true>(cref, f0, f1, c0, c1, mode == kModeAssembleOnly)};
-    if (!team_allreduce<1>(tm, v, sh)) return;
-    clk.lap(kPhAssembly);
-    if (mode == kModeAssembleOnly) {
-      pass_rows_only<B, W, true>(cref, c0, c1);
-      return;
-    }
-    const double xRef = v[0] / (double)cs.N;
-
-    double nf = 0.0, init_res = 0.0, res = 0.0;
-    int iters = 0, sweeps = 0, status = 0;
-    for (;;) {
-      // ---- T: FP64 true residual r = b - A x, seeded into the FP32 inner solve; on the
-      //      first sweep computed together with pass 2 of the assembly and normFactor -----
-      const Sums3 ui = sweeps == 0 ? pass_true_residual<B, W, true>(cref, c0, c1, xRef)
-                                   : pass_true_residual<B, W, false>(cref, c0, c1, xRef);
-      double u[3] = {ui.a, ui.b, ui.c};  // normFactor sum (first sweep), sum|r|, rho
-      if (!team_allreduce<3>(tm, u, sh)) return;
-      clk.lap(kPhInit);
-      if (sweeps == 0) {
-        nf = u[0] + kSmall;
-        init_res = u[1] / nf;
+    int iters_tot = 0, sweeps_tot = 0, status = 0;
+    double nf0 = 0.0, init0 = 0.0, res = 0.0;
+    bool conv = false;
+    for (int pass = 0; pass <= cs.n_corr; ++pass) {
+      double sum_x = 0.0;
+      if (!assemble_prologue<B, true>(cs, cref, tm, c0, c1, f0, f1, mode == kModeAssembleOnly,
+                                      pass == 0 && cs.n_corr > 0, sum_x, sh))
+        return;
+      clk.lap(kPhAssembly);
+      if (mode == kModeAssembleOnly) {
+        pass_rows_only<B, W, true>(cref, c0, c1);
+        return;
       }
-      res = u[1] / nf;
-      if (!isfinite(res)) {
-        status = LFM_ENONFINITE;
-        break;
-      }
-      const bool conv = converged(res, init_res, cs.tol, cs.rel_tol);
-      if ((conv && !(sweeps == 0 && cs.min_iter > 0)) || sweeps == kMaxSweeps || iters >= cs.max_iter) break;
+      const double xRef = sum_x / (double)cs.N;
 
-      // ---- inner FP32 CG on A dx = r --------------------------------------------------
-      const double inner_tol = fmax(cs.tol, kInnerRel * res);
-      const int min_inner = sweeps == 0 ? cs.min_iter : 0;
-      double rho = u[2], beta = 0.0;
-      int k = 0;
+      double nf = 0.0, init_res = 0.0;
+      int iters = 0, sweeps = 0;
       for (;;) {
-        if (k > 0) {
-          pass_direction<B, float>(c0, c1, (float)beta, p, w);
-          if (!team_barrier(tm, sh)) return;
-          clk.lap(kPhP);
+        // ---- T: FP64 true residual r = b - A x, seeded into the FP32 inner solve; on the
+        //      first sweep computed together with pass 2 of the assembly and normFactor ---
+        Sums3 ui;
+        if (sweeps > 0)
+          ui = pass_true_residual<B, W, false, false>(cref, c0, c1, xRef);
+        else if (corr_mode)
+          ui = pass_true_residual<B, W, true, true>(cref, c0, c1, xRef);
+        else
+          ui = pass_true_residual<B, W, true, false>(cref, c0, c1, xRef);
+        double u[3] = {ui.a, ui.b, ui.c};  // normFactor sum (first sweep), sum|r|, rho
+        if (!team_allreduce<3>(tm, u, sh)) return;
+        clk.lap(kPhInit);
+        if (sweeps == 0) {
+          nf = u[0] + kSmall;
+          init_res = u[1] / nf;
         }
-        double s1[1] = {pass_amul_dot_f32<B, W>(slots32(cs), c0, c1, p, q)};
-        if (!team_allreduce<1>(tm, s1, sh)) return;
-        clk.lap(kPhM);
-        const double sigma = s1[0];
-        if (fabs(sigma) / nf < kVSmall) {
-          status = LFM_ESINGULAR;
-          break;
-        }
-        const double2 su = pass_update_f32<B>(c0, c1, (float)(rho / sigma), dx, r, w, p, q, rD);
-        double s2[2] = {su.x, su.y};
-        if (!team_allreduce<2>(tm, s2, sh)) return;
-        clk.lap(kPhU);
-        const double inner_res = s2[0] / nf;
-        beta = s2[1] / rho;
-        rho = s2[1];
-        ++k;
-        ++iters;
-        if (!isfinite(inner_res)) {
+        res = u[1] / nf;
+        if (!isfinite(res)) {
           status = LFM_ENONFINITE;
           break;
         }
-        const bool inner_conv = inner_res < inner_tol;
-        if (!((iters < cs.max_iter && !inner_conv) || k < min_inner)) break;
+        const bool c_ok = converged(res, init_res, cs.tol, cs.rel_tol);
+        if ((c_ok && !(sweeps == 0 && cs.min_iter > 0)) || sweeps == kMaxSweeps || iters >= cs.max_iter) break;
+
+        // ---- inner FP32 CG on A dx = r ------------------------------------------------
+        const double inner_tol = fmax(cs.tol, kInnerRel * res);
+        const int min_inner = sweeps == 0 ? cs.min_iter : 0;
+        double rho = u[2], beta = 0.0;
+        int k = 0;
+        for (;;) {
+          if (k > 0) {
+            pass_direction<B, float>(c0, c1, (float)beta, p, w);
+            if (!team_barrier(tm, sh)) return;
+            clk.lap(kPhP);
+          }
+          double s1[1] = {pass_amul_dot_f32<B, W>(slots32(cs), c0, c1, p, q)};
+          if (!team_allreduce<1>(tm, s1, sh)) return;
+          clk.lap(kPhM);
+          const double sigma = s1[0];
+          if (fabs(sigma) / nf < kVSmall) {
+            status = LFM_ESINGULAR;
+            break;
+          }
+          const double2 su = pass_update_f32<B>(c0, c1, (float)(rho / sigma), dx, r, w, p, q, rD);
+          double s2[2] = {su.x, su.y};
+          if (!team_allreduce<2>(tm, s2, sh)) return;
+          clk.lap(kPhU);
+          const double inner_res = s2[0] / nf;
+          beta = s2[1] / rho;
+          rho = s2[1];
+          ++k;
+          ++iters;
+          if (!isfinite(inner_res)) {
+            status = LFM_ENONFINITE;
+            break;
+          }
+          const bool inner_conv = inner_res < inner_tol;
+          if (!((iters < cs.max_iter && !inner_conv) || k < min_inner)) break;
+        }
+        if (status != 0) break;
+        // ---- x += dx (FP64) ----------------------------------------------------------
+        pass_correct<B>(c0, c1, x, dx);
+        if (!team_barrier(tm, sh)) return;
+        clk.lap(kPhCorrect);
+        ++sweeps;
       }
+      conv = converged(res, init_res, cs.tol, cs.rel_tol);
+      if (pass == 0) {
+        nf0 = nf;
+        init0 = init_res;
+      }
+      iters_tot += iters;
+      sweeps_tot += sweeps;
       if (status != 0) break;
-      // ---- x += dx (FP64) ------------------------------------------------------------
-      pass_correct<B>(c0, c1, x, dx);
-      if (!team_barrier(tm, sh)) return;
-      clk.lap(kPhCorrect);
-      ++sweeps;
     }
-    const bool conv = converged(res, init_res, cs.tol, cs.rel_tol);
-    write_stats(cs, tm, stats_base + step, iters, conv ? 1 : 0, sweeps, status, init_res, res, nf);
+    write_stats(cs, tm, stats_base + step, iters_tot, conv ? 1 : 0, sweeps_tot, status, init0, res, nf0);
     if (status != 0) {
       if (tm.rank == 0 && tid == 0) set_status(cs.sync, status);
       return;

@@ -37,6 +37,37 @@ __global__ void boundary_values_kernel(CaseDev cs, double* Tb) {
   if (b < cs.NB) Tb[b] = cs.btype[b] == LFM_FIXED_VALUE ? cs.bval[b] : cs.x[cs.bcell[b]];
 }
 
+// Gauss gradient of the current T per cell (into cs.grad).
+__global__ void grad_cells_kernel(CaseDev cs) {
+  const int c = blockIdx.x * blockDim.x + threadIdx.x;
+  if (c < cs.N) {
+    double g[3];
+    cell_grad(cs, c, cs.x, g);
+    cs.grad[3 * (size_t)c] = g[0];
+    cs.grad[3 * (size_t)c + 1] = g[1];
+    cs.grad[3 * (size_t)c + 2] = g[2];
+  }
+}
+
+// Boundary values of the gradient (correctBoundaryConditions): the cell's gradient with its
+// normal component replaced by the patch snGrad ((T_b - T_P) deltaCoeff for fixedValue, 0
+// for zeroGradient).
+__global__ void grad_boundary_kernel(CaseDev cs, double* __restrict__ bgrad) {
+  const int b = blockIdx.x * blockDim.x + threadIdx.x;
+  if (b < cs.NB) {
+    const int c = cs.bcell[b];
+    const double* s = cs.bSf + 3 * (size_t)b;
+    const double mag = sqrt(s[0] * s[0] + s[1] * s[1] + s[2] * s[2]);
+    const double n0 = s[0] / mag, n1 = s[1] / mag, n2 = s[2] / mag;
+    const double* g = cs.grad + 3 * (size_t)c;
+    const double sn = cs.btype[b] == LFM_FIXED_VALUE ? (cs.bval[b] - cs.x[c]) * cs.bdelta[b] : 0.0;
+    const double gn = n0 * g[0] + n1 * g[1] + n2 * g[2];
+    bgrad[3 * (size_t)b] = g[0] + n0 * (sn - gn);
+    bgrad[3 * (size_t)b + 1] = g[1] + n1 * (sn - gn);
+    bgrad[3 * (size_t)b + 2] = g[2] + n2 * (sn - gn);
+  }
+}
+
 __global__ void vdt_kernel(const double* __restrict__ V, double dt, double* __restrict__ vdt, int n) {
   const int c = blockIdx.x * blockDim.x + threadIdx.x;
   if (c < n) vdt[c] = V[c] / dt;
@@ -84,6 +115,15 @@ cudaError_t launch_steps(const CaseDev& cs, const Launch& L, int n_steps, int mo
   int a2 = n_steps, a3 = mode;
   void* args[] = {&a0, &a1, &a2, &a3};
   return cudaLaunchCooperativeKernel(fn, dim3(L.ctas), dim3(L.threads), args, 0, stream);
+}
+
+cudaError_t launch_grad(const CaseDev& cs, double* bgrad, cudaStream_t stream) {
+  if (!cs.Sf || !cs.grad) return cudaErrorInvalidValue;
+  grad_cells_kernel<<<(cs.N + 255) / 256, 256, 0, stream>>>(cs);
+  cudaError_t e = cudaGetLastError();
+  if (e != cudaSuccess || !bgrad || cs.NB == 0) return e;
+  grad_boundary_kernel<<<(cs.NB + 255) / 256, 256, 0, stream>>>(cs, bgrad);
+  return cudaGetLastError();
 }
 
 cudaError_t launch_boundary_values(const CaseDev& cs, double* Tb, cudaStream_t stream) {

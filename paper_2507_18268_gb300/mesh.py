@@ -145,3 +145,130 @@ def field_by_label(case: lapcase.RawCase, mesh: LduMesh) -> np.ndarray:
 
 def uniform_dt(case: lapcase.RawCase) -> bool:
     return case.DTx is None and case.DTy is None and case.DTz is None
+
+
+# ---------------------------------------------------------------------------------------
+# General (non-orthogonal) hexahedral boxes from vertex positions
+# ---------------------------------------------------------------------------------------
+
+@dataclasses.dataclass
+class HexGeometry:
+    """The arrays ``lfm_upload_mesh_geometry`` takes, plus the centres they derive from."""
+    Sf: np.ndarray        # [F, 3] internal face area vectors, owner -> neighbour
+    weights: np.ndarray   # [F]    linear-interpolation weight of the owner value
+    corr_vec: np.ndarray  # [F, 3] non-orthogonal correction vectors
+    bSf: np.ndarray       # [NB, 3] boundary face area vectors, outward
+    Cf: np.ndarray        # [F, 3] face centres
+    bCf: np.ndarray       # [NB, 3]
+    C: np.ndarray         # [N, 3] cell centres
+
+
+def _dot3(a, b):
+    return (a[:, 0] * b[:, 0] + a[:, 1] * b[:, 1]) + a[:, 2] * b[:, 2]
+
+
+def _quad_geometry(q: np.ndarray):
+    """Centres and area vectors of quadrilaterals q [M, 4, 3]: triangles (p_i, p_i+1, c) about
+    the average point c of the four points; the area vector is half the sum of the triangle
+    normals (p_i+1 - p_i) x (c - p_i), the centre the triangle centroids weighted by the
+    normals' lengths."""
+    fc = (((q[:, 0] + q[:, 1]) + q[:, 2]) + q[:, 3]) / 4.0
+    sumN = np.zeros_like(fc)
+    sumA = np.zeros(len(q))
+    sumAc = np.zeros_like(fc)
+    for p in range(4):
+        a, b = q[:, p], q[:, (p + 1) % 4]
+        e, t = b - a, fc - a
+        n = np.stack([e[:, 1] * t[:, 2] - e[:, 2] * t[:, 1], e[:, 2] * t[:, 0] - e[:, 0] * t[:, 2],
+                      e[:, 0] * t[:, 1] - e[:, 1] * t[:, 0]], axis=1)
+        mag = np.sqrt(_dot3(n, n))
+        sumN += n
+        sumA += mag
+        sumAc += mag[:, None] * ((a + b) + fc)
+    ok = sumA > 1e-300
+    Cf = np.where(ok[:, None], (1.0 / 3.0) * sumAc / np.where(ok, sumA, 1.0)[:, None], fc)
+    return Cf, 0.5 * sumN
+
+
+def hex_mesh(case: lapcase.RawCase):
+    """LDU mesh and geometry of a general hexahedral box (``case.points``; natural
+    numbering). Face point order as documented in :mod:`lapcase`. Returns
+    (LduMesh, HexGeometry); the mesh's deltaCoeffs are the non-orthogonal implicit
+    coefficients 1 / max(n.d, 0.05 |d|) and bdeltaCoeffs the inverse patch-normal
+    distances 1 / |n.(Cf - C_P)|."""
+    if case.points is None:
+        raise ValueError("case has no vertex array")
+    if case.perm is not None:
+        raise ValueError("general hexahedral boxes use natural numbering")
+    nx, ny, nz = case.nx, case.ny, case.nz
+    P = np.asarray(case.points, dtype=np.float64)
+    if P.shape != (nz + 1, ny + 1, nx + 1, 3):
+        raise ValueError("points must have shape (nz+1, ny+1, nx+1, 3)")
+    base = box_mesh(case)  # topology, patches and per-face DT (natural numbering)
+    N, F, NB = base.n_cells, base.n_faces, base.n_bfaces
+    nat = np.arange(N, dtype=np.int64).reshape(nz, ny, nx)
+
+    def quads(*corners):
+        return np.stack([c.reshape(-1, 3) for c in corners], axis=1)
+
+    # internal faces by direction, then merged into (owner, neighbour) order
+    qx = quads(P[:-1, :-1, 1:-1], P[:-1, 1:, 1:-1], P[1:, 1:, 1:-1], P[1:, :-1, 1:-1])
+    qy = quads(P[:-1, 1:-1, :-1], P[1:, 1:-1, :-1], P[1:, 1:-1, 1:], P[:-1, 1:-1, 1:])
+    qz = quads(P[1:-1, :-1, :-1], P[1:-1, :-1, 1:], P[1:-1, 1:, 1:], P[1:-1, 1:, :-1])
+    own = np.concatenate([nat[:, :, :-1].ravel(), nat[:, :-1, :].ravel(), nat[:-1, :, :].ravel()])
+    nei = np.concatenate([nat[:, :, 1:].ravel(), nat[:, 1:, :].ravel(), nat[1:, :, :].ravel()])
+    order = np.lexsort((nei, own))
+    q = np.concatenate([qx, qy, qz])[order]
+    assert np.array_equal(own[order], base.owner) and np.array_equal(nei[order], base.neighbour)
+    Cf, Sf = _quad_geometry(q)
+
+    # boundary faces: x0, x1 over (k, j); y0, y1 over (k, i); z0, z1 over (j, i)
+    bq = np.concatenate([
+        quads(P[:-1, :-1, 0], P[1:, :-1, 0], P[1:, 1:, 0], P[:-1, 1:, 0]),
+        quads(P[:-1, :-1, nx], P[:-1, 1:, nx], P[1:, 1:, nx], P[1:, :-1, nx]),
+        quads(P[:-1, 0, :-1], P[:-1, 0, 1:], P[1:, 0, 1:], P[1:, 0, :-1]),
+        quads(P[:-1, ny, :-1], P[1:, ny, :-1], P[1:, ny, 1:], P[:-1, ny, 1:]),
+        quads(P[0, :-1, :-1], P[0, 1:, :-1], P[0, 1:, 1:], P[0, :-1, 1:]),
+        quads(P[nz, :-1, :-1], P[nz, :-1, 1:], P[nz, 1:, 1:], P[nz, 1:, :-1]),
+    ])
+    bCf, bSf = _quad_geometry(bq)
+    bcell = base.bface_cell.astype(np.int64)
+    owner, neighbour = base.owner.astype(np.int64), base.neighbour.astype(np.int64)
+
+    # cell centres and volumes: pyramids from each face to the average of the face centres,
+    # contributions taken face by face (owner, then neighbour), boundary faces last
+    targets = np.concatenate([np.stack([owner, neighbour], 1).ravel(), bcell])
+    cEst = np.zeros((N, 3))
+    np.add.at(cEst, targets, np.concatenate([np.repeat(Cf, 2, axis=0), bCf]))
+    cEst /= np.bincount(targets, minlength=N)[:, None].astype(np.float64)
+    fcs = np.concatenate([np.repeat(Cf, 2, axis=0), bCf])
+    sfs = np.concatenate([np.repeat(Sf, 2, axis=0), bSf])
+    sign_out = np.concatenate([np.tile([1.0, -1.0], F), np.ones(NB)])  # outward from the target cell
+    pv = np.maximum(sign_out * _dot3(sfs, fcs - cEst[targets]), 1e-300)
+    Csum = np.zeros((N, 3))
+    vol = np.zeros(N)
+    np.add.at(Csum, targets, pv[:, None] * (0.75 * fcs + 0.25 * cEst[targets]))
+    np.add.at(vol, targets, pv)
+    C = Csum / vol[:, None]
+    V = vol / 3.0
+
+    # interpolation weights, implicit coefficients, correction vectors
+    SfdOwn = np.abs(_dot3(Sf, Cf - C[owner]))
+    SfdNei = np.abs(_dot3(Sf, C[neighbour] - Cf))
+    tot = SfdOwn + SfdNei
+    weights = np.where(np.abs(tot) > 1e-150, SfdNei / np.where(tot != 0, tot, 1.0), 0.5)
+    magSf = np.sqrt(_dot3(Sf, Sf))
+    n = Sf / magSf[:, None]
+    d = C[neighbour] - C[owner]
+    nd = np.maximum(_dot3(n, d), 0.05 * np.sqrt(_dot3(d, d)))
+    delta = 1.0 / nd
+    corr = n - d * delta[:, None]
+    bmagSf = np.sqrt(_dot3(bSf, bSf))
+    bn = bSf / bmagSf[:, None]
+    bdelta = 1.0 / np.abs(_dot3(bn, bCf - C[bcell]))
+
+    mesh = dataclasses.replace(base, V=V, magSf=np.ascontiguousarray(magSf), deltaCoeffs=np.ascontiguousarray(delta),
+                               bmagSf=np.ascontiguousarray(bmagSf), bdeltaCoeffs=np.ascontiguousarray(bdelta))
+    geo = HexGeometry(Sf=np.ascontiguousarray(Sf), weights=np.ascontiguousarray(weights),
+                      corr_vec=np.ascontiguousarray(corr), bSf=np.ascontiguousarray(bSf), Cf=Cf, bCf=bCf, C=C)
+    return mesh, geo

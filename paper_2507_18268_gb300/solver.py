@@ -12,7 +12,7 @@ import numpy as np
 import lapcase
 
 from . import binding as B
-from .mesh import LduMesh, box_mesh, field_by_label
+from .mesh import HexGeometry, LduMesh, box_mesh, field_by_label, hex_mesh
 
 
 def _stream_handle(stream) -> Optional[int]:
@@ -38,7 +38,8 @@ class Solver:
     (another Solver whose uploaded mesh this one uses) gives the mesh."""
 
     def __init__(self, mesh: Optional[LduMesh] = None, device: int = 0, stream=None, workspace: str = "torch",
-                 layout: int = B.LFM_BOTH, box=None, share: Optional["Solver"] = None):
+                 layout: int = B.LFM_BOTH, box=None, share: Optional["Solver"] = None,
+                 geometry: Optional[HexGeometry] = None):
         assert (mesh is not None) + (box is not None) + (share is not None) == 1
         self.device = device
         self.stream = stream
@@ -48,7 +49,8 @@ class Solver:
         try:
             if mesh is not None:
                 self.mesh = mesh
-                nbytes = B.lfm_workspace_bytes(mesh, layout)
+                nbytes = (B.lfm_workspace_bytes(mesh, layout) if geometry is None
+                          else B.lfm_workspace_bytes_geometry(mesh, layout))
             elif box is not None:
                 xs, ys, zs = box
                 n, f, nb, _ = B.lfm_box_counts(len(xs) - 1, len(ys) - 1, len(zs) - 1)
@@ -63,7 +65,9 @@ class Solver:
 
                 self._ws = torch.empty(nbytes, dtype=torch.uint8, device=f"cuda:{device}")
                 B.lfm_bind_workspace(self.ctx, self._ws.data_ptr(), nbytes, layout)
-            if mesh is not None:
+            if mesh is not None and geometry is not None:
+                B.lfm_upload_mesh_geometry(self.ctx, mesh, geometry)
+            elif mesh is not None:
                 B.lfm_upload_mesh(self.ctx, mesh)
             elif box is not None:
                 B.lfm_upload_box(self.ctx, *box)
@@ -76,9 +80,14 @@ class Solver:
 
     # ---- configuration ---------------------------------------------------------------
     @classmethod
-    def from_case(cls, case: lapcase.RawCase, mesh: Optional[LduMesh] = None, **kw) -> "Solver":
+    def from_case(cls, case: lapcase.RawCase, mesh: Optional[LduMesh] = None,
+                  geometry: Optional[HexGeometry] = None, **kw) -> "Solver":
+        """A case on a host-built mesh: the rectilinear box, or with ``case.points`` the
+        general hexahedral mesh and its geometry (corrected laplacian)."""
+        if mesh is None and case.points is not None:
+            mesh, geometry = hex_mesh(case)
         mesh = mesh or box_mesh(case)
-        s = cls(mesh, **kw)
+        s = cls(mesh, geometry=geometry, **kw)
         s.configure(case)
         return s
 
@@ -109,6 +118,7 @@ class Solver:
             B.lfm_set_patch(self.ctx, p, int(ptype), None, float(value))
         B.lfm_set_time_step(self.ctx, case.dt)
         B.lfm_set_solver(self.ctx, case.tol, case.rel_tol, case.max_iter, case.min_iter, case.precision)
+        B.lfm_set_nonorth_correctors(self.ctx, int(case.n_nonorth_corr))
         if field:
             if np.isscalar(case.T0):
                 B.lfm_fill_field(self.ctx, float(case.T0))
@@ -119,6 +129,10 @@ class Solver:
 
     def set_solver(self, tol, rel_tol=0.0, max_iter=1000, min_iter=0, precision=B.LFM_FP64):
         B.lfm_set_solver(self.ctx, tol, rel_tol, max_iter, min_iter, precision)
+
+    def grad(self, boundary: bool = True):
+        """Gauss linear gradient of the current T: (cells [N, 3], boundary faces [NB, 3])."""
+        return B.lfm_grad(self.ctx, self.mesh.n_cells, self.mesh.n_bfaces, boundary)
 
     def set_field(self, T: np.ndarray):
         B.lfm_set_field(self.ctx, T)
