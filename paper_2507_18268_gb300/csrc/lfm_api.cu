@@ -37,7 +37,7 @@ struct Layout {
   size_t slot_other, slot_face, face_slots, b_start, b_face, bcell, btype;
   size_t V, magSf, delta, DT, bmagSf, bdelta, bDT, bval;
   size_t diag, upper, slot_coef, src, rD, vdt, x, x_old, r, w, p, q, Tb;
-  size_t Sf, fw, corr, bSf, grad, cflux;  // general geometry (0 when absent)
+  size_t Sf, fw, corr, bSf, gE, gD, gH, cK, cL, grad;  // general geometry (0 when absent)
   size_t diag32, slot_coef32, rD32, dx32, r32, w32, p32, q32;
   size_t total;
 };
@@ -77,11 +77,15 @@ Layout make_layout(int64_t N, int64_t F, int64_t NB, int64_t W, int kind, bool s
       L.fw = take(8 * F);
       L.corr = take(24 * F);
       L.bSf = take(24 * NB);
+      L.gE = take(24 * W * N);
     }
   }
   if (geom) {
     L.grad = take(24 * N);
-    L.cflux = take(8 * F);
+    L.gD = take(24 * N);
+    L.gH = take(24 * N);
+    L.cK = take(24 * N);
+    L.cL = take(24 * W * N);
   }
   L.btype = take(4 * NB);
   L.DT = take(8 * F);
@@ -159,6 +163,7 @@ struct lfm_ctx {
   lfm_solver_opts opts{1e-6, 0.0, 1000, 0, LFM_FP64};
   bool has64 = false, has32 = false;  // solver blocks present in the workspace
   bool has_geom = false;              // general geometry uploaded (corrected laplacian)
+  bool ops_dirty = false;             // operator weights to rebuild before the next launch
   int32_t n_corr = 0;                 // non-orthogonal corrector passes per step
 
   // launch
@@ -381,6 +386,7 @@ void bind_pointers(lfm_ctx* c) {
     cs.fw = m.fw;
     cs.corr = m.corr;
     cs.bSf = m.bSf;
+    cs.gE = m.gE;
   } else {
     cs.slot_other = reinterpret_cast<const int32_t*>(b + L.slot_other);
     cs.slot_face = reinterpret_cast<const int32_t*>(b + L.slot_face);
@@ -398,9 +404,14 @@ void bind_pointers(lfm_ctx* c) {
     cs.fw = g ? reinterpret_cast<const double*>(b + L.fw) : nullptr;
     cs.corr = g ? reinterpret_cast<const double*>(b + L.corr) : nullptr;
     cs.bSf = g ? reinterpret_cast<const double*>(b + L.bSf) : nullptr;
+    cs.gE = g ? reinterpret_cast<const double*>(b + L.gE) : nullptr;
   }
-  cs.grad = c->has_geom ? reinterpret_cast<double*>(b + L.grad) : nullptr;
-  cs.cflux = c->has_geom ? reinterpret_cast<double*>(b + L.cflux) : nullptr;
+  const bool gc = c->has_geom;
+  cs.grad = gc ? reinterpret_cast<double*>(b + L.grad) : nullptr;
+  cs.gD = gc ? reinterpret_cast<const double*>(b + L.gD) : nullptr;
+  cs.gH = gc ? reinterpret_cast<const double*>(b + L.gH) : nullptr;
+  cs.cK = gc ? reinterpret_cast<const double*>(b + L.cK) : nullptr;
+  cs.cL = gc ? reinterpret_cast<const double*>(b + L.cL) : nullptr;
   cs.x_old = reinterpret_cast<double*>(b + L.x_old);
   cs.diag = reinterpret_cast<double*>(b + L.diag);
   cs.upper = reinterpret_cast<double*>(b + L.upper);
@@ -433,6 +444,17 @@ int refresh_vdt(lfm_ctx* c) {
   return LFM_OK;
 }
 
+// Rebuilds the case's operator weights (general geometry) when patches, boundary values or
+// DT changed since the last launch. Enqueued on the context's stream.
+int refresh_ops(lfm_ctx* c) {
+  if (!c->has_geom || !c->ops_dirty) return LFM_OK;
+  refresh_case(c);
+  CK(c, launch_geom_ops(c->cs, false, c->stream));
+  CK(c, cudaStreamSynchronize(c->stream));  // batches launch on their own stream
+  c->ops_dirty = false;
+  return LFM_OK;
+}
+
 int need_uploaded(lfm_ctx* c) {
   if (!c) return fail_free(LFM_EINVAL, "context is NULL");
   if (!c->uploaded) return fail(c, LFM_ESTATE, "no mesh uploaded");
@@ -443,6 +465,7 @@ int need_uploaded(lfm_ctx* c) {
 // and status into pinned host memory.
 int enqueue_chunk(lfm_ctx* c, int steps, int mode) {
   refresh_case(c);
+  if (int rc = refresh_ops(c)) return rc;
   int e = 0;
   Launch L = current_launch(c, e);
   if (e) return fail(c, LFM_ECUDA, "no co-resident CTA fits the step kernel");
@@ -641,6 +664,7 @@ static int upload_mesh_impl(lfm_ctx* c, const lfm_mesh* m, const lfm_geometry* g
   if (geo && ((rc = h2d(c, Y.Sf, geo->Sf, 3 * (size_t)F)) || (rc = h2d(c, Y.fw, geo->weights, F)) ||
               (rc = h2d(c, Y.corr, geo->corr_vec, 3 * (size_t)F)) || (rc = h2d(c, Y.bSf, geo->bSf, 3 * (size_t)NB))))
     return rc;
+  c->ops_dirty = geo != nullptr;
   if (WN > 0) {
     CK(c, cudaMemsetAsync(c->ws + Y.slot_coef, 0, sizeof(double) * WN, c->stream));
     if (has32) CK(c, cudaMemsetAsync(c->ws + Y.slot_coef32, 0, sizeof(float) * WN, c->stream));
@@ -649,6 +673,10 @@ static int upload_mesh_impl(lfm_ctx* c, const lfm_mesh* m, const lfm_geometry* g
   c->cs.DT_is_uniform = 1;
   c->cs.DT_uniform = 0.0;
   CK(c, cudaMemsetAsync(c->ws + Y.x, 0, sizeof(double) * N, c->stream));
+  if (geo) {  // the geometry-only gradient weights, once per mesh (meshes sharing it read them)
+    refresh_case(c);
+    CK(c, launch_geom_ops(c->cs, true, c->stream));
+  }
   CK(c, cudaStreamSynchronize(c->stream));
   c->dt = 1.0;
   c->opts = lfm_solver_opts{1e-6, 0.0, 1000, 0, has64 ? LFM_FP64 : LFM_MIXED};
@@ -839,6 +867,7 @@ int lfm_upload_mesh_shared(lfm_ctx* c, lfm_ctx* src) {
   c->has64 = has64;
   c->has32 = has32;
   c->has_geom = root->has_geom;
+  c->ops_dirty = root->has_geom;
   c->n_corr = 0;
   c->n_patches = root->n_patches;
   c->patch_start = root->patch_start;
@@ -903,6 +932,7 @@ int lfm_set_diffusivity(lfm_ctx* c, double uniform, const double* DT_faces, cons
     CK(c, launch_fill(const_cast<double*>(c->cs.bDT), c->NB, uniform, c->stream));
   }
   CK(c, cudaStreamSynchronize(c->stream));
+  c->ops_dirty = true;
   return LFM_OK;
 }
 
@@ -924,6 +954,7 @@ int lfm_set_patch(lfm_ctx* c, int32_t patch, int32_t type, const double* values,
   if (type == LFM_FIXED_VALUE && (rc = h2d(c, c->lay.bval + 8 * (size_t)s, vals.data(), n))) return rc;
   CK(c, cudaStreamSynchronize(c->stream));
   c->patch_type[patch] = type;
+  c->ops_dirty = true;
   return LFM_OK;
 }
 
@@ -971,19 +1002,24 @@ int lfm_grad(lfm_ctx* c, double* grad, double* bgrad) {
   if (c->pending_steps > 0) return fail(c, LFM_ESTATE, "an advance is pending");
   DeviceGuard g(c->device);
   refresh_case(c);
+  if ((rc = refresh_ops(c))) return rc;
   double* bdev = nullptr;
   if (bgrad && c->NB > 0) {
     cudaError_t e = cudaMalloc(&bdev, sizeof(double) * 3 * (size_t)c->NB);
     if (e != cudaSuccess) return fail(c, LFM_ENOMEM, "boundary gradient buffer: %s", cudaGetErrorString(e));
   }
+  const size_t N = (size_t)c->N;
+  std::vector<double> soa(3 * N);
   cudaError_t e = launch_grad(c->cs, bdev, c->stream);
   if (e == cudaSuccess)
-    e = cudaMemcpyAsync(grad, c->cs.grad, sizeof(double) * 3 * (size_t)c->N, cudaMemcpyDeviceToHost, c->stream);
+    e = cudaMemcpyAsync(soa.data(), c->cs.grad, sizeof(double) * 3 * N, cudaMemcpyDeviceToHost, c->stream);
   if (e == cudaSuccess && bdev)
     e = cudaMemcpyAsync(bgrad, bdev, sizeof(double) * 3 * (size_t)c->NB, cudaMemcpyDeviceToHost, c->stream);
   if (e == cudaSuccess) e = cudaStreamSynchronize(c->stream);
   if (bdev) cudaFree(bdev);
   if (e != cudaSuccess) return cuda_fail(c, e, "lfm_grad");
+  for (size_t i = 0; i < N; ++i)
+    for (int d = 0; d < 3; ++d) grad[3 * i + d] = soa[d * N + i];  // cell-major for the caller
   return LFM_OK;
 }
 
@@ -1409,6 +1445,7 @@ int lfm_batch_advance_async(lfm_batch* b, int32_t n_steps, int32_t use_graph) {
     lfm_ctx* c = b->slots[b->order[i]];
     if (c->pending_steps) return bfail(b, LFM_ESTATE, "case %d has a pending advance of its own", b->order[i]);
     refresh_case(c);
+    if (refresh_ops(c) != LFM_OK) return bfail(b, LFM_ECUDA, "case %d: operator rebuild failed", b->order[i]);
     if ((c->opts.precision == LFM_FP64 && !c->has64) || (c->opts.precision == LFM_MIXED && !c->has32))
       return bfail(b, LFM_ENOMEM, "case %d has no buffers for its precision", b->order[i]);
     b->h_cases[i] = c->cs;

@@ -72,13 +72,22 @@ struct CaseDev {
 
   // general (non-orthogonal) geometry; null for orthogonal meshes. With it, delta holds the
   // implicit (nonOrthDeltaCoeffs) coefficients and the corrected laplacian adds an explicit
-  // flux DT |Sf| k_f . (w_f (G_P - G_N) + G_N) from the Gauss gradient G of the current T.
-  const double* Sf;          // [3F] internal face area vectors, owner -> neighbour
+  // flux DT |Sf| k_f . (w_f G_P + (1 - w_f) G_N) from the Gauss gradient G of the current T.
+  const double* Sf;          // [3F] internal face area vectors, owner -> neighbour (x,y,z)
   const double* fw;          // [F]  interpolation weight of the owner value
-  const double* corr;        // [3F] correction vectors k_f
-  const double* bSf;         // [3NB] boundary face area vectors, outward
-  double* grad;              // [3N] Gauss gradient of T (per assembly)
-  double* cflux;             // [F]  explicit correction flux (per assembly)
+  const double* corr;        // [3F] correction vectors k_f (x,y,z)
+  const double* bSf;         // [3NB] boundary face area vectors, outward (x,y,z)
+  // Both are linear in T, so they are applied as operators whose weights are built from the
+  // geometry (and the case's patches and DT) when those change. Component-major layout:
+  // component d of cell c at d*N + c, of slot k of cell c at d*W*N + k*N + c.
+  //   G_c = gD_c T_c + gH_c + sum_k gE_ck T_other(k)
+  //   correction source of row c = cK_c . G_c + sum_k cL_ck . G_other(k)
+  const double* gE;          // [3*W*N] (geometry only; shared with meshes that share this one)
+  const double* gD;          // [3N]
+  const double* gH;          // [3N]    fixedValue boundary faces
+  const double* cK;          // [3N]
+  const double* cL;          // [3*W*N]
+  double* grad;              // [3N]    Gauss gradient of T (per assembly), component-major
   double* x_old;             // [N]  T at the start of the step (non-orthogonal correctors)
   int32_t n_corr;            // extra corrector passes per step (nNonOrthogonalCorrectors)
 
@@ -146,8 +155,11 @@ cudaError_t launch_steps(const CaseDev& cs, const Launch& L, int n_steps, int mo
 int max_coresident_ctas(int precision, int threads, int W, int device);
 cudaError_t launch_boundary_values(const CaseDev& cs, double* Tb, cudaStream_t stream);
 // Gauss linear gradient of the current T: cells into cs.grad, and (bgrad non-null) the
-// corrected boundary values [3NB].
+// corrected boundary values [3NB] (x,y,z per face).
 cudaError_t launch_grad(const CaseDev& cs, double* bgrad, cudaStream_t stream);
+// Operator weights of the general-geometry path: gE (geometry only) when `with_E`, and the
+// case's gD, gH, cK, cL (patches, boundary values, DT).
+cudaError_t launch_geom_ops(const CaseDev& cs, bool with_E, cudaStream_t stream);
 
 // Box meshes built from closed forms (lfm_box.cu).
 int box_slot_width(long long nx, long long ny, long long nz);

@@ -154,86 +154,52 @@ __device__ __forceinline__ void row_boundary(const CaseDev& cs, int c, double xo
 }
 
 // ---- general geometry: Gauss gradient and the explicit non-orthogonal correction ---------
-// Sum over the cell's faces of the correction flux, + for faces it owns and - for the
-// others, in slot order (the same order as a scatter over faces in face order).
-__device__ __forceinline__ double corr_source(const CaseDev& cs, int c) {
+// Gauss linear gradient of x at cell c through the operator weights (gD, gH, gE; see
+// CaseDev): one fused multiply-add per slot and component.
+template <int W>
+__device__ __forceinline__ void op_grad(const CaseDev& cs, int c, const double* __restrict__ x, double* g) {
   const size_t N = (size_t)cs.N;
-  double v = 0.0;
-  for (int k = 0; k < cs.W; ++k) {
+  const int ns = W > 0 ? W : cs.W;
+  const size_t WN = (size_t)ns * N;
+  const double xc = x[c];
+  double g0 = fma(__ldg(cs.gD + c), xc, __ldg(cs.gH + c));
+  double g1 = fma(__ldg(cs.gD + N + c), xc, __ldg(cs.gH + N + c));
+  double g2 = fma(__ldg(cs.gD + 2 * N + c), xc, __ldg(cs.gH + 2 * N + c));
+#pragma unroll
+  for (int k = 0; k < (W > 0 ? W : kMaxSlots); ++k) {
+    if (W == 0 && k >= ns) break;
     const size_t at = (size_t)k * N + c;
-    const int f = __ldg(cs.slot_face + at);
-    if (f < 0) break;  // padding comes last
-    const double fl = cs.cflux[f];
-    v = __ldg(cs.slot_other + at) > c ? __dadd_rn(v, fl) : __dsub_rn(v, fl);
+    const double xo = x[__ldg(cs.slot_other + at)];
+    g0 = fma(__ldg(cs.gE + at), xo, g0);
+    g1 = fma(__ldg(cs.gE + WN + at), xo, g1);
+    g2 = fma(__ldg(cs.gE + 2 * WN + at), xo, g2);
+  }
+  g[0] = g0;
+  g[1] = g1;
+  g[2] = g2;
+}
+
+// Explicit correction source of row c: the sum over the cell's faces of the correction flux
+// (+ where it owns the face, - where it is the neighbour), through the weights cK, cL.
+template <int W>
+__device__ __forceinline__ double op_corr_source(const CaseDev& cs, int c) {
+  const size_t N = (size_t)cs.N;
+  const int ns = W > 0 ? W : cs.W;
+  const size_t WN = (size_t)ns * N;
+  const double* G = cs.grad;
+  double v = __ldg(cs.cK + c) * G[c];
+  v = fma(__ldg(cs.cK + N + c), G[N + c], v);
+  v = fma(__ldg(cs.cK + 2 * N + c), G[2 * N + c], v);
+#pragma unroll
+  for (int k = 0; k < (W > 0 ? W : kMaxSlots); ++k) {
+    if (W == 0 && k >= ns) break;
+    const size_t at = (size_t)k * N + c;
+    const int o = __ldg(cs.slot_other + at);
+    v = fma(__ldg(cs.cL + at), G[o], v);
+    v = fma(__ldg(cs.cL + WN + at), G[N + o], v);
+    v = fma(__ldg(cs.cL + 2 * WN + at), G[2 * N + o], v);
   }
   return v;
-}
-
-// Gauss linear gradient of x at cell c (section "Code Porting": face values
-// w (x_P - x_N) + x_N, the Gauss sum Sf x_f over the cell's faces -- + where it owns the
-// face, - where it is the neighbour -- and its boundary faces, divided by V). Faces are
-// taken in slot order, which is face order, as in a scatter over faces; the division is a
-// multiplication by the rounded reciprocal of V.
-__device__ __forceinline__ void cell_grad(const CaseDev& cs, int c, const double* __restrict__ x, double* g) {
-  const size_t N = (size_t)cs.N;
-  const double xc = x[c];
-  double gx = 0.0, gy = 0.0, gz = 0.0;
-  for (int k = 0; k < cs.W; ++k) {
-    const size_t at = (size_t)k * N + c;
-    const int f = __ldg(cs.slot_face + at);
-    if (f < 0) break;
-    const int o = __ldg(cs.slot_other + at);
-    const bool own = o > c;
-    const double xo = x[o];
-    const double xP = own ? xc : xo, xN = own ? xo : xc;
-    const double xf = __dadd_rn(__dmul_rn(__ldg(cs.fw + f), __dsub_rn(xP, xN)), xN);
-    const double vx = __dmul_rn(__ldg(cs.Sf + 3 * (size_t)f), xf);
-    const double vy = __dmul_rn(__ldg(cs.Sf + 3 * (size_t)f + 1), xf);
-    const double vz = __dmul_rn(__ldg(cs.Sf + 3 * (size_t)f + 2), xf);
-    if (own) {
-      gx = __dadd_rn(gx, vx);
-      gy = __dadd_rn(gy, vy);
-      gz = __dadd_rn(gz, vz);
-    } else {
-      gx = __dsub_rn(gx, vx);
-      gy = __dsub_rn(gy, vy);
-      gz = __dsub_rn(gz, vz);
-    }
-  }
-  const int b0 = __ldg(cs.b_start + c), b1 = __ldg(cs.b_start + c + 1);
-  for (int k = b0; k < b1; ++k) {
-    const int bf = __ldg(cs.b_face + k);
-    const double xb = __ldg(cs.btype + bf) == LFM_FIXED_VALUE ? __ldg(cs.bval + bf) : xc;
-    gx = __dadd_rn(gx, __dmul_rn(__ldg(cs.bSf + 3 * (size_t)bf), xb));
-    gy = __dadd_rn(gy, __dmul_rn(__ldg(cs.bSf + 3 * (size_t)bf + 1), xb));
-    gz = __dadd_rn(gz, __dmul_rn(__ldg(cs.bSf + 3 * (size_t)bf + 2), xb));
-  }
-  const double rv = __drcp_rn(__ldg(cs.V + c));
-  g[0] = gx * rv;
-  g[1] = gy * rv;
-  g[2] = gz * rv;
-}
-
-// Explicit correction flux of face f: DT |Sf| k . (w (G_P - G_N) + G_N), the face value of
-// the gradient by the same linear interpolation (dotInterpolate of the correction vectors),
-// products and sums rounded separately. Owner and neighbour come from the face's two slots.
-__device__ __forceinline__ double face_corr_flux(const CaseDev& cs, int f) {
-  const uint2 at = __ldg(reinterpret_cast<const uint2*>(cs.face_slots) + f);
-  const int P = __ldg(cs.slot_other + at.y), Q = __ldg(cs.slot_other + at.x);
-  const double w = __ldg(cs.fw + f);
-  const double* gP = cs.grad + 3 * (size_t)P;
-  const double* gQ = cs.grad + 3 * (size_t)Q;
-  const double* k = cs.corr + 3 * (size_t)f;
-  double dot = 0.0;
-#pragma unroll
-  for (int d = 0; d < 3; ++d) {
-    const double gq = gQ[d];
-    const double gf = __dadd_rn(__dmul_rn(w, __dsub_rn(gP[d], gq)), gq);
-    const double t = __dmul_rn(__ldg(k + d), gf);
-    dot = d == 0 ? t : __dadd_rn(dot, t);
-  }
-  const double DTf = cs.DT_is_uniform ? cs.DT_uniform : __ldg(cs.DT + f);
-  return __dmul_rn(__dmul_rn(DTf, __ldg(cs.magSf + f)), dot);
 }
 
 // kCorr: the step has non-orthogonal corrector passes or general geometry: the ddt source
@@ -270,7 +236,7 @@ __device__ __forceinline__ Row assemble_row(const CaseDev& cs, int c, const doub
     }
   }
   row_boundary(cs, c, kCorr && cs.n_corr > 0 ? cs.x_old[c] : o.xc, o);
-  if (kCorr && cs.cflux) o.s = __dadd_rn(o.s, corr_source(cs, c));
+  if (kCorr && cs.Sf) o.s = __dadd_rn(o.s, op_corr_source<W>(cs, c));
   o.ax = fma(o.d, o.xc, off);
   return o;
 }
@@ -316,24 +282,18 @@ __device__ __noinline__ double pass_faces(const CaseDev& cs, int f0, int f1, int
 }
 
 // Gauss gradient of T over the cells [c0, c1) into cs.grad (same phase as the face pass:
-// it reads only T and the geometry).
-template <int B>
+// it reads only T and the operator weights).
+template <int B, int W>
 __device__ __noinline__ void pass_grad(const CaseDev& cs, int c0, int c1) {
   double* __restrict__ G = cs.grad;
+  const size_t N = (size_t)cs.N;
   for (int c = c0 + (int)threadIdx.x; c < c1; c += B) {
     double g[3];
-    cell_grad(cs, c, cs.x, g);
-    G[3 * (size_t)c] = g[0];
-    G[3 * (size_t)c + 1] = g[1];
-    G[3 * (size_t)c + 2] = g[2];
+    op_grad<W>(cs, c, cs.x, g);
+    G[c] = g[0];
+    G[N + c] = g[1];
+    G[2 * N + c] = g[2];
   }
-}
-
-// Correction fluxes of the faces [f0, f1) into cs.cflux (after the gradient's barrier).
-template <int B>
-__device__ __noinline__ void pass_corr_flux(const CaseDev& cs, int f0, int f1) {
-  double* __restrict__ out = cs.cflux;
-  for (int f = f0 + (int)threadIdx.x; f < f1; f += B) out[f] = face_corr_flux(cs, f);
 }
 
 // Pass 2 alone, for matrix read-back (every array of the assembled system written).
@@ -658,21 +618,15 @@ __device__ __forceinline__ void write_stats(const CaseDev& cs, const Team& tm, i
 }
 
 // Start of an assembly: the face pass (with the copy of T at the start of the step when
-// save_old, and with general geometry the Gauss gradient in the same phase), the team sum
-// of T for xRef, then with general geometry the correction-flux pass. False when a barrier
-// failed (the caller leaves the kernel).
-template <int B, bool kMixed>
+// save_old, and with general geometry the Gauss gradient in the same phase) and the team sum
+// of T for xRef. False when a barrier failed (the caller leaves the kernel).
+template <int B, int W, bool kMixed>
 __device__ __forceinline__ bool assemble_prologue(const CaseDev& cs, const CaseDev& cref, const Team& tm, int c0,
                                                   int c1, int f0, int f1, bool write_upper, bool save_old,
                                                   double& sum_x, TeamShared& sh) {
   double v[1] = {pass_faces<B, kMixed>(cref, f0, f1, c0, c1, write_upper, save_old)};
-  const bool geom = cs.Sf != nullptr;
-  if (geom) pass_grad<B>(cref, c0, c1);
+  if (cs.Sf) pass_grad<B, W>(cref, c0, c1);
   if (!team_allreduce<1>(tm, v, sh)) return false;
-  if (geom) {
-    pass_corr_flux<B>(cref, f0, f1);
-    if (!team_barrier(tm, sh)) return false;
-  }
   sum_x = v[0];
   return true;
 }
@@ -704,7 +658,7 @@ __device__ void run_steps_f64(const CaseDev& cs, const CaseDev& cref, const Team
     for (int pass = 0; pass <= cs.n_corr; ++pass) {
       // ---- A1: face coefficients, sum of T (and the gradient / correction fluxes) --------
       double sum_x = 0.0;
-      if (!assemble_prologue<B, false>(cs, cref, tm, c0, c1, f0, f1, mode == kModeAssembleOnly,
+      if (!assemble_prologue<B, W, false>(cs, cref, tm, c0, c1, f0, f1, mode == kModeAssembleOnly,
                                        pass == 0 && cs.n_corr > 0, sum_x, sh))
         return;
       clk.lap(kPhAssembly);
@@ -804,7 +758,7 @@ __device__ void run_steps_mixed(const CaseDev& cs, const CaseDev& cref, const Te
     bool conv = false;
     for (int pass = 0; pass <= cs.n_corr; ++pass) {
       double sum_x = 0.0;
-      if (!assemble_prologue<B, true>(cs, cref, tm, c0, c1, f0, f1, mode == kModeAssembleOnly,
+      if (!assemble_prologue<B, W, true>(cs, cref, tm, c0, c1, f0, f1, mode == kModeAssembleOnly,
                                       pass == 0 && cs.n_corr > 0, sum_x, sh))
         return;
       clk.lap(kPhAssembly);

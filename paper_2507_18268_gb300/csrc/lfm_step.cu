@@ -37,15 +37,15 @@ __global__ void boundary_values_kernel(CaseDev cs, double* Tb) {
   if (b < cs.NB) Tb[b] = cs.btype[b] == LFM_FIXED_VALUE ? cs.bval[b] : cs.x[cs.bcell[b]];
 }
 
-// Gauss gradient of the current T per cell (into cs.grad).
+// Gauss gradient of the current T per cell (into cs.grad, component-major).
 __global__ void grad_cells_kernel(CaseDev cs) {
   const int c = blockIdx.x * blockDim.x + threadIdx.x;
   if (c < cs.N) {
     double g[3];
-    cell_grad(cs, c, cs.x, g);
-    cs.grad[3 * (size_t)c] = g[0];
-    cs.grad[3 * (size_t)c + 1] = g[1];
-    cs.grad[3 * (size_t)c + 2] = g[2];
+    op_grad<0>(cs, c, cs.x, g);
+    cs.grad[c] = g[0];
+    cs.grad[(size_t)cs.N + c] = g[1];
+    cs.grad[2 * (size_t)cs.N + c] = g[2];
   }
 }
 
@@ -55,16 +55,99 @@ __global__ void grad_cells_kernel(CaseDev cs) {
 __global__ void grad_boundary_kernel(CaseDev cs, double* __restrict__ bgrad) {
   const int b = blockIdx.x * blockDim.x + threadIdx.x;
   if (b < cs.NB) {
+    const size_t N = (size_t)cs.N;
     const int c = cs.bcell[b];
     const double* s = cs.bSf + 3 * (size_t)b;
     const double mag = sqrt(s[0] * s[0] + s[1] * s[1] + s[2] * s[2]);
     const double n0 = s[0] / mag, n1 = s[1] / mag, n2 = s[2] / mag;
-    const double* g = cs.grad + 3 * (size_t)c;
+    const double g0 = cs.grad[c], g1 = cs.grad[N + c], g2 = cs.grad[2 * N + c];
     const double sn = cs.btype[b] == LFM_FIXED_VALUE ? (cs.bval[b] - cs.x[c]) * cs.bdelta[b] : 0.0;
-    const double gn = n0 * g[0] + n1 * g[1] + n2 * g[2];
-    bgrad[3 * (size_t)b] = g[0] + n0 * (sn - gn);
-    bgrad[3 * (size_t)b + 1] = g[1] + n1 * (sn - gn);
-    bgrad[3 * (size_t)b + 2] = g[2] + n2 * (sn - gn);
+    const double gn = n0 * g0 + n1 * g1 + n2 * g2;
+    bgrad[3 * (size_t)b] = g0 + n0 * (sn - gn);
+    bgrad[3 * (size_t)b + 1] = g1 + n1 * (sn - gn);
+    bgrad[3 * (size_t)b + 2] = g2 + n2 * (sn - gn);
+  }
+}
+
+// Gradient weights of the slots' other cells (geometry only): the Gauss sum
+// V G_c = sum_faces +-Sf (w T_P + (1 - w) T_N) + sum_boundary bSf T_b gives the other cell of
+// an owned face the weight (1 - w) Sf and of a neighbour-side face -w Sf; divided by V.
+__global__ void grad_weights_kernel(CaseDev cs, double* __restrict__ E) {
+  const int c = blockIdx.x * blockDim.x + threadIdx.x;
+  if (c >= cs.N) return;
+  const size_t N = (size_t)cs.N, WN = (size_t)cs.W * N;
+  const double rv = 1.0 / cs.V[c];
+  for (int k = 0; k < cs.W; ++k) {
+    const size_t at = (size_t)k * N + c;
+    const int f = cs.slot_face[at];
+    double e0 = 0.0, e1 = 0.0, e2 = 0.0;
+    if (f >= 0) {
+      const double w = cs.fw[f];
+      const double coef = (cs.slot_other[at] > c ? 1.0 - w : -w) * rv;
+      e0 = coef * cs.Sf[3 * (size_t)f];
+      e1 = coef * cs.Sf[3 * (size_t)f + 1];
+      e2 = coef * cs.Sf[3 * (size_t)f + 2];
+    }
+    E[at] = e0;
+    E[WN + at] = e1;
+    E[2 * WN + at] = e2;
+  }
+}
+
+// The case's operator weights: the gradient's own-cell weight gD (w Sf for owned faces,
+// -(1 - w) Sf for neighbour-side faces, bSf for zeroGradient boundary faces) and constant gH
+// (bSf T_b for fixedValue faces), both divided by V; and the correction weights: with the
+// face flux a.G_P + b.G_N, a = w DT|Sf| k, b = (1 - w) DT|Sf| k, the row gets +a.G_c + b.G_other
+// for an owned face and -(b.G_c + a.G_other) for a neighbour-side face.
+__global__ void case_ops_kernel(CaseDev cs, double* __restrict__ D, double* __restrict__ H, double* __restrict__ K,
+                                double* __restrict__ L) {
+  const int c = blockIdx.x * blockDim.x + threadIdx.x;
+  if (c >= cs.N) return;
+  const size_t N = (size_t)cs.N, WN = (size_t)cs.W * N;
+  double d[3] = {0.0, 0.0, 0.0}, h[3] = {0.0, 0.0, 0.0}, kk[3] = {0.0, 0.0, 0.0};
+  for (int k = 0; k < cs.W; ++k) {
+    const size_t at = (size_t)k * N + c;
+    const int f = cs.slot_face[at];
+    double l[3] = {0.0, 0.0, 0.0};
+    if (f >= 0) {
+      const double w = cs.fw[f];
+      const double gam = (cs.DT_is_uniform ? cs.DT_uniform : cs.DT[f]) * cs.magSf[f];
+      const bool own = cs.slot_other[at] > c;
+      for (int q = 0; q < 3; ++q) {
+        const double sf = cs.Sf[3 * (size_t)f + q];
+        const double kv = cs.corr[3 * (size_t)f + q];
+        const double a = (w * gam) * kv, bb = ((1.0 - w) * gam) * kv;
+        if (own) {
+          d[q] += w * sf;
+          kk[q] += a;
+          l[q] = bb;
+        } else {
+          d[q] -= (1.0 - w) * sf;
+          kk[q] -= bb;
+          l[q] = -a;
+        }
+      }
+    }
+    L[at] = l[0];
+    L[WN + at] = l[1];
+    L[2 * WN + at] = l[2];
+  }
+  for (int k = cs.b_start[c]; k < cs.b_start[c + 1]; ++k) {
+    const int bf = cs.b_face[k];
+    const bool fv = cs.btype[bf] == LFM_FIXED_VALUE;
+    for (int q = 0; q < 3; ++q) {
+      const double s = cs.bSf[3 * (size_t)bf + q];
+      if (fv)
+        h[q] += s * cs.bval[bf];
+      else
+        d[q] += s;
+    }
+  }
+  const double rv = 1.0 / cs.V[c];
+  for (int q = 0; q < 3; ++q) {
+    D[q * N + c] = d[q] * rv;
+    H[q * N + c] = h[q] * rv;
+    K[q * N + c] = kk[q];
   }
 }
 
@@ -115,6 +198,15 @@ cudaError_t launch_steps(const CaseDev& cs, const Launch& L, int n_steps, int mo
   int a2 = n_steps, a3 = mode;
   void* args[] = {&a0, &a1, &a2, &a3};
   return cudaLaunchCooperativeKernel(fn, dim3(L.ctas), dim3(L.threads), args, 0, stream);
+}
+
+cudaError_t launch_geom_ops(const CaseDev& cs, bool with_E, cudaStream_t stream) {
+  if (!cs.Sf || cs.N == 0) return cudaErrorInvalidValue;
+  const unsigned blocks = (unsigned)((cs.N + 255) / 256);
+  if (with_E) grad_weights_kernel<<<blocks, 256, 0, stream>>>(cs, const_cast<double*>(cs.gE));
+  case_ops_kernel<<<blocks, 256, 0, stream>>>(cs, const_cast<double*>(cs.gD), const_cast<double*>(cs.gH),
+                                              const_cast<double*>(cs.cK), const_cast<double*>(cs.cL));
+  return cudaGetLastError();
 }
 
 cudaError_t launch_grad(const CaseDev& cs, double* bgrad, cudaStream_t stream) {
