@@ -25,6 +25,13 @@
 //   M  q = A p, sigma = p.q                   -> alpha = rho / sigma
 //   U  x += alpha p, r -= alpha q, w = rD r, sum|r|, rho' = w.r -> beta = rho'/rho
 //
+// General (non-orthogonal) meshes (section "Code Porting": the gradient passes): A1 also
+// evaluates the Gauss linear gradient of T per cell, and A2 adds to each row's source the
+// explicit correction of the corrected laplacian (the face fluxes DT |Sf| k . G_f summed
+// over the cell's faces), both through operator weights built from the geometry when it,
+// the patches or DT change. With n_corr > 0 every step runs 1 + n_corr assemble-and-solve
+// passes, the ddt source taken from T at the start of the step (x_old).
+//
 // Mixed step (defect correction, FP64 field x): the matrix is assembled in FP64 and copied
 // to FP32; each sweep computes the FP64 true residual r = b - A x (the first one in the
 // assembly's row pass), solves A dx = r by the
