@@ -28,6 +28,12 @@ Face conventions every consumer must follow (they define the order of the LDU ar
   (k, j) with j fastest, inside a y-patch over (k, i) with i fastest, inside a z-patch over
   (j, i) with i fastest.
 
+Optional physics (section "The laplacianFoam application", Eq. (1)): ``DT_cells`` gives the
+diffusivity as a cell field (over natural cell ids; it replaces the per-face DT and is
+interpolated to faces by the consumer), ``Su`` and ``Sp`` a volumetric source
+S_T = Su + Sp T per unit volume (scalars or arrays over natural cell ids). Cases with
+``DT_cells`` use natural numbering.
+
 General (non-orthogonal) hexahedral boxes add ``points`` -- vertex coordinates of shape
 (nz+1, ny+1, nx+1, 3), vertex (i, j, k) at ``points[k, j, i]`` -- which replace the
 rectilinear geometry (xs, ys, zs then only give the cell counts), and ``n_nonorth_corr``,
@@ -82,6 +88,17 @@ class RawCase:
     name: str = "case"
     points: Optional[np.ndarray] = None
     n_nonorth_corr: int = 0
+    DT_cells: Optional[np.ndarray] = None
+    Su: object = None
+    Sp: object = None
+
+    def cell_array(self, v) -> Optional[np.ndarray]:
+        """A scalar or per-natural-cell quantity as an array over natural cell ids."""
+        if v is None:
+            return None
+        if np.isscalar(v):
+            return np.full(self.n_cells, float(v))
+        return np.ascontiguousarray(v, dtype=np.float64).reshape(self.n_cells)
 
     @property
     def nx(self) -> int:
@@ -305,3 +322,23 @@ def skewed_box(n: int = 200, n_steps: int = 100, precision: int = FP64) -> RawCa
     base = graded_box(n, n_steps=n_steps, precision=precision)
     M = [[1.0, 0.25, 0.15], [0.0, 1.0, 0.0], [0.0, 0.0, 1.0]]
     return mapped_box(base, M, n_nonorth_corr=1).with_(name=f"skewed{n}")
+
+
+def two_material_box(n: int = 24, ratio: float = 20.0, n_steps: int = 5) -> RawCase:
+    """A graded box split at x = 0.5 into two materials (DT 1e-2 and 1e-2 / ratio as a cell
+    field), x0 = 373 K / x1 = 273 K fixedValue, insulated elsewhere."""
+    xs = graded_axis(n, 1.05)
+    cx = 0.5 * (xs[1:] + xs[:-1])
+    DTc = np.where(cx < 0.5, 1e-2, 1e-2 / ratio)
+    nat = np.broadcast_to(DTc[None, None, :], (n, n, n)).ravel().copy()
+    return RawCase(xs=xs, ys=uniform_axis(n), zs=uniform_axis(n), DT_cells=nat, dt=0.5, n_steps=n_steps,
+                   tol=1e-10, T0=300.0, name=f"two_material{n}")
+
+
+def heated_box(n: int = 20, Su: float = 50.0, Sp: float = -0.5, n_steps: int = 5, seed: int = 6) -> RawCase:
+    """A uniform box with a seeded random heat source Su in [0, 2 Su] per cell and a uniform
+    implicit sink Sp, x0 = 373 K / x1 = 273 K fixedValue, insulated elsewhere."""
+    rng = np.random.default_rng(seed)
+    ax = uniform_axis(n)
+    return RawCase(xs=ax, ys=ax.copy(), zs=ax.copy(), DT_uniform=4e-3, dt=0.05, n_steps=n_steps, tol=1e-10,
+                   T0=300.0, Su=rng.uniform(0.0, 2.0 * Su, n ** 3), Sp=Sp, name=f"heated{n}")

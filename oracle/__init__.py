@@ -87,7 +87,9 @@ def _load():
         lib.ora_box_mesh.restype = ctypes.c_int
         lib.ora_assemble.argtypes = [ctypes.c_int64, ctypes.c_int64, _i32p, _i32p, _f64p, _f64p, _f64p,
                                      _f64p, ctypes.c_int64, _i32p, _i32p, _f64p, _f64p, _f64p, _f64p,
-                                     ctypes.c_double, _f64p, _f64p, _f64p, _f64p]
+                                     ctypes.c_double, _f64p, _f64p, _f64p, _f64p, _f64p, _f64p]
+        lib.ora_cell_dt_to_faces.argtypes = [ctypes.c_int64, ctypes.c_int64, _i32p, _i32p, _f64p, _i32p, _f64p,
+                                             _f64p, _f64p]
         lib.ora_amul.argtypes = [ctypes.c_int64, ctypes.c_int64, _i32p, _i32p, _f64p, _f64p, _f64p, _f64p]
         lib.ora_pcg.argtypes = [ctypes.c_int64, ctypes.c_int64, _i32p, _i32p, _f64p, _f64p, _f64p, _f64p,
                                 ctypes.c_double, ctypes.c_double, ctypes.c_int32, ctypes.c_int32,
@@ -96,7 +98,7 @@ def _load():
         lib.ora_advance.argtypes = [ctypes.c_int64, ctypes.c_int64, _i32p, _i32p, _f64p, _f64p, _f64p,
                                     _f64p, ctypes.c_int64, _i32p, _i32p, _f64p, _f64p, _f64p, _f64p,
                                     ctypes.c_double, ctypes.c_int32, ctypes.c_double, ctypes.c_double,
-                                    ctypes.c_int32, ctypes.c_int32, _f64p, ctypes.POINTER(_Stats)]
+                                    ctypes.c_int32, ctypes.c_int32, _f64p, _f64p, _f64p, ctypes.POINTER(_Stats)]
         lib.ora_advance.restype = ctypes.c_int
         lib.ora_boundary_values.argtypes = [ctypes.c_int64, _i32p, _i32p, _f64p, _f64p, _f64p]
         lib.ora_hex_counts.argtypes = [ctypes.POINTER(_Hex), _i64p, _i64p, _i64p]
@@ -114,8 +116,8 @@ def _load():
                                               _f64p, _f64p, _f64p, _f64p, _f64p, ctypes.c_int64, _i32p, _i32p,
                                               _f64p, _f64p, _f64p, _f64p, _f64p, ctypes.c_double,
                                               ctypes.c_int32, ctypes.c_int32, ctypes.c_double,
-                                              ctypes.c_double, ctypes.c_int32, ctypes.c_int32, _f64p,
-                                              ctypes.POINTER(_Stats)]
+                                              ctypes.c_double, ctypes.c_int32, ctypes.c_int32, _f64p, _f64p,
+                                              _f64p, ctypes.POINTER(_Stats)]
         lib.ora_advance_corrected.restype = ctypes.c_int
         _lib = lib
     return _lib
@@ -221,8 +223,40 @@ def hex_mesh(case: lapcase.RawCase) -> Mesh:
                 Sf=Sf, Cf=Cf, C=C, w=w, corr=corr, bSf=bSf, bCf=bCf)
 
 
+def interpolation_weights(case: lapcase.RawCase, mesh: Mesh) -> np.ndarray:
+    """Owner interpolation weights of the mesh's internal faces (from the general geometry;
+    for a rectilinear box, from the geometry of its vertex lattice)."""
+    if mesh.w is not None:
+        return mesh.w
+    if case.perm is not None:
+        raise ValueError("cell-field DT needs natural numbering")
+    return hex_mesh(case.with_(points=lapcase.box_points(case.xs, case.ys, case.zs), n_nonorth_corr=0)).w
+
+
+def cell_dt_to_faces(case: lapcase.RawCase, mesh: Mesh):
+    """(DTf, DTb) of the case's cell-field DT."""
+    lib = _load()
+    DTc = np.ascontiguousarray(case.cell_array(case.DT_cells))
+    w = np.ascontiguousarray(interpolation_weights(case, mesh))
+    DTf, DTb = np.empty(mesh.n_faces), np.empty(mesh.n_bfaces)
+    lib.ora_cell_dt_to_faces(mesh.n_faces, mesh.n_bfaces, _p(mesh.owner, _i32p), _p(mesh.neighbour, _i32p),
+                             _p(w, _f64p), _p(mesh.bcell, _i32p), _p(DTc, _f64p), _p(DTf, _f64p), _p(DTb, _f64p))
+    return DTf, DTb
+
+
 def mesh_of(case: lapcase.RawCase) -> Mesh:
-    return hex_mesh(case) if case.points is not None else box_mesh(case)
+    """The case's mesh, with the face diffusivities of a cell-field DT when the case has one."""
+    m = hex_mesh(case) if case.points is not None else box_mesh(case)
+    if case.DT_cells is not None:
+        m.DTf, m.DTb = cell_dt_to_faces(case, m)
+    return m
+
+
+def source_arrays(case: lapcase.RawCase):
+    """(Su, Sp) per cell label, or None."""
+    if case.perm is not None and (case.Su is not None or case.Sp is not None):
+        raise ValueError("sources need natural numbering")
+    return case.cell_array(case.Su), case.cell_array(case.Sp)
 
 
 def gauss_grad(mesh: Mesh, T: np.ndarray, Tb: np.ndarray) -> np.ndarray:
@@ -275,16 +309,21 @@ def initial_field(case: lapcase.RawCase) -> np.ndarray:
     return T
 
 
-def assemble(mesh: Mesh, btype: np.ndarray, bvalue: np.ndarray, dt: float, T_old: np.ndarray):
-    """Returns (diag, upper, source) of fvm::ddt(T) - fvm::laplacian(DT, T)."""
+def assemble(mesh: Mesh, btype: np.ndarray, bvalue: np.ndarray, dt: float, T_old: np.ndarray,
+             Su: Optional[np.ndarray] = None, Sp: Optional[np.ndarray] = None):
+    """Returns (diag, upper, source) of fvm::ddt(T) - fvm::laplacian(DT, T) (- the source
+    S_T = Su + Sp T when given, per cell label)."""
     lib = _load()
     T_old = np.ascontiguousarray(T_old, dtype=np.float64)
+    Su = None if Su is None else np.ascontiguousarray(Su, dtype=np.float64)
+    Sp = None if Sp is None else np.ascontiguousarray(Sp, dtype=np.float64)
     diag, upper, source = np.empty(mesh.n_cells), np.empty(mesh.n_faces), np.empty(mesh.n_cells)
     lib.ora_assemble(mesh.n_cells, mesh.n_faces, _p(mesh.owner, _i32p), _p(mesh.neighbour, _i32p),
                      _p(mesh.V, _f64p), _p(mesh.magSf, _f64p), _p(mesh.delta, _f64p), _p(mesh.DTf, _f64p),
                      mesh.n_bfaces, _p(mesh.bcell, _i32p), _p(btype, _i32p), _p(bvalue, _f64p),
                      _p(mesh.bmagSf, _f64p), _p(mesh.bdelta, _f64p), _p(mesh.DTb, _f64p), float(dt),
-                     _p(T_old, _f64p), _p(diag, _f64p), _p(upper, _f64p), _p(source, _f64p))
+                     _p(T_old, _f64p), _p(Su, _f64p), _p(Sp, _f64p), _p(diag, _f64p), _p(upper, _f64p),
+                     _p(source, _f64p))
     return diag, upper, source
 
 
@@ -333,6 +372,7 @@ def advance(case: lapcase.RawCase, n_steps: Optional[int] = None, mesh: Optional
     btype, bvalue = boundary_types_values(case, mesh)
     T = initial_field(case) if T is None else np.array(T, dtype=np.float64, copy=True)
     stats = (_Stats * max(n_steps, 1))()
+    Su, Sp = source_arrays(case)
     if mesh.Sf is not None:
         rc = lib.ora_advance_corrected(
             mesh.n_cells, mesh.n_faces, _p(mesh.owner, _i32p), _p(mesh.neighbour, _i32p), _p(mesh.V, _f64p),
@@ -340,7 +380,8 @@ def advance(case: lapcase.RawCase, n_steps: Optional[int] = None, mesh: Optional
             _p(mesh.w, _f64p), _p(mesh.corr, _f64p), mesh.n_bfaces, _p(mesh.bcell, _i32p), _p(btype, _i32p),
             _p(bvalue, _f64p), _p(mesh.bmagSf, _f64p), _p(mesh.bdelta, _f64p), _p(mesh.DTb, _f64p),
             _p(mesh.bSf, _f64p), float(case.dt), int(n_steps), int(case.n_nonorth_corr), float(case.tol),
-            float(case.rel_tol), int(case.max_iter), int(case.min_iter), _p(T, _f64p), stats)
+            float(case.rel_tol), int(case.max_iter), int(case.min_iter), _p(Su, _f64p), _p(Sp, _f64p),
+            _p(T, _f64p), stats)
         if rc != 0:
             raise MemoryError("oracle advance ran out of memory")
         return T, [_stats(stats[i]) for i in range(n_steps)]
@@ -349,7 +390,8 @@ def advance(case: lapcase.RawCase, n_steps: Optional[int] = None, mesh: Optional
                          _p(mesh.DTf, _f64p), mesh.n_bfaces, _p(mesh.bcell, _i32p), _p(btype, _i32p),
                          _p(bvalue, _f64p), _p(mesh.bmagSf, _f64p), _p(mesh.bdelta, _f64p),
                          _p(mesh.DTb, _f64p), float(case.dt), int(n_steps), float(case.tol),
-                         float(case.rel_tol), int(case.max_iter), int(case.min_iter), _p(T, _f64p), stats)
+                         float(case.rel_tol), int(case.max_iter), int(case.min_iter), _p(Su, _f64p),
+                         _p(Sp, _f64p), _p(T, _f64p), stats)
     if rc != 0:
         raise MemoryError("oracle advance ran out of memory")
     return T, [_stats(stats[i]) for i in range(n_steps)]

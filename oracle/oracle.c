@@ -36,7 +36,10 @@
  *
  * Parity status: every function here is pinned by the CPU tests (dense LU solve, closed-form
  * steady and transient solutions, matrix symmetry and row sums, energy balance, permutation
- * invariance, finite termination of CG, a hand-computed two-cell normFactor).
+ * invariance, finite termination of CG, a hand-computed two-cell normFactor; for the general
+ * geometry, gradient and corrected laplacian see the block below; cell-field DT and sources:
+ * uniform and linear interpolation, the series-conductance steady state, closed-form source
+ * steps and energy balance).
  */
 #include <math.h>
 #include <stdint.h>
@@ -201,11 +204,15 @@ int ora_box_mesh(const ora_box *b, int32_t *owner, int32_t *neighbour, double *V
 /* Assembly: fvm::ddt(T) - fvm::laplacian(DT, T), scatter over faces                      */
 /* ------------------------------------------------------------------------------------ */
 
+/* Su, Sp (may be NULL): the source S_T = Su + Sp T of Eq. (1) per unit volume (fvOptions);
+ * on the right-hand side of the equation it adds V Su to the source and -V Sp to the
+ * diagonal. */
 void ora_assemble(int64_t N, int64_t F, const int32_t *owner, const int32_t *neighbour,
                   const double *V, const double *magSf, const double *delta, const double *DTf,
                   int64_t NB, const int32_t *bcell, const int32_t *btype, const double *bvalue,
                   const double *bmagSf, const double *bdelta, const double *DTb, double dt,
-                  const double *T_old, double *diag, double *upper, double *source) {
+                  const double *T_old, const double *Su, const double *Sp, double *diag, double *upper,
+                  double *source) {
   for (int64_t c = 0; c < N; ++c) {
     diag[c] = 0.0;
     source[c] = 0.0;
@@ -230,6 +237,22 @@ void ora_assemble(int64_t N, int64_t F, const int32_t *owner, const int32_t *nei
     diag[c] += vdt;
     source[c] += vdt * T_old[c];
   }
+  /* volumetric source S_T = Su + Sp T */
+  for (int64_t c = 0; c < N; ++c) {
+    if (Sp) diag[c] -= V[c] * Sp[c];
+    if (Su) source[c] += V[c] * Su[c];
+  }
+}
+
+/*
+ * Diffusivity given as a cell field (a volScalarField): internal faces take the linear
+ * interpolate in the form of the paper's listing "dotInterpolate loop",
+ * w_f (DT_P - DT_N) + DT_N, boundary faces the value of their cell.
+ */
+void ora_cell_dt_to_faces(int64_t F, int64_t NB, const int32_t *owner, const int32_t *neighbour,
+                          const double *w, const int32_t *bcell, const double *DTc, double *DTf, double *DTb) {
+  for (int64_t f = 0; f < F; ++f) DTf[f] = w[f] * (DTc[owner[f]] - DTc[neighbour[f]]) + DTc[neighbour[f]];
+  for (int64_t b = 0; b < NB; ++b) DTb[b] = DTc[bcell[b]];
 }
 
 /* y = A x with A in LDU form (lower = upper), scatter over faces. */
@@ -353,7 +376,7 @@ int ora_advance(int64_t N, int64_t F, const int32_t *owner, const int32_t *neigh
                 int64_t NB, const int32_t *bcell, const int32_t *btype, const double *bvalue,
                 const double *bmagSf, const double *bdelta, const double *DTb, double dt,
                 int32_t n_steps, double tol, double rel_tol, int32_t max_iter, int32_t min_iter,
-                double *T, ora_stats *stats) {
+                const double *Su, const double *Sp, double *T, ora_stats *stats) {
   double *diag = (double *)malloc(sizeof(double) * (size_t)N);
   double *upper = (double *)malloc(sizeof(double) * (size_t)(F > 0 ? F : 1));
   double *source = (double *)malloc(sizeof(double) * (size_t)N);
@@ -363,7 +386,7 @@ int ora_advance(int64_t N, int64_t F, const int32_t *owner, const int32_t *neigh
   for (int32_t s = 0; s < n_steps && rc == 0; ++s) {
     memcpy(T_old, T, sizeof(double) * (size_t)N);
     ora_assemble(N, F, owner, neighbour, V, magSf, delta, DTf, NB, bcell, btype, bvalue, bmagSf,
-                 bdelta, DTb, dt, T_old, diag, upper, source);
+                 bdelta, DTb, dt, T_old, Su, Sp, diag, upper, source);
     rc = ora_pcg(N, F, owner, neighbour, diag, upper, source, T, tol, rel_tol, max_iter, min_iter,
                  &stats[s], NULL, 0);
   }
@@ -688,7 +711,8 @@ int ora_advance_corrected(int64_t N, int64_t F, const int32_t *owner, const int3
                           int64_t NB, const int32_t *bcell, const int32_t *btype, const double *bvalue,
                           const double *bmagSf, const double *bdelta, const double *DTb, const double *bSf,
                           double dt, int32_t n_steps, int32_t n_corr, double tol, double rel_tol,
-                          int32_t max_iter, int32_t min_iter, double *T, ora_stats *stats) {
+                          int32_t max_iter, int32_t min_iter, const double *Su, const double *Sp, double *T,
+                          ora_stats *stats) {
   double *diag = (double *)malloc(sizeof(double) * (size_t)N);
   double *upper = (double *)malloc(sizeof(double) * (size_t)(F > 0 ? F : 1));
   double *source = (double *)malloc(sizeof(double) * (size_t)N);
@@ -707,7 +731,7 @@ int ora_advance_corrected(int64_t N, int64_t F, const int32_t *owner, const int3
       rc = ora_gauss_grad(N, F, NB, owner, neighbour, Sf, w, V, bcell, bSf, Tb, T, G);
       if (rc) break;
       ora_assemble(N, F, owner, neighbour, V, magSf, nonOrthDelta, DTf, NB, bcell, btype, bvalue, bmagSf,
-                   bdelta, DTb, dt, T_old, diag, upper, source);
+                   bdelta, DTb, dt, T_old, Su, Sp, diag, upper, source);
       /* explicit correction flux, surface-integrated (scatter over faces), / V then * V */
       for (int64_t c = 0; c < N; ++c) divc[c] = 0.0;
       for (int64_t f = 0; f < F; ++f) {
