@@ -230,6 +230,19 @@ int lfm_fill_field(lfm_ctx *ctx, double value);
 int lfm_set_diffusivity(lfm_ctx *ctx, double uniform, const double *DT_faces,
                         const double *DT_bfaces);
 
+/* Diffusivity as a cell field DT_cells[n_cells] >= 0 (a volScalarField DT in Eq. (1)): each
+ * internal face takes the linear interpolate w (DT_P - DT_N) + DT_N (the dotInterpolate form
+ * of section "Code Porting"), each boundary face the value of its cell. weights[n_faces] in
+ * [0, 1] are the owner weights (NULL: those of the uploaded general geometry; LFM_EINVAL when
+ * there is none). Computed on the device; replaces any earlier diffusivity. */
+int lfm_set_diffusivity_cells(lfm_ctx *ctx, const double *DT_cells, const double *weights);
+
+/* Volumetric source S_T = Su + Sp T of Eq. (1) per unit volume (OpenFOAM's fvOptions, e.g. a
+ * semi-implicit source), on the right-hand side: every assembly adds V Su to the source and
+ * -V Sp to the diagonal (Sp <= 0 keeps the matrix diagonally dominant). Su, Sp: host arrays
+ * [n_cells] or NULL (0); both NULL removes the source. */
+int lfm_set_source(lfm_ctx *ctx, const double *Su, const double *Sp);
+
 /* Patch type (LFM_FIXED_VALUE / LFM_ZERO_GRADIENT) and, for fixedValue, the boundary
  * values: values[patch_size[patch]] or, when values is NULL, `uniform` on every face. */
 int lfm_set_patch(lfm_ctx *ctx, int32_t patch, int32_t type, const double *values,

@@ -70,6 +70,8 @@ _SIGS = {
     "lfm_workspace_bytes_geometry": ([POINTER(lfm_mesh), c_int32], c_size_t),
     "lfm_upload_mesh_geometry": ([_ctx_p, POINTER(lfm_mesh), POINTER(lfm_geometry)], c_int),
     "lfm_set_nonorth_correctors": ([_ctx_p, c_int32], c_int),
+    "lfm_set_diffusivity_cells": ([_ctx_p, POINTER(c_double), POINTER(c_double)], c_int),
+    "lfm_set_source": ([_ctx_p, POINTER(c_double), POINTER(c_double)], c_int),
     "lfm_grad": ([_ctx_p, POINTER(c_double), POINTER(c_double)], c_int),
     "lfm_create": ([POINTER(_ctx_p), c_int, c_void_p], c_int),
     "lfm_bind_workspace": ([_ctx_p, c_void_p, c_size_t, c_int32], c_int),
@@ -264,6 +266,17 @@ def lfm_upload_mesh_geometry(ctx, mesh, geometry):
     args = MeshArgs(mesh)
     gargs = GeometryArgs(geometry)
     _check(load().lfm_upload_mesh_geometry(ctx, ctypes.byref(args.struct), ctypes.byref(gargs.struct)), ctx)
+
+
+def lfm_set_diffusivity_cells(ctx, DT_cells, weights=None):
+    DT_cells = _f64(DT_cells)
+    weights = _f64(weights)
+    _check(load().lfm_set_diffusivity_cells(ctx, _ptr(DT_cells, c_double), _ptr(weights, c_double)), ctx)
+
+
+def lfm_set_source(ctx, Su=None, Sp=None):
+    Su, Sp = _f64(Su), _f64(Sp)
+    _check(load().lfm_set_source(ctx, _ptr(Su, c_double), _ptr(Sp, c_double)), ctx)
 
 
 def lfm_set_nonorth_correctors(ctx, n_corr: int):

@@ -36,7 +36,7 @@ struct Layout {
   size_t sync, partials, stats;
   size_t slot_other, slot_face, face_slots, b_start, b_face, bcell, btype;
   size_t V, magSf, delta, DT, bmagSf, bdelta, bDT, bval;
-  size_t diag, upper, slot_coef, src, rD, vdt, x, x_old, r, w, p, q, Tb;
+  size_t diag, upper, slot_coef, src, rD, vdt, x, x_old, vSu, vSp, r, w, p, q, Tb;
   size_t Sf, fw, corr, bSf, gE, gD, gH, cK, cL, grad;  // general geometry (0 when absent)
   size_t diag32, slot_coef32, rD32, dx32, r32, w32, p32, q32;
   size_t total;
@@ -99,6 +99,8 @@ Layout make_layout(int64_t N, int64_t F, int64_t NB, int64_t W, int kind, bool s
   L.vdt = take(8 * N);
   L.x = take(8 * N);
   L.x_old = take(8 * N);
+  L.vSu = take(8 * N);
+  L.vSp = take(8 * N);
   L.Tb = take(8 * NB);
   L.r = L.w = L.p = L.q = 0;
   L.diag32 = L.slot_coef32 = L.rD32 = L.dx32 = L.r32 = L.w32 = L.p32 = L.q32 = 0;
@@ -164,6 +166,7 @@ struct lfm_ctx {
   bool has64 = false, has32 = false;  // solver blocks present in the workspace
   bool has_geom = false;              // general geometry uploaded (corrected laplacian)
   bool ops_dirty = false;             // operator weights to rebuild before the next launch
+  bool has_Su = false, has_Sp = false;  // volumetric source set (lfm_set_source)
   int32_t n_corr = 0;                 // non-orthogonal corrector passes per step
 
   // launch
@@ -413,6 +416,8 @@ void bind_pointers(lfm_ctx* c) {
   cs.cK = gc ? reinterpret_cast<const double*>(b + L.cK) : nullptr;
   cs.cL = gc ? reinterpret_cast<const double*>(b + L.cL) : nullptr;
   cs.x_old = reinterpret_cast<double*>(b + L.x_old);
+  cs.vSu = c->has_Su ? reinterpret_cast<const double*>(b + L.vSu) : nullptr;
+  cs.vSp = c->has_Sp ? reinterpret_cast<const double*>(b + L.vSp) : nullptr;
   cs.diag = reinterpret_cast<double*>(b + L.diag);
   cs.upper = reinterpret_cast<double*>(b + L.upper);
   cs.slot_coef = reinterpret_cast<double*>(b + L.slot_coef);
@@ -612,6 +617,7 @@ static int upload_mesh_impl(lfm_ctx* c, const lfm_mesh* m, const lfm_geometry* g
   c->has32 = has32;
   c->has_geom = geo != nullptr;
   c->n_corr = 0;
+  c->has_Su = c->has_Sp = false;
   c->n_patches = m->n_patches;
   c->patch_start.assign(m->patch_start, m->patch_start + m->n_patches);
   c->patch_size.assign(m->patch_size, m->patch_size + m->n_patches);
@@ -785,6 +791,7 @@ int lfm_upload_box(lfm_ctx* c, int32_t nx, int32_t ny, int32_t nz, const double*
   c->has32 = has32;
   c->has_geom = false;
   c->n_corr = 0;
+  c->has_Su = c->has_Sp = false;
   c->n_patches = 6;
   const int32_t sizes[6] = {ny * nz, ny * nz, nx * nz, nx * nz, nx * ny, nx * ny};
   c->patch_start.assign(6, 0);
@@ -869,6 +876,7 @@ int lfm_upload_mesh_shared(lfm_ctx* c, lfm_ctx* src) {
   c->has_geom = root->has_geom;
   c->ops_dirty = root->has_geom;
   c->n_corr = 0;
+  c->has_Su = c->has_Sp = false;
   c->n_patches = root->n_patches;
   c->patch_start = root->patch_start;
   c->patch_size = root->patch_size;
@@ -933,6 +941,66 @@ int lfm_set_diffusivity(lfm_ctx* c, double uniform, const double* DT_faces, cons
   }
   CK(c, cudaStreamSynchronize(c->stream));
   c->ops_dirty = true;
+  return LFM_OK;
+}
+
+int lfm_set_diffusivity_cells(lfm_ctx* c, const double* DT_cells, const double* weights) {
+  int rc = need_uploaded(c);
+  if (rc) return rc;
+  if (!DT_cells) return fail(c, LFM_EINVAL, "DT_cells is NULL");
+  if (!weights && !c->has_geom) return fail(c, LFM_EINVAL, "weights needed (the mesh has no geometry)");
+  for (int32_t i = 0; i < c->N; ++i)
+    if (!(std::isfinite(DT_cells[i]) && DT_cells[i] >= 0)) return fail(c, LFM_EINVAL, "DT_cells[%d] must be finite and >= 0", i);
+  for (int32_t f = 0; weights && f < c->F; ++f)
+    if (!(std::isfinite(weights[f]) && weights[f] >= 0 && weights[f] <= 1))
+      return fail(c, LFM_EINVAL, "weights[%d] not in [0, 1]", f);
+  DeviceGuard g(c->device);
+  double* tmp = nullptr;
+  const size_t n = (size_t)c->N + (weights ? (size_t)c->F : 0);
+  cudaError_t e = cudaMalloc(&tmp, sizeof(double) * (n > 0 ? n : 1));
+  if (e != cudaSuccess) return fail(c, LFM_ENOMEM, "staging buffer: %s", cudaGetErrorString(e));
+  e = cudaMemcpyAsync(tmp, DT_cells, sizeof(double) * c->N, cudaMemcpyHostToDevice, c->stream);
+  if (e == cudaSuccess && weights)
+    e = cudaMemcpyAsync(tmp + c->N, weights, sizeof(double) * c->F, cudaMemcpyHostToDevice, c->stream);
+  if (e == cudaSuccess)
+    e = launch_dt_cells(c->cs, tmp, weights ? tmp + c->N : c->cs.fw, const_cast<double*>(c->cs.DT),
+                        const_cast<double*>(c->cs.bDT), c->stream);
+  if (e == cudaSuccess) e = cudaStreamSynchronize(c->stream);
+  cudaFree(tmp);
+  if (e != cudaSuccess) return cuda_fail(c, e, "lfm_set_diffusivity_cells");
+  c->cs.DT_is_uniform = 0;
+  c->ops_dirty = true;
+  return LFM_OK;
+}
+
+int lfm_set_source(lfm_ctx* c, const double* Su, const double* Sp) {
+  int rc = need_uploaded(c);
+  if (rc) return rc;
+  if (c->pending_steps > 0) return fail(c, LFM_ESTATE, "an advance is pending");
+  for (int32_t i = 0; Su && i < c->N; ++i)
+    if (!std::isfinite(Su[i])) return fail(c, LFM_EINVAL, "Su[%d] not finite", i);
+  for (int32_t i = 0; Sp && i < c->N; ++i)
+    if (!std::isfinite(Sp[i])) return fail(c, LFM_EINVAL, "Sp[%d] not finite", i);
+  DeviceGuard g(c->device);
+  double* tmp = nullptr;
+  if (Su || Sp) {
+    cudaError_t e = cudaMalloc(&tmp, sizeof(double) * c->N);
+    if (e != cudaSuccess) return fail(c, LFM_ENOMEM, "staging buffer: %s", cudaGetErrorString(e));
+  }
+  const double* src[2] = {Su, Sp};
+  const size_t off[2] = {c->lay.vSu, c->lay.vSp};
+  cudaError_t e = cudaSuccess;
+  for (int k = 0; k < 2 && e == cudaSuccess; ++k) {
+    if (!src[k]) continue;
+    e = cudaMemcpyAsync(tmp, src[k], sizeof(double) * c->N, cudaMemcpyHostToDevice, c->stream);
+    if (e == cudaSuccess) e = launch_times_volume(c->cs, tmp, reinterpret_cast<double*>(c->ws + off[k]), c->stream);
+    if (e == cudaSuccess) e = cudaStreamSynchronize(c->stream);
+  }
+  if (tmp) cudaFree(tmp);
+  if (e != cudaSuccess) return cuda_fail(c, e, "lfm_set_source");
+  c->has_Su = Su != nullptr;
+  c->has_Sp = Sp != nullptr;
+  bind_pointers(c);
   return LFM_OK;
 }
 

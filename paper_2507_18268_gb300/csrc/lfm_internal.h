@@ -89,6 +89,10 @@ struct CaseDev {
   const double* cL;          // [3*W*N]
   double* grad;              // [3N]    Gauss gradient of T (per assembly), component-major
   double* x_old;             // [N]  T at the start of the step (non-orthogonal correctors)
+  // volumetric source S_T = Su + Sp T of Eq. (1) (fvOptions), times V; null when unset:
+  // the row gets source += V Su, diag -= V Sp
+  const double* vSu;         // [N]
+  const double* vSp;         // [N]
   int32_t n_corr;            // extra corrector passes per step (nNonOrthogonalCorrectors)
 
   // assembled matrix (FP64): LDU (diag, upper) plus the per-slot copy of the off-diagonals
@@ -160,6 +164,11 @@ cudaError_t launch_grad(const CaseDev& cs, double* bgrad, cudaStream_t stream);
 // Operator weights of the general-geometry path: gE (geometry only) when `with_E`, and the
 // case's gD, gH, cK, cL (patches, boundary values, DT).
 cudaError_t launch_geom_ops(const CaseDev& cs, bool with_E, cudaStream_t stream);
+// Face diffusivities from a cell field: DTf = w (DT_P - DT_N) + DT_N, DTb = DT of the cell.
+cudaError_t launch_dt_cells(const CaseDev& cs, const double* DTc, const double* w, double* DTf, double* DTb,
+                            cudaStream_t stream);
+// out[c] = V[c] * a[c] (a null: out = 0).
+cudaError_t launch_times_volume(const CaseDev& cs, const double* a, double* out, cudaStream_t stream);
 
 // Box meshes built from closed forms (lfm_box.cu).
 int box_slot_width(long long nx, long long ny, long long nz);

@@ -209,9 +209,10 @@ __device__ __forceinline__ double op_corr_source(const CaseDev& cs, int c) {
   return v;
 }
 
-// kCorr: the step has non-orthogonal corrector passes or general geometry: the ddt source
-// comes from x_old, and the explicit correction fluxes of the row's faces (owner +,
-// neighbour -, slot order = face order) are added to the source.
+// kCorr: the step has non-orthogonal corrector passes, general geometry or a volumetric
+// source: the ddt source comes from x_old (with correctors), the source S_T = Su + Sp T
+// enters (V Su to the source, -V Sp to the diagonal), and the explicit correction of the
+// row's faces is added to the source.
 template <int W, bool kCorr = false>
 __device__ __forceinline__ Row assemble_row(const CaseDev& cs, int c, const double* __restrict__ x) {
   const size_t N = (size_t)cs.N;
@@ -243,6 +244,12 @@ __device__ __forceinline__ Row assemble_row(const CaseDev& cs, int c, const doub
     }
   }
   row_boundary(cs, c, kCorr && cs.n_corr > 0 ? cs.x_old[c] : o.xc, o);
+  if (kCorr && cs.vSp) {  // implicit part of the source S_T = Su + Sp T
+    const double v = cs.vSp[c];
+    o.d = __dsub_rn(o.d, v);
+    o.sa = o.sa - v;
+  }
+  if (kCorr && cs.vSu) o.s = __dadd_rn(o.s, cs.vSu[c]);
   if (kCorr && cs.Sf) o.s = __dadd_rn(o.s, op_corr_source<W>(cs, c));
   o.ax = fma(o.d, o.xc, off);
   return o;
@@ -657,7 +664,7 @@ __device__ void run_steps_f64(const CaseDev& cs, const CaseDev& cref, const Team
   const double* __restrict__ rD = cs.rD;
 
   PhaseClock clk(cs, tm);
-  const bool corr_mode = cs.n_corr > 0 || cs.Sf != nullptr;
+  const bool corr_mode = cs.n_corr > 0 || cs.Sf != nullptr || cs.vSu != nullptr || cs.vSp != nullptr;
   for (int step = 0; step < n_steps; ++step) {
     int iters_tot = 0, solves = 0, status = 0;
     double nf0 = 0.0, init0 = 0.0, res = 0.0;
@@ -758,7 +765,7 @@ __device__ void run_steps_mixed(const CaseDev& cs, const CaseDev& cref, const Te
   const float* __restrict__ rD = cs.rD32;
 
   PhaseClock clk(cs, tm);
-  const bool corr_mode = cs.n_corr > 0 || cs.Sf != nullptr;
+  const bool corr_mode = cs.n_corr > 0 || cs.Sf != nullptr || cs.vSu != nullptr || cs.vSp != nullptr;
   for (int step = 0; step < n_steps; ++step) {
     int iters_tot = 0, sweeps_tot = 0, status = 0;
     double nf0 = 0.0, init0 = 0.0, res = 0.0;

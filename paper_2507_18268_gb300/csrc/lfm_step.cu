@@ -151,6 +151,26 @@ __global__ void case_ops_kernel(CaseDev cs, double* __restrict__ D, double* __re
   }
 }
 
+// Face diffusivities from a cell field (the dotInterpolate form of the paper's listing):
+// internal faces w (DT_P - DT_N) + DT_N, owner and neighbour from the face's two slots;
+// boundary faces the value of their cell. Products and sums rounded separately.
+__global__ void dt_cells_kernel(CaseDev cs, const double* __restrict__ DTc, const double* __restrict__ w,
+                                double* __restrict__ DTf, double* __restrict__ DTb) {
+  const int i = blockIdx.x * blockDim.x + threadIdx.x;
+  if (i < cs.F) {
+    const uint2 at = reinterpret_cast<const uint2*>(cs.face_slots)[i];
+    const double dP = DTc[cs.slot_other[at.y]], dN = DTc[cs.slot_other[at.x]];
+    DTf[i] = __dadd_rn(__dmul_rn(w[i], __dsub_rn(dP, dN)), dN);
+  }
+  if (i < cs.NB) DTb[i] = DTc[cs.bcell[i]];
+}
+
+__global__ void times_volume_kernel(const double* __restrict__ V, const double* __restrict__ a,
+                                    double* __restrict__ out, int n) {
+  const int c = blockIdx.x * blockDim.x + threadIdx.x;
+  if (c < n) out[c] = a ? __dmul_rn(V[c], a[c]) : 0.0;
+}
+
 __global__ void vdt_kernel(const double* __restrict__ V, double dt, double* __restrict__ vdt, int n) {
   const int c = blockIdx.x * blockDim.x + threadIdx.x;
   if (c < n) vdt[c] = V[c] / dt;
@@ -206,6 +226,19 @@ cudaError_t launch_geom_ops(const CaseDev& cs, bool with_E, cudaStream_t stream)
   if (with_E) grad_weights_kernel<<<blocks, 256, 0, stream>>>(cs, const_cast<double*>(cs.gE));
   case_ops_kernel<<<blocks, 256, 0, stream>>>(cs, const_cast<double*>(cs.gD), const_cast<double*>(cs.gH),
                                               const_cast<double*>(cs.cK), const_cast<double*>(cs.cL));
+  return cudaGetLastError();
+}
+
+cudaError_t launch_dt_cells(const CaseDev& cs, const double* DTc, const double* w, double* DTf, double* DTb,
+                            cudaStream_t stream) {
+  const int n = cs.F > cs.NB ? cs.F : cs.NB;
+  if (n == 0) return cudaSuccess;
+  dt_cells_kernel<<<(n + 255) / 256, 256, 0, stream>>>(cs, DTc, w, DTf, DTb);
+  return cudaGetLastError();
+}
+
+cudaError_t launch_times_volume(const CaseDev& cs, const double* a, double* out, cudaStream_t stream) {
+  times_volume_kernel<<<(cs.N + 255) / 256, 256, 0, stream>>>(cs.V, a, out, cs.N);
   return cudaGetLastError();
 }
 

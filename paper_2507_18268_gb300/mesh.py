@@ -14,7 +14,7 @@ cell centre to the face centre.
 from __future__ import annotations
 
 import dataclasses
-from typing import List
+from typing import List, Optional
 
 import numpy as np
 
@@ -39,6 +39,7 @@ class LduMesh:
     DT_faces: np.ndarray       # float64 [F]   diffusivity per internal face
     DT_bfaces: np.ndarray      # float64 [NB]  diffusivity per boundary face
     cell_of_label: np.ndarray  # int64 [N]     natural cell id of each label
+    weights: Optional[np.ndarray] = None  # float64 [F] owner interpolation weight (rectilinear: h_N / (h_P + h_N))
 
     @property
     def n_patches(self) -> int:
@@ -66,25 +67,28 @@ def box_mesh(case: lapcase.RawCase) -> LduMesh:
     V = np.empty(N)
     V[lab3] = (hx[None, None, :] * hy[None, :, None]) * hz[:, None, None]
 
-    a_list, b_list, area, dcoef, dtf = [], [], [], [], []
+    a_list, b_list, area, dcoef, dtf, wts = [], [], [], [], [], []
     # x-normal internal faces: (i, j, k) - (i+1, j, k)
     a_list.append(lab3[:, :, :-1].ravel())
     b_list.append(lab3[:, :, 1:].ravel())
     area.append(np.broadcast_to((hy[None, :, None] * hz[:, None, None]), (nz, ny, nx - 1)).ravel())
     dcoef.append(np.broadcast_to(1.0 / (cx[1:] - cx[:-1]), (nz, ny, nx - 1)).ravel())
     dtf.append(DTx[:, :, 1:nx].ravel())
+    wts.append(np.broadcast_to(hx[1:] / (hx[:-1] + hx[1:]), (nz, ny, nx - 1)).ravel())
     # y-normal
     a_list.append(lab3[:, :-1, :].ravel())
     b_list.append(lab3[:, 1:, :].ravel())
     area.append(np.broadcast_to((hx[None, None, :] * hz[:, None, None]), (nz, ny - 1, nx)).ravel())
     dcoef.append(np.broadcast_to((1.0 / (cy[1:] - cy[:-1]))[None, :, None], (nz, ny - 1, nx)).ravel())
     dtf.append(DTy[:, 1:ny, :].ravel())
+    wts.append(np.broadcast_to((hy[1:] / (hy[:-1] + hy[1:]))[None, :, None], (nz, ny - 1, nx)).ravel())
     # z-normal
     a_list.append(lab3[:-1, :, :].ravel())
     b_list.append(lab3[1:, :, :].ravel())
     area.append(np.broadcast_to((hx[None, None, :] * hy[None, :, None]), (nz - 1, ny, nx)).ravel())
     dcoef.append(np.broadcast_to((1.0 / (cz[1:] - cz[:-1]))[:, None, None], (nz - 1, ny, nx)).ravel())
     dtf.append(DTz[1:nz, :, :].ravel())
+    wts.append(np.broadcast_to((hz[1:] / (hz[:-1] + hz[1:]))[:, None, None], (nz - 1, ny, nx)).ravel())
 
     a = np.concatenate(a_list)
     b = np.concatenate(b_list)
@@ -96,6 +100,10 @@ def box_mesh(case: lapcase.RawCase) -> LduMesh:
     magSf = np.concatenate(area)[order]
     deltaCoeffs = np.concatenate(dcoef)[order]
     DT_faces = np.concatenate(dtf)[order]
+    # owner weight: the neighbour cell's share of the centre distance, with owner/neighbour
+    # possibly swapped by the relabelling
+    w_nat = np.concatenate(wts)
+    weights = np.where(a <= b, w_nat, 1.0 - w_nat)[order]
 
     # boundary patches x0, x1, y0, y1, z0, z1
     cells, barea, bdel, bdt, sizes = [], [], [], [], []
@@ -135,7 +143,7 @@ def box_mesh(case: lapcase.RawCase) -> LduMesh:
         bmagSf=np.ascontiguousarray(np.concatenate(barea)),
         bdeltaCoeffs=np.ascontiguousarray(np.concatenate(bdel)),
         DT_faces=np.ascontiguousarray(DT_faces), DT_bfaces=np.ascontiguousarray(np.concatenate(bdt)),
-        cell_of_label=cell_of_label)
+        cell_of_label=cell_of_label, weights=np.ascontiguousarray(weights))
 
 
 def field_by_label(case: lapcase.RawCase, mesh: LduMesh) -> np.ndarray:

@@ -45,6 +45,7 @@ class Solver:
         self.stream = stream
         self._ws = None
         self._share = share
+        self.geometry = geometry
         self.ctx = B.lfm_create(device, _stream_handle(stream))
         try:
             if mesh is not None:
@@ -119,6 +120,18 @@ class Solver:
         B.lfm_set_time_step(self.ctx, case.dt)
         B.lfm_set_solver(self.ctx, case.tol, case.rel_tol, case.max_iter, case.min_iter, case.precision)
         B.lfm_set_nonorth_correctors(self.ctx, int(case.n_nonorth_corr))
+        if case.DT_cells is not None:
+            if m.cell_of_label is None:
+                raise ValueError("a cell-field DT needs a host mesh")
+            w = None if self.geometry is not None else m.weights
+            B.lfm_set_diffusivity_cells(self.ctx, case.cell_array(case.DT_cells)[m.cell_of_label], w)
+        if case.Su is not None or case.Sp is not None:
+            if m.cell_of_label is None and case.perm is not None:
+                raise ValueError("sources on a relabelled mesh need a host mesh")
+            order = m.cell_of_label if m.cell_of_label is not None else slice(None)
+            Su = case.cell_array(case.Su)
+            Sp = case.cell_array(case.Sp)
+            B.lfm_set_source(self.ctx, None if Su is None else Su[order], None if Sp is None else Sp[order])
         if field:
             if np.isscalar(case.T0):
                 B.lfm_fill_field(self.ctx, float(case.T0))
