@@ -177,7 +177,9 @@ int lfm_bind_workspace(lfm_ctx *ctx, void *dev_ptr, size_t bytes, int32_t precis
 size_t lfm_workspace_bytes_geometry(const lfm_mesh *mesh, int32_t precision);
 
 /* Validates and uploads the mesh (deep copy), builds the face-to-cell addressing and the
- * cell-side boundary-face lists. Resets DT to 0, every patch to zeroGradient, dt to 1,
+ * cell-side boundary-face lists on the device (section "Code Porting": the lists of lists,
+ * by binary search over the owner-sorted faces, a counting sort by neighbour and by boundary
+ * cell -- atomic counts, scan, placement, per-cell sort -- and the slot-major rows). Resets DT to 0, every patch to zeroGradient, dt to 1,
  * the solver to {1e-6, 0, 1000, 0, LFM_FP64} and T to 0. LFM_EINVAL also when a cell has
  * more than 32 internal faces or (largest internal faces of a cell) x n_cells >= 2^32. */
 int lfm_upload_mesh(lfm_ctx *ctx, const lfm_mesh *mesh);
@@ -288,6 +290,13 @@ int lfm_field_device_ptr(lfm_ctx *ctx, double **T_dev);
 /* Reads the assembled matrix of the current T (diag[n_cells], upper[n_faces],
  * source[n_cells]) to host memory, running only the assembly. Diagnostic / test use. */
 int lfm_get_matrix(lfm_ctx *ctx, double *diag, double *upper, double *source);
+
+/* Reads back the face-to-cell addressing built at upload (diagnostic / test use): the
+ * slot-major rows slot_other, slot_face [W*N] (W = lfm_box_counts' slot width for boxes, else
+ * the largest number of internal faces of a cell), face_slots [2*n_faces], b_start
+ * [n_cells+1], b_face [n_bfaces]; any pointer may be NULL. */
+int lfm_get_addressing(lfm_ctx *ctx, int32_t *slot_other, int32_t *slot_face, uint32_t *face_slots,
+                       int32_t *b_start, int32_t *b_face);
 
 /* Device time of the last advance by phase kind, in milliseconds (ms[8]): 0 assembly pass
  * over faces (coefficients, sum of T), 1 assembly pass over rows together with the initial

@@ -72,6 +72,8 @@ _SIGS = {
     "lfm_set_nonorth_correctors": ([_ctx_p, c_int32], c_int),
     "lfm_set_diffusivity_cells": ([_ctx_p, POINTER(c_double), POINTER(c_double)], c_int),
     "lfm_set_source": ([_ctx_p, POINTER(c_double), POINTER(c_double)], c_int),
+    "lfm_get_addressing": ([_ctx_p, POINTER(c_int32), POINTER(c_int32), POINTER(ctypes.c_uint32),
+                            POINTER(c_int32), POINTER(c_int32)], c_int),
     "lfm_grad": ([_ctx_p, POINTER(c_double), POINTER(c_double)], c_int),
     "lfm_create": ([POINTER(_ctx_p), c_int, c_void_p], c_int),
     "lfm_bind_workspace": ([_ctx_p, c_void_p, c_size_t, c_int32], c_int),
@@ -272,6 +274,18 @@ def lfm_set_diffusivity_cells(ctx, DT_cells, weights=None):
     DT_cells = _f64(DT_cells)
     weights = _f64(weights)
     _check(load().lfm_set_diffusivity_cells(ctx, _ptr(DT_cells, c_double), _ptr(weights, c_double)), ctx)
+
+
+def lfm_get_addressing(ctx, n_cells: int, n_faces: int, n_bfaces: int, W: int) -> dict:
+    out = dict(slot_other=np.empty(max(W * n_cells, 1), np.int32), slot_face=np.empty(max(W * n_cells, 1), np.int32),
+               face_slots=np.empty(max(2 * n_faces, 2), np.uint32), b_start=np.empty(n_cells + 1, np.int32),
+               b_face=np.empty(max(n_bfaces, 1), np.int32))
+    _check(load().lfm_get_addressing(ctx, _ptr(out["slot_other"], c_int32), _ptr(out["slot_face"], c_int32),
+                                     _ptr(out["face_slots"], ctypes.c_uint32), _ptr(out["b_start"], c_int32),
+                                     _ptr(out["b_face"], c_int32)), ctx)
+    out["slot_other"], out["slot_face"] = out["slot_other"][:W * n_cells], out["slot_face"][:W * n_cells]
+    out["face_slots"], out["b_face"] = out["face_slots"][:2 * n_faces], out["b_face"][:n_bfaces]
+    return out
 
 
 def lfm_set_source(ctx, Su=None, Sp=None):

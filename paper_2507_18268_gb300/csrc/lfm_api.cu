@@ -625,44 +625,33 @@ static int upload_mesh_impl(lfm_ctx* c, const lfm_mesh* m, const lfm_geometry* g
   bind_pointers(c);
 
   const int32_t N = c->N, F = c->F, NB = c->NB;
-  std::vector<int32_t> own_start(N + 1), lo_start(N + 1), losort(F > 0 ? F : 1);
-  int rc = lfm_face_addressing(N, F, m->owner, m->neighbour, own_start.data(), losort.data(), lo_start.data());
-  if (rc != LFM_OK) return fail(c, rc, "%s", g_last_error.c_str());
-  // Slot-major copy of the face-to-cell lists: neighbour-side faces, owned faces, padding;
-  // and, per face, the slot it occupies in its owner's row and in its neighbour's row.
-  std::vector<int32_t> slot_other((size_t)W * N), slot_face((size_t)W * N);
-  std::vector<uint32_t> face_slots(F > 0 ? 2 * (size_t)F : 2);
-  for (int32_t cell = 0; cell < N; ++cell) {
-    int k = 0;
-    for (int32_t i = lo_start[cell]; i < lo_start[cell + 1]; ++i, ++k) {
-      const size_t at = (size_t)k * N + cell;
-      slot_other[at] = m->owner[losort[i]];
-      slot_face[at] = losort[i];
-      face_slots[2 * (size_t)losort[i] + 1] = (uint32_t)at;
-    }
-    for (int32_t f = own_start[cell]; f < own_start[cell + 1]; ++f, ++k) {
-      const size_t at = (size_t)k * N + cell;
-      slot_other[at] = m->neighbour[f];
-      slot_face[at] = f;
-      face_slots[2 * (size_t)f] = (uint32_t)at;
-    }
-    for (; k < W; ++k) {
-      slot_other[(size_t)k * N + cell] = cell;
-      slot_face[(size_t)k * N + cell] = -1;
-    }
-  }
-  std::vector<int32_t> b_start(N + 1), b_face(NB > 0 ? NB : 1);
-  bucket(N, NB, m->bface_cell, b_start.data(), b_face.data());
+  int rc;
   std::vector<int32_t> btype(NB > 0 ? NB : 1, LFM_ZERO_GRADIENT);
   std::vector<double> zeros_b(NB > 0 ? NB : 1, 0.0);
 
+  // Face-to-cell addressing and the slot-major rows, built on the device from owner,
+  // neighbour and bface_cell (staged in a temporary buffer; bface_cell lands in bcell).
   const Layout& Y = c->lay;
   const size_t WN = (size_t)W * N;
-  if ((rc = h2d(c, Y.slot_other, slot_other.data(), WN)) || (rc = h2d(c, Y.slot_face, slot_face.data(), WN)) ||
-      (rc = h2d(c, Y.face_slots, face_slots.data(), 2 * (size_t)F)) ||
-      (rc = h2d(c, Y.b_start, b_start.data(), N + 1)) ||
-      (rc = h2d(c, Y.b_face, b_face.data(), NB)) || (rc = h2d(c, Y.bcell, m->bface_cell, NB)) ||
-      (rc = h2d(c, Y.btype, btype.data(), NB)) || (rc = h2d(c, Y.V, m->V, N)) ||
+  if ((rc = h2d(c, Y.bcell, m->bface_cell, NB))) return rc;
+  {
+    int32_t* on = nullptr;
+    CK(c, cudaMalloc(&on, sizeof(int32_t) * 2 * (size_t)(F > 0 ? F : 1)));
+    cudaError_t e = cudaSuccess;
+    if (F > 0) {
+      e = cudaMemcpyAsync(on, m->owner, sizeof(int32_t) * F, cudaMemcpyHostToDevice, c->stream);
+      if (e == cudaSuccess)
+        e = cudaMemcpyAsync(on + F, m->neighbour, sizeof(int32_t) * F, cudaMemcpyHostToDevice, c->stream);
+    }
+    if (e == cudaSuccess)
+      e = build_addressing(N, F, NB, W, on, on + F, c->cs.bcell, const_cast<int32_t*>(c->cs.slot_other),
+                           const_cast<int32_t*>(c->cs.slot_face), const_cast<uint32_t*>(c->cs.face_slots),
+                           const_cast<int32_t*>(c->cs.b_start), const_cast<int32_t*>(c->cs.b_face), c->stream);
+    if (e == cudaSuccess) e = cudaStreamSynchronize(c->stream);
+    cudaFree(on);
+    if (e != cudaSuccess) return cuda_fail(c, e, "device face addressing");
+  }
+  if ((rc = h2d(c, Y.btype, btype.data(), NB)) || (rc = h2d(c, Y.V, m->V, N)) ||
       (rc = h2d(c, Y.magSf, m->magSf, F)) || (rc = h2d(c, Y.delta, m->deltaCoeffs, F)) ||
       (rc = h2d(c, Y.bmagSf, m->bmagSf, NB)) || (rc = h2d(c, Y.bdelta, m->bdeltaCoeffs, NB)) ||
       (rc = h2d(c, Y.bDT, zeros_b.data(), NB)) || (rc = h2d(c, Y.bval, zeros_b.data(), NB)))
@@ -1207,6 +1196,22 @@ int lfm_get_matrix(lfm_ctx* c, double* diag, double* upper, double* source) {
   CK(c, cudaMemcpyAsync(diag, c->cs.diag, sizeof(double) * c->N, cudaMemcpyDeviceToHost, c->stream));
   if (c->F > 0) CK(c, cudaMemcpyAsync(upper, c->cs.upper, sizeof(double) * c->F, cudaMemcpyDeviceToHost, c->stream));
   CK(c, cudaMemcpyAsync(source, c->cs.src, sizeof(double) * c->N, cudaMemcpyDeviceToHost, c->stream));
+  CK(c, cudaStreamSynchronize(c->stream));
+  return LFM_OK;
+}
+
+int lfm_get_addressing(lfm_ctx* c, int32_t* slot_other, int32_t* slot_face, uint32_t* face_slots, int32_t* b_start,
+                       int32_t* b_face) {
+  int rc = need_uploaded(c);
+  if (rc) return rc;
+  DeviceGuard g(c->device);
+  const size_t WN = (size_t)c->W * c->N;
+  if (slot_other && WN) CK(c, cudaMemcpyAsync(slot_other, c->cs.slot_other, 4 * WN, cudaMemcpyDeviceToHost, c->stream));
+  if (slot_face && WN) CK(c, cudaMemcpyAsync(slot_face, c->cs.slot_face, 4 * WN, cudaMemcpyDeviceToHost, c->stream));
+  if (face_slots && c->F)
+    CK(c, cudaMemcpyAsync(face_slots, c->cs.face_slots, 8 * (size_t)c->F, cudaMemcpyDeviceToHost, c->stream));
+  if (b_start) CK(c, cudaMemcpyAsync(b_start, c->cs.b_start, 4 * ((size_t)c->N + 1), cudaMemcpyDeviceToHost, c->stream));
+  if (b_face && c->NB) CK(c, cudaMemcpyAsync(b_face, c->cs.b_face, 4 * (size_t)c->NB, cudaMemcpyDeviceToHost, c->stream));
   CK(c, cudaStreamSynchronize(c->stream));
   return LFM_OK;
 }

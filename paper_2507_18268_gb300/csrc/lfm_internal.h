@@ -170,6 +170,13 @@ cudaError_t launch_dt_cells(const CaseDev& cs, const double* DTc, const double* 
 // out[c] = V[c] * a[c] (a null: out = 0).
 cudaError_t launch_times_volume(const CaseDev& cs, const double* a, double* out, cudaStream_t stream);
 
+// Face-to-cell addressing of a general mesh built on the device (lfm_addr.cu): owner,
+// neighbour, bface_cell are device arrays; W the largest internal-face count of a cell.
+cudaError_t build_addressing(int32_t N, int32_t F, int32_t NB, int32_t W, const int32_t* owner,
+                             const int32_t* neighbour, const int32_t* bface_cell, int32_t* slot_other,
+                             int32_t* slot_face, uint32_t* face_slots, int32_t* b_start, int32_t* b_face,
+                             cudaStream_t stream);
+
 // Box meshes built from closed forms (lfm_box.cu).
 int box_slot_width(long long nx, long long ny, long long nz);
 cudaError_t launch_box(long long nx, long long ny, long long nz, int W, const double* xs, const double* ys,
