@@ -404,7 +404,7 @@ def main_skewed(args, world, rank, local):
     torch.cuda.set_device(local)
     K = args.steps if args.steps_given else 20
     W = args.warmup
-    case = lapcase.skewed_box(200)
+    case = lapcase.skewed_box(args.skewed_n)
     mesh, geo = hex_mesh(case)
     N, F = mesh.n_cells, mesh.n_faces
     stream = torch.cuda.Stream(device=local)
@@ -457,7 +457,8 @@ def main_skewed(args, world, rank, local):
         "metric": METRIC, "value": value, "unit": UNIT, "n_gpus": world, "steps": K, "warmup": W,
         "ms_per_step": 1e3 * secs_max / K, "higher_is_better": True, "scaling": "weak", "vs_baseline": None,
         "dtype": "f64", "data": "synthetic",
-        "config": {"workload": SKEWED, "cells": N, "internal_faces": F, "precision": "fp64",
+        "config": {"workload": SKEWED if args.skewed_n == 200 else SKEWED.replace("skewed200", f"skewed{args.skewed_n}"),
+                   "cells": N, "internal_faces": F, "precision": "fp64",
                    "parallelism": f"replicas x{world}" if world > 1 else "single GPU",
                    "l2": "inputs larger than L2; no flush", "launch": {"ctas": launch[0], "threads": launch[1]}},
         "iters_per_step": iters / K, "passes_per_step": 1 + case.n_nonorth_corr,
@@ -634,6 +635,7 @@ def main():
     ap.add_argument("--no-cpu-baseline", action="store_true")
     ap.add_argument("--workload", choices=["graded200", "batch512", "serve", "skewed200"], default="graded200")
     ap.add_argument("--batch-cases", type=int, default=512)
+    ap.add_argument("--skewed-n", type=int, default=200, help="edge of the skewed box (profiling: smaller)")
     ap.add_argument("--requests", type=int, default=1000)
     ap.add_argument("--only", choices=["fp64", "mixed"], default=None,
                     help="profiling: run only this precision, device-resident, no e2e or CPU baseline")
