@@ -426,6 +426,7 @@ def main_skewed(args, world, rank, local):
     secs_max = reduce_max(secs, world)
     value = reduce_sum(float(N) * iters, world) / secs_max
     alg = algorithmic_bytes_corrected(N, F, iters, passes)
+    sratio = load_traffic_ratio("skewed_fp64")
     T64 = s64.field()
     launch = s64.launch()
     s64.close()
@@ -464,7 +465,8 @@ def main_skewed(args, world, rank, local):
         "iters_per_step": iters / K, "passes_per_step": 1 + case.n_nonorth_corr,
         "phases_ms_per_step": phases,
         "roofline": {"bound": "hbm", "achieved": alg / secs / 1e9, "peak": hbm_peak, "unit": "GB/s",
-                     "frac": alg / secs / 1e9 / hbm_peak, "traffic": None, "peak_kind": peak_kind,
+                     "frac": alg / secs / 1e9 / hbm_peak, "traffic": (sratio * alg / K) if sratio else None,
+                     "peak_kind": peak_kind,
                      "kernel": "step_kernel_f64", "per": "one step (one launch runs all timed steps)"},
         "gpu_launches": 1, "clocks": clk, "mixed": mixed, "cpu_baseline": cpu,
         "e2e": None,
