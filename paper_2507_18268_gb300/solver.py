@@ -58,7 +58,10 @@ class Solver:
                 self.mesh = BoxInfo(n, f, nb)
                 nbytes = B.lfm_workspace_bytes_box(len(xs) - 1, len(ys) - 1, len(zs) - 1, layout)
             else:
-                self.mesh = BoxInfo(share.mesh.n_cells, share.mesh.n_faces, share.mesh.n_bfaces)
+                # a host mesh's arrays (per-face DT, labels, weights) serve the sharer too
+                self.mesh = (share.mesh if isinstance(share.mesh, LduMesh)
+                             else BoxInfo(share.mesh.n_cells, share.mesh.n_faces, share.mesh.n_bfaces))
+                self.geometry = share.geometry
                 nbytes = B.lfm_workspace_bytes_shared(share.ctx, layout)
             self.workspace_bytes = nbytes
             if workspace == "torch":

@@ -177,3 +177,45 @@ def test_geometry_validation_and_state():
             B.lfm_set_nonorth_correctors(ctx, -1)
     finally:
         B.lfm_destroy(ctx)
+
+
+def test_batched_general_meshes_with_ragged_slot_widths():
+    # a 2-cell-thick and a 1-cell-thick mesh force the generic-width batch kernel
+    cases = [perturbed(50, nx=8, ny=2, nz=3, n_corr=1), perturbed(51, nx=7, ny=1, nz=5, amp=0.2, n_corr=2),
+             perturbed(52, n_corr=0)]
+    solvers = [Solver.from_case(c) for c in cases]
+    try:
+        bt = Batch()
+        for s in solvers:
+            bt.add(s)
+        bt.advance(3)
+        got = [s.field() for s in solvers]
+        bt.close()
+    finally:
+        for s in solvers:
+            s.close()
+    for c, T in zip(cases, got):
+        To, _ = oracle.advance(c, n_steps=3)
+        assert rel(T, To) <= 1e-10, c.name
+
+
+def test_shared_general_mesh_matches_alone():
+    case = CASES["perturbed_corr2_facedt"]()
+    To, _ = oracle.advance(case)
+    mesh, geo = hex_mesh(case)
+    with Solver(mesh, geometry=geo) as owner:
+        with Solver.sharing(owner, case) as s:
+            s.advance(case.n_steps)
+            T = s.field()
+            G, _ = s.grad()
+    assert rel(T, To) <= 1e-10
+    G0, _ = oracle.grad(case, oracle.hex_mesh(case), To)
+    assert rel(G, G0) <= 1e-12
+
+
+def test_corrector_count_limits():
+    with Solver.from_case(CASES["perturbed_corr1"]()) as s:
+        with pytest.raises(B.LfmError) as e:
+            B.lfm_set_nonorth_correctors(s.ctx, 65)
+        assert e.value.code == B.LFM_EINVAL
+        B.lfm_set_nonorth_correctors(s.ctx, 64)
