@@ -258,8 +258,8 @@ def main_ours(args, world, rank, local):
     hbm_peak, peak_kind = load_peaks()
     K, W = args.steps, args.warmup
 
-    if args.only == "mixed":
-        return main_mixed_only(args, world, rank, local, case, mesh, stream)
+    if args.only in ("mixed", "df64"):
+        return main_only(args, world, rank, local, case, mesh, stream)
 
     # ---- FP64, device-resident --------------------------------------------------------
     s64 = Solver.from_case(case, mesh=mesh, device=local, stream=stream)
@@ -283,6 +283,36 @@ def main_ours(args, world, rank, local):
     ratio = load_traffic_ratio("graded200_fp64")
     T64 = s64.field()
     launch = s64.launch()
+
+    # ---- df64 (double-float on the FP32 pipe), device-resident -----------------------
+    df64 = None
+    if not args.no_df64:
+        sdf = Solver.from_case(case.with_(precision=B.LFM_DF64), mesh=mesh, device=local, stream=stream)
+        sdf.advance(W)
+        barrier(world)
+        dsecs, dst = time_device_resident(sdf, B, torch, stream, K)
+        barrier(world)
+        diters = sum(x["iters"] for x in dst)
+        dphases = {k: v / K for k, v in sdf.phase_times().items()}
+        assert all(x["converged"] for x in dst), "df64 step did not converge"
+        dsecs_max = reduce_max(dsecs, world)
+        dvalue = reduce_sum(float(N) * diters, world) / dsecs_max
+        dalg = algorithmic_bytes(N, F, diters, K, 0)
+        Td = sdf.field()
+        dratio = load_traffic_ratio("graded200_df64")
+        df64 = {"value": dvalue, "unit": UNIT, "ms_per_step": 1e3 * dsecs_max / K,
+                "iters_per_step": diters / K,
+                "iters_equal_fp64": [x["iters"] for x in dst] == [x["iters"] for x in st],
+                "speedup_vs_fp64": secs_max / dsecs_max,
+                "max_rel_diff_vs_fp64": float(np.max(np.abs(Td - T64) / np.abs(T64))),
+                "dtype": "df64 (FP32 pairs, 48-bit significand; FP64 scalars)",
+                "phases_ms_per_step": dphases,
+                "roofline": {"bound": "hbm", "achieved": dalg / dsecs / 1e9, "peak": hbm_peak, "unit": "GB/s",
+                             "frac": dalg / dsecs / 1e9 / hbm_peak,
+                             "traffic": (dratio * dalg / K) if dratio else None,
+                             "peak_kind": peak_kind, "kernel": "step_kernel_df64",
+                             "per": "one step (one launch runs all timed steps)"}}
+        sdf.close()
 
     # ---- mixed precision, device-resident ------------------------------------------
     mixed = None
@@ -373,6 +403,7 @@ def main_ours(args, world, rank, local):
                                "note": "ncu: FP64 pipe 70% busy, DRAM 65% (profiles/step_kernel_f64_graded200.md)"},
         "gpu_launches": 1,
         "clocks": clk,
+        "df64": df64,
         "mixed": mixed,
         "e2e": e2e,
         "cpu_baseline": cpu,
@@ -473,22 +504,23 @@ def main_skewed(args, world, rank, local):
     }), flush=True)
 
 
-def main_mixed_only(args, world, rank, local, case, mesh, stream):
-    """Profiling mode: the mixed form alone (one warm-up launch, one timed launch)."""
+def main_only(args, world, rank, local, case, mesh, stream):
+    """Profiling mode: the mixed or the df64 form alone (one warm-up launch, one timed launch)."""
     import torch
 
     from paper_2507_18268_gb300 import Solver
     from paper_2507_18268_gb300 import binding as B
 
     K, W = args.steps, args.warmup
-    smx = Solver.from_case(case.with_(precision=B.LFM_MIXED), mesh=mesh, device=local, stream=stream)
+    prec = B.LFM_MIXED if args.only == "mixed" else B.LFM_DF64
+    smx = Solver.from_case(case.with_(precision=prec), mesh=mesh, device=local, stream=stream)
     smx.advance(W)
     secs, st = time_device_resident(smx, B, torch, stream, K)
     iters = sum(x["iters"] for x in st)
     smx.close()
     if rank == 0:
         print(json.dumps({"metric": METRIC, "value": mesh.n_cells * iters / secs, "unit": UNIT,
-                          "mode": "mixed only (profiling)", "steps": K, "warmup": W,
+                          "mode": f"{args.only} only (profiling)", "steps": K, "warmup": W,
                           "ms_per_step": 1e3 * secs / K, "iters_per_step": iters / K}), flush=True)
 
 
@@ -633,13 +665,14 @@ def main():
     ap.add_argument("--warmup", type=int, default=5)
     ap.add_argument("--impl", default="ours", choices=["ours", "reference"])
     ap.add_argument("--no-mixed", action="store_true")
+    ap.add_argument("--no-df64", action="store_true")
     ap.add_argument("--no-e2e", action="store_true")
     ap.add_argument("--no-cpu-baseline", action="store_true")
     ap.add_argument("--workload", choices=["graded200", "batch512", "serve", "skewed200"], default="graded200")
     ap.add_argument("--batch-cases", type=int, default=512)
     ap.add_argument("--skewed-n", type=int, default=200, help="edge of the skewed box (profiling: smaller)")
     ap.add_argument("--requests", type=int, default=1000)
-    ap.add_argument("--only", choices=["fp64", "mixed"], default=None,
+    ap.add_argument("--only", choices=["fp64", "mixed", "df64"], default=None,
                     help="profiling: run only this precision, device-resident, no e2e or CPU baseline")
     args = ap.parse_args()
     args.steps_given = any(a.startswith("--steps") for a in sys.argv[1:])
@@ -647,7 +680,7 @@ def main():
         ap.error("--warmup must be >= 3")
     if args.only:
         args.no_e2e = args.no_cpu_baseline = True
-        args.no_mixed = args.only == "fp64"
+        args.no_mixed = args.no_df64 = args.only == "fp64"
     world, rank, local = dist_setup()
     try:
         if args.impl == "reference":

@@ -46,7 +46,15 @@ enum {
 };
 
 enum { LFM_FIXED_VALUE = 0, LFM_ZERO_GRADIENT = 1 };
-enum { LFM_FP64 = 0, LFM_MIXED = 1 };
+/* Arithmetic of the step (lfm_solver_opts.precision):
+ *   LFM_FP64   IEEE FP64 throughout; the assembled system is bitwise the CPU reference's.
+ *   LFM_MIXED  FP32 inner CG inside FP64 defect correction (results ~1e-6 relative).
+ *   LFM_DF64   every per-cell operation in double-float (pairs of FP32 numbers, 48-bit
+ *              significand) on the FP32 pipe, per-CTA scalars in FP64: results agree with
+ *              FP64 to rounding (~1e-13 relative), at FP32-pipe speed. Orthogonal meshes
+ *              (lfm_upload_mesh, lfm_upload_box and their sharers), with any DT, sources and
+ *              corrector passes; general geometry needs LFM_FP64 or LFM_MIXED. */
+enum { LFM_FP64 = 0, LFM_MIXED = 1, LFM_DF64 = 2 };
 
 typedef struct lfm_ctx lfm_ctx;
 
@@ -96,9 +104,9 @@ typedef struct {
 
 /* PCG controls. tol: stop when sum|r| / normFactor < tol; rel_tol > 0 also stops when the
  * residual falls below rel_tol times the step's initial residual; max_iter caps and
- * min_iter forces iterations (OpenFOAM defaults: 1000, 0). precision: LFM_FP64 or
+ * min_iter forces iterations (OpenFOAM defaults: 1000, 0). precision: LFM_FP64,
  * LFM_MIXED (FP32 matrix and vectors, FP64 dots / normFactor / convergence test / true
- * residual, FP64 field updated by defect correction). */
+ * residual, FP64 field updated by defect correction) or LFM_DF64 (see above). */
 typedef struct {
   double tol, rel_tol;
   int32_t max_iter, min_iter, precision;
@@ -156,9 +164,10 @@ int lfm_box_layout(int32_t nx, int32_t ny, int32_t nz, const double *xs, const d
 
 /* ---- single-case context ----------------------------------------------------------- */
 
-/* Device bytes lfm_upload_mesh needs for this mesh: precision LFM_FP64 or LFM_MIXED for a
- * workspace serving that precision only, any other value (e.g. -1) for one serving both.
- * A library-owned workspace (no lfm_bind_workspace) always serves both. */
+/* Device bytes lfm_upload_mesh needs for this mesh: precision LFM_FP64, LFM_MIXED or
+ * LFM_DF64 for a workspace serving that precision only (an LFM_DF64 workspace also serves
+ * LFM_FP64), any other value (e.g. -1) for one serving all three.
+ * A library-owned workspace (no lfm_bind_workspace) always serves all three. */
 size_t lfm_workspace_bytes(const lfm_mesh *mesh, int32_t precision);
 
 /* Creates a context on CUDA device `device`, issuing work on `cuda_stream` (a
@@ -167,7 +176,7 @@ int lfm_create(lfm_ctx **out, int device, void *cuda_stream);
 
 /* Binds caller-owned device memory that upload carves all device arrays from: at least
  * lfm_workspace_bytes(mesh, precision) bytes, 256-byte aligned; `precision` (LFM_FP64,
- * LFM_MIXED, or -1 for both) selects which solver buffers it holds, and lfm_set_solver
+ * LFM_MIXED, LFM_DF64, or -1 for all) selects which solver buffers it holds, and lfm_set_solver
  * refuses a precision it does not hold (LFM_ENOMEM). Must precede lfm_upload_mesh; the
  * library never frees it. */
 int lfm_bind_workspace(lfm_ctx *ctx, void *dev_ptr, size_t bytes, int32_t precision);

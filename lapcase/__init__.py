@@ -62,6 +62,7 @@ PATCH_NAMES = ("x0", "x1", "y0", "y1", "z0", "z1")
 
 FP64 = 0
 MIXED = 1
+DF64 = 2
 
 
 @dataclasses.dataclass

@@ -18,7 +18,7 @@ from . import _build
 LFM_OK, LFM_EINVAL, LFM_ENOMEM, LFM_ECUDA = 0, -1, -2, -3
 LFM_ESINGULAR, LFM_ENONFINITE, LFM_ETIMEOUT, LFM_ESTATE = -4, -5, -6, -7
 LFM_FIXED_VALUE, LFM_ZERO_GRADIENT = 0, 1
-LFM_FP64, LFM_MIXED = 0, 1
+LFM_FP64, LFM_MIXED, LFM_DF64 = 0, 1, 2
 LFM_BOTH = -1
 
 _NAMES = {0: "LFM_OK", -1: "LFM_EINVAL", -2: "LFM_ENOMEM", -3: "LFM_ECUDA", -4: "LFM_ESINGULAR",

@@ -39,12 +39,22 @@ struct Layout {
   size_t diag, upper, slot_coef, src, rD, vdt, x, x_old, vSu, vSp, r, w, p, q, Tb;
   size_t Sf, fw, corr, bSf, gE, gD, gH, cK, cL, grad;  // general geometry (0 when absent)
   size_t diag32, slot_coef32, rD32, dx32, r32, w32, p32, q32;
+  size_t x2, diag2, rD2, vdt2, g2;  // df64 form (0 when absent)
   size_t total;
 };
 
-// kind: LFM_FP64 (FP64 solver vectors), LFM_MIXED (FP32 matrix copy + FP32 vectors) or
-// kLayoutBoth (both sets, so that the precision may change after upload).
+// kind: LFM_FP64 (FP64 solver vectors), LFM_MIXED (FP32 matrix copy + FP32 vectors),
+// LFM_DF64 (the FP64 solver vectors, used as double-float pairs by the df64 form, plus the
+// df64 field, diagonal, reciprocal, V/dt and slot conductances) or kLayoutBoth (every set,
+// so that the precision may change after upload).
 constexpr int kLayoutBoth = -1;
+
+int layout_kind(int32_t precision) {
+  return (precision == LFM_FP64 || precision == LFM_MIXED || precision == LFM_DF64) ? precision : kLayoutBoth;
+}
+bool kind_has64(int kind) { return kind != LFM_MIXED; }
+bool kind_has32(int kind) { return kind == LFM_MIXED || kind == kLayoutBoth; }
+bool kind_hasdf(int kind) { return kind == LFM_DF64 || kind == kLayoutBoth; }
 
 // shared_mesh: the mesh arrays (slots, boundary lists, geometry) live in another context.
 // geom: general (non-orthogonal) geometry arrays and the per-case gradient / correction flux.
@@ -104,13 +114,21 @@ Layout make_layout(int64_t N, int64_t F, int64_t NB, int64_t W, int kind, bool s
   L.Tb = take(8 * NB);
   L.r = L.w = L.p = L.q = 0;
   L.diag32 = L.slot_coef32 = L.rD32 = L.dx32 = L.r32 = L.w32 = L.p32 = L.q32 = 0;
-  if (kind == LFM_FP64 || kind == kLayoutBoth) {
+  L.x2 = L.diag2 = L.rD2 = L.vdt2 = L.g2 = 0;
+  if (kind_has64(kind)) {
     L.r = take(8 * N);
     L.w = take(8 * N);
     L.p = take(8 * N);
     L.q = take(8 * N);
   }
-  if (kind == LFM_MIXED || kind == kLayoutBoth) {
+  if (kind_hasdf(kind)) {
+    L.x2 = take(8 * N);
+    L.diag2 = take(8 * N);
+    L.rD2 = take(8 * N);
+    L.vdt2 = take(8 * N);
+    L.g2 = take(8 * W * N);
+  }
+  if (kind_has32(kind)) {
     L.diag32 = take(4 * N);
     L.slot_coef32 = take(4 * W * N);
     L.rD32 = take(4 * N);
@@ -164,6 +182,9 @@ struct lfm_ctx {
   double dt = 1.0;
   lfm_solver_opts opts{1e-6, 0.0, 1000, 0, LFM_FP64};
   bool has64 = false, has32 = false;  // solver blocks present in the workspace
+  bool hasdf = false;                 // df64 block present
+  bool df_dirty = true;               // df64 conductances / V/dt to rebuild before the next df64 launch
+  double mean_V = 1.0;                // mean cell volume (sets the df64 scale with dt)
   bool has_geom = false;              // general geometry uploaded (corrected laplacian)
   bool ops_dirty = false;             // operator weights to rebuild before the next launch
   bool has_Su = false, has_Sp = false;  // volumetric source set (lfm_set_source)
@@ -357,6 +378,16 @@ void refresh_case(lfm_ctx* c) {
   cs.n_corr = c->n_corr;
 }
 
+// Power-of-two scale of the df64 form's system: V/dt near one for a cell of mean volume.
+double df_scale_for(double mean_V, double dt) {
+  const double v = mean_V / dt;
+  if (!(std::isfinite(v) && v > 0)) return 1.0;
+  long k = std::lround(std::log2(v));
+  if (k > 900) k = 900;
+  if (k < -900) k = -900;
+  return std::ldexp(1.0, (int)-k);
+}
+
 void bind_pointers(lfm_ctx* c) {
   const Layout& L = c->lay;
   char* b = c->ws;
@@ -438,6 +469,13 @@ void bind_pointers(lfm_ctx* c) {
   cs.w32 = m ? reinterpret_cast<float*>(b + L.w32) : nullptr;
   cs.p32 = m ? reinterpret_cast<float*>(b + L.p32) : nullptr;
   cs.q32 = m ? reinterpret_cast<float*>(b + L.q32) : nullptr;
+  const bool f = c->hasdf;
+  cs.x2 = f ? reinterpret_cast<float2*>(b + L.x2) : nullptr;
+  cs.diag2 = f ? reinterpret_cast<float2*>(b + L.diag2) : nullptr;
+  cs.rD2 = f ? reinterpret_cast<float2*>(b + L.rD2) : nullptr;
+  cs.vdt2 = f ? reinterpret_cast<const float2*>(b + L.vdt2) : nullptr;
+  cs.g2 = f ? reinterpret_cast<const float2*>(b + L.g2) : nullptr;
+  cs.df_scale = df_scale_for(c->mean_V, c->dt);
 }
 
 // V/dt per cell, recomputed when dt or the mesh changes (the assembly reads it every step).
@@ -446,6 +484,19 @@ bool ctx_batch_pending(const lfm_ctx* c);
 int refresh_vdt(lfm_ctx* c) {
   CK(c, launch_vdt(c->cs.V, c->dt, const_cast<double*>(c->cs.vdt), c->N, c->stream));
   CK(c, cudaStreamSynchronize(c->stream));
+  c->cs.df_scale = df_scale_for(c->mean_V, c->dt);
+  c->df_dirty = true;
+  return LFM_OK;
+}
+
+// Rebuilds the df64 conductances and V/dt (a0 of the df64 form) when the mesh, DT or dt
+// changed since they were built. Enqueued on the context's stream.
+int refresh_df(lfm_ctx* c) {
+  if (c->opts.precision != LFM_DF64 || !c->df_dirty) return LFM_OK;
+  if (!c->hasdf) return fail(c, LFM_ENOMEM, "the workspace has no df64 buffers");
+  CK(c, launch_df_setup(c->cs, c->stream));
+  CK(c, cudaStreamSynchronize(c->stream));  // batches launch on their own stream
+  c->df_dirty = false;
   return LFM_OK;
 }
 
@@ -471,9 +522,16 @@ int need_uploaded(lfm_ctx* c) {
 int enqueue_chunk(lfm_ctx* c, int steps, int mode) {
   refresh_case(c);
   if (int rc = refresh_ops(c)) return rc;
+  if (mode == kModeSteps)
+    if (int rc = refresh_df(c)) return rc;
   int e = 0;
   Launch L = current_launch(c, e);
   if (e) return fail(c, LFM_ECUDA, "no co-resident CTA fits the step kernel");
+  if (mode == kModeAssembleOnly && c->opts.precision == LFM_DF64) {  // read-back runs the FP64 assembly
+    const int m = max_coresident_ctas(LFM_FP64, L.threads, c->W, c->device);
+    if (L.ctas > m) L.ctas = m;
+    if (L.ctas <= 0) return fail(c, LFM_ECUDA, "no co-resident CTA fits the assembly kernel");
+  }
   if (L.skip_cta >= 0 && L.ctas < 2) return fail(c, LFM_EINVAL, "the skip-arrival hook needs >= 2 CTAs");
   CK(c, cudaMemsetAsync(c->cs.sync, 0, sizeof(SyncWords), c->stream));
   CK(c, launch_steps(c->cs, L, steps, mode, c->stream));
@@ -540,7 +598,7 @@ size_t lfm_workspace_bytes(const lfm_mesh* mesh, int32_t precision) {
     g_last_error = why;
     return 0;
   }
-  if (precision != LFM_FP64 && precision != LFM_MIXED) precision = kLayoutBoth;
+  precision = layout_kind(precision);
   return make_layout(mesh->n_cells, mesh->n_faces, mesh->n_bfaces, slot_width(mesh), precision).total;
 }
 
@@ -575,7 +633,7 @@ int lfm_bind_workspace(lfm_ctx* c, void* dev_ptr, size_t bytes, int32_t precisio
   c->ws_bytes = bytes;
   c->ws_bound = true;
   c->ws_owned = false;
-  c->ws_kind = (precision == LFM_FP64 || precision == LFM_MIXED) ? precision : kLayoutBoth;
+  c->ws_kind = layout_kind(precision);
   return LFM_OK;
 }
 
@@ -593,7 +651,7 @@ static int upload_mesh_impl(lfm_ctx* c, const lfm_mesh* m, const lfm_geometry* g
                 (unsigned long long)W * (unsigned long long)m->n_cells);
   const int kind = c->ws_bound ? c->ws_kind : kLayoutBoth;
   const Layout use = make_layout(m->n_cells, m->n_faces, m->n_bfaces, W, kind, false, geo != nullptr);
-  const bool has64 = kind != LFM_MIXED, has32 = kind != LFM_FP64;
+  const bool has64 = kind_has64(kind), has32 = kind_has32(kind), hasdf = kind_hasdf(kind);
   if (c->ws_bound) {
     if (c->ws_bytes < use.total) return fail(c, LFM_ENOMEM, "workspace has %zu bytes, needs %zu", c->ws_bytes, use.total);
   } else {
@@ -609,12 +667,19 @@ static int upload_mesh_impl(lfm_ctx* c, const lfm_mesh* m, const lfm_geometry* g
     c->ws_owned = true;
   }
   c->lay = use;
+  {
+    double sv = 0.0;
+    for (int32_t i = 0; i < m->n_cells; ++i) sv += m->V[i];
+    c->mean_V = sv / (double)m->n_cells;
+  }
   c->N = m->n_cells;
   c->F = m->n_faces;
   c->NB = m->n_bfaces;
   c->W = W;
   c->has64 = has64;
   c->has32 = has32;
+  c->hasdf = hasdf;
+  c->df_dirty = true;
   c->has_geom = geo != nullptr;
   c->n_corr = 0;
   c->has_Su = c->has_Sp = false;
@@ -694,7 +759,7 @@ size_t lfm_workspace_bytes_geometry(const lfm_mesh* mesh, int32_t precision) {
     g_last_error = why;
     return 0;
   }
-  if (precision != LFM_FP64 && precision != LFM_MIXED) precision = kLayoutBoth;
+  precision = layout_kind(precision);
   return make_layout(mesh->n_cells, mesh->n_faces, mesh->n_bfaces, slot_width(mesh), precision, false, true).total;
 }
 
@@ -760,7 +825,7 @@ int lfm_upload_box(lfm_ctx* c, int32_t nx, int32_t ny, int32_t nz, const double*
   lfm_box_counts(nx, ny, nz, &N, &F, &NB, &W);
   const int kind = c->ws_bound ? c->ws_kind : kLayoutBoth;
   const Layout use = make_layout(N, F, NB, W, kind);
-  const bool has64 = kind != LFM_MIXED, has32 = kind != LFM_FP64;
+  const bool has64 = kind_has64(kind), has32 = kind_has32(kind), hasdf = kind_hasdf(kind);
   if (c->ws_bound) {
     if (c->ws_bytes < use.total) return fail(c, LFM_ENOMEM, "workspace has %zu bytes, needs %zu", c->ws_bytes, use.total);
   } else {
@@ -772,12 +837,15 @@ int lfm_upload_box(lfm_ctx* c, int32_t nx, int32_t ny, int32_t nz, const double*
     c->ws_owned = true;
   }
   c->lay = use;
+  c->mean_V = (xs[nx] - xs[0]) * (ys[ny] - ys[0]) * (zs[nz] - zs[0]) / (double)N;
   c->N = N;
   c->F = F;
   c->NB = NB;
   c->W = W;
   c->has64 = has64;
   c->has32 = has32;
+  c->hasdf = hasdf;
+  c->df_dirty = true;
   c->has_geom = false;
   c->n_corr = 0;
   c->has_Su = c->has_Sp = false;
@@ -821,13 +889,13 @@ int lfm_upload_box(lfm_ctx* c, int32_t nx, int32_t ny, int32_t nz, const double*
 size_t lfm_workspace_bytes_box(int32_t nx, int32_t ny, int32_t nz, int32_t precision) {
   int32_t N, F, NB, W;
   if (lfm_box_counts(nx, ny, nz, &N, &F, &NB, &W) != LFM_OK) return 0;
-  if (precision != LFM_FP64 && precision != LFM_MIXED) precision = kLayoutBoth;
+  precision = layout_kind(precision);
   return make_layout(N, F, NB, W, precision).total;
 }
 
 size_t lfm_workspace_bytes_shared(const lfm_ctx* src, int32_t precision) {
   if (!src || !src->uploaded) return 0;
-  if (precision != LFM_FP64 && precision != LFM_MIXED) precision = kLayoutBoth;
+  precision = layout_kind(precision);
   const lfm_ctx* root = src->mesh_src ? src->mesh_src : src;
   return make_layout(src->N, src->F, src->NB, src->W, precision, true, root->has_geom).total;
 }
@@ -842,7 +910,7 @@ int lfm_upload_mesh_shared(lfm_ctx* c, lfm_ctx* src) {
   DeviceGuard g(c->device);
   const int kind = c->ws_bound ? c->ws_kind : kLayoutBoth;
   const Layout use = make_layout(root->N, root->F, root->NB, root->W, kind, true, root->has_geom);
-  const bool has64 = kind != LFM_MIXED, has32 = kind != LFM_FP64;
+  const bool has64 = kind_has64(kind), has32 = kind_has32(kind), hasdf = kind_hasdf(kind);
   if (c->ws_bound) {
     if (c->ws_bytes < use.total) return fail(c, LFM_ENOMEM, "workspace has %zu bytes, needs %zu", c->ws_bytes, use.total);
   } else {
@@ -856,12 +924,15 @@ int lfm_upload_mesh_shared(lfm_ctx* c, lfm_ctx* src) {
   c->mesh_src = root;
   root->n_sharers++;
   c->lay = use;
+  c->mean_V = root->mean_V;
   c->N = root->N;
   c->F = root->F;
   c->NB = root->NB;
   c->W = root->W;
   c->has64 = has64;
   c->has32 = has32;
+  c->hasdf = hasdf;
+  c->df_dirty = true;
   c->has_geom = root->has_geom;
   c->ops_dirty = root->has_geom;
   c->n_corr = 0;
@@ -930,6 +1001,7 @@ int lfm_set_diffusivity(lfm_ctx* c, double uniform, const double* DT_faces, cons
   }
   CK(c, cudaStreamSynchronize(c->stream));
   c->ops_dirty = true;
+  c->df_dirty = true;
   return LFM_OK;
 }
 
@@ -959,6 +1031,7 @@ int lfm_set_diffusivity_cells(lfm_ctx* c, const double* DT_cells, const double* 
   if (e != cudaSuccess) return cuda_fail(c, e, "lfm_set_diffusivity_cells");
   c->cs.DT_is_uniform = 0;
   c->ops_dirty = true;
+  c->df_dirty = true;
   return LFM_OK;
 }
 
@@ -1031,11 +1104,14 @@ int lfm_set_solver(lfm_ctx* c, const lfm_solver_opts* o) {
   if (!o) return fail(c, LFM_EINVAL, "opts is NULL");
   if (!(std::isfinite(o->tol) && o->tol >= 0) || !(std::isfinite(o->rel_tol) && o->rel_tol >= 0) ||
       o->max_iter < 1 || o->min_iter < 0 || o->min_iter > o->max_iter ||
-      (o->precision != LFM_FP64 && o->precision != LFM_MIXED))
+      (o->precision != LFM_FP64 && o->precision != LFM_MIXED && o->precision != LFM_DF64))
     return fail(c, LFM_EINVAL, "invalid solver options");
-  if ((o->precision == LFM_FP64 && !c->has64) || (o->precision == LFM_MIXED && !c->has32))
+  if ((o->precision == LFM_FP64 && !c->has64) || (o->precision == LFM_MIXED && !c->has32) ||
+      (o->precision == LFM_DF64 && !c->hasdf))
     return fail(c, LFM_ENOMEM, "the workspace was laid out without the %s solver buffers",
-                o->precision == LFM_FP64 ? "FP64" : "mixed-precision");
+                o->precision == LFM_FP64 ? "FP64" : (o->precision == LFM_MIXED ? "mixed-precision" : "df64"));
+  if (o->precision == LFM_DF64 && c->has_geom)
+    return fail(c, LFM_EINVAL, "the df64 form serves orthogonal meshes; general geometry needs FP64 or mixed");
   const bool launch_changes = o->precision != c->opts.precision;
   c->opts = *o;
   if (launch_changes) return choose_launch(c);
@@ -1519,8 +1595,10 @@ int lfm_batch_advance_async(lfm_batch* b, int32_t n_steps, int32_t use_graph) {
     if (c->pending_steps) return bfail(b, LFM_ESTATE, "case %d has a pending advance of its own", b->order[i]);
     refresh_case(c);
     if (refresh_ops(c) != LFM_OK) return bfail(b, LFM_ECUDA, "case %d: operator rebuild failed", b->order[i]);
-    if ((c->opts.precision == LFM_FP64 && !c->has64) || (c->opts.precision == LFM_MIXED && !c->has32))
+    if ((c->opts.precision == LFM_FP64 && !c->has64) || (c->opts.precision == LFM_MIXED && !c->has32) ||
+        (c->opts.precision == LFM_DF64 && !c->hasdf))
       return bfail(b, LFM_ENOMEM, "case %d has no buffers for its precision", b->order[i]);
+    if (refresh_df(c) != LFM_OK) return bfail(b, LFM_ECUDA, "case %d: df64 set-up failed", b->order[i]);
     b->h_cases[i] = c->cs;
     if (c->W != 6) W = 0;
   }

@@ -14,6 +14,7 @@
 #include "lfm_device.cuh"
 #include "lfm_internal.h"
 #include "lfm_solve.cuh"
+#include "lfm_solve_df.cuh"
 
 namespace lfm {
 namespace {
@@ -58,6 +59,8 @@ __global__ void __launch_bounds__(B, 1024 / B) batch_kernel(const CaseDev* __res
     const int base = case_step[c];
     if (s_cs.precision == LFM_MIXED)
       run_steps_mixed<B, W>(s_cs, s_cs, tm, n_steps, kModeSteps, sh, base);
+    else if (s_cs.precision == LFM_DF64)
+      run_steps_df64<B, W>(s_cs, s_cs, tm, n_steps, sh, base);
     else
       run_steps_f64<B, W>(s_cs, s_cs, tm, n_steps, kModeSteps, sh, base);
     __syncthreads();

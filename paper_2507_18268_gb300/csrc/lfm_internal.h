@@ -119,6 +119,16 @@ struct CaseDev {
   float* p32;
   float* q32;
 
+  // df64 form (lfm_solve_df.cuh): the field, the diagonal and its reciprocal, V/dt and the
+  // per-slot face conductances as double-float pairs (hi, lo), all scaled by df_scale (a
+  // power of two); r, w, p, q and x_old are used as float2 arrays of the same size
+  float2* x2;                // [N]
+  float2* diag2;             // [N]
+  float2* rD2;               // [N]
+  const float2* vdt2;        // [N]   V/dt * df_scale
+  const float2* g2;          // [W*N] DT |Sf| deltaCoeff * df_scale at both slots of each face
+  double df_scale;
+
   // team state
   SyncWords* sync;
   double* partials;          // [kMaxCtas * kMaxSums]
@@ -169,6 +179,8 @@ cudaError_t launch_dt_cells(const CaseDev& cs, const double* DTc, const double* 
                             cudaStream_t stream);
 // out[c] = V[c] * a[c] (a null: out = 0).
 cudaError_t launch_times_volume(const CaseDev& cs, const double* a, double* out, cudaStream_t stream);
+// df64 form set-up: the per-slot conductances g2 and V/dt (vdt2), both times cs.df_scale.
+cudaError_t launch_df_setup(const CaseDev& cs, cudaStream_t stream);
 
 // Face-to-cell addressing of a general mesh built on the device (lfm_addr.cu): owner,
 // neighbour, bface_cell are device arrays; W the largest internal-face count of a cell.

@@ -1,0 +1,423 @@
+// lfm_solve_df.cuh -- the implicit laplacianFoam step in df64 (double-float) arithmetic,
+// shared by the single-case kernel (lfm_step.cu) and the batched kernel (lfm_batch.cu).
+//
+// The same method as the FP64 step in lfm_solve.cuh (Eq. (1), the listing "laplacianFoam
+// application": per step assemble fvm::ddt(T) - fvm::laplacian(DT, T) and solve it with the
+// diagonal-preconditioned CG, convergence on OpenFOAM's normFactor-scaled L1 residual), with
+// every per-cell operation done in df64 on the FP32 pipe (lfm_df64.cuh) and only per-CTA
+// scalars (alpha, beta, the reduced sums) in FP64. Storage is 8 bytes per value as in FP64.
+//
+// Set-up (a0, when the mesh, DT or dt change): the face conductances g_f = DT_f |S_f|
+// deltaCoeff_f, formed in FP64, are stored per slot as df64 (g2, the face's value at its
+// slot in both of its cells' rows), and V/dt per cell (vdt2). Both are multiplied by the
+// case's power-of-two scale s (df_scale), chosen so that V/dt is of order one: PCG is
+// invariant under scaling A and b by a common factor, a power of two scales every FP64
+// and df64 value exactly, and the scaled values keep far from FP32's underflow. Reported
+// normFactors are divided by s.
+//
+// Per launch: the field T (FP64, x) is split into df64 (x2) by the first pass and written
+// back to x after the last step. Per step (phases separated by team barriers):
+//   S  sum of x (for xRef); with correctors also x at the start of the step
+//   R  per row: diag = sum of the slot conductances (slot order) + boundary + V/dt, the
+//      source, 1/diag (FP32 reciprocal + one df64 Newton step), the row sum; r = b - A x
+//      (in flux form, see pass_rows_init_df), normFactor terms, sum|r|, w = rD r, rho; p = w
+//   loop: P p = w + beta p; M q = A p, p.q; U x += alpha p, r -= alpha q, w = rD r, sum|r|, w.r
+// A row of A v is diag_c v_c - sum_k g_ck v_other(k): the off-diagonal coefficient of face f
+// is -g_f in both rows (the matrix is symmetric), so the slot array of conductances is the
+// matrix's off-diagonal part.
+//
+// Boundary faces (a few per cent of cells) are summed in FP64 and converted once per row;
+// so are the optional volumetric sources. General (non-orthogonal) geometry is served by the
+// FP64 and mixed forms only.
+#pragma once
+
+#include <cuda_runtime.h>
+
+#include "lfm_device.cuh"
+#include "lfm_df64.cuh"
+#include "lfm_internal.h"
+#include "lfm_solve.cuh"
+
+namespace lfm {
+namespace {
+
+__device__ __forceinline__ df df_from_scalar(double v) { return df_from_double(v); }
+
+// S: this thread's sum of x over [c0, c1) (per-thread df64 sum, converted once). `convert`:
+// first pass of the launch, x2 is split from the FP64 field x. `save_old`: keep x as the
+// step's starting field (the ddt source of the corrector passes).
+template <int B>
+__device__ __noinline__ double pass_sum_df(const CaseDev& cs, int c0, int c1, bool convert, bool save_old) {
+  float2* __restrict__ x2 = cs.x2;
+  float2* __restrict__ xo2 = reinterpret_cast<float2*>(cs.x_old);
+  DfAcc acc;
+  int c = c0 + (int)threadIdx.x;
+  if (!convert && !save_old) {  // the common case: four cells per trip, loads first
+    for (; c + 3 * B < c1; c += 4 * B) {
+      const df a = ld_df(x2 + c), b = ld_df(x2 + c + B), d = ld_df(x2 + c + 2 * B), e = ld_df(x2 + c + 3 * B);
+      acc.add(a);
+      acc.add(b);
+      acc.add(d);
+      acc.add(e);
+    }
+  }
+  for (; c < c1; c += B) {
+    df v;
+    if (convert) {
+      v = df_from_double(cs.x[c]);
+      st_df(x2 + c, v);
+    } else {
+      v = ld_df(x2 + c);
+    }
+    if (save_old) st_df(xo2 + c, v);
+    acc.add(v);
+  }
+  return acc.value();
+}
+
+// The FP64 field from the df64 one (end of the launch; each CTA its own cells).
+template <int B>
+__device__ __noinline__ void pass_store_x(const CaseDev& cs, int c0, int c1) {
+  const float2* __restrict__ x2 = cs.x2;
+  double* __restrict__ x = cs.x;
+  for (int c = c0 + (int)threadIdx.x; c < c1; c += B) x[c] = df_to_double(ld_df(x2 + c));
+}
+
+// Boundary conductance, source and flux g_b (T_b - x_c) of row c (fixedValue faces;
+// zeroGradient adds nothing), in FP64 with the case scale, in ascending face order.
+__device__ __forceinline__ void row_boundary_df(const CaseDev& cs, int c, df xc, df& gsum, df& ssum, df& flux) {
+  const int b0 = __ldg(cs.b_start + c), b1 = __ldg(cs.b_start + c + 1);
+  gsum = mkdf(0.0f, 0.0f);
+  ssum = mkdf(0.0f, 0.0f);
+  flux = mkdf(0.0f, 0.0f);
+  if (b0 == b1) return;
+  const double x = df_to_double(xc);
+  double g = 0.0, s = 0.0, fl = 0.0;
+  for (int k = b0; k < b1; ++k) {
+    const int bf = __ldg(cs.b_face + k);
+    if (__ldg(cs.btype + bf) == LFM_FIXED_VALUE) {
+      const double gb = __ldg(cs.bDT + bf) * __ldg(cs.bmagSf + bf) * __ldg(cs.bdelta + bf) * cs.df_scale;
+      const double tb = __ldg(cs.bval + bf);
+      g += gb;
+      s += gb * tb;
+      fl += gb * (tb - x);
+    }
+  }
+  gsum = df_from_double(g);
+  ssum = df_from_double(s);
+  flux = df_from_double(fl);
+}
+
+// R: rows of the matrix and, from the same loaded row, the initial residual, normFactor
+// terms, sum|r| and rho; p = w. kSrc: correctors (ddt source from x_old) or volumetric
+// sources present.
+// The residual is evaluated in flux form,
+//   r_c = sum_k g_k (x_other(k) - x_c) + sum_b g_b (T_b - x_c) + V/dt (x_old,c - x_c)
+//         + V Su_c + V Sp_c x_c,
+// which equals b - A x term by term. Formed as b - A x, r would be the small difference of
+// two values of order V/dt T and carry their rounding error, ~2^-48 |b|, amplified by
+// |b| / |r| (about 1e6 for a time step that changes T by one part in a million); the
+// differences of nearby values here are almost exact, so r keeps the format's relative
+// accuracy. A x for the normFactor terms is then b - r.
+template <int B, int W, bool kSrc>
+__device__ __noinline__ Sums3 pass_rows_init_df(const CaseDev& cs, int c0, int c1, double xRef) {
+  const float2* __restrict__ x2 = cs.x2;
+  const float2* __restrict__ g2 = cs.g2;
+  float2* __restrict__ r2 = reinterpret_cast<float2*>(cs.r);
+  float2* __restrict__ p2 = reinterpret_cast<float2*>(cs.p);
+  const size_t N = (size_t)cs.N;
+  const df xr = df_from_scalar(xRef);
+  DfAcc a_nf, a_r, a_rho;
+  for (int c = c0 + (int)threadIdx.x; c < c1; c += B) {
+    const df xc = ld_df(x2 + c);
+    df d, flux;
+    if constexpr (W > 0) {
+      int o[W];
+      df g[W];
+#pragma unroll
+      for (int k = 0; k < W; ++k) {
+        o[k] = __ldg(cs.slot_other + (size_t)k * N + c);
+        g[k] = ldg_df(g2 + (size_t)k * N + c);
+      }
+      df xo_[W];
+#pragma unroll
+      for (int k = 0; k < W; ++k) xo_[k] = ld_df(x2 + o[k]);
+      d = g[0];
+#pragma unroll
+      for (int k = 1; k < W; ++k) d = df_add(d, g[k]);  // padding slots hold 0
+      flux = df_mul(g[0], df_sub(xo_[0], xc));
+#pragma unroll
+      for (int k = 1; k < W; ++k) flux = df_fma(g[k], df_sub(xo_[k], xc), flux);
+    } else {
+      d = mkdf(0.0f, 0.0f);
+      flux = mkdf(0.0f, 0.0f);
+      for (int k = 0; k < cs.W; ++k) {
+        const size_t at = (size_t)k * N + c;
+        const df gk = ldg_df(g2 + at);
+        d = df_add(d, gk);
+        flux = df_fma(gk, df_sub(ld_df(x2 + __ldg(cs.slot_other + at)), xc), flux);
+      }
+    }
+    df gb, sb, fb;
+    row_boundary_df(cs, c, xc, gb, sb, fb);
+    const df vdt = ldg_df(cs.vdt2 + c);
+    const bool has_old = kSrc && cs.n_corr > 0;
+    const df xo = has_old ? ld_df(reinterpret_cast<const float2*>(cs.x_old) + c) : xc;
+    d = df_add(df_add(d, gb), vdt);
+    df src = df_fma(vdt, xo, sb);
+    df sa = df_add(vdt, gb);
+    df rc = df_add(flux, fb);
+    if (has_old) rc = df_fma(vdt, df_sub(xo, xc), rc);
+    if (kSrc && cs.vSp) {
+      const df v = df_from_double(cs.vSp[c] * cs.df_scale);
+      d = df_sub(d, v);
+      sa = df_sub(sa, v);
+      rc = df_fma(v, xc, rc);
+    }
+    if (kSrc && cs.vSu) {
+      const df v = df_from_double(cs.vSu[c] * cs.df_scale);
+      src = df_add(src, v);
+      rc = df_add(rc, v);
+    }
+    const df ax = df_sub(src, rc);
+    const df rd = df_rcp(d);
+    const df sx = df_mul(sa, xr);
+    a_nf.add(df_abs(df_sub(ax, sx)));
+    a_nf.add(df_abs(df_sub(src, sx)));
+    a_r.add(df_abs(rc));
+    const df wc = df_mul(rd, rc);
+    a_rho.add(df_mul(wc, rc));
+    st_df(cs.diag2 + c, d);
+    st_df(cs.rD2 + c, rd);
+    st_df(r2 + c, rc);
+    st_df(p2 + c, wc);
+  }
+  return Sums3{a_nf.value(), a_r.value(), a_rho.value()};
+}
+
+// Rows c and c2 of A v, all loads of both rows issued before any is used.
+template <int W>
+__device__ __forceinline__ void rows2_df(const CaseDev& cs, int c, int c2, const float2* __restrict__ v, df& y,
+                                         df& y2, df& vc, df& vc2) {
+  const size_t N = (size_t)cs.N;
+  const float2* __restrict__ g2 = cs.g2;
+  vc = ld_df(v + c);
+  vc2 = ld_df(v + c2);
+  df acc = df_mul(ld_df(cs.diag2 + c), vc), acc2 = df_mul(ld_df(cs.diag2 + c2), vc2);
+  if constexpr (W > 0) {
+    int o[W], o2[W];
+    df g[W], h[W];
+#pragma unroll
+    for (int k = 0; k < W; ++k) {
+      o[k] = __ldg(cs.slot_other + (size_t)k * N + c);
+      o2[k] = __ldg(cs.slot_other + (size_t)k * N + c2);
+      g[k] = ldg_df(g2 + (size_t)k * N + c);
+      h[k] = ldg_df(g2 + (size_t)k * N + c2);
+    }
+#pragma unroll
+    for (int k = 0; k < W; ++k) {
+      acc = df_fma(df_neg(g[k]), ld_df(v + o[k]), acc);
+      acc2 = df_fma(df_neg(h[k]), ld_df(v + o2[k]), acc2);
+    }
+  } else {
+    for (int k = 0; k < cs.W; ++k) {
+      const size_t at = (size_t)k * N;
+      acc = df_fma(df_neg(ldg_df(g2 + at + c)), ld_df(v + __ldg(cs.slot_other + at + c)), acc);
+      acc2 = df_fma(df_neg(ldg_df(g2 + at + c2)), ld_df(v + __ldg(cs.slot_other + at + c2)), acc2);
+    }
+  }
+  y = acc;
+  y2 = acc2;
+}
+
+template <int W>
+__device__ __forceinline__ df row1_df(const CaseDev& cs, int c, const float2* __restrict__ v, df& vc) {
+  const size_t N = (size_t)cs.N;
+  const int ns = W > 0 ? W : cs.W;
+  vc = ld_df(v + c);
+  df acc = df_mul(ld_df(cs.diag2 + c), vc);
+#pragma unroll
+  for (int k = 0; k < (W > 0 ? W : kMaxSlots); ++k) {
+    if (W == 0 && k >= ns) break;
+    const size_t at = (size_t)k * N + c;
+    acc = df_fma(df_neg(ldg_df(cs.g2 + at)), ld_df(v + __ldg(cs.slot_other + at)), acc);
+  }
+  return acc;
+}
+
+// P: p = w + beta p.
+template <int B>
+__device__ __forceinline__ void pass_direction_df(int c0, int c1, df beta, float2* __restrict__ p,
+                                                  const float2* __restrict__ w) {
+  int c = c0 + (int)threadIdx.x;
+  for (; c + B < c1; c += 2 * B) {
+    const df p1 = ld_df(p + c), p2 = ld_df(p + c + B), w1 = ld_df(w + c), w2 = ld_df(w + c + B);
+    st_df(p + c, df_fma(beta, p1, w1));
+    st_df(p + c + B, df_fma(beta, p2, w2));
+  }
+  if (c < c1) st_df(p + c, df_fma(beta, ld_df(p + c), ld_df(w + c)));
+}
+
+// M: q = A p; returns this thread's share of p.q.
+template <int B, int W>
+__device__ __forceinline__ double pass_amul_dot_df(const CaseDev& cs, int c0, int c1, const float2* __restrict__ p,
+                                                   float2* __restrict__ q) {
+  DfAcc s;
+  int c = c0 + (int)threadIdx.x;
+  for (; c + B < c1; c += 2 * B) {
+    df y1, y2, pc1, pc2;
+    rows2_df<W>(cs, c, c + B, p, y1, y2, pc1, pc2);
+    st_df(q + c, y1);
+    st_df(q + c + B, y2);
+    s.add(df_mul(y1, pc1));
+    s.add(df_mul(y2, pc2));
+  }
+  if (c < c1) {
+    df pc;
+    const df y = row1_df<W>(cs, c, p, pc);
+    st_df(q + c, y);
+    s.add(df_mul(y, pc));
+  }
+  return s.value();
+}
+
+// U: x += alpha p, r -= alpha q, w = rD r; returns this thread's sum|r| and w.r.
+template <int B>
+__device__ __forceinline__ double2 pass_update_df(int c0, int c1, df alpha, float2* __restrict__ x,
+                                                  float2* __restrict__ r, float2* __restrict__ w,
+                                                  const float2* __restrict__ p, const float2* __restrict__ q,
+                                                  const float2* __restrict__ rD) {
+  DfAcc sa, sr;
+  const df nalpha = df_neg(alpha);
+  int c = c0 + (int)threadIdx.x;
+  for (; c + B < c1; c += 2 * B) {
+    const int e = c + B;
+    const df pa = ld_df(p + c), pb = ld_df(p + e), qa = ld_df(q + c), qb = ld_df(q + e);
+    const df xa = ld_df(x + c), xb = ld_df(x + e), ra = ld_df(r + c), rb = ld_df(r + e);
+    const df da = ld_df(rD + c), db = ld_df(rD + e);
+    const df rna = df_fma(nalpha, qa, ra), rnb = df_fma(nalpha, qb, rb);
+    const df wa = df_mul(da, rna), wb = df_mul(db, rnb);
+    st_df(x + c, df_fma(alpha, pa, xa));
+    st_df(x + e, df_fma(alpha, pb, xb));
+    st_df(r + c, rna);
+    st_df(r + e, rnb);
+    st_df(w + c, wa);
+    st_df(w + e, wb);
+    sa.add(df_abs(rna));
+    sa.add(df_abs(rnb));
+    sr.add(df_mul(wa, rna));
+    sr.add(df_mul(wb, rnb));
+  }
+  if (c < c1) {
+    const df rn = df_fma(nalpha, ld_df(q + c), ld_df(r + c));
+    const df wn = df_mul(ld_df(rD + c), rn);
+    st_df(x + c, df_fma(alpha, ld_df(p + c), ld_df(x + c)));
+    st_df(r + c, rn);
+    st_df(w + c, wn);
+    sa.add(df_abs(rn));
+    sr.add(df_mul(wn, rn));
+  }
+  return make_double2(sa.value(), sr.value());
+}
+
+// The steps of one launch. Returns false when a barrier failed (the caller leaves).
+template <int B, int W>
+__device__ bool steps_df64(const CaseDev& cs, const CaseDev& cref, const Team& tm, int n_steps, TeamShared& sh,
+                           int stats_base, int c0, int c1) {
+  const int tid = threadIdx.x;
+  float2* __restrict__ x = cs.x2;
+  float2* __restrict__ r = reinterpret_cast<float2*>(cs.r);
+  float2* __restrict__ w = reinterpret_cast<float2*>(cs.w);
+  float2* __restrict__ p = reinterpret_cast<float2*>(cs.p);
+  float2* __restrict__ q = reinterpret_cast<float2*>(cs.q);
+  const float2* __restrict__ rD = cs.rD2;
+  const double inv_scale = 1.0 / cs.df_scale;  // a power of two: exact
+
+  PhaseClock clk(cs, tm);
+  const bool src_mode = cs.n_corr > 0 || cs.vSu != nullptr || cs.vSp != nullptr;
+  for (int step = 0; step < n_steps; ++step) {
+    int iters_tot = 0, solves = 0, status = 0;
+    double nf0 = 0.0, init0 = 0.0, res = 0.0;
+    bool conv = false;
+    for (int pass = 0; pass <= cs.n_corr; ++pass) {
+      // ---- S: sum of x (first pass of the launch: split the FP64 field) ----------------
+      double v[1] = {pass_sum_df<B>(cref, c0, c1, step == 0 && pass == 0, pass == 0 && cs.n_corr > 0)};
+      if (!team_allreduce<1>(tm, v, sh)) return false;
+      clk.lap(kPhAssembly);
+      // ---- R: rows, initial residual, normFactor, first direction ----------------------
+      const double xRef = v[0] / (double)cs.N;
+      const Sums3 ui = src_mode ? pass_rows_init_df<B, W, true>(cref, c0, c1, xRef)
+                                : pass_rows_init_df<B, W, false>(cref, c0, c1, xRef);
+      double u[3] = {ui.a, ui.b, ui.c};
+      if (!team_allreduce<3>(tm, u, sh)) return false;
+      clk.lap(kPhInit);
+      const double nf = u[0] + kSmall * cs.df_scale;
+      const double init_res = u[1] / nf;
+      res = init_res;
+      double rho = u[2], beta = 0.0;
+      int iters = 0;
+      conv = converged(res, init_res, cs.tol, cs.rel_tol);
+      if (cs.min_iter > 0 || !conv) {
+        for (;;) {
+          if (iters > 0) {
+            pass_direction_df<B>(c0, c1, df_from_scalar(beta), p, w);
+            if (!team_barrier(tm, sh)) return false;
+            clk.lap(kPhP);
+          }
+          double s1[1] = {pass_amul_dot_df<B, W>(cs, c0, c1, p, q)};
+          if (!team_allreduce<1>(tm, s1, sh)) return false;
+          clk.lap(kPhM);
+          const double sigma = s1[0];
+          if (fabs(sigma) / nf < kVSmall) {
+            status = LFM_ESINGULAR;
+            break;
+          }
+          const double alpha = rho / sigma;
+          const double2 su = pass_update_df<B>(c0, c1, df_from_scalar(alpha), x, r, w, p, q, rD);
+          double s2[2] = {su.x, su.y};
+          if (!team_allreduce<2>(tm, s2, sh)) return false;
+          clk.lap(kPhU);
+          res = s2[0] / nf;
+          beta = s2[1] / rho;
+          rho = s2[1];
+          ++iters;
+          if (!isfinite(res)) {
+            status = LFM_ENONFINITE;
+            break;
+          }
+          conv = converged(res, init_res, cs.tol, cs.rel_tol);
+          if (!((iters < cs.max_iter && !conv) || iters < cs.min_iter)) break;
+        }
+      }
+      conv = converged(res, init_res, cs.tol, cs.rel_tol);
+      if (pass == 0) {
+        nf0 = nf * inv_scale;
+        init0 = init_res;
+      }
+      iters_tot += iters;
+      solves += iters > 0 ? 1 : 0;
+      if (status != 0) break;
+    }
+    write_stats(cs, tm, stats_base + step, iters_tot, conv ? 1 : 0, solves, status, init0, res, nf0);
+    if (status != 0) {
+      if (tm.rank == 0 && tid == 0) set_status(cs.sync, status);
+      return true;
+    }
+  }
+  return true;
+}
+
+template <int B, int W>
+__device__ void run_steps_df64(const CaseDev& cs, const CaseDev& cref, const Team& tm, int n_steps, TeamShared& sh,
+                               int stats_base = 0) {
+  if (n_steps <= 0) return;
+  int c0, c1;
+  cta_range(cs.N, tm.size, tm.rank, c0, c1);
+  steps_df64<B, W>(cs, cref, tm, n_steps, sh, stats_base, c0, c1);
+  // x2 of the CTA's own cells is written by this CTA only (U pass), so the FP64 field can
+  // be written back without another barrier, also after an early exit.
+  pass_store_x<B>(cref, c0, c1);
+}
+
+}  // namespace
+}  // namespace lfm

@@ -5,6 +5,7 @@
 #include "lfm_device.cuh"
 #include "lfm_internal.h"
 #include "lfm_solve.cuh"
+#include "lfm_solve_df.cuh"
 
 namespace lfm {
 namespace {
@@ -30,6 +31,36 @@ __global__ void __launch_bounds__(B, 1024 / B) step_kernel_mixed(CaseDev cs, Lau
   __syncthreads();
   const Team tm{(int)gridDim.x, (int)blockIdx.x, cs.sync, cs.partials, L.timeout_ns};
   run_steps_mixed<B, W>(cs, s_cs, tm, n_steps, mode, sh);
+}
+
+template <int B, int W>
+__global__ void __launch_bounds__(B, 1024 / B) step_kernel_df64(CaseDev cs, Launch L, int n_steps, int mode) {
+  __shared__ TeamShared sh;
+  __shared__ CaseDev s_cs;  // addressable copy for the per-step passes
+  if ((int)blockIdx.x == L.skip_cta) return;
+  if (threadIdx.x == 0) s_cs = cs;
+  __syncthreads();
+  const Team tm{(int)gridDim.x, (int)blockIdx.x, cs.sync, cs.partials, L.timeout_ns};
+  run_steps_df64<B, W>(cs, s_cs, tm, n_steps, sh);
+}
+
+// df64 set-up (a0): per face g = (DT |Sf|) deltaCoeff in FP64 (the FP64 assembly's order)
+// times the case scale, split into a double-float pair and stored at the face's slot in
+// its owner's and its neighbour's row (padding slots are cleared before).
+__global__ void df_coef_kernel(CaseDev cs, float2* __restrict__ g2) {
+  const int f = blockIdx.x * blockDim.x + threadIdx.x;
+  if (f >= cs.F) return;
+  const uint2 at = reinterpret_cast<const uint2*>(cs.face_slots)[f];
+  const double DTf = cs.DT_is_uniform ? cs.DT_uniform : cs.DT[f];
+  const double g = __dmul_rn(__dmul_rn(__dmul_rn(DTf, cs.magSf[f]), cs.delta[f]), cs.df_scale);
+  const df v = df_from_double(g);
+  st_df(g2 + at.x, v);
+  st_df(g2 + at.y, v);
+}
+
+__global__ void df_vdt_kernel(CaseDev cs, float2* __restrict__ vdt2) {
+  const int c = blockIdx.x * blockDim.x + threadIdx.x;
+  if (c < cs.N) st_df(vdt2 + c, df_from_double(__dmul_rn(cs.vdt[c], cs.df_scale)));
 }
 
 __global__ void boundary_values_kernel(CaseDev cs, double* Tb) {
@@ -184,8 +215,14 @@ __global__ void fill_kernel(double* a, size_t n, double v) {
 
 template <int B>
 void* step_fn_w(int precision, int W) {
-  if (W == 6) return precision == LFM_MIXED ? (void*)step_kernel_mixed<B, 6> : (void*)step_kernel_f64<B, 6>;
-  return precision == LFM_MIXED ? (void*)step_kernel_mixed<B, 0> : (void*)step_kernel_f64<B, 0>;
+  if (W == 6) {
+    if (precision == LFM_MIXED) return (void*)step_kernel_mixed<B, 6>;
+    if (precision == LFM_DF64) return (void*)step_kernel_df64<B, 6>;
+    return (void*)step_kernel_f64<B, 6>;
+  }
+  if (precision == LFM_MIXED) return (void*)step_kernel_mixed<B, 0>;
+  if (precision == LFM_DF64) return (void*)step_kernel_df64<B, 0>;
+  return (void*)step_kernel_f64<B, 0>;
 }
 
 void* step_fn_for(int precision, int threads, int W) {
@@ -211,13 +248,29 @@ int max_coresident_ctas(int precision, int threads, int W, int device) {
 
 cudaError_t launch_steps(const CaseDev& cs, const Launch& L, int n_steps, int mode,
                          cudaStream_t stream) {
-  void* fn = step_fn_for(cs.precision, L.threads, cs.W);
+  // matrix read-back of a df64 case runs the FP64 assembly (its arrays are the ones read)
+  const int prec = (mode == kModeAssembleOnly && cs.precision == LFM_DF64) ? LFM_FP64 : cs.precision;
+  void* fn = step_fn_for(prec, L.threads, cs.W);
   if (!fn) return cudaErrorInvalidValue;
   CaseDev a0 = cs;
+  a0.precision = prec;
   Launch a1 = L;
   int a2 = n_steps, a3 = mode;
   void* args[] = {&a0, &a1, &a2, &a3};
   return cudaLaunchCooperativeKernel(fn, dim3(L.ctas), dim3(L.threads), args, 0, stream);
+}
+
+cudaError_t launch_df_setup(const CaseDev& cs, cudaStream_t stream) {
+  if (!cs.g2 || !cs.vdt2) return cudaErrorInvalidValue;
+  float2* g2 = const_cast<float2*>(cs.g2);
+  const size_t WN = (size_t)cs.W * cs.N;
+  if (WN > 0) {
+    cudaError_t e = cudaMemsetAsync(g2, 0, sizeof(float2) * WN, stream);
+    if (e != cudaSuccess) return e;
+  }
+  if (cs.F > 0) df_coef_kernel<<<(cs.F + 255) / 256, 256, 0, stream>>>(cs, g2);
+  df_vdt_kernel<<<(cs.N + 255) / 256, 256, 0, stream>>>(cs, const_cast<float2*>(cs.vdt2));
+  return cudaGetLastError();
 }
 
 cudaError_t launch_geom_ops(const CaseDev& cs, bool with_E, cudaStream_t stream) {

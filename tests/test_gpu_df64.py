@@ -1,0 +1,231 @@
+"""The df64 form (double-float arithmetic on the FP32 pipe) against the FP64 CPU oracle
+(GPU required).
+
+Bar, as for FP64: max |T_gpu - T_oracle| / |T_oracle| <= 1e-10 after every run and PCG
+iteration counts equal to the oracle's on every step. The df64 form keeps 48 significand
+bits instead of 53, so it is rounding-level close to FP64 (~1e-13 relative on these cases),
+not bitwise; its reported normFactor and initial residual agree with the oracle's to 1e-8.
+"""
+import functools
+
+import numpy as np
+import pytest
+
+import lapcase
+import oracle
+from paper_2507_18268_gb300 import Solver
+from paper_2507_18268_gb300 import binding as B
+from paper_2507_18268_gb300.batch import Batch
+
+from test_gpu_parity import CASES, oracle_run, relerr
+
+pytestmark = pytest.mark.gpu
+
+RTOL = 1e-10
+
+
+def df_run(case, n_steps=None, ctas=0, threads=0, layout=B.LFM_BOTH):
+    s = Solver.from_case(case, layout=layout)
+    try:
+        s.set_solver(case.tol, case.rel_tol, case.max_iter, case.min_iter, B.LFM_DF64)
+        if ctas or threads:
+            s.set_launch(ctas, threads)
+        st = s.advance(case.n_steps if n_steps is None else n_steps)
+        T = s.field()
+        launch = s.launch()
+    finally:
+        s.close()
+    return T, st, launch
+
+
+def assert_df_parity(T, st, To, so):
+    assert len(st) == len(so)
+    for k, (g, o) in enumerate(zip(st, so)):
+        assert g["iters"] == o.iters, (k, g, o)
+        assert bool(g["converged"]) == o.converged
+        assert g["status"] == 0
+        assert abs(g["norm_factor"] - o.norm_factor) <= 1e-8 * o.norm_factor
+        assert abs(g["init_res"] - o.init_res) <= 1e-8 * o.init_res + 1e-300
+    assert relerr(T, To) <= RTOL
+
+
+@pytest.mark.parametrize("name", ["plain20", "plain7", "permuted20", "graded40", "ragged",
+                                  "small_perm_graded", "line", "one_cell", "insulated"])
+def test_df64_parity(name):
+    T, st, _ = df_run(CASES[name]())
+    To, so = oracle_run(name)
+    assert_df_parity(T, st, To, so)
+
+
+def test_df64_parity_permuted_100cubed_full():
+    T, st, launch = df_run(CASES["permuted100"]())
+    assert launch[0] > 1
+    To, so = oracle_run("permuted100")
+    assert_df_parity(T, st, To, so)
+
+
+def test_graded200_full_size_all_forms():
+    # the bench's workload at full size (200^3 graded box, 8 M cells), two steps, default
+    # launch shape, every cell against the oracle: FP64 and df64 to 1e-10 with the oracle's
+    # iteration counts, mixed to 1e-5
+    case = lapcase.graded_box(200, n_steps=2)
+    To, so = oracle.advance(case)
+    for prec in (B.LFM_FP64, B.LFM_DF64, B.LFM_MIXED):
+        with Solver.from_case(case.with_(precision=prec)) as s:
+            st = s.advance(case.n_steps)
+            T = s.field()
+            assert s.launch()[0] >= 152
+        if prec == B.LFM_MIXED:
+            assert relerr(T, To) <= 1e-5
+        else:
+            assert_df_parity(T, st, To, so)
+
+
+@functools.lru_cache(maxsize=None)
+def _graded_oracle(n):
+    return oracle.advance(lapcase.graded_box(n, n_steps=100))
+
+
+@pytest.mark.parametrize("prec", [B.LFM_FP64, B.LFM_DF64])
+@pytest.mark.parametrize("n", [40, 100])
+def test_long_run_parity(prec, n):
+    # 100 steps of the graded box's recipe: each step changes T by a small fraction, so the
+    # initial residual is a small difference (see the flux form of the df64 row pass)
+    case = lapcase.graded_box(n, n_steps=100)
+    To, so = _graded_oracle(n)
+    with Solver.from_case(case.with_(precision=prec)) as s:
+        st = s.advance(case.n_steps)
+        T = s.field()
+    assert_df_parity(T, st, To, so)
+
+
+@pytest.mark.parametrize("ctas,threads", [(1, 256), (1, 1024), (3, 256), (7, 512), (64, 256), (10000, 512)])
+def test_df64_launch_shapes(ctas, threads):
+    T, st, launch = df_run(CASES["permuted20"](), ctas=ctas, threads=threads)
+    assert launch[1] == threads
+    To, so = oracle_run("permuted20")
+    assert_df_parity(T, st, To, so)
+
+
+def test_df64_bitwise_deterministic():
+    case = CASES["permuted20"]()
+    T1, s1, _ = df_run(case, ctas=37, threads=256)
+    T2, s2, _ = df_run(case, ctas=37, threads=256)
+    assert np.array_equal(T1, T2)
+    assert s1 == s2
+
+
+def test_df64_only_workspace():
+    case = CASES["ragged"]()
+    T1, s1, _ = df_run(case, layout=B.LFM_DF64)
+    T2, s2, _ = df_run(case, layout=B.LFM_BOTH)
+    assert np.array_equal(T1, T2)
+    with Solver.from_case(case, layout=B.LFM_DF64) as s:
+        with pytest.raises(B.LfmError) as e:
+            s.set_solver(case.tol, 0.0, 1000, 0, B.LFM_MIXED)
+        assert e.value.code == B.LFM_ENOMEM
+    with Solver.from_case(case.with_(precision=lapcase.MIXED), layout=B.LFM_MIXED) as s:
+        with pytest.raises(B.LfmError) as e:
+            s.set_solver(case.tol, 0.0, 1000, 0, B.LFM_DF64)
+        assert e.value.code == B.LFM_ENOMEM
+
+
+def test_df64_zero_diffusivity_and_iteration_limits():
+    case = lapcase.plain_box(6).with_(DT_uniform=0.0, T0=np.linspace(250, 300, 216))
+    T, st, _ = df_run(case, n_steps=2)
+    To, so = oracle.advance(case, n_steps=2)
+    assert all(s["iters"] == 0 and s["converged"] for s in st)
+    assert relerr(T, To) <= 1e-14  # T passes through the 48-bit format once per launch
+    case = CASES["permuted20"]().with_(min_iter=5, n_steps=2)
+    T, st, _ = df_run(case)
+    To, so = oracle.advance(case)
+    assert [s["iters"] for s in st] == [s.iters for s in so]
+    assert relerr(T, To) <= RTOL
+    case = CASES["permuted20"]().with_(tol=1e-14, max_iter=3, n_steps=2)
+    T, st, _ = df_run(case)
+    To, so = oracle.advance(case)
+    assert [s["iters"] for s in st] == [3, 3] and not st[0]["converged"]
+    assert relerr(T, To) <= RTOL
+
+
+def test_df64_dt_change_and_precision_switch():
+    # the df64 conductances and V/dt are rebuilt after DT and dt change; switching to FP64 and
+    # back continues from the same field
+    case = CASES["permuted20"]().with_(n_steps=3)
+    c2 = case.with_(DT_uniform=2.5e-3, DTx=None, DTy=None, DTz=None, dt=0.02)
+    To, _ = oracle.advance(case)
+    To2, _ = oracle.advance(c2, n_steps=3, T=To)
+    with Solver.from_case(case) as s:
+        s.set_solver(case.tol, 0.0, 1000, 0, B.LFM_DF64)
+        s.advance(3)
+        assert relerr(s.field(), To) <= RTOL
+        B.lfm_set_diffusivity(s.ctx, 2.5e-3, None, None)
+        B.lfm_set_time_step(s.ctx, 0.02)
+        s.set_solver(case.tol, 0.0, 1000, 0, B.LFM_FP64)
+        s.advance(1)
+        s.set_solver(case.tol, 0.0, 1000, 0, B.LFM_DF64)
+        s.advance(2)
+        T = s.field()
+    assert relerr(T, To2) <= RTOL
+
+
+def test_df64_matrix_readback_is_the_fp64_assembly():
+    case = CASES["graded40"]()
+    with Solver.from_case(case) as s:
+        d0, u0, s0 = s.matrix()
+    with Solver.from_case(case) as s:
+        s.set_solver(case.tol, 0.0, 1000, 0, B.LFM_DF64)
+        s.advance(1)
+        s.set_field(oracle.initial_field(case))
+        d, u, src = s.matrix()
+    assert np.array_equal(d, d0) and np.array_equal(u, u0) and np.array_equal(src, s0)
+
+
+def test_df64_sources_and_correctors_on_orthogonal_mesh():
+    case = lapcase.random_small_case(33, nx=7, ny=6, nz=5, permute=False).with_(
+        Su=150.0, Sp=-0.3, tol=1e-10, n_steps=3)
+    To, so = oracle.advance(case)
+    T, st, _ = df_run(case)
+    assert relerr(T, To) <= RTOL
+    assert [s["iters"] for s in st] == [s.iters for s in so]
+    # extra passes on a box uploaded without geometry: zero correction, re-solves only
+    base = lapcase.random_small_case(10, nx=6, ny=6, nz=5, permute=False).with_(tol=1e-11, n_steps=3)
+    To, so = oracle.advance(base.with_(points=lapcase.box_points(base.xs, base.ys, base.zs), n_nonorth_corr=2))
+    with Solver.from_case(base) as s:
+        s.set_solver(base.tol, 0.0, 1000, 0, B.LFM_DF64)
+        B.lfm_set_nonorth_correctors(s.ctx, 2)
+        st = s.advance(base.n_steps)
+        T = s.field()
+    assert relerr(T, To) <= RTOL
+    assert [x["iters"] for x in st] == [x.iters for x in so]
+
+
+def test_df64_refused_for_general_geometry():
+    base = lapcase.random_small_case(3, nx=4, ny=4, nz=4, permute=False)
+    case = lapcase.perturbed_box(base, amp=0.2, seed=3)
+    with Solver.from_case(case) as s:
+        with pytest.raises(B.LfmError) as e:
+            s.set_solver(case.tol, 0.0, 1000, 0, B.LFM_DF64)
+        assert e.value.code == B.LFM_EINVAL
+
+
+def test_df64_batched_matches_alone_and_oracle():
+    n_steps = 4
+    cases = lapcase.batch_cases(n_cases=12, seed=21, n_min=5, n_max=30, n_steps=n_steps)
+    cases = [c.with_(precision=[lapcase.DF64, lapcase.FP64, lapcase.MIXED][i % 3]) for i, c in enumerate(cases)]
+    with Batch() as bt:
+        ids = [bt.add_case(c) for c in cases]
+        bt.set_launch(256, (1, 1, 1))  # several CTAs per case
+        assert bt.advance(n_steps) == B.LFM_OK
+        for cid, c in zip(ids, cases):
+            T = bt.field(cid)
+            st = bt.stats(cid, n_steps)
+            To, so = oracle.advance(c, n_steps=n_steps)
+            if c.precision == lapcase.MIXED:
+                assert relerr(T, To) <= 1e-5
+                continue
+            assert [x["iters"] for x in st] == [x.iters for x in so]
+            assert relerr(T, To) <= RTOL
+            if c.precision == lapcase.DF64:
+                Ta, sa, _ = df_run(c, n_steps=n_steps)
+                assert relerr(T, Ta) <= 1e-13
