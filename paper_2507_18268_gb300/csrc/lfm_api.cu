@@ -39,7 +39,7 @@ struct Layout {
   size_t diag, upper, slot_coef, src, rD, vdt, x, x_old, vSu, vSp, r, w, p, q, Tb;
   size_t Sf, fw, corr, bSf, gE, gD, gH, cK, cL, grad;  // general geometry (0 when absent)
   size_t diag32, slot_coef32, rD32, dx32, r32, w32, p32, q32;
-  size_t x2, diag2, rD2, vdt2, g2;  // df64 form (0 when absent)
+  size_t x2, xlo, xolo, diag2, rD2, vdt2, g2;  // df64 form (0 when absent)
   size_t total;
 };
 
@@ -114,7 +114,7 @@ Layout make_layout(int64_t N, int64_t F, int64_t NB, int64_t W, int kind, bool s
   L.Tb = take(8 * NB);
   L.r = L.w = L.p = L.q = 0;
   L.diag32 = L.slot_coef32 = L.rD32 = L.dx32 = L.r32 = L.w32 = L.p32 = L.q32 = 0;
-  L.x2 = L.diag2 = L.rD2 = L.vdt2 = L.g2 = 0;
+  L.x2 = L.xlo = L.xolo = L.diag2 = L.rD2 = L.vdt2 = L.g2 = 0;
   if (kind_has64(kind)) {
     L.r = take(8 * N);
     L.w = take(8 * N);
@@ -123,6 +123,8 @@ Layout make_layout(int64_t N, int64_t F, int64_t NB, int64_t W, int kind, bool s
   }
   if (kind_hasdf(kind)) {
     L.x2 = take(8 * N);
+    L.xlo = take(4 * N);
+    L.xolo = take(4 * N);
     L.diag2 = take(8 * N);
     L.rD2 = take(8 * N);
     L.vdt2 = take(8 * N);
@@ -184,6 +186,7 @@ struct lfm_ctx {
   bool has64 = false, has32 = false;  // solver blocks present in the workspace
   bool hasdf = false;                 // df64 block present
   bool df_dirty = true;               // df64 conductances / V/dt to rebuild before the next df64 launch
+  bool coef_dirty = true;             // FP64 / FP32 slot coefficients to rebuild before the next launch
   double mean_V = 1.0;                // mean cell volume (sets the df64 scale with dt)
   bool has_geom = false;              // general geometry uploaded (corrected laplacian)
   bool ops_dirty = false;             // operator weights to rebuild before the next launch
@@ -471,6 +474,8 @@ void bind_pointers(lfm_ctx* c) {
   cs.q32 = m ? reinterpret_cast<float*>(b + L.q32) : nullptr;
   const bool f = c->hasdf;
   cs.x2 = f ? reinterpret_cast<float2*>(b + L.x2) : nullptr;
+  cs.xlo = f ? reinterpret_cast<float*>(b + L.xlo) : nullptr;
+  cs.xolo = f ? reinterpret_cast<float*>(b + L.xolo) : nullptr;
   cs.diag2 = f ? reinterpret_cast<float2*>(b + L.diag2) : nullptr;
   cs.rD2 = f ? reinterpret_cast<float2*>(b + L.rD2) : nullptr;
   cs.vdt2 = f ? reinterpret_cast<const float2*>(b + L.vdt2) : nullptr;
@@ -486,6 +491,16 @@ int refresh_vdt(lfm_ctx* c) {
   CK(c, cudaStreamSynchronize(c->stream));
   c->cs.df_scale = df_scale_for(c->mean_V, c->dt);
   c->df_dirty = true;
+  return LFM_OK;
+}
+
+// Rebuilds the face coefficients of the slot arrays (a0) when the mesh or DT changed since
+// they were built (the df64 form keeps its own, see refresh_df).
+int refresh_coef(lfm_ctx* c) {
+  if (!c->coef_dirty || c->opts.precision == LFM_DF64) return LFM_OK;
+  CK(c, launch_coef_setup(c->cs, c->stream));
+  CK(c, cudaStreamSynchronize(c->stream));
+  c->coef_dirty = false;
   return LFM_OK;
 }
 
@@ -522,8 +537,10 @@ int need_uploaded(lfm_ctx* c) {
 int enqueue_chunk(lfm_ctx* c, int steps, int mode) {
   refresh_case(c);
   if (int rc = refresh_ops(c)) return rc;
-  if (mode == kModeSteps)
+  if (mode == kModeSteps) {
+    if (int rc = refresh_coef(c)) return rc;
     if (int rc = refresh_df(c)) return rc;
+  }
   int e = 0;
   Launch L = current_launch(c, e);
   if (e) return fail(c, LFM_ECUDA, "no co-resident CTA fits the step kernel");
@@ -680,6 +697,7 @@ static int upload_mesh_impl(lfm_ctx* c, const lfm_mesh* m, const lfm_geometry* g
   c->has32 = has32;
   c->hasdf = hasdf;
   c->df_dirty = true;
+  c->coef_dirty = true;
   c->has_geom = geo != nullptr;
   c->n_corr = 0;
   c->has_Su = c->has_Sp = false;
@@ -846,6 +864,7 @@ int lfm_upload_box(lfm_ctx* c, int32_t nx, int32_t ny, int32_t nz, const double*
   c->has32 = has32;
   c->hasdf = hasdf;
   c->df_dirty = true;
+  c->coef_dirty = true;
   c->has_geom = false;
   c->n_corr = 0;
   c->has_Su = c->has_Sp = false;
@@ -933,6 +952,7 @@ int lfm_upload_mesh_shared(lfm_ctx* c, lfm_ctx* src) {
   c->has32 = has32;
   c->hasdf = hasdf;
   c->df_dirty = true;
+  c->coef_dirty = true;
   c->has_geom = root->has_geom;
   c->ops_dirty = root->has_geom;
   c->n_corr = 0;
@@ -1002,6 +1022,7 @@ int lfm_set_diffusivity(lfm_ctx* c, double uniform, const double* DT_faces, cons
   CK(c, cudaStreamSynchronize(c->stream));
   c->ops_dirty = true;
   c->df_dirty = true;
+  c->coef_dirty = true;
   return LFM_OK;
 }
 
@@ -1032,6 +1053,7 @@ int lfm_set_diffusivity_cells(lfm_ctx* c, const double* DT_cells, const double* 
   c->cs.DT_is_uniform = 0;
   c->ops_dirty = true;
   c->df_dirty = true;
+  c->coef_dirty = true;
   return LFM_OK;
 }
 
@@ -1598,7 +1620,8 @@ int lfm_batch_advance_async(lfm_batch* b, int32_t n_steps, int32_t use_graph) {
     if ((c->opts.precision == LFM_FP64 && !c->has64) || (c->opts.precision == LFM_MIXED && !c->has32) ||
         (c->opts.precision == LFM_DF64 && !c->hasdf))
       return bfail(b, LFM_ENOMEM, "case %d has no buffers for its precision", b->order[i]);
-    if (refresh_df(c) != LFM_OK) return bfail(b, LFM_ECUDA, "case %d: df64 set-up failed", b->order[i]);
+    if (refresh_coef(c) != LFM_OK || refresh_df(c) != LFM_OK)
+      return bfail(b, LFM_ECUDA, "case %d: coefficient set-up failed", b->order[i]);
     b->h_cases[i] = c->cs;
     if (c->W != 6) W = 0;
   }

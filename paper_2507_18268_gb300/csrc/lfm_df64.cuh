@@ -100,6 +100,60 @@ __device__ __forceinline__ df df_from_double(double d) {
 }
 __device__ __forceinline__ double df_to_double(df a) { return (double)a.hi + (double)a.lo; }
 
+// ---- triple-float: the field ------------------------------------------------------------
+// T itself is kept as hi + mid + lo (three FP32 numbers, ~72 significand bits): every flux
+// and every ddt term is a difference of two field values, formed exactly from the three
+// parts, so the field's rounding never enters the method at the 2^-48 level of df64 (it
+// would otherwise be injected every step at 2^-48 |T|, far above FP64's 2^-53 |T|).
+struct tf {
+  float hi, mid, lo;
+};
+
+__device__ __forceinline__ tf ld_tf(const float2* hm, const float* l, int c) {
+  const float2 v = hm[c];
+  return tf{v.x, v.y, l[c]};
+}
+__device__ __forceinline__ void st_tf(float2* hm, float* l, int c, tf v) {
+  hm[c] = make_float2(v.hi, v.mid);
+  l[c] = v.lo;
+}
+
+// x + d (d df64, |d| typically far below |x|): exact sums of the matching parts, then
+// renormalised so that each part is below half an ulp of the one before.
+__device__ __forceinline__ tf tf_add_df(tf a, df b) {
+  const df s0 = two_sum(a.hi, b.hi);
+  const df s1 = two_sum(a.mid, b.lo);
+  const df t = two_sum(s1.hi, s0.lo);
+  const float r2 = __fadd_rn(__fadd_rn(s1.lo, t.lo), a.lo);
+  const df u = two_sum(s0.hi, t.hi);
+  const df v = two_sum(u.lo, r2);
+  const df w = fast_two_sum(u.hi, v.hi);
+  return tf{w.hi, w.lo, v.lo};
+}
+
+// a - b as df64, for field values: the leading difference is exact (Sterbenz) when the two
+// are within a factor of two, and every rounding error is collected, so the difference
+// keeps df64's relative accuracy.
+__device__ __forceinline__ df tf_diff(tf a, tf b) {
+  const df s0 = two_sum(a.hi, -b.hi);
+  const df s1 = two_sum(a.mid, -b.mid);
+  const float s2 = __fsub_rn(a.lo, b.lo);
+  const df t = two_sum(s1.hi, s0.lo);
+  const df h = two_sum(s0.hi, t.hi);
+  const float l = __fadd_rn(h.lo, __fadd_rn(t.lo, __fadd_rn(s1.lo, s2)));
+  return fast_two_sum(h.hi, l);
+}
+
+__device__ __forceinline__ df tf_to_df(tf a) { return fast_two_sum(a.hi, a.mid); }
+
+__device__ __forceinline__ tf tf_from_double(double d) {
+  const float h = __double2float_rn(d);
+  const double r = d - (double)h;  // exact
+  const float m = __double2float_rn(r);
+  return tf{h, m, __double2float_rn(r - (double)m)};
+}
+__device__ __forceinline__ double tf_to_double(tf a) { return ((double)a.hi + (double)a.mid) + (double)a.lo; }
+
 // Per-thread running sum of df64 terms: the leading parts through TwoSum, their rounding
 // errors and the trailing parts collected in lo. Converted to FP64 once per thread; the
 // block and team reductions then run in FP64.

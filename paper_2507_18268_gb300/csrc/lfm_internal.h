@@ -119,10 +119,13 @@ struct CaseDev {
   float* p32;
   float* q32;
 
-  // df64 form (lfm_solve_df.cuh): the field, the diagonal and its reciprocal, V/dt and the
-  // per-slot face conductances as double-float pairs (hi, lo), all scaled by df_scale (a
-  // power of two); r, w, p, q and x_old are used as float2 arrays of the same size
-  float2* x2;                // [N]
+  // df64 form (lfm_solve_df.cuh): the diagonal and its reciprocal, V/dt and the per-slot
+  // face conductances as double-float pairs (hi, lo), all scaled by df_scale (a power of
+  // two), and the field as a triple-float; r, w, p, q and x_old are used as float2 arrays of
+  // the same size
+  float2* x2;                // [N]   field: leading and middle parts of a triple-float
+  float* xlo;                // [N]   field: trailing part
+  float* xolo;               // [N]   trailing part of x_old (x_old holds the other two)
   float2* diag2;             // [N]
   float2* rD2;               // [N]
   const float2* vdt2;        // [N]   V/dt * df_scale
@@ -179,6 +182,9 @@ cudaError_t launch_dt_cells(const CaseDev& cs, const double* DTc, const double* 
                             cudaStream_t stream);
 // out[c] = V[c] * a[c] (a null: out = 0).
 cudaError_t launch_times_volume(const CaseDev& cs, const double* a, double* out, cudaStream_t stream);
+// Set-up of the face coefficients: -DT |Sf| deltaCoeff at both slots of every face in the
+// FP64 slot array and, when present, the FP32 one.
+cudaError_t launch_coef_setup(const CaseDev& cs, cudaStream_t stream);
 // df64 form set-up: the per-slot conductances g2 and V/dt (vdt2), both times cs.df_scale.
 cudaError_t launch_df_setup(const CaseDev& cs, cudaStream_t stream);
 

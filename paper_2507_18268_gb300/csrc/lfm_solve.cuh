@@ -98,10 +98,12 @@ struct Acc2f {
   __device__ __forceinline__ double value() const { return (double)hi + (double)lo; }
 };
 
-// ---- assembly of fvm::ddt(T) - fvm::laplacian(DT, T), two passes ---------------------
-// Pass 1 (per face, in face order): g = (DT |Sf|) deltaCoeff, computed once per face and
-// stored as -g at the face's slot in its owner's row and in its neighbour's row. Faces are
-// read and the face-indexed LDU copy written with unit stride; two faces per loop trip.
+// ---- assembly of fvm::ddt(T) - fvm::laplacian(DT, T) ----------------------------------
+// Face part (per face, in face order): g = (DT |Sf|) deltaCoeff, computed once per face and
+// stored as -g at the face's slot in its owner's row and in its neighbour's row. It depends
+// on the mesh and DT only, so the set-up kernel (coef_kernel) forms it when those change
+// (the a0 step: precomputed face conductances); the step kernel repeats it only for matrix
+// read-back, where the face-indexed LDU copy is written too.
 template <bool kMixed>
 __device__ __forceinline__ void assemble_face(const CaseDev& cs, int f, bool write_upper) {
   const uint2 at = __ldg(reinterpret_cast<const uint2*>(cs.face_slots) + f);
@@ -273,24 +275,35 @@ __device__ __forceinline__ double store_row(const CaseDev& cs, int c, const Row&
 // functions of their own (__noinline__, taking an addressable copy of the case descriptor):
 // their register demand then does not shape the allocation of the iteration passes.
 
-// Pass 1 over the faces [f0, f1) of this CTA; returns this thread's sum of T over the cells
-// [c0, c1) (for xRef).
+// First phase of an assembly: this thread's sum of T over the cells [c0, c1) (for xRef).
+// The face coefficients are set-up data (written by the set-up kernel when the mesh or DT
+// change); with `faces` (matrix read-back) the faces [f0, f1) of this CTA are assembled here
+// as well, the face-indexed LDU copy included.
 // save_old: also keep T as the step's starting field (x_old) for the corrector passes.
 template <int B, bool kMixed>
-__device__ __noinline__ double pass_faces(const CaseDev& cs, int f0, int f1, int c0, int c1, bool write_upper,
+__device__ __noinline__ double pass_faces(const CaseDev& cs, int f0, int f1, int c0, int c1, bool faces,
                                           bool save_old) {
-  for (int f = f0 + (int)threadIdx.x; f < f1; f += B) assemble_face<kMixed>(cs, f, write_upper);
+  if (faces)
+    for (int f = f0 + (int)threadIdx.x; f < f1; f += B) assemble_face<kMixed>(cs, f, true);
   const double* __restrict__ x = cs.x;
   double v = 0.0;
+  int c = c0 + (int)threadIdx.x;
   if (save_old) {
     double* __restrict__ xo = cs.x_old;
-    for (int c = c0 + (int)threadIdx.x; c < c1; c += B) {
+    for (; c < c1; c += B) {
       const double xc = x[c];
       xo[c] = xc;
       v += xc;
     }
   } else {
-    for (int c = c0 + (int)threadIdx.x; c < c1; c += B) v += x[c];
+    for (; c + 3 * B < c1; c += 4 * B) {  // four cells per trip, loads first (fixed order)
+      const double a = x[c], b = x[c + B], d = x[c + 2 * B], e = x[c + 3 * B];
+      v += a;
+      v += b;
+      v += d;
+      v += e;
+    }
+    for (; c < c1; c += B) v += x[c];
   }
   return v;
 }

@@ -15,8 +15,14 @@
 // and df64 value exactly, and the scaled values keep far from FP32's underflow. Reported
 // normFactors are divided by s.
 //
-// Per launch: the field T (FP64, x) is split into df64 (x2) by the first pass and written
-// back to x after the last step. Per step (phases separated by team barriers):
+// Per launch: the field T (FP64, x) is split into a triple-float (x2 = hi, mid; xlo = lo;
+// see lfm_df64.cuh) by the first pass and written back to x after the last step. Fluxes and
+// ddt terms are differences of field values formed exactly from the three parts, and the
+// per-iteration update adds the df64 correction to all three, so rounding at df64's 2^-48 is
+// relative to corrections and differences, never to T itself. (A per-step rounding of T to
+// 48 bits is a noise source that truncated-CG time stepping amplifies from step to step:
+// on the 200^3 graded box it grew to 7e-10 relative over 100 steps.)
+// Per step (phases separated by team barriers):
 //   S  sum of x (for xRef); with correctors also x at the start of the step
 //   R  per row: diag = sum of the slot conductances (slot order) + boundary + V/dt, the
 //      source, 1/diag (FP32 reciprocal + one df64 Newton step), the row sum; r = b - A x
@@ -44,54 +50,55 @@ namespace {
 __device__ __forceinline__ df df_from_scalar(double v) { return df_from_double(v); }
 
 // S: this thread's sum of x over [c0, c1) (per-thread df64 sum, converted once). `convert`:
-// first pass of the launch, x2 is split from the FP64 field x. `save_old`: keep x as the
-// step's starting field (the ddt source of the corrector passes).
+// first pass of the launch, the triple-float field is split from the FP64 field x.
+// `save_old`: keep x as the step's starting field (the ddt source of the corrector passes).
 template <int B>
 __device__ __noinline__ double pass_sum_df(const CaseDev& cs, int c0, int c1, bool convert, bool save_old) {
   float2* __restrict__ x2 = cs.x2;
-  float2* __restrict__ xo2 = reinterpret_cast<float2*>(cs.x_old);
+  float* __restrict__ xl = cs.xlo;
   DfAcc acc;
   int c = c0 + (int)threadIdx.x;
   if (!convert && !save_old) {  // the common case: four cells per trip, loads first
     for (; c + 3 * B < c1; c += 4 * B) {
-      const df a = ld_df(x2 + c), b = ld_df(x2 + c + B), d = ld_df(x2 + c + 2 * B), e = ld_df(x2 + c + 3 * B);
-      acc.add(a);
-      acc.add(b);
-      acc.add(d);
-      acc.add(e);
+      const float2 a = x2[c], b = x2[c + B], d = x2[c + 2 * B], e = x2[c + 3 * B];
+      acc.add(fast_two_sum(a.x, a.y));
+      acc.add(fast_two_sum(b.x, b.y));
+      acc.add(fast_two_sum(d.x, d.y));
+      acc.add(fast_two_sum(e.x, e.y));
     }
   }
   for (; c < c1; c += B) {
-    df v;
+    tf v;
     if (convert) {
-      v = df_from_double(cs.x[c]);
-      st_df(x2 + c, v);
+      v = tf_from_double(cs.x[c]);
+      st_tf(x2, xl, c, v);
     } else {
-      v = ld_df(x2 + c);
+      v = ld_tf(x2, xl, c);
     }
-    if (save_old) st_df(xo2 + c, v);
-    acc.add(v);
+    if (save_old) st_tf(reinterpret_cast<float2*>(cs.x_old), cs.xolo, c, v);
+    acc.add(tf_to_df(v));
   }
   return acc.value();
 }
 
-// The FP64 field from the df64 one (end of the launch; each CTA its own cells).
+// The FP64 field from the triple-float one (end of the launch; each CTA its own cells).
 template <int B>
 __device__ __noinline__ void pass_store_x(const CaseDev& cs, int c0, int c1) {
   const float2* __restrict__ x2 = cs.x2;
+  const float* __restrict__ xl = cs.xlo;
   double* __restrict__ x = cs.x;
-  for (int c = c0 + (int)threadIdx.x; c < c1; c += B) x[c] = df_to_double(ld_df(x2 + c));
+  for (int c = c0 + (int)threadIdx.x; c < c1; c += B) x[c] = tf_to_double(ld_tf(x2, xl, c));
 }
 
 // Boundary conductance, source and flux g_b (T_b - x_c) of row c (fixedValue faces;
 // zeroGradient adds nothing), in FP64 with the case scale, in ascending face order.
-__device__ __forceinline__ void row_boundary_df(const CaseDev& cs, int c, df xc, df& gsum, df& ssum, df& flux) {
+__device__ __forceinline__ void row_boundary_df(const CaseDev& cs, int c, tf xc, df& gsum, df& ssum, df& flux) {
   const int b0 = __ldg(cs.b_start + c), b1 = __ldg(cs.b_start + c + 1);
   gsum = mkdf(0.0f, 0.0f);
   ssum = mkdf(0.0f, 0.0f);
   flux = mkdf(0.0f, 0.0f);
   if (b0 == b1) return;
-  const double x = df_to_double(xc);
+  const double x = tf_to_double(xc);
   double g = 0.0, s = 0.0, fl = 0.0;
   for (int k = b0; k < b1; ++k) {
     const int bf = __ldg(cs.b_face + k);
@@ -122,6 +129,7 @@ __device__ __forceinline__ void row_boundary_df(const CaseDev& cs, int c, df xc,
 template <int B, int W, bool kSrc>
 __device__ __noinline__ Sums3 pass_rows_init_df(const CaseDev& cs, int c0, int c1, double xRef) {
   const float2* __restrict__ x2 = cs.x2;
+  const float* __restrict__ xl = cs.xlo;
   const float2* __restrict__ g2 = cs.g2;
   float2* __restrict__ r2 = reinterpret_cast<float2*>(cs.r);
   float2* __restrict__ p2 = reinterpret_cast<float2*>(cs.p);
@@ -129,7 +137,7 @@ __device__ __noinline__ Sums3 pass_rows_init_df(const CaseDev& cs, int c0, int c
   const df xr = df_from_scalar(xRef);
   DfAcc a_nf, a_r, a_rho;
   for (int c = c0 + (int)threadIdx.x; c < c1; c += B) {
-    const df xc = ld_df(x2 + c);
+    const tf xc = ld_tf(x2, xl, c);
     df d, flux;
     if constexpr (W > 0) {
       int o[W];
@@ -139,15 +147,15 @@ __device__ __noinline__ Sums3 pass_rows_init_df(const CaseDev& cs, int c0, int c
         o[k] = __ldg(cs.slot_other + (size_t)k * N + c);
         g[k] = ldg_df(g2 + (size_t)k * N + c);
       }
-      df xo_[W];
+      tf xo_[W];
 #pragma unroll
-      for (int k = 0; k < W; ++k) xo_[k] = ld_df(x2 + o[k]);
+      for (int k = 0; k < W; ++k) xo_[k] = ld_tf(x2, xl, o[k]);
       d = g[0];
 #pragma unroll
       for (int k = 1; k < W; ++k) d = df_add(d, g[k]);  // padding slots hold 0
-      flux = df_mul(g[0], df_sub(xo_[0], xc));
+      flux = df_mul(g[0], tf_diff(xo_[0], xc));
 #pragma unroll
-      for (int k = 1; k < W; ++k) flux = df_fma(g[k], df_sub(xo_[k], xc), flux);
+      for (int k = 1; k < W; ++k) flux = df_fma(g[k], tf_diff(xo_[k], xc), flux);
     } else {
       d = mkdf(0.0f, 0.0f);
       flux = mkdf(0.0f, 0.0f);
@@ -155,29 +163,29 @@ __device__ __noinline__ Sums3 pass_rows_init_df(const CaseDev& cs, int c0, int c
         const size_t at = (size_t)k * N + c;
         const df gk = ldg_df(g2 + at);
         d = df_add(d, gk);
-        flux = df_fma(gk, df_sub(ld_df(x2 + __ldg(cs.slot_other + at)), xc), flux);
+        flux = df_fma(gk, tf_diff(ld_tf(x2, xl, __ldg(cs.slot_other + at)), xc), flux);
       }
     }
     df gb, sb, fb;
     row_boundary_df(cs, c, xc, gb, sb, fb);
     const df vdt = ldg_df(cs.vdt2 + c);
+    const df xcd = tf_to_df(xc);
     const bool has_old = kSrc && cs.n_corr > 0;
-    const df xo = has_old ? ld_df(reinterpret_cast<const float2*>(cs.x_old) + c) : xc;
+    const tf xo = has_old ? ld_tf(reinterpret_cast<const float2*>(cs.x_old), cs.xolo, c) : xc;
     d = df_add(df_add(d, gb), vdt);
-    df src = df_fma(vdt, xo, sb);
+    df src = df_fma(vdt, has_old ? tf_to_df(xo) : xcd, sb);
     df sa = df_add(vdt, gb);
     df rc = df_add(flux, fb);
-    if (has_old) rc = df_fma(vdt, df_sub(xo, xc), rc);
-    if (kSrc && cs.vSp) {
-      const df v = df_from_double(cs.vSp[c] * cs.df_scale);
-      d = df_sub(d, v);
-      sa = df_sub(sa, v);
-      rc = df_fma(v, xc, rc);
-    }
-    if (kSrc && cs.vSu) {
-      const df v = df_from_double(cs.vSu[c] * cs.df_scale);
-      src = df_add(src, v);
-      rc = df_add(rc, v);
+    if (has_old) rc = df_fma(vdt, tf_diff(xo, xc), rc);
+    if (kSrc && (cs.vSp || cs.vSu)) {
+      // the volumetric source V Su + V Sp T of the row's residual, in FP64 (proportional to T)
+      const double sp = cs.vSp ? cs.vSp[c] * cs.df_scale : 0.0;
+      const double su = cs.vSu ? cs.vSu[c] * cs.df_scale : 0.0;
+      const df vsp = df_from_double(sp);
+      d = df_sub(d, vsp);
+      sa = df_sub(sa, vsp);
+      src = df_add(src, df_from_double(su));
+      rc = df_add(rc, df_from_double(fma(sp, tf_to_double(xc), su)));
     }
     const df ax = df_sub(src, rc);
     const df rd = df_rcp(d);
@@ -281,24 +289,26 @@ __device__ __forceinline__ double pass_amul_dot_df(const CaseDev& cs, int c0, in
   return s.value();
 }
 
-// U: x += alpha p, r -= alpha q, w = rD r; returns this thread's sum|r| and w.r.
+// U: x += alpha p (x triple-float), r -= alpha q, w = rD r; returns this thread's sum|r|
+// and w.r.
 template <int B>
 __device__ __forceinline__ double2 pass_update_df(int c0, int c1, df alpha, float2* __restrict__ x,
-                                                  float2* __restrict__ r, float2* __restrict__ w,
-                                                  const float2* __restrict__ p, const float2* __restrict__ q,
-                                                  const float2* __restrict__ rD) {
+                                                  float* __restrict__ xl, float2* __restrict__ r,
+                                                  float2* __restrict__ w, const float2* __restrict__ p,
+                                                  const float2* __restrict__ q, const float2* __restrict__ rD) {
   DfAcc sa, sr;
   const df nalpha = df_neg(alpha);
   int c = c0 + (int)threadIdx.x;
   for (; c + B < c1; c += 2 * B) {
     const int e = c + B;
     const df pa = ld_df(p + c), pb = ld_df(p + e), qa = ld_df(q + c), qb = ld_df(q + e);
-    const df xa = ld_df(x + c), xb = ld_df(x + e), ra = ld_df(r + c), rb = ld_df(r + e);
+    const tf xa = ld_tf(x, xl, c), xb = ld_tf(x, xl, e);
+    const df ra = ld_df(r + c), rb = ld_df(r + e);
     const df da = ld_df(rD + c), db = ld_df(rD + e);
     const df rna = df_fma(nalpha, qa, ra), rnb = df_fma(nalpha, qb, rb);
     const df wa = df_mul(da, rna), wb = df_mul(db, rnb);
-    st_df(x + c, df_fma(alpha, pa, xa));
-    st_df(x + e, df_fma(alpha, pb, xb));
+    st_tf(x, xl, c, tf_add_df(xa, df_mul(alpha, pa)));
+    st_tf(x, xl, e, tf_add_df(xb, df_mul(alpha, pb)));
     st_df(r + c, rna);
     st_df(r + e, rnb);
     st_df(w + c, wa);
@@ -311,7 +321,7 @@ __device__ __forceinline__ double2 pass_update_df(int c0, int c1, df alpha, floa
   if (c < c1) {
     const df rn = df_fma(nalpha, ld_df(q + c), ld_df(r + c));
     const df wn = df_mul(ld_df(rD + c), rn);
-    st_df(x + c, df_fma(alpha, ld_df(p + c), ld_df(x + c)));
+    st_tf(x, xl, c, tf_add_df(ld_tf(x, xl, c), df_mul(alpha, ld_df(p + c))));
     st_df(r + c, rn);
     st_df(w + c, wn);
     sa.add(df_abs(rn));
@@ -373,7 +383,7 @@ __device__ bool steps_df64(const CaseDev& cs, const CaseDev& cref, const Team& t
             break;
           }
           const double alpha = rho / sigma;
-          const double2 su = pass_update_df<B>(c0, c1, df_from_scalar(alpha), x, r, w, p, q, rD);
+          const double2 su = pass_update_df<B>(c0, c1, df_from_scalar(alpha), x, cs.xlo, r, w, p, q, rD);
           double s2[2] = {su.x, su.y};
           if (!team_allreduce<2>(tm, s2, sh)) return false;
           clk.lap(kPhU);
@@ -414,7 +424,7 @@ __device__ void run_steps_df64(const CaseDev& cs, const CaseDev& cref, const Tea
   int c0, c1;
   cta_range(cs.N, tm.size, tm.rank, c0, c1);
   steps_df64<B, W>(cs, cref, tm, n_steps, sh, stats_base, c0, c1);
-  // x2 of the CTA's own cells is written by this CTA only (U pass), so the FP64 field can
+  // the field of the CTA's own cells is written by this CTA only (U pass), so the FP64 field can
   // be written back without another barrier, also after an early exit.
   pass_store_x<B>(cref, c0, c1);
 }

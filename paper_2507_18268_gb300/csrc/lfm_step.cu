@@ -44,6 +44,24 @@ __global__ void __launch_bounds__(B, 1024 / B) step_kernel_df64(CaseDev cs, Laun
   run_steps_df64<B, W>(cs, s_cs, tm, n_steps, sh);
 }
 
+// Set-up (a0): per face g = (DT |Sf|) deltaCoeff (the assembly's products, in its order),
+// stored as -g at the face's slot in its owner's and its neighbour's row of the FP64 (and,
+// present, FP32) slot arrays. Padding slots keep the zero written at upload.
+__global__ void coef_kernel(CaseDev cs) {
+  const int f = blockIdx.x * blockDim.x + threadIdx.x;
+  if (f < cs.F) {
+    const uint2 at = reinterpret_cast<const uint2*>(cs.face_slots)[f];
+    const double DTf = cs.DT_is_uniform ? cs.DT_uniform : cs.DT[f];
+    const double g = __dmul_rn(__dmul_rn(DTf, cs.magSf[f]), cs.delta[f]);
+    cs.slot_coef[at.x] = -g;
+    cs.slot_coef[at.y] = -g;
+    if (cs.slot_coef32) {
+      cs.slot_coef32[at.x] = (float)(-g);
+      cs.slot_coef32[at.y] = (float)(-g);
+    }
+  }
+}
+
 // df64 set-up (a0): per face g = (DT |Sf|) deltaCoeff in FP64 (the FP64 assembly's order)
 // times the case scale, split into a double-float pair and stored at the face's slot in
 // its owner's and its neighbour's row (padding slots are cleared before).
@@ -258,6 +276,11 @@ cudaError_t launch_steps(const CaseDev& cs, const Launch& L, int n_steps, int mo
   int a2 = n_steps, a3 = mode;
   void* args[] = {&a0, &a1, &a2, &a3};
   return cudaLaunchCooperativeKernel(fn, dim3(L.ctas), dim3(L.threads), args, 0, stream);
+}
+
+cudaError_t launch_coef_setup(const CaseDev& cs, cudaStream_t stream) {
+  if (cs.F > 0) coef_kernel<<<(cs.F + 255) / 256, 256, 0, stream>>>(cs);
+  return cudaGetLastError();
 }
 
 cudaError_t launch_df_setup(const CaseDev& cs, cudaStream_t stream) {
