@@ -40,14 +40,19 @@ UNIT = "cell-iterations/s"
 WORKLOAD = ("graded200: 200^3 unit box graded 1.02x per cell in x (8.0M cells, 23.88M internal "
             "faces), DT=4e-5, dt=0.005, x0=373 K / x1=273 K fixedValue, zeroGradient elsewhere, "
             "T0=273 K, diagonal PCG tol 1e-6 relTol 0")
-KERNEL_SOURCES = ["paper_2507_18268_gb300/csrc/lfm_step.cu", "paper_2507_18268_gb300/csrc/lfm_solve.cuh",
-                  "paper_2507_18268_gb300/csrc/lfm_device.cuh", "paper_2507_18268_gb300/csrc/lfm_internal.h"]
+# Sources of each step kernel's arithmetic and memory traffic: a stored ncu traffic ratio is
+# used only while these are unchanged since the capture.
+KERNEL_SOURCES = {
+    "fp64": ["csrc/lfm_solve.cuh", "csrc/lfm_device.cuh", "csrc/lfm_internal.h"],
+    "df64": ["csrc/lfm_solve_df.cuh", "csrc/lfm_df64.cuh", "csrc/lfm_solve.cuh", "csrc/lfm_device.cuh",
+             "csrc/lfm_internal.h"],
+}
 
 
-def kernel_hash() -> str:
+def kernel_hash(family: str = "fp64") -> str:
     h = hashlib.sha256()
-    for p in KERNEL_SOURCES:
-        with open(os.path.join(ROOT, p), "rb") as f:
+    for p in KERNEL_SOURCES[family]:
+        with open(os.path.join(ROOT, "paper_2507_18268_gb300", p), "rb") as f:
             h.update(f.read())
     return h.hexdigest()[:16]
 
@@ -97,7 +102,7 @@ def load_traffic_ratio(name: str):
         return None
     with open(p) as f:
         d = json.load(f)
-    if d.get("kernel_hash") != kernel_hash():
+    if d.get("kernel_hash") != kernel_hash("df64" if "df64" in name else "fp64"):
         return None
     return float(d["dram_bytes"]) / float(d["algorithmic_bytes"])
 
