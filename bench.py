@@ -544,7 +544,7 @@ def _cases_with_meshes(cases):
 
 def main_batch(args, world, rank, local):
     """batch512: 512 independent cases (edge log-uniform 16..96), 10 steps each, in one
-    persistent launch per step (graph replay), FP64 and mixed, against the plain FP64
+    persistent launch per step (graph replay), FP64, df64 and mixed, against the plain FP64
     single-case path run case after case."""
     import torch
 
@@ -559,7 +559,7 @@ def main_batch(args, world, rank, local):
     stream = torch.cuda.Stream(device=local)
     results = {}
     fields = {}
-    for prec, name in ((B.LFM_FP64, "fp64"), (B.LFM_MIXED, "mixed")):
+    for prec, name in ((B.LFM_FP64, "fp64"), (B.LFM_DF64, "df64"), (B.LFM_MIXED, "mixed")):
         cases = [c.with_(precision=prec) for c in base_cases]
         bt = Batch(device=local, stream=stream)
         ids = [bt.add_case(c, mesh=m) for c, m in _cases_with_meshes(cases)]
@@ -621,9 +621,10 @@ def main_batch(args, world, rank, local):
             "config": {"workload": f"batch{n_cases}: {n_cases} cases, edge log-uniform 16..96 (seed 3), "
                                    f"{total_cells} cells in total, {steps} steps each, graph-replayed step",
                        "parallelism": "single GPU"},
-            "batched_fp64": results["fp64"], "batched_mixed": results["mixed"],
+            "batched_fp64": results["fp64"], "batched_df64": results["df64"], "batched_mixed": results["mixed"],
             "plain_fp64_sequential": results["plain_fp64_sequential"],
             "speedup_batched_fp64_vs_plain": results["fp64"]["value"] / results["plain_fp64_sequential"]["value"],
+            "speedup_batched_df64_vs_plain": results["df64"]["value"] / results["plain_fp64_sequential"]["value"],
             "speedup_batched_mixed_vs_plain": results["mixed"]["value"] / results["plain_fp64_sequential"]["value"]}
     print(json.dumps(line), flush=True)
 
