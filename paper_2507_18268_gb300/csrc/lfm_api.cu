@@ -39,7 +39,7 @@ struct Layout {
   size_t diag, upper, slot_coef, src, rD, vdt, x, x_old, vSu, vSp, r, w, p, q, Tb;
   size_t Sf, fw, corr, bSf, gE, gD, gH, cK, cL, grad;  // general geometry (0 when absent)
   size_t diag32, slot_coef32, rD32, dx32, r32, w32, p32, q32;
-  size_t x2, xlo, xolo, diag2, rD2, vdt2, g2;  // df64 form (0 when absent)
+  size_t x2, xlo, xolo, e2, diag2, rD2, vdt2, g2;  // df64 form (0 when absent)
   size_t total;
 };
 
@@ -114,7 +114,7 @@ Layout make_layout(int64_t N, int64_t F, int64_t NB, int64_t W, int kind, bool s
   L.Tb = take(8 * NB);
   L.r = L.w = L.p = L.q = 0;
   L.diag32 = L.slot_coef32 = L.rD32 = L.dx32 = L.r32 = L.w32 = L.p32 = L.q32 = 0;
-  L.x2 = L.xlo = L.xolo = L.diag2 = L.rD2 = L.vdt2 = L.g2 = 0;
+  L.x2 = L.xlo = L.xolo = L.e2 = L.diag2 = L.rD2 = L.vdt2 = L.g2 = 0;
   if (kind_has64(kind)) {
     L.r = take(8 * N);
     L.w = take(8 * N);
@@ -125,6 +125,7 @@ Layout make_layout(int64_t N, int64_t F, int64_t NB, int64_t W, int kind, bool s
     L.x2 = take(8 * N);
     L.xlo = take(4 * N);
     L.xolo = take(4 * N);
+    L.e2 = take(8 * N);
     L.diag2 = take(8 * N);
     L.rD2 = take(8 * N);
     L.vdt2 = take(8 * N);
@@ -476,6 +477,7 @@ void bind_pointers(lfm_ctx* c) {
   cs.x2 = f ? reinterpret_cast<float2*>(b + L.x2) : nullptr;
   cs.xlo = f ? reinterpret_cast<float*>(b + L.xlo) : nullptr;
   cs.xolo = f ? reinterpret_cast<float*>(b + L.xolo) : nullptr;
+  cs.e2 = f ? reinterpret_cast<float2*>(b + L.e2) : nullptr;
   cs.diag2 = f ? reinterpret_cast<float2*>(b + L.diag2) : nullptr;
   cs.rD2 = f ? reinterpret_cast<float2*>(b + L.rD2) : nullptr;
   cs.vdt2 = f ? reinterpret_cast<const float2*>(b + L.vdt2) : nullptr;

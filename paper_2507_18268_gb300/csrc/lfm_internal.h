@@ -126,6 +126,7 @@ struct CaseDev {
   float2* x2;                // [N]   field: leading and middle parts of a triple-float
   float* xlo;                // [N]   field: trailing part
   float* xolo;               // [N]   trailing part of x_old (x_old holds the other two)
+  float2* e2;                // [N]   the current solve's correction to the field
   float2* diag2;             // [N]
   float2* rD2;               // [N]
   const float2* vdt2;        // [N]   V/dt * df_scale

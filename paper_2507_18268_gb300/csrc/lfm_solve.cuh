@@ -350,23 +350,25 @@ __device__ __forceinline__ double fmadd(double a, double b, double c) { return f
 __device__ __forceinline__ float fmadd(float a, float b, float c) { return fmaf(a, b, c); }
 
 // Rows c and c2 of A v (diag * v_c, then the slots in order, fused multiply-adds), all loads
-// of both rows issued before any is used.
+// of both rows issued before any is used. The matrix arrays are read once per pass with
+// evict-first (streaming) loads, so that they do not displace the gathered vector from L1
+// and L2.
 template <int W, typename T>
 __device__ __forceinline__ void rows2(const Slots<T>& A, int c, int c2, const T* __restrict__ v, T& y, T& y2,
                                       T& vc, T& vc2) {
   const size_t N = (size_t)A.N;
   vc = v[c];
   vc2 = v[c2];
-  T acc = A.diag[c] * vc, acc2 = A.diag[c2] * vc2;
+  T acc = __ldcs(A.diag + c) * vc, acc2 = __ldcs(A.diag + c2) * vc2;
   if constexpr (W > 0) {
     int o[W], o2[W];
     T u[W], u2[W];
 #pragma unroll
     for (int k = 0; k < W; ++k) {
-      o[k] = __ldg(A.other + (size_t)k * N + c);
-      o2[k] = __ldg(A.other + (size_t)k * N + c2);
-      u[k] = A.coef[(size_t)k * N + c];
-      u2[k] = A.coef[(size_t)k * N + c2];
+      o[k] = __ldcs(A.other + (size_t)k * N + c);
+      o2[k] = __ldcs(A.other + (size_t)k * N + c2);
+      u[k] = __ldcs(A.coef + (size_t)k * N + c);
+      u2[k] = __ldcs(A.coef + (size_t)k * N + c2);
     }
 #pragma unroll
     for (int k = 0; k < W; ++k) {

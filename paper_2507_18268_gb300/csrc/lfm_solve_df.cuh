@@ -23,11 +23,13 @@
 // 48 bits is a noise source that truncated-CG time stepping amplifies from step to step:
 // on the 200^3 graded box it grew to 7e-10 relative over 100 steps.)
 // Per step (phases separated by team barriers):
-//   S  sum of x (for xRef); with correctors also x at the start of the step
+//   S  the last solve's correction added to the field; sum of x (for xRef); with correctors
+//      also x at the start of the step
 //   R  per row: diag = sum of the slot conductances (slot order) + boundary + V/dt, the
 //      source, 1/diag (FP32 reciprocal + one df64 Newton step), the row sum; r = b - A x
 //      (in flux form, see pass_rows_init_df), normFactor terms, sum|r|, w = rD r, rho; p = w
-//   loop: P p = w + beta p; M q = A p, p.q; U x += alpha p, r -= alpha q, w = rD r, sum|r|, w.r
+//   loop: P p = w + beta p; M q = A p, p.q; U e += alpha p, r -= alpha q, w = rD r, sum|r|, w.r
+//   (e: the solve's correction to the field, df64)
 // A row of A v is diag_c v_c - sum_k g_ck v_other(k): the off-diagonal coefficient of face f
 // is -g_f in both rows (the matrix is symmetric), so the slot array of conductances is the
 // matrix's off-diagonal part.
@@ -50,21 +52,29 @@ namespace {
 __device__ __forceinline__ df df_from_scalar(double v) { return df_from_double(v); }
 
 // S: this thread's sum of x over [c0, c1) (per-thread df64 sum, converted once). `convert`:
-// first pass of the launch, the triple-float field is split from the FP64 field x.
+// first pass of the launch, the triple-float field is split from the FP64 field x. `fold`:
+// the previous solve's correction e (df64, see pass_update_df) is added to the field first.
 // `save_old`: keep x as the step's starting field (the ddt source of the corrector passes).
 template <int B>
-__device__ __noinline__ double pass_sum_df(const CaseDev& cs, int c0, int c1, bool convert, bool save_old) {
+__device__ __noinline__ double pass_sum_df(const CaseDev& cs, int c0, int c1, bool convert, bool fold,
+                                           bool save_old) {
   float2* __restrict__ x2 = cs.x2;
   float* __restrict__ xl = cs.xlo;
+  const float2* __restrict__ e2 = cs.e2;
   DfAcc acc;
   int c = c0 + (int)threadIdx.x;
-  if (!convert && !save_old) {  // the common case: four cells per trip, loads first
-    for (; c + 3 * B < c1; c += 4 * B) {
-      const float2 a = x2[c], b = x2[c + B], d = x2[c + 2 * B], e = x2[c + 3 * B];
-      acc.add(fast_two_sum(a.x, a.y));
-      acc.add(fast_two_sum(b.x, b.y));
-      acc.add(fast_two_sum(d.x, d.y));
-      acc.add(fast_two_sum(e.x, e.y));
+  if (!convert && !save_old) {  // two cells per trip, loads first
+    for (; c + B < c1; c += 2 * B) {
+      tf a = ld_tf(x2, xl, c), b = ld_tf(x2, xl, c + B);
+      if (fold) {
+        const df ea = ld_df(e2 + c), eb = ld_df(e2 + c + B);
+        a = tf_add_df(a, ea);
+        b = tf_add_df(b, eb);
+        st_tf(x2, xl, c, a);
+        st_tf(x2, xl, c + B, b);
+      }
+      acc.add(tf_to_df(a));
+      acc.add(tf_to_df(b));
     }
   }
   for (; c < c1; c += B) {
@@ -74,6 +84,10 @@ __device__ __noinline__ double pass_sum_df(const CaseDev& cs, int c0, int c1, bo
       st_tf(x2, xl, c, v);
     } else {
       v = ld_tf(x2, xl, c);
+      if (fold) {
+        v = tf_add_df(v, ld_df(e2 + c));
+        st_tf(x2, xl, c, v);
+      }
     }
     if (save_old) st_tf(reinterpret_cast<float2*>(cs.x_old), cs.xolo, c, v);
     acc.add(tf_to_df(v));
@@ -81,13 +95,18 @@ __device__ __noinline__ double pass_sum_df(const CaseDev& cs, int c0, int c1, bo
   return acc.value();
 }
 
-// The FP64 field from the triple-float one (end of the launch; each CTA its own cells).
+// The FP64 field from the triple-float one (end of the launch; each CTA its own cells), with
+// the last solve's correction when it is not folded yet.
 template <int B>
-__device__ __noinline__ void pass_store_x(const CaseDev& cs, int c0, int c1) {
+__device__ __noinline__ void pass_store_x(const CaseDev& cs, int c0, int c1, bool fold) {
   const float2* __restrict__ x2 = cs.x2;
   const float* __restrict__ xl = cs.xlo;
   double* __restrict__ x = cs.x;
-  for (int c = c0 + (int)threadIdx.x; c < c1; c += B) x[c] = tf_to_double(ld_tf(x2, xl, c));
+  for (int c = c0 + (int)threadIdx.x; c < c1; c += B) {
+    tf v = ld_tf(x2, xl, c);
+    if (fold) v = tf_add_df(v, ld_df(cs.e2 + c));
+    x[c] = tf_to_double(v);
+  }
 }
 
 // Boundary conductance, source and flux g_b (T_b - x_c) of row c (fixedValue faces;
@@ -203,7 +222,8 @@ __device__ __noinline__ Sums3 pass_rows_init_df(const CaseDev& cs, int c0, int c
   return Sums3{a_nf.value(), a_r.value(), a_rho.value()};
 }
 
-// Rows c and c2 of A v, all loads of both rows issued before any is used.
+// Rows c and c2 of A v, all loads of both rows issued before any is used; the matrix arrays
+// with evict-first (streaming) loads, so that they do not displace the gathered vector.
 template <int W>
 __device__ __forceinline__ void rows2_df(const CaseDev& cs, int c, int c2, const float2* __restrict__ v, df& y,
                                          df& y2, df& vc, df& vc2) {
@@ -211,16 +231,18 @@ __device__ __forceinline__ void rows2_df(const CaseDev& cs, int c, int c2, const
   const float2* __restrict__ g2 = cs.g2;
   vc = ld_df(v + c);
   vc2 = ld_df(v + c2);
-  df acc = df_mul(ld_df(cs.diag2 + c), vc), acc2 = df_mul(ld_df(cs.diag2 + c2), vc2);
+  const float2 dd1 = __ldcs(cs.diag2 + c), dd2 = __ldcs(cs.diag2 + c2);
+  df acc = df_mul(df{dd1.x, dd1.y}, vc), acc2 = df_mul(df{dd2.x, dd2.y}, vc2);
   if constexpr (W > 0) {
     int o[W], o2[W];
     df g[W], h[W];
 #pragma unroll
     for (int k = 0; k < W; ++k) {
-      o[k] = __ldg(cs.slot_other + (size_t)k * N + c);
-      o2[k] = __ldg(cs.slot_other + (size_t)k * N + c2);
-      g[k] = ldg_df(g2 + (size_t)k * N + c);
-      h[k] = ldg_df(g2 + (size_t)k * N + c2);
+      o[k] = __ldcs(cs.slot_other + (size_t)k * N + c);
+      o2[k] = __ldcs(cs.slot_other + (size_t)k * N + c2);
+      const float2 a = __ldcs(g2 + (size_t)k * N + c), b = __ldcs(g2 + (size_t)k * N + c2);
+      g[k] = df{a.x, a.y};
+      h[k] = df{b.x, b.y};
     }
 #pragma unroll
     for (int k = 0; k < W; ++k) {
@@ -289,30 +311,37 @@ __device__ __forceinline__ double pass_amul_dot_df(const CaseDev& cs, int c0, in
   return s.value();
 }
 
-// U: x += alpha p (x triple-float), r -= alpha q, w = rD r; returns this thread's sum|r|
-// and w.r.
+// U: e += alpha p (first iteration of a solve: e = alpha p), r -= alpha q, w = rD r; returns
+// this thread's sum|r| and w.r. e, the solve's correction to the field, is added to the
+// triple-float field once per solve (pass_sum_df, pass_store_x), so an iteration moves 8
+// bytes of field state per cell instead of reading and writing the field's 12.
 template <int B>
-__device__ __forceinline__ double2 pass_update_df(int c0, int c1, df alpha, float2* __restrict__ x,
-                                                  float* __restrict__ xl, float2* __restrict__ r,
-                                                  float2* __restrict__ w, const float2* __restrict__ p,
-                                                  const float2* __restrict__ q, const float2* __restrict__ rD) {
+__device__ __forceinline__ double2 pass_update_df(int c0, int c1, df alpha, float2* __restrict__ e, bool first,
+                                                  float2* __restrict__ r, float2* __restrict__ w,
+                                                  const float2* __restrict__ p, const float2* __restrict__ q,
+                                                  const float2* __restrict__ rD) {
   DfAcc sa, sr;
   const df nalpha = df_neg(alpha);
   int c = c0 + (int)threadIdx.x;
   for (; c + B < c1; c += 2 * B) {
-    const int e = c + B;
-    const df pa = ld_df(p + c), pb = ld_df(p + e), qa = ld_df(q + c), qb = ld_df(q + e);
-    const tf xa = ld_tf(x, xl, c), xb = ld_tf(x, xl, e);
-    const df ra = ld_df(r + c), rb = ld_df(r + e);
-    const df da = ld_df(rD + c), db = ld_df(rD + e);
+    const int k = c + B;
+    const df pa = ld_df(p + c), pb = ld_df(p + k), qa = ld_df(q + c), qb = ld_df(q + k);
+    const df ra = ld_df(r + c), rb = ld_df(r + k);
+    const df da = ld_df(rD + c), db = ld_df(rD + k);
     const df rna = df_fma(nalpha, qa, ra), rnb = df_fma(nalpha, qb, rb);
     const df wa = df_mul(da, rna), wb = df_mul(db, rnb);
-    st_tf(x, xl, c, tf_add_df(xa, df_mul(alpha, pa)));
-    st_tf(x, xl, e, tf_add_df(xb, df_mul(alpha, pb)));
+    if (first) {
+      st_df(e + c, df_mul(alpha, pa));
+      st_df(e + k, df_mul(alpha, pb));
+    } else {
+      const df ea = ld_df(e + c), eb = ld_df(e + k);
+      st_df(e + c, df_fma(alpha, pa, ea));
+      st_df(e + k, df_fma(alpha, pb, eb));
+    }
     st_df(r + c, rna);
-    st_df(r + e, rnb);
+    st_df(r + k, rnb);
     st_df(w + c, wa);
-    st_df(w + e, wb);
+    st_df(w + k, wb);
     sa.add(df_abs(rna));
     sa.add(df_abs(rnb));
     sr.add(df_mul(wa, rna));
@@ -321,7 +350,8 @@ __device__ __forceinline__ double2 pass_update_df(int c0, int c1, df alpha, floa
   if (c < c1) {
     const df rn = df_fma(nalpha, ld_df(q + c), ld_df(r + c));
     const df wn = df_mul(ld_df(rD + c), rn);
-    st_tf(x, xl, c, tf_add_df(ld_tf(x, xl, c), df_mul(alpha, ld_df(p + c))));
+    const df pc = ld_df(p + c);
+    st_df(e + c, first ? df_mul(alpha, pc) : df_fma(alpha, pc, ld_df(e + c)));
     st_df(r + c, rn);
     st_df(w + c, wn);
     sa.add(df_abs(rn));
@@ -331,11 +361,13 @@ __device__ __forceinline__ double2 pass_update_df(int c0, int c1, df alpha, floa
 }
 
 // The steps of one launch. Returns false when a barrier failed (the caller leaves).
+// `pending` tracks whether e holds a correction not yet added to the field (the same in every
+// CTA: it follows the team-wide iteration counts).
 template <int B, int W>
 __device__ bool steps_df64(const CaseDev& cs, const CaseDev& cref, const Team& tm, int n_steps, TeamShared& sh,
-                           int stats_base, int c0, int c1) {
+                           int stats_base, int c0, int c1, bool& pending) {
   const int tid = threadIdx.x;
-  float2* __restrict__ x = cs.x2;
+  float2* __restrict__ e = cs.e2;
   float2* __restrict__ r = reinterpret_cast<float2*>(cs.r);
   float2* __restrict__ w = reinterpret_cast<float2*>(cs.w);
   float2* __restrict__ p = reinterpret_cast<float2*>(cs.p);
@@ -350,8 +382,10 @@ __device__ bool steps_df64(const CaseDev& cs, const CaseDev& cref, const Team& t
     double nf0 = 0.0, init0 = 0.0, res = 0.0;
     bool conv = false;
     for (int pass = 0; pass <= cs.n_corr; ++pass) {
-      // ---- S: sum of x (first pass of the launch: split the FP64 field) ----------------
-      double v[1] = {pass_sum_df<B>(cref, c0, c1, step == 0 && pass == 0, pass == 0 && cs.n_corr > 0)};
+      // ---- S: sum of x (first pass of the launch: split the FP64 field; otherwise the last
+      //      solve's correction is added first) ---------------------------------------------
+      double v[1] = {pass_sum_df<B>(cref, c0, c1, step == 0 && pass == 0, pending, pass == 0 && cs.n_corr > 0)};
+      pending = false;
       if (!team_allreduce<1>(tm, v, sh)) return false;
       clk.lap(kPhAssembly);
       // ---- R: rows, initial residual, normFactor, first direction ----------------------
@@ -383,7 +417,8 @@ __device__ bool steps_df64(const CaseDev& cs, const CaseDev& cref, const Team& t
             break;
           }
           const double alpha = rho / sigma;
-          const double2 su = pass_update_df<B>(c0, c1, df_from_scalar(alpha), x, cs.xlo, r, w, p, q, rD);
+          const double2 su = pass_update_df<B>(c0, c1, df_from_scalar(alpha), e, iters == 0, r, w, p, q, rD);
+          pending = true;
           double s2[2] = {su.x, su.y};
           if (!team_allreduce<2>(tm, s2, sh)) return false;
           clk.lap(kPhU);
@@ -423,10 +458,11 @@ __device__ void run_steps_df64(const CaseDev& cs, const CaseDev& cref, const Tea
   if (n_steps <= 0) return;
   int c0, c1;
   cta_range(cs.N, tm.size, tm.rank, c0, c1);
-  steps_df64<B, W>(cs, cref, tm, n_steps, sh, stats_base, c0, c1);
-  // the field of the CTA's own cells is written by this CTA only (U pass), so the FP64 field can
-  // be written back without another barrier, also after an early exit.
-  pass_store_x<B>(cref, c0, c1);
+  bool pending = false;
+  steps_df64<B, W>(cs, cref, tm, n_steps, sh, stats_base, c0, c1, pending);
+  // the field and the correction of the CTA's own cells are written by this CTA only, so the
+  // FP64 field can be written back without another barrier, also after an early exit.
+  pass_store_x<B>(cref, c0, c1, pending);
 }
 
 }  // namespace
