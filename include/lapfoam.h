@@ -293,7 +293,11 @@ int lfm_finish(lfm_ctx *ctx, lfm_step_stats *out, int32_t n);
  * both computed on the device. Synchronises before return. */
 int lfm_get_field(lfm_ctx *ctx, double *T_out, double *T_boundary);
 
-/* Device pointer of the context's T[n_cells] (float64), valid until lfm_destroy. */
+/* Device pointer of the context's T[n_cells] (float64), valid until lfm_destroy, for reading
+ * (it holds the field after every advance). Write the field with lfm_set_field,
+ * lfm_set_field_device or lfm_fill_field: the LFM_DF64 and LFM_MIXED forms carry the field
+ * between advances at higher precision (a triple-float) and re-read this array only after
+ * one of those calls. */
 int lfm_field_device_ptr(lfm_ctx *ctx, double **T_dev);
 
 /* Reads the assembled matrix of the current T (diag[n_cells], upper[n_faces],

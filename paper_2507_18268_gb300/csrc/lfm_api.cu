@@ -40,13 +40,14 @@ struct Layout {
   size_t Sf, fw, corr, bSf, gE, gD, gH, cK, cL, grad;  // general geometry (0 when absent)
   size_t diag32, slot_coef32, rD32, dx32, r32, w32, p32, q32;
   size_t x2, xlo, xolo, e2, diag2, rD2, vdt2, g2;  // df64 form (0 when absent)
+  size_t flags;
   size_t total;
 };
 
-// kind: LFM_FP64 (FP64 solver vectors), LFM_MIXED (FP32 matrix copy + FP32 vectors),
-// LFM_DF64 (the FP64 solver vectors, used as double-float pairs by the df64 form, plus the
-// df64 field, diagonal, reciprocal, V/dt and slot conductances) or kLayoutBoth (every set,
-// so that the precision may change after upload).
+// kind: LFM_FP64 (FP64 solver vectors), LFM_MIXED (FP32 matrix copy + FP32 vectors, plus the
+// df64 block for its outer passes), LFM_DF64 (the FP64 solver vectors, used as double-float
+// pairs by the df64 form, plus the df64 block: field, diagonal, reciprocal, V/dt and slot
+// conductances) or kLayoutBoth (every set, so that the precision may change after upload).
 constexpr int kLayoutBoth = -1;
 
 int layout_kind(int32_t precision) {
@@ -54,7 +55,7 @@ int layout_kind(int32_t precision) {
 }
 bool kind_has64(int kind) { return kind != LFM_MIXED; }
 bool kind_has32(int kind) { return kind == LFM_MIXED || kind == kLayoutBoth; }
-bool kind_hasdf(int kind) { return kind == LFM_DF64 || kind == kLayoutBoth; }
+bool kind_hasdf(int kind) { return kind != LFM_FP64; }  // the df64 form and the mixed form's outer passes
 
 // shared_mesh: the mesh arrays (slots, boundary lists, geometry) live in another context.
 // geom: general (non-orthogonal) geometry arrays and the per-case gradient / correction flux.
@@ -70,6 +71,7 @@ Layout make_layout(int64_t N, int64_t F, int64_t NB, int64_t W, int kind, bool s
   L.sync = take(sizeof(SyncWords));
   L.partials = take(sizeof(double) * kMaxCtas * kMaxSums);
   L.stats = take(sizeof(lfm_step_stats) * kStatsCap);
+  L.flags = take(256);
   if (!shared_mesh) {
     L.slot_other = take(4 * W * N);
     L.slot_face = take(4 * W * N);
@@ -402,6 +404,7 @@ void bind_pointers(lfm_ctx* c) {
   cs.sync = reinterpret_cast<SyncWords*>(b + L.sync);
   cs.partials = reinterpret_cast<double*>(b + L.partials);
   cs.stats = reinterpret_cast<lfm_step_stats*>(b + L.stats);
+  cs.flags = reinterpret_cast<int32_t*>(b + L.flags);
   cs.W = c->W;
   cs.btype = reinterpret_cast<const int32_t*>(b + L.btype);
   cs.DT = reinterpret_cast<const double*>(b + L.DT);
@@ -509,7 +512,8 @@ int refresh_coef(lfm_ctx* c) {
 // Rebuilds the df64 conductances and V/dt (a0 of the df64 form) when the mesh, DT or dt
 // changed since they were built. Enqueued on the context's stream.
 int refresh_df(lfm_ctx* c) {
-  if (c->opts.precision != LFM_DF64 || !c->df_dirty) return LFM_OK;
+  const bool want = c->opts.precision == LFM_DF64 || (c->opts.precision == LFM_MIXED && c->hasdf && !c->has_geom);
+  if (!want || !c->df_dirty) return LFM_OK;
   if (!c->hasdf) return fail(c, LFM_ENOMEM, "the workspace has no df64 buffers");
   CK(c, launch_df_setup(c->cs, c->stream));
   CK(c, cudaStreamSynchronize(c->stream));  // batches launch on their own stream
@@ -528,6 +532,13 @@ int refresh_ops(lfm_ctx* c) {
   return LFM_OK;
 }
 
+// The FP64 field is about to be written other than by a df64 launch: the triple-float copy
+// the df64 forms carry across launches is stale from then on (see lfm_solve_df.cuh).
+int invalidate_split(lfm_ctx* c) {
+  CK(c, cudaMemsetAsync(c->cs.flags, 0, sizeof(int32_t), c->stream));
+  return LFM_OK;
+}
+
 int need_uploaded(lfm_ctx* c) {
   if (!c) return fail_free(LFM_EINVAL, "context is NULL");
   if (!c->uploaded) return fail(c, LFM_ESTATE, "no mesh uploaded");
@@ -542,6 +553,9 @@ int enqueue_chunk(lfm_ctx* c, int steps, int mode) {
   if (mode == kModeSteps) {
     if (int rc = refresh_coef(c)) return rc;
     if (int rc = refresh_df(c)) return rc;
+    const int p = c->opts.precision;
+    if (p == LFM_FP64 || (p == LFM_MIXED && !mixed_runs_df(c->cs)))
+      if (int rc = invalidate_split(c)) return rc;
   }
   int e = 0;
   Launch L = current_launch(c, e);
@@ -708,6 +722,7 @@ static int upload_mesh_impl(lfm_ctx* c, const lfm_mesh* m, const lfm_geometry* g
   c->patch_size.assign(m->patch_size, m->patch_size + m->n_patches);
   c->patch_type.assign(m->n_patches, LFM_ZERO_GRADIENT);
   bind_pointers(c);
+  if (int e = invalidate_split(c)) return e;
 
   const int32_t N = c->N, F = c->F, NB = c->NB;
   int rc;
@@ -877,6 +892,7 @@ int lfm_upload_box(lfm_ctx* c, int32_t nx, int32_t ny, int32_t nz, const double*
   for (int p = 1; p < 6; ++p) c->patch_start[p] = c->patch_start[p - 1] + sizes[p - 1];
   c->patch_type.assign(6, LFM_ZERO_GRADIENT);
   bind_pointers(c);
+  if (int e = invalidate_split(c)) return e;
   // vertex coordinates staged in the (not yet used) partial-sum table
   double* coords = c->cs.partials;
   const Layout& Y = c->lay;
@@ -964,6 +980,7 @@ int lfm_upload_mesh_shared(lfm_ctx* c, lfm_ctx* src) {
   c->patch_size = root->patch_size;
   c->patch_type.assign(root->n_patches, LFM_ZERO_GRADIENT);
   bind_pointers(c);
+  if (int e = invalidate_split(c)) return e;
   const int32_t N = c->N, F = c->F, NB = c->NB;
   const Layout& Y = c->lay;
   const size_t WN = (size_t)c->W * N;
@@ -994,6 +1011,7 @@ int lfm_fill_field(lfm_ctx* c, double value) {
   if (rc) return rc;
   if (!std::isfinite(value)) return fail(c, LFM_EINVAL, "value must be finite");
   DeviceGuard g(c->device);
+  if ((rc = invalidate_split(c))) return rc;
   CK(c, launch_fill(c->cs.x, c->N, value, c->stream));
   CK(c, cudaStreamSynchronize(c->stream));
   return LFM_OK;
@@ -1131,7 +1149,7 @@ int lfm_set_solver(lfm_ctx* c, const lfm_solver_opts* o) {
       (o->precision != LFM_FP64 && o->precision != LFM_MIXED && o->precision != LFM_DF64))
     return fail(c, LFM_EINVAL, "invalid solver options");
   if ((o->precision == LFM_FP64 && !c->has64) || (o->precision == LFM_MIXED && !c->has32) ||
-      (o->precision == LFM_DF64 && !c->hasdf))
+      (o->precision == LFM_DF64 && !(c->hasdf && c->has64)))
     return fail(c, LFM_ENOMEM, "the workspace was laid out without the %s solver buffers",
                 o->precision == LFM_FP64 ? "FP64" : (o->precision == LFM_MIXED ? "mixed-precision" : "df64"));
   if (o->precision == LFM_DF64 && c->has_geom)
@@ -1185,6 +1203,7 @@ int lfm_set_field(lfm_ctx* c, const double* T) {
   if (rc) return rc;
   if (!T) return fail(c, LFM_EINVAL, "T is NULL");
   DeviceGuard g(c->device);
+  if ((rc = invalidate_split(c))) return rc;
   CK(c, cudaMemcpyAsync(c->cs.x, T, sizeof(double) * c->N, cudaMemcpyHostToDevice, c->stream));
   CK(c, cudaStreamSynchronize(c->stream));
   return LFM_OK;
@@ -1195,6 +1214,7 @@ int lfm_set_field_device(lfm_ctx* c, const double* T_dev) {
   if (rc) return rc;
   if (!T_dev) return fail(c, LFM_EINVAL, "T_dev is NULL");
   DeviceGuard g(c->device);
+  if ((rc = invalidate_split(c))) return rc;
   CK(c, cudaMemcpyAsync(c->cs.x, T_dev, sizeof(double) * c->N, cudaMemcpyDeviceToDevice, c->stream));
   return LFM_OK;
 }
@@ -1620,7 +1640,7 @@ int lfm_batch_advance_async(lfm_batch* b, int32_t n_steps, int32_t use_graph) {
     refresh_case(c);
     if (refresh_ops(c) != LFM_OK) return bfail(b, LFM_ECUDA, "case %d: operator rebuild failed", b->order[i]);
     if ((c->opts.precision == LFM_FP64 && !c->has64) || (c->opts.precision == LFM_MIXED && !c->has32) ||
-        (c->opts.precision == LFM_DF64 && !c->hasdf))
+        (c->opts.precision == LFM_DF64 && !(c->hasdf && c->has64)))
       return bfail(b, LFM_ENOMEM, "case %d has no buffers for its precision", b->order[i]);
     if (refresh_coef(c) != LFM_OK || refresh_df(c) != LFM_OK)
       return bfail(b, LFM_ECUDA, "case %d: coefficient set-up failed", b->order[i]);

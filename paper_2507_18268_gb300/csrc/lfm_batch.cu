@@ -58,7 +58,7 @@ __global__ void __launch_bounds__(B, 1024 / B) batch_kernel(const CaseDev* __res
     const Team tm{s_job[2], s_job[1], s_cs.sync, s_cs.partials, L.timeout_ns};
     const int base = case_step[c];
     if (s_cs.precision == LFM_MIXED)
-      run_steps_mixed<B, W>(s_cs, s_cs, tm, n_steps, kModeSteps, sh, base);
+      run_steps_mixed_any<B, W>(s_cs, s_cs, tm, n_steps, kModeSteps, sh, base);
     else if (s_cs.precision == LFM_DF64)
       run_steps_df64<B, W>(s_cs, s_cs, tm, n_steps, sh, base);
     else
@@ -77,6 +77,9 @@ __global__ void batch_prepare_kernel(const CaseDev* __restrict__ cases, int n_ca
     sw->count = 0;
     sw->status = 0;
     case_step[i] = 0;
+    // forms that update the FP64 field directly leave the triple-float one stale
+    const int prec = cases[i].precision;
+    if (prec == LFM_FP64 || (prec == LFM_MIXED && !mixed_uses_df(cases[i]))) cases[i].flags[0] = 0;
   }
 }
 

@@ -127,6 +127,8 @@ struct CaseDev {
   float* xlo;                // [N]   field: trailing part
   float* xolo;               // [N]   trailing part of x_old (x_old holds the other two)
   float2* e2;                // [N]   the current solve's correction to the field
+  int32_t* flags;            // [1]   flags[0] != 0: the triple-float field (x2, xlo) is current and
+                             //       x holds its rounding; 0: x was written otherwise (split it)
   float2* diag2;             // [N]
   float2* rD2;               // [N]
   const float2* vdt2;        // [N]   V/dt * df_scale
@@ -186,6 +188,9 @@ cudaError_t launch_times_volume(const CaseDev& cs, const double* a, double* out,
 // Set-up of the face coefficients: -DT |Sf| deltaCoeff at both slots of every face in the
 // FP64 slot array and, when present, the FP32 one.
 cudaError_t launch_coef_setup(const CaseDev& cs, cudaStream_t stream);
+// Whether the mixed form of this case runs its outer passes in df64 (orthogonal mesh, df64
+// block present, scale an FP32 power of two).
+bool mixed_runs_df(const CaseDev& cs);
 // df64 form set-up: the per-slot conductances g2 and V/dt (vdt2), both times cs.df_scale.
 cudaError_t launch_df_setup(const CaseDev& cs, cudaStream_t stream);
 

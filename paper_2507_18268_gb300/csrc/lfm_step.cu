@@ -33,6 +33,18 @@ __global__ void __launch_bounds__(B, 1024 / B) step_kernel_mixed(CaseDev cs, Lau
   run_steps_mixed<B, W>(cs, s_cs, tm, n_steps, mode, sh);
 }
 
+// The mixed form with df64 outer passes (orthogonal meshes; the host chooses it).
+template <int B, int W>
+__global__ void __launch_bounds__(B, 1024 / B) step_kernel_mixed_df(CaseDev cs, Launch L, int n_steps, int mode) {
+  __shared__ TeamShared sh;
+  __shared__ CaseDev s_cs;
+  if ((int)blockIdx.x == L.skip_cta) return;
+  if (threadIdx.x == 0) s_cs = cs;
+  __syncthreads();
+  const Team tm{(int)gridDim.x, (int)blockIdx.x, cs.sync, cs.partials, L.timeout_ns};
+  run_steps_mixed_df<B, W>(cs, s_cs, tm, n_steps, sh);
+}
+
 template <int B, int W>
 __global__ void __launch_bounds__(B, 1024 / B) step_kernel_df64(CaseDev cs, Launch L, int n_steps, int mode) {
   __shared__ TeamShared sh;
@@ -231,13 +243,18 @@ __global__ void fill_kernel(double* a, size_t n, double v) {
   for (; i < n; i += stride) a[i] = v;
 }
 
+// kMixedDf: the mixed form with df64 outer passes (a precision code for kernel choice only).
+constexpr int kMixedDf = 100;
+
 template <int B>
 void* step_fn_w(int precision, int W) {
   if (W == 6) {
+    if (precision == kMixedDf) return (void*)step_kernel_mixed_df<B, 6>;
     if (precision == LFM_MIXED) return (void*)step_kernel_mixed<B, 6>;
     if (precision == LFM_DF64) return (void*)step_kernel_df64<B, 6>;
     return (void*)step_kernel_f64<B, 6>;
   }
+  if (precision == kMixedDf) return (void*)step_kernel_mixed_df<B, 0>;
   if (precision == LFM_MIXED) return (void*)step_kernel_mixed<B, 0>;
   if (precision == LFM_DF64) return (void*)step_kernel_df64<B, 0>;
   return (void*)step_kernel_f64<B, 0>;
@@ -259,6 +276,13 @@ int max_coresident_ctas(int precision, int threads, int W, int device) {
   if (!fn) return 0;
   int per_sm = 0, sms = 0;
   if (cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, fn, threads, 0) != cudaSuccess) return 0;
+  if (precision == LFM_MIXED) {  // either mixed kernel may run: the smaller residency
+    int per_sm_df = 0;
+    if (cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm_df, step_fn_for(kMixedDf, threads, W), threads, 0) !=
+        cudaSuccess)
+      return 0;
+    if (per_sm_df < per_sm) per_sm = per_sm_df;
+  }
   if (cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, device) != cudaSuccess) return 0;
   int n = per_sm * sms;
   return n < kMaxCtas ? n : kMaxCtas;
@@ -267,8 +291,10 @@ int max_coresident_ctas(int precision, int threads, int W, int device) {
 cudaError_t launch_steps(const CaseDev& cs, const Launch& L, int n_steps, int mode,
                          cudaStream_t stream) {
   // matrix read-back of a df64 case runs the FP64 assembly (its arrays are the ones read)
-  const int prec = (mode == kModeAssembleOnly && cs.precision == LFM_DF64) ? LFM_FP64 : cs.precision;
-  void* fn = step_fn_for(prec, L.threads, cs.W);
+  int prec = (mode == kModeAssembleOnly && cs.precision == LFM_DF64) ? LFM_FP64 : cs.precision;
+  // the mixed form runs its outer passes in df64 when the case allows (see mixed_uses_df)
+  const bool mixed_df = prec == LFM_MIXED && mode == kModeSteps && mixed_runs_df(cs);
+  void* fn = step_fn_for(mixed_df ? kMixedDf : prec, L.threads, cs.W);
   if (!fn) return cudaErrorInvalidValue;
   CaseDev a0 = cs;
   a0.precision = prec;
@@ -276,6 +302,10 @@ cudaError_t launch_steps(const CaseDev& cs, const Launch& L, int n_steps, int mo
   int a2 = n_steps, a3 = mode;
   void* args[] = {&a0, &a1, &a2, &a3};
   return cudaLaunchCooperativeKernel(fn, dim3(L.ctas), dim3(L.threads), args, 0, stream);
+}
+
+bool mixed_runs_df(const CaseDev& cs) {
+  return cs.x2 != nullptr && cs.Sf == nullptr && cs.df_scale >= 0x1p-100 && cs.df_scale <= 0x1p100;
 }
 
 cudaError_t launch_coef_setup(const CaseDev& cs, cudaStream_t stream) {

@@ -229,3 +229,43 @@ def test_df64_batched_matches_alone_and_oracle():
             if c.precision == lapcase.DF64:
                 Ta, sa, _ = df_run(c, n_steps=n_steps)
                 assert relerr(T, Ta) <= 1e-13
+
+
+@pytest.mark.parametrize("prec", [B.LFM_DF64, B.LFM_MIXED])
+def test_field_carried_between_launches(prec):
+    # the triple-float field persists across launches: 3 + 3 steps equal 6 steps bitwise
+    case = CASES["permuted20"]().with_(precision=prec)
+    with Solver.from_case(case) as s:
+        s.advance(3)
+        s.advance(3)
+        Ta = s.field()
+    with Solver.from_case(case) as s:
+        s.advance(6)
+        Tb = s.field()
+    assert np.array_equal(Ta, Tb)
+    # a field written from the host replaces it: the same as a fresh case started there
+    with Solver.from_case(case) as s:
+        s.advance(3)
+        T3 = s.field().copy()
+        s.set_field(T3)
+        s.advance(3)
+        Tc = s.field()
+    with Solver.from_case(case) as s:
+        s.set_field(T3)
+        s.advance(3)
+        Td = s.field()
+    assert np.array_equal(Tc, Td)
+    # an FP64 launch in between writes the FP64 field: the next df launch starts from it
+    with Solver.from_case(case) as s:
+        s.advance(2)
+        s.set_solver(case.tol, 0.0, 1000, 0, B.LFM_FP64)
+        s.advance(1)
+        T3 = s.field().copy()
+        s.set_solver(case.tol, 0.0, 1000, 0, prec)
+        s.advance(2)
+        Te = s.field()
+    with Solver.from_case(case) as s:
+        s.set_field(T3)
+        s.advance(2)
+        Tf = s.field()
+    assert np.array_equal(Te, Tf)
