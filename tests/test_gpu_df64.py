@@ -269,3 +269,35 @@ def test_field_carried_between_launches(prec):
         s.advance(2)
         Tf = s.field()
     assert np.array_equal(Te, Tf)
+
+
+def _scaled_case(kind):
+    base = lapcase.random_small_case(41, nx=9, ny=7, nz=6).with_(tol=1e-10, n_steps=4)
+    if kind == "celsius":
+        # a field that crosses zero: leading parts of neighbouring values differ in sign
+        return base.with_(patches=((lapcase.FIXED_VALUE, 50.0), (lapcase.FIXED_VALUE, -50.0),
+                                   (lapcase.ZERO_GRADIENT, 0.0), (lapcase.ZERO_GRADIENT, 0.0),
+                                   (lapcase.FIXED_VALUE, 0.0), (lapcase.ZERO_GRADIENT, 0.0)), T0=0.0)
+    if kind == "micro":
+        # a 1 mm box, small time step: V/dt and the conductances far from one
+        return base.with_(xs=base.xs * 1e-3, ys=base.ys * 1e-3, zs=base.zs * 1e-3, dt=1e-4, DT_uniform=1e-7,
+                          DTx=None, DTy=None, DTz=None)
+    if kind == "large":
+        # a 1 km box with a large diffusivity and time step
+        return base.with_(xs=base.xs * 1e3, ys=base.ys * 1e3, zs=base.zs * 1e3, dt=1e5, DT_uniform=30.0,
+                          DTx=None, DTy=None, DTz=None)
+    raise KeyError(kind)
+
+
+@pytest.mark.parametrize("kind", ["celsius", "micro", "large"])
+def test_df64_and_mixed_at_extreme_scales(kind):
+    case = _scaled_case(kind)
+    To, so = oracle.advance(case)
+    T, st, _ = df_run(case)
+    scale = float(np.max(np.abs(To)))  # relative to the field's magnitude (T crosses zero)
+    assert float(np.max(np.abs(T - To))) <= 1e-10 * scale
+    assert [s["iters"] for s in st] == [s.iters for s in so]
+    with Solver.from_case(case.with_(precision=lapcase.MIXED)) as s:
+        s.advance(case.n_steps)
+        Tm = s.field()
+    assert float(np.max(np.abs(Tm - To))) <= 1e-5 * scale
