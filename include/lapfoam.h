@@ -48,7 +48,9 @@ enum {
 enum { LFM_FIXED_VALUE = 0, LFM_ZERO_GRADIENT = 1 };
 /* Arithmetic of the step (lfm_solver_opts.precision):
  *   LFM_FP64   IEEE FP64 throughout; the assembled system is bitwise the CPU reference's.
- *   LFM_MIXED  FP32 inner CG inside FP64 defect correction (results ~1e-6 relative).
+ *   LFM_MIXED  FP32 inner CG inside FP64-class defect correction (results ~1e-6 relative):
+ *              the outer passes (true residual, correction) use the LFM_DF64 machinery on
+ *              orthogonal meshes and FP64 on general ones.
  *   LFM_DF64   every per-cell operation in double-float (pairs of FP32 numbers, 48-bit
  *              significand) on the FP32 pipe, per-CTA scalars in FP64: results agree with
  *              FP64 to rounding (~1e-13 relative), at FP32-pipe speed. Orthogonal meshes
@@ -105,8 +107,8 @@ typedef struct {
 /* PCG controls. tol: stop when sum|r| / normFactor < tol; rel_tol > 0 also stops when the
  * residual falls below rel_tol times the step's initial residual; max_iter caps and
  * min_iter forces iterations (OpenFOAM defaults: 1000, 0). precision: LFM_FP64,
- * LFM_MIXED (FP32 matrix and vectors, FP64 dots / normFactor / convergence test / true
- * residual, FP64 field updated by defect correction) or LFM_DF64 (see above). */
+ * LFM_MIXED (FP32 matrix and vectors, FP64-accurate dots / normFactor / convergence test /
+ * true residual, field updated by defect correction) or LFM_DF64 (see above). */
 typedef struct {
   double tol, rel_tol;
   int32_t max_iter, min_iter, precision;
