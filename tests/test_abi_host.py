@@ -127,3 +127,24 @@ def test_create_without_gpu_fails_loudly():
     with pytest.raises(B.LfmError) as e:
         B.lfm_create(0, None)
     assert e.value.code == B.LFM_ECUDA
+
+
+def test_workspace_sizes_by_precision():
+    # host arithmetic only: the layout of each precision's solver buffers (8-byte FP64 /
+    # double-float arrays, 4-byte FP32 arrays, the df64 block with its 4-byte triple-float part)
+    m = _mesh(2)
+    N, F, W = m.n_cells, m.n_faces, 6
+    b64 = B.lfm_workspace_bytes(m, B.LFM_FP64)
+    bmx = B.lfm_workspace_bytes(m, B.LFM_MIXED)
+    bdf = B.lfm_workspace_bytes(m, B.LFM_DF64)
+    ball = B.lfm_workspace_bytes(m, B.LFM_BOTH)
+    assert 0 < b64 < bdf < ball and bmx < ball
+    assert B.lfm_workspace_bytes(m, 7) == ball  # an unknown value lays out every form
+    # the df64 block: x2, e2, diag2, rD2, vdt2 [8N], xlo, xolo [4N], g2 [8WN], each 256-aligned
+    df_block = bdf - b64
+    assert 5 * 8 * N + 2 * 4 * N + 8 * W * N <= df_block <= 5 * 8 * N + 2 * 4 * N + 8 * W * N + 8 * 256
+    # every form's box workspace agrees with the general one for the same box
+    case = lapcase.plain_box(7)
+    bm = pm.box_mesh(case)
+    for prec in (B.LFM_FP64, B.LFM_MIXED, B.LFM_DF64, B.LFM_BOTH):
+        assert B.lfm_workspace_bytes_box(7, 7, 7, prec) == B.lfm_workspace_bytes(bm, prec)
