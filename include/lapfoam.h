@@ -53,9 +53,8 @@ enum { LFM_FIXED_VALUE = 0, LFM_ZERO_GRADIENT = 1 };
  *              orthogonal meshes and FP64 on general ones.
  *   LFM_DF64   every per-cell operation in double-float (pairs of FP32 numbers, 48-bit
  *              significand) on the FP32 pipe, per-CTA scalars in FP64: results agree with
- *              FP64 to rounding (~1e-13 relative), at FP32-pipe speed. Orthogonal meshes
- *              (lfm_upload_mesh, lfm_upload_box and their sharers), with any DT, sources and
- *              corrector passes; general geometry needs LFM_FP64 or LFM_MIXED. */
+ *              FP64 to rounding (~1e-13 relative), at FP32-pipe speed; any mesh (general
+ *              geometry included), DT, sources and corrector passes. */
 enum { LFM_FP64 = 0, LFM_MIXED = 1, LFM_DF64 = 2 };
 
 typedef struct lfm_ctx lfm_ctx;

@@ -50,9 +50,11 @@ class Batch:
         return cid
 
     def add_case(self, case: lapcase.RawCase, mesh=None, workspace: str = "torch") -> int:
+        """Adds a case on a host-built mesh: `mesh`, else the case's box, or its general
+        hexahedral mesh and geometry when the case has vertex points."""
         layout = case.precision if workspace == "torch" else B.LFM_BOTH
-        s = Solver.from_case(case, mesh=mesh or box_mesh(case), device=self.device, stream=self.stream,
-                             workspace=workspace, layout=layout)
+        s = Solver.from_case(case, mesh=mesh, device=self.device, stream=self.stream, workspace=workspace,
+                             layout=layout)
         return self.add(s)
 
     def remove(self, cid: int, close: bool = True) -> Solver:

@@ -40,6 +40,7 @@ struct Layout {
   size_t Sf, fw, corr, bSf, gE, gD, gH, cK, cL, grad;  // general geometry (0 when absent)
   size_t diag32, slot_coef32, rD32, dx32, r32, w32, p32, q32;
   size_t x2, xlo, xolo, e2, diag2, rD2, vdt2, g2;  // df64 form (0 when absent)
+  size_t gE2, cK2, cL2, gZ, grad2;                  // df64 form on general geometry
   size_t flags;
   size_t total;
 };
@@ -117,6 +118,7 @@ Layout make_layout(int64_t N, int64_t F, int64_t NB, int64_t W, int kind, bool s
   L.r = L.w = L.p = L.q = 0;
   L.diag32 = L.slot_coef32 = L.rD32 = L.dx32 = L.r32 = L.w32 = L.p32 = L.q32 = 0;
   L.x2 = L.xlo = L.xolo = L.e2 = L.diag2 = L.rD2 = L.vdt2 = L.g2 = 0;
+  L.gE2 = L.cK2 = L.cL2 = L.gZ = L.grad2 = 0;
   if (kind_has64(kind)) {
     L.r = take(8 * N);
     L.w = take(8 * N);
@@ -132,6 +134,13 @@ Layout make_layout(int64_t N, int64_t F, int64_t NB, int64_t W, int kind, bool s
     L.rD2 = take(8 * N);
     L.vdt2 = take(8 * N);
     L.g2 = take(8 * W * N);
+    if (geom && kind != LFM_MIXED) {  // the mixed form keeps FP64 outer passes on general meshes
+      L.gE2 = take(24 * W * N);
+      L.cK2 = take(24 * N);
+      L.cL2 = take(24 * W * N);
+      L.gZ = take(24 * N);
+      L.grad2 = take(24 * N);
+    }
   }
   if (kind_has32(kind)) {
     L.diag32 = take(4 * N);
@@ -481,6 +490,12 @@ void bind_pointers(lfm_ctx* c) {
   cs.xlo = f ? reinterpret_cast<float*>(b + L.xlo) : nullptr;
   cs.xolo = f ? reinterpret_cast<float*>(b + L.xolo) : nullptr;
   cs.e2 = f ? reinterpret_cast<float2*>(b + L.e2) : nullptr;
+  const bool fg = f && c->has_geom && L.gE2 != 0;
+  cs.gE2 = fg ? reinterpret_cast<const float2*>(b + L.gE2) : nullptr;
+  cs.cK2 = fg ? reinterpret_cast<const float2*>(b + L.cK2) : nullptr;
+  cs.cL2 = fg ? reinterpret_cast<const float2*>(b + L.cL2) : nullptr;
+  cs.gZ = fg ? reinterpret_cast<const double*>(b + L.gZ) : nullptr;
+  cs.grad2 = fg ? reinterpret_cast<float2*>(b + L.grad2) : nullptr;
   cs.diag2 = f ? reinterpret_cast<float2*>(b + L.diag2) : nullptr;
   cs.rD2 = f ? reinterpret_cast<float2*>(b + L.rD2) : nullptr;
   cs.vdt2 = f ? reinterpret_cast<const float2*>(b + L.vdt2) : nullptr;
@@ -529,6 +544,7 @@ int refresh_ops(lfm_ctx* c) {
   CK(c, launch_geom_ops(c->cs, false, c->stream));
   CK(c, cudaStreamSynchronize(c->stream));  // batches launch on their own stream
   c->ops_dirty = false;
+  c->df_dirty = true;  // the df64 copies of the operators follow them
   return LFM_OK;
 }
 
@@ -1152,8 +1168,8 @@ int lfm_set_solver(lfm_ctx* c, const lfm_solver_opts* o) {
       (o->precision == LFM_DF64 && !(c->hasdf && c->has64)))
     return fail(c, LFM_ENOMEM, "the workspace was laid out without the %s solver buffers",
                 o->precision == LFM_FP64 ? "FP64" : (o->precision == LFM_MIXED ? "mixed-precision" : "df64"));
-  if (o->precision == LFM_DF64 && c->has_geom)
-    return fail(c, LFM_EINVAL, "the df64 form serves orthogonal meshes; general geometry needs FP64 or mixed");
+  if (o->precision == LFM_DF64 && c->has_geom && !c->cs.gE2)
+    return fail(c, LFM_ENOMEM, "the workspace was laid out without the df64 general-geometry buffers");
   const bool launch_changes = o->precision != c->opts.precision;
   c->opts = *o;
   if (launch_changes) return choose_launch(c);

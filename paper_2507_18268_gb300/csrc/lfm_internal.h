@@ -134,6 +134,15 @@ struct CaseDev {
   const float2* vdt2;        // [N]   V/dt * df_scale
   const float2* g2;          // [W*N] DT |Sf| deltaCoeff * df_scale at both slots of each face
   double df_scale;
+  // df64 form on general geometry: the operator weights gE (gradient) and cK, cL (correction,
+  // times df_scale) as pairs, the closure weight gZ = gD + sum_k gE_k + sum_fixedValue bSf / V
+  // (FP64; zero for a closed cell up to rounding) of the gradient's difference form, and the
+  // gradient itself (component-major as the FP64 arrays)
+  const float2* gE2;         // [3*W*N]
+  const float2* cK2;         // [3N]
+  const float2* cL2;         // [3*W*N]
+  const double* gZ;          // [3N]
+  float2* grad2;             // [3N]
 
   // team state
   SyncWords* sync;
@@ -191,7 +200,8 @@ cudaError_t launch_coef_setup(const CaseDev& cs, cudaStream_t stream);
 // Whether the mixed form of this case runs its outer passes in df64 (orthogonal mesh, df64
 // block present, scale an FP32 power of two).
 bool mixed_runs_df(const CaseDev& cs);
-// df64 form set-up: the per-slot conductances g2 and V/dt (vdt2), both times cs.df_scale.
+// df64 form set-up: the per-slot conductances g2 and V/dt (vdt2), both times cs.df_scale,
+// and on general geometry the operator weights gE2, cK2, cL2 and gZ (see CaseDev).
 cudaError_t launch_df_setup(const CaseDev& cs, cudaStream_t stream);
 
 // Face-to-cell addressing of a general mesh built on the device (lfm_addr.cu): owner,

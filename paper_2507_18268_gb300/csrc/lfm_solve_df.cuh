@@ -147,6 +147,76 @@ __device__ __forceinline__ void row_boundary_df(const CaseDev& cs, int c, tf xc,
   flux = df_from_double(fl);
 }
 
+// ---- general geometry ----------------------------------------------------------------
+// G: the Gauss linear gradient of the field over [c0, c1) into grad2, in difference form
+//   G_c = sum_k gE_k (T_k - T_c) + sum_fixedValue (bSf / V)(T_b - T_c) + gZ T_c
+// (equal to the operator form gD T_c + gH + sum_k gE_k T_k; see CaseDev): a weighted sum of
+// T values that nearly cancel would carry their rounding, ~2^-48 |T| / h, into the explicit
+// correction; differences formed exactly from the triple-float field do not. The boundary
+// terms (boundary cells only) and gZ T_c (gZ is zero up to the geometry's rounding) are FP64.
+template <int B, int W>
+__device__ __noinline__ void pass_grad_df(const CaseDev& cs, int c0, int c1) {
+  const float2* __restrict__ x2 = cs.x2;
+  const float* __restrict__ xl = cs.xlo;
+  const size_t N = (size_t)cs.N;
+  const int ns = W > 0 ? W : cs.W;
+  const size_t WN = (size_t)ns * N;
+  for (int c = c0 + (int)threadIdx.x; c < c1; c += B) {
+    const tf xc = ld_tf(x2, xl, c);
+    df g0 = mkdf(0.0f, 0.0f), g1 = g0, g2 = g0;
+#pragma unroll
+    for (int k = 0; k < (W > 0 ? W : kMaxSlots); ++k) {
+      if (W == 0 && k >= ns) break;
+      const size_t at = (size_t)k * N + c;
+      const df d = tf_diff(ld_tf(x2, xl, __ldg(cs.slot_other + at)), xc);
+      g0 = df_fma(ldg_df(cs.gE2 + at), d, g0);
+      g1 = df_fma(ldg_df(cs.gE2 + WN + at), d, g1);
+      g2 = df_fma(ldg_df(cs.gE2 + 2 * WN + at), d, g2);
+    }
+    const double xd = tf_to_double(xc);
+    double b0 = cs.gZ[c] * xd, b1 = cs.gZ[N + c] * xd, b2 = cs.gZ[2 * N + c] * xd;
+    const int k0 = __ldg(cs.b_start + c), k1 = __ldg(cs.b_start + c + 1);
+    if (k0 != k1) {
+      const double rv = 1.0 / cs.V[c];
+      for (int k = k0; k < k1; ++k) {
+        const int bf = __ldg(cs.b_face + k);
+        if (__ldg(cs.btype + bf) == LFM_FIXED_VALUE) {
+          const double dT = (__ldg(cs.bval + bf) - xd) * rv;
+          b0 = fma(cs.bSf[3 * (size_t)bf], dT, b0);
+          b1 = fma(cs.bSf[3 * (size_t)bf + 1], dT, b1);
+          b2 = fma(cs.bSf[3 * (size_t)bf + 2], dT, b2);
+        }
+      }
+    }
+    st_df(cs.grad2 + c, df_add(g0, df_from_double(b0)));
+    st_df(cs.grad2 + N + c, df_add(g1, df_from_double(b1)));
+    st_df(cs.grad2 + 2 * N + c, df_add(g2, df_from_double(b2)));
+  }
+}
+
+// The explicit non-orthogonal correction of row c (scaled with the system): the sum over the
+// cell's faces of the correction flux, through the weights cK, cL of the gradient.
+template <int W>
+__device__ __forceinline__ df op_corr_df(const CaseDev& cs, int c) {
+  const size_t N = (size_t)cs.N;
+  const int ns = W > 0 ? W : cs.W;
+  const size_t WN = (size_t)ns * N;
+  const float2* __restrict__ G = cs.grad2;
+  df v = df_mul(ldg_df(cs.cK2 + c), ld_df(G + c));
+  v = df_fma(ldg_df(cs.cK2 + N + c), ld_df(G + N + c), v);
+  v = df_fma(ldg_df(cs.cK2 + 2 * N + c), ld_df(G + 2 * N + c), v);
+#pragma unroll
+  for (int k = 0; k < (W > 0 ? W : kMaxSlots); ++k) {
+    if (W == 0 && k >= ns) break;
+    const size_t at = (size_t)k * N + c;
+    const int o = __ldg(cs.slot_other + at);
+    v = df_fma(ldg_df(cs.cL2 + at), ld_df(G + o), v);
+    v = df_fma(ldg_df(cs.cL2 + WN + at), ld_df(G + N + o), v);
+    v = df_fma(ldg_df(cs.cL2 + 2 * WN + at), ld_df(G + 2 * N + o), v);
+  }
+  return v;
+}
+
 // R: rows of the matrix and, from the same loaded row, the initial residual, normFactor
 // terms, sum|r| and rho; p = w. kSrc: correctors (ddt source from x_old) or volumetric
 // sources present.
@@ -218,6 +288,11 @@ __device__ __noinline__ Sums3 pass_rows_init_df(const CaseDev& cs, int c0, int c
       sa = df_sub(sa, vsp);
       src = df_add(src, df_from_double(su));
       rc = df_add(rc, df_from_double(fma(sp, tf_to_double(xc), su)));
+    }
+    if (kSrc && cs.Sf) {  // the explicit non-orthogonal correction joins the source
+      const df corr = op_corr_df<W>(cs, c);
+      src = df_add(src, corr);
+      rc = df_add(rc, corr);
     }
     const df ax = df_sub(src, rc);
     const df rd = df_rcp(d);
@@ -389,7 +464,7 @@ __device__ bool steps_df64(const CaseDev& cs, const CaseDev& cref, const Team& t
   const double inv_scale = 1.0 / cs.df_scale;  // a power of two: exact
 
   PhaseClock clk(cs, tm);
-  const bool src_mode = cs.n_corr > 0 || cs.vSu != nullptr || cs.vSp != nullptr;
+  const bool src_mode = cs.n_corr > 0 || cs.vSu != nullptr || cs.vSp != nullptr || cs.Sf != nullptr;
   bool convert = ld_volatile_i32(cs.flags) == 0;  // read by every CTA before the first barrier
   for (int step = 0; step < n_steps; ++step) {
     int iters_tot = 0, solves = 0, status = 0;
@@ -402,6 +477,10 @@ __device__ bool steps_df64(const CaseDev& cs, const CaseDev& cref, const Team& t
       pending = false;
       if (!team_allreduce<1>(tm, v, sh)) return false;
       mark_split(cs, tm, convert);
+      if (cs.Sf) {  // ---- G: the gradient of the (folded) field, for the correction ----------
+        pass_grad_df<B, W>(cref, c0, c1);
+        if (!team_barrier(tm, sh)) return false;
+      }
       clk.lap(kPhAssembly);
       // ---- R: rows, initial residual, normFactor, first direction ----------------------
       const double xRef = v[0] / (double)cs.N;

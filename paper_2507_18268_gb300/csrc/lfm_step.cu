@@ -88,6 +88,40 @@ __global__ void df_coef_kernel(CaseDev cs, float2* __restrict__ g2) {
   st_df(g2 + at.y, v);
 }
 
+// df64 operator weights of the general-geometry path: gE and (times the case scale) cK, cL as
+// pairs; the closure weight gZ = gD + sum_k gE_k + sum_fixedValue bSf / V in FP64, so that
+// G_c = sum_k gE_k (T_k - T_c) + sum_fixedValue (bSf / V)(T_b - T_c) + gZ T_c equals the
+// operator form gD T_c + gH + sum_k gE_k T_k.
+__global__ void df_ops_kernel(CaseDev cs, float2* __restrict__ E2, float2* __restrict__ K2, float2* __restrict__ L2,
+                              double* __restrict__ Z) {
+  const int c = blockIdx.x * blockDim.x + threadIdx.x;
+  if (c >= cs.N) return;
+  const size_t N = (size_t)cs.N, WN = (size_t)cs.W * N;
+  const double s = cs.df_scale;
+  double z[3] = {cs.gD[c], cs.gD[N + c], cs.gD[2 * N + c]};
+  for (int q = 0; q < 3; ++q) {
+    const df v = df_from_double(cs.cK[q * N + c] * s);
+    K2[q * N + c] = make_float2(v.hi, v.lo);
+  }
+  for (int k = 0; k < cs.W; ++k) {
+    const size_t at = (size_t)k * N + c;
+    for (int q = 0; q < 3; ++q) {
+      const double e = cs.gE[q * WN + at];
+      z[q] += e;
+      const df ev = df_from_double(e), lv = df_from_double(cs.cL[q * WN + at] * s);
+      E2[q * WN + at] = make_float2(ev.hi, ev.lo);
+      L2[q * WN + at] = make_float2(lv.hi, lv.lo);
+    }
+  }
+  const double rv = 1.0 / cs.V[c];
+  for (int k = cs.b_start[c]; k < cs.b_start[c + 1]; ++k) {
+    const int bf = cs.b_face[k];
+    if (cs.btype[bf] == LFM_FIXED_VALUE)
+      for (int q = 0; q < 3; ++q) z[q] += cs.bSf[3 * (size_t)bf + q] * rv;
+  }
+  for (int q = 0; q < 3; ++q) Z[q * N + c] = z[q];
+}
+
 __global__ void df_vdt_kernel(CaseDev cs, float2* __restrict__ vdt2) {
   const int c = blockIdx.x * blockDim.x + threadIdx.x;
   if (c < cs.N) st_df(vdt2 + c, df_from_double(__dmul_rn(cs.vdt[c], cs.df_scale)));
@@ -323,6 +357,9 @@ cudaError_t launch_df_setup(const CaseDev& cs, cudaStream_t stream) {
   }
   if (cs.F > 0) df_coef_kernel<<<(cs.F + 255) / 256, 256, 0, stream>>>(cs, g2);
   df_vdt_kernel<<<(cs.N + 255) / 256, 256, 0, stream>>>(cs, const_cast<float2*>(cs.vdt2));
+  if (cs.Sf && cs.gE2)
+    df_ops_kernel<<<(cs.N + 255) / 256, 256, 0, stream>>>(cs, const_cast<float2*>(cs.gE2), const_cast<float2*>(cs.cK2),
+                                                          const_cast<float2*>(cs.cL2), const_cast<double*>(cs.gZ));
   return cudaGetLastError();
 }
 

@@ -112,10 +112,12 @@ class Solver:
 
     def configure(self, case: lapcase.RawCase, field: bool = True):
         m = self.mesh
-        if m.DT_faces is None:
-            if not (case.DTx is None and case.DTy is None and case.DTz is None):
-                raise ValueError("per-face DT needs a host mesh (Solver(mesh=...))")
+        if case.DTx is None and case.DTy is None and case.DTz is None:
+            # the case's own uniform DT (a host mesh shared between cases carries the
+            # diffusivity of the case it was built from)
             B.lfm_set_diffusivity(self.ctx, float(case.DT_uniform), None, None)
+        elif m.DT_faces is None:
+            raise ValueError("per-face DT needs a host mesh built from the case (Solver(mesh=...))")
         else:
             B.lfm_set_diffusivity(self.ctx, 0.0, m.DT_faces, m.DT_bfaces)
         for p, (ptype, value) in enumerate(case.patches):

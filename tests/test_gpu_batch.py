@@ -151,3 +151,47 @@ def oracle_cached(c):
     if key not in _ORACLE:
         _ORACLE[key] = oracle.advance(c)
     return _ORACLE[key]
+
+
+def test_batch512_full_size_sampled_against_oracle():
+    # the batched workload at full size (512 cases, edge log-uniform 16..96, 10 steps, 85.8 M
+    # cells), in the launch shape the bench's autotuner picks, graph-replayed steps; a seeded
+    # sample of cases (the largest among them) against the oracle cell by cell
+    from paper_2507_18268_gb300.mesh import box_mesh
+    cases = lapcase.batch_cases(n_cases=512, seed=3, n_steps=10)
+    meshes = {}
+    with Batch() as bt:
+        ids = []
+        for c in cases:
+            key = (c.nx, c.ny, c.nz)
+            if key not in meshes:
+                meshes[key] = box_mesh(c)
+            ids.append(bt.add_case(c, mesh=meshes[key]))
+        bt.autotune()
+        for cid, c in zip(ids, cases):  # the autotuner advanced the cases: restart them
+            bt.cases[cid].set_field(oracle.initial_field(c))
+        assert bt.advance(10, use_graph=True) == B.LFM_OK
+        rng = np.random.default_rng(11)
+        pick = set(rng.choice(len(cases), size=6, replace=False).tolist())
+        pick.add(int(np.argmax([c.n_cells for c in cases])))
+        for i in sorted(pick):
+            To, so = oracle.advance(cases[i])
+            st = bt.stats(ids[i], 10)
+            assert [x["iters"] for x in st] == [x.iters for x in so], i
+            assert relerr(bt.field(ids[i]), To) <= 1e-10, i
+
+
+def test_cases_sharing_a_host_mesh_keep_their_own_diffusivity():
+    # one host mesh object serves several cases of the same box: each case's own DT, dt and
+    # boundary values reach the device
+    from paper_2507_18268_gb300.mesh import box_mesh
+    cases = lapcase.batch_cases(n_cases=6, seed=17, n_min=12, n_max=12, n_steps=3)
+    m = box_mesh(cases[0])
+    assert len({(c.nx, c.ny, c.nz) for c in cases}) == 1 and len({c.DT_uniform for c in cases}) == 6
+    with Batch() as bt:
+        ids = [bt.add_case(c, mesh=m) for c in cases]
+        assert bt.advance(3) == B.LFM_OK
+        for cid, c in zip(ids, cases):
+            To, so = oracle.advance(c)
+            assert relerr(bt.field(cid), To) <= 1e-10
+            assert [x["iters"] for x in bt.stats(cid, 3)] == [x.iters for x in so]

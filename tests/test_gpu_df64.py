@@ -200,13 +200,25 @@ def test_df64_sources_and_correctors_on_orthogonal_mesh():
     assert [x["iters"] for x in st] == [x.iters for x in so]
 
 
-def test_df64_refused_for_general_geometry():
-    base = lapcase.random_small_case(3, nx=4, ny=4, nz=4, permute=False)
-    case = lapcase.perturbed_box(base, amp=0.2, seed=3)
-    with Solver.from_case(case) as s:
+def test_df64_general_geometry_in_a_df64_only_workspace():
+    # general geometry with the df64 form in a workspace laid out for it alone, and in a batch
+    base = lapcase.random_small_case(3, nx=6, ny=5, nz=4, permute=False)
+    case = lapcase.perturbed_box(base, amp=0.2, seed=3).with_(tol=1e-10, n_steps=3, precision=lapcase.DF64)
+    To, so = oracle.advance(case)
+    with Solver.from_case(case, layout=B.LFM_DF64) as s:
+        st = s.advance(case.n_steps)
+        T = s.field()
+    assert relerr(T, To) <= RTOL
+    with Solver.from_case(case.with_(precision=lapcase.MIXED), layout=B.LFM_MIXED) as s:
         with pytest.raises(B.LfmError) as e:
             s.set_solver(case.tol, 0.0, 1000, 0, B.LFM_DF64)
-        assert e.value.code == B.LFM_EINVAL
+        assert e.value.code == B.LFM_ENOMEM
+    with Batch() as bt:
+        ids = [bt.add_case(case), bt.add_case(case.with_(precision=lapcase.FP64))]
+        bt.set_launch(256, (1, 1, 1))
+        assert bt.advance(case.n_steps) == B.LFM_OK
+        for cid in ids:
+            assert relerr(bt.field(cid), To) <= RTOL
 
 
 def test_df64_batched_matches_alone_and_oracle():

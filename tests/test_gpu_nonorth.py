@@ -2,7 +2,7 @@
 gradient (lfm_grad), the corrected assembly and the non-orthogonal corrector passes, in
 FP64, mixed precision, several launch shapes and the batched form (GPU required).
 
-Bars: FP64 fields within 1e-10 of the oracle and iteration counts within one per step
+Bars: FP64 and df64 fields within 1e-10 of the oracle and iteration counts within one per step
 (the gradient divides by V through a rounded reciprocal, so the correction term -- and
 with it the source -- agrees to rounding, not bitwise); the implicit matrix bitwise; the
 gradient within 1e-12; mixed precision within 1e-5 of the FP64 oracle.
@@ -62,6 +62,27 @@ def test_fp64_parity(name):
         assert abs(a["iters"] - b.iters) <= 1, (a, b)
         assert a["converged"] == 1
         assert abs(a["init_res"] - b.init_res) <= 1e-8 * b.init_res
+
+
+@pytest.mark.parametrize("name", list(CASES))
+def test_df64_parity(name):
+    # the df64 form on general meshes: gradient in difference form, correction in df64
+    case = CASES[name]()
+    To, so = oracle.advance(case)
+    T, st = gpu_advance(case, precision=B.LFM_DF64)
+    assert rel(T, To) <= 1e-10, name
+    for a, b in zip(st, so):
+        assert abs(a["iters"] - b.iters) <= 1, (a, b)
+        assert a["converged"] == 1
+        assert abs(a["init_res"] - b.init_res) <= 1e-8 * b.init_res
+
+
+@pytest.mark.parametrize("launch", [(1, 256), (7, 512), (0, 1024)])
+def test_df64_parity_launch_shapes(launch):
+    case = CASES["perturbed40"]()
+    To, _ = oracle.advance(case)
+    T, _ = gpu_advance(case, precision=B.LFM_DF64, launch=launch)
+    assert rel(T, To) <= 1e-10
 
 
 @pytest.mark.parametrize("launch", [(1, 256), (3, 512), (0, 1024)])
