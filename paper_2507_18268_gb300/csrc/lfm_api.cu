@@ -494,7 +494,7 @@ void bind_pointers(lfm_ctx* c) {
   cs.gE2 = fg ? reinterpret_cast<const float2*>(b + L.gE2) : nullptr;
   cs.cK2 = fg ? reinterpret_cast<const float2*>(b + L.cK2) : nullptr;
   cs.cL2 = fg ? reinterpret_cast<const float2*>(b + L.cL2) : nullptr;
-  cs.gZ = fg ? reinterpret_cast<const double*>(b + L.gZ) : nullptr;
+  cs.gZ = fg ? reinterpret_cast<const float2*>(b + L.gZ) : nullptr;
   cs.grad2 = fg ? reinterpret_cast<float2*>(b + L.grad2) : nullptr;
   cs.diag2 = f ? reinterpret_cast<float2*>(b + L.diag2) : nullptr;
   cs.rD2 = f ? reinterpret_cast<float2*>(b + L.rD2) : nullptr;

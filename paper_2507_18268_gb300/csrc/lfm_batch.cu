@@ -60,7 +60,7 @@ __global__ void __launch_bounds__(B, 1024 / B) batch_kernel(const CaseDev* __res
     if (s_cs.precision == LFM_MIXED)
       run_steps_mixed_any<B, W>(s_cs, s_cs, tm, n_steps, kModeSteps, sh, base);
     else if (s_cs.precision == LFM_DF64)
-      run_steps_df64<B, W>(s_cs, s_cs, tm, n_steps, sh, base);
+      run_steps_df64<B, W, true>(s_cs, s_cs, tm, n_steps, sh, base);
     else
       run_steps_f64<B, W>(s_cs, s_cs, tm, n_steps, kModeSteps, sh, base);
     __syncthreads();

@@ -136,12 +136,12 @@ struct CaseDev {
   double df_scale;
   // df64 form on general geometry: the operator weights gE (gradient) and cK, cL (correction,
   // times df_scale) as pairs, the closure weight gZ = gD + sum_k gE_k + sum_fixedValue bSf / V
-  // (FP64; zero for a closed cell up to rounding) of the gradient's difference form, and the
-  // gradient itself (component-major as the FP64 arrays)
+  // (formed in FP64; zero for a closed cell up to rounding) of the gradient's difference form,
+  // and the gradient itself (component-major as the FP64 arrays)
   const float2* gE2;         // [3*W*N]
   const float2* cK2;         // [3N]
   const float2* cL2;         // [3*W*N]
-  const double* gZ;          // [3N]
+  const float2* gZ;          // [3N]   (pairs of the FP64 closure weight)
   float2* grad2;             // [3N]
 
   // team state

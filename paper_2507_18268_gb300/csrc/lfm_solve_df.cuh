@@ -153,7 +153,7 @@ __device__ __forceinline__ void row_boundary_df(const CaseDev& cs, int c, tf xc,
 // (equal to the operator form gD T_c + gH + sum_k gE_k T_k; see CaseDev): a weighted sum of
 // T values that nearly cancel would carry their rounding, ~2^-48 |T| / h, into the explicit
 // correction; differences formed exactly from the triple-float field do not. The boundary
-// terms (boundary cells only) and gZ T_c (gZ is zero up to the geometry's rounding) are FP64.
+// terms (boundary cells only) are FP64; gZ T_c (gZ is zero up to the geometry's rounding) df64.
 template <int B, int W>
 __device__ __noinline__ void pass_grad_df(const CaseDev& cs, int c0, int c1) {
   const float2* __restrict__ x2 = cs.x2;
@@ -173,11 +173,14 @@ __device__ __noinline__ void pass_grad_df(const CaseDev& cs, int c0, int c1) {
       g1 = df_fma(ldg_df(cs.gE2 + WN + at), d, g1);
       g2 = df_fma(ldg_df(cs.gE2 + 2 * WN + at), d, g2);
     }
-    const double xd = tf_to_double(xc);
-    double b0 = cs.gZ[c] * xd, b1 = cs.gZ[N + c] * xd, b2 = cs.gZ[2 * N + c] * xd;
+    const df xcd = tf_to_df(xc);
+    g0 = df_fma(ldg_df(cs.gZ + c), xcd, g0);
+    g1 = df_fma(ldg_df(cs.gZ + N + c), xcd, g1);
+    g2 = df_fma(ldg_df(cs.gZ + 2 * N + c), xcd, g2);
     const int k0 = __ldg(cs.b_start + c), k1 = __ldg(cs.b_start + c + 1);
-    if (k0 != k1) {
-      const double rv = 1.0 / cs.V[c];
+    if (k0 != k1) {  // boundary cells: the fixedValue faces' terms in FP64
+      const double xd = tf_to_double(xc), rv = 1.0 / cs.V[c];
+      double b0 = 0.0, b1 = 0.0, b2 = 0.0;
       for (int k = k0; k < k1; ++k) {
         const int bf = __ldg(cs.b_face + k);
         if (__ldg(cs.btype + bf) == LFM_FIXED_VALUE) {
@@ -187,10 +190,13 @@ __device__ __noinline__ void pass_grad_df(const CaseDev& cs, int c0, int c1) {
           b2 = fma(cs.bSf[3 * (size_t)bf + 2], dT, b2);
         }
       }
+      g0 = df_add(g0, df_from_double(b0));
+      g1 = df_add(g1, df_from_double(b1));
+      g2 = df_add(g2, df_from_double(b2));
     }
-    st_df(cs.grad2 + c, df_add(g0, df_from_double(b0)));
-    st_df(cs.grad2 + N + c, df_add(g1, df_from_double(b1)));
-    st_df(cs.grad2 + 2 * N + c, df_add(g2, df_from_double(b2)));
+    st_df(cs.grad2 + c, g0);
+    st_df(cs.grad2 + N + c, g1);
+    st_df(cs.grad2 + 2 * N + c, g2);
   }
 }
 
@@ -451,7 +457,7 @@ __device__ __forceinline__ double2 pass_update_df(int c0, int c1, df alpha, floa
 // The steps of one launch. Returns false when a barrier failed (the caller leaves).
 // `pending` tracks whether e holds a correction not yet added to the field (the same in every
 // CTA: it follows the team-wide iteration counts).
-template <int B, int W>
+template <int B, int W, bool kGeom>
 __device__ bool steps_df64(const CaseDev& cs, const CaseDev& cref, const Team& tm, int n_steps, TeamShared& sh,
                            int stats_base, int c0, int c1, bool& pending) {
   const int tid = threadIdx.x;
@@ -464,7 +470,7 @@ __device__ bool steps_df64(const CaseDev& cs, const CaseDev& cref, const Team& t
   const double inv_scale = 1.0 / cs.df_scale;  // a power of two: exact
 
   PhaseClock clk(cs, tm);
-  const bool src_mode = cs.n_corr > 0 || cs.vSu != nullptr || cs.vSp != nullptr || cs.Sf != nullptr;
+  const bool src_mode = cs.n_corr > 0 || cs.vSu != nullptr || cs.vSp != nullptr || (kGeom && cs.Sf != nullptr);
   bool convert = ld_volatile_i32(cs.flags) == 0;  // read by every CTA before the first barrier
   for (int step = 0; step < n_steps; ++step) {
     int iters_tot = 0, solves = 0, status = 0;
@@ -477,9 +483,11 @@ __device__ bool steps_df64(const CaseDev& cs, const CaseDev& cref, const Team& t
       pending = false;
       if (!team_allreduce<1>(tm, v, sh)) return false;
       mark_split(cs, tm, convert);
-      if (cs.Sf) {  // ---- G: the gradient of the (folded) field, for the correction ----------
-        pass_grad_df<B, W>(cref, c0, c1);
-        if (!team_barrier(tm, sh)) return false;
+      if constexpr (kGeom) {
+        if (cs.Sf) {  // ---- G: the gradient of the (folded) field, for the correction --------
+          pass_grad_df<B, W>(cref, c0, c1);
+          if (!team_barrier(tm, sh)) return false;
+        }
       }
       clk.lap(kPhAssembly);
       // ---- R: rows, initial residual, normFactor, first direction ----------------------
@@ -845,14 +853,15 @@ __device__ void run_steps_mixed_any(const CaseDev& cs, const CaseDev& cref, cons
     run_steps_mixed_df<B, W>(cs, cref, tm, n_steps, sh, stats_base);
 }
 
-template <int B, int W>
+// kGeom: the kernel serves general geometry (the gradient phase is compiled in).
+template <int B, int W, bool kGeom = false>
 __device__ void run_steps_df64(const CaseDev& cs, const CaseDev& cref, const Team& tm, int n_steps, TeamShared& sh,
                                int stats_base = 0) {
   if (n_steps <= 0) return;
   int c0, c1;
   cta_range(cs.N, tm.size, tm.rank, c0, c1);
   bool pending = false;
-  steps_df64<B, W>(cs, cref, tm, n_steps, sh, stats_base, c0, c1, pending);
+  steps_df64<B, W, kGeom>(cs, cref, tm, n_steps, sh, stats_base, c0, c1, pending);
   // the field and the correction of the CTA's own cells are written by this CTA only, so the
   // FP64 field can be written back without another barrier, also after an early exit.
   pass_store_x<B>(cref, c0, c1, pending);

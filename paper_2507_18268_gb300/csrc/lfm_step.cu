@@ -45,7 +45,7 @@ __global__ void __launch_bounds__(B, 1024 / B) step_kernel_mixed_df(CaseDev cs, 
   run_steps_mixed_df<B, W>(cs, s_cs, tm, n_steps, sh);
 }
 
-template <int B, int W>
+template <int B, int W, bool kGeom>
 __global__ void __launch_bounds__(B, 1024 / B) step_kernel_df64(CaseDev cs, Launch L, int n_steps, int mode) {
   __shared__ TeamShared sh;
   __shared__ CaseDev s_cs;  // addressable copy for the per-step passes
@@ -53,7 +53,7 @@ __global__ void __launch_bounds__(B, 1024 / B) step_kernel_df64(CaseDev cs, Laun
   if (threadIdx.x == 0) s_cs = cs;
   __syncthreads();
   const Team tm{(int)gridDim.x, (int)blockIdx.x, cs.sync, cs.partials, L.timeout_ns};
-  run_steps_df64<B, W>(cs, s_cs, tm, n_steps, sh);
+  run_steps_df64<B, W, kGeom>(cs, s_cs, tm, n_steps, sh);
 }
 
 // Set-up (a0): per face g = (DT |Sf|) deltaCoeff (the assembly's products, in its order),
@@ -93,7 +93,7 @@ __global__ void df_coef_kernel(CaseDev cs, float2* __restrict__ g2) {
 // G_c = sum_k gE_k (T_k - T_c) + sum_fixedValue (bSf / V)(T_b - T_c) + gZ T_c equals the
 // operator form gD T_c + gH + sum_k gE_k T_k.
 __global__ void df_ops_kernel(CaseDev cs, float2* __restrict__ E2, float2* __restrict__ K2, float2* __restrict__ L2,
-                              double* __restrict__ Z) {
+                              float2* __restrict__ Z) {
   const int c = blockIdx.x * blockDim.x + threadIdx.x;
   if (c >= cs.N) return;
   const size_t N = (size_t)cs.N, WN = (size_t)cs.W * N;
@@ -119,7 +119,10 @@ __global__ void df_ops_kernel(CaseDev cs, float2* __restrict__ E2, float2* __res
     if (cs.btype[bf] == LFM_FIXED_VALUE)
       for (int q = 0; q < 3; ++q) z[q] += cs.bSf[3 * (size_t)bf + q] * rv;
   }
-  for (int q = 0; q < 3; ++q) Z[q * N + c] = z[q];
+  for (int q = 0; q < 3; ++q) {
+    const df v = df_from_double(z[q]);
+    Z[q * N + c] = make_float2(v.hi, v.lo);
+  }
 }
 
 __global__ void df_vdt_kernel(CaseDev cs, float2* __restrict__ vdt2) {
@@ -277,20 +280,24 @@ __global__ void fill_kernel(double* a, size_t n, double v) {
   for (; i < n; i += stride) a[i] = v;
 }
 
-// kMixedDf: the mixed form with df64 outer passes (a precision code for kernel choice only).
+// Kernel-choice codes beside the public precisions: the mixed form with df64 outer passes,
+// and the df64 form on general geometry (the orthogonal df64 kernel carries no gradient phase).
 constexpr int kMixedDf = 100;
+constexpr int kDf64Geom = 101;
 
 template <int B>
 void* step_fn_w(int precision, int W) {
   if (W == 6) {
     if (precision == kMixedDf) return (void*)step_kernel_mixed_df<B, 6>;
     if (precision == LFM_MIXED) return (void*)step_kernel_mixed<B, 6>;
-    if (precision == LFM_DF64) return (void*)step_kernel_df64<B, 6>;
+    if (precision == kDf64Geom) return (void*)step_kernel_df64<B, 6, true>;
+    if (precision == LFM_DF64) return (void*)step_kernel_df64<B, 6, false>;
     return (void*)step_kernel_f64<B, 6>;
   }
   if (precision == kMixedDf) return (void*)step_kernel_mixed_df<B, 0>;
   if (precision == LFM_MIXED) return (void*)step_kernel_mixed<B, 0>;
-  if (precision == LFM_DF64) return (void*)step_kernel_df64<B, 0>;
+  if (precision == kDf64Geom) return (void*)step_kernel_df64<B, 0, true>;
+  if (precision == LFM_DF64) return (void*)step_kernel_df64<B, 0, false>;
   return (void*)step_kernel_f64<B, 0>;
 }
 
@@ -310,12 +317,11 @@ int max_coresident_ctas(int precision, int threads, int W, int device) {
   if (!fn) return 0;
   int per_sm = 0, sms = 0;
   if (cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, fn, threads, 0) != cudaSuccess) return 0;
-  if (precision == LFM_MIXED) {  // either mixed kernel may run: the smaller residency
-    int per_sm_df = 0;
-    if (cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm_df, step_fn_for(kMixedDf, threads, W), threads, 0) !=
-        cudaSuccess)
-      return 0;
-    if (per_sm_df < per_sm) per_sm = per_sm_df;
+  if (precision == LFM_MIXED || precision == LFM_DF64) {  // either kernel of the form may run
+    int per_sm_2 = 0;
+    void* fn2 = step_fn_for(precision == LFM_MIXED ? kMixedDf : kDf64Geom, threads, W);
+    if (cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm_2, fn2, threads, 0) != cudaSuccess) return 0;
+    if (per_sm_2 < per_sm) per_sm = per_sm_2;
   }
   if (cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, device) != cudaSuccess) return 0;
   int n = per_sm * sms;
@@ -328,7 +334,8 @@ cudaError_t launch_steps(const CaseDev& cs, const Launch& L, int n_steps, int mo
   int prec = (mode == kModeAssembleOnly && cs.precision == LFM_DF64) ? LFM_FP64 : cs.precision;
   // the mixed form runs its outer passes in df64 when the case allows (see mixed_uses_df)
   const bool mixed_df = prec == LFM_MIXED && mode == kModeSteps && mixed_runs_df(cs);
-  void* fn = step_fn_for(mixed_df ? kMixedDf : prec, L.threads, cs.W);
+  const bool df_geom = prec == LFM_DF64 && cs.Sf != nullptr;
+  void* fn = step_fn_for(mixed_df ? kMixedDf : (df_geom ? kDf64Geom : prec), L.threads, cs.W);
   if (!fn) return cudaErrorInvalidValue;
   CaseDev a0 = cs;
   a0.precision = prec;
@@ -359,7 +366,7 @@ cudaError_t launch_df_setup(const CaseDev& cs, cudaStream_t stream) {
   df_vdt_kernel<<<(cs.N + 255) / 256, 256, 0, stream>>>(cs, const_cast<float2*>(cs.vdt2));
   if (cs.Sf && cs.gE2)
     df_ops_kernel<<<(cs.N + 255) / 256, 256, 0, stream>>>(cs, const_cast<float2*>(cs.gE2), const_cast<float2*>(cs.cK2),
-                                                          const_cast<float2*>(cs.cL2), const_cast<double*>(cs.gZ));
+                                                          const_cast<float2*>(cs.cL2), const_cast<float2*>(cs.gZ));
   return cudaGetLastError();
 }
 
