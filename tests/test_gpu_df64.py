@@ -313,3 +313,31 @@ def test_df64_and_mixed_at_extreme_scales(kind):
         s.advance(case.n_steps)
         Tm = s.field()
     assert float(np.max(np.abs(Tm - To))) <= 1e-5 * scale
+
+
+@pytest.mark.parametrize("prec", [B.LFM_DF64, B.LFM_MIXED])
+def test_timeout_and_nonfinite_in_the_df64_forms(prec):
+    # a CTA that never arrives makes the others' bounded waits run out: LFM_ETIMEOUT, and the
+    # same context then solves correctly (no GPU fault: the kernel returns)
+    case = CASES["permuted20"]().with_(precision=prec)
+    To, _ = oracle.advance(case)
+    with Solver.from_case(case) as s:
+        s.set_launch(4, 256)
+        B.lfm_set_barrier_timeout(s.ctx, 200_000_000)  # 0.2 s
+        B.lfm_debug_skip_arrival(s.ctx, 1)
+        B.lfm_advance_async(s.ctx, 1)
+        rc, _ = B.lfm_finish_status(s.ctx, 1)
+        assert rc == B.LFM_ETIMEOUT
+        s.set_field(oracle.initial_field(case))
+        s.advance(case.n_steps)
+        T = s.field()
+    tol = RTOL if prec == B.LFM_DF64 else 1e-5
+    assert relerr(T, To) <= tol
+    # a non-finite field is reported, not propagated silently
+    with Solver.from_case(case) as s:
+        T0 = oracle.initial_field(case)
+        T0[7] = np.nan
+        s.set_field(T0)
+        with pytest.raises(B.LfmError) as e:
+            s.advance(1)
+        assert e.value.code == B.LFM_ENONFINITE
