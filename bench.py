@@ -454,7 +454,7 @@ def main_ours(args, world, rank, local):
                                "peak": FP64_NOMINAL_TFLOPS, "unit": "TFLOP/s",
                                "frac": algorithmic_flops(N, F, iters, K) / secs / 1e12 / FP64_NOMINAL_TFLOPS,
                                "peak_kind": "nominal (1.25 TFLOP/s dense FP64)",
-                               "note": "ncu: FP64 pipe 70% busy, DRAM 65% (profiles/step_kernel_f64_graded200.md)"},
+                               "note": "ncu: FP64 pipe 73% busy, DRAM 62% (profiles/step_kernel_f64_graded200.md)"},
         "gpu_launches": 1,
         "clocks": clk,
         "df64": df64,
