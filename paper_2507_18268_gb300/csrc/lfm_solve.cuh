@@ -12,10 +12,12 @@
 // two cells per loop trip and issues all their loads before using any, so that each thread
 // keeps a dozen independent memory requests in flight.
 //
+// The face coefficients -g, g = DT |Sf| deltaCoeff, depend on the mesh and DT only: the
+// set-up kernel (coef_kernel, lfm_step.cu) stores them at both of each face's slots when
+// those change; the step kernel assembles faces itself only for matrix read-back.
+//
 // FP64 step (phases separated by team barriers):
-//   A1 faces           per owned face g = DT |Sf| deltaCoeff, stored at both of its cells'
-//                      slots (the face-indexed LDU `upper` is written only for matrix
-//                      read-back); sum x for xRef
+//   A1 sum             sum x for xRef
 //   A2+I rows          diag, source, rD = 1/diag, row sum; from the same loaded row
 //                      A x, r = b - A x, normFactor, sum|r|, w = rD r, rho; p = w (first
 //                      search direction). The source is needed by no later phase of an
@@ -32,10 +34,11 @@
 // the patches or DT change. With n_corr > 0 every step runs 1 + n_corr assemble-and-solve
 // passes, the ddt source taken from T at the start of the step (x_old).
 //
-// Mixed step (defect correction, FP64 field x): the matrix is assembled in FP64 and copied
-// to FP32; each sweep computes the FP64 true residual r = b - A x (the first one in the
-// assembly's row pass), solves A dx = r by the
-// same CG recurrence on FP32 vectors with FP32 row sums, and adds dx to x in FP64. Dot
+// Mixed step (defect correction, FP64 field x; on orthogonal meshes the df64 variant in
+// lfm_solve_df.cuh runs instead): the matrix is assembled in FP64 with FP32 copies of the
+// diagonal and 1/diag (the FP32 off-diagonals are set-up data); each sweep computes the FP64
+// true residual r = b - A x (the first one in the assembly's row pass), solves A dx = r by
+// the same CG recurrence on FP32 vectors with FP32 row sums, and adds dx to x in FP64. Dot
 // products, sum|r|, normFactor and every convergence test are FP64-accurate: FP64 for the
 // FP64 quantities; for FP32 terms, exact products summed as unevaluated FP32 pairs per
 // thread and FP64 across threads (see Acc2f).
@@ -308,7 +311,7 @@ __device__ __noinline__ double pass_faces(const CaseDev& cs, int f0, int f1, int
   return v;
 }
 
-// Gauss gradient of T over the cells [c0, c1) into cs.grad (same phase as the face pass:
+// Gauss gradient of T over the cells [c0, c1) into cs.grad (same phase as the sum of T:
 // it reads only T and the operator weights).
 template <int B, int W>
 __device__ __noinline__ void pass_grad(const CaseDev& cs, int c0, int c1) {
@@ -646,9 +649,10 @@ __device__ __forceinline__ void write_stats(const CaseDev& cs, const Team& tm, i
   }
 }
 
-// Start of an assembly: the face pass (with the copy of T at the start of the step when
-// save_old, and with general geometry the Gauss gradient in the same phase) and the team sum
-// of T for xRef. False when a barrier failed (the caller leaves the kernel).
+// Start of an assembly: the per-thread sums of T (with the faces for matrix read-back, the
+// copy of T at the start of the step when save_old, and with general geometry the Gauss
+// gradient in the same phase) and their team sum for xRef. False when a barrier failed (the
+// caller leaves the kernel).
 template <int B, int W, bool kMixed>
 __device__ __forceinline__ bool assemble_prologue(const CaseDev& cs, const CaseDev& cref, const Team& tm, int c0,
                                                   int c1, int f0, int f1, bool write_upper, bool save_old,
