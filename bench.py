@@ -43,9 +43,8 @@ WORKLOAD = ("graded200: 200^3 unit box graded 1.02x per cell in x (8.0M cells, 2
 # Sources of each step kernel's arithmetic and memory traffic: a stored ncu traffic ratio is
 # used only while these are unchanged since the capture.
 KERNEL_SOURCES = {
-    "fp64": ["csrc/lfm_solve.cuh", "csrc/lfm_device.cuh", "csrc/lfm_internal.h"],
-    "df64": ["csrc/lfm_solve_df.cuh", "csrc/lfm_df64.cuh", "csrc/lfm_solve.cuh", "csrc/lfm_device.cuh",
-             "csrc/lfm_internal.h"],
+    "fp64": ["csrc/lfm_solve.cuh", "csrc/lfm_device.cuh"],
+    "df64": ["csrc/lfm_solve_df.cuh", "csrc/lfm_df64.cuh", "csrc/lfm_solve.cuh", "csrc/lfm_device.cuh"],
 }
 
 
@@ -102,7 +101,8 @@ def load_traffic_ratio(name: str):
         return None
     with open(p) as f:
         d = json.load(f)
-    if d.get("kernel_hash") != kernel_hash("df64" if "df64" in name else "fp64"):
+    family = "df64" if ("df64" in name or "mixed" in name) else "fp64"  # the mixed kernel runs df64 outer passes
+    if d.get("kernel_hash") != kernel_hash(family):
         return None
     return float(d["dram_bytes"]) / float(d["algorithmic_bytes"])
 
