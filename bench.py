@@ -45,6 +45,8 @@ WORKLOAD = ("graded200: 200^3 unit box graded 1.02x per cell in x (8.0M cells, 2
 KERNEL_SOURCES = {
     "fp64": ["csrc/lfm_solve.cuh", "csrc/lfm_device.cuh"],
     "df64": ["csrc/lfm_solve_df.cuh", "csrc/lfm_df64.cuh", "csrc/lfm_solve.cuh", "csrc/lfm_device.cuh"],
+    "mixed": ["csrc/lfm_solve_mixed_df.cuh", "csrc/lfm_solve_df.cuh", "csrc/lfm_df64.cuh", "csrc/lfm_solve.cuh",
+              "csrc/lfm_device.cuh"],
 }
 
 
@@ -101,7 +103,7 @@ def load_traffic_ratio(name: str):
         return None
     with open(p) as f:
         d = json.load(f)
-    family = "df64" if ("df64" in name or "mixed" in name) else "fp64"  # the mixed kernel runs df64 outer passes
+    family = "mixed" if "mixed" in name else ("df64" if "df64" in name else "fp64")
     if d.get("kernel_hash") != kernel_hash(family):
         return None
     return float(d["dram_bytes"]) / float(d["algorithmic_bytes"])

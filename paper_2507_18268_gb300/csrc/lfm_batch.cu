@@ -15,6 +15,7 @@
 #include "lfm_internal.h"
 #include "lfm_solve.cuh"
 #include "lfm_solve_df.cuh"
+#include "lfm_solve_mixed_df.cuh"
 
 namespace lfm {
 namespace {

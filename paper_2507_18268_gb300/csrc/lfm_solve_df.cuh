@@ -37,8 +37,9 @@
 // matrix's off-diagonal part.
 //
 // Boundary faces (a few per cent of cells) are summed in FP64 and converted once per row;
-// so are the optional volumetric sources. General (non-orthogonal) geometry is served by the
-// FP64 and mixed forms only.
+// so are the optional volumetric sources. On general (non-orthogonal) geometry (kGeom) a
+// phase G after S forms the Gauss gradient of the field and R adds the explicit correction.
+// The mixed form's df64 outer passes are in lfm_solve_mixed_df.cuh.
 #pragma once
 
 #include <cuda_runtime.h>
@@ -552,305 +553,6 @@ __device__ bool steps_df64(const CaseDev& cs, const CaseDev& cref, const Team& t
     }
   }
   return true;
-}
-
-// =======================================================================================
-// Mixed form with df64 outer passes
-// =======================================================================================
-// The mixed form's defect correction (FP32 inner CG on A dx = r, FP64-class outer residual;
-// lfm_solve.cuh) with its outer passes in the df64 machinery: the field as a triple-float,
-// the true residual in flux form (T0 with the assembly of the rows, T1 after each
-// correction), the correction x += dx on the FP32 pipe. The inner solve works in the
-// unscaled units of the FP32 slot coefficients: T0 and T1 hand it r / s, diag / s and s / diag
-// (s the case's power-of-two scale, exact), and the scalars it tests are unscaled too.
-
-// T0: rows of the matrix (FP32 copies for the inner solve), the true residual (flux form),
-// normFactor terms, sum|r| (scaled; the caller unscales), and the seed of the inner solve:
-// r32 = r / s, w32 = rD32 r32, p32 = w32, dx32 = 0, rho = w32.r32 (FP32 pairs).
-template <int B, int W, bool kSrc>
-__device__ __noinline__ Sums3 pass_rows_init_mixed_df(const CaseDev& cs, int c0, int c1, double xRef, float s32,
-                                                      float inv_s32) {
-  const float2* __restrict__ x2 = cs.x2;
-  const float* __restrict__ xl = cs.xlo;
-  const float2* __restrict__ g2 = cs.g2;
-  const size_t N = (size_t)cs.N;
-  const df xr = df_from_scalar(xRef);
-  DfAcc a_nf, a_r;
-  Acc2f a_rho;
-  for (int c = c0 + (int)threadIdx.x; c < c1; c += B) {
-    const tf xc = ld_tf(x2, xl, c);
-    df d = mkdf(0.0f, 0.0f), flux = mkdf(0.0f, 0.0f);
-    if constexpr (W > 0) {
-      int o[W];
-      df g[W];
-#pragma unroll
-      for (int k = 0; k < W; ++k) {
-        o[k] = __ldg(cs.slot_other + (size_t)k * N + c);
-        g[k] = ldg_df(g2 + (size_t)k * N + c);
-      }
-      tf xo_[W];
-#pragma unroll
-      for (int k = 0; k < W; ++k) xo_[k] = ld_tf(x2, xl, o[k]);
-      d = g[0];
-#pragma unroll
-      for (int k = 1; k < W; ++k) d = df_add(d, g[k]);
-      flux = df_mul(g[0], tf_diff(xo_[0], xc));
-#pragma unroll
-      for (int k = 1; k < W; ++k) flux = df_fma(g[k], tf_diff(xo_[k], xc), flux);
-    } else {
-      for (int k = 0; k < cs.W; ++k) {
-        const size_t at = (size_t)k * N + c;
-        const df gk = ldg_df(g2 + at);
-        d = df_add(d, gk);
-        flux = df_fma(gk, tf_diff(ld_tf(x2, xl, __ldg(cs.slot_other + at)), xc), flux);
-      }
-    }
-    df gb, sb, fb;
-    row_boundary_df(cs, c, xc, gb, sb, fb);
-    const df vdt = ldg_df(cs.vdt2 + c);
-    const bool has_old = kSrc && cs.n_corr > 0;
-    const tf xo = has_old ? ld_tf(reinterpret_cast<const float2*>(cs.x_old), cs.xolo, c) : xc;
-    d = df_add(df_add(d, gb), vdt);
-    df src = df_fma(vdt, tf_to_df(xo), sb);
-    df sa = df_add(vdt, gb);
-    df rc = df_add(flux, fb);
-    if (has_old) rc = df_fma(vdt, tf_diff(xo, xc), rc);
-    if (kSrc && (cs.vSp || cs.vSu)) {
-      const double sp = cs.vSp ? cs.vSp[c] * cs.df_scale : 0.0;
-      const double su = cs.vSu ? cs.vSu[c] * cs.df_scale : 0.0;
-      const df vsp = df_from_double(sp);
-      d = df_sub(d, vsp);
-      sa = df_sub(sa, vsp);
-      src = df_add(src, df_from_double(su));
-      rc = df_add(rc, df_from_double(fma(sp, tf_to_double(xc), su)));
-    }
-    const df ax = df_sub(src, rc);
-    const df rd = df_rcp(d);
-    const df sx = df_mul(sa, xr);
-    a_nf.add(df_abs(df_sub(ax, sx)));
-    a_nf.add(df_abs(df_sub(src, sx)));
-    a_r.add(df_abs(rc));
-    const float rd32 = __fmul_rn(rd.hi, s32);
-    const float r32 = __fmul_rn(rc.hi, inv_s32);
-    const float w32 = __fmul_rn(rd32, r32);
-    a_rho.add_prod(w32, r32);
-    cs.diag32[c] = __fmul_rn(d.hi, inv_s32);
-    cs.rD32[c] = rd32;
-    cs.r32[c] = r32;
-    cs.w32[c] = w32;
-    cs.p32[c] = w32;
-    cs.dx32[c] = 0.0f;
-  }
-  return Sums3{a_nf.value(), a_r.value(), a_rho.value()};
-}
-
-// T1: the true residual after a correction, in flux form (x differs from the step's starting
-// field x_old now); sum|r| (scaled) and the seed of the next inner solve as in T0.
-template <int B, int W, bool kSrc>
-__device__ __noinline__ double2 pass_true_residual_df(const CaseDev& cs, int c0, int c1, float inv_s32) {
-  const float2* __restrict__ x2 = cs.x2;
-  const float* __restrict__ xl = cs.xlo;
-  const float2* __restrict__ g2 = cs.g2;
-  const size_t N = (size_t)cs.N;
-  DfAcc a_r;
-  Acc2f a_rho;
-  for (int c = c0 + (int)threadIdx.x; c < c1; c += B) {
-    const tf xc = ld_tf(x2, xl, c);
-    df flux = mkdf(0.0f, 0.0f);
-    if constexpr (W > 0) {
-      int o[W];
-      df g[W];
-#pragma unroll
-      for (int k = 0; k < W; ++k) {
-        o[k] = __ldg(cs.slot_other + (size_t)k * N + c);
-        g[k] = ldg_df(g2 + (size_t)k * N + c);
-      }
-      tf xo_[W];
-#pragma unroll
-      for (int k = 0; k < W; ++k) xo_[k] = ld_tf(x2, xl, o[k]);
-      flux = df_mul(g[0], tf_diff(xo_[0], xc));
-#pragma unroll
-      for (int k = 1; k < W; ++k) flux = df_fma(g[k], tf_diff(xo_[k], xc), flux);
-    } else {
-      for (int k = 0; k < cs.W; ++k) {
-        const size_t at = (size_t)k * N + c;
-        flux = df_fma(ldg_df(g2 + at), tf_diff(ld_tf(x2, xl, __ldg(cs.slot_other + at)), xc), flux);
-      }
-    }
-    df gb, sb, fb;
-    row_boundary_df(cs, c, xc, gb, sb, fb);
-    const tf xo = ld_tf(reinterpret_cast<const float2*>(cs.x_old), cs.xolo, c);
-    df rc = df_fma(ldg_df(cs.vdt2 + c), tf_diff(xo, xc), df_add(flux, fb));
-    if (kSrc && (cs.vSp || cs.vSu)) {
-      const double sp = cs.vSp ? cs.vSp[c] * cs.df_scale : 0.0;
-      const double su = cs.vSu ? cs.vSu[c] * cs.df_scale : 0.0;
-      rc = df_add(rc, df_from_double(fma(sp, tf_to_double(xc), su)));
-    }
-    a_r.add(df_abs(rc));
-    const float r32 = __fmul_rn(rc.hi, inv_s32);
-    const float w32 = __fmul_rn(cs.rD32[c], r32);
-    a_rho.add_prod(w32, r32);
-    cs.r32[c] = r32;
-    cs.w32[c] = w32;
-    cs.p32[c] = w32;
-    cs.dx32[c] = 0.0f;
-  }
-  return make_double2(a_r.value(), a_rho.value());
-}
-
-// x += dx (the triple-float field and the FP32 correction of the inner solve).
-template <int B>
-__device__ __noinline__ void pass_correct_df(const CaseDev& cs, int c0, int c1) {
-  float2* __restrict__ x2 = cs.x2;
-  float* __restrict__ xl = cs.xlo;
-  const float* __restrict__ dx = cs.dx32;
-  for (int c = c0 + (int)threadIdx.x; c < c1; c += B) st_tf(x2, xl, c, tf_add_df(ld_tf(x2, xl, c), mkdf(dx[c], 0.0f)));
-}
-
-// Whether the mixed form of this case runs its outer passes in df64: the df64 arrays are
-// present, the mesh is orthogonal and the scale is an FP32 power of two.
-__device__ __forceinline__ bool mixed_uses_df(const CaseDev& cs) {
-  return cs.x2 != nullptr && cs.Sf == nullptr && cs.df_scale >= 0x1p-100 && cs.df_scale <= 0x1p100;
-}
-
-template <int B, int W>
-__device__ bool steps_mixed_df(const CaseDev& cs, const CaseDev& cref, const Team& tm, int n_steps, TeamShared& sh,
-                               int stats_base, int c0, int c1) {
-  const int tid = threadIdx.x;
-  float* __restrict__ dx = cs.dx32;
-  float* __restrict__ r = cs.r32;
-  float* __restrict__ w = cs.w32;
-  float* __restrict__ p = cs.p32;
-  float* __restrict__ q = cs.q32;
-  const float* __restrict__ rD = cs.rD32;
-  const double inv_scale = 1.0 / cs.df_scale;  // a power of two: exact
-  const float s32 = (float)cs.df_scale, inv_s32 = (float)inv_scale;
-
-  PhaseClock clk(cs, tm);
-  const bool src_mode = cs.n_corr > 0 || cs.vSu != nullptr || cs.vSp != nullptr;
-  bool convert = ld_volatile_i32(cs.flags) == 0;  // read by every CTA before the first barrier
-  for (int step = 0; step < n_steps; ++step) {
-    int iters_tot = 0, sweeps_tot = 0, status = 0;
-    double nf0 = 0.0, init0 = 0.0, res = 0.0;
-    bool conv = false;
-    for (int pass = 0; pass <= cs.n_corr; ++pass) {
-      // ---- S: sum of x; the step's starting field (T1's ddt term) --------------------
-      double v[1] = {pass_sum_df<B>(cref, c0, c1, convert, false, pass == 0)};
-      if (!team_allreduce<1>(tm, v, sh)) return false;
-      mark_split(cs, tm, convert);
-      clk.lap(kPhAssembly);
-      const double xRef = v[0] / (double)cs.N;
-      double nf = 0.0, init_res = 0.0;
-      int iters = 0, sweeps = 0;
-      for (;;) {
-        // ---- T0 (rows + true residual) or T1 (true residual after a correction) ----------
-        double u[3];
-        if (sweeps == 0) {
-          const Sums3 ui = src_mode ? pass_rows_init_mixed_df<B, W, true>(cref, c0, c1, xRef, s32, inv_s32)
-                                    : pass_rows_init_mixed_df<B, W, false>(cref, c0, c1, xRef, s32, inv_s32);
-          u[0] = ui.a;
-          u[1] = ui.b;
-          u[2] = ui.c;
-        } else {
-          const double2 ut = src_mode ? pass_true_residual_df<B, W, true>(cref, c0, c1, inv_s32)
-                                      : pass_true_residual_df<B, W, false>(cref, c0, c1, inv_s32);
-          u[0] = 0.0;
-          u[1] = ut.x;
-          u[2] = ut.y;
-        }
-        if (!team_allreduce<3>(tm, u, sh)) return false;
-        clk.lap(kPhInit);
-        if (sweeps == 0) {
-          nf = (u[0] + kSmall * cs.df_scale) * inv_scale;
-          init_res = u[1] * inv_scale / nf;
-        }
-        res = u[1] * inv_scale / nf;
-        if (!isfinite(res)) {
-          status = LFM_ENONFINITE;
-          break;
-        }
-        const bool c_ok = converged(res, init_res, cs.tol, cs.rel_tol);
-        if ((c_ok && !(sweeps == 0 && cs.min_iter > 0)) || sweeps == kMaxSweeps || iters >= cs.max_iter) break;
-
-        // ---- inner FP32 CG on A dx = r (unscaled) -----------------------------------------
-        const double inner_tol = fmax(cs.tol, kInnerRel * res);
-        const int min_inner = sweeps == 0 ? cs.min_iter : 0;
-        double rho = u[2], beta = 0.0;
-        int k = 0;
-        for (;;) {
-          if (k > 0) {
-            pass_direction<B, float>(c0, c1, (float)beta, p, w);
-            if (!team_barrier(tm, sh)) return false;
-            clk.lap(kPhP);
-          }
-          double s1[1] = {pass_amul_dot_f32<B, W>(slots32(cs), c0, c1, p, q)};
-          if (!team_allreduce<1>(tm, s1, sh)) return false;
-          clk.lap(kPhM);
-          const double sigma = s1[0];
-          if (fabs(sigma) / nf < kVSmall) {
-            status = LFM_ESINGULAR;
-            break;
-          }
-          const double2 su = pass_update_f32<B>(c0, c1, (float)(rho / sigma), dx, r, w, p, q, rD);
-          double s2[2] = {su.x, su.y};
-          if (!team_allreduce<2>(tm, s2, sh)) return false;
-          clk.lap(kPhU);
-          const double inner_res = s2[0] / nf;
-          beta = s2[1] / rho;
-          rho = s2[1];
-          ++k;
-          ++iters;
-          if (!isfinite(inner_res)) {
-            status = LFM_ENONFINITE;
-            break;
-          }
-          const bool inner_conv = inner_res < inner_tol;
-          if (!((iters < cs.max_iter && !inner_conv) || k < min_inner)) break;
-        }
-        if (status != 0) break;
-        // ---- x += dx --------------------------------------------------------------------
-        pass_correct_df<B>(cref, c0, c1);
-        if (!team_barrier(tm, sh)) return false;
-        clk.lap(kPhCorrect);
-        ++sweeps;
-      }
-      conv = converged(res, init_res, cs.tol, cs.rel_tol);
-      if (pass == 0) {
-        nf0 = nf;
-        init0 = init_res;
-      }
-      iters_tot += iters;
-      sweeps_tot += sweeps;
-      if (status != 0) break;
-    }
-    write_stats(cs, tm, stats_base + step, iters_tot, conv ? 1 : 0, sweeps_tot, status, init0, res, nf0);
-    if (status != 0) {
-      if (tm.rank == 0 && tid == 0) set_status(cs.sync, status);
-      return true;
-    }
-  }
-  return true;
-}
-
-// The mixed form with df64 outer passes (the case must satisfy mixed_uses_df).
-template <int B, int W>
-__device__ void run_steps_mixed_df(const CaseDev& cs, const CaseDev& cref, const Team& tm, int n_steps,
-                                   TeamShared& sh, int stats_base = 0) {
-  if (n_steps <= 0) return;
-  int c0, c1;
-  cta_range(cs.N, tm.size, tm.rank, c0, c1);
-  steps_mixed_df<B, W>(cs, cref, tm, n_steps, sh, stats_base, c0, c1);
-  pass_store_x<B>(cref, c0, c1, false);
-}
-
-// The mixed form: df64 outer passes where mixed_uses_df, else FP64 ones (lfm_solve.cuh).
-template <int B, int W>
-__device__ void run_steps_mixed_any(const CaseDev& cs, const CaseDev& cref, const Team& tm, int n_steps, int mode,
-                                    TeamShared& sh, int stats_base = 0) {
-  if (mode != kModeSteps || !mixed_uses_df(cs))
-    run_steps_mixed<B, W>(cs, cref, tm, n_steps, mode, sh, stats_base);
-  else
-    run_steps_mixed_df<B, W>(cs, cref, tm, n_steps, sh, stats_base);
 }
 
 // kGeom: the kernel serves general geometry (the gradient phase is compiled in).

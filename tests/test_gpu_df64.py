@@ -283,6 +283,45 @@ def test_field_carried_between_launches(prec):
     assert np.array_equal(Te, Tf)
 
 
+@pytest.mark.parametrize("name,tol,max_iter,sweeps", [
+    ("plain20", None, 1000, "conv"),      # every step converges
+    ("permuted20", None, 1000, "more"),   # verifications that ask for another sweep
+    ("graded40", 1e-11, 1000, "more"),
+    ("graded40", None, 1, "cap"),         # steps that end at the iteration limit, not converged
+    ("graded40", None, 3, "any"),         # some steps end at the iteration limit
+])
+def test_mixed_fused_verification_bitwise(name, tol, max_iter, sweeps):
+    # In one launch every mixed step after the first starts from the previous step's
+    # verification pass (its rows and first residual formed there); one-step launches start
+    # each step with its own sum and row passes. Same field, same statistics, bit for bit.
+    case = CASES[name]().with_(precision=B.LFM_MIXED)
+    if tol is not None:
+        case = case.with_(tol=tol)
+    n = 5
+
+    def run(chunks):
+        with Solver.from_case(case) as s:
+            s.set_solver(case.tol, case.rel_tol, max_iter, case.min_iter, B.LFM_MIXED)
+            st = []
+            for k in chunks:
+                st += s.advance(k)
+            return s.field(), st
+
+    Ta, sa = run([n])
+    Tb, sb = run([1] * n)
+    assert np.array_equal(Ta, Tb)
+    assert sa == sb
+    most = max(s["sweeps"] for s in sa)
+    if sweeps == "conv":
+        assert all(s["converged"] for s in sa)
+    elif sweeps == "more":
+        assert most > 1 and all(s["converged"] for s in sa)
+    elif sweeps == "cap":
+        assert not all(s["converged"] for s in sa)
+    else:
+        assert all(s["iters"] <= max_iter for s in sa)
+
+
 def _scaled_case(kind):
     base = lapcase.random_small_case(41, nx=9, ny=7, nz=6).with_(tol=1e-10, n_steps=4)
     if kind == "celsius":
