@@ -333,6 +333,21 @@ __device__ __noinline__ void pass_rows_only(const CaseDev& cs, int c0, int c1) {
     store_row<kMixed>(cs, c, assemble_row<W, true>(cs, c, cs.x), true);
 }
 
+// ---- L2 prefetch --------------------------------------------------------------------
+// The streaming passes request the lines of their next loop trip into L2 before using the
+// current one. A prefetch holds no register, so it adds bytes in flight at the 64-register
+// occupancy the passes run at. Used where it measured faster: the P and U passes, and the
+// row passes of the df64 machinery (lfm_solve_df.cuh); not in A p, whose gathers it slowed.
+__device__ __forceinline__ void prefetch_l2(const void* p) { asm volatile("prefetch.global.L2 [%0];" ::"l"(p)); }
+
+// v[c + 2B] and v[c + 3B] (the cells of the next trip of a two-cells-per-trip loop), where
+// they are below c1.
+template <int B, typename T>
+__device__ __forceinline__ void pf_next(const T* v, int c, int c1) {
+  if (c + 2 * B < c1) prefetch_l2(v + c + 2 * B);
+  if (c + 3 * B < c1) prefetch_l2(v + c + 3 * B);
+}
+
 // ---- A v over the slot-major matrix (FP64 or FP32 copy) --------------------------------
 template <typename T>
 struct Slots {
@@ -414,6 +429,8 @@ template <int B, typename T>
 __device__ __forceinline__ void pass_direction(int c0, int c1, T beta, T* __restrict__ p, const T* __restrict__ w) {
   int c = c0 + (int)threadIdx.x;
   for (; c + B < c1; c += 2 * B) {
+    pf_next<B>(p, c, c1);
+    pf_next<B>(w, c, c1);
     const T p1 = p[c], p2 = p[c + B], w1 = w[c], w2 = w[c + B];
     p[c] = fmadd(beta, p1, w1);
     p[c + B] = fmadd(beta, p2, w2);
@@ -476,6 +493,11 @@ __device__ __forceinline__ double2 pass_update_f64(int c0, int c1, double alpha,
   double sa = 0.0, sr = 0.0;
   int c = c0 + (int)threadIdx.x;
   for (; c + B < c1; c += 2 * B) {
+    pf_next<B>(p, c, c1);
+    pf_next<B>(q, c, c1);
+    pf_next<B>(x, c, c1);
+    pf_next<B>(r, c, c1);
+    pf_next<B>(rD, c, c1);
     const int e = c + B;
     const double pa = p[c], pb = p[e], qa = q[c], qb = q[e];
     const double xa = x[c], xb = x[e], ra = r[c], rb = r[e], da = rD[c], db = rD[e];
@@ -514,6 +536,11 @@ __device__ __forceinline__ double2 pass_update_f32(int c0, int c1, float a32, fl
   Acc2f rsum, rho_n;
   int c = c0 + (int)threadIdx.x;
   for (; c + B < c1; c += 2 * B) {
+    pf_next<B>(p, c, c1);
+    pf_next<B>(q, c, c1);
+    pf_next<B>(dx, c, c1);
+    pf_next<B>(r, c, c1);
+    pf_next<B>(rD, c, c1);
     const int e = c + B;
     const float pa = p[c], pb = p[e], qa = q[c], qb = q[e];
     const float xa = dx[c], xb = dx[e], ra = r[c], rb = r[e], da = rD[c], db = rD[e];

@@ -224,6 +224,24 @@ __device__ __forceinline__ df op_corr_df(const CaseDev& cs, int c) {
   return v;
 }
 
+// L2 prefetch of what a row pass loads for row c before its gathers: the slot indices and
+// conductances, the field value and V/dt. Issued one trip ahead (c + B), it shortens the
+// dependent chain index -> neighbour value of the next row (row pass 0.32 -> 0.30 ms per
+// step on the 200^3 graded box).
+template <int W>
+__device__ __forceinline__ void prefetch_row_df(const CaseDev& cs, int c) {
+  const size_t N = (size_t)cs.N;
+  const int ns = W > 0 ? W : cs.W;
+  for (int k = 0; k < (W > 0 ? W : kMaxSlots); ++k) {
+    if (W == 0 && k >= ns) break;
+    prefetch_l2(cs.slot_other + (size_t)k * N + c);
+    prefetch_l2(cs.g2 + (size_t)k * N + c);
+  }
+  prefetch_l2(cs.x2 + c);
+  prefetch_l2(cs.xlo + c);
+  prefetch_l2(cs.vdt2 + c);
+}
+
 // R: rows of the matrix and, from the same loaded row, the initial residual, normFactor
 // terms, sum|r| and rho; p = w. kSrc: correctors (ddt source from x_old) or volumetric
 // sources present.
@@ -246,6 +264,7 @@ __device__ __noinline__ Sums3 pass_rows_init_df(const CaseDev& cs, int c0, int c
   const df xr = df_from_scalar(xRef);
   DfAcc a_nf, a_r, a_rho;
   for (int c = c0 + (int)threadIdx.x; c < c1; c += B) {
+    if (c + B < c1) prefetch_row_df<W>(cs, c + B);
     const tf xc = ld_tf(x2, xl, c);
     df d, flux;
     if constexpr (W > 0) {
@@ -376,6 +395,8 @@ __device__ __forceinline__ void pass_direction_df(int c0, int c1, df beta, float
                                                   const float2* __restrict__ w) {
   int c = c0 + (int)threadIdx.x;
   for (; c + B < c1; c += 2 * B) {
+    pf_next<B>(p, c, c1);
+    pf_next<B>(w, c, c1);
     const df p1 = ld_df(p + c), p2 = ld_df(p + c + B), w1 = ld_df(w + c), w2 = ld_df(w + c + B);
     st_df(p + c, df_fma(beta, p1, w1));
     st_df(p + c + B, df_fma(beta, p2, w2));

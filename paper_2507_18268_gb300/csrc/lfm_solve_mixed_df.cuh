@@ -111,6 +111,7 @@ __device__ __noinline__ Sums3 pass_rows_init_mixed_df(const CaseDev& cs, int c0,
   DfAcc a_nf, a_r;
   Acc2f a_rho;
   for (int c = c0 + (int)threadIdx.x; c < c1; c += B) {
+    if (c + B < c1) prefetch_row_df<W>(cs, c + B);
     const tf xc = ld_tf(cs.x2, cs.xlo, c);
     df d, flux;
     row_flux_df<W, true>(cs, c, xc, d, flux);
@@ -179,6 +180,7 @@ __device__ __noinline__ double4 pass_verify_next_df(const CaseDev& cs, int c0, i
   DfAcc a_v, a_nf, a_r;
   Acc2f a_rho;
   for (int c = c0 + (int)threadIdx.x; c < c1; c += B) {
+    if (c + B < c1) prefetch_row_df<W>(cs, c + B);
     const tf xc = ld_tf(cs.x2, cs.xlo, c);
     df d, flux;
     row_flux_df<W, true>(cs, c, xc, d, flux);
