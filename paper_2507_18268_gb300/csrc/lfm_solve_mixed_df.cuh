@@ -170,11 +170,16 @@ __device__ __noinline__ double2 pass_true_residual_df(const CaseDev& cs, int c0,
   return make_double2(a_r.value(), a_rho.value());
 }
 
+// Four partial sums of a pass, per thread.
+struct Sums4 {
+  double a, b, c, d;
+};
+
 // V: the step's verification residual and the next step's T0 in one pass over the rows (no
 // sources, no correctors; see the head of this file). xRef_next: mean of the corrected x.
 // Returns sum|r_v| (scaled), then the next step's normFactor sum, sum|r'| and rho.
 template <int B, int W>
-__device__ __noinline__ double4 pass_verify_next_df(const CaseDev& cs, int c0, int c1, double xRef_next, float s32,
+__device__ __noinline__ Sums4 pass_verify_next_df(const CaseDev& cs, int c0, int c1, double xRef_next, float s32,
                                                     float inv_s32) {
   const df xr = df_from_scalar(xRef_next);
   DfAcc a_v, a_nf, a_r;
@@ -193,7 +198,7 @@ __device__ __noinline__ double4 pass_verify_next_df(const CaseDev& cs, int c0, i
     d = df_add(df_add(d, gb), vdt);
     seed_row_df(cs, c, d, df_fma(vdt, tf_to_df(xc), sb), df_add(vdt, gb), rn, xr, s32, inv_s32, a_nf, a_r, a_rho);
   }
-  return make_double4(a_v.value(), a_nf.value(), a_r.value(), a_rho.value());
+  return Sums4{a_v.value(), a_nf.value(), a_r.value(), a_rho.value()};
 }
 
 // C: x += dx (the triple-float field and the FP32 correction of the inner solve). save_old:
@@ -340,8 +345,8 @@ __device__ bool steps_mixed_df(const CaseDev& cs, const CaseDev& cref, const Tea
         ++sweeps;
         if (fuse) {
           // ---- V: the verification residual and the next step's T0 -----------------------
-          const double4 uv = pass_verify_next_df<B, W>(cref, c0, c1, sx[0] / (double)cs.N, s32, inv_s32);
-          double v4[4] = {uv.x, uv.y, uv.z, uv.w};
+          const Sums4 uv = pass_verify_next_df<B, W>(cref, c0, c1, sx[0] / (double)cs.N, s32, inv_s32);
+          double v4[4] = {uv.a, uv.b, uv.c, uv.d};
           if (!team_allreduce<4>(tm, v4, sh)) return false;
           clk.lap(kPhInit);
           res = v4[0] * inv_scale / nf;

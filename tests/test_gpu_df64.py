@@ -283,14 +283,14 @@ def test_field_carried_between_launches(prec):
     assert np.array_equal(Te, Tf)
 
 
-@pytest.mark.parametrize("name,tol,max_iter,sweeps", [
-    ("plain20", None, 1000, "conv"),      # every step converges
-    ("permuted20", None, 1000, "more"),   # verifications that ask for another sweep
-    ("graded40", 1e-11, 1000, "more"),
-    ("graded40", None, 1, "cap"),         # steps that end at the iteration limit, not converged
-    ("graded40", None, 3, "any"),         # some steps end at the iteration limit
+@pytest.mark.parametrize("name,tol,max_iter,min_iter,sweeps", [
+    ("plain20", None, 1000, 0, "conv"),      # every step converges
+    ("permuted20", None, 1000, 0, "more"),   # verifications that ask for another sweep
+    ("graded40", 1e-11, 1000, 0, "more"),
+    ("graded40", None, 1, 0, "cap"),         # steps that end at the iteration limit, not converged
+    ("graded40", None, 3, 0, "any"),         # some steps end at the iteration limit
 ])
-def test_mixed_fused_verification_bitwise(name, tol, max_iter, sweeps):
+def test_mixed_fused_verification_bitwise(name, tol, max_iter, min_iter, sweeps):
     # In one launch every mixed step after the first starts from the previous step's
     # verification pass (its rows and first residual formed there); one-step launches start
     # each step with its own sum and row passes. Same field, same statistics, bit for bit.
@@ -301,7 +301,7 @@ def test_mixed_fused_verification_bitwise(name, tol, max_iter, sweeps):
 
     def run(chunks):
         with Solver.from_case(case) as s:
-            s.set_solver(case.tol, case.rel_tol, max_iter, case.min_iter, B.LFM_MIXED)
+            s.set_solver(case.tol, case.rel_tol, max_iter, min_iter, B.LFM_MIXED)
             st = []
             for k in chunks:
                 st += s.advance(k)
