@@ -22,9 +22,10 @@
 //   r'    = sum_k g_k (x_other(k) - x_c) + sum_b g_b (T_b - x_c)
 // (the next step starts from this x, so its ddt term vanishes), and xRef of the next step is
 // the sum of x that C returned. The next step then starts at its inner solve: S and T0 are
-// not repeated. Every value is formed by the same operations in the same order as S and T0
-// would form it, so the results are those of the unfused sequence bit for bit. When the
-// verification asks for another sweep, T1 re-seeds the inner solve from r_v.
+// not repeated, and its first C keeps x_old. Every value is formed by the same operations in
+// the same order as S and T0 would form it, so the results are those of the unfused sequence
+// bit for bit. When the verification asks for another sweep, T1 re-seeds the inner solve
+// from r_v.
 #pragma once
 
 #include <cuda_runtime.h>
