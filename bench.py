@@ -22,6 +22,7 @@ import argparse
 import hashlib
 import json
 import os
+import re
 import statistics
 import subprocess
 import sys
@@ -50,11 +51,19 @@ KERNEL_SOURCES = {
 }
 
 
+def _code_tokens(text: str) -> str:
+    """A source file without its comments and with whitespace collapsed: edits to comments
+    or layout do not invalidate a stored capture, edits to code do."""
+    text = re.sub(r"/\*.*?\*/", " ", text, flags=re.S)
+    text = re.sub(r"//[^\n]*", " ", text)
+    return " ".join(text.split())
+
+
 def kernel_hash(family: str = "fp64") -> str:
     h = hashlib.sha256()
     for p in KERNEL_SOURCES[family]:
-        with open(os.path.join(ROOT, "paper_2507_18268_gb300", p), "rb") as f:
-            h.update(f.read())
+        with open(os.path.join(ROOT, "paper_2507_18268_gb300", p), encoding="utf-8") as f:
+            h.update(_code_tokens(f.read()).encode())
     return h.hexdigest()[:16]
 
 
