@@ -11,6 +11,6 @@ for sm_103a behind the C ABI of ``include/lapfoam.h``:
 from . import binding
 from .binding import LfmError, load
 from .mesh import LduMesh, box_mesh, field_by_label
-from .solver import Solver
+from .solver import Solver, solver_log
 
-__all__ = ["binding", "LfmError", "load", "LduMesh", "box_mesh", "field_by_label", "Solver"]
+__all__ = ["binding", "LfmError", "load", "LduMesh", "box_mesh", "field_by_label", "Solver", "solver_log"]

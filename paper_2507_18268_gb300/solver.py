@@ -23,6 +23,28 @@ def _stream_handle(stream) -> Optional[int]:
     return int(stream.cuda_stream)  # torch.cuda.Stream
 
 
+def solver_log(stats: List[dict], field: str = "T", dt: Optional[float] = None, t0: float = 0.0,
+               mixed: bool = False) -> str:
+    """The per-step statistics as a solver log in the layout laplacianFoam prints: with dt, a
+    "Time = t" line per step, then the solve line with the solver (diagonal-preconditioned
+    CG), the field, the initial and final normFactor-scaled residuals and the iteration count.
+    mixed: the steps ran the mixed form; its defect-correction sweeps are added. A step that
+    stopped on an error status shows the status."""
+    lines = []
+    for k, s in enumerate(stats):
+        if dt is not None:
+            lines.append(f"Time = {t0 + (k + 1) * dt:g}")
+            lines.append("")
+        line = (f"diagonalPCG:  Solving for {field}, Initial residual = {s['init_res']:.6g}, "
+                f"Final residual = {s['final_res']:.6g}, No Iterations {s['iters']}")
+        if mixed:
+            line += f", sweeps {s['sweeps']}"
+        if s.get("status", 0) != 0:
+            line += f", status {B._NAMES.get(s['status'], s['status'])}"
+        lines.append(line)
+    return "\n".join(lines)
+
+
 class BoxInfo:
     """Sizes of a mesh that was built on the device or is shared (no host arrays)."""
 

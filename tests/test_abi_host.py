@@ -148,3 +148,21 @@ def test_workspace_sizes_by_precision():
     bm = pm.box_mesh(case)
     for prec in (B.LFM_FP64, B.LFM_MIXED, B.LFM_DF64, B.LFM_BOTH):
         assert B.lfm_workspace_bytes_box(7, 7, 7, prec) == B.lfm_workspace_bytes(bm, prec)
+
+
+def test_solver_log_layout():
+    from paper_2507_18268_gb300 import solver_log
+    st = [{"iters": 12, "converged": 1, "sweeps": 1, "status": 0, "init_res": 1.0, "final_res": 9.51e-07,
+           "norm_factor": 3.2},
+          {"iters": 0, "converged": 1, "sweeps": 0, "status": 0, "init_res": 4.0e-07, "final_res": 4.0e-07,
+           "norm_factor": 3.1},
+          {"iters": 3, "converged": 0, "sweeps": 1, "status": B.LFM_ENONFINITE, "init_res": 0.5,
+           "final_res": float("nan"), "norm_factor": 3.0}]
+    lines = solver_log(st, dt=0.005).split("\n")
+    assert lines[0] == "Time = 0.005" and lines[1] == ""
+    assert lines[2] == ("diagonalPCG:  Solving for T, Initial residual = 1, Final residual = 9.51e-07, "
+                        "No Iterations 12")
+    assert lines[3] == "Time = 0.01"
+    assert lines[5].endswith("No Iterations 0")
+    assert lines[8].endswith("No Iterations 3, status LFM_ENONFINITE")
+    assert solver_log(st[:1], mixed=True).endswith("No Iterations 12, sweeps 1")
