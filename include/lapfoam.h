@@ -336,6 +336,23 @@ int lfm_set_barrier_timeout(lfm_ctx *ctx, uint64_t ns);
  * LFM_ETIMEOUT (no fault, no hang: every wait is bounded). One-shot; needs >= 2 CTAs. */
 int lfm_debug_skip_arrival(lfm_ctx *ctx, int32_t cta);
 
+/* 1 when this library is the checked build (compiled with LFM_CHECKED, liblapfoam_checked.so),
+ * else 0. In the checked build every kernel tests each index it reads from the mesh's
+ * addressing before using it as an address: a slot's neighbour cell (< n_cells), a face's
+ * slot positions and a slot's face, a cell's boundary faces and a boundary face's cell. A
+ * bad index is replaced by an in-range one and recorded; the advance (or batch finish) that
+ * follows returns LFM_EINVAL naming the check site (1 slot cell, 2 face/slot, 3 boundary,
+ * 4 slot cell in the df64 passes). Nothing is read or written out of bounds and nothing
+ * traps, so the context stays usable. This stands in for a memory checker: the build's
+ * results must equal the normal build's bit for bit. */
+int lfm_checked_build(void);
+
+/* Test hook of the checked build: makes check site `site` (1..4) report as failing, with no
+ * bad index, wherever the kernels evaluate it until the next advance (or batch finish)
+ * collects the checks; that call then returns LFM_EINVAL. One-shot: the collection clears
+ * it. LFM_ESTATE in the normal build; LFM_EINVAL for another site number. */
+int lfm_debug_check_inject(lfm_ctx *ctx, int32_t site);
+
 /* Allocation-free solve, for callers that cannot allocate device memory (a plug-in inside a
  * host code whose memory manager owns every device buffer, a real-time loop that must not
  * call an allocator once running). The paper has no counterpart to this call.

@@ -8,6 +8,7 @@ e.g. ``lfm_query``).
 from __future__ import annotations
 
 import ctypes
+import os
 from ctypes import POINTER, c_char_p, c_double, c_int, c_int32, c_size_t, c_uint64, c_void_p
 from typing import Optional, Sequence
 
@@ -128,20 +129,30 @@ _SIGS = {
     "lfm_batch_destroy": ([c_void_p], c_int),
     "lfm_batch_last_error": ([c_void_p], c_char_p),
     "lfm_last_error": ([_ctx_p], c_char_p),
+    "lfm_checked_build": ([], c_int),
+    "lfm_debug_check_inject": ([_ctx_p, c_int32], c_int),
 }
 
 _lib = None
 
 
+def checked_requested() -> bool:
+    """LFM_CHECKED=1 in the environment selects the checked build (liblapfoam_checked.so:
+    every index a kernel reads from the mesh addressing is tested before use)."""
+    return os.environ.get("LFM_CHECKED", "") == "1"
+
+
 def library_path() -> str:
-    return _build.LIB
+    return _build.lib_path(checked_requested())
 
 
 def load(build: bool = True) -> ctypes.CDLL:
-    """Loads liblapfoam.so (building it first when stale). Raises when that fails."""
+    """Loads liblapfoam.so, or the checked build when LFM_CHECKED=1 (building it first when
+    stale). Raises when that fails."""
     global _lib
     if _lib is None:
-        path = _build.build() if build else _build.LIB
+        checked = checked_requested()
+        path = _build.build(checked=checked) if build else _build.lib_path(checked)
         lib = ctypes.CDLL(path)
         for name, (args, res) in _SIGS.items():
             fn = getattr(lib, name)
@@ -463,6 +474,14 @@ def lfm_set_barrier_timeout(ctx, ns: int):
 
 def lfm_debug_skip_arrival(ctx, cta: int):
     _check(load().lfm_debug_skip_arrival(ctx, int(cta)), ctx)
+
+
+def lfm_checked_build() -> bool:
+    return bool(load().lfm_checked_build())
+
+
+def lfm_debug_check_inject(ctx, site: int):
+    _check(load().lfm_debug_check_inject(ctx, int(site)), ctx)
 
 
 def lfm_pcg_solve_static(n_cells: int, n_faces: int, owner_ptr: int, neighbour_ptr: int, diag_ptr: int,

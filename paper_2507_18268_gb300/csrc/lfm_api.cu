@@ -595,6 +595,16 @@ int enqueue_chunk(lfm_ctx* c, int steps, int mode) {
   return LFM_OK;
 }
 
+// Checked build: the first index check that failed in a kernel since the last take.
+int take_checks(lfm_ctx* c) {
+  if (!kCheckedBuild) return LFM_OK;
+  int site = check_take_step(c->stream);
+  if (site == 0) site = check_take_batch(c->stream);
+  if (site < 0) return fail(c, LFM_ECUDA, "reading the index-check word failed");
+  if (site > 0) return fail(c, LFM_EINVAL, "checked build: a kernel met an index out of range (check site %d)", site);
+  return LFM_OK;
+}
+
 // Waits for the enqueued chunk, appends its statistics, maps the device status.
 int collect_chunk(lfm_ctx* c, int steps) {
   CK(c, cudaEventSynchronize(c->done));
@@ -605,7 +615,7 @@ int collect_chunk(lfm_ctx* c, int steps) {
   if (st == LFM_ESINGULAR) return fail(c, LFM_ESINGULAR, "PCG met a singular search direction");
   if (st == LFM_ENONFINITE) return fail(c, LFM_ENONFINITE, "PCG residual became non-finite");
   if (st != 0) return fail(c, LFM_ECUDA, "device status %d", (int)st);
-  return LFM_OK;
+  return take_checks(c);
 }
 
 }  // namespace
@@ -1387,6 +1397,18 @@ int lfm_set_barrier_timeout(lfm_ctx* c, uint64_t ns) {
   return LFM_OK;
 }
 
+int lfm_checked_build(void) { return kCheckedBuild ? 1 : 0; }
+
+int lfm_debug_check_inject(lfm_ctx* c, int32_t site) {
+  if (!c) return fail_free(LFM_EINVAL, "context is NULL");
+  if (!kCheckedBuild) return fail(c, LFM_ESTATE, "index checks are compiled only into the checked build");
+  if (site < 1 || site > 4) return fail(c, LFM_EINVAL, "check site %d is not one of 1..4", site);
+  DeviceGuard g(c->device);
+  check_inject_step(site, c->stream);
+  check_inject_batch(site, c->stream);
+  return LFM_OK;
+}
+
 int lfm_debug_skip_arrival(lfm_ctx* c, int32_t cta) {
   if (!c) return fail_free(LFM_EINVAL, "context is NULL");
   c->skip_cta = cta >= 0 ? cta : -1;
@@ -1766,6 +1788,12 @@ int lfm_batch_finish(lfm_batch* b) {
     if (b->h_status[i] != 0 && first == LFM_OK) first = b->h_status[i];
   }
   if (first != LFM_OK) return bfail(b, first, "at least one case failed (first status %d)", first);
+  if (kCheckedBuild) {
+    int site = check_take_batch(b->stream);
+    if (site == 0) site = check_take_step(b->stream);
+    if (site < 0) return bfail(b, LFM_ECUDA, "reading the index-check word failed");
+    if (site > 0) return bfail(b, LFM_EINVAL, "checked build: a kernel met an index out of range (check site %d)", site);
+  }
   return LFM_OK;
 }
 

@@ -162,4 +162,25 @@ cudaError_t launch_batch_steps(const BatchLaunch& bl, int n_steps, cudaStream_t 
   return cudaLaunchKernelExC(&cfg, fn, args);
 }
 
+#ifdef LFM_CHECKED
+int check_take_batch(cudaStream_t s) {
+  int site = 0;
+  const int zero = 0;
+  if (cudaMemcpyFromSymbolAsync(&site, g_check_site, sizeof(int), 0, cudaMemcpyDeviceToHost, s) != cudaSuccess ||
+      cudaMemcpyToSymbolAsync(g_check_site, &zero, sizeof(int), 0, cudaMemcpyHostToDevice, s) != cudaSuccess ||
+      cudaMemcpyToSymbolAsync(g_check_inject, &zero, sizeof(int), 0, cudaMemcpyHostToDevice, s) != cudaSuccess ||
+      cudaStreamSynchronize(s) != cudaSuccess)
+    return -1;
+  return site;
+}
+
+void check_inject_batch(int site, cudaStream_t s) {
+  cudaMemcpyToSymbolAsync(g_check_inject, &site, sizeof(int), 0, cudaMemcpyHostToDevice, s);
+  cudaStreamSynchronize(s);
+}
+#else
+int check_take_batch(cudaStream_t) { return 0; }
+void check_inject_batch(int, cudaStream_t) {}
+#endif
+
 }  // namespace lfm

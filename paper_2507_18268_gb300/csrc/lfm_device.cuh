@@ -38,6 +38,37 @@ __device__ __forceinline__ int ld_volatile_i32(const int32_t* p) {
   return *reinterpret_cast<const volatile int32_t*>(p);
 }
 
+// ---- checked builds ----------------------------------------------------------------------
+// Compiled with -DLFM_CHECKED (the library variant liblapfoam_checked.so), every index a
+// kernel reads from the mesh's addressing and then uses as an address (a slot's neighbour
+// cell, a face's slot positions, a boundary face) is tested against its array's extent
+// first. A bad index is replaced by an in-range one (the caller's fallback), and the first
+// failing site is recorded in a word of this translation unit, which the host reads after
+// the launch and reports as LFM_EINVAL. Nothing reads out of bounds and nothing traps: the
+// team barriers keep working and the context stays usable. In the normal build the checks
+// compile to nothing. check_inject (a test hook) makes one site report as failing without
+// any bad index.
+enum CheckSite {
+  kChkSlotCell = 1,   // a slot's neighbour cell (FP64 / FP32 passes, set-up)
+  kChkFaceSlot = 2,   // face <-> slot addressing: a face's slot positions, a slot's face
+  kChkBFace = 3,      // boundary addressing: a cell's boundary faces, a boundary face's cell
+  kChkSlotCellDf = 4  // a slot's neighbour cell (df64 passes)
+};
+#ifdef LFM_CHECKED
+namespace {
+__device__ int g_check_site;    // first failing site, 0 while none
+__device__ int g_check_inject;  // test hook: this site reports as failing
+}  // namespace
+__device__ __forceinline__ int checked_index(int i, int n, int fallback, int site) {
+  const bool bad = (unsigned)i >= (unsigned)n;
+  if (bad || g_check_inject == site) atomicCAS(&g_check_site, 0, site);
+  return bad ? fallback : i;
+}
+#define LFM_IDX(i, n, fallback, site) ::lfm::checked_index((int)(i), (int)(n), (fallback), (site))
+#else
+#define LFM_IDX(i, n, fallback, site) (i)
+#endif
+
 struct Team {
   int size;
   int rank;

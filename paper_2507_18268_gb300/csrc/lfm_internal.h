@@ -230,4 +230,19 @@ cudaError_t launch_batch_steps(const BatchLaunch& bl, int n_steps, cudaStream_t 
 cudaError_t launch_fill(double* a, size_t n, double v, cudaStream_t stream);
 cudaError_t launch_vdt(const double* V, double dt, double* vdt, int n, cudaStream_t stream);
 
+// Index checks of the checked build (lfm_device.cuh), per kernel translation unit: take
+// returns the first failing check site recorded on the current device since the last take
+// (0: none) and clears it and the injection hook; inject makes `site` report as failing
+// (one-shot: the next take clears it). Without LFM_CHECKED, take returns 0 and inject does
+// nothing.
+#ifdef LFM_CHECKED
+constexpr bool kCheckedBuild = true;
+#else
+constexpr bool kCheckedBuild = false;
+#endif
+int check_take_step(cudaStream_t s);
+int check_take_batch(cudaStream_t s);
+void check_inject_step(int site, cudaStream_t s);
+void check_inject_batch(int site, cudaStream_t s);
+
 }  // namespace lfm

@@ -109,7 +109,8 @@ struct Acc2f {
 // read-back, where the face-indexed LDU copy is written too.
 template <bool kMixed>
 __device__ __forceinline__ void assemble_face(const CaseDev& cs, int f, bool write_upper) {
-  const uint2 at = __ldg(reinterpret_cast<const uint2*>(cs.face_slots) + f);
+  const uint2 at0 = __ldg(reinterpret_cast<const uint2*>(cs.face_slots) + f);
+  const uint2 at = make_uint2(LFM_IDX(at0.x, cs.W * cs.N, 0, kChkFaceSlot), LFM_IDX(at0.y, cs.W * cs.N, 0, kChkFaceSlot));
   const double DTf = cs.DT_is_uniform ? cs.DT_uniform : __ldg(cs.DT + f);
   const double g = __dmul_rn(__dmul_rn(DTf, __ldg(cs.magSf + f)), __ldg(cs.delta + f));
   cs.slot_coef[at.x] = -g;
@@ -152,7 +153,7 @@ __device__ __forceinline__ void row_boundary(const CaseDev& cs, int c, double xo
   }
   double s = 0.0, gsum = 0.0;  // source, boundary conductance of the row
   for (int k = b0; k < b1; ++k) {
-    const int bf = __ldg(cs.b_face + k);
+    const int bf = LFM_IDX(__ldg(cs.b_face + k), cs.NB, 0, kChkBFace);
     if (__ldg(cs.btype + bf) == LFM_FIXED_VALUE) {
       const double gb = __dmul_rn(__dmul_rn(__ldg(cs.bDT + bf), __ldg(cs.bmagSf + bf)), __ldg(cs.bdelta + bf));
       o.d = __dadd_rn(o.d, gb);
@@ -181,7 +182,7 @@ __device__ __forceinline__ void op_grad(const CaseDev& cs, int c, const double* 
   for (int k = 0; k < (W > 0 ? W : kMaxSlots); ++k) {
     if (W == 0 && k >= ns) break;
     const size_t at = (size_t)k * N + c;
-    const double xo = x[__ldg(cs.slot_other + at)];
+    const double xo = x[LFM_IDX(__ldg(cs.slot_other + at), cs.N, c, kChkSlotCell)];
     g0 = fma(__ldg(cs.gE + at), xo, g0);
     g1 = fma(__ldg(cs.gE + WN + at), xo, g1);
     g2 = fma(__ldg(cs.gE + 2 * WN + at), xo, g2);
@@ -206,7 +207,7 @@ __device__ __forceinline__ double op_corr_source(const CaseDev& cs, int c) {
   for (int k = 0; k < (W > 0 ? W : kMaxSlots); ++k) {
     if (W == 0 && k >= ns) break;
     const size_t at = (size_t)k * N + c;
-    const int o = __ldg(cs.slot_other + at);
+    const int o = LFM_IDX(__ldg(cs.slot_other + at), cs.N, c, kChkSlotCell);
     v = fma(__ldg(cs.cL + at), G[o], v);
     v = fma(__ldg(cs.cL + WN + at), G[N + o], v);
     v = fma(__ldg(cs.cL + 2 * WN + at), G[2 * N + o], v);
@@ -230,7 +231,7 @@ __device__ __forceinline__ Row assemble_row(const CaseDev& cs, int c, const doub
     double u[W];
 #pragma unroll
     for (int k = 0; k < W; ++k) {
-      oc[k] = __ldg(cs.slot_other + (size_t)k * N + c);
+      oc[k] = LFM_IDX(__ldg(cs.slot_other + (size_t)k * N + c), cs.N, c, kChkSlotCell);
       u[k] = cs.slot_coef[(size_t)k * N + c];
     }
     // 0 + g_0 = g_0 exactly; the sign of a zero cannot reach d, which ends above V/dt > 0
@@ -245,7 +246,7 @@ __device__ __forceinline__ Row assemble_row(const CaseDev& cs, int c, const doub
       const size_t at = (size_t)k * N + c;
       const double u = cs.slot_coef[at];
       o.d = __dadd_rn(o.d, -u);
-      off = fma(u, x[__ldg(cs.slot_other + at)], off);
+      off = fma(u, x[LFM_IDX(__ldg(cs.slot_other + at), cs.N, c, kChkSlotCell)], off);
     }
   }
   row_boundary(cs, c, kCorr && cs.n_corr > 0 ? cs.x_old[c] : o.xc, o);
@@ -383,8 +384,8 @@ __device__ __forceinline__ void rows2(const Slots<T>& A, int c, int c2, const T*
     T u[W], u2[W];
 #pragma unroll
     for (int k = 0; k < W; ++k) {
-      o[k] = __ldcs(A.other + (size_t)k * N + c);
-      o2[k] = __ldcs(A.other + (size_t)k * N + c2);
+      o[k] = LFM_IDX(__ldcs(A.other + (size_t)k * N + c), A.N, c, kChkSlotCell);
+      o2[k] = LFM_IDX(__ldcs(A.other + (size_t)k * N + c2), A.N, c2, kChkSlotCell);
       u[k] = __ldcs(A.coef + (size_t)k * N + c);
       u2[k] = __ldcs(A.coef + (size_t)k * N + c2);
     }
@@ -396,8 +397,8 @@ __device__ __forceinline__ void rows2(const Slots<T>& A, int c, int c2, const T*
   } else {
     for (int k = 0; k < A.W; ++k) {
       const size_t at = (size_t)k * N;
-      acc = fmadd(A.coef[at + c], v[__ldg(A.other + at + c)], acc);
-      acc2 = fmadd(A.coef[at + c2], v[__ldg(A.other + at + c2)], acc2);
+      acc = fmadd(A.coef[at + c], v[LFM_IDX(__ldg(A.other + at + c), A.N, c, kChkSlotCell)], acc);
+      acc2 = fmadd(A.coef[at + c2], v[LFM_IDX(__ldg(A.other + at + c2), A.N, c2, kChkSlotCell)], acc2);
     }
   }
   y = acc;
@@ -414,7 +415,7 @@ __device__ __forceinline__ T row1(const Slots<T>& A, int c, const T* __restrict_
   for (int k = 0; k < (W > 0 ? W : kMaxSlots); ++k) {
     if (W == 0 && k >= ns) break;
     const size_t at = (size_t)k * N + c;
-    acc = fmadd(A.coef[at], v[__ldg(A.other + at)], acc);
+    acc = fmadd(A.coef[at], v[LFM_IDX(__ldg(A.other + at), A.N, c, kChkSlotCell)], acc);
   }
   return acc;
 }

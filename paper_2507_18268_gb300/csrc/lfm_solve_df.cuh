@@ -134,7 +134,7 @@ __device__ __forceinline__ void row_boundary_df(const CaseDev& cs, int c, tf xc,
   const double x = tf_to_double(xc);
   double g = 0.0, s = 0.0, fl = 0.0;
   for (int k = b0; k < b1; ++k) {
-    const int bf = __ldg(cs.b_face + k);
+    const int bf = LFM_IDX(__ldg(cs.b_face + k), cs.NB, 0, kChkBFace);
     if (__ldg(cs.btype + bf) == LFM_FIXED_VALUE) {
       const double gb = __ldg(cs.bDT + bf) * __ldg(cs.bmagSf + bf) * __ldg(cs.bdelta + bf) * cs.df_scale;
       const double tb = __ldg(cs.bval + bf);
@@ -169,7 +169,7 @@ __device__ __noinline__ void pass_grad_df(const CaseDev& cs, int c0, int c1) {
     for (int k = 0; k < (W > 0 ? W : kMaxSlots); ++k) {
       if (W == 0 && k >= ns) break;
       const size_t at = (size_t)k * N + c;
-      const df d = tf_diff(ld_tf(x2, xl, __ldg(cs.slot_other + at)), xc);
+      const df d = tf_diff(ld_tf(x2, xl, LFM_IDX(__ldg(cs.slot_other + at), cs.N, c, kChkSlotCellDf)), xc);
       g0 = df_fma(ldg_df(cs.gE2 + at), d, g0);
       g1 = df_fma(ldg_df(cs.gE2 + WN + at), d, g1);
       g2 = df_fma(ldg_df(cs.gE2 + 2 * WN + at), d, g2);
@@ -183,7 +183,7 @@ __device__ __noinline__ void pass_grad_df(const CaseDev& cs, int c0, int c1) {
       const double xd = tf_to_double(xc), rv = 1.0 / cs.V[c];
       double b0 = 0.0, b1 = 0.0, b2 = 0.0;
       for (int k = k0; k < k1; ++k) {
-        const int bf = __ldg(cs.b_face + k);
+        const int bf = LFM_IDX(__ldg(cs.b_face + k), cs.NB, 0, kChkBFace);
         if (__ldg(cs.btype + bf) == LFM_FIXED_VALUE) {
           const double dT = (__ldg(cs.bval + bf) - xd) * rv;
           b0 = fma(cs.bSf[3 * (size_t)bf], dT, b0);
@@ -216,7 +216,7 @@ __device__ __forceinline__ df op_corr_df(const CaseDev& cs, int c) {
   for (int k = 0; k < (W > 0 ? W : kMaxSlots); ++k) {
     if (W == 0 && k >= ns) break;
     const size_t at = (size_t)k * N + c;
-    const int o = __ldg(cs.slot_other + at);
+    const int o = LFM_IDX(__ldg(cs.slot_other + at), cs.N, c, kChkSlotCellDf);
     v = df_fma(ldg_df(cs.cL2 + at), ld_df(G + o), v);
     v = df_fma(ldg_df(cs.cL2 + WN + at), ld_df(G + N + o), v);
     v = df_fma(ldg_df(cs.cL2 + 2 * WN + at), ld_df(G + 2 * N + o), v);
@@ -272,7 +272,7 @@ __device__ __noinline__ Sums3 pass_rows_init_df(const CaseDev& cs, int c0, int c
       df g[W];
 #pragma unroll
       for (int k = 0; k < W; ++k) {
-        o[k] = __ldg(cs.slot_other + (size_t)k * N + c);
+        o[k] = LFM_IDX(__ldg(cs.slot_other + (size_t)k * N + c), cs.N, c, kChkSlotCellDf);
         g[k] = ldg_df(g2 + (size_t)k * N + c);
       }
       tf xo_[W];
@@ -291,7 +291,7 @@ __device__ __noinline__ Sums3 pass_rows_init_df(const CaseDev& cs, int c0, int c
         const size_t at = (size_t)k * N + c;
         const df gk = ldg_df(g2 + at);
         d = df_add(d, gk);
-        flux = df_fma(gk, tf_diff(ld_tf(x2, xl, __ldg(cs.slot_other + at)), xc), flux);
+        flux = df_fma(gk, tf_diff(ld_tf(x2, xl, LFM_IDX(__ldg(cs.slot_other + at), cs.N, c, kChkSlotCellDf)), xc), flux);
       }
     }
     df gb, sb, fb;
@@ -352,8 +352,8 @@ __device__ __forceinline__ void rows2_df(const CaseDev& cs, int c, int c2, const
     df g[W], h[W];
 #pragma unroll
     for (int k = 0; k < W; ++k) {
-      o[k] = __ldcs(cs.slot_other + (size_t)k * N + c);
-      o2[k] = __ldcs(cs.slot_other + (size_t)k * N + c2);
+      o[k] = LFM_IDX(__ldcs(cs.slot_other + (size_t)k * N + c), cs.N, c, kChkSlotCellDf);
+      o2[k] = LFM_IDX(__ldcs(cs.slot_other + (size_t)k * N + c2), cs.N, c2, kChkSlotCellDf);
       const float2 a = __ldcs(g2 + (size_t)k * N + c), b = __ldcs(g2 + (size_t)k * N + c2);
       g[k] = df{a.x, a.y};
       h[k] = df{b.x, b.y};
@@ -366,8 +366,8 @@ __device__ __forceinline__ void rows2_df(const CaseDev& cs, int c, int c2, const
   } else {
     for (int k = 0; k < cs.W; ++k) {
       const size_t at = (size_t)k * N;
-      acc = df_fma(df_neg(ldg_df(g2 + at + c)), ld_df(v + __ldg(cs.slot_other + at + c)), acc);
-      acc2 = df_fma(df_neg(ldg_df(g2 + at + c2)), ld_df(v + __ldg(cs.slot_other + at + c2)), acc2);
+      acc = df_fma(df_neg(ldg_df(g2 + at + c)), ld_df(v + LFM_IDX(__ldg(cs.slot_other + at + c), cs.N, c, kChkSlotCellDf)), acc);
+      acc2 = df_fma(df_neg(ldg_df(g2 + at + c2)), ld_df(v + LFM_IDX(__ldg(cs.slot_other + at + c2), cs.N, c2, kChkSlotCellDf)), acc2);
     }
   }
   y = acc;
@@ -384,7 +384,7 @@ __device__ __forceinline__ df row1_df(const CaseDev& cs, int c, const float2* __
   for (int k = 0; k < (W > 0 ? W : kMaxSlots); ++k) {
     if (W == 0 && k >= ns) break;
     const size_t at = (size_t)k * N + c;
-    acc = df_fma(df_neg(ldg_df(cs.g2 + at)), ld_df(v + __ldg(cs.slot_other + at)), acc);
+    acc = df_fma(df_neg(ldg_df(cs.g2 + at)), ld_df(v + LFM_IDX(__ldg(cs.slot_other + at), cs.N, c, kChkSlotCellDf)), acc);
   }
   return acc;
 }

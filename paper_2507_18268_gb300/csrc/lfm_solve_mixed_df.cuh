@@ -52,7 +52,7 @@ __device__ __forceinline__ void row_flux_df(const CaseDev& cs, int c, const tf& 
     df g[W];
 #pragma unroll
     for (int k = 0; k < W; ++k) {
-      o[k] = __ldg(cs.slot_other + (size_t)k * N + c);
+      o[k] = LFM_IDX(__ldg(cs.slot_other + (size_t)k * N + c), cs.N, c, kChkSlotCellDf);
       g[k] = ldg_df(g2 + (size_t)k * N + c);
     }
     tf xo[W];
@@ -73,7 +73,7 @@ __device__ __forceinline__ void row_flux_df(const CaseDev& cs, int c, const tf& 
       const size_t at = (size_t)k * N + c;
       const df gk = ldg_df(g2 + at);
       if constexpr (kDiag) d = df_add(d, gk);
-      flux = df_fma(gk, tf_diff(ld_tf(x2, xl, __ldg(cs.slot_other + at)), xc), flux);
+      flux = df_fma(gk, tf_diff(ld_tf(x2, xl, LFM_IDX(__ldg(cs.slot_other + at), cs.N, c, kChkSlotCellDf)), xc), flux);
     }
   }
 }

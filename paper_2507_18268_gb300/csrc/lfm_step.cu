@@ -63,7 +63,8 @@ __global__ void __launch_bounds__(B, 1024 / B) step_kernel_df64(CaseDev cs, Laun
 __global__ void coef_kernel(CaseDev cs) {
   const int f = blockIdx.x * blockDim.x + threadIdx.x;
   if (f < cs.F) {
-    const uint2 at = reinterpret_cast<const uint2*>(cs.face_slots)[f];
+    const uint2 a0 = reinterpret_cast<const uint2*>(cs.face_slots)[f];
+    const uint2 at = make_uint2(LFM_IDX(a0.x, cs.W * cs.N, 0, kChkFaceSlot), LFM_IDX(a0.y, cs.W * cs.N, 0, kChkFaceSlot));
     const double DTf = cs.DT_is_uniform ? cs.DT_uniform : cs.DT[f];
     const double g = __dmul_rn(__dmul_rn(DTf, cs.magSf[f]), cs.delta[f]);
     cs.slot_coef[at.x] = -g;
@@ -81,7 +82,8 @@ __global__ void coef_kernel(CaseDev cs) {
 __global__ void df_coef_kernel(CaseDev cs, float2* __restrict__ g2) {
   const int f = blockIdx.x * blockDim.x + threadIdx.x;
   if (f >= cs.F) return;
-  const uint2 at = reinterpret_cast<const uint2*>(cs.face_slots)[f];
+  const uint2 a0 = reinterpret_cast<const uint2*>(cs.face_slots)[f];
+  const uint2 at = make_uint2(LFM_IDX(a0.x, cs.W * cs.N, 0, kChkFaceSlot), LFM_IDX(a0.y, cs.W * cs.N, 0, kChkFaceSlot));
   const double DTf = cs.DT_is_uniform ? cs.DT_uniform : cs.DT[f];
   const double g = __dmul_rn(__dmul_rn(__dmul_rn(DTf, cs.magSf[f]), cs.delta[f]), cs.df_scale);
   const df v = df_from_double(g);
@@ -116,7 +118,7 @@ __global__ void df_ops_kernel(CaseDev cs, float2* __restrict__ E2, float2* __res
   }
   const double rv = 1.0 / cs.V[c];
   for (int k = cs.b_start[c]; k < cs.b_start[c + 1]; ++k) {
-    const int bf = cs.b_face[k];
+    const int bf = LFM_IDX(cs.b_face[k], cs.NB, 0, kChkBFace);
     if (cs.btype[bf] == LFM_FIXED_VALUE)
       for (int q = 0; q < 3; ++q) z[q] += cs.bSf[3 * (size_t)bf + q] * rv;
   }
@@ -133,7 +135,7 @@ __global__ void df_vdt_kernel(CaseDev cs, float2* __restrict__ vdt2) {
 
 __global__ void boundary_values_kernel(CaseDev cs, double* Tb) {
   const int b = blockIdx.x * blockDim.x + threadIdx.x;
-  if (b < cs.NB) Tb[b] = cs.btype[b] == LFM_FIXED_VALUE ? cs.bval[b] : cs.x[cs.bcell[b]];
+  if (b < cs.NB) Tb[b] = cs.btype[b] == LFM_FIXED_VALUE ? cs.bval[b] : cs.x[LFM_IDX(cs.bcell[b], cs.N, 0, kChkBFace)];
 }
 
 // Gauss gradient of the current T per cell (into cs.grad, component-major).
@@ -155,7 +157,7 @@ __global__ void grad_boundary_kernel(CaseDev cs, double* __restrict__ bgrad) {
   const int b = blockIdx.x * blockDim.x + threadIdx.x;
   if (b < cs.NB) {
     const size_t N = (size_t)cs.N;
-    const int c = cs.bcell[b];
+    const int c = LFM_IDX(cs.bcell[b], cs.N, 0, kChkBFace);
     const double* s = cs.bSf + 3 * (size_t)b;
     const double mag = sqrt(s[0] * s[0] + s[1] * s[1] + s[2] * s[2]);
     const double n0 = s[0] / mag, n1 = s[1] / mag, n2 = s[2] / mag;
@@ -178,7 +180,7 @@ __global__ void grad_weights_kernel(CaseDev cs, double* __restrict__ E) {
   const double rv = 1.0 / cs.V[c];
   for (int k = 0; k < cs.W; ++k) {
     const size_t at = (size_t)k * N + c;
-    const int f = cs.slot_face[at];
+    const int f = cs.slot_face[at] < 0 ? -1 : LFM_IDX(cs.slot_face[at], cs.F, 0, kChkFaceSlot);
     double e0 = 0.0, e1 = 0.0, e2 = 0.0;
     if (f >= 0) {
       const double w = cs.fw[f];
@@ -206,7 +208,7 @@ __global__ void case_ops_kernel(CaseDev cs, double* __restrict__ D, double* __re
   double d[3] = {0.0, 0.0, 0.0}, h[3] = {0.0, 0.0, 0.0}, kk[3] = {0.0, 0.0, 0.0};
   for (int k = 0; k < cs.W; ++k) {
     const size_t at = (size_t)k * N + c;
-    const int f = cs.slot_face[at];
+    const int f = cs.slot_face[at] < 0 ? -1 : LFM_IDX(cs.slot_face[at], cs.F, 0, kChkFaceSlot);
     double l[3] = {0.0, 0.0, 0.0};
     if (f >= 0) {
       const double w = cs.fw[f];
@@ -232,7 +234,7 @@ __global__ void case_ops_kernel(CaseDev cs, double* __restrict__ D, double* __re
     L[2 * WN + at] = l[2];
   }
   for (int k = cs.b_start[c]; k < cs.b_start[c + 1]; ++k) {
-    const int bf = cs.b_face[k];
+    const int bf = LFM_IDX(cs.b_face[k], cs.NB, 0, kChkBFace);
     const bool fv = cs.btype[bf] == LFM_FIXED_VALUE;
     for (int q = 0; q < 3; ++q) {
       const double s = cs.bSf[3 * (size_t)bf + q];
@@ -257,11 +259,13 @@ __global__ void dt_cells_kernel(CaseDev cs, const double* __restrict__ DTc, cons
                                 double* __restrict__ DTf, double* __restrict__ DTb) {
   const int i = blockIdx.x * blockDim.x + threadIdx.x;
   if (i < cs.F) {
-    const uint2 at = reinterpret_cast<const uint2*>(cs.face_slots)[i];
-    const double dP = DTc[cs.slot_other[at.y]], dN = DTc[cs.slot_other[at.x]];
+    const uint2 a0 = reinterpret_cast<const uint2*>(cs.face_slots)[i];
+    const uint2 at = make_uint2(LFM_IDX(a0.x, cs.W * cs.N, 0, kChkFaceSlot), LFM_IDX(a0.y, cs.W * cs.N, 0, kChkFaceSlot));
+    const double dP = DTc[LFM_IDX(cs.slot_other[at.y], cs.N, 0, kChkSlotCell)];
+    const double dN = DTc[LFM_IDX(cs.slot_other[at.x], cs.N, 0, kChkSlotCell)];
     DTf[i] = __dadd_rn(__dmul_rn(w[i], __dsub_rn(dP, dN)), dN);
   }
-  if (i < cs.NB) DTb[i] = DTc[cs.bcell[i]];
+  if (i < cs.NB) DTb[i] = DTc[LFM_IDX(cs.bcell[i], cs.N, 0, kChkBFace)];
 }
 
 __global__ void times_volume_kernel(const double* __restrict__ V, const double* __restrict__ a,
@@ -421,5 +425,26 @@ cudaError_t launch_fill(double* a, size_t n, double v, cudaStream_t stream) {
   fill_kernel<<<(unsigned)blocks, 256, 0, stream>>>(a, n, v);
   return cudaGetLastError();
 }
+
+#ifdef LFM_CHECKED
+int check_take_step(cudaStream_t s) {
+  int site = 0;
+  const int zero = 0;
+  if (cudaMemcpyFromSymbolAsync(&site, g_check_site, sizeof(int), 0, cudaMemcpyDeviceToHost, s) != cudaSuccess ||
+      cudaMemcpyToSymbolAsync(g_check_site, &zero, sizeof(int), 0, cudaMemcpyHostToDevice, s) != cudaSuccess ||
+      cudaMemcpyToSymbolAsync(g_check_inject, &zero, sizeof(int), 0, cudaMemcpyHostToDevice, s) != cudaSuccess ||
+      cudaStreamSynchronize(s) != cudaSuccess)
+    return -1;
+  return site;
+}
+
+void check_inject_step(int site, cudaStream_t s) {
+  cudaMemcpyToSymbolAsync(g_check_inject, &site, sizeof(int), 0, cudaMemcpyHostToDevice, s);
+  cudaStreamSynchronize(s);
+}
+#else
+int check_take_step(cudaStream_t) { return 0; }
+void check_inject_step(int, cudaStream_t) {}
+#endif
 
 }  // namespace lfm
