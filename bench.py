@@ -314,6 +314,20 @@ def time_device_resident(solver, B, torch, stream, n_steps: int):
     return ev0.elapsed_time(ev1) * 1e-3, stats
 
 
+def repeat_runs(solver, B, torch, stream, n_steps: int, N: int, T_start, first: float, runs: int) -> dict:
+    """Spread of the timed region: `runs` regions of the same n_steps from the same starting
+    field (the headline region first; each other one restarts from T_start, set outside the
+    timed region), as cell-iterations/s of this rank."""
+    vals = [first]
+    for _ in range(max(0, runs - 1)):
+        solver.set_field(T_start)
+        secs, st = time_device_resident(solver, B, torch, stream, n_steps)
+        vals.append(float(N) * sum(x["iters"] for x in st) / secs)
+    return {"runs": len(vals), "median": statistics.median(vals),
+            "std": statistics.pstdev(vals) if len(vals) > 1 else 0.0, "min": min(vals), "max": max(vals),
+            "unit": UNIT, "note": "the headline region and its repeats from the same starting field"}
+
+
 def main_ours(args, world, rank, local):
     import torch
 
@@ -335,6 +349,7 @@ def main_ours(args, world, rank, local):
     # ---- FP64, device-resident --------------------------------------------------------
     s64 = Solver.from_case(case, mesh=mesh, device=local, stream=stream)
     s64.advance(W)
+    T_start = s64.field().copy()
     clocks = ClockSampler(local)
     barrier(world)
     torch.cuda.synchronize()
@@ -354,12 +369,14 @@ def main_ours(args, world, rank, local):
     ratio = load_traffic_ratio("graded200_fp64")
     T64 = s64.field()
     launch = s64.launch()
+    spread = repeat_runs(s64, B, torch, stream, K, N, T_start, float(N) * iters / secs, args.repeats)
 
     # ---- df64 (double-float on the FP32 pipe), device-resident -----------------------
     df64 = None
     if not args.no_df64:
         sdf = Solver.from_case(case.with_(precision=B.LFM_DF64), mesh=mesh, device=local, stream=stream)
         sdf.advance(W)
+        Td_start = sdf.field().copy()
         barrier(world)
         dsecs, dst = time_device_resident(sdf, B, torch, stream, K)
         barrier(world)
@@ -370,6 +387,7 @@ def main_ours(args, world, rank, local):
         dvalue = reduce_sum(float(N) * diters, world) / dsecs_max
         dalg = algorithmic_bytes(N, F, diters, K, 0)
         Td = sdf.field()
+        dspread = repeat_runs(sdf, B, torch, stream, K, N, Td_start, float(N) * diters / dsecs, args.repeats)
         dratio = load_traffic_ratio("graded200_df64")
         df64 = {"value": dvalue, "unit": UNIT, "ms_per_step": 1e3 * dsecs_max / K,
                 "iters_per_step": diters / K,
@@ -379,6 +397,7 @@ def main_ours(args, world, rank, local):
                 "dtype": "df64 (FP32 pairs, 48-bit significand; FP64 scalars)",
                 "phases_ms_per_step": dphases,
                 "solve_only": solve_only(N, diters, K, dphases),
+                "spread": dspread,
                 "roofline": {"bound": "hbm", "achieved": dalg / dsecs / 1e9, "peak": hbm_peak, "unit": "GB/s",
                              "frac": dalg / dsecs / 1e9 / hbm_peak,
                              "frac_of_nominal": dalg / dsecs / 1e9 / HBM_NOMINAL_GBS,
@@ -392,6 +411,7 @@ def main_ours(args, world, rank, local):
     if not args.no_mixed:
         smx = Solver.from_case(case.with_(precision=B.LFM_MIXED), mesh=mesh, device=local, stream=stream)
         smx.advance(W)
+        Tm_start = smx.field().copy()
         barrier(world)
         msecs, mst = time_device_resident(smx, B, torch, stream, K)
         barrier(world)
@@ -402,6 +422,7 @@ def main_ours(args, world, rank, local):
         mvalue = reduce_sum(float(N) * miters, world) / msecs_max
         malg = algorithmic_bytes(N, F, miters, K, 1)
         Tm = smx.field()
+        mspread = repeat_runs(smx, B, torch, stream, K, N, Tm_start, float(N) * miters / msecs, args.repeats)
         mratio = load_traffic_ratio("graded200_mixed")
         mixed = {"value": mvalue, "unit": UNIT, "ms_per_step": 1e3 * msecs_max / K,
                  "iters_per_step": miters / K, "sweeps_per_step": sum(x["sweeps"] for x in mst) / K,
@@ -409,6 +430,7 @@ def main_ours(args, world, rank, local):
                  "max_rel_diff_vs_fp64": float(np.max(np.abs(Tm - T64) / np.abs(T64))),
                  "phases_ms_per_step": mphases,
                  "solve_only": solve_only(N, miters, K, mphases),
+                 "spread": mspread,
                  "roofline": {"bound": "hbm", "achieved": malg / msecs / 1e9, "peak": hbm_peak, "unit": "GB/s",
                               "frac": malg / msecs / 1e9 / hbm_peak,
                               "frac_of_nominal": malg / msecs / 1e9 / HBM_NOMINAL_GBS,
@@ -473,6 +495,7 @@ def main_ours(args, world, rank, local):
         "per_step_passes_ms": phases["assembly_faces"] + phases["rows_initial_residual"],
         "iteration_passes_ms_per_step": phases["p_update"] + phases["amul_dot"] + phases["update_dots"],
         "solve_only": solve_only(N, iters, K, phases),
+        "spread": spread,
         "roofline": {"bound": "hbm", "achieved": achieved_gbs, "peak": hbm_peak, "unit": "GB/s",
                      "frac": achieved_gbs / hbm_peak, "traffic": (ratio * alg / K) if ratio else None,
                      "frac_of_nominal": achieved_gbs / HBM_NOMINAL_GBS,
@@ -771,6 +794,8 @@ def main():
     ap.add_argument("--warmup", type=int, default=5)
     ap.add_argument("--impl", default="ours", choices=["ours", "reference"])
     ap.add_argument("--no-mixed", action="store_true")
+    ap.add_argument("--repeats", type=int, default=5,
+                    help="graded200: timed regions per form for the median / spread (the first is the headline)")
     ap.add_argument("--no-df64", action="store_true")
     ap.add_argument("--no-e2e", action="store_true")
     ap.add_argument("--no-cpu-baseline", action="store_true")
@@ -784,9 +809,10 @@ def main():
     args.steps_given = any(a.startswith("--steps") for a in sys.argv[1:])
     if args.warmup < 3:
         ap.error("--warmup must be >= 3")
-    if args.only:
+    if args.only:  # profiling: one timed launch per form
         args.no_e2e = args.no_cpu_baseline = True
         args.no_mixed = args.no_df64 = args.only == "fp64"
+        args.repeats = 1
     world, rank, local = dist_setup()
     try:
         if args.impl == "reference":
