@@ -252,7 +252,7 @@ def test_bound_workspace_too_small():
 
 # ---- mixed precision ------------------------------------------------------------------
 
-@pytest.mark.parametrize("name", ["plain20", "graded40", "permuted20", "ragged", "insulated", "line"])
+@pytest.mark.parametrize("name", ["plain20", "graded40", "permuted20", "ragged", "insulated", "line", "permuted100"])
 def test_mixed_within_1e5_of_fp64_oracle(name):
     case = CASES[name]()
     T, st, _ = gpu_run(case, precision=B.LFM_MIXED)
