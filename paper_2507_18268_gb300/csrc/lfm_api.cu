@@ -1479,8 +1479,8 @@ struct lfm_batch {
   int n_active = 0;
   // captured one-step graph
   cudaGraphExec_t gexec = nullptr;
-  int g_threads = 0, g_W = -1, g_ctas = 0;
-  int last_ctas = 0, last_W = 6;
+  int g_threads = 0, g_W = -1, g_ctas = 0, g_form = -1;
+  int last_ctas = 0, last_W = 6, last_form = kBatchAny;
 };
 
 namespace {
@@ -1643,7 +1643,7 @@ int lfm_batch_set_launch(lfm_batch* b, int32_t threads, const int32_t* cells_per
 int lfm_batch_get_launch(lfm_batch* b, int32_t* ctas, int32_t* threads, int32_t* cells_per_thread) {
   if (!b) return bfail(nullptr, LFM_EINVAL, "batch is NULL");
   DeviceGuard g(b->device);
-  if (ctas) *ctas = max_coresident_batch_ctas(b->threads, b->last_W, b->device);
+  if (ctas) *ctas = max_coresident_batch_ctas(b->threads, b->last_W, b->last_form, b->device);
   if (threads) *threads = b->threads;
   if (cells_per_thread)
     for (int k = 0; k < 3; ++k) cells_per_thread[k] = b->cpt[k];
@@ -1671,7 +1671,7 @@ int lfm_batch_advance_async(lfm_batch* b, int32_t n_steps, int32_t use_graph) {
   if (n == 0 || n_steps == 0) return LFM_OK;
   int rc = ensure_capacity(b, n);
   if (rc) return rc;
-  int W = 6;
+  int W = 6, form = kBatchAny;
   for (int i = 0; i < n; ++i) {
     lfm_ctx* c = b->slots[b->order[i]];
     if (c->pending_steps) return bfail(b, LFM_ESTATE, "case %d has a pending advance of its own", b->order[i]);
@@ -1684,8 +1684,11 @@ int lfm_batch_advance_async(lfm_batch* b, int32_t n_steps, int32_t use_graph) {
       return bfail(b, LFM_ECUDA, "case %d: coefficient set-up failed", b->order[i]);
     b->h_cases[i] = c->cs;
     if (c->W != 6) W = 0;
+    const int p = c->opts.precision;
+    const int f = p == LFM_FP64 ? kBatchFp64 : p == LFM_DF64 ? kBatchDf64 : kBatchAny;
+    form = i == 0 ? f : (form == f ? form : kBatchAny);
   }
-  const int ctas = max_coresident_batch_ctas(b->threads, W, b->device);
+  const int ctas = max_coresident_batch_ctas(b->threads, W, form, b->device);
   if (ctas <= 0) return bfail(b, LFM_ECUDA, "no co-resident CTA fits the batch kernel");
   // jobs: team sizes from the size classes, longest (estimated) job first
   std::vector<int> k(n), idx(n);
@@ -1729,10 +1732,12 @@ int lfm_batch_advance_async(lfm_batch* b, int32_t n_steps, int32_t use_graph) {
   bl.launch.timeout_ns = b->timeout_ns;
   bl.launch.skip_cta = -1;
   bl.W = W;
+  bl.form = form;
   b->last_ctas = ctas;
   b->last_W = W;
+  b->last_form = form;
   if (use_graph) {
-    if (!b->gexec || b->g_threads != b->threads || b->g_W != W || b->g_ctas != ctas) {
+    if (!b->gexec || b->g_threads != b->threads || b->g_W != W || b->g_ctas != ctas || b->g_form != form) {
       if (b->gexec) cudaGraphExecDestroy(b->gexec);
       b->gexec = nullptr;
       cudaGraph_t graph = nullptr;
@@ -1750,6 +1755,7 @@ int lfm_batch_advance_async(lfm_batch* b, int32_t n_steps, int32_t use_graph) {
       b->g_threads = b->threads;
       b->g_W = W;
       b->g_ctas = ctas;
+      b->g_form = form;
     }
     for (int s = 0; s < n_steps; ++s) BCK(b, cudaGraphLaunch(b->gexec, b->stream));
   } else {

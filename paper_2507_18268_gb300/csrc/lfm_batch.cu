@@ -20,7 +20,7 @@
 namespace lfm {
 namespace {
 
-template <int B, int W>
+template <int B, int W, int kForm>
 __global__ void __launch_bounds__(B, 1024 / B) batch_kernel(const CaseDev* __restrict__ cases,
                                                   const int32_t* __restrict__ job_case,
                                                   const int32_t* __restrict__ job_start, BatchHeader* hdr,
@@ -58,12 +58,18 @@ __global__ void __launch_bounds__(B, 1024 / B) batch_kernel(const CaseDev* __res
     __syncthreads();
     const Team tm{s_job[2], s_job[1], s_cs.sync, s_cs.partials, L.timeout_ns};
     const int base = case_step[c];
-    if (s_cs.precision == LFM_MIXED)
-      run_steps_mixed_any<B, W>(s_cs, s_cs, tm, n_steps, kModeSteps, sh, base);
-    else if (s_cs.precision == LFM_DF64)
-      run_steps_df64<B, W, true>(s_cs, s_cs, tm, n_steps, sh, base);
-    else
+    if constexpr (kForm == kBatchFp64) {
       run_steps_f64<B, W>(s_cs, s_cs, tm, n_steps, kModeSteps, sh, base);
+    } else if constexpr (kForm == kBatchDf64) {
+      run_steps_df64<B, W, true>(s_cs, s_cs, tm, n_steps, sh, base);
+    } else {
+      if (s_cs.precision == LFM_MIXED)
+        run_steps_mixed_any<B, W>(s_cs, s_cs, tm, n_steps, kModeSteps, sh, base);
+      else if (s_cs.precision == LFM_DF64)
+        run_steps_df64<B, W, true>(s_cs, s_cs, tm, n_steps, sh, base);
+      else
+        run_steps_f64<B, W>(s_cs, s_cs, tm, n_steps, kModeSteps, sh, base);
+    }
     __syncthreads();
     if (tm.rank == 0 && threadIdx.x == 0) case_step[c] = base + n_steps;
     __syncthreads();
@@ -97,22 +103,25 @@ __global__ void batch_collect_kernel(const CaseDev* __restrict__ cases, int n_ca
 }
 
 template <int B>
-void* batch_fn_w(int W) {
-  return W == 6 ? (void*)batch_kernel<B, 6> : (void*)batch_kernel<B, 0>;
+void* batch_fn_w(int W, int form) {
+  if (W != 6) return (void*)batch_kernel<B, 0, kBatchAny>;
+  if (form == kBatchFp64) return (void*)batch_kernel<B, 6, kBatchFp64>;
+  if (form == kBatchDf64) return (void*)batch_kernel<B, 6, kBatchDf64>;
+  return (void*)batch_kernel<B, 6, kBatchAny>;
 }
 
-void* batch_fn(int threads, int W) {
+void* batch_fn(int threads, int W, int form) {
   switch (threads) {
-    case 256: return batch_fn_w<256>(W);
-    case 512: return batch_fn_w<512>(W);
+    case 256: return batch_fn_w<256>(W, form);
+    case 512: return batch_fn_w<512>(W, form);
     default: return nullptr;
   }
 }
 
 }  // namespace
 
-int max_coresident_batch_ctas(int threads, int W, int device) {
-  void* fn = batch_fn(threads, W);
+int max_coresident_batch_ctas(int threads, int W, int form, int device) {
+  void* fn = batch_fn(threads, W, form);
   if (!fn) return 0;
   int per_sm = 0, sms = 0;
   if (cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, fn, threads, 0) != cudaSuccess) return 0;
@@ -137,7 +146,7 @@ cudaError_t launch_batch_collect(const CaseDev* cases, int n_cases, const int32_
 // One batch step (or n fused steps): reset the ticket counter, then the cooperative launch.
 // Written with cudaLaunchKernelEx so that it can be captured into a CUDA graph.
 cudaError_t launch_batch_steps(const BatchLaunch& bl, int n_steps, cudaStream_t s) {
-  void* fn = batch_fn(bl.launch.threads, bl.W);
+  void* fn = batch_fn(bl.launch.threads, bl.W, bl.form);
   if (!fn) return cudaErrorInvalidValue;
   cudaError_t e = cudaMemsetAsync(&bl.hdr->ticket, 0, sizeof(int32_t), s);
   if (e != cudaSuccess) return e;

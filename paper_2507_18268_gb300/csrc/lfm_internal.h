@@ -175,7 +175,13 @@ struct BatchLaunch {
   int32_t* case_step;        // [n_cases] steps done in the current advance
   Launch launch;
   int W;
+  int form;  // kBatchAny, or the one precision every member runs (kernel compiled for it)
 };
+
+// Kernel variants of the batched step: any member precision, or FP64 / df64 members only
+// (the single-form kernels carry only their form's passes: less code around the iteration
+// loops; slot width 6 only).
+enum BatchForm { kBatchAny = 0, kBatchFp64 = 1, kBatchDf64 = 2 };
 
 // Kernel launchers (lfm_step.cu). Return a cudaError_t.
 cudaError_t launch_steps(const CaseDev& cs, const Launch& L, int n_steps, int mode,
@@ -222,7 +228,7 @@ void box_layout_host(long long nx, long long ny, long long nz, int W, const doub
                      double* bdelta);
 
 // Batched launchers (lfm_batch.cu).
-int max_coresident_batch_ctas(int threads, int W, int device);
+int max_coresident_batch_ctas(int threads, int W, int form, int device);
 cudaError_t launch_batch_prepare(const CaseDev* cases, int n_cases, int32_t* case_step, cudaStream_t s);
 cudaError_t launch_batch_collect(const CaseDev* cases, int n_cases, const int32_t* case_step, int32_t* status,
                                  int32_t* iters, cudaStream_t s);
