@@ -682,6 +682,7 @@ def main_batch(args, world, rank, local):
     stream = torch.cuda.Stream(device=local)
     results = {}
     fields = {}
+    clocks, clk = ClockSampler(local), None
     for prec, name in ((B.LFM_FP64, "fp64"), (B.LFM_DF64, "df64"), (B.LFM_MIXED, "mixed")):
         cases = [c.with_(precision=prec) for c in base_cases]
         bt = Batch(device=local, stream=stream)
@@ -694,6 +695,8 @@ def main_batch(args, world, rank, local):
             bt.cases[cid].set_field(T0[cid])
         torch.cuda.synchronize()
         mark = args.profile_range and prec == B.LFM_FP64
+        if prec == B.LFM_FP64 and rank == 0:  # clocks during the headline (FP64) timed region
+            clocks.start()
         if mark:  # the FP64 timed region is the profiler range (ncu --profile-from-start off)
             torch.cuda.profiler.start()
         ev0, ev1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
@@ -704,6 +707,8 @@ def main_batch(args, world, rank, local):
         torch.cuda.synchronize()
         if mark:
             torch.cuda.profiler.stop()
+        if prec == B.LFM_FP64 and rank == 0:
+            clk = clocks.stop()
         assert rc == B.LFM_OK, B.lfm_batch_last_error(bt.handle)
         secs = ev0.elapsed_time(ev1) * 1e-3
         cell_iters = 0
@@ -749,6 +754,7 @@ def main_batch(args, world, rank, local):
             "config": {"workload": f"batch{n_cases}: {n_cases} cases, edge log-uniform 16..96 (seed 3), "
                                    f"{total_cells} cells in total, {steps} steps each, graph-replayed step",
                        "parallelism": "single GPU"},
+            "clocks": clk,
             "batched_fp64": results["fp64"], "batched_df64": results["df64"], "batched_mixed": results["mixed"],
             "plain_fp64_sequential": results["plain_fp64_sequential"],
             "speedup_batched_fp64_vs_plain": results["fp64"]["value"] / results["plain_fp64_sequential"]["value"],
@@ -770,7 +776,11 @@ def main_serve(args, world, rank, local):
     warm = lapcase.serving_stream(n_requests=8, seed=99, n_min=16, n_max=24, max_steps=2)
     srv = Server(device=local, budget_bytes=120e9)
     srv.run(warm)
+    clocks = ClockSampler(local)
+    if rank == 0:
+        clocks.start()
     rep = srv.run(reqs)
+    clk = clocks.stop() if rank == 0 else None
     srv.close()
     serial = serve_serial_fp64(reqs, device=local)
     if rank != 0:
@@ -786,7 +796,7 @@ def main_serve(args, world, rank, local):
             "data": "synthetic",
             "config": {"workload": f"serve: {args.requests} requests, Poisson 200/s (seed 4), edge log-uniform "
                                    "32..160, 1..50 steps, FP64/mixed 50/50, 120 GB HBM budget, one step per tick"},
-            "served": served, "serial_plain_fp64": {k: serial[k] for k in keys},
+            "clocks": clk, "served": served, "serial_plain_fp64": {k: serial[k] for k in keys},
             "p99_latency_ratio_serial_over_served": serial["p99_latency_s"] / rep["p99_latency_s"],
             "throughput_ratio_served_over_serial": rep["throughput_req_s"] / serial["throughput_req_s"]}
     print(json.dumps(line), flush=True)
