@@ -50,7 +50,9 @@ enum { LFM_FIXED_VALUE = 0, LFM_ZERO_GRADIENT = 1 };
  *   LFM_FP64   IEEE FP64 throughout; the assembled system is bitwise the CPU reference's.
  *   LFM_MIXED  FP32 inner CG inside FP64-class defect correction (results ~1e-6 relative):
  *              the outer passes (true residual, correction) use the LFM_DF64 machinery on
- *              orthogonal meshes and FP64 on general ones.
+ *              orthogonal meshes and FP64 on general ones. Within one advance, each step's
+ *              verification pass also assembles the next step (no sources or correctors);
+ *              results equal those of one-step advances bit for bit.
  *   LFM_DF64   every per-cell operation in double-float (pairs of FP32 numbers, 48-bit
  *              significand) on the FP32 pipe, per-CTA scalars in FP64: results agree with
  *              FP64 to rounding (~1e-13 relative), at FP32-pipe speed; any mesh (general
@@ -419,13 +421,18 @@ int lfm_batch_set_barrier_timeout(lfm_batch *b, uint64_t ns);
 
 /* Enqueues n_steps (<= 1024) steps of every member case. use_graph != 0: one step is
  * captured once into a CUDA graph (ticket reset + persistent kernel) and the graph is
- * launched n_steps times; use_graph == 0: one launch runs all n_steps. */
+ * launched n_steps times; use_graph == 0: one launch runs all n_steps. Members may mix
+ * precisions; when every member runs LFM_FP64, or every member LFM_DF64 (hexahedral slot
+ * width), the launch uses a kernel compiled for that precision alone (same results, less
+ * code around the iteration loops). */
 int lfm_batch_advance_async(lfm_batch *b, int32_t n_steps, int32_t use_graph);
 
 /* 1 while the pending advance runs, LFM_OK when done or none pending. */
 int lfm_batch_query(lfm_batch *b);
 
-/* Waits for the pending advance; returns LFM_OK or the first failing case's status. */
+/* Waits for the pending advance; returns LFM_OK or the first failing case's status (the
+ * checked build also returns LFM_EINVAL when a kernel met an index out of range; see
+ * lfm_checked_build). */
 int lfm_batch_finish(lfm_batch *b);
 
 /* Status of one case in the last finished advance. */
