@@ -36,7 +36,9 @@
  *
  * Parity status: every function here is pinned by the CPU tests (dense LU solve, closed-form
  * steady and transient solutions, matrix symmetry and row sums, energy balance, permutation
- * invariance, finite termination of CG, a hand-computed two-cell normFactor; for the general
+ * invariance, finite termination of CG, hand-computed two-cell normFactors -- one with unequal
+ * volumes, diagonals and row sums, which fixes the unweighted mean and the row sums -- and the
+ * strict '<' of the convergence test at exact ties; for the general
  * geometry, gradient and corrected laplacian see the block below; cell-field DT and sources:
  * uniform and linear interpolation, the series-conductance steady state, closed-form source
  * steps and energy balance).

@@ -189,6 +189,68 @@ def test_two_cell_worked_example():
     np.testing.assert_allclose(x, g["solution"], rtol=1e-13)
 
 
+def test_two_cell_unequal_volumes_pins_the_plain_mean():
+    # Unequal cell volumes, diagonals and row sums: normFactor uses the plain cell mean of the
+    # initial guess and the row sums of the assembled matrix (63/2). Weighted means, or the
+    # diagonal in place of the row sum, give other values (listed in the golden). One
+    # iteration is pinned too (x, and the recurrence residual), worked by hand.
+    g = json.load(open(os.path.join(GOLDEN, "two_cell_unequal.json")))
+    case = lapcase.RawCase(xs=np.array([0.0, 0.5, 2.0]), ys=np.array([0.0, 1.0]),
+                           zs=np.array([0.0, 1.0]), DT_uniform=g["DT"], dt=g["dt"],
+                           patches=((lapcase.FIXED_VALUE, g["patch_x0"]),) +
+                                   ((lapcase.ZERO_GRADIENT, 0.0),) * 5,
+                           T0=np.array(g["T_old"]), tol=1e-13)
+    mesh, btype, bvalue, T_old, diag, upper, source = _assembled(case)
+    np.testing.assert_allclose(mesh.V, g["V"], rtol=1e-15)
+    np.testing.assert_allclose(diag, g["diag"], rtol=1e-15)
+    np.testing.assert_allclose(upper, g["upper"], rtol=1e-15)
+    np.testing.assert_allclose(source, g["source"], rtol=1e-15)
+    x, st, _ = oracle.pcg(mesh.owner, mesh.neighbour, diag, upper, source, T_old, tol=1e-13)
+    assert math.isclose(st.norm_factor, g["norm_factor"], rel_tol=1e-15)
+    for wrong in g["norm_factor_wrong"].values():
+        assert not math.isclose(st.norm_factor, wrong, rel_tol=1e-3)
+    assert math.isclose(st.init_res, g["init_res"], rel_tol=1e-15)
+    assert st.iters == g["iterations"]
+    np.testing.assert_allclose(x, g["solution"], rtol=1e-14)
+    x1, st1, _ = oracle.pcg(mesh.owner, mesh.neighbour, diag, upper, source, T_old, tol=1e-13, max_iter=1)
+    assert st1.iters == 1 and not st1.converged
+    np.testing.assert_allclose(x1, g["x_after_1"], rtol=1e-14)
+    assert math.isclose(st1.final_res, g["res_after_1"], rel_tol=1e-14)
+    # the same system through the whole step (assembly + solve) of the advance entry point
+    T, sts = oracle.advance(case, n_steps=1)
+    np.testing.assert_allclose(T, g["solution"], rtol=1e-14)
+    assert math.isclose(sts[0].norm_factor, g["norm_factor"], rel_tol=1e-15)
+
+
+def test_convergence_test_is_strict_at_a_tie():
+    # res == tol exactly must not count as converged (strict '<'), before the first iteration
+    # and after one: with '<=' the solve would stop one iteration earlier.
+    g = json.load(open(os.path.join(GOLDEN, "two_cell_unequal.json")))
+    case = lapcase.RawCase(xs=np.array([0.0, 0.5, 2.0]), ys=np.array([0.0, 1.0]),
+                           zs=np.array([0.0, 1.0]), DT_uniform=g["DT"], dt=g["dt"],
+                           patches=((lapcase.FIXED_VALUE, g["patch_x0"]),) +
+                                   ((lapcase.ZERO_GRADIENT, 0.0),) * 5,
+                           T0=np.array(g["T_old"]))
+    mesh, btype, bvalue, T_old, diag, upper, source = _assembled(case)
+    args = (mesh.owner, mesh.neighbour, diag, upper, source, T_old)
+    _, st0, _ = oracle.pcg(*args, tol=1e-13, max_iter=1)
+    assert math.isclose(st0.init_res, 19.0 / 21.0, rel_tol=1e-15)
+    _, st, _ = oracle.pcg(*args, tol=st0.init_res)           # tie before the first iteration
+    assert st.iters >= 1
+    _, st, _ = oracle.pcg(*args, tol=math.nextafter(st0.init_res, 1.0))
+    assert st.iters == 0 and st.converged
+    st1 = st0
+    _, st, _ = oracle.pcg(*args, tol=st1.final_res)          # tie after the first iteration
+    assert st.iters == 2 and st.final_res < st1.final_res
+    _, st, _ = oracle.pcg(*args, tol=math.nextafter(st1.final_res, 1.0))
+    assert st.iters == 1 and st.converged
+    # relTol ties: res == relTol * initRes is not converged either
+    rel = st1.final_res / st0.init_res
+    if rel * st0.init_res == st1.final_res:
+        _, st, _ = oracle.pcg(*args, tol=0.0, rel_tol=rel)
+        assert st.iters == 2
+
+
 # ---------------------------------------------------------------------------------------
 # Closed forms: linear steady state and the 1D Fourier-series transient
 # ---------------------------------------------------------------------------------------
