@@ -258,11 +258,18 @@ int lfm_set_diffusivity_cells(lfm_ctx *ctx, const double *DT_cells, const double
 int lfm_set_source(lfm_ctx *ctx, const double *Su, const double *Sp);
 
 /* Patch type (LFM_FIXED_VALUE / LFM_ZERO_GRADIENT) and, for fixedValue, the boundary
- * values: values[patch_size[patch]] or, when values is NULL, `uniform` on every face. */
+ * values: values[patch_size[patch]] or, when values is NULL, `uniform` on every face. The
+ * boundary conditions of T in Eq. (1) (section "The laplacianFoam application": T is read
+ * with its patch types): a fixedValue face adds its conductance DT|Sb|/|C_b - C_P| to the
+ * diagonal and that times the value to the source; a zeroGradient face adds nothing. The
+ * values are deep-copied; LFM_EINVAL for a patch index or type out of range or a
+ * non-finite value. */
 int lfm_set_patch(lfm_ctx *ctx, int32_t patch, int32_t type, const double *values,
                   double uniform);
 
-/* Time step (finite, > 0). */
+/* Time step deltaT of the implicit Euler ddt term of Eq. (1) (fvm::ddt(T) in the listing
+ * "laplacianFoam application": V/deltaT on the diagonal, V/deltaT T_old in the source).
+ * LFM_EINVAL unless finite and > 0; V/deltaT is recomputed on the device. */
 int lfm_set_time_step(lfm_ctx *ctx, double dt);
 
 /* Solver controls (tol >= 0, rel_tol >= 0, max_iter >= 1, 0 <= min_iter <= max_iter). */
@@ -276,8 +283,13 @@ int lfm_set_field_device(lfm_ctx *ctx, const double *T_dev);
 
 /* Runs n_steps implicit steps on the device: per step assemble, initial residual and
  * normFactor, PCG iterations, all inside device-side control flow; T_old <- T each step.
- * Synchronises before return; out (host, n_steps records, may be NULL) receives the
- * per-step statistics. */
+ * One step is one pass of the time loop in the listing "laplacianFoam application":
+ * assemble TEqn = fvm::ddt(T) - fvm::laplacian(DT, T) (Eq. (1)) and solve it with the
+ * diagonal-preconditioned CG named in section "Evaluation" (stopping on the normFactor-
+ * scaled L1 residual). Synchronises before return; out (host, n_steps records, may be
+ * NULL) receives the per-step statistics. Non-convergence is reported in the records, not
+ * as an error; LFM_ESTATE before an upload, LFM_ETIMEOUT / LFM_ENONFINITE / LFM_ESINGULAR
+ * from the device (the context stays usable). */
 int lfm_advance(lfm_ctx *ctx, int32_t n_steps, lfm_step_stats *out);
 
 /* Enqueues n_steps like lfm_advance without waiting (statistics stay on the device until
@@ -293,7 +305,10 @@ int lfm_finish(lfm_ctx *ctx, lfm_step_stats *out, int32_t n);
 
 /* Reads T[n_cells] to host memory and, when T_boundary is not NULL, the boundary-face
  * values T_boundary[n_bfaces] (fixedValue: the set value; zeroGradient: the face cell's T),
- * both computed on the device. Synchronises before return. */
+ * both computed on the device: the field the laplacianFoam listing writes at the end of a
+ * time step, with its boundary values as the patch types define them (section "Code
+ * Porting": the boundary evaluation of a field). T_out is a caller-owned host buffer;
+ * synchronises before return; LFM_ESTATE before an upload. */
 int lfm_get_field(lfm_ctx *ctx, double *T_out, double *T_boundary);
 
 /* Device pointer of the context's T[n_cells] (float64), valid until lfm_destroy, for reading
@@ -362,10 +377,15 @@ int lfm_debug_check_inject(lfm_ctx *ctx, int32_t site);
  * lfm_advance, FP64 only (opts->precision must be LFM_FP64), where A is given in LDU form
  * in device memory the caller owns: owner/neighbour[n_faces] (owner < neighbour, sorted by
  * owner), diag[n_cells], upper[n_faces] (lower == upper), source[n_cells]; x[n_cells]
- * (device) holds the initial guess and receives the solution. stats (host, may be NULL)
- * receives the solve record. Runs on cuda_stream and synchronises before return.
+ * (device) holds the initial guess and receives the solution. x must not overlap any input
+ * array (LFM_EINVAL). stats (host, may be NULL) receives the solve record. Runs on
+ * cuda_stream; every call synchronises that stream before it returns (it reads the record
+ * back), so the result is in x on return.
  * Limits: n_cells <= 65536 and n_faces <= 262144, else LFM_EINVAL before any device work;
- * an invalid owner/neighbour array is reported as LFM_EINVAL by the kernel.
+ * at most 32 internal faces per cell (as lfm_upload_mesh). A face out of range, faces not
+ * sorted by owner or a cell above the face limit are reported as LFM_EINVAL by the kernel
+ * before it uses any of those indices as an address; x is then left unchanged. Every
+ * non-OK return sets the text of lfm_last_error(NULL) on the calling thread.
  * Working memory: one fixed device array of about 4.8 MB inside the library, present on
  * every GPU that loads it until the process exits; no call allocates, frees or calls an
  * allocating library routine. All calls share that array (each call re-initialises what it

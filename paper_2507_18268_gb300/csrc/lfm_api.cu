@@ -170,6 +170,16 @@ struct DeviceGuard {
 
 }  // namespace
 
+int lfm::set_last_error(int code, const char* fmt, ...) {
+  char buf[512];
+  va_list ap;
+  va_start(ap, fmt);
+  vsnprintf(buf, sizeof buf, fmt, ap);
+  va_end(ap);
+  g_last_error = buf;
+  return code;
+}
+
 struct lfm_batch;
 
 struct lfm_ctx {

@@ -236,6 +236,10 @@ cudaError_t launch_batch_steps(const BatchLaunch& bl, int n_steps, cudaStream_t 
 cudaError_t launch_fill(double* a, size_t n, double v, cudaStream_t stream);
 cudaError_t launch_vdt(const double* V, double dt, double* vdt, int n, cudaStream_t stream);
 
+// Records the reason for a failed context-free call (the text lfm_last_error(NULL) returns
+// on this thread); defined with the thread-local error text in lfm_api.cu. Returns code.
+int set_last_error(int code, const char* fmt, ...);
+
 // Index checks of the checked build (lfm_device.cuh), per kernel translation unit: take
 // returns the first failing check site recorded on the current device since the last take
 // (0: none) and clears it and the injection hook; inject makes `site` report as failing

@@ -40,7 +40,12 @@ constexpr size_t kOffLoFill = kOffLoStart + align256(4 * ((size_t)kMaxCells + 1)
 constexpr size_t kOffLosort = kOffLoFill + align256(4 * (size_t)kMaxCells);
 constexpr size_t kOffLoOther = kOffLosort + align256(4 * (size_t)kMaxFaces);
 constexpr size_t kOffStats = kOffLoOther + align256(4 * (size_t)kMaxFaces);
-constexpr size_t kScratchBytes = kOffStats + align256(sizeof(lfm_step_stats));
+constexpr size_t kOffReason = kOffStats + align256(sizeof(lfm_step_stats));
+constexpr size_t kScratchBytes = kOffReason + align256(2 * sizeof(int32_t));
+
+// Why the kernel rejected the addressing (first int of the reason words; the second holds a
+// face or cell id).
+enum Reason { kBadNone = 0, kBadFace = 1, kBadOrder = 2, kBadDegree = 3 };
 
 static __device__ __align__(256) unsigned char g_static_scratch[kScratchBytes];
 
@@ -48,6 +53,7 @@ struct Scratch {
   double *r, *w, *p, *q;
   int32_t *own_start, *lo_start, *lo_fill, *losort, *lo_other;
   lfm_step_stats* stats;
+  int32_t* reason;  // [2] Reason and the offending face or cell
 };
 
 __device__ __forceinline__ Scratch carve(unsigned char* base) {
@@ -62,6 +68,7 @@ __device__ __forceinline__ Scratch carve(unsigned char* base) {
   s.losort = reinterpret_cast<int32_t*>(base + kOffLosort);
   s.lo_other = reinterpret_cast<int32_t*>(base + kOffLoOther);
   s.stats = reinterpret_cast<lfm_step_stats*>(base + kOffStats);
+  s.reason = reinterpret_cast<int32_t*>(base + kOffReason);
   return s;
 }
 
@@ -120,14 +127,20 @@ __global__ void __launch_bounds__(kThreads) static_pcg_kernel(
   __syncthreads();
 
   // ---- face-to-cell lists ---------------------------------------------------------------
+  // Nothing read from owner/neighbour is used as an address before it has been checked; a
+  // rejected system leaves x untouched.
   for (int f = tid; f < F; f += kThreads) {
     const int32_t o = owner[f], n = neighbour[f];
-    if (o < 0 || n <= o || n >= N || (f > 0 && owner[f - 1] > o)) s_bad = 1;
+    const int bad = (o < 0 || n <= o || n >= N) ? kBadFace : (f > 0 && owner[f - 1] > o) ? kBadOrder : kBadNone;
+    if (bad && atomicCAS(&s_bad, 0, bad) == 0) s.reason[1] = f;
   }
   for (int c = tid; c < N; c += kThreads) s.lo_fill[c] = 0;
   __syncthreads();
   if (s_bad) {
-    if (tid == 0) s.stats->status = LFM_EINVAL;
+    if (tid == 0) {
+      s.reason[0] = s_bad;
+      s.stats->status = LFM_EINVAL;
+    }
     return;
   }
   for (int f = tid; f < F; f += kThreads) atomicAdd(&s.lo_fill[neighbour[f]], 1);
@@ -141,6 +154,19 @@ __global__ void __launch_bounds__(kThreads) static_pcg_kernel(
     s.own_start[c] = lo;
   }
   __syncthreads();
+  // at most kMaxSlots internal faces per cell (the limit of the context path): it bounds the
+  // per-cell list sort below and every row's work
+  for (int c = tid; c < N; c += kThreads)
+    if (s.lo_fill[c] + s.own_start[c + 1] - s.own_start[c] > lfm::kMaxSlots && atomicCAS(&s_bad, 0, kBadDegree) == 0)
+      s.reason[1] = c;
+  __syncthreads();
+  if (s_bad) {
+    if (tid == 0) {
+      s.reason[0] = s_bad;
+      s.stats->status = LFM_EINVAL;
+    }
+    return;
+  }
   // exclusive scan of the neighbour-side counts: each thread scans a contiguous run
   const int per = (N + kThreads - 1) / kThreads;
   const int a0 = tid * per, a1 = min(N, a0 + per);
@@ -180,7 +206,8 @@ __global__ void __launch_bounds__(kThreads) static_pcg_kernel(
     s.losort[s.lo_start[n] + atomicAdd(&s.lo_fill[n], 1)] = f;
   }
   __syncthreads();
-  // ascending face order inside each cell's short list, so every run sums in the same order
+  // ascending face order inside each cell's short list (at most kMaxSlots entries), so every
+  // run sums in the same order
   for (int c = tid; c < N; c += kThreads) {
     const int b = s.lo_start[c], e = s.lo_start[c + 1];
     for (int i = b + 1; i < e; ++i) {
@@ -298,29 +325,73 @@ int scratch_for_current_device(unsigned char** out) {
 
 }  // namespace
 
+namespace {
+
+// Whether the byte ranges [a, a + na) and [b, b + nb) overlap.
+bool overlaps(const void* a, size_t na, const void* b, size_t nb) {
+  const uintptr_t x = reinterpret_cast<uintptr_t>(a), y = reinterpret_cast<uintptr_t>(b);
+  return na > 0 && nb > 0 && x < y + nb && y < x + na;
+}
+
+}  // namespace
+
 extern "C" int lfm_pcg_solve_static(int32_t n_cells, int32_t n_faces, const int32_t* owner,
                                     const int32_t* neighbour, const double* diag, const double* upper,
                                     const double* source, double* x, const lfm_solver_opts* opts,
                                     lfm_step_stats* stats, void* cuda_stream) {
-  if (n_cells <= 0 || n_faces < 0) return LFM_EINVAL;
-  if (n_cells > kMaxCells || n_faces > kMaxFaces) return LFM_EINVAL;
-  if (!diag || !source || !x || !opts || (n_faces > 0 && (!owner || !neighbour || !upper))) return LFM_EINVAL;
+  using lfm::set_last_error;
+  const char* me = "lfm_pcg_solve_static";
+  if (n_cells <= 0 || n_faces < 0)
+    return set_last_error(LFM_EINVAL, "%s: n_cells = %d, n_faces = %d (need n_cells > 0, n_faces >= 0)", me, n_cells,
+                          n_faces);
+  if (n_cells > kMaxCells || n_faces > kMaxFaces)
+    return set_last_error(LFM_EINVAL, "%s: %d cells, %d faces exceed the fixed limits of %d cells and %d faces", me,
+                          n_cells, n_faces, kMaxCells, kMaxFaces);
+  if (!diag || !source || !x || !opts || (n_faces > 0 && (!owner || !neighbour || !upper)))
+    return set_last_error(LFM_EINVAL, "%s: a required pointer is NULL", me);
   if (!(opts->tol >= 0) || !(opts->rel_tol >= 0) || opts->max_iter < 1 || opts->min_iter < 0 ||
       opts->min_iter > opts->max_iter || opts->precision != LFM_FP64)
-    return LFM_EINVAL;
+    return set_last_error(LFM_EINVAL,
+                          "%s: solver options (tol %g, rel_tol %g, max_iter %d, min_iter %d, precision %d) invalid; "
+                          "precision must be LFM_FP64",
+                          me, opts->tol, opts->rel_tol, opts->max_iter, opts->min_iter, opts->precision);
+  const size_t xb = sizeof(double) * (size_t)n_cells;
+  if (overlaps(x, xb, source, xb) || overlaps(x, xb, diag, xb) ||
+      overlaps(x, xb, upper, sizeof(double) * (size_t)n_faces) ||
+      overlaps(x, xb, owner, sizeof(int32_t) * (size_t)n_faces) ||
+      overlaps(x, xb, neighbour, sizeof(int32_t) * (size_t)n_faces))
+    return set_last_error(LFM_EINVAL, "%s: x overlaps an input array (the solve is not in place)", me);
   unsigned char* scratch = nullptr;
-  int rc = scratch_for_current_device(&scratch);
-  if (rc != LFM_OK) return rc;
+  if (scratch_for_current_device(&scratch) != LFM_OK)
+    return set_last_error(LFM_ECUDA, "%s: device address of the fixed working array not available", me);
   cudaStream_t stream = static_cast<cudaStream_t>(cuda_stream);
   lfm_step_stats* dev_stats = reinterpret_cast<lfm_step_stats*>(scratch + kOffStats);
-  // the status word must start at zero for every call
-  if (cudaMemsetAsync(dev_stats, 0, sizeof(lfm_step_stats), stream) != cudaSuccess) return LFM_ECUDA;
+  cudaError_t e;
+  // the status and reason words must start at zero for every call
+  if ((e = cudaMemsetAsync(scratch + kOffStats, 0, kScratchBytes - kOffStats, stream)) != cudaSuccess)
+    return set_last_error(LFM_ECUDA, "%s: clearing the status words: %s", me, cudaGetErrorString(e));
   static_pcg_kernel<<<1, kThreads, 0, stream>>>(scratch, n_cells, n_faces, owner, neighbour, diag, upper, source,
                                                 x, opts->tol, opts->rel_tol, opts->max_iter, opts->min_iter);
-  if (cudaGetLastError() != cudaSuccess) return LFM_ECUDA;
+  if ((e = cudaGetLastError()) != cudaSuccess)
+    return set_last_error(LFM_ECUDA, "%s: kernel launch: %s", me, cudaGetErrorString(e));
   lfm_step_stats st;
-  if (cudaMemcpyAsync(&st, dev_stats, sizeof st, cudaMemcpyDeviceToHost, stream) != cudaSuccess) return LFM_ECUDA;
-  if (cudaStreamSynchronize(stream) != cudaSuccess) return LFM_ECUDA;
+  int32_t reason[2] = {0, 0};
+  if ((e = cudaMemcpyAsync(&st, dev_stats, sizeof st, cudaMemcpyDeviceToHost, stream)) != cudaSuccess ||
+      (e = cudaMemcpyAsync(reason, scratch + kOffReason, sizeof reason, cudaMemcpyDeviceToHost, stream)) != cudaSuccess ||
+      (e = cudaStreamSynchronize(stream)) != cudaSuccess)
+    return set_last_error(LFM_ECUDA, "%s: %s", me, cudaGetErrorString(e));
   if (stats) *stats = st;
-  return st.status;
+  switch (st.status) {
+    case LFM_OK: return LFM_OK;
+    case LFM_EINVAL:
+      if (reason[0] == kBadFace)
+        return set_last_error(LFM_EINVAL, "%s: face %d: owner/neighbour out of range or owner >= neighbour", me,
+                              reason[1]);
+      if (reason[0] == kBadOrder)
+        return set_last_error(LFM_EINVAL, "%s: faces not sorted by owner at face %d", me, reason[1]);
+      return set_last_error(LFM_EINVAL, "%s: cell %d has more than %d internal faces", me, reason[1], lfm::kMaxSlots);
+    case LFM_ESINGULAR: return set_last_error(LFM_ESINGULAR, "%s: singular system (p.Ap / normFactor < 1e-300)", me);
+    case LFM_ENONFINITE: return set_last_error(LFM_ENONFINITE, "%s: non-finite residual", me);
+    default: return set_last_error(st.status, "%s: solver status %d", me, st.status);
+  }
 }

@@ -4,7 +4,8 @@
 Bar, as for FP64: max |T_gpu - T_oracle| / |T_oracle| <= 1e-10 after every run and PCG
 iteration counts equal to the oracle's on every step. The df64 form keeps 48 significand
 bits instead of 53, so it is rounding-level close to FP64 (~1e-13 relative on these cases),
-not bitwise; its reported normFactor and initial residual agree with the oracle's to 1e-8.
+not bitwise; its reported normFactor and initial residual are checked against the oracle's
+within the derived rounding bound (test_gpu_parity.py::test_stats_within_rounding_bound).
 """
 import functools
 
@@ -44,8 +45,8 @@ def assert_df_parity(T, st, To, so):
         assert g["iters"] == o.iters, (k, g, o)
         assert bool(g["converged"]) == o.converged
         assert g["status"] == 0
-        assert abs(g["norm_factor"] - o.norm_factor) <= 1e-8 * o.norm_factor
-        assert abs(g["init_res"] - o.init_res) <= 1e-8 * o.init_res + 1e-300
+    # normFactor and the initial residual of every step are checked against the derived
+    # rounding bound in test_gpu_parity.py::test_stats_within_rounding_bound (df64 form)
     assert relerr(T, To) <= RTOL
 
 
