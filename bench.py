@@ -328,6 +328,19 @@ def repeat_runs(solver, B, torch, stream, n_steps: int, N: int, T_start, first: 
             "unit": UNIT, "note": "the headline region and its repeats from the same starting field"}
 
 
+def run_workload(argv, timeout_s: float = 900.0):
+    """Runs this script with argv in a subprocess and returns its JSON line (None on failure)."""
+    try:
+        r = subprocess.run([sys.executable, os.path.abspath(__file__)] + argv, capture_output=True, text=True,
+                           timeout=timeout_s, cwd=ROOT)
+    except subprocess.TimeoutExpired:
+        return None
+    lines = [x for x in r.stdout.splitlines() if x.startswith("{")]
+    if r.returncode != 0 or not lines:
+        return None
+    return json.loads(lines[-1])
+
+
 def main_ours(args, world, rank, local):
     import torch
 
@@ -479,6 +492,24 @@ def main_ours(args, world, rank, local):
                          f"{citers} PCG iterations, {csecs:.1f} s for the slowest)",
                "single_core_value": sval}
 
+    # ---- the FP64 issue rate this step is bound by, measured on this GPU -------------
+    fclk = ClockSampler(local)
+    if rank == 0:
+        fclk.start()
+    fma_rate = B.lfm_measure_fp64_fma_rate(local)
+    fclk = fclk.stop() if rank == 0 else None
+    fp64_peak_tflops = 2.0 * fma_rate / 1e12
+
+    # ---- the batched and served forms beside the headline ---------------------------
+    # each in a fresh process, exactly as `--workload batch512` / `--workload serve` run alone
+    # (a served run's latency is host-bound and suffers from what earlier legs leave in the
+    # process); under torchrun each workload is its own launch instead
+    subs = {}
+    if not args.no_sub and world == 1:
+        subs["batch512"] = run_workload(["--workload", "batch512", "--warmup", str(args.warmup)])
+        subs["serve1000"] = run_workload(["--workload", "serve", "--requests", "1000"])
+        subs["serve100"] = run_workload(["--workload", "serve", "--requests", "100"])
+
     if rank != 0:
         return
     line = {
@@ -502,9 +533,13 @@ def main_ours(args, world, rank, local):
                      "peak_kind": peak_kind, "kernel": "step_kernel_f64",
                      "per": "one step (one launch runs all timed steps)"},
         "roofline_fp64_pipe": {"bound": "alu", "achieved": algorithmic_flops(N, F, iters, K) / secs / 1e12,
-                               "peak": FP64_NOMINAL_TFLOPS, "unit": "TFLOP/s",
-                               "frac": algorithmic_flops(N, F, iters, K) / secs / 1e12 / FP64_NOMINAL_TFLOPS,
-                               "peak_kind": "nominal (1.25 TFLOP/s dense FP64)",
+                               "peak": fp64_peak_tflops, "unit": "TFLOP/s",
+                               "frac": algorithmic_flops(N, F, iters, K) / secs / 1e12 / fp64_peak_tflops,
+                               "peak_kind": "measured: lfm_measure_fp64_fma_rate (independent FMA chains on "
+                                            "every SM, 2 flops per FMA)",
+                               "fma_per_s": fma_rate, "clocks": fclk,
+                               "frac_of_nominal": algorithmic_flops(N, F, iters, K) / secs / 1e12
+                               / FP64_NOMINAL_TFLOPS,
                                "note": "ncu: FP64 pipe 75% busy, DRAM 64% (profiles/step_kernel_f64_graded200.md)"},
         "gpu_launches": 1,
         "clocks": clk,
@@ -513,6 +548,21 @@ def main_ours(args, world, rank, local):
         "e2e": e2e,
         "cpu_baseline": cpu,
     }
+    for k, v in subs.items():  # compact: the headline figures of each, with their clocks
+        if v is None:
+            continue
+        if k == "batch512":
+            line[k] = {"config": v["config"]["workload"], "clocks": v["clocks"],
+                       "batched_fp64": v["batched_fp64"]["value"], "batched_df64": v["batched_df64"]["value"],
+                       "batched_mixed": v["batched_mixed"]["value"],
+                       "plain_fp64_sequential": v["plain_fp64_sequential"]["value"], "unit": UNIT,
+                       "max_rel_diff_batched_vs_alone":
+                           v["plain_fp64_sequential"]["max_rel_diff_batched_vs_alone"],
+                       "mixed_max_rel_diff_vs_fp64_batch": v["batched_mixed"]["max_rel_diff_vs_fp64_batch"]}
+        else:
+            line[k] = {"config": v["config"]["workload"], "clocks": v["clocks"], "served": v["served"],
+                       "serial_plain_fp64": v["serial_plain_fp64"],
+                       "p99_latency_ratio_serial_over_served": v["p99_latency_ratio_serial_over_served"]}
     print(json.dumps(line), flush=True)
 
 
@@ -645,11 +695,13 @@ def main_only(args, world, rank, local, case, mesh, stream):
     smx.advance(W)
     secs, st = time_device_resident(smx, B, torch, stream, K)
     iters = sum(x["iters"] for x in st)
+    phases = {k: v / K for k, v in smx.phase_times().items()}
     smx.close()
     if rank == 0:
         print(json.dumps({"metric": METRIC, "value": mesh.n_cells * iters / secs, "unit": UNIT,
                           "mode": f"{args.only} only (profiling)", "steps": K, "warmup": W,
-                          "ms_per_step": 1e3 * secs / K, "iters_per_step": iters / K}), flush=True)
+                          "ms_per_step": 1e3 * secs / K, "iters_per_step": iters / K,
+                          "phases_ms_per_step": phases}), flush=True)
 
 
 def _cases_with_meshes(cases):
@@ -665,20 +717,26 @@ def _cases_with_meshes(cases):
     return out
 
 
-def main_batch(args, world, rank, local):
+def batch_record(args, world, rank, local):
     """batch512: 512 independent cases (edge log-uniform 16..96), 10 steps each, in one
     persistent launch per step (graph replay), FP64, df64 and mixed, against the plain FP64
-    single-case path run case after case."""
+    single-case path run case after case. With N ranks the 512 cases are split over the
+    GPUs by the longest-processing-time plan of shard.py (no collective on the data path;
+    strong scaling: the batch is the same at every N); times are the maximum over ranks and
+    the work the sum."""
     import torch
 
     from paper_2507_18268_gb300 import binding as B
+    from paper_2507_18268_gb300 import shard
     from paper_2507_18268_gb300.batch import Batch
 
     torch.cuda.set_device(local)
     n_cases = args.batch_cases
     steps = args.steps if args.steps_given else 10
-    base_cases = lapcase.batch_cases(n_cases=n_cases, seed=3 + 1000 * rank, n_steps=steps)
-    total_cells = sum(c.n_cells for c in base_cases)
+    all_cases = lapcase.batch_cases(n_cases=n_cases, seed=3, n_steps=steps)
+    mine = shard.shard_of([shard.case_cost(c) for c in all_cases], world, rank)
+    base_cases = [all_cases[i] for i in mine]
+    total_cells = sum(c.n_cells for c in all_cases)
     stream = torch.cuda.Stream(device=local)
     results = {}
     fields = {}
@@ -710,13 +768,15 @@ def main_batch(args, world, rank, local):
         if prec == B.LFM_FP64 and rank == 0:
             clk = clocks.stop()
         assert rc == B.LFM_OK, B.lfm_batch_last_error(bt.handle)
-        secs = ev0.elapsed_time(ev1) * 1e-3
+        secs = reduce_max(ev0.elapsed_time(ev1) * 1e-3, world)
         cell_iters = 0
         conv = True
         for cid in ids:
             st = bt.stats(cid, steps)
             cell_iters += bt.cases[cid].mesh.n_cells * sum(x["iters"] for x in st)
             conv = conv and all(x["converged"] for x in st)
+        cell_iters = reduce_sum(cell_iters, world)
+        conv = reduce_sum(0.0 if conv else 1.0, world) == 0.0
         fields[name] = {cid: bt.field(cid) for cid in ids}
         results[name] = {"value": cell_iters / secs, "ms_total": 1e3 * secs, "converged": conv,
                          "cell_steps_per_s": total_cells * steps / secs,
@@ -734,45 +794,63 @@ def main_batch(args, world, rank, local):
                 st = s.advance(steps)
                 plain_iters += s.mesh.n_cells * sum(x["iters"] for x in st)
             torch.cuda.synchronize()
-            psecs = time.perf_counter() - t0
-            diff = max(float(np.max(np.abs(s.field() - fields["fp64"][cid]) / np.abs(fields["fp64"][cid])))
-                       for cid, s in zip(ids, solvers))
+            psecs = reduce_max(time.perf_counter() - t0, world)
+            plain_iters = reduce_sum(plain_iters, world)
+            diff = reduce_max(max(float(np.max(np.abs(s.field() - fields["fp64"][cid]) / np.abs(fields["fp64"][cid])))
+                                  for cid, s in zip(ids, solvers)), world)
             results["plain_fp64_sequential"] = {"value": plain_iters / psecs, "ms_total": 1e3 * psecs,
                                                 "max_rel_diff_batched_vs_alone": diff}
             for s in solvers:
                 s.close()
         else:
             ref = fields["fp64"]
-            results[name]["max_rel_diff_vs_fp64_batch"] = max(
-                float(np.max(np.abs(fields[name][cid] - ref[cid]) / np.abs(ref[cid]))) for cid in ids)
+            results[name]["max_rel_diff_vs_fp64_batch"] = reduce_max(max(
+                float(np.max(np.abs(fields[name][cid] - ref[cid]) / np.abs(ref[cid]))) for cid in ids), world)
         bt.close()
     if rank != 0:
-        return
+        return None
     line = {"metric": METRIC, "value": results["fp64"]["value"], "unit": UNIT, "n_gpus": world, "steps": steps,
             "warmup": args.warmup, "ms_per_step": results["fp64"]["ms_total"] / steps, "higher_is_better": True,
-            "scaling": "weak", "vs_baseline": None, "dtype": "f64", "data": "synthetic",
+            "scaling": "strong" if world > 1 else "weak", "vs_baseline": None, "dtype": "f64", "data": "synthetic",
             "config": {"workload": f"batch{n_cases}: {n_cases} cases, edge log-uniform 16..96 (seed 3), "
                                    f"{total_cells} cells in total, {steps} steps each, graph-replayed step",
-                       "parallelism": "single GPU"},
+                       "parallelism": "single GPU" if world == 1 else
+                       f"{world} GPUs, cases split by the longest-processing-time plan (no collective)"},
             "clocks": clk,
             "batched_fp64": results["fp64"], "batched_df64": results["df64"], "batched_mixed": results["mixed"],
             "plain_fp64_sequential": results["plain_fp64_sequential"],
             "speedup_batched_fp64_vs_plain": results["fp64"]["value"] / results["plain_fp64_sequential"]["value"],
             "speedup_batched_df64_vs_plain": results["df64"]["value"] / results["plain_fp64_sequential"]["value"],
             "speedup_batched_mixed_vs_plain": results["mixed"]["value"] / results["plain_fp64_sequential"]["value"]}
-    print(json.dumps(line), flush=True)
+    return line
 
 
-def main_serve(args, world, rank, local):
+def main_batch(args, world, rank, local):
+    line = batch_record(args, world, rank, local)
+    if line is not None:
+        print(json.dumps(line), flush=True)
+
+
+def serve_record(args, world, rank, local, n_requests: int):
     """serve: Poisson arrivals (200/s, seed 4) of requests with edge log-uniform 32..160,
     1..50 steps, FP64 or mixed with probability 1/2, under a 120 GB HBM budget; continuous
-    batching against the same requests solved alone one after another in FP64."""
+    batching (up to 8 steps per tick, each request capped at its own count) against the same
+    requests solved alone one after another in FP64. With N ranks the stream is dispatched
+    over the GPUs by shard.dispatch_stream (no collective on the data path); latencies are
+    gathered over ranks."""
     import torch
 
+    from paper_2507_18268_gb300 import shard
     from paper_2507_18268_gb300.serve import Server, serve_serial_fp64
 
     torch.cuda.set_device(local)
-    reqs = lapcase.serving_stream(n_requests=args.requests, seed=4 + 1000 * rank)
+    reqs_all = lapcase.serving_stream(n_requests=n_requests, seed=4)
+    if world > 1:
+        # each GPU serves ~2e10 cost units per second (cells x (iterations + 2) x steps)
+        dev = shard.dispatch_stream(reqs_all, world, rate=2e10)
+        reqs = [r for r, d in zip(reqs_all, dev) if d == rank]
+    else:
+        reqs = reqs_all
     warm = lapcase.serving_stream(n_requests=8, seed=99, n_min=16, n_max=24, max_steps=2)
     srv = Server(device=local, budget_bytes=120e9)
     srv.run(warm)
@@ -783,23 +861,44 @@ def main_serve(args, world, rank, local):
     clk = clocks.stop() if rank == 0 else None
     srv.close()
     serial = serve_serial_fp64(reqs, device=local)
+    lat = [d.latency_s for d in rep["done"]]
+    lat_serial = serial["latencies_s"]
+    if world > 1:
+        import torch.distributed as dist
+        got, got_s = [None] * world, [None] * world
+        dist.all_gather_object(got, lat)
+        dist.all_gather_object(got_s, lat_serial)
+        lat = [x for g in got for x in g]
+        lat_serial = [x for g in got_s for x in g]
+    makespan = reduce_max(rep["makespan_s"], world)
+    smakespan = reduce_max(serial["makespan_s"], world)
+    cell_iters = reduce_sum(rep["cell_iterations_per_s"] * rep["makespan_s"], world)
     if rank != 0:
-        return
-    keys = ("requests", "makespan_s", "throughput_req_s", "cell_iterations_per_s", "cell_steps_per_s",
-            "p50_latency_s", "p99_latency_s", "mean_latency_s")
-    served = {k: rep[k] for k in keys}
-    served.update(ticks=rep["ticks"], gpu_busy_s=rep["gpu_busy_s"], peak_hbm_bytes=rep["peak_hbm_bytes"],
-                  failed=rep["failed"])
-    line = {"metric": METRIC, "value": rep["cell_iterations_per_s"], "unit": UNIT, "n_gpus": world,
-            "steps": args.requests, "warmup": 1, "ms_per_step": 1e3 * rep["makespan_s"] / max(args.requests, 1),
-            "higher_is_better": True, "scaling": "weak", "vs_baseline": None, "dtype": "f64+mixed",
-            "data": "synthetic",
-            "config": {"workload": f"serve: {args.requests} requests, Poisson 200/s (seed 4), edge log-uniform "
-                                   "32..160, 1..50 steps, FP64/mixed 50/50, 120 GB HBM budget, one step per tick"},
-            "clocks": clk, "served": served, "serial_plain_fp64": {k: serial[k] for k in keys},
-            "p99_latency_ratio_serial_over_served": serial["p99_latency_s"] / rep["p99_latency_s"],
-            "throughput_ratio_served_over_serial": rep["throughput_req_s"] / serial["throughput_req_s"]}
-    print(json.dumps(line), flush=True)
+        return None
+    pct = lambda xs, q: float(np.percentile(np.asarray(xs), q))  # noqa: E731
+    served = {"requests": len(lat), "makespan_s": makespan, "throughput_req_s": len(lat) / makespan,
+              "cell_iterations_per_s": cell_iters / makespan, "p50_latency_s": pct(lat, 50),
+              "p99_latency_s": pct(lat, 99), "mean_latency_s": float(np.mean(lat)), "ticks": rep["ticks"],
+              "steps_per_tick": 8, "peak_hbm_bytes": rep["peak_hbm_bytes"], "failed": rep["failed"]}
+    ser = {"requests": len(lat_serial), "makespan_s": smakespan, "throughput_req_s": len(lat_serial) / smakespan,
+           "p50_latency_s": pct(lat_serial, 50), "p99_latency_s": pct(lat_serial, 99),
+           "mean_latency_s": float(np.mean(lat_serial))}
+    return {"metric": METRIC, "value": served["cell_iterations_per_s"], "unit": UNIT, "n_gpus": world,
+            "steps": n_requests, "warmup": 1, "ms_per_step": 1e3 * makespan / max(n_requests, 1),
+            "higher_is_better": True, "scaling": "strong" if world > 1 else "weak", "vs_baseline": None,
+            "dtype": "f64+mixed", "data": "synthetic",
+            "config": {"workload": f"serve: {n_requests} requests, Poisson 200/s (seed 4), edge log-uniform "
+                                   "32..160, 1..50 steps, FP64/mixed 50/50, 120 GB HBM budget, up to 8 steps "
+                                   "per tick"},
+            "clocks": clk, "served": served, "serial_plain_fp64": ser,
+            "p99_latency_ratio_serial_over_served": ser["p99_latency_s"] / served["p99_latency_s"],
+            "throughput_ratio_served_over_serial": served["throughput_req_s"] / ser["throughput_req_s"]}
+
+
+def main_serve(args, world, rank, local):
+    line = serve_record(args, world, rank, local, args.requests)
+    if line is not None:
+        print(json.dumps(line), flush=True)
 
 
 def main():
@@ -814,6 +913,8 @@ def main():
     ap.add_argument("--no-df64", action="store_true")
     ap.add_argument("--no-e2e", action="store_true")
     ap.add_argument("--no-cpu-baseline", action="store_true")
+    ap.add_argument("--no-sub", action="store_true",
+                    help="graded200: leave out the batch512 / serve1000 / serve100 records")
     ap.add_argument("--workload", choices=["graded200", "batch512", "serve", "skewed200"], default="graded200")
     ap.add_argument("--batch-cases", type=int, default=512)
     ap.add_argument("--profile-range", action="store_true",
@@ -827,7 +928,7 @@ def main():
     if args.warmup < 3:
         ap.error("--warmup must be >= 3")
     if args.only:  # profiling: one timed launch per form
-        args.no_e2e = args.no_cpu_baseline = True
+        args.no_e2e = args.no_cpu_baseline = args.no_sub = True
         args.no_mixed = args.no_df64 = args.only == "fp64"
         args.repeats = 1
     world, rank, local = dist_setup()

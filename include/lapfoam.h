@@ -397,6 +397,16 @@ int lfm_pcg_solve_static(int32_t n_cells, int32_t n_faces, const int32_t *owner,
                          const double *source, double *x, const lfm_solver_opts *opts,
                          lfm_step_stats *stats, void *cuda_stream);
 
+/* Measures the FP64 fused multiply-add rate of `device` (FMAs per second, into *fma_per_s):
+ * independent FMA chains on every SM, the best of three timed launches after a warm-up.
+ * It bounds the FP64 form, which issues about 14 FP64 instructions per cell and PCG
+ * iteration (the PCG recurrence of section "Evaluation" in IEEE FP64) against 160 bytes, so
+ * that on a part with few FP64 units the issue rate, not HBM, can set the step time. Takes
+ * about 0.1 s; allocates 8 bytes of device memory and frees it. The paper has no
+ * counterpart (it is measurement, not the method). LFM_EINVAL for a bad device or a NULL
+ * pointer; sets lfm_last_error(NULL) on failure. */
+int lfm_measure_fp64_fma_rate(int device, double *fma_per_s);
+
 /* Destroys the context (frees library-owned device memory; never a bound workspace). */
 int lfm_destroy(lfm_ctx *ctx);
 
@@ -447,6 +457,15 @@ int lfm_batch_set_barrier_timeout(lfm_batch *b, uint64_t ns);
  * code around the iteration loops). */
 int lfm_batch_advance_async(lfm_batch *b, int32_t n_steps, int32_t use_graph);
 
+/* As lfm_batch_advance_async, with a cap per case: case id runs min(n_steps, caps[id]) steps
+ * of this advance (ids >= n_caps run all n_steps; caps[id] >= 0, else LFM_EINVAL). A case
+ * whose cap is reached takes no further step; its team's CTAs serve the other cases' jobs
+ * in the same launch. The serving form uses it to run several steps per tick while each
+ * request stops at its own step count (section "Evaluation": the time loop of each case is
+ * the listing's; only how many of its steps share one launch changes). */
+int lfm_batch_advance_capped_async(lfm_batch *b, int32_t n_steps, int32_t use_graph, const int32_t *caps,
+                                   int32_t n_caps);
+
 /* 1 while the pending advance runs, LFM_OK when done or none pending. */
 int lfm_batch_query(lfm_batch *b);
 
@@ -463,6 +482,12 @@ int lfm_batch_case_iters(lfm_batch *b, int32_t case_id);
 
 /* Copies the first n per-step records of one case's last advance to host memory. */
 int lfm_batch_case_stats(lfm_batch *b, int32_t case_id, lfm_step_stats *out, int32_t n);
+
+/* Results of the last finished advance for case ids 0 .. n-1, into host arrays of n entries
+ * (each may be NULL): status (LFM_ESTATE for an id with no member), steps run and PCG
+ * iterations summed over those steps. One call in place of a status and iteration query per
+ * case. LFM_ESTATE while an advance is pending. */
+int lfm_batch_results(lfm_batch *b, int32_t *status, int32_t *steps, int32_t *iters, int32_t n);
 
 /* Destroys the batch (the member contexts are released, not destroyed). */
 int lfm_batch_destroy(lfm_batch *b);

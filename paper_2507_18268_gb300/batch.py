@@ -75,6 +75,21 @@ class Batch:
     def advance_async(self, n_steps: int, use_graph: bool = True):
         B.lfm_batch_advance_async(self.handle, n_steps, use_graph)
 
+    def advance_capped_async(self, n_steps: int, caps: Dict[int, int], use_graph: bool = False):
+        """n_steps for every case, but case id i at most caps[i] of them (the serving form's
+        multi-step ticks); fused launch by default (one launch runs all n_steps)."""
+        n = max(caps) + 1 if caps else 0
+        arr = [n_steps] * n
+        for cid, c in caps.items():
+            arr[cid] = c
+        B.lfm_batch_advance_capped_async(self.handle, n_steps, arr, use_graph)
+
+    def results(self):
+        """{case id: (status, steps run, PCG iterations summed)} after the last advance."""
+        n = max(self.cases) + 1 if self.cases else 0
+        st, sp, it = B.lfm_batch_results(self.handle, n)
+        return {cid: (st[cid], sp[cid], it[cid]) for cid in self.cases}
+
     def done(self) -> bool:
         return B.lfm_batch_query(self.handle) == B.LFM_OK
 

@@ -113,6 +113,7 @@ _SIGS = {
     "lfm_pcg_solve_static": ([c_int32, c_int32, c_void_p, c_void_p, c_void_p, c_void_p, c_void_p, c_void_p,
                               POINTER(lfm_solver_opts), POINTER(lfm_step_stats), c_void_p], c_int),
     "lfm_destroy": ([_ctx_p], c_int),
+    "lfm_measure_fp64_fma_rate": ([c_int, POINTER(c_double)], c_int),
     "lfm_batch_create": ([POINTER(c_void_p), c_int, c_void_p], c_int),
     "lfm_batch_add": ([c_void_p, _ctx_p, POINTER(c_int32)], c_int),
     "lfm_batch_remove": ([c_void_p, c_int32], c_int),
@@ -121,6 +122,8 @@ _SIGS = {
     "lfm_batch_get_launch": ([c_void_p, POINTER(c_int32), POINTER(c_int32), POINTER(c_int32)], c_int),
     "lfm_batch_set_barrier_timeout": ([c_void_p, c_uint64], c_int),
     "lfm_batch_advance_async": ([c_void_p, c_int32, c_int32], c_int),
+    "lfm_batch_advance_capped_async": ([c_void_p, c_int32, c_int32, POINTER(c_int32), c_int32], c_int),
+    "lfm_batch_results": ([c_void_p, POINTER(c_int32), POINTER(c_int32), POINTER(c_int32), c_int32], c_int),
     "lfm_batch_query": ([c_void_p], c_int),
     "lfm_batch_finish": ([c_void_p], c_int),
     "lfm_batch_case_status": ([c_void_p, c_int32], c_int),
@@ -502,6 +505,15 @@ def lfm_destroy(ctx):
     load().lfm_destroy(ctx)
 
 
+def lfm_measure_fp64_fma_rate(device: int = 0) -> float:
+    """FP64 fused multiply-adds per second measured on the device."""
+    v = c_double(0.0)
+    rc = load().lfm_measure_fp64_fma_rate(int(device), ctypes.byref(v))
+    if rc != LFM_OK:
+        raise LfmError(rc, _err(None))
+    return v.value
+
+
 def lfm_last_error(ctx=None) -> str:
     return _err(ctx)
 
@@ -556,6 +568,20 @@ def lfm_batch_set_barrier_timeout(b, ns: int):
 
 def lfm_batch_advance_async(b, n_steps: int, use_graph: bool = True):
     _bcheck(load().lfm_batch_advance_async(b, int(n_steps), 1 if use_graph else 0), b)
+
+
+def lfm_batch_advance_capped_async(b, n_steps: int, caps, use_graph: bool = True):
+    """caps: per case id, at most this many of the n_steps (a sequence of ints)."""
+    n = len(caps)
+    arr = (c_int32 * max(n, 1))(*[int(x) for x in caps])
+    _bcheck(load().lfm_batch_advance_capped_async(b, int(n_steps), 1 if use_graph else 0, arr, n), b)
+
+
+def lfm_batch_results(b, n: int):
+    """(status, steps, iterations) lists for case ids 0 .. n-1 after the last advance."""
+    st, sp, it = (c_int32 * max(n, 1))(), (c_int32 * max(n, 1))(), (c_int32 * max(n, 1))()
+    _bcheck(load().lfm_batch_results(b, st, sp, it, int(n)), b)
+    return list(st[:n]), list(sp[:n]), list(it[:n])
 
 
 def lfm_batch_query(b) -> int:

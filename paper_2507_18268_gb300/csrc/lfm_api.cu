@@ -1464,6 +1464,8 @@ struct lfm_batch {
   std::vector<double> est_iters;    // per case id: PCG iterations of its last step
   std::vector<int32_t> status;      // per case id: status of the last advance
   std::vector<int32_t> last_iters;  // per case id: PCG iterations of its last step (-1: none)
+  std::vector<int32_t> steps_run;   // per case id: steps run by the last advance
+  std::vector<int32_t> iters_run;   // per case id: PCG iterations summed over those steps
   std::vector<int32_t> order;       // compact index of the last advance -> case id
   int threads = 512;
   int cpt[3] = {4, 8, 16};          // cells per thread by size class
@@ -1477,6 +1479,9 @@ struct lfm_batch {
   int32_t* d_case_step = nullptr;
   int32_t* d_status = nullptr;
   int32_t* d_iters = nullptr;
+  int32_t* d_cap = nullptr;
+  int32_t* d_steps = nullptr;
+  int32_t* d_iters_sum = nullptr;
   // pinned staging
   CaseDev* h_cases = nullptr;
   int32_t* h_job_case = nullptr;
@@ -1484,6 +1489,9 @@ struct lfm_batch {
   BatchHeader* h_hdr = nullptr;
   int32_t* h_status = nullptr;
   int32_t* h_iters = nullptr;
+  int32_t* h_cap = nullptr;
+  int32_t* h_steps = nullptr;
+  int32_t* h_iters_sum = nullptr;
   cudaEvent_t done = nullptr;
   int pending = 0;
   int n_active = 0;
@@ -1530,14 +1538,22 @@ void free_buffers(lfm_batch* b) {
   cudaFree(b->d_case_step);
   cudaFree(b->d_status);
   cudaFree(b->d_iters);
+  cudaFree(b->d_cap);
+  cudaFree(b->d_steps);
+  cudaFree(b->d_iters_sum);
   cudaFreeHost(b->h_cases);
   cudaFreeHost(b->h_job_case);
   cudaFreeHost(b->h_job_start);
   cudaFreeHost(b->h_hdr);
   cudaFreeHost(b->h_status);
   cudaFreeHost(b->h_iters);
+  cudaFreeHost(b->h_cap);
+  cudaFreeHost(b->h_steps);
+  cudaFreeHost(b->h_iters_sum);
   b->d_cases = nullptr;
   b->d_job_case = b->d_job_start = b->d_case_step = b->d_status = b->d_iters = nullptr;
+  b->d_cap = b->d_steps = b->d_iters_sum = nullptr;
+  b->h_cap = b->h_steps = b->h_iters_sum = nullptr;
   b->d_hdr = nullptr;
   b->h_cases = nullptr;
   b->h_job_case = b->h_job_start = b->h_status = b->h_iters = nullptr;
@@ -1559,12 +1575,18 @@ int ensure_capacity(lfm_batch* b, int n) {
   BCK(b, cudaMalloc(&b->d_case_step, sizeof(int32_t) * cap));
   BCK(b, cudaMalloc(&b->d_status, sizeof(int32_t) * cap));
   BCK(b, cudaMalloc(&b->d_iters, sizeof(int32_t) * cap));
+  BCK(b, cudaMalloc(&b->d_cap, sizeof(int32_t) * cap));
+  BCK(b, cudaMalloc(&b->d_steps, sizeof(int32_t) * cap));
+  BCK(b, cudaMalloc(&b->d_iters_sum, sizeof(int32_t) * cap));
   BCK(b, cudaMallocHost(&b->h_cases, sizeof(CaseDev) * cap));
   BCK(b, cudaMallocHost(&b->h_job_case, sizeof(int32_t) * cap));
   BCK(b, cudaMallocHost(&b->h_job_start, sizeof(int32_t) * (cap + 1)));
   BCK(b, cudaMallocHost(&b->h_hdr, sizeof(BatchHeader)));
   BCK(b, cudaMallocHost(&b->h_status, sizeof(int32_t) * cap));
   BCK(b, cudaMallocHost(&b->h_iters, sizeof(int32_t) * cap));
+  BCK(b, cudaMallocHost(&b->h_cap, sizeof(int32_t) * cap));
+  BCK(b, cudaMallocHost(&b->h_steps, sizeof(int32_t) * cap));
+  BCK(b, cudaMallocHost(&b->h_iters_sum, sizeof(int32_t) * cap));
   b->cap = cap;
   return LFM_OK;
 }
@@ -1612,11 +1634,15 @@ int lfm_batch_add(lfm_batch* b, lfm_ctx* c, int32_t* case_id) {
     b->est_iters.push_back(5.0);
     b->status.push_back(0);
     b->last_iters.push_back(-1);
+    b->steps_run.push_back(0);
+    b->iters_run.push_back(0);
   }
   b->slots[id] = c;
   b->est_iters[id] = 5.0;
   b->status[id] = 0;
   b->last_iters[id] = -1;
+  b->steps_run[id] = 0;
+  b->iters_run[id] = 0;
   c->batch = b;
   if (case_id) *case_id = id;
   return LFM_OK;
@@ -1669,9 +1695,17 @@ int lfm_batch_set_barrier_timeout(lfm_batch* b, uint64_t ns) {
 }
 
 int lfm_batch_advance_async(lfm_batch* b, int32_t n_steps, int32_t use_graph) {
+  return lfm_batch_advance_capped_async(b, n_steps, use_graph, nullptr, 0);
+}
+
+int lfm_batch_advance_capped_async(lfm_batch* b, int32_t n_steps, int32_t use_graph, const int32_t* caps,
+                                   int32_t n_caps) {
   if (!b) return bfail(nullptr, LFM_EINVAL, "batch is NULL");
   if (b->pending) return bfail(b, LFM_ESTATE, "an advance is pending");
   if (n_steps < 0 || n_steps > kStatsCap) return bfail(b, LFM_EINVAL, "n_steps must be in [0, %d]", kStatsCap);
+  if (n_caps < 0 || (n_caps > 0 && !caps)) return bfail(b, LFM_EINVAL, "caps is NULL or n_caps < 0");
+  for (int32_t i = 0; i < n_caps; ++i)
+    if (caps[i] < 0) return bfail(b, LFM_EINVAL, "caps[%d] = %d is negative", i, caps[i]);
   DeviceGuard g(b->device);
   b->order.clear();
   for (size_t i = 0; i < b->slots.size(); ++i)
@@ -1710,7 +1744,10 @@ int lfm_batch_advance_async(lfm_batch* b, int32_t n_steps, int32_t use_graph) {
     if (kk < 1) kk = 1;
     if (kk > ctas) kk = ctas;
     k[i] = (int)kk;
-    t[i] = (double)N * (b->est_iters[b->order[i]] + 2.0) / (double)kk;
+    const int32_t id = b->order[i];
+    const int32_t run = (id < n_caps && caps[id] < n_steps) ? caps[id] : n_steps;
+    b->h_cap[i] = run;
+    t[i] = (double)N * (b->est_iters[id] + 2.0) * (double)run / (double)kk;
     idx[i] = i;
   }
   std::stable_sort(idx.begin(), idx.end(), [&](int a, int c) { return t[a] > t[c]; });
@@ -1729,6 +1766,7 @@ int lfm_batch_advance_async(lfm_batch* b, int32_t n_steps, int32_t use_graph) {
   BCK(b, cudaMemcpyAsync(b->d_job_case, b->h_job_case, sizeof(int32_t) * n, cudaMemcpyHostToDevice, b->stream));
   BCK(b, cudaMemcpyAsync(b->d_job_start, b->h_job_start, sizeof(int32_t) * (n + 1), cudaMemcpyHostToDevice, b->stream));
   BCK(b, cudaMemcpyAsync(b->d_hdr, b->h_hdr, sizeof(BatchHeader), cudaMemcpyHostToDevice, b->stream));
+  BCK(b, cudaMemcpyAsync(b->d_cap, b->h_cap, sizeof(int32_t) * n, cudaMemcpyHostToDevice, b->stream));
   BCK(b, launch_batch_prepare(b->d_cases, n, b->d_case_step, b->stream));
 
   BatchLaunch bl{};
@@ -1737,6 +1775,7 @@ int lfm_batch_advance_async(lfm_batch* b, int32_t n_steps, int32_t use_graph) {
   bl.job_start = b->d_job_start;
   bl.hdr = b->d_hdr;
   bl.case_step = b->d_case_step;
+  bl.case_cap = b->d_cap;
   bl.launch.ctas = ctas;
   bl.launch.threads = b->threads;
   bl.launch.timeout_ns = b->timeout_ns;
@@ -1771,9 +1810,12 @@ int lfm_batch_advance_async(lfm_batch* b, int32_t n_steps, int32_t use_graph) {
   } else {
     BCK(b, launch_batch_steps(bl, n_steps, b->stream));
   }
-  BCK(b, launch_batch_collect(b->d_cases, n, b->d_case_step, b->d_status, b->d_iters, b->stream));
+  BCK(b, launch_batch_collect(b->d_cases, n, b->d_case_step, b->d_status, b->d_iters, b->d_steps, b->d_iters_sum,
+                              b->stream));
   BCK(b, cudaMemcpyAsync(b->h_status, b->d_status, sizeof(int32_t) * n, cudaMemcpyDeviceToHost, b->stream));
   BCK(b, cudaMemcpyAsync(b->h_iters, b->d_iters, sizeof(int32_t) * n, cudaMemcpyDeviceToHost, b->stream));
+  BCK(b, cudaMemcpyAsync(b->h_steps, b->d_steps, sizeof(int32_t) * n, cudaMemcpyDeviceToHost, b->stream));
+  BCK(b, cudaMemcpyAsync(b->h_iters_sum, b->d_iters_sum, sizeof(int32_t) * n, cudaMemcpyDeviceToHost, b->stream));
   BCK(b, cudaEventRecord(b->done, b->stream));
   b->pending = n_steps;
   return LFM_OK;
@@ -1800,6 +1842,8 @@ int lfm_batch_finish(lfm_batch* b) {
     const int32_t id = b->order[i];
     b->status[id] = b->h_status[i];
     b->last_iters[id] = b->h_iters[i];
+    b->steps_run[id] = b->h_steps[i];
+    b->iters_run[id] = b->h_iters_sum[i];
     if (b->h_iters[i] >= 0) b->est_iters[id] = b->h_iters[i];
     if (b->h_status[i] != 0 && first == LFM_OK) first = b->h_status[i];
   }
@@ -1821,6 +1865,19 @@ int lfm_batch_case_status(lfm_batch* b, int32_t id) {
 int lfm_batch_case_iters(lfm_batch* b, int32_t id) {
   if (!b || id < 0 || id >= (int32_t)b->slots.size()) return -1;
   return b->last_iters[id];
+}
+
+int lfm_batch_results(lfm_batch* b, int32_t* status, int32_t* steps, int32_t* iters, int32_t n) {
+  if (!b) return bfail(nullptr, LFM_EINVAL, "batch is NULL");
+  if (b->pending) return bfail(b, LFM_ESTATE, "an advance is pending");
+  if (n < 0) return bfail(b, LFM_EINVAL, "n = %d is negative", n);
+  for (int32_t id = 0; id < n; ++id) {
+    const bool live = id < (int32_t)b->slots.size() && b->slots[id] != nullptr;
+    if (status) status[id] = live ? b->status[id] : LFM_ESTATE;
+    if (steps) steps[id] = live ? b->steps_run[id] : 0;
+    if (iters) iters[id] = live ? b->iters_run[id] : 0;
+  }
+  return LFM_OK;
 }
 
 int lfm_batch_case_stats(lfm_batch* b, int32_t id, lfm_step_stats* out, int32_t n) {

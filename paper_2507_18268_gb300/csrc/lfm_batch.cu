@@ -24,7 +24,8 @@ template <int B, int W, int kForm>
 __global__ void __launch_bounds__(B, 1024 / B) batch_kernel(const CaseDev* __restrict__ cases,
                                                   const int32_t* __restrict__ job_case,
                                                   const int32_t* __restrict__ job_start, BatchHeader* hdr,
-                                                  int32_t* __restrict__ case_step, Launch L, int n_steps) {
+                                                  int32_t* __restrict__ case_step,
+                                                  const int32_t* __restrict__ case_cap, Launch L, int n_steps) {
   __shared__ TeamShared sh;
   __shared__ CaseDev s_cs;
   __shared__ int s_job[4];
@@ -58,20 +59,24 @@ __global__ void __launch_bounds__(B, 1024 / B) batch_kernel(const CaseDev* __res
     __syncthreads();
     const Team tm{s_job[2], s_job[1], s_cs.sync, s_cs.partials, L.timeout_ns};
     const int base = case_step[c];
-    if constexpr (kForm == kBatchFp64) {
-      run_steps_f64<B, W>(s_cs, s_cs, tm, n_steps, kModeSteps, sh, base);
-    } else if constexpr (kForm == kBatchDf64) {
-      run_steps_df64<B, W, true>(s_cs, s_cs, tm, n_steps, sh, base);
-    } else {
-      if (s_cs.precision == LFM_MIXED)
-        run_steps_mixed_any<B, W>(s_cs, s_cs, tm, n_steps, kModeSteps, sh, base);
-      else if (s_cs.precision == LFM_DF64)
-        run_steps_df64<B, W, true>(s_cs, s_cs, tm, n_steps, sh, base);
-      else
-        run_steps_f64<B, W>(s_cs, s_cs, tm, n_steps, kModeSteps, sh, base);
+    // a case whose cap is reached runs no step; its team's CTAs go back for tickets at once
+    const int run = min(n_steps, case_cap[c] - base);
+    if (run > 0) {
+      if constexpr (kForm == kBatchFp64) {
+        run_steps_f64<B, W>(s_cs, s_cs, tm, run, kModeSteps, sh, base);
+      } else if constexpr (kForm == kBatchDf64) {
+        run_steps_df64<B, W, true>(s_cs, s_cs, tm, run, sh, base);
+      } else {
+        if (s_cs.precision == LFM_MIXED)
+          run_steps_mixed_any<B, W>(s_cs, s_cs, tm, run, kModeSteps, sh, base);
+        else if (s_cs.precision == LFM_DF64)
+          run_steps_df64<B, W, true>(s_cs, s_cs, tm, run, sh, base);
+        else
+          run_steps_f64<B, W>(s_cs, s_cs, tm, run, kModeSteps, sh, base);
+      }
     }
     __syncthreads();
-    if (tm.rank == 0 && threadIdx.x == 0) case_step[c] = base + n_steps;
+    if (run > 0 && tm.rank == 0 && threadIdx.x == 0) case_step[c] = base + run;
     __syncthreads();
   }
 }
@@ -81,7 +86,7 @@ __global__ void batch_prepare_kernel(const CaseDev* __restrict__ cases, int n_ca
   const int i = blockIdx.x * blockDim.x + threadIdx.x;
   if (i < n_cases) {
     SyncWords* sw = cases[i].sync;
-    sw->count = 0;
+    sw->count = 0ull;
     sw->status = 0;
     case_step[i] = 0;
     // forms that update the FP64 field directly leave the triple-float one stale
@@ -90,15 +95,20 @@ __global__ void batch_prepare_kernel(const CaseDev* __restrict__ cases, int n_ca
   }
 }
 
-// After an advance: each case's status and the iterations of its last step, gathered for
-// one copy to the host.
+// After an advance: each case's status, the iterations of its last step, the steps it ran
+// and the iterations summed over them, gathered for one copy to the host.
 __global__ void batch_collect_kernel(const CaseDev* __restrict__ cases, int n_cases,
-                                     const int32_t* __restrict__ case_step, int32_t* status, int32_t* iters) {
+                                     const int32_t* __restrict__ case_step, int32_t* status, int32_t* iters,
+                                     int32_t* steps, int32_t* iters_sum) {
   const int i = blockIdx.x * blockDim.x + threadIdx.x;
   if (i < n_cases) {
     status[i] = cases[i].sync->status;
     const int k = case_step[i];
     iters[i] = k > 0 ? cases[i].stats[k - 1].iters : -1;
+    int sum = 0;
+    for (int j = 0; j < k; ++j) sum += cases[i].stats[j].iters;
+    steps[i] = k;
+    iters_sum[i] = sum;
   }
 }
 
@@ -137,9 +147,10 @@ cudaError_t launch_batch_prepare(const CaseDev* cases, int n_cases, int32_t* cas
 }
 
 cudaError_t launch_batch_collect(const CaseDev* cases, int n_cases, const int32_t* case_step, int32_t* status,
-                                 int32_t* iters, cudaStream_t s) {
+                                 int32_t* iters, int32_t* steps, int32_t* iters_sum, cudaStream_t s) {
   if (n_cases <= 0) return cudaSuccess;
-  batch_collect_kernel<<<(n_cases + 255) / 256, 256, 0, s>>>(cases, n_cases, case_step, status, iters);
+  batch_collect_kernel<<<(n_cases + 255) / 256, 256, 0, s>>>(cases, n_cases, case_step, status, iters, steps,
+                                                              iters_sum);
   return cudaGetLastError();
 }
 
@@ -165,9 +176,10 @@ cudaError_t launch_batch_steps(const BatchLaunch& bl, int n_steps, cudaStream_t 
   const int32_t* a2 = bl.job_start;
   BatchHeader* a3 = bl.hdr;
   int32_t* a4 = bl.case_step;
-  Launch a5 = bl.launch;
-  int a6 = n_steps;
-  void* args[] = {&a0, &a1, &a2, &a3, &a4, &a5, &a6};
+  const int32_t* a5 = bl.case_cap;
+  Launch a6 = bl.launch;
+  int a7 = n_steps;
+  void* args[] = {&a0, &a1, &a2, &a3, &a4, &a5, &a6, &a7};
   return cudaLaunchKernelExC(&cfg, fn, args);
 }
 

@@ -21,8 +21,8 @@ constexpr int kStaticMaxFaces = 1 << 18;
 
 // Barrier words of one team of CTAs; each field sits on its own 128-byte line.
 struct alignas(128) SyncWords {
-  unsigned int count;                // arrivals at the current barrier
-  unsigned int pad0[31];
+  unsigned long long count;          // arrivals since the launch began (never reset within it)
+  unsigned int pad0[30];
   unsigned int gen;                  // barrier generation (released by the last arrival)
   unsigned int pad1[31];
   double scalars[kMaxSums];          // reduced values published by the last arrival
@@ -173,6 +173,7 @@ struct BatchLaunch {
   const int32_t* job_start;  // [n_jobs + 1] first ticket of job j
   BatchHeader* hdr;
   int32_t* case_step;        // [n_cases] steps done in the current advance
+  const int32_t* case_cap;   // [n_cases] at most this many steps of the current advance
   Launch launch;
   int W;
   int form;  // kBatchAny, or the one precision every member runs (kernel compiled for it)
@@ -230,8 +231,10 @@ void box_layout_host(long long nx, long long ny, long long nz, int W, const doub
 // Batched launchers (lfm_batch.cu).
 int max_coresident_batch_ctas(int threads, int W, int form, int device);
 cudaError_t launch_batch_prepare(const CaseDev* cases, int n_cases, int32_t* case_step, cudaStream_t s);
+// After an advance, per case: status, iterations of its last step (-1: none), steps run and
+// iterations summed over them.
 cudaError_t launch_batch_collect(const CaseDev* cases, int n_cases, const int32_t* case_step, int32_t* status,
-                                 int32_t* iters, cudaStream_t s);
+                                 int32_t* iters, int32_t* steps, int32_t* iters_sum, cudaStream_t s);
 cudaError_t launch_batch_steps(const BatchLaunch& bl, int n_steps, cudaStream_t s);
 cudaError_t launch_fill(double* a, size_t n, double v, cudaStream_t stream);
 cudaError_t launch_vdt(const double* V, double dt, double* vdt, int n, cudaStream_t stream);

@@ -3,8 +3,10 @@
 Requests (a box case and a number of implicit steps, FP64 or mixed precision) arrive over
 time. The server keeps every admitted case resident on the device (matrix, PCG state and
 field live in its workspace) and advances all of them together: each scheduling tick is
-one batched launch that moves every admitted case forward one time step, so requests that
-arrive while others run join at the next tick and their work overlaps on the device.
+one batched launch that moves every admitted case forward up to ``steps_per_tick`` time
+steps (each request stops at its own step count; the CTAs of a finished request serve the
+others' jobs in the same launch), so requests that arrive while others run join at the next
+tick and their work overlaps on the device.
 Admission is first-come first-served against an HBM budget (the workspaces of admitted
 cases plus the shared meshes); a finished case's field is read back, its workspace is
 released, and the next waiting request takes the space.
@@ -12,6 +14,13 @@ released, and the next waiting request takes the space.
 Cases with the same box share one mesh built on the device (``lfm_upload_box`` once per
 size, then ``lfm_upload_mesh_shared`` per request), so admitting a request costs a
 workspace allocation and a few small uploads, not a host mesh build.
+
+The host work of a tick overlaps the device work of the previous one: once tick k is
+enqueued, the server reads back and releases the cases that finished at tick k - 1, admits
+waiting requests into contexts of their own (on a stream of their own, so that their
+uploads do not wait for the batch), and only then waits for tick k. At the tick boundary it
+removes finished cases from the batch, adds the admitted ones and enqueues tick k + 1
+before any further host work.
 """
 from __future__ import annotations
 
@@ -53,13 +62,17 @@ def percentile(xs, q):
 
 class Server:
     def __init__(self, device: int = 0, budget_bytes: float = 120e9, use_graph: bool = True,
-                 launch: Optional[tuple] = None, batch: Optional[Batch] = None):
+                 launch: Optional[tuple] = None, batch: Optional[Batch] = None, steps_per_tick: int = 8):
         self.device = device
         self.budget = float(budget_bytes)
         self.use_graph = use_graph
+        self.steps_per_tick = max(1, int(steps_per_tick))
+        # admissions and read-backs run on a stream of their own, beside the batch's
+        self.side = None
         if batch is None:
             import torch
 
+            self.side = torch.cuda.Stream(device=device)
             self.stream = torch.cuda.Stream(device=device)
             batch = Batch(device=device, stream=self.stream)
         self.batch = batch
@@ -71,6 +84,9 @@ class Server:
         self.peak_used = 0.0
 
     # ---- resources -----------------------------------------------------------------------
+    def _on_side(self) -> dict:
+        return {} if self.side is None else {"stream": self.side}
+
     def _key(self, case: lapcase.RawCase):
         return (case.nx, case.ny, case.nz, case.xs.tobytes(), case.ys.tobytes(), case.zs.tobytes())
 
@@ -79,7 +95,7 @@ class Server:
         if key in self.meshes:
             self.meshes.move_to_end(key)
             return self.meshes[key]
-        owner = Solver(box=(case.xs, case.ys, case.zs), device=self.device, layout=B.LFM_FP64)
+        owner = Solver(box=(case.xs, case.ys, case.zs), device=self.device, layout=B.LFM_FP64, **self._on_side())
         self.meshes[key] = owner
         self.used += owner.workspace_bytes
         return owner
@@ -107,60 +123,77 @@ class Server:
     # ---- the loop ------------------------------------------------------------------------
     def run(self, requests: List[lapcase.Request], keep_fields: bool = False, time_scale: float = 1.0) -> dict:
         """Serves the requests (arrival times scaled by time_scale) and returns a report."""
-        pending = collections.deque()
-        active: Dict[int, dict] = {}
+        pending = collections.deque()   # arrived, not yet admitted
+        ready = []                      # admitted contexts, joining the batch at the next tick
+        active: Dict[int, dict] = {}    # members of the batch
+        leaving = []                    # finished at the last tick: read back, then released
         done: List[Done] = []
         nxt = 0
         ticks = 0
         busy = 0.0
+        in_flight = False
         t0 = time.perf_counter()
         clock = lambda: time.perf_counter() - t0  # noqa: E731
-        while nxt < len(requests) or pending or active:
+        while nxt < len(requests) or pending or ready or active or leaving or in_flight:
             now = clock()
             while nxt < len(requests) and requests[nxt].arrival_s * time_scale <= now:
                 pending.append(nxt)
                 nxt += 1
+            # ---- host work that overlaps the tick in flight ----------------------------------
+            for a, s, st in leaving:
+                r = requests[a["req"]]
+                field = s.field()  # the result is served once it is on the host
+                if not keep_fields:
+                    field = None
+                done.append(Done(a["req"], s.mesh.n_cells, r.case.n_steps, r.case.precision,
+                                 r.arrival_s * time_scale, a["admitted"], clock(), a["cell_iters"], st, field))
+                self.used -= s.workspace_bytes
+                self.mesh_users[self._key(r.case)] -= 1
+                s.close()
+            leaving = []
             # admission: first come, first served, while the budget allows
             while pending:
                 r = requests[pending[0]]
                 need = self._need(r.case)
                 if self.used + need > self.budget:
                     self._evict_idle_meshes(need, keep=self._key(r.case))
-                if self.used + need > self.budget and active:
+                if self.used + need > self.budget and (active or ready or in_flight):
                     break
                 owner = self._mesh_for(r.case)
-                s = Solver.sharing(owner, r.case, device=self.device, layout=r.case.precision)
+                s = Solver.sharing(owner, r.case, device=self.device, layout=r.case.precision, **self._on_side())
                 self.mesh_users[self._key(r.case)] += 1
                 self.used += s.workspace_bytes
                 self.peak_used = max(self.peak_used, self.used)
-                cid = self.batch.add(s)
-                active[cid] = {"req": pending.popleft(), "left": r.case.n_steps, "admitted": clock(),
-                               "cell_iters": 0, "solver": s}
-            if not active:
-                if nxt < len(requests):
-                    time.sleep(max(0.0, requests[nxt].arrival_s * time_scale - clock()))
-                continue
-            tb = time.perf_counter()
-            self.batch.advance_async(1, self.use_graph)
-            self.batch.finish()
-            busy += time.perf_counter() - tb
-            ticks += 1
-            now = clock()
-            for cid in list(active):
-                a = active[cid]
-                a["left"] -= 1
-                st = self.batch.status(cid)
-                a["cell_iters"] += a["solver"].mesh.n_cells * max(self.batch.last_iters(cid), 0)
-                if a["left"] == 0 or st != 0:
-                    r = requests[a["req"]]
-                    s = self.batch.remove(cid, close=False)
-                    field = s.field() if keep_fields else None
-                    done.append(Done(a["req"], s.mesh.n_cells, r.case.n_steps, r.case.precision,
-                                     r.arrival_s * time_scale, a["admitted"], now, a["cell_iters"], st, field))
-                    self.used -= s.workspace_bytes
-                    self.mesh_users[self._key(r.case)] -= 1
-                    s.close()
-                    del active[cid]
+                ready.append({"req": pending.popleft(), "left": r.case.n_steps, "admitted": clock(),
+                              "cell_iters": 0, "solver": s})
+            # ---- tick boundary -------------------------------------------------------------
+            if in_flight:
+                tb = time.perf_counter()
+                self.batch.finish()
+                busy += time.perf_counter() - tb
+                in_flight = False
+                ticks += 1
+                res = self.batch.results()
+                for cid in list(active):
+                    a = active[cid]
+                    st, steps, iters = res[cid]
+                    a["left"] -= steps
+                    a["cell_iters"] += a["solver"].mesh.n_cells * iters
+                    if a["left"] <= 0 or st != 0:
+                        leaving.append((a, self.batch.remove(cid, close=False), st))
+                        del active[cid]
+            for a in ready:
+                active[self.batch.add(a["solver"])] = a
+            ready = []
+            if active:
+                k = min(self.steps_per_tick, max(a["left"] for a in active.values()))
+                if k == 1:
+                    self.batch.advance_async(1, self.use_graph)
+                else:  # one fused launch of k steps, each request capped at what it has left
+                    self.batch.advance_capped_async(k, {cid: min(k, a["left"]) for cid, a in active.items()})
+                in_flight = True
+            elif not leaving and not pending and nxt < len(requests):
+                time.sleep(max(0.0, requests[nxt].arrival_s * time_scale - clock()))
         makespan = clock()
         lat = [d.latency_s for d in done]
         cells_steps = sum(d.n_cells * d.steps for d in done)
@@ -169,7 +202,7 @@ class Server:
                 "cell_steps_per_s": cells_steps / makespan, "cell_iterations_per_s": cell_iters / makespan,
                 "p50_latency_s": percentile(lat, 50),
                 "p99_latency_s": percentile(lat, 99), "mean_latency_s": float(np.mean(lat)) if lat else float("nan"),
-                "ticks": ticks, "gpu_busy_s": busy, "peak_hbm_bytes": self.peak_used,
+                "ticks": ticks, "gpu_wait_s": busy, "peak_hbm_bytes": self.peak_used,
                 "failed": sum(1 for d in done if d.status != 0), "done": done}
 
     def close(self):
@@ -218,4 +251,4 @@ def serve_serial_fp64(requests: List[lapcase.Request], device: int = 0, keep_fie
     return {"requests": len(requests), "makespan_s": makespan, "throughput_req_s": len(requests) / makespan,
             "cell_steps_per_s": cells_steps / makespan, "cell_iterations_per_s": cell_iters / makespan,
             "p50_latency_s": percentile(lat, 50), "p99_latency_s": percentile(lat, 99),
-            "mean_latency_s": float(np.mean(lat)), "fields": done if keep_fields else None}
+            "mean_latency_s": float(np.mean(lat)), "latencies_s": lat, "fields": done if keep_fields else None}

@@ -62,6 +62,44 @@ def test_batch_matches_alone_and_oracle(use_graph, threads, cpt):
                 assert all(x["converged"] for x in st)
 
 
+@pytest.mark.parametrize("use_graph", [False, True])
+def test_capped_advance_runs_each_case_its_own_step_count(use_graph):
+    # a capped advance of k steps: case i runs min(k, cap_i) steps and then idles, bitwise as
+    # if its advance had that many steps; the bulk results report steps and iterations
+    n_steps = 5
+    cases = small_batch_cases(seed=13, n_cases=9, n_steps=n_steps)
+    caps_list = [0, 1, 2, 5, 3, 9, 1, 4, 2]
+    # reference: each case in a batch of its own, uncapped, for min(cap, k) steps
+    T_ref = {}
+    for cid, (c, cap) in enumerate(zip(cases, caps_list)):
+        run = min(cap, n_steps)
+        with Batch() as one:
+            i = one.add_case(c)
+            one.set_launch(256, (2, 2, 2))
+            if run:
+                assert one.advance(run, use_graph=use_graph) == B.LFM_OK
+            T_ref[cid] = (one.field(i), one.stats(i, run) if run else [])
+    with Batch() as bt:
+        ids = [bt.add_case(c) for c in cases]
+        bt.set_launch(256, (2, 2, 2))
+        caps = dict(zip(ids, caps_list))
+        B.lfm_batch_advance_capped_async(bt.handle, n_steps, [caps[i] for i in range(len(ids))], use_graph)
+        assert bt.finish() == B.LFM_OK
+        res = bt.results()
+        for k, cid in enumerate(ids):
+            run = min(caps_list[k], n_steps)
+            T1, st1 = T_ref[k]
+            st, steps, iters = res[cid]
+            assert st == B.LFM_OK and steps == run
+            assert iters == sum(x["iters"] for x in st1)
+            assert np.array_equal(bt.field(cid), T1), k
+    # argument checks
+    with Batch() as bt:
+        bt.add_case(cases[0])
+        with pytest.raises(B.LfmError):
+            B.lfm_batch_advance_capped_async(bt.handle, 2, [-1], False)
+
+
 def test_batch_graph_and_fused_are_bitwise_equal():
     cases = small_batch_cases(seed=11, n_cases=10, n_steps=3)
     fields = []

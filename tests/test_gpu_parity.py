@@ -205,6 +205,38 @@ def test_min_and_max_iter():
     assert relerr(T, To) <= RTOL64
 
 
+def _two_cell_unequal():
+    # the hand-worked case of tests/golden/two_cell_unequal.json (unequal volumes)
+    return lapcase.RawCase(xs=np.array([0.0, 0.5, 2.0]), ys=np.array([0.0, 1.0]), zs=np.array([0.0, 1.0]),
+                           DT_uniform=0.75, dt=0.5,
+                           patches=((lapcase.FIXED_VALUE, 10.0),) + ((lapcase.ZERO_GRADIENT, 0.0),) * 5,
+                           T0=np.array([1.0, 2.0]), n_steps=1, tol=1e-13)
+
+
+@pytest.mark.parametrize("precision", [B.LFM_FP64, B.LFM_DF64])
+def test_convergence_test_is_strict_at_a_tie(precision):
+    # res == tol must not stop the solve: a run repeats its own residuals bit for bit, so a
+    # tolerance set to the residual after one iteration (or to the initial residual) is an
+    # exact tie, which a strict '<' resolves by iterating on
+    case = _two_cell_unequal()
+
+    def run(tol, max_iter=1000):
+        with Solver.from_case(case) as s:
+            s.set_solver(tol, 0.0, max_iter, 0, precision)
+            return s.advance(1)[0]
+
+    one = run(1e-13, max_iter=1)
+    assert one["iters"] == 1 and not one["converged"]
+    assert run(one["final_res"])["iters"] == 2
+    assert run(float(np.nextafter(one["final_res"], 1.0)))["iters"] == 1
+    assert run(one["init_res"])["iters"] >= 1
+    assert run(float(np.nextafter(one["init_res"], 1.0)))["iters"] == 0
+    # and the hand-worked values themselves
+    g = run(1e-13)
+    assert g["iters"] == 2
+    assert abs(g["norm_factor"] - 31.5) <= 1e-13 * 31.5 and abs(g["init_res"] - 19 / 21) <= 1e-13
+
+
 # ---- failure paths (no fault: host-made or bounded waits) -------------------------------
 
 def test_barrier_timeout_returns_status_and_context_stays_usable():

@@ -4,7 +4,8 @@ The server is driven with stand-ins for the device objects (a batch that finishe
 step at once, solvers that only report their workspace sizes, taken from the library's own
 size functions), so what is checked is the scheduling: every request is served, admission
 is first come first served, the bytes held never exceed the budget even when meshes have to
-be evicted, and a mesh is shared by every admitted request of its box size.
+be evicted, a mesh is shared by every admitted request of its box size, and every request
+runs exactly its own step count when a tick runs several steps.
 """
 import numpy as np
 import pytest
@@ -39,6 +40,8 @@ class FakeSolver:
         s.owner = owner
         s.is_mesh = False
         s.closed = False
+        s.n_steps = case.n_steps
+        s.steps_done = 0
         assert not owner.closed, "a case was admitted on an evicted mesh"
         FakeSolver.live.append(s)
         return s
@@ -70,6 +73,17 @@ class FakeBatch:
     def finish(self):
         pass
 
+    def advance_capped_async(self, n, caps, use_graph=False):
+        self.caps = dict(caps)
+
+    def results(self):
+        caps = getattr(self, "caps", {})
+        out = {cid: (0, caps.get(cid, 1), 3 * caps.get(cid, 1)) for cid in self.members}
+        for cid, s in self.members.items():
+            s.steps_done += out[cid][1]
+        self.caps = {}
+        return out
+
     def status(self, cid):
         return 0
 
@@ -77,21 +91,23 @@ class FakeBatch:
         return 3
 
     def remove(self, cid, close=True):
-        return self.members.pop(cid)
+        s = self.members.pop(cid)
+        assert s.steps_done == s.n_steps, "a request left with another step count than it asked for"
+        return s
 
     def close(self):
         pass
 
 
-@pytest.mark.parametrize("seed", [1, 2, 3])
-def test_budget_is_never_exceeded_and_every_request_is_served(monkeypatch, seed):
+@pytest.mark.parametrize("seed,steps_per_tick", [(1, 1), (2, 4), (3, 3)])
+def test_budget_is_never_exceeded_and_every_request_is_served(monkeypatch, seed, steps_per_tick):
     monkeypatch.setattr(serve, "Solver", FakeSolver)
     FakeSolver.live = []
     reqs = lapcase.serving_stream(n_requests=60, seed=seed, rate_per_s=1e6, n_min=6, n_max=16, max_steps=6)
     biggest = max(B.lfm_workspace_bytes_box(r.case.nx, r.case.ny, r.case.nz, B.LFM_BOTH) for r in reqs)
     budget = 3 * biggest
     batch = FakeBatch()
-    server = serve.Server(budget_bytes=budget, batch=batch)
+    server = serve.Server(budget_bytes=budget, batch=batch, steps_per_tick=steps_per_tick)
     rep = server.run(reqs)
     server.close()
     assert rep["requests"] == len(reqs) and rep["failed"] == 0
