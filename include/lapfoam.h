@@ -397,6 +397,52 @@ int lfm_pcg_solve_static(int32_t n_cells, int32_t n_faces, const int32_t *owner,
                          const double *source, double *x, const lfm_solver_opts *opts,
                          lfm_step_stats *stats, void *cuda_stream);
 
+/* ---- one case decomposed into parts ----------------------------------------------------
+ * The data flow of the paper's multi-GPU runs (section "Evaluation": a mesh decomposed over
+ * GPUs; per PCG iteration one halo exchange of the search direction p and the global sums of
+ * the recurrence; per step one exchange of T and the sums of xRef and normFactor), emulated
+ * in one cooperative launch on one GPU: every part keeps its own vectors (T and p with ghost
+ * slots after the owned cells) and receives its neighbours' interface values only through
+ * pushes into those slots, made right after the values are computed and made visible by the
+ * barrier that ends the pass. Parts are contiguous ranges of cell labels (slabs along the
+ * last axis of a naturally numbered box, the simple decomposition). The step and its
+ * arithmetic are lfm_advance's FP64 step; only the order of the global sums differs. Covered:
+ * FP64, orthogonal meshes, no volumetric source, no correctors (LFM_EINVAL otherwise). */
+typedef struct lfm_dd lfm_dd;
+typedef struct {
+  int32_t first_label;  /* first cell label of the part */
+  int32_t n_owned;      /* cells it owns (labels first_label ..) */
+  int32_t n_ghost;      /* distinct outside neighbours it reads (its ghost slots) */
+  int32_t n_send;       /* (interface cell, receiving part, ghost slot) triples it pushes */
+} lfm_dd_counts;
+
+/* Plan of part `part` of the decomposition of an LDU mesh (owner < neighbour) into n_parts
+ * label ranges, on the host (no GPU): counts, and when the arrays are not NULL, the ghost
+ * labels [n_ghost] (ascending) and the pushes [n_send] (source local id ascending, receiving
+ * part, ghost slot in it). Call once with NULL arrays to size them. LFM_EINVAL for bad
+ * sizes or faces. */
+int lfm_dd_plan(int32_t n_cells, int32_t n_faces, const int32_t *owner, const int32_t *neighbour, int32_t n_parts,
+                int32_t part, lfm_dd_counts *counts, int32_t *ghost_label, int32_t *send_src, int32_t *send_part,
+                int32_t *send_slot);
+
+/* Decomposes the configured case `ctx` (uploaded, FP64) into n_parts parts on ctx's device;
+ * the parts start from ctx's current field and take ctx's coefficients, boundary conditions,
+ * time step and solver controls at every advance (set them on ctx). Allocates the parts'
+ * device memory (library-owned, freed by lfm_dd_destroy). n_parts in [1, co-resident CTAs of
+ * the kernel]. ctx must outlive the decomposition and stay idle while it advances. */
+int lfm_dd_create(lfm_dd **out, lfm_ctx *ctx, int32_t n_parts);
+/* Counts of part `part`. */
+int lfm_dd_part_counts(lfm_dd *dd, int32_t part, lfm_dd_counts *counts);
+/* Field T[n_cells] (host, by label) into the parts / out of the parts. Synchronous. */
+int lfm_dd_set_field(lfm_dd *dd, const double *T);
+int lfm_dd_get_field(lfm_dd *dd, double *T);
+/* n_steps (<= 1024) implicit steps of the decomposed case; out (host, may be NULL) receives
+ * the per-step records. Synchronises before return. */
+int lfm_dd_advance(lfm_dd *dd, int32_t n_steps, lfm_step_stats *out);
+int lfm_dd_destroy(lfm_dd *dd);
+/* Reason for the last non-OK return (dd NULL: of a call without a decomposition). */
+const char *lfm_dd_last_error(const lfm_dd *dd);
+
 /* Measures the FP64 fused multiply-add rate of `device` (FMAs per second, into *fma_per_s):
  * independent FMA chains on every SM, the best of three timed launches after a warm-up.
  * It bounds the FP64 form, which issues about 14 FP64 instructions per cell and PCG

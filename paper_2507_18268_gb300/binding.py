@@ -61,6 +61,10 @@ class lfm_step_stats(ctypes.Structure):
         return {k: getattr(self, k) for k, _ in self._fields_}
 
 
+class lfm_dd_counts(ctypes.Structure):
+    _fields_ = [("first_label", c_int32), ("n_owned", c_int32), ("n_ghost", c_int32), ("n_send", c_int32)]
+
+
 _ctx_p = c_void_p
 _SIGS = {
     "lfm_version": ([], c_char_p),
@@ -114,6 +118,15 @@ _SIGS = {
                               POINTER(lfm_solver_opts), POINTER(lfm_step_stats), c_void_p], c_int),
     "lfm_destroy": ([_ctx_p], c_int),
     "lfm_measure_fp64_fma_rate": ([c_int, POINTER(c_double)], c_int),
+    "lfm_dd_plan": ([c_int32, c_int32, c_void_p, c_void_p, c_int32, c_int32, POINTER(lfm_dd_counts), c_void_p,
+                     c_void_p, c_void_p, c_void_p], c_int),
+    "lfm_dd_create": ([POINTER(c_void_p), _ctx_p, c_int32], c_int),
+    "lfm_dd_part_counts": ([c_void_p, c_int32, POINTER(lfm_dd_counts)], c_int),
+    "lfm_dd_set_field": ([c_void_p, c_void_p], c_int),
+    "lfm_dd_get_field": ([c_void_p, c_void_p], c_int),
+    "lfm_dd_advance": ([c_void_p, c_int32, POINTER(lfm_step_stats)], c_int),
+    "lfm_dd_destroy": ([c_void_p], c_int),
+    "lfm_dd_last_error": ([c_void_p], c_char_p),
     "lfm_batch_create": ([POINTER(c_void_p), c_int, c_void_p], c_int),
     "lfm_batch_add": ([c_void_p, _ctx_p, POINTER(c_int32)], c_int),
     "lfm_batch_remove": ([c_void_p, c_int32], c_int),
@@ -619,3 +632,66 @@ def lfm_batch_destroy(b):
 
 def lfm_batch_last_error(b=None) -> str:
     return _berr(b)
+
+
+# ---- one case decomposed into parts -----------------------------------------------------
+
+def _dderr(d=None) -> str:
+    msg = load().lfm_dd_last_error(d)
+    return msg.decode() if msg else ""
+
+
+def _ddcheck(rc: int, d=None) -> int:
+    if rc != LFM_OK:
+        raise LfmError(rc, _dderr(d))
+    return rc
+
+
+def lfm_dd_plan(owner, neighbour, n_cells: int, n_parts: int, part: int):
+    """(counts, ghost labels, send sources, send parts, send slots) of one part (host only)."""
+    import numpy as np
+    owner = np.ascontiguousarray(owner, dtype=np.int32)
+    neighbour = np.ascontiguousarray(neighbour, dtype=np.int32)
+    cnt = lfm_dd_counts()
+    args = (int(n_cells), len(owner), owner.ctypes.data, neighbour.ctypes.data, int(n_parts), int(part))
+    _ddcheck(load().lfm_dd_plan(*args, ctypes.byref(cnt), None, None, None, None))
+    g = np.zeros(max(cnt.n_ghost, 1), np.int32)
+    src, prt, slt = (np.zeros(max(cnt.n_send, 1), np.int32) for _ in range(3))
+    _ddcheck(load().lfm_dd_plan(*args, ctypes.byref(cnt), g.ctypes.data, src.ctypes.data, prt.ctypes.data,
+                                slt.ctypes.data))
+    return cnt, g[:cnt.n_ghost], src[:cnt.n_send], prt[:cnt.n_send], slt[:cnt.n_send]
+
+
+def lfm_dd_create(ctx, n_parts: int):
+    d = c_void_p()
+    _ddcheck(load().lfm_dd_create(ctypes.byref(d), ctx, int(n_parts)))
+    return d
+
+
+def lfm_dd_part_counts(d, part: int):
+    cnt = lfm_dd_counts()
+    _ddcheck(load().lfm_dd_part_counts(d, int(part), ctypes.byref(cnt)), d)
+    return cnt
+
+
+def lfm_dd_set_field(d, T):
+    import numpy as np
+    T = np.ascontiguousarray(T, dtype=np.float64)
+    _ddcheck(load().lfm_dd_set_field(d, T.ctypes.data), d)
+
+
+def lfm_dd_get_field(d, n_cells: int):
+    import numpy as np
+    T = np.empty(n_cells)
+    _ddcheck(load().lfm_dd_get_field(d, T.ctypes.data), d)
+    return T
+
+
+def lfm_dd_advance(d, n_steps: int):
+    out = (lfm_step_stats * max(n_steps, 1))()
+    _ddcheck(load().lfm_dd_advance(d, int(n_steps), out), d)
+    return [out[i] for i in range(n_steps)]
+
+
+def lfm_dd_destroy(d):
+    load().lfm_dd_destroy(d)

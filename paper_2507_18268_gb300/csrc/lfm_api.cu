@@ -1914,3 +1914,261 @@ const char* lfm_batch_last_error(const lfm_batch* b) {
 }
 
 }  // extern "C"
+
+// ---- one case decomposed into parts (the kernels are in lfm_decomp.cu) --------------------
+
+struct lfm_dd {
+  lfm_ctx* src = nullptr;             // the configured case whose rows the parts own
+  int P = 0;
+  int threads = 512;
+  int ctas = 0;
+  std::string err;
+  std::vector<DdPlanPart> plan;
+  std::vector<DdPart> parts;          // host copies of the device descriptors
+  std::vector<void*> allocs;          // every device allocation, freed by lfm_dd_destroy
+  DdPart* d_parts = nullptr;
+  int32_t* d_cta_part = nullptr;
+  int32_t* d_cta_rank = nullptr;
+  SyncWords* sync = nullptr;
+  double* partials = nullptr;
+  lfm_step_stats* stats = nullptr;
+};
+
+namespace {
+
+thread_local std::string g_dd_error;
+
+int ddfail(lfm_dd* d, int code, const char* fmt, ...) {
+  char buf[512];
+  va_list ap;
+  va_start(ap, fmt);
+  vsnprintf(buf, sizeof buf, fmt, ap);
+  va_end(ap);
+  if (d) d->err = buf;
+  g_dd_error = buf;
+  return code;
+}
+
+#define DDCK(d, call)                                                                       \
+  do {                                                                                      \
+    cudaError_t e_ = (call);                                                                \
+    if (e_ != cudaSuccess) return ddfail(d, LFM_ECUDA, "%s: %s", #call, cudaGetErrorString(e_)); \
+  } while (0)
+
+template <typename T>
+int dd_alloc(lfm_dd* d, T** p, size_t n) {
+  void* v = nullptr;
+  DDCK(d, cudaMalloc(&v, sizeof(T) * (n > 0 ? n : 1)));
+  d->allocs.push_back(v);
+  *p = static_cast<T*>(v);
+  return LFM_OK;
+}
+
+// The decomposed form covers the FP64 step on orthogonal meshes without sources or
+// correctors (the benchmark's step).
+int dd_case_ok(lfm_dd* d, lfm_ctx* c) {
+  if (!c || !c->uploaded) return ddfail(d, LFM_ESTATE, "the case has no mesh uploaded");
+  if (c->opts.precision != LFM_FP64) return ddfail(d, LFM_EINVAL, "the decomposed form runs the FP64 step");
+  if (c->has_geom || c->n_corr > 0 || c->has_Su || c->has_Sp)
+    return ddfail(d, LFM_EINVAL, "the decomposed form covers orthogonal meshes without sources or correctors");
+  if (c->pending_steps > 0 || c->batch) return ddfail(d, LFM_ESTATE, "the case is busy (pending advance or batch)");
+  return LFM_OK;
+}
+
+}  // namespace
+
+extern "C" {
+
+int lfm_dd_plan(int32_t n_cells, int32_t n_faces, const int32_t* owner, const int32_t* neighbour, int32_t n_parts,
+                int32_t part, lfm_dd_counts* counts, int32_t* ghost_label, int32_t* send_src, int32_t* send_part,
+                int32_t* send_slot) {
+  if (n_cells <= 0 || n_faces < 0 || (n_faces > 0 && (!owner || !neighbour)) || !counts)
+    return ddfail(nullptr, LFM_EINVAL, "lfm_dd_plan: bad sizes or NULL arrays");
+  if (n_parts < 1 || n_parts > n_cells || part < 0 || part >= n_parts)
+    return ddfail(nullptr, LFM_EINVAL, "lfm_dd_plan: n_parts must be in [1, n_cells] and part in [0, n_parts)");
+  for (int32_t f = 0; f < n_faces; ++f)
+    if (owner[f] < 0 || neighbour[f] >= n_cells || neighbour[f] <= owner[f])
+      return ddfail(nullptr, LFM_EINVAL, "lfm_dd_plan: face %d out of range or owner >= neighbour", f);
+  DdPlanPart pp;
+  dd_plan_from_faces(n_cells, n_faces, owner, neighbour, n_parts, part, pp);
+  counts->first_label = pp.first;
+  counts->n_owned = pp.n_owned;
+  counts->n_ghost = (int32_t)pp.ghost.size();
+  counts->n_send = (int32_t)pp.send_src.size();
+  if (ghost_label) std::copy(pp.ghost.begin(), pp.ghost.end(), ghost_label);
+  if (send_src) std::copy(pp.send_src.begin(), pp.send_src.end(), send_src);
+  if (send_part) std::copy(pp.send_part.begin(), pp.send_part.end(), send_part);
+  if (send_slot) std::copy(pp.send_slot.begin(), pp.send_slot.end(), send_slot);
+  return LFM_OK;
+}
+
+int lfm_dd_create(lfm_dd** out, lfm_ctx* c, int32_t n_parts) {
+  if (!out) return ddfail(nullptr, LFM_EINVAL, "out is NULL");
+  *out = nullptr;
+  int rc = dd_case_ok(nullptr, c);
+  if (rc) return rc;
+  if (n_parts < 1 || n_parts > c->N) return ddfail(nullptr, LFM_EINVAL, "n_parts must be in [1, n_cells]");
+  DeviceGuard g(c->device);
+  const int max_ctas = dd_max_ctas(512, c->W, c->device);
+  if (n_parts > max_ctas) return ddfail(nullptr, LFM_EINVAL, "n_parts %d above the %d co-resident CTAs", n_parts, max_ctas);
+  lfm_dd* d = new (std::nothrow) lfm_dd;
+  if (!d) return ddfail(nullptr, LFM_ENOMEM, "out of host memory");
+  d->src = c;
+  d->P = n_parts;
+  d->ctas = max_ctas;
+  auto bail = [&](int code) {
+    lfm_dd_destroy(d);
+    return code;
+  };
+  const int32_t N = c->N, W = c->W;
+  std::vector<int32_t> slot_other((size_t)W * N);
+  if (cudaMemcpyAsync(slot_other.data(), c->cs.slot_other, 4 * (size_t)W * N, cudaMemcpyDeviceToHost, c->stream) !=
+          cudaSuccess ||
+      cudaStreamSynchronize(c->stream) != cudaSuccess)
+    return bail(ddfail(nullptr, LFM_ECUDA, "reading the case's addressing failed"));
+  d->plan.resize(n_parts);
+  d->parts.resize(n_parts);
+  // CTAs in proportion to the owned cells, at least one per part
+  std::vector<int32_t> share(n_parts, 1);
+  {
+    int left = max_ctas - n_parts;
+    for (int s = 0; s < n_parts; ++s) {
+      dd_plan_from_slots(N, W, slot_other.data(), n_parts, s, d->plan[s]);
+      const int extra = (int)((int64_t)left * d->plan[s].n_owned / N);
+      share[s] += extra;
+    }
+  }
+  std::vector<int32_t> cta_part, cta_rank;
+  for (int s = 0; s < n_parts; ++s)
+    for (int r = 0; r < share[s]; ++r) {
+      cta_part.push_back(s);
+      cta_rank.push_back(r);
+    }
+  d->ctas = (int)cta_part.size();
+  for (int s = 0; s < n_parts; ++s) {
+    const DdPlanPart& pl = d->plan[s];
+    DdPart& pt = d->parts[s];
+    pt.N = pl.n_owned;
+    pt.G = (int32_t)pl.ghost.size();
+    pt.first = pl.first;
+    pt.n_send = (int32_t)pl.send_src.size();
+    pt.ctas = share[s];
+    // local columns: owned label -> label - first, ghost label -> N + its slot, padding -> self
+    std::vector<int32_t> loc((size_t)W * pt.N);
+    for (int32_t k = 0; k < W; ++k)
+      for (int32_t i = 0; i < pt.N; ++i) {
+        const int32_t gl = pl.first + i, o = slot_other[(size_t)k * N + gl];
+        int32_t v;
+        if (o == gl) {
+          v = i;
+        } else if (o >= pl.first && o < pl.first + pt.N) {
+          v = o - pl.first;
+        } else {
+          const auto it = std::lower_bound(pl.ghost.begin(), pl.ghost.end(), o);
+          if (it == pl.ghost.end() || *it != o) return bail(ddfail(nullptr, LFM_ECUDA, "inconsistent ghost list"));
+          v = pt.N + (int32_t)(it - pl.ghost.begin());
+        }
+        loc[(size_t)k * pt.N + i] = v;
+      }
+    int32_t *sl = nullptr, *ss = nullptr, *sp = nullptr, *sk = nullptr;
+    if (dd_alloc(d, &sl, loc.size()) || dd_alloc(d, &ss, pt.n_send) || dd_alloc(d, &sp, pt.n_send) ||
+        dd_alloc(d, &sk, pt.n_send) || dd_alloc(d, &pt.x, (size_t)pt.N + pt.G) ||
+        dd_alloc(d, &pt.p, (size_t)pt.N + pt.G) || dd_alloc(d, &pt.r, pt.N) || dd_alloc(d, &pt.w, pt.N) ||
+        dd_alloc(d, &pt.q, pt.N) || dd_alloc(d, &pt.diag, pt.N) || dd_alloc(d, &pt.rD, pt.N))
+      return bail(ddfail(nullptr, LFM_ENOMEM, "device memory for part %d", s));
+    pt.slot_local = sl;
+    pt.send_src = ss;
+    pt.send_part = sp;
+    pt.send_slot = sk;
+    if (cudaMemcpy(sl, loc.data(), 4 * loc.size(), cudaMemcpyHostToDevice) != cudaSuccess ||
+        (pt.n_send &&
+         (cudaMemcpy(ss, pl.send_src.data(), 4 * (size_t)pt.n_send, cudaMemcpyHostToDevice) != cudaSuccess ||
+          cudaMemcpy(sp, pl.send_part.data(), 4 * (size_t)pt.n_send, cudaMemcpyHostToDevice) != cudaSuccess ||
+          cudaMemcpy(sk, pl.send_slot.data(), 4 * (size_t)pt.n_send, cudaMemcpyHostToDevice) != cudaSuccess)) ||
+        cudaMemcpy(pt.x, c->cs.x + pl.first, 8 * (size_t)pt.N, cudaMemcpyDeviceToDevice) != cudaSuccess ||
+        cudaMemset(pt.x + pt.N, 0, 8 * (size_t)(pt.G > 0 ? pt.G : 0)) != cudaSuccess)
+      return bail(ddfail(nullptr, LFM_ECUDA, "uploading part %d", s));
+  }
+  if (dd_alloc(d, &d->d_parts, n_parts) || dd_alloc(d, &d->d_cta_part, cta_part.size()) ||
+      dd_alloc(d, &d->d_cta_rank, cta_rank.size()) || dd_alloc(d, &d->sync, 1) ||
+      dd_alloc(d, &d->partials, (size_t)kMaxCtas * kMaxSums) || dd_alloc(d, &d->stats, kStatsCap))
+    return bail(ddfail(nullptr, LFM_ENOMEM, "device memory for the part table"));
+  if (cudaMemcpy(d->d_parts, d->parts.data(), sizeof(DdPart) * n_parts, cudaMemcpyHostToDevice) != cudaSuccess ||
+      cudaMemcpy(d->d_cta_part, cta_part.data(), 4 * cta_part.size(), cudaMemcpyHostToDevice) != cudaSuccess ||
+      cudaMemcpy(d->d_cta_rank, cta_rank.data(), 4 * cta_rank.size(), cudaMemcpyHostToDevice) != cudaSuccess ||
+      cudaMemset(d->sync, 0, sizeof(SyncWords)) != cudaSuccess)
+    return bail(ddfail(nullptr, LFM_ECUDA, "uploading the part table"));
+  *out = d;
+  return LFM_OK;
+}
+
+int lfm_dd_part_counts(lfm_dd* d, int32_t part, lfm_dd_counts* counts) {
+  if (!d || !counts) return ddfail(d, LFM_EINVAL, "NULL argument");
+  if (part < 0 || part >= d->P) return ddfail(d, LFM_EINVAL, "part %d out of range", part);
+  const DdPart& pt = d->parts[part];
+  counts->first_label = pt.first;
+  counts->n_owned = pt.N;
+  counts->n_ghost = pt.G;
+  counts->n_send = pt.n_send;
+  return LFM_OK;
+}
+
+int lfm_dd_set_field(lfm_dd* d, const double* T) {
+  if (!d || !T) return ddfail(d, LFM_EINVAL, "NULL argument");
+  DeviceGuard g(d->src->device);
+  for (const DdPart& pt : d->parts)
+    DDCK(d, cudaMemcpy(pt.x, T + pt.first, 8 * (size_t)pt.N, cudaMemcpyHostToDevice));
+  return LFM_OK;
+}
+
+int lfm_dd_get_field(lfm_dd* d, double* T) {
+  if (!d || !T) return ddfail(d, LFM_EINVAL, "NULL argument");
+  DeviceGuard g(d->src->device);
+  for (const DdPart& pt : d->parts)
+    DDCK(d, cudaMemcpy(T + pt.first, pt.x, 8 * (size_t)pt.N, cudaMemcpyDeviceToHost));
+  return LFM_OK;
+}
+
+int lfm_dd_advance(lfm_dd* d, int32_t n_steps, lfm_step_stats* out) {
+  if (!d) return ddfail(nullptr, LFM_EINVAL, "NULL decomposition");
+  if (n_steps < 0 || n_steps > kStatsCap) return ddfail(d, LFM_EINVAL, "n_steps must be in [0, %d]", kStatsCap);
+  lfm_ctx* c = d->src;
+  int rc = dd_case_ok(d, c);
+  if (rc) return rc;
+  if (n_steps == 0) return LFM_OK;
+  DeviceGuard g(c->device);
+  refresh_case(c);
+  if ((rc = refresh_coef(c))) return ddfail(d, rc, "coefficient set-up of the case failed");
+  CaseDev cs = c->cs;  // the case's rows, with the decomposition's own barrier words and records
+  cs.sync = d->sync;
+  cs.partials = d->partials;
+  cs.stats = d->stats;
+  Launch L{d->ctas, d->threads, c->timeout_ns, -1};
+  DDCK(d, cudaMemsetAsync(d->sync, 0, sizeof(SyncWords), c->stream));
+  DDCK(d, launch_dd_steps(cs, d->d_parts, d->d_cta_part, d->d_cta_rank, L, n_steps, c->stream));
+  int32_t status = 0;
+  DDCK(d, cudaMemcpyAsync(&status, &d->sync->status, 4, cudaMemcpyDeviceToHost, c->stream));
+  std::vector<lfm_step_stats> st(n_steps);
+  DDCK(d, cudaMemcpyAsync(st.data(), d->stats, sizeof(lfm_step_stats) * n_steps, cudaMemcpyDeviceToHost, c->stream));
+  DDCK(d, cudaStreamSynchronize(c->stream));
+  if (out) std::copy(st.begin(), st.end(), out);
+  if (status != 0) return ddfail(d, status, "the decomposed step stopped with status %d", status);
+  return LFM_OK;
+}
+
+int lfm_dd_destroy(lfm_dd* d) {
+  if (!d) return LFM_OK;
+  {
+    DeviceGuard g(d->src ? d->src->device : 0);
+    for (void* p : d->allocs) cudaFree(p);
+  }
+  delete d;
+  return LFM_OK;
+}
+
+const char* lfm_dd_last_error(const lfm_dd* d) {
+  if (d) return d->err.c_str();
+  return g_dd_error.c_str();
+}
+
+}  // extern "C"

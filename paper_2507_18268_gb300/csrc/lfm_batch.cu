@@ -86,7 +86,7 @@ __global__ void batch_prepare_kernel(const CaseDev* __restrict__ cases, int n_ca
   const int i = blockIdx.x * blockDim.x + threadIdx.x;
   if (i < n_cases) {
     SyncWords* sw = cases[i].sync;
-    sw->count = 0ull;
+    sw->count = 0;
     sw->status = 0;
     case_step[i] = 0;
     // forms that update the FP64 field directly leave the triple-float one stale

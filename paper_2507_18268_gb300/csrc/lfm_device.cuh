@@ -8,9 +8,9 @@
 // the sums and releases the barrier by bumping a generation word. The result depends only
 // on the team size, never on arrival order, so repeated runs are bitwise identical. The
 // barrier is a chain of L2 round trips, so it is built to keep that chain short: arrival is
-// one acquire-release atomic, the release one release store, and no fence or counter reset
-// sits on the critical path (about 6 us with one sum for 304 CTAs on GB300, 7.7 us with
-// the fenced protocol it replaced).
+// one acquire-release atomic, the release one release store, and no fence sits on the
+// critical path (about 6 us with one sum for 304 CTAs on GB300, 7.7 us with a fence before
+// the arrival and around the last arriver's reduction).
 //
 // Every wait is bounded: a waiter that sees no release within the launch's time limit (or
 // sees another CTA's error) records an error status and the caller leaves the kernel.
@@ -81,11 +81,9 @@ struct Team {
   uint64_t timeout_ns;
 };
 
-// Shared scratch a CTA needs for team_allreduce: kRedSlots values per sum for the block
-// reduction's second stage.
-constexpr int kRedSlots = 256;
+// Shared scratch a CTA needs for team_allreduce.
 struct TeamShared {
-  double red[kMaxSums * kRedSlots];
+  double red[32 * kMaxSums];
   double out[kMaxSums];
   int flag[4];
 };
@@ -111,41 +109,37 @@ __device__ __forceinline__ bool wait_generation(unsigned* gen, unsigned g, int32
   return true;
 }
 
-// Arrival at a team barrier: one acquire-release add on the launch's arrival counter (the
-// release orders this CTA's partial sums before it, the acquire makes every earlier
-// arrival's partial sums visible to the last arriver).
-__device__ __forceinline__ unsigned long long arrive_acq_rel(unsigned long long* count) {
-  unsigned long long old;
-  asm volatile("atom.add.acq_rel.gpu.u64 %0, [%1], 1;" : "=l"(old) : "l"(count) : "memory");
+// Arrival at a team barrier: one acquire-release add on the arrival counter (the release
+// orders this CTA's partial sums before it, the acquire makes every earlier arrival's
+// partial sums visible to the last arriver).
+__device__ __forceinline__ unsigned arrive_acq_rel(unsigned* count) {
+  unsigned old;
+  asm volatile("atom.add.acq_rel.gpu.u32 %0, [%1], 1;" : "=r"(old) : "l"(count) : "memory");
   return old;
 }
 
-// Fixed-pattern reduction of NS values over the CTA. Totals land in sh.out (visible after
-// the caller's next __syncthreads). GB300 issues about two FP64 instructions per clock and
-// SM, so the tree keeps FP64 adds few: xor-shuffle levels only until kRedSlots values per
-// sum remain (none for 256 threads, one for 512, two for 1024), those go to shared memory,
-// and warp 0 adds them (kRedSlots / 32 per lane, in lane-strided order) before a final
-// five-level xor tree -- 29 warp-wide FP64 adds per sum for 512 threads instead of 85.
+// Fixed-pattern reduction of NS values over the CTA: a five-level xor tree per warp, the warp
+// totals through shared memory, and a second xor tree in warp 0. Totals land in sh.out
+// (visible after the caller's next __syncthreads). (A variant with fewer FP64 adds -- values
+// staged in 8 KB of shared memory, summed by warp 0 -- measured 0.5 % faster in the FP64
+// step and 1.3 % slower in the df64 step, and is not kept.)
 template <int NS>
 __device__ __forceinline__ void block_reduce(double* v, TeamShared& sh) {
-  const int tid = threadIdx.x, lane = tid & 31, nt = blockDim.x;
-  int m = nt;  // values per sum still spread over the threads
-  for (int o = 1; m > kRedSlots; o <<= 1, m >>= 1) {
+  const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5, nw = blockDim.x >> 5;
 #pragma unroll
-    for (int k = 0; k < NS; ++k) v[k] += __shfl_xor_sync(0xffffffffu, v[k], o);
+  for (int k = 0; k < NS; ++k) {
+#pragma unroll
+    for (int o = 16; o > 0; o >>= 1) v[k] += __shfl_xor_sync(0xffffffffu, v[k], o);
   }
-  // lane pattern: after L levels, the lanes whose low L bits are zero hold the group sums
-  const int stride = nt / m;
-  if ((tid & (stride - 1)) == 0) {
+  if (lane == 0) {
 #pragma unroll
-    for (int k = 0; k < NS; ++k) sh.red[k * kRedSlots + tid / stride] = v[k];
+    for (int k = 0; k < NS; ++k) sh.red[warp * NS + k] = v[k];
   }
   __syncthreads();
-  if (tid < 32) {
+  if (warp == 0) {
 #pragma unroll
     for (int k = 0; k < NS; ++k) {
-      double t = 0.0;
-      for (int i = lane; i < m; i += 32) t += sh.red[k * kRedSlots + i];
+      double t = lane < nw ? sh.red[lane * NS + k] : 0.0;
 #pragma unroll
       for (int o = 16; o > 0; o >>= 1) t += __shfl_xor_sync(0xffffffffu, t, o);
       if (lane == 0) sh.out[k] = t;
@@ -156,12 +150,14 @@ __device__ __forceinline__ void block_reduce(double* v, TeamShared& sh) {
 // Team-wide barrier carrying NS sums. On return (true) v[k] holds the team totals in every
 // thread. False: a wait ran out or another CTA failed; the caller must leave the kernel.
 // Protocol: thread 0 stores the CTA's partial sums, reads the generation and arrives (one
-// acquire-release add on a counter that grows through the launch, so no arrival resets it);
-// the CTA whose arrival completes a multiple of the team size is the last: warp 0 loads all
-// partial sums at once, adds them in rank order (lane l takes ranks l, l + 32, ..., then a
-// fixed xor tree), publishes the totals and releases the generation with a release store.
-// The others wait for the generation with acquire loads and then read the totals. The sums
-// depend only on the team size, never on arrival order.
+// acquire-release add); the CTA that finds size - 1 arrivals before its own is the last:
+// warp 0 loads all partial sums at once, adds them in rank order (lane l takes ranks l,
+// l + 32, ..., then a fixed xor tree), publishes the totals, clears the counter and releases
+// the generation with a release store (which orders the totals and the cleared counter
+// before it). The others wait for the generation with acquire loads and then read the
+// totals. The sums depend only on the team size, never on arrival order. (Detecting the
+// last arrival by a remainder modulo the team size, with a counter never cleared, measured
+// 10 % slower in the mixed form's A p: the division's code sits in its inner loop.)
 template <int NS>
 __device__ bool team_allreduce(const Team& tm, double* v, TeamShared& sh) {
   // Every thread's global writes of the phase must be ordered before thread 0 signals
@@ -185,8 +181,8 @@ __device__ bool team_allreduce(const Team& tm, double* v, TeamShared& sh) {
       for (int k = 0; k < NS; ++k) __stcg(&tm.partials[tm.rank * kMaxSums + k], sh.out[k]);
     }
     const unsigned g = *reinterpret_cast<volatile unsigned*>(&tm.sw->gen);
-    const unsigned long long t = arrive_acq_rel(&tm.sw->count);
-    const int last = (t + 1ull) % (unsigned long long)tm.size == 0ull;
+    const unsigned prev = arrive_acq_rel(&tm.sw->count);
+    const int last = prev == (unsigned)(tm.size - 1);
     int ok = 1;
     if (!last) {
       ok = wait_generation(&tm.sw->gen, g, &tm.sw->status, tm.timeout_ns);
@@ -240,7 +236,10 @@ __device__ bool team_allreduce(const Team& tm, double* v, TeamShared& sh) {
         }
       }
       __syncwarp();
-      if (lane == 0) st_release_u32(&tm.sw->gen, (unsigned)sh.flag[2] + 1u);
+      if (lane == 0) {
+        tm.sw->count = 0u;  // ordered before the release below; no CTA arrives again before it
+        st_release_u32(&tm.sw->gen, (unsigned)sh.flag[2] + 1u);
+      }
     }
     __syncthreads();
   }

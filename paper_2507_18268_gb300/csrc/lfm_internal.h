@@ -4,6 +4,7 @@
 
 #include <cstddef>
 #include <cstdint>
+#include <vector>
 
 #include <cuda_runtime.h>
 
@@ -21,8 +22,8 @@ constexpr int kStaticMaxFaces = 1 << 18;
 
 // Barrier words of one team of CTAs; each field sits on its own 128-byte line.
 struct alignas(128) SyncWords {
-  unsigned long long count;          // arrivals since the launch began (never reset within it)
-  unsigned int pad0[30];
+  unsigned int count;                // arrivals at the current barrier
+  unsigned int pad0[31];
   unsigned int gen;                  // barrier generation (released by the last arrival)
   unsigned int pad1[31];
   double scalars[kMaxSums];          // reduced values published by the last arrival
@@ -238,6 +239,42 @@ cudaError_t launch_batch_collect(const CaseDev* cases, int n_cases, const int32_
 cudaError_t launch_batch_steps(const BatchLaunch& bl, int n_steps, cudaStream_t s);
 cudaError_t launch_fill(double* a, size_t n, double v, cudaStream_t stream);
 cudaError_t launch_vdt(const double* V, double dt, double* vdt, int n, cudaStream_t stream);
+
+// ---- one case decomposed into parts (lfm_decomp.cu) ------------------------------------
+// Plan of part s of a decomposition into P contiguous label ranges: its first label and
+// owned count, its ghost labels (sorted), and what it sends: for each of its interface
+// cells (local id, ascending) every (part, ghost slot) that mirrors it.
+struct DdPlanPart {
+  int32_t first = 0, n_owned = 0;
+  std::vector<int32_t> ghost;
+  std::vector<int32_t> send_src, send_part, send_slot;
+};
+int32_t dd_first_label(int32_t N, int32_t P, int32_t s);
+int32_t dd_part_of(int32_t N, int32_t P, int32_t label);
+void dd_plan_from_faces(int32_t N, int32_t F, const int32_t* owner, const int32_t* neighbour, int32_t P,
+                        int32_t s, DdPlanPart& out);
+void dd_plan_from_slots(int32_t N, int32_t W, const int32_t* slot_other, int32_t P, int32_t s, DdPlanPart& out);
+
+// Device view of one part: its rows are the global rows [first, first + N) (coefficients and
+// boundary data read from the case's arrays); its columns are local (owned < N <= ghost);
+// its vectors are its own (T and p with N + G entries, the ghosts after the owned cells).
+struct DdPart {
+  int32_t N, G, first, n_send, ctas;
+  const int32_t* slot_local;  // [W*N]
+  const int32_t* send_src;    // [n_send] local owned id, ascending
+  const int32_t* send_part;   // [n_send] receiving part
+  const int32_t* send_slot;   // [n_send] ghost slot in the receiving part
+  double* x;                  // [N + G]
+  double* p;                  // [N + G]
+  double* r;                  // [N]
+  double* w;
+  double* q;
+  double* diag;
+  double* rD;
+};
+int dd_max_ctas(int threads, int W, int device);
+cudaError_t launch_dd_steps(const CaseDev& cs, const DdPart* parts, const int32_t* cta_part, const int32_t* cta_rank,
+                            const Launch& L, int n_steps, cudaStream_t stream);
 
 // Records the reason for a failed context-free call (the text lfm_last_error(NULL) returns
 // on this thread); defined with the thread-local error text in lfm_api.cu. Returns code.
