@@ -424,6 +424,7 @@ void bind_pointers(lfm_ctx* c) {
   cs.partials = reinterpret_cast<double*>(b + L.partials);
   cs.stats = reinterpret_cast<lfm_step_stats*>(b + L.stats);
   cs.flags = reinterpret_cast<int32_t*>(b + L.flags);
+  cs.seed_sums = reinterpret_cast<double*>(b + L.flags + 64);
   cs.W = c->W;
   cs.btype = reinterpret_cast<const int32_t*>(b + L.btype);
   cs.DT = reinterpret_cast<const double*>(b + L.DT);
@@ -559,9 +560,19 @@ int refresh_ops(lfm_ctx* c) {
 }
 
 // The FP64 field is about to be written other than by a df64 launch: the triple-float copy
-// the df64 forms carry across launches is stale from then on (see lfm_solve_df.cuh).
+// the df64 forms carry across launches is stale from then on (see lfm_solve_df.cuh), and so
+// is the mixed form's seed of its next step (flags[1]).
 int invalidate_split(lfm_ctx* c) {
-  CK(c, cudaMemsetAsync(c->cs.flags, 0, sizeof(int32_t), c->stream));
+  CK(c, cudaMemsetAsync(c->cs.flags, 0, 2 * sizeof(int32_t), c->stream));
+  return LFM_OK;
+}
+
+// The case changed (its matrix, source, controls or launch shape): the next step's rows and
+// inner-solve seed that the mixed form's last launch left in place no longer apply
+// (lfm_solve_mixed_df.cuh). Stream-ordered after any launch still pending.
+int invalidate_seed(lfm_ctx* c) {
+  DeviceGuard g(c->device);
+  CK(c, cudaMemsetAsync(c->cs.flags + 1, 0, sizeof(int32_t), c->stream));
   return LFM_OK;
 }
 
@@ -580,8 +591,11 @@ int enqueue_chunk(lfm_ctx* c, int steps, int mode) {
     if (int rc = refresh_coef(c)) return rc;
     if (int rc = refresh_df(c)) return rc;
     const int p = c->opts.precision;
-    if (p == LFM_FP64 || (p == LFM_MIXED && !mixed_runs_df(c->cs)))
+    if (p == LFM_FP64 || (p == LFM_MIXED && !mixed_runs_df(c->cs))) {
       if (int rc = invalidate_split(c)) return rc;
+    } else if (p == LFM_DF64) {
+      if (int rc = invalidate_seed(c)) return rc;
+    }
   }
   int e = 0;
   Launch L = current_launch(c, e);
@@ -621,6 +635,7 @@ int collect_chunk(lfm_ctx* c, int steps) {
   for (int i = 0; i < steps; ++i) c->stats_acc.push_back(c->h_stats[i]);
   for (int k = 0; k < kPhases; ++k) c->phase_ms[k] += 1e-6 * (double)c->h_phase[k];
   int32_t st = *c->h_status;
+  if (st != 0) invalidate_seed(c);  // a launch that stopped early left no seed to trust
   if (st == LFM_ETIMEOUT) return fail(c, LFM_ETIMEOUT, "a device barrier wait ran out (kernel stopped)");
   if (st == LFM_ESINGULAR) return fail(c, LFM_ESINGULAR, "PCG met a singular search direction");
   if (st == LFM_ENONFINITE) return fail(c, LFM_ENONFINITE, "PCG residual became non-finite");
@@ -1056,6 +1071,7 @@ int lfm_fill_field(lfm_ctx* c, double value) {
 int lfm_set_diffusivity(lfm_ctx* c, double uniform, const double* DT_faces, const double* DT_bfaces) {
   int rc = need_uploaded(c);
   if (rc) return rc;
+  if ((rc = invalidate_seed(c))) return rc;
   if (!(std::isfinite(uniform) && uniform >= 0)) return fail(c, LFM_EINVAL, "uniform DT must be finite and >= 0");
   for (int32_t f = 0; DT_faces && f < c->F; ++f)
     if (!(std::isfinite(DT_faces[f]) && DT_faces[f] >= 0)) return fail(c, LFM_EINVAL, "DT_faces[%d] must be finite and >= 0", f);
@@ -1085,6 +1101,7 @@ int lfm_set_diffusivity(lfm_ctx* c, double uniform, const double* DT_faces, cons
 int lfm_set_diffusivity_cells(lfm_ctx* c, const double* DT_cells, const double* weights) {
   int rc = need_uploaded(c);
   if (rc) return rc;
+  if ((rc = invalidate_seed(c))) return rc;
   if (!DT_cells) return fail(c, LFM_EINVAL, "DT_cells is NULL");
   if (!weights && !c->has_geom) return fail(c, LFM_EINVAL, "weights needed (the mesh has no geometry)");
   for (int32_t i = 0; i < c->N; ++i)
@@ -1116,6 +1133,7 @@ int lfm_set_diffusivity_cells(lfm_ctx* c, const double* DT_cells, const double* 
 int lfm_set_source(lfm_ctx* c, const double* Su, const double* Sp) {
   int rc = need_uploaded(c);
   if (rc) return rc;
+  if ((rc = invalidate_seed(c))) return rc;
   if (c->pending_steps > 0) return fail(c, LFM_ESTATE, "an advance is pending");
   for (int32_t i = 0; Su && i < c->N; ++i)
     if (!std::isfinite(Su[i])) return fail(c, LFM_EINVAL, "Su[%d] not finite", i);
@@ -1147,6 +1165,7 @@ int lfm_set_source(lfm_ctx* c, const double* Su, const double* Sp) {
 int lfm_set_patch(lfm_ctx* c, int32_t patch, int32_t type, const double* values, double uniform) {
   int rc = need_uploaded(c);
   if (rc) return rc;
+  if ((rc = invalidate_seed(c))) return rc;
   if (patch < 0 || patch >= c->n_patches) return fail(c, LFM_EINVAL, "patch %d out of range", patch);
   if (type != LFM_FIXED_VALUE && type != LFM_ZERO_GRADIENT) return fail(c, LFM_EINVAL, "unknown patch type %d", type);
   const int32_t n = c->patch_size[patch], s = c->patch_start[patch];
@@ -1169,6 +1188,7 @@ int lfm_set_patch(lfm_ctx* c, int32_t patch, int32_t type, const double* values,
 int lfm_set_time_step(lfm_ctx* c, double dt) {
   int rc = need_uploaded(c);
   if (rc) return rc;
+  if ((rc = invalidate_seed(c))) return rc;
   if (!(std::isfinite(dt) && dt > 0)) return fail(c, LFM_EINVAL, "dt must be finite and > 0");
   if (c->pending_steps > 0 || ctx_batch_pending(c)) return fail(c, LFM_ESTATE, "an advance is pending");
   c->dt = dt;
@@ -1179,6 +1199,7 @@ int lfm_set_time_step(lfm_ctx* c, double dt) {
 int lfm_set_solver(lfm_ctx* c, const lfm_solver_opts* o) {
   int rc = need_uploaded(c);
   if (rc) return rc;
+  if ((rc = invalidate_seed(c))) return rc;
   if (!o) return fail(c, LFM_EINVAL, "opts is NULL");
   if (!(std::isfinite(o->tol) && o->tol >= 0) || !(std::isfinite(o->rel_tol) && o->rel_tol >= 0) ||
       o->max_iter < 1 || o->min_iter < 0 || o->min_iter > o->max_iter ||
@@ -1199,6 +1220,7 @@ int lfm_set_solver(lfm_ctx* c, const lfm_solver_opts* o) {
 int lfm_set_nonorth_correctors(lfm_ctx* c, int32_t n_corr) {
   int rc = need_uploaded(c);
   if (rc) return rc;
+  if ((rc = invalidate_seed(c))) return rc;
   if (n_corr < 0 || n_corr > 64) return fail(c, LFM_EINVAL, "n_corr must be in [0, 64] (got %d)", n_corr);
   if (c->pending_steps > 0) return fail(c, LFM_ESTATE, "an advance is pending");
   c->n_corr = n_corr;
@@ -1342,6 +1364,7 @@ int lfm_field_device_ptr(lfm_ctx* c, double** T_dev) {
 int lfm_get_matrix(lfm_ctx* c, double* diag, double* upper, double* source) {
   int rc = need_uploaded(c);
   if (rc) return rc;
+  if ((rc = invalidate_seed(c))) return rc;
   if (!diag || !source || (c->F > 0 && !upper)) return fail(c, LFM_EINVAL, "output arrays missing");
   if (c->pending_steps > 0) return fail(c, LFM_ESTATE, "an advance is pending");
   DeviceGuard g(c->device);
@@ -1393,6 +1416,7 @@ int lfm_get_launch(lfm_ctx* c, int32_t* ctas, int32_t* threads) {
 int lfm_set_launch(lfm_ctx* c, int32_t ctas, int32_t threads) {
   int rc = need_uploaded(c);
   if (rc) return rc;
+  if ((rc = invalidate_seed(c))) return rc;
   if (threads > 0 && threads != 256 && threads != 512 && threads != 1024)
     return fail(c, LFM_EINVAL, "threads must be 256, 512 or 1024");
   c->ctas = ctas > 0 ? ctas : 0;
@@ -1841,6 +1865,10 @@ int lfm_batch_finish(lfm_batch* b) {
   for (int i = 0; i < b->n_active; ++i) {
     const int32_t id = b->order[i];
     b->status[id] = b->h_status[i];
+    if (b->h_status[i] != 0) {  // a case that stopped early left no seed of its next step to trust
+      BCK(b, cudaMemsetAsync(b->slots[id]->cs.flags + 1, 0, sizeof(int32_t), b->stream));
+      BCK(b, cudaStreamSynchronize(b->stream));
+    }
     b->last_iters[id] = b->h_iters[i];
     b->steps_run[id] = b->h_steps[i];
     b->iters_run[id] = b->h_iters_sum[i];

@@ -128,8 +128,12 @@ struct CaseDev {
   float* xlo;                // [N]   field: trailing part
   float* xolo;               // [N]   trailing part of x_old (x_old holds the other two)
   float2* e2;                // [N]   the current solve's correction to the field
-  int32_t* flags;            // [1]   flags[0] != 0: the triple-float field (x2, xlo) is current and
-                             //       x holds its rounding; 0: x was written otherwise (split it)
+  int32_t* flags;            // [2]   flags[0] != 0: the triple-float field (x2, xlo) is current and
+                             //       x holds its rounding; 0: x was written otherwise (split it).
+                             //       flags[1] != 0: the mixed form's last launch ended with the
+                             //       next step's rows and inner-solve seed in place (seed_sums);
+                             //       cleared by every host change to the case
+  double* seed_sums;         // [3]   their team totals: normFactor sum, sum|r|, rho
   float2* diag2;             // [N]
   float2* rD2;               // [N]
   const float2* vdt2;        // [N]   V/dt * df_scale

@@ -243,8 +243,16 @@ __device__ bool steps_mixed_df(const CaseDev& cs, const CaseDev& cref, const Tea
   PhaseClock clk(cs, tm);
   const bool src_mode = cs.n_corr > 0 || cs.vSu != nullptr || cs.vSp != nullptr;
   const bool fuse = !src_mode;  // verification fused with the next step's T0 (pass V)
-  bool seeded = false;          // this step's rows and seed come from the last V pass
+  // this step's rows and seed come from the last V pass: of this launch, or of the last
+  // launch when it ended with them in place and nothing changed since (flags[1], cleared by
+  // the host with every change to the case; read by every CTA before the first barrier)
+  bool seeded = fuse && ld_volatile_i32(cs.flags + 1) != 0 && ld_volatile_i32(cs.flags) != 0;
   double seed[3] = {0.0, 0.0, 0.0};  // their team totals: normFactor sum, sum|r|, rho
+  if (seeded) {
+    seed[0] = __ldcg(cs.seed_sums);
+    seed[1] = __ldcg(cs.seed_sums + 1);
+    seed[2] = __ldcg(cs.seed_sums + 2);
+  }
   bool convert = ld_volatile_i32(cs.flags) == 0;  // read by every CTA before the first barrier
   for (int step = 0; step < n_steps; ++step) {
     int iters_tot = 0, sweeps_tot = 0, status = 0;
@@ -379,6 +387,16 @@ __device__ bool steps_mixed_df(const CaseDev& cs, const CaseDev& cref, const Tea
       if (tm.rank == 0 && tid == 0) set_status(cs.sync, status);
       return true;
     }
+  }
+  // the launch ends: whether the next step's rows and seed are in place, for the next launch
+  // (every CTA read flags[1] before the first barrier of this launch)
+  if (tm.rank == 0 && tid == 0) {
+    if (seeded) {
+      cs.seed_sums[0] = seed[0];
+      cs.seed_sums[1] = seed[1];
+      cs.seed_sums[2] = seed[2];
+    }
+    *reinterpret_cast<volatile int32_t*>(cs.flags + 1) = seeded ? 1 : 0;
   }
   return true;
 }

@@ -292,26 +292,32 @@ def test_field_carried_between_launches(prec):
     ("graded40", None, 3, 0, "any"),         # some steps end at the iteration limit
 ])
 def test_mixed_fused_verification_bitwise(name, tol, max_iter, min_iter, sweeps):
-    # In one launch every mixed step after the first starts from the previous step's
-    # verification pass (its rows and first residual formed there); one-step launches start
-    # each step with its own sum and row passes. Same field, same statistics, bit for bit.
+    # Every mixed step after the first starts from the previous step's verification pass
+    # (its rows and first residual formed there) -- within a launch, and across launches when
+    # nothing changed in between (the seed carried in device memory); a step after a change
+    # starts with its own sum and row passes. Same field, same statistics, bit for bit, for
+    # one launch, one-step launches, and one-step launches with the seed invalidated between
+    # them (a no-op change: the same time step set again).
     case = CASES[name]().with_(precision=B.LFM_MIXED)
     if tol is not None:
         case = case.with_(tol=tol)
     n = 5
 
-    def run(chunks):
+    def run(chunks, touch=False):
         with Solver.from_case(case) as s:
             s.set_solver(case.tol, case.rel_tol, max_iter, min_iter, B.LFM_MIXED)
             st = []
             for k in chunks:
+                if touch:
+                    B.lfm_set_time_step(s.ctx, case.dt)
                 st += s.advance(k)
             return s.field(), st
 
     Ta, sa = run([n])
     Tb, sb = run([1] * n)
-    assert np.array_equal(Ta, Tb)
-    assert sa == sb
+    Tc, sc = run([1] * n, touch=True)
+    assert np.array_equal(Ta, Tb) and np.array_equal(Ta, Tc)
+    assert sa == sb == sc
     most = max(s["sweeps"] for s in sa)
     if sweeps == "conv":
         assert all(s["converged"] for s in sa)
@@ -381,3 +387,26 @@ def test_timeout_and_nonfinite_in_the_df64_forms(prec):
         with pytest.raises(B.LfmError) as e:
             s.advance(1)
         assert e.value.code == B.LFM_ENONFINITE
+
+
+def test_mixed_seed_is_not_carried_across_a_change():
+    # a launch after a change of the time step must not start from the rows the last launch
+    # left for the old one: equal to a new context started from the same field (up to the
+    # triple-float field's rounding to FP64, which the new context starts from; rows of the
+    # old time step would be off by far more)
+    case = CASES["graded40"]().with_(precision=B.LFM_MIXED)
+    with Solver.from_case(case) as s:
+        s.set_solver(case.tol, 0.0, 1000, 0, B.LFM_MIXED)
+        s.advance(3)
+        T3 = s.field().copy()
+        B.lfm_set_time_step(s.ctx, 2.5 * case.dt)
+        st_a = s.advance(3)
+        Ta = s.field()
+    with Solver.from_case(case.with_(dt=2.5 * case.dt)) as t:
+        t.set_solver(case.tol, 0.0, 1000, 0, B.LFM_MIXED)
+        t.set_field(T3)
+        st_b = t.advance(3)
+        Tb = t.field()
+    assert [x["iters"] for x in st_a] == [x["iters"] for x in st_b]
+    assert [x["sweeps"] for x in st_a] == [x["sweeps"] for x in st_b]
+    assert relerr(Ta, Tb) <= 1e-12
