@@ -353,6 +353,13 @@ int lfm_set_barrier_timeout(lfm_ctx *ctx, uint64_t ns);
  * LFM_ETIMEOUT (no fault, no hang: every wait is bounded). One-shot; needs >= 2 CTAs. */
 int lfm_debug_skip_arrival(lfm_ctx *ctx, int32_t cta);
 
+/* Test switch: on != 0 (the default) lets the passes that can stream their matrix rows into
+ * shared memory with bulk copies do so (the FP32 A p of the mixed form in single-case
+ * launches, on meshes of six slots per cell with N a multiple of 4); 0 makes them load the
+ * rows into registers. Both give the same results bit for bit; the switch exists to test
+ * that. */
+int lfm_debug_stage_rows(lfm_ctx *ctx, int32_t on);
+
 /* 1 when this library is the checked build (compiled with LFM_CHECKED, liblapfoam_checked.so),
  * else 0. In the checked build every kernel tests each index it reads from the mesh's
  * addressing before using it as an address: a slot's neighbour cell (< n_cells), a face's

@@ -220,6 +220,7 @@ struct lfm_ctx {
   int ctas = 0, threads = 0;  // overrides (0 = tuned)
   uint64_t timeout_ns = 2000000000ull;
   int skip_cta = -1;
+  int stage_rows = 1;  // bulk-staged matrix rows where a pass supports them
 
   // async state
   lfm_step_stats* h_stats = nullptr;  // pinned, kStatsCap records
@@ -389,6 +390,7 @@ Launch current_launch(lfm_ctx* c, int& err) {
   err = L.ctas <= 0 ? 1 : 0;
   L.timeout_ns = c->timeout_ns;
   L.skip_cta = c->skip_cta;
+  L.stage_rows = c->stage_rows;
   return L;
 }
 
@@ -1449,6 +1451,12 @@ int lfm_debug_skip_arrival(lfm_ctx* c, int32_t cta) {
   return LFM_OK;
 }
 
+int lfm_debug_stage_rows(lfm_ctx* c, int32_t on) {
+  if (!c) return fail_free(LFM_EINVAL, "context is NULL");
+  c->stage_rows = on != 0 ? 1 : 0;
+  return LFM_OK;
+}
+
 int lfm_destroy(lfm_ctx* c) {
   if (!c) return LFM_OK;
   if (c->batch) return fail(c, LFM_ESTATE, "remove the context from its batch first");
@@ -1804,6 +1812,7 @@ int lfm_batch_advance_capped_async(lfm_batch* b, int32_t n_steps, int32_t use_gr
   bl.launch.threads = b->threads;
   bl.launch.timeout_ns = b->timeout_ns;
   bl.launch.skip_cta = -1;
+  bl.launch.stage_rows = 0;
   bl.W = W;
   bl.form = form;
   b->last_ctas = ctas;

@@ -255,6 +255,94 @@ __device__ __forceinline__ bool team_barrier(const Team& tm, TeamShared& sh) {
   return team_allreduce<0>(tm, nullptr, sh);
 }
 
+// ---- bulk copies global -> shared, completed on an mbarrier ------------------------------
+// One thread arms a stage's mbarrier with the byte count it expects and issues the bulk
+// copies (cp.async.bulk: the copy engine moves the bytes, no thread registers hold them);
+// every thread then waits on the barrier's phase. Source and destination must be 16-byte
+// aligned and each size a multiple of 16 bytes.
+extern __shared__ __align__(128) unsigned char lfm_dyn_smem[];
+
+__device__ __forceinline__ unsigned dyn_smem_bytes() {
+  unsigned v;
+  asm volatile("mov.u32 %0, %%dynamic_smem_size;" : "=r"(v));
+  return v;
+}
+
+__device__ __forceinline__ uint32_t smem_addr(const void* p) { return (uint32_t)__cvta_generic_to_shared(p); }
+
+__device__ __forceinline__ void mbar_init(uint64_t* bar, unsigned count) {
+  asm volatile("mbarrier.init.shared::cta.b64 [%0], %1;" ::"r"(smem_addr(bar)), "r"(count) : "memory");
+}
+
+// Makes the initialised barriers visible to the copy engine (the async proxy).
+__device__ __forceinline__ void mbar_init_fence() {
+  asm volatile("fence.mbarrier_init.release.cluster;" ::: "memory");
+}
+
+__device__ __forceinline__ void mbar_inval(uint64_t* bar) {
+  asm volatile("mbarrier.inval.shared::cta.b64 [%0];" ::"r"(smem_addr(bar)) : "memory");
+}
+
+__device__ __forceinline__ void mbar_arrive_expect_tx(uint64_t* bar, unsigned bytes) {
+  asm volatile("mbarrier.arrive.expect_tx.shared::cta.b64 _, [%0], %1;" ::"r"(smem_addr(bar)), "r"(bytes)
+               : "memory");
+}
+
+__device__ __forceinline__ bool mbar_try_wait(uint64_t* bar, unsigned parity) {
+  uint32_t done;
+  asm volatile(
+      "{\n\t.reg .pred p;\n\t"
+      "mbarrier.try_wait.parity.shared::cta.b64 p, [%1], %2;\n\t"
+      "selp.u32 %0, 1, 0, p;\n\t}"
+      : "=r"(done)
+      : "r"(smem_addr(bar)), "r"(parity)
+      : "memory");
+  return done != 0;
+}
+
+// L2 policy for data read once per pass (the matrix): evicted first, so that it does not
+// displace the gathered vector.
+__device__ __forceinline__ uint64_t l2_evict_first_policy() {
+  uint64_t pol;
+  asm volatile("createpolicy.fractional.L2::evict_first.b64 %0, 1.0;" : "=l"(pol));
+  return pol;
+}
+
+__device__ __forceinline__ void bulk_g2s(void* dst, const void* src, unsigned bytes, uint64_t* bar, uint64_t pol) {
+  asm volatile(
+      "cp.async.bulk.shared::cluster.global.mbarrier::complete_tx::bytes.L2::cache_hint [%0], [%1], %2, [%3], %4;" ::"r"(
+          smem_addr(dst)),
+      "l"(src), "r"(bytes), "r"(smem_addr(bar)), "l"(pol)
+      : "memory");
+}
+
+// Waits for the barrier's phase with the given parity. False (with LFM_ETIMEOUT recorded,
+// unless another error was) when the launch's time limit runs out or another CTA has
+// recorded an error.
+__device__ __forceinline__ bool mbar_wait(uint64_t* bar, unsigned parity, int32_t* status, uint64_t timeout_ns) {
+  if (mbar_try_wait(bar, parity)) return true;
+  const uint64_t t0 = global_timer_ns();
+  for (unsigned spins = 1;; ++spins) {
+    if (mbar_try_wait(bar, parity)) return true;
+    if ((spins & 15u) == 0) {
+      if (ld_volatile_i32(status) != 0) return false;
+      if (global_timer_ns() - t0 > timeout_ns) {
+        atomicCAS(status, 0, (int32_t)LFM_ETIMEOUT);
+        return false;
+      }
+    }
+  }
+}
+
+// Waits for the barrier's phase without regard to the launch's status (bounded by the time
+// limit): the drain of copies still in flight before a CTA that failed leaves.
+__device__ __forceinline__ void mbar_drain(uint64_t* bar, unsigned parity, uint64_t timeout_ns) {
+  const uint64_t t0 = global_timer_ns();
+  while (!mbar_try_wait(bar, parity)) {
+    if (global_timer_ns() - t0 > timeout_ns) return;
+  }
+}
+
 // Records an error status for the launch (first error wins).
 __device__ __forceinline__ void set_status(SyncWords* sw, int32_t code) {
   atomicCAS(&sw->status, 0, code);

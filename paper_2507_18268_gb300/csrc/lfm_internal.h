@@ -160,6 +160,7 @@ struct Launch {
   int threads;
   uint64_t timeout_ns;
   int skip_cta;              // test hook: CTA that leaves before its first arrival (-1: none)
+  int stage_rows;            // 0: passes load their matrix rows into registers (test switch)
 };
 
 enum Mode { kModeSteps = 0, kModeAssembleOnly = 1 };

@@ -485,6 +485,139 @@ __device__ __forceinline__ double pass_amul_dot_f32(Slots<float> A, int c0, int 
   return sig.value();
 }
 
+// ---- M (FP32) with the matrix rows streamed into shared memory by bulk copies ----------
+// The CTA's cells go in tiles of 2B, the cells two loop trips of pass_amul_dot_f32 take (a
+// thread takes cells j and j + B of a tile). The slot indices, coefficients and diagonal of a
+// tile arrive in one of two shared-memory stages (cp.async.bulk, completed on an mbarrier,
+// issued by one thread) while the threads work on the other, so the matrix bytes are in
+// flight without occupying registers and a thread's global loads are its vector gathers.
+// Same cells per thread in the same order, same operations in the same order as the
+// register form: equal results bit for bit. Needs N a multiple of 4 (16-byte aligned plane
+// starts and tile sizes) and the dynamic shared memory of stage_bytes_f32; ok = false when a
+// wait ran out (status recorded; the caller leaves). (The FP64 A p measured slower staged:
+// its 8-byte coefficients leave room for one row per thread per tile, or only the indices
+// can be staged, and that pass is bound by FP64 issue and the gathers, not by its loads.)
+template <int B, int W>
+__host__ __device__ constexpr unsigned stage_bytes_f32() {
+  return W > 0 ? 2u * (2u * B) * (4u * W + 4u * (W + 1u)) + 16u : 0u;
+}
+
+template <int B, int W>
+__device__ __forceinline__ bool use_bulk_f32(const Slots<float>& A) {
+  return W > 0 && (A.N & 3) == 0 && dyn_smem_bytes() >= stage_bytes_f32<B, W>();
+}
+
+template <int B, int W>
+__device__ __noinline__ double pass_amul_dot_f32_bulk(Slots<float> A, int c0, int c1, const float* __restrict__ p,
+                                                   float* __restrict__ q, const Team& tm, bool& ok) {
+  constexpr int TC = 2 * B;
+  constexpr int kW = W > 0 ? W : 1;
+  constexpr unsigned kPlane = TC * 4u;
+  constexpr unsigned kStage = (2u * kW + 1u) * kPlane;
+  unsigned char* sm = lfm_dyn_smem;
+  uint64_t* bar = reinterpret_cast<uint64_t*>(sm + 2 * kStage);
+  const int tid = threadIdx.x;
+  const int ntiles = c1 > c0 ? (c1 - c0 + TC - 1) / TC : 0;
+  const size_t N = (size_t)A.N;
+  uint64_t pol = 0;
+  auto issue = [&](int t) {
+    const int s = t & 1;
+    const int t0 = c0 + t * TC;
+    const unsigned n = (unsigned)min(TC, c1 - t0);
+    unsigned char* st = sm + s * kStage;
+    mbar_arrive_expect_tx(bar + s, (2u * kW + 1u) * n * 4u);
+#pragma unroll
+    for (int k = 0; k < kW; ++k) {
+      bulk_g2s(st + k * kPlane, A.other + (size_t)k * N + t0, n * 4u, bar + s, pol);
+      bulk_g2s(st + (kW + k) * kPlane, A.coef + (size_t)k * N + t0, n * 4u, bar + s, pol);
+    }
+    bulk_g2s(st + 2 * kW * kPlane, A.diag + t0, n * 4u, bar + s, pol);
+  };
+  if (tid == 0) {
+    mbar_init(bar, 1);
+    mbar_init(bar + 1, 1);
+    mbar_init_fence();
+    pol = l2_evict_first_policy();
+    for (int t = 0; t < 2 && t < ntiles; ++t) issue(t);
+  }
+  __syncthreads();
+  Acc2f sig;
+  int t = 0;
+  bool failed = false;
+  for (; t < ntiles; ++t) {
+    const int s = t & 1;
+    const bool got = mbar_wait(bar + s, (t >> 1) & 1, &tm.sw->status, tm.timeout_ns);
+    if (got) {
+      const int t0 = c0 + t * TC;
+      const int nt = min(TC, c1 - t0);
+      const unsigned char* st = sm + s * kStage;
+      const int32_t* so = reinterpret_cast<const int32_t*>(st);
+      const float* sc = reinterpret_cast<const float*>(st + kW * kPlane);
+      const float* sd = reinterpret_cast<const float*>(st + 2 * kW * kPlane);
+      const int j = tid;
+      if (j + B < nt) {
+        // both rows' loads issued before either is used (as in rows2)
+        const int j2 = j + B, c = t0 + j, c2 = t0 + j2;
+        const float vc = p[c], vc2 = p[c2];
+        float acc = sd[j] * vc, acc2 = sd[j2] * vc2;
+        int o[kW], o2[kW];
+        float u[kW], u2[kW];
+#pragma unroll
+        for (int k = 0; k < kW; ++k) {
+          o[k] = LFM_IDX(so[k * TC + j], A.N, c, kChkSlotCell);
+          o2[k] = LFM_IDX(so[k * TC + j2], A.N, c2, kChkSlotCell);
+          u[k] = sc[k * TC + j];
+          u2[k] = sc[k * TC + j2];
+        }
+#pragma unroll
+        for (int k = 0; k < kW; ++k) {
+          acc = fmaf(u[k], p[o[k]], acc);
+          acc2 = fmaf(u2[k], p[o2[k]], acc2);
+        }
+        q[c] = acc;
+        q[c2] = acc2;
+        sig.add_prod(acc, vc);
+        sig.add_prod(acc2, vc2);
+      } else if (j < nt) {
+        const int c = t0 + j;
+        const float vc = p[c];
+        float y = sd[j] * vc;
+#pragma unroll
+        for (int k = 0; k < kW; ++k) y = fmaf(sc[k * TC + j], p[LFM_IDX(so[k * TC + j], A.N, c, kChkSlotCell)], y);
+        q[c] = y;
+        sig.add_prod(y, vc);
+      }
+    }
+    if (__syncthreads_or(!got)) {  // every thread is done with stage s (or one wait failed)
+      failed = true;
+      break;
+    }
+    if (tid == 0 && t + 2 < ntiles) issue(t + 2);
+  }
+  if (tid == 0) {
+    // a failed wait: let the copies still in flight land before the CTA leaves
+    if (failed)
+      for (int u = t; u < ntiles && u < t + 2; ++u) mbar_drain(bar + (u & 1), (u >> 1) & 1, tm.timeout_ns);
+    mbar_inval(bar);
+    mbar_inval(bar + 1);
+  }
+  __syncthreads();
+  ok = !failed;
+  return sig.value();
+}
+
+// M (FP32) over the bulk-staged rows where the launch gave the shared memory for them, else
+// the register form.
+template <int B, int W>
+__device__ __forceinline__ double amul_dot_f32(Slots<float> A, int c0, int c1, const float* __restrict__ p,
+                                               float* __restrict__ q, const Team& tm, bool& ok) {
+  ok = true;
+  if constexpr (W > 0) {
+    if (use_bulk_f32<B, W>(A)) return pass_amul_dot_f32_bulk<B, W>(A, c0, c1, p, q, tm, ok);
+  }
+  return pass_amul_dot_f32<B, W>(A, c0, c1, p, q);
+}
+
 // U (FP64): x += alpha p, r -= alpha q, w = rD r; returns this thread's sum|r| and w.r.
 template <int B>
 __device__ __forceinline__ double2 pass_update_f64(int c0, int c1, double alpha, double* __restrict__ x,
@@ -867,7 +1000,9 @@ __device__ void run_steps_mixed(const CaseDev& cs, const CaseDev& cref, const Te
             if (!team_barrier(tm, sh)) return;
             clk.lap(kPhP);
           }
-          double s1[1] = {pass_amul_dot_f32<B, W>(slots32(cs), c0, c1, p, q)};
+          bool m_ok;
+          double s1[1] = {amul_dot_f32<B, W>(slots32(cs), c0, c1, p, q, tm, m_ok)};
+          if (!m_ok) return;
           if (!team_allreduce<1>(tm, s1, sh)) return;
           clk.lap(kPhM);
           const double sigma = s1[0];

@@ -321,7 +321,9 @@ __device__ bool steps_mixed_df(const CaseDev& cs, const CaseDev& cref, const Tea
             if (!team_barrier(tm, sh)) return false;
             clk.lap(kPhP);
           }
-          double s1[1] = {pass_amul_dot_f32<B, W>(slots32(cs), c0, c1, p, q)};
+          bool m_ok;
+          double s1[1] = {amul_dot_f32<B, W>(slots32(cs), c0, c1, p, q, tm, m_ok)};
+          if (!m_ok) return false;
           if (!team_allreduce<1>(tm, s1, sh)) return false;
           clk.lap(kPhM);
           const double sigma = s1[0];

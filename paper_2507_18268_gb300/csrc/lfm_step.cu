@@ -2,6 +2,10 @@
 // one case with every CTA of the grid in its team (the step itself is in lfm_solve.cuh).
 #include <cuda_runtime.h>
 
+#include <mutex>
+#include <utility>
+#include <vector>
+
 #include "lfm_device.cuh"
 #include "lfm_internal.h"
 #include "lfm_solve.cuh"
@@ -315,19 +319,57 @@ void* step_fn_for(int precision, int threads, int W) {
   }
 }
 
+// Dynamic shared memory of a step kernel: the two stages of the bulk-staged FP32 A p of the
+// mixed form (kernels specialised for six slots).
+unsigned step_dyn_smem(int precision, int threads, int W) {
+  if ((precision == LFM_MIXED || precision == kMixedDf) && W == 6) {
+    switch (threads) {
+      case 256: return stage_bytes_f32<256, 6>();
+      case 512: return stage_bytes_f32<512, 6>();
+      case 1024: return stage_bytes_f32<1024, 6>();
+      default: return 0;
+    }
+  }
+  return 0;
+}
+
+// Opts a kernel into more than 48 KB of dynamic shared memory, once per kernel and device.
+cudaError_t allow_dyn_smem(void* fn, unsigned bytes) {
+  if (bytes <= 48u * 1024u) return cudaSuccess;
+  static std::mutex mu;
+  static std::vector<std::pair<void*, int>> done;
+  int dev = 0;
+  cudaError_t e = cudaGetDevice(&dev);
+  if (e != cudaSuccess) return e;
+  std::lock_guard<std::mutex> lk(mu);
+  for (const auto& d : done)
+    if (d.first == fn && d.second == dev) return cudaSuccess;
+  e = cudaFuncSetAttribute(fn, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)bytes);
+  if (e == cudaSuccess) done.emplace_back(fn, dev);
+  return e;
+}
+
+int per_sm_ctas(int precision, int threads, int W) {
+  void* fn = step_fn_for(precision, threads, W);
+  if (!fn) return 0;
+  const unsigned dyn = step_dyn_smem(precision, threads, W);
+  int per_sm = 0;
+  if (allow_dyn_smem(fn, dyn) != cudaSuccess ||
+      cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, fn, threads, dyn) != cudaSuccess)
+    return 0;
+  return per_sm;
+}
+
 }  // namespace
 
 int max_coresident_ctas(int precision, int threads, int W, int device) {
-  void* fn = step_fn_for(precision, threads, W);
-  if (!fn) return 0;
-  int per_sm = 0, sms = 0;
-  if (cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, fn, threads, 0) != cudaSuccess) return 0;
-  if (precision == LFM_MIXED || precision == LFM_DF64) {  // either kernel of the form may run
-    int per_sm_2 = 0;
-    void* fn2 = step_fn_for(precision == LFM_MIXED ? kMixedDf : kDf64Geom, threads, W);
-    if (cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm_2, fn2, threads, 0) != cudaSuccess) return 0;
+  int sms = 0;
+  int per_sm = per_sm_ctas(precision, threads, W);
+  if (per_sm > 0 && (precision == LFM_MIXED || precision == LFM_DF64)) {  // either kernel of the form may run
+    const int per_sm_2 = per_sm_ctas(precision == LFM_MIXED ? kMixedDf : kDf64Geom, threads, W);
     if (per_sm_2 < per_sm) per_sm = per_sm_2;
   }
+  if (per_sm <= 0) return 0;
   if (cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, device) != cudaSuccess) return 0;
   int n = per_sm * sms;
   return n < kMaxCtas ? n : kMaxCtas;
@@ -340,14 +382,18 @@ cudaError_t launch_steps(const CaseDev& cs, const Launch& L, int n_steps, int mo
   // the mixed form runs its outer passes in df64 when the case allows (see mixed_uses_df)
   const bool mixed_df = prec == LFM_MIXED && mode == kModeSteps && mixed_runs_df(cs);
   const bool df_geom = prec == LFM_DF64 && cs.Sf != nullptr;
-  void* fn = step_fn_for(mixed_df ? kMixedDf : (df_geom ? kDf64Geom : prec), L.threads, cs.W);
+  const int kind = mixed_df ? kMixedDf : (df_geom ? kDf64Geom : prec);
+  void* fn = step_fn_for(kind, L.threads, cs.W);
   if (!fn) return cudaErrorInvalidValue;
+  const unsigned dyn = L.stage_rows ? step_dyn_smem(kind, L.threads, cs.W) : 0u;
+  const cudaError_t e = allow_dyn_smem(fn, dyn);
+  if (e != cudaSuccess) return e;
   CaseDev a0 = cs;
   a0.precision = prec;
   Launch a1 = L;
   int a2 = n_steps, a3 = mode;
   void* args[] = {&a0, &a1, &a2, &a3};
-  return cudaLaunchCooperativeKernel(fn, dim3(L.ctas), dim3(L.threads), args, 0, stream);
+  return cudaLaunchCooperativeKernel(fn, dim3(L.ctas), dim3(L.threads), args, dyn, stream);
 }
 
 bool mixed_runs_df(const CaseDev& cs) {
