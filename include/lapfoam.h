@@ -496,6 +496,12 @@ int lfm_batch_size(const lfm_batch *b);
  * classes (NULL keeps the current ones; defaults 512 and {4, 8, 16}). */
 int lfm_batch_set_launch(lfm_batch *b, int32_t threads, const int32_t *cells_per_thread);
 
+/* Test switch of a batch, as lfm_debug_stage_rows for a context: on != 0 (the default) lets
+ * the batched kernel stream A p's matrix rows into shared memory for mixed cases of six slots
+ * per cell with N a multiple of 4; 0 makes it load them into registers. Same results bit for
+ * bit. */
+int lfm_batch_debug_stage_rows(lfm_batch *b, int32_t on);
+
 /* Current launch shape (ctas = CTAs of the persistent launch). */
 int lfm_batch_get_launch(lfm_batch *b, int32_t *ctas, int32_t *threads, int32_t *cells_per_thread);
 

@@ -133,6 +133,7 @@ _SIGS = {
     "lfm_batch_remove": ([c_void_p, c_int32], c_int),
     "lfm_batch_size": ([c_void_p], c_int),
     "lfm_batch_set_launch": ([c_void_p, c_int32, POINTER(c_int32)], c_int),
+    "lfm_batch_debug_stage_rows": ([c_void_p, c_int32], c_int),
     "lfm_batch_get_launch": ([c_void_p, POINTER(c_int32), POINTER(c_int32), POINTER(c_int32)], c_int),
     "lfm_batch_set_barrier_timeout": ([c_void_p, c_uint64], c_int),
     "lfm_batch_advance_async": ([c_void_p, c_int32, c_int32], c_int),
@@ -582,6 +583,10 @@ def lfm_batch_get_launch(b):
 
 def lfm_batch_set_barrier_timeout(b, ns: int):
     _bcheck(load().lfm_batch_set_barrier_timeout(b, int(ns)), b)
+
+
+def lfm_batch_debug_stage_rows(b, on: bool):
+    _bcheck(load().lfm_batch_debug_stage_rows(b, 1 if on else 0), b)
 
 
 def lfm_batch_advance_async(b, n_steps: int, use_graph: bool = True):

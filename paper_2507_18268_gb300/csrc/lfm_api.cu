@@ -1529,7 +1529,8 @@ struct lfm_batch {
   int n_active = 0;
   // captured one-step graph
   cudaGraphExec_t gexec = nullptr;
-  int g_threads = 0, g_W = -1, g_ctas = 0, g_form = -1;
+  int g_threads = 0, g_W = -1, g_ctas = 0, g_form = -1, g_stage = -1;
+  int stage_rows = 1;  // bulk-staged matrix rows where a pass supports them
   int last_ctas = 0, last_W = 6, last_form = kBatchAny;
 };
 
@@ -1696,6 +1697,12 @@ int lfm_batch_size(const lfm_batch* b) {
   return n;
 }
 
+int lfm_batch_debug_stage_rows(lfm_batch* b, int32_t on) {
+  if (!b) return fail_free(LFM_EINVAL, "batch is NULL");
+  b->stage_rows = on != 0 ? 1 : 0;
+  return LFM_OK;
+}
+
 int lfm_batch_set_launch(lfm_batch* b, int32_t threads, const int32_t* cells_per_thread) {
   if (!b) return bfail(nullptr, LFM_EINVAL, "batch is NULL");
   if (threads != 256 && threads != 512) return bfail(b, LFM_EINVAL, "threads must be 256 or 512");
@@ -1812,14 +1819,15 @@ int lfm_batch_advance_capped_async(lfm_batch* b, int32_t n_steps, int32_t use_gr
   bl.launch.threads = b->threads;
   bl.launch.timeout_ns = b->timeout_ns;
   bl.launch.skip_cta = -1;
-  bl.launch.stage_rows = 0;
+  bl.launch.stage_rows = b->stage_rows;
   bl.W = W;
   bl.form = form;
   b->last_ctas = ctas;
   b->last_W = W;
   b->last_form = form;
   if (use_graph) {
-    if (!b->gexec || b->g_threads != b->threads || b->g_W != W || b->g_ctas != ctas || b->g_form != form) {
+    if (!b->gexec || b->g_threads != b->threads || b->g_W != W || b->g_ctas != ctas || b->g_form != form ||
+        b->g_stage != b->stage_rows) {
       if (b->gexec) cudaGraphExecDestroy(b->gexec);
       b->gexec = nullptr;
       cudaGraph_t graph = nullptr;
@@ -1838,6 +1846,7 @@ int lfm_batch_advance_capped_async(lfm_batch* b, int32_t n_steps, int32_t use_gr
       b->g_W = W;
       b->g_ctas = ctas;
       b->g_form = form;
+      b->g_stage = b->stage_rows;
     }
     for (int s = 0; s < n_steps; ++s) BCK(b, cudaGraphLaunch(b->gexec, b->stream));
   } else {

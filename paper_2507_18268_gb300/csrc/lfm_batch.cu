@@ -128,13 +128,27 @@ void* batch_fn(int threads, int W, int form) {
   }
 }
 
+// Dynamic shared memory of a batched kernel: the stages of the bulk-staged FP32 A p, for the
+// kernel that runs mixed cases (six slots).
+unsigned batch_dyn_smem(int threads, int W, int form) {
+  if (W != 6 || form != kBatchAny) return 0;
+  switch (threads) {
+    case 256: return stage_bytes_f32<256, 6>();
+    case 512: return stage_bytes_f32<512, 6>();
+    default: return 0;
+  }
+}
+
 }  // namespace
 
 int max_coresident_batch_ctas(int threads, int W, int form, int device) {
   void* fn = batch_fn(threads, W, form);
   if (!fn) return 0;
   int per_sm = 0, sms = 0;
-  if (cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, fn, threads, 0) != cudaSuccess) return 0;
+  const unsigned dyn = batch_dyn_smem(threads, W, form);
+  if (allow_dyn_smem(fn, dyn) != cudaSuccess ||
+      cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, fn, threads, dyn) != cudaSuccess)
+    return 0;
   if (cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, device) != cudaSuccess) return 0;
   const int n = per_sm * sms;
   return n < kMaxCtas ? n : kMaxCtas;
@@ -159,12 +173,17 @@ cudaError_t launch_batch_collect(const CaseDev* cases, int n_cases, const int32_
 cudaError_t launch_batch_steps(const BatchLaunch& bl, int n_steps, cudaStream_t s) {
   void* fn = batch_fn(bl.launch.threads, bl.W, bl.form);
   if (!fn) return cudaErrorInvalidValue;
-  cudaError_t e = cudaMemsetAsync(&bl.hdr->ticket, 0, sizeof(int32_t), s);
+  // the opt-in above 48 KB was made when the launch shape was sized (max_coresident_batch_ctas),
+  // outside any stream capture; this call finds it recorded
+  const unsigned dyn = bl.launch.stage_rows ? batch_dyn_smem(bl.launch.threads, bl.W, bl.form) : 0u;
+  cudaError_t e = allow_dyn_smem(fn, dyn);
+  if (e != cudaSuccess) return e;
+  e = cudaMemsetAsync(&bl.hdr->ticket, 0, sizeof(int32_t), s);
   if (e != cudaSuccess) return e;
   cudaLaunchConfig_t cfg = {};
   cfg.gridDim = dim3(bl.launch.ctas);
   cfg.blockDim = dim3(bl.launch.threads);
-  cfg.dynamicSmemBytes = 0;
+  cfg.dynamicSmemBytes = dyn;
   cfg.stream = s;
   cudaLaunchAttribute attr[1];
   attr[0].id = cudaLaunchAttributeCooperative;

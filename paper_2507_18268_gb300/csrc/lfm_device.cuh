@@ -343,6 +343,57 @@ __device__ __forceinline__ void mbar_drain(uint64_t* bar, unsigned parity, uint6
   }
 }
 
+// Runs body over the CTA's cells [c0, c1) in tiles of TC cells whose per-cell rows arrive in
+// shared memory by bulk copies, two stages of kStage bytes at the start of the dynamic shared
+// memory (their mbarriers after them). issue(stage, t0, n, bar, pol), called by thread 0
+// only, arms bar with the tile's byte count and issues its copies into stage; body(stage, t0,
+// nt) processes tile [t0, t0 + nt) once its copies have landed. The copy of tile t + 2 is
+// issued as soon as every thread is done with tile t. False when a wait ran out or another CTA
+// failed (status recorded): the CTA then lets its copies in flight land (bounded) before the
+// caller leaves.
+template <int TC, unsigned kStage, typename Issue, typename Body>
+__device__ __forceinline__ bool staged_tiles(int c0, int c1, const Team& tm, Issue&& issue, Body&& body) {
+  unsigned char* sm = lfm_dyn_smem;
+  uint64_t* bar = reinterpret_cast<uint64_t*>(sm + 2 * kStage);
+  const int tid = threadIdx.x;
+  const int ntiles = c1 > c0 ? (c1 - c0 + TC - 1) / TC : 0;
+  if (tid == 0) {
+    mbar_init(bar, 1);
+    mbar_init(bar + 1, 1);
+    mbar_init_fence();
+    const uint64_t pol = l2_evict_first_policy();
+    for (int t = 0; t < 2 && t < ntiles; ++t) {
+      const int t0 = c0 + t * TC;
+      issue(sm + (t & 1) * kStage, t0, min(TC, c1 - t0), bar + (t & 1), pol);
+    }
+  }
+  __syncthreads();
+  int t = 0;
+  bool failed = false;
+  for (; t < ntiles; ++t) {
+    const int s = t & 1;
+    const bool got = mbar_wait(bar + s, (t >> 1) & 1, &tm.sw->status, tm.timeout_ns);
+    const int t0 = c0 + t * TC;
+    if (got) body(static_cast<const unsigned char*>(sm + s * kStage), t0, min(TC, c1 - t0));
+    if (__syncthreads_or(!got)) {  // every thread is done with stage s (or one wait failed)
+      failed = true;
+      break;
+    }
+    if (tid == 0 && t + 2 < ntiles) {
+      const int t2 = t0 + 2 * TC;
+      issue(sm + s * kStage, t2, min(TC, c1 - t2), bar + s, l2_evict_first_policy());
+    }
+  }
+  if (tid == 0) {
+    if (failed)
+      for (int u = t; u < ntiles && u < t + 2; ++u) mbar_drain(bar + (u & 1), (u >> 1) & 1, tm.timeout_ns);
+    mbar_inval(bar);
+    mbar_inval(bar + 1);
+  }
+  __syncthreads();
+  return !failed;
+}
+
 // Records an error status for the launch (first error wins).
 __device__ __forceinline__ void set_status(SyncWords* sw, int32_t code) {
   atomicCAS(&sw->status, 0, code);

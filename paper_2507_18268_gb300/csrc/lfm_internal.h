@@ -194,6 +194,8 @@ enum BatchForm { kBatchAny = 0, kBatchFp64 = 1, kBatchDf64 = 2 };
 cudaError_t launch_steps(const CaseDev& cs, const Launch& L, int n_steps, int mode,
                          cudaStream_t stream);
 // Largest co-resident CTA count for the step kernel at `threads` per CTA.
+// Opts a kernel into more than 48 KB of dynamic shared memory (once per kernel and device).
+cudaError_t allow_dyn_smem(void* fn, unsigned bytes);
 int max_coresident_ctas(int precision, int threads, int W, int device);
 cudaError_t launch_boundary_values(const CaseDev& cs, double* Tb, cudaStream_t stream);
 // Gauss linear gradient of the current T: cells into cs.grad, and (bgrad non-null) the

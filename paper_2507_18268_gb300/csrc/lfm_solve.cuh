@@ -514,95 +514,58 @@ __device__ __noinline__ double pass_amul_dot_f32_bulk(Slots<float> A, int c0, in
   constexpr int kW = W > 0 ? W : 1;
   constexpr unsigned kPlane = TC * 4u;
   constexpr unsigned kStage = (2u * kW + 1u) * kPlane;
-  unsigned char* sm = lfm_dyn_smem;
-  uint64_t* bar = reinterpret_cast<uint64_t*>(sm + 2 * kStage);
-  const int tid = threadIdx.x;
-  const int ntiles = c1 > c0 ? (c1 - c0 + TC - 1) / TC : 0;
   const size_t N = (size_t)A.N;
-  uint64_t pol = 0;
-  auto issue = [&](int t) {
-    const int s = t & 1;
-    const int t0 = c0 + t * TC;
-    const unsigned n = (unsigned)min(TC, c1 - t0);
-    unsigned char* st = sm + s * kStage;
-    mbar_arrive_expect_tx(bar + s, (2u * kW + 1u) * n * 4u);
+  const int tid = threadIdx.x;
+  Acc2f sig;
+  auto issue = [&](unsigned char* st, int t0, int n, uint64_t* bar, uint64_t pol) {
+    const unsigned bytes = (unsigned)n * 4u;
+    mbar_arrive_expect_tx(bar, (2u * kW + 1u) * bytes);
 #pragma unroll
     for (int k = 0; k < kW; ++k) {
-      bulk_g2s(st + k * kPlane, A.other + (size_t)k * N + t0, n * 4u, bar + s, pol);
-      bulk_g2s(st + (kW + k) * kPlane, A.coef + (size_t)k * N + t0, n * 4u, bar + s, pol);
+      bulk_g2s(st + k * kPlane, A.other + (size_t)k * N + t0, bytes, bar, pol);
+      bulk_g2s(st + (kW + k) * kPlane, A.coef + (size_t)k * N + t0, bytes, bar, pol);
     }
-    bulk_g2s(st + 2 * kW * kPlane, A.diag + t0, n * 4u, bar + s, pol);
+    bulk_g2s(st + 2 * kW * kPlane, A.diag + t0, bytes, bar, pol);
   };
-  if (tid == 0) {
-    mbar_init(bar, 1);
-    mbar_init(bar + 1, 1);
-    mbar_init_fence();
-    pol = l2_evict_first_policy();
-    for (int t = 0; t < 2 && t < ntiles; ++t) issue(t);
-  }
-  __syncthreads();
-  Acc2f sig;
-  int t = 0;
-  bool failed = false;
-  for (; t < ntiles; ++t) {
-    const int s = t & 1;
-    const bool got = mbar_wait(bar + s, (t >> 1) & 1, &tm.sw->status, tm.timeout_ns);
-    if (got) {
-      const int t0 = c0 + t * TC;
-      const int nt = min(TC, c1 - t0);
-      const unsigned char* st = sm + s * kStage;
-      const int32_t* so = reinterpret_cast<const int32_t*>(st);
-      const float* sc = reinterpret_cast<const float*>(st + kW * kPlane);
-      const float* sd = reinterpret_cast<const float*>(st + 2 * kW * kPlane);
-      const int j = tid;
-      if (j + B < nt) {
-        // both rows' loads issued before either is used (as in rows2)
-        const int j2 = j + B, c = t0 + j, c2 = t0 + j2;
-        const float vc = p[c], vc2 = p[c2];
-        float acc = sd[j] * vc, acc2 = sd[j2] * vc2;
-        int o[kW], o2[kW];
-        float u[kW], u2[kW];
+  auto body = [&](const unsigned char* st, int t0, int nt) {
+    const int32_t* so = reinterpret_cast<const int32_t*>(st);
+    const float* sc = reinterpret_cast<const float*>(st + kW * kPlane);
+    const float* sd = reinterpret_cast<const float*>(st + 2 * kW * kPlane);
+    const int j = tid;
+    if (j + B < nt) {
+      // both rows' loads issued before either is used (as in rows2)
+      const int j2 = j + B, c = t0 + j, c2 = t0 + j2;
+      const float vc = p[c], vc2 = p[c2];
+      float acc = sd[j] * vc, acc2 = sd[j2] * vc2;
+      int o[kW], o2[kW];
+      float u[kW], u2[kW];
 #pragma unroll
-        for (int k = 0; k < kW; ++k) {
-          o[k] = LFM_IDX(so[k * TC + j], A.N, c, kChkSlotCell);
-          o2[k] = LFM_IDX(so[k * TC + j2], A.N, c2, kChkSlotCell);
-          u[k] = sc[k * TC + j];
-          u2[k] = sc[k * TC + j2];
-        }
-#pragma unroll
-        for (int k = 0; k < kW; ++k) {
-          acc = fmaf(u[k], p[o[k]], acc);
-          acc2 = fmaf(u2[k], p[o2[k]], acc2);
-        }
-        q[c] = acc;
-        q[c2] = acc2;
-        sig.add_prod(acc, vc);
-        sig.add_prod(acc2, vc2);
-      } else if (j < nt) {
-        const int c = t0 + j;
-        const float vc = p[c];
-        float y = sd[j] * vc;
-#pragma unroll
-        for (int k = 0; k < kW; ++k) y = fmaf(sc[k * TC + j], p[LFM_IDX(so[k * TC + j], A.N, c, kChkSlotCell)], y);
-        q[c] = y;
-        sig.add_prod(y, vc);
+      for (int k = 0; k < kW; ++k) {
+        o[k] = LFM_IDX(so[k * TC + j], A.N, c, kChkSlotCell);
+        o2[k] = LFM_IDX(so[k * TC + j2], A.N, c2, kChkSlotCell);
+        u[k] = sc[k * TC + j];
+        u2[k] = sc[k * TC + j2];
       }
+#pragma unroll
+      for (int k = 0; k < kW; ++k) {
+        acc = fmaf(u[k], p[o[k]], acc);
+        acc2 = fmaf(u2[k], p[o2[k]], acc2);
+      }
+      q[c] = acc;
+      q[c2] = acc2;
+      sig.add_prod(acc, vc);
+      sig.add_prod(acc2, vc2);
+    } else if (j < nt) {
+      const int c = t0 + j;
+      const float vc = p[c];
+      float y = sd[j] * vc;
+#pragma unroll
+      for (int k = 0; k < kW; ++k) y = fmaf(sc[k * TC + j], p[LFM_IDX(so[k * TC + j], A.N, c, kChkSlotCell)], y);
+      q[c] = y;
+      sig.add_prod(y, vc);
     }
-    if (__syncthreads_or(!got)) {  // every thread is done with stage s (or one wait failed)
-      failed = true;
-      break;
-    }
-    if (tid == 0 && t + 2 < ntiles) issue(t + 2);
-  }
-  if (tid == 0) {
-    // a failed wait: let the copies still in flight land before the CTA leaves
-    if (failed)
-      for (int u = t; u < ntiles && u < t + 2; ++u) mbar_drain(bar + (u & 1), (u >> 1) & 1, tm.timeout_ns);
-    mbar_inval(bar);
-    mbar_inval(bar + 1);
-  }
-  __syncthreads();
-  ok = !failed;
+  };
+  ok = staged_tiles<TC, kStage>(c0, c1, tm, issue, body);
   return sig.value();
 }
 

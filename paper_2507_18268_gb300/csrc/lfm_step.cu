@@ -333,6 +333,19 @@ unsigned step_dyn_smem(int precision, int threads, int W) {
   return 0;
 }
 
+int per_sm_ctas(int precision, int threads, int W) {
+  void* fn = step_fn_for(precision, threads, W);
+  if (!fn) return 0;
+  const unsigned dyn = step_dyn_smem(precision, threads, W);
+  int per_sm = 0;
+  if (allow_dyn_smem(fn, dyn) != cudaSuccess ||
+      cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, fn, threads, dyn) != cudaSuccess)
+    return 0;
+  return per_sm;
+}
+
+}  // namespace
+
 // Opts a kernel into more than 48 KB of dynamic shared memory, once per kernel and device.
 cudaError_t allow_dyn_smem(void* fn, unsigned bytes) {
   if (bytes <= 48u * 1024u) return cudaSuccess;
@@ -348,19 +361,6 @@ cudaError_t allow_dyn_smem(void* fn, unsigned bytes) {
   if (e == cudaSuccess) done.emplace_back(fn, dev);
   return e;
 }
-
-int per_sm_ctas(int precision, int threads, int W) {
-  void* fn = step_fn_for(precision, threads, W);
-  if (!fn) return 0;
-  const unsigned dyn = step_dyn_smem(precision, threads, W);
-  int per_sm = 0;
-  if (allow_dyn_smem(fn, dyn) != cudaSuccess ||
-      cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, fn, threads, dyn) != cudaSuccess)
-    return 0;
-  return per_sm;
-}
-
-}  // namespace
 
 int max_coresident_ctas(int precision, int threads, int W, int device) {
   int sms = 0;

@@ -65,3 +65,28 @@ def test_staged_rows_on_a_full_size_mesh(prec):
     # the 1 M-cell relabelled box: gathers without locality, many tiles per CTA
     case = CASES["permuted100"]()
     assert_same(run(case, prec, True, n_steps=2), run(case, prec, False, n_steps=2))
+
+
+def batch_run(cases, n_steps, stage: bool, use_graph: bool):
+    from paper_2507_18268_gb300.batch import Batch
+    with Batch() as bt:
+        ids = [bt.add_case(c) for c in cases]
+        B.lfm_batch_debug_stage_rows(bt.handle, stage)
+        assert bt.advance(n_steps, use_graph=use_graph) == B.LFM_OK
+        return [(bt.field(cid).copy(), bt.stats(cid, n_steps)) for cid in ids]
+
+
+@pytest.mark.parametrize("use_graph", [True, False])
+def test_staged_rows_in_the_batched_kernel(use_graph):
+    # mixed cases with even and odd edges (N a multiple of 4 or not), teams of one to many
+    # CTAs, beside FP64 and df64 cases that keep the register form
+    import lapcase
+    n_steps = 3
+    cases = []
+    for i, c in enumerate(lapcase.batch_cases(n_cases=12, seed=21, n_min=6, n_max=60, n_steps=n_steps)):
+        prec = [lapcase.MIXED, lapcase.MIXED, lapcase.FP64, lapcase.DF64][i % 4]
+        cases.append(c.with_(precision=prec))
+    on = batch_run(cases, n_steps, True, use_graph)
+    off = batch_run(cases, n_steps, False, use_graph)
+    for a, b in zip(on, off):
+        assert_same(a, b)
