@@ -186,7 +186,13 @@ __device__ __noinline__ Sums4 pass_verify_next_df(const CaseDev& cs, int c0, int
   DfAcc a_v, a_nf, a_r;
   Acc2f a_rho;
   for (int c = c0 + (int)threadIdx.x; c < c1; c += B) {
-    if (c + B < c1) prefetch_row_df<W>(cs, c + B);
+    if (c + B < c1) {
+      prefetch_row_df<W>(cs, c + B);
+      // and the next row's per-cell values only this pass reads
+      prefetch_l2(cs.x_old + c + B);
+      prefetch_l2(cs.xolo + c + B);
+      prefetch_l2(cs.b_start + c + B);
+    }
     const tf xc = ld_tf(cs.x2, cs.xlo, c);
     df d, flux;
     row_flux_df<W, true>(cs, c, xc, d, flux);
@@ -205,15 +211,37 @@ __device__ __noinline__ Sums4 pass_verify_next_df(const CaseDev& cs, int c0, int
 // C: x += dx (the triple-float field and the FP32 correction of the inner solve). save_old:
 // keep x before the correction as the step's starting field (the first correction of a step
 // that began without S). Returns this thread's sum of the corrected x, formed as S forms it.
+// Two cells per loop trip (c, c + B), all their loads issued first and the next trip's
+// prefetched into L2; the sum is taken in the same order as one cell per trip.
 template <int B>
 __device__ __noinline__ double pass_correct_df(const CaseDev& cs, int c0, int c1, bool save_old) {
   float2* __restrict__ x2 = cs.x2;
   float* __restrict__ xl = cs.xlo;
   const float* __restrict__ dx = cs.dx32;
+  float2* __restrict__ xo2 = reinterpret_cast<float2*>(cs.x_old);
   DfAcc acc;
-  for (int c = c0 + (int)threadIdx.x; c < c1; c += B) {
+  int c = c0 + (int)threadIdx.x;
+  for (; c + B < c1; c += 2 * B) {
+    pf_next<B>(x2, c, c1);
+    pf_next<B>(xl, c, c1);
+    pf_next<B>(dx, c, c1);
+    const int e = c + B;
+    tf a = ld_tf(x2, xl, c), b = ld_tf(x2, xl, e);
+    const float da = dx[c], db = dx[e];
+    if (save_old) {
+      st_tf(xo2, cs.xolo, c, a);
+      st_tf(xo2, cs.xolo, e, b);
+    }
+    a = tf_add_df(a, mkdf(da, 0.0f));
+    b = tf_add_df(b, mkdf(db, 0.0f));
+    st_tf(x2, xl, c, a);
+    st_tf(x2, xl, e, b);
+    acc.add(tf_to_df(a));
+    acc.add(tf_to_df(b));
+  }
+  if (c < c1) {
     tf v = ld_tf(x2, xl, c);
-    if (save_old) st_tf(reinterpret_cast<float2*>(cs.x_old), cs.xolo, c, v);
+    if (save_old) st_tf(xo2, cs.xolo, c, v);
     v = tf_add_df(v, mkdf(dx[c], 0.0f));
     st_tf(x2, xl, c, v);
     acc.add(tf_to_df(v));
