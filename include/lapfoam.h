@@ -353,6 +353,12 @@ int lfm_set_barrier_timeout(lfm_ctx *ctx, uint64_t ns);
  * LFM_ETIMEOUT (no fault, no hang: every wait is bounded). One-shot; needs >= 2 CTAs. */
 int lfm_debug_skip_arrival(lfm_ctx *ctx, int32_t cta);
 
+/* Test hook: when cta >= 0, the next advance makes CTA `cta` issue no copy for the first tile
+ * of its first shared-memory-staged pass (see lfm_debug_stage_rows), so that its wait for
+ * those bytes runs out and the advance returns LFM_ETIMEOUT (no fault, no hang: every wait is
+ * bounded). One-shot; no effect when the launch stages no rows. */
+int lfm_debug_skip_stage_copy(lfm_ctx *ctx, int32_t cta);
+
 /* Test switch: on != 0 (the default) lets the passes that can stream their matrix rows into
  * shared memory with bulk copies do so (the FP32 A p of the mixed form in single-case
  * launches, on meshes of six slots per cell with N a multiple of 4); 0 makes them load the

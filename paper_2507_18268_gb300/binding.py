@@ -115,6 +115,7 @@ _SIGS = {
     "lfm_set_barrier_timeout": ([_ctx_p, c_uint64], c_int),
     "lfm_debug_skip_arrival": ([_ctx_p, c_int32], c_int),
     "lfm_debug_stage_rows": ([_ctx_p, c_int32], c_int),
+    "lfm_debug_skip_stage_copy": ([_ctx_p, c_int32], c_int),
     "lfm_pcg_solve_static": ([c_int32, c_int32, c_void_p, c_void_p, c_void_p, c_void_p, c_void_p, c_void_p,
                               POINTER(lfm_solver_opts), POINTER(lfm_step_stats), c_void_p], c_int),
     "lfm_destroy": ([_ctx_p], c_int),
@@ -496,6 +497,10 @@ def lfm_debug_skip_arrival(ctx, cta: int):
 
 def lfm_debug_stage_rows(ctx, on: bool):
     _check(load().lfm_debug_stage_rows(ctx, 1 if on else 0), ctx)
+
+
+def lfm_debug_skip_stage_copy(ctx, cta: int):
+    _check(load().lfm_debug_skip_stage_copy(ctx, int(cta)), ctx)
 
 
 def lfm_checked_build() -> bool:

@@ -221,6 +221,7 @@ struct lfm_ctx {
   uint64_t timeout_ns = 2000000000ull;
   int skip_cta = -1;
   int stage_rows = 1;  // bulk-staged matrix rows where a pass supports them
+  int skip_copy_cta = -1;
 
   // async state
   lfm_step_stats* h_stats = nullptr;  // pinned, kStatsCap records
@@ -391,6 +392,7 @@ Launch current_launch(lfm_ctx* c, int& err) {
   L.timeout_ns = c->timeout_ns;
   L.skip_cta = c->skip_cta;
   L.stage_rows = c->stage_rows;
+  L.skip_copy_cta = c->skip_copy_cta;
   return L;
 }
 
@@ -611,6 +613,7 @@ int enqueue_chunk(lfm_ctx* c, int steps, int mode) {
   CK(c, cudaMemsetAsync(c->cs.sync, 0, sizeof(SyncWords), c->stream));
   CK(c, launch_steps(c->cs, L, steps, mode, c->stream));
   c->skip_cta = -1;
+  c->skip_copy_cta = -1;
   if (steps > 0)
     CK(c, cudaMemcpyAsync(c->h_stats, c->cs.stats, sizeof(lfm_step_stats) * steps, cudaMemcpyDeviceToHost,
                           c->stream));
@@ -1451,6 +1454,12 @@ int lfm_debug_skip_arrival(lfm_ctx* c, int32_t cta) {
   return LFM_OK;
 }
 
+int lfm_debug_skip_stage_copy(lfm_ctx* c, int32_t cta) {
+  if (!c) return fail_free(LFM_EINVAL, "context is NULL");
+  c->skip_copy_cta = cta >= 0 ? cta : -1;
+  return LFM_OK;
+}
+
 int lfm_debug_stage_rows(lfm_ctx* c, int32_t on) {
   if (!c) return fail_free(LFM_EINVAL, "context is NULL");
   c->stage_rows = on != 0 ? 1 : 0;
@@ -1820,6 +1829,7 @@ int lfm_batch_advance_capped_async(lfm_batch* b, int32_t n_steps, int32_t use_gr
   bl.launch.timeout_ns = b->timeout_ns;
   bl.launch.skip_cta = -1;
   bl.launch.stage_rows = b->stage_rows;
+  bl.launch.skip_copy_cta = -1;
   bl.W = W;
   bl.form = form;
   b->last_ctas = ctas;
@@ -2189,7 +2199,7 @@ int lfm_dd_advance(lfm_dd* d, int32_t n_steps, lfm_step_stats* out) {
   cs.sync = d->sync;
   cs.partials = d->partials;
   cs.stats = d->stats;
-  Launch L{d->ctas, d->threads, c->timeout_ns, -1};
+  Launch L{d->ctas, d->threads, c->timeout_ns, -1, 0, -1};
   DDCK(d, cudaMemsetAsync(d->sync, 0, sizeof(SyncWords), c->stream));
   DDCK(d, launch_dd_steps(cs, d->d_parts, d->d_cta_part, d->d_cta_rank, L, n_steps, c->stream));
   int32_t status = 0;

@@ -262,6 +262,12 @@ __device__ __forceinline__ bool team_barrier(const Team& tm, TeamShared& sh) {
 // aligned and each size a multiple of 16 bytes.
 extern __shared__ __align__(128) unsigned char lfm_dyn_smem[];
 
+namespace {
+// Test hook (set by the host for one launch): this CTA issues no copy for its first staged
+// tile, so that its bounded wait runs out (-1: none).
+__device__ int g_skip_copy_cta = -1;
+}  // namespace
+
 __device__ __forceinline__ unsigned dyn_smem_bytes() {
   unsigned v;
   asm volatile("mov.u32 %0, %%dynamic_smem_size;" : "=r"(v));
@@ -364,6 +370,7 @@ __device__ __forceinline__ bool staged_tiles(int c0, int c1, const Team& tm, Iss
     const uint64_t pol = l2_evict_first_policy();
     for (int t = 0; t < 2 && t < ntiles; ++t) {
       const int t0 = c0 + t * TC;
+      if (t == 0 && (int)blockIdx.x == g_skip_copy_cta) continue;
       issue(sm + (t & 1) * kStage, t0, min(TC, c1 - t0), bar + (t & 1), pol);
     }
   }

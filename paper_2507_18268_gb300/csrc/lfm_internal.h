@@ -161,6 +161,7 @@ struct Launch {
   uint64_t timeout_ns;
   int skip_cta;              // test hook: CTA that leaves before its first arrival (-1: none)
   int stage_rows;            // 0: passes load their matrix rows into registers (test switch)
+  int skip_copy_cta;         // test hook: CTA that issues no copy for its first staged tile (-1: none)
 };
 
 enum Mode { kModeSteps = 0, kModeAssembleOnly = 1 };

@@ -393,6 +393,16 @@ cudaError_t launch_steps(const CaseDev& cs, const Launch& L, int n_steps, int mo
   Launch a1 = L;
   int a2 = n_steps, a3 = mode;
   void* args[] = {&a0, &a1, &a2, &a3};
+  if (L.skip_copy_cta >= 0) {  // test hook, for this launch only
+    const int none = -1;
+    cudaError_t he = cudaMemcpyToSymbolAsync(g_skip_copy_cta, &L.skip_copy_cta, sizeof(int), 0,
+                                             cudaMemcpyHostToDevice, stream);
+    if (he != cudaSuccess) return he;
+    he = cudaLaunchCooperativeKernel(fn, dim3(L.ctas), dim3(L.threads), args, dyn, stream);
+    const cudaError_t re =
+        cudaMemcpyToSymbolAsync(g_skip_copy_cta, &none, sizeof(int), 0, cudaMemcpyHostToDevice, stream);
+    return he != cudaSuccess ? he : re;
+  }
   return cudaLaunchCooperativeKernel(fn, dim3(L.ctas), dim3(L.threads), args, dyn, stream);
 }
 

@@ -90,3 +90,23 @@ def test_staged_rows_in_the_batched_kernel(use_graph):
     off = batch_run(cases, n_steps, False, use_graph)
     for a, b in zip(on, off):
         assert_same(a, b)
+
+
+def test_a_staged_copy_that_never_lands_times_out_and_the_context_recovers():
+    # CTA 1 issues no copy for its first tile: its bounded wait runs out (LFM_ETIMEOUT, the
+    # other CTAs leave at their next barrier), and the same context then solves exactly as a
+    # fresh one does (no GPU fault: every wait is bounded and the kernel returns)
+    import oracle
+    case = CASES["graded40"]()
+    fresh = run(case, B.LFM_MIXED, True)
+    with Solver.from_case(case) as s:
+        s.set_solver(case.tol, case.rel_tol, case.max_iter, case.min_iter, B.LFM_MIXED)
+        B.lfm_set_barrier_timeout(s.ctx, 200_000_000)  # 0.2 s
+        B.lfm_debug_skip_stage_copy(s.ctx, 1)
+        B.lfm_advance_async(s.ctx, 1)
+        rc, _ = B.lfm_finish_status(s.ctx, 1)
+        assert rc == B.LFM_ETIMEOUT
+        s.set_field(oracle.initial_field(case))
+        st = s.advance(case.n_steps)
+        again = (s.field().copy(), st)
+    assert_same(again, fresh)
