@@ -456,6 +456,29 @@ int lfm_dd_destroy(lfm_dd *dd);
 /* Reason for the last non-OK return (dd NULL: of a call without a decomposition). */
 const char *lfm_dd_last_error(const lfm_dd *dd);
 
+/* Face coefficients of a general mesh on the device: the linear-interpolation weights of
+ * the paper's "weights" loop (section "Code Porting") and the other per-face quantities of
+ * the corrected laplacian, one thread per face. Every pointer is DEVICE memory the caller
+ * owns, in the layouts of lfm_mesh / lfm_geometry (vectors as x, y, z per face or cell);
+ * the call enqueues on `stream` (a cudaStream_t; NULL: the legacy default stream), waits
+ * for it, and allocates and frees 4 bytes of device memory. For internal face f with owner P
+ * and neighbour N, from its area vector Sf and centre Cf and the cell centres C:
+ *   weights[f]     = |Sf.(C_N - Cf)| / (|Sf.(Cf - C_P)| + |Sf.(C_N - Cf)|), 0.5 when that
+ *                    sum is not above 1e-150 (owner weight: face value w (T_P - T_N) + T_N)
+ *   magSf[f]       = |Sf|
+ *   deltaCoeffs[f] = 1 / max(n.d, 0.05 |d|), n = Sf / |Sf|, d = C_N - C_P
+ *   corr_vec[3f..] = n - d deltaCoeffs[f]
+ * and for boundary face b of cell bface_cell[b]: bmagSf[b] = |bSf|, bdeltaCoeffs[b] =
+ * 1 / |n.(bCf - C)|. Each operation is rounded on its own, left to right (no fused
+ * multiply-adds). LFM_EINVAL for a negative count, a NULL array that is needed, or a cell
+ * index out of [0, n_cells) (found on the device; nothing is read through it), LFM_ECUDA for
+ * a failed launch; the message in lfm_last_error(NULL). */
+int lfm_face_coeffs_device(int32_t n_cells, int32_t n_faces, int32_t n_bfaces, const int32_t *owner,
+                           const int32_t *neighbour, const double *Sf, const double *Cf, const double *C,
+                           const int32_t *bface_cell, const double *bSf, const double *bCf, double *weights,
+                           double *magSf, double *deltaCoeffs, double *corr_vec, double *bmagSf,
+                           double *bdeltaCoeffs, void *stream);
+
 /* Measures the FP64 fused multiply-add rate of `device` (FMAs per second, into *fma_per_s):
  * independent FMA chains on every SM, the best of three timed launches after a warm-up.
  * It bounds the FP64 form, which issues about 14 FP64 instructions per cell and PCG

@@ -120,6 +120,7 @@ _SIGS = {
                               POINTER(lfm_solver_opts), POINTER(lfm_step_stats), c_void_p], c_int),
     "lfm_destroy": ([_ctx_p], c_int),
     "lfm_measure_fp64_fma_rate": ([c_int, POINTER(c_double)], c_int),
+    "lfm_face_coeffs_device": ([c_int32, c_int32, c_int32] + [c_void_p] * 15, c_int),
     "lfm_dd_plan": ([c_int32, c_int32, c_void_p, c_void_p, c_int32, c_int32, POINTER(lfm_dd_counts), c_void_p,
                      c_void_p, c_void_p, c_void_p], c_int),
     "lfm_dd_create": ([POINTER(c_void_p), _ctx_p, c_int32], c_int),
@@ -527,6 +528,18 @@ def lfm_pcg_solve_static(n_cells: int, n_faces: int, owner_ptr: int, neighbour_p
 
 def lfm_destroy(ctx):
     load().lfm_destroy(ctx)
+
+
+def lfm_face_coeffs_device(n_cells: int, n_faces: int, n_bfaces: int, owner, neighbour, Sf, Cf, C, bface_cell,
+                           bSf, bCf, weights, magSf, deltaCoeffs, corr_vec, bmagSf, bdeltaCoeffs, stream=0):
+    """Face weights and corrected-laplacian coefficients on the device; every array argument
+    is a device address (int), stream a cudaStream_t handle (0: the legacy default)."""
+    ptrs = [owner, neighbour, Sf, Cf, C, bface_cell, bSf, bCf, weights, magSf, deltaCoeffs, corr_vec, bmagSf,
+            bdeltaCoeffs, stream]
+    rc = load().lfm_face_coeffs_device(int(n_cells), int(n_faces), int(n_bfaces),
+                                       *[c_void_p(int(p)) if p else None for p in ptrs])
+    if rc != LFM_OK:
+        raise LfmError(rc, _err(None))
 
 
 def lfm_measure_fp64_fma_rate(device: int = 0) -> float:

@@ -198,12 +198,43 @@ def _quad_geometry(q: np.ndarray):
     return Cf, 0.5 * sumN
 
 
-def hex_mesh(case: lapcase.RawCase):
+def _face_coeffs_on_device(device: int, N: int, owner, neighbour, Sf, Cf, C, bcell, bSf, bCf):
+    """The per-face coefficients of hex_mesh computed on GPU ``device`` by the library's
+    kernel (lfm_face_coeffs_device): weights, |Sf|, deltaCoeffs, correction vectors, boundary
+    |Sf| and deltaCoeffs, returned as host arrays."""
+    import torch
+
+    from . import binding as B
+
+    dev = torch.device("cuda", device)
+
+    def up(a, dtype):
+        return torch.from_numpy(np.ascontiguousarray(a, dtype=dtype)).to(dev)
+
+    F, NB = len(owner), len(bcell)
+    own, nei, bc = up(owner, np.int32), up(neighbour, np.int32), up(bcell, np.int32)
+    sf, cf, c, bsf, bcf = (up(a, np.float64) for a in (Sf, Cf, C, bSf, bCf))
+    f64 = dict(dtype=torch.float64, device=dev)
+    w, mag, delta, corr = torch.empty(F, **f64), torch.empty(F, **f64), torch.empty(F, **f64), torch.empty((F, 3), **f64)
+    bmag, bdelta = torch.empty(NB, **f64), torch.empty(NB, **f64)
+    stream = torch.cuda.current_stream(dev)
+    with torch.cuda.device(dev):
+        B.lfm_face_coeffs_device(N, F, NB, own.data_ptr(), nei.data_ptr(), sf.data_ptr(), cf.data_ptr(), c.data_ptr(),
+                                 bc.data_ptr(), bsf.data_ptr(), bcf.data_ptr(), w.data_ptr(), mag.data_ptr(),
+                                 delta.data_ptr(), corr.data_ptr(), bmag.data_ptr(), bdelta.data_ptr(),
+                                 stream.cuda_stream)
+    return tuple(t.cpu().numpy() for t in (w, mag, delta, corr, bmag, bdelta))
+
+
+def hex_mesh(case: lapcase.RawCase, device: Optional[int] = None):
     """LDU mesh and geometry of a general hexahedral box (``case.points``; natural
     numbering). Face point order as documented in :mod:`lapcase`. Returns
     (LduMesh, HexGeometry); the mesh's deltaCoeffs are the non-orthogonal implicit
     coefficients 1 / max(n.d, 0.05 |d|) and bdeltaCoeffs the inverse patch-normal
-    distances 1 / |n.(Cf - C_P)|."""
+    distances 1 / |n.(Cf - C_P)|. With ``device`` the per-face coefficients (the
+    interpolation weights, the implicit coefficients, the correction vectors) are computed
+    on that GPU by the library's kernel; without it, here on the host, by the same formulas
+    in the same order."""
     if case.points is None:
         raise ValueError("case has no vertex array")
     if case.perm is not None:
@@ -260,6 +291,11 @@ def hex_mesh(case: lapcase.RawCase):
     C = Csum / vol[:, None]
     V = vol / 3.0
 
+    if device is not None:
+        weights, magSf, delta, corr, bmagSf, bdelta = _face_coeffs_on_device(device, N, owner, neighbour, Sf, Cf, C,
+                                                                           bcell, bSf, bCf)
+        return _hex_result(base, V, magSf, delta, bmagSf, bdelta, Sf, weights, corr, bSf, Cf, bCf, C)
+
     # interpolation weights, implicit coefficients, correction vectors
     SfdOwn = np.abs(_dot3(Sf, Cf - C[owner]))
     SfdNei = np.abs(_dot3(Sf, C[neighbour] - Cf))
@@ -275,6 +311,10 @@ def hex_mesh(case: lapcase.RawCase):
     bn = bSf / bmagSf[:, None]
     bdelta = 1.0 / np.abs(_dot3(bn, bCf - C[bcell]))
 
+    return _hex_result(base, V, magSf, delta, bmagSf, bdelta, Sf, weights, corr, bSf, Cf, bCf, C)
+
+
+def _hex_result(base, V, magSf, delta, bmagSf, bdelta, Sf, weights, corr, bSf, Cf, bCf, C):
     mesh = dataclasses.replace(base, V=V, magSf=np.ascontiguousarray(magSf), deltaCoeffs=np.ascontiguousarray(delta),
                                bmagSf=np.ascontiguousarray(bmagSf), bdeltaCoeffs=np.ascontiguousarray(bdelta))
     geo = HexGeometry(Sf=np.ascontiguousarray(Sf), weights=np.ascontiguousarray(weights),

@@ -109,9 +109,10 @@ class Solver:
     def from_case(cls, case: lapcase.RawCase, mesh: Optional[LduMesh] = None,
                   geometry: Optional[HexGeometry] = None, **kw) -> "Solver":
         """A case on a host-built mesh: the rectilinear box, or with ``case.points`` the
-        general hexahedral mesh and its geometry (corrected laplacian)."""
+        general hexahedral mesh and its geometry (corrected laplacian; the face weights and
+        coefficients computed on the solver's GPU)."""
         if mesh is None and case.points is not None:
-            mesh, geometry = hex_mesh(case)
+            mesh, geometry = hex_mesh(case, device=kw.get("device", 0))
         mesh = mesh or box_mesh(case)
         s = cls(mesh, geometry=geometry, **kw)
         s.configure(case)
