@@ -755,10 +755,10 @@ def batch_record(args, world, rank, local):
         for cid in ids:
             bt.cases[cid].set_field(T0[cid])
         torch.cuda.synchronize()
-        mark = args.profile_range and prec == B.LFM_FP64
+        mark = args.profile_range == name
         if prec == B.LFM_FP64 and rank == 0:  # clocks during the headline (FP64) timed region
             clocks.start()
-        if mark:  # the FP64 timed region is the profiler range (ncu --profile-from-start off)
+        if mark:  # this form's timed region is the profiler range (ncu --profile-from-start off)
             torch.cuda.profiler.start()
         ev0, ev1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
         ev0.record(stream)
@@ -920,8 +920,9 @@ def main():
                     help="graded200: leave out the batch512 / serve1000 / serve100 records")
     ap.add_argument("--workload", choices=["graded200", "batch512", "serve", "skewed200"], default="graded200")
     ap.add_argument("--batch-cases", type=int, default=512)
-    ap.add_argument("--profile-range", action="store_true",
-                    help="batch512: make the FP64 timed region the CUDA profiler range (ncu --profile-from-start off)")
+    ap.add_argument("--profile-range", nargs="?", const="fp64", default=None, choices=["fp64", "df64", "mixed"],
+                    help="batch512: make this form's timed region (default FP64) the CUDA profiler range "
+                         "(ncu --profile-from-start off)")
     ap.add_argument("--skewed-n", type=int, default=200, help="edge of the skewed box (profiling: smaller)")
     ap.add_argument("--requests", type=int, default=1000)
     ap.add_argument("--only", choices=["fp64", "mixed", "df64"], default=None,

@@ -58,6 +58,7 @@ __global__ void __launch_bounds__(B, 1024 / B) batch_kernel(const CaseDev* __res
     }
     __syncthreads();
     const Team tm{s_job[2], s_job[1], s_cs.sync, s_cs.partials, L.timeout_ns};
+    if (threadIdx.x == 0) team_join(tm, sh);
     const int base = case_step[c];
     // a case whose cap is reached runs no step; its team's CTAs go back for tickets at once
     const int run = min(n_steps, case_cap[c] - base);

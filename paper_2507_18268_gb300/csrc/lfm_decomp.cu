@@ -177,6 +177,7 @@ __global__ void __launch_bounds__(B, 1024 / B) dd_step_kernel(CaseDev cs, const 
   if (threadIdx.x == 0) me = parts[cta_part[blockIdx.x]];
   __syncthreads();
   const Team tm{(int)gridDim.x, (int)blockIdx.x, cs.sync, cs.partials, L.timeout_ns};
+  if (threadIdx.x == 0) team_join(tm, sh);
   int c0, c1;
   cta_range(me.N, me.ctas, cta_rank[blockIdx.x], c0, c1);
   // this CTA's send entries: those with source cells in [c0, c1) (send_src ascending)

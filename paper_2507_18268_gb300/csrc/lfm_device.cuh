@@ -86,7 +86,16 @@ struct TeamShared {
   double red[32 * kMaxSums];
   double out[kMaxSums];
   int flag[4];
+  unsigned gen;  // thread 0: the team's generation before this CTA's next arrival
 };
+
+// Thread 0 of a CTA, when the CTA joins a team (before its first arrival): the team's
+// generation word, which no barrier can move before this CTA has arrived. team_allreduce
+// then tracks the generation itself (one more per barrier passed), so that no load of it
+// sits before an arrival.
+__device__ __forceinline__ void team_join(const Team& tm, TeamShared& sh) {
+  sh.gen = *reinterpret_cast<volatile unsigned*>(&tm.sw->gen);
+}
 
 // Spins until *gen != g. False (with the error recorded) when the time limit runs out or
 // another CTA has recorded an error. The load is an acquire: what the releasing CTA wrote
@@ -149,8 +158,8 @@ __device__ __forceinline__ void block_reduce(double* v, TeamShared& sh) {
 
 // Team-wide barrier carrying NS sums. On return (true) v[k] holds the team totals in every
 // thread. False: a wait ran out or another CTA failed; the caller must leave the kernel.
-// Protocol: thread 0 stores the CTA's partial sums, reads the generation and arrives (one
-// acquire-release add); the CTA that finds size - 1 arrivals before its own is the last:
+// Protocol: thread 0 stores the CTA's partial sums and arrives (one acquire-release add;
+// the generation it waits on is its own count, see team_join); the CTA that finds size - 1 arrivals before its own is the last:
 // warp 0 loads all partial sums at once, adds them in rank order (lane l takes ranks l,
 // l + 32, ..., then a fixed xor tree), publishes the totals, clears the counter and releases
 // the generation with a release store (which orders the totals and the cleared counter
@@ -180,7 +189,7 @@ __device__ bool team_allreduce(const Team& tm, double* v, TeamShared& sh) {
 #pragma unroll
       for (int k = 0; k < NS; ++k) __stcg(&tm.partials[tm.rank * kMaxSums + k], sh.out[k]);
     }
-    const unsigned g = *reinterpret_cast<volatile unsigned*>(&tm.sw->gen);
+    const unsigned g = sh.gen;
     const unsigned prev = arrive_acq_rel(&tm.sw->count);
     const int last = prev == (unsigned)(tm.size - 1);
     int ok = 1;
@@ -196,6 +205,7 @@ __device__ bool team_allreduce(const Team& tm, double* v, TeamShared& sh) {
     sh.flag[0] = last;
     sh.flag[1] = ok;
     sh.flag[2] = (int)g;
+    sh.gen = g + 1u;
   }
   __syncthreads();
   if (!sh.flag[1]) return false;

@@ -24,6 +24,7 @@ __global__ void __launch_bounds__(B, 1024 / B) step_kernel_f64(CaseDev cs, Launc
   if (threadIdx.x == 0) s_cs = cs;
   __syncthreads();
   const Team tm{(int)gridDim.x, (int)blockIdx.x, cs.sync, cs.partials, L.timeout_ns};
+  if (threadIdx.x == 0) team_join(tm, sh);
   run_steps_f64<B, W>(cs, s_cs, tm, n_steps, mode, sh);
 }
 
@@ -35,6 +36,7 @@ __global__ void __launch_bounds__(B, 1024 / B) step_kernel_mixed(CaseDev cs, Lau
   if (threadIdx.x == 0) s_cs = cs;
   __syncthreads();
   const Team tm{(int)gridDim.x, (int)blockIdx.x, cs.sync, cs.partials, L.timeout_ns};
+  if (threadIdx.x == 0) team_join(tm, sh);
   run_steps_mixed<B, W>(cs, s_cs, tm, n_steps, mode, sh);
 }
 
@@ -47,6 +49,7 @@ __global__ void __launch_bounds__(B, 1024 / B) step_kernel_mixed_df(CaseDev cs, 
   if (threadIdx.x == 0) s_cs = cs;
   __syncthreads();
   const Team tm{(int)gridDim.x, (int)blockIdx.x, cs.sync, cs.partials, L.timeout_ns};
+  if (threadIdx.x == 0) team_join(tm, sh);
   run_steps_mixed_df<B, W>(cs, s_cs, tm, n_steps, sh);
 }
 
@@ -58,6 +61,7 @@ __global__ void __launch_bounds__(B, 1024 / B) step_kernel_df64(CaseDev cs, Laun
   if (threadIdx.x == 0) s_cs = cs;
   __syncthreads();
   const Team tm{(int)gridDim.x, (int)blockIdx.x, cs.sync, cs.partials, L.timeout_ns};
+  if (threadIdx.x == 0) team_join(tm, sh);
   run_steps_df64<B, W, kGeom>(cs, s_cs, tm, n_steps, sh);
 }
 
