@@ -582,6 +582,70 @@ def algorithmic_bytes_corrected(N: int, F: int, iters: int, passes: int) -> floa
     return float(iters) * (112 * N + 16 * F) + float(passes) * ((88 + 32 + 24) * N + (32 + 32 + 56) * F)
 
 
+def main_decomp(args, world, rank, local):
+    """One graded200 case decomposed into label-range parts (the paper's multi-GPU data flow
+    emulated on one GPU: halo exchange of T per step and of p per PCG iteration, global sums
+    over all parts) against the undecomposed FP64 step, from the same starting field."""
+    import torch
+
+    from paper_2507_18268_gb300 import Solver
+    from paper_2507_18268_gb300 import binding as B
+    from paper_2507_18268_gb300.decomp import Decomposed
+
+    torch.cuda.set_device(local)
+    K = args.steps if args.steps_given else 20
+    W = args.warmup
+    case = lapcase.graded_box(args.decomp_n, n_steps=K)
+    stream = torch.cuda.Stream(device=local)
+    s = Solver.from_case(case, device=local, stream=stream)
+    N = s.mesh.n_cells
+    T0 = s.field().copy()
+    s.advance(W)
+    s.set_field(T0)
+    clocks = ClockSampler(local)
+    barrier(world)
+    if rank == 0:
+        clocks.start()
+    secs, st = time_device_resident(s, B, torch, stream, K)
+    iters = sum(x["iters"] for x in st)
+    Tref = s.field().copy()
+    single = {"value": float(N) * iters / secs, "unit": UNIT, "ms_per_step": 1e3 * secs / K, "iters": iters}
+    parts = {}
+    for n_parts in args.decomp_parts:
+        s.set_field(T0)
+        with Decomposed(s, n_parts) as dd:
+            dd.set_field(T0)
+            dd.advance(W)
+            dd.set_field(T0)
+            torch.cuda.synchronize()
+            ev0, ev1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+            ev0.record(stream)
+            sd = dd.advance(K)  # enqueued on the case's stream, waited for inside
+            ev1.record(stream)
+            torch.cuda.synchronize()
+            dsecs = ev0.elapsed_time(ev1) * 1e-3
+            diters = sum(x["iters"] for x in sd)
+            Td = dd.field()
+            halo = sum(c.n_ghost for c in dd.counts())
+        parts[str(n_parts)] = {"value": float(N) * diters / dsecs, "unit": UNIT, "ms_per_step": 1e3 * dsecs / K,
+                               "iters_equal_single": diters == iters, "ghost_cells": halo,
+                               "time_vs_single": dsecs / secs,
+                               "max_rel_diff_vs_single": float(np.max(np.abs(Td - Tref) / np.abs(Tref)))}
+    clk = clocks.stop() if rank == 0 else None
+    s.close()
+    if rank != 0:
+        return
+    last = parts[str(args.decomp_parts[-1])]
+    line = {"metric": METRIC, "value": last["value"], "unit": UNIT, "n_gpus": world, "steps": K, "warmup": W,
+            "ms_per_step": last["ms_per_step"], "higher_is_better": True, "scaling": "weak", "vs_baseline": None,
+            "dtype": "f64", "data": "synthetic",
+            "config": {"workload": f"decomp{args.decomp_n}: graded{args.decomp_n} ({N} cells) in label-range "
+                                   f"parts, emulated on one GPU; value = {args.decomp_parts[-1]} parts",
+                       "parallelism": "single GPU (the parts' data flow, not several GPUs)"},
+            "clocks": clk, "single_fp64": single, "parts": parts}
+    print(json.dumps(line))
+
+
 def main_skewed(args, world, rank, local):
     """The non-orthogonal workload: device-resident FP64 and mixed, the oracle on a slab."""
     import torch
@@ -918,7 +982,9 @@ def main():
     ap.add_argument("--no-cpu-baseline", action="store_true")
     ap.add_argument("--no-sub", action="store_true",
                     help="graded200: leave out the batch512 / serve1000 / serve100 records")
-    ap.add_argument("--workload", choices=["graded200", "batch512", "serve", "skewed200"], default="graded200")
+    ap.add_argument("--workload", choices=["graded200", "batch512", "serve", "skewed200", "decomp"], default="graded200")
+    ap.add_argument("--decomp-n", type=int, default=200, help="decomp: edge of the graded box")
+    ap.add_argument("--decomp-parts", type=int, nargs="+", default=[1, 2, 4, 8], help="decomp: part counts")
     ap.add_argument("--batch-cases", type=int, default=512)
     ap.add_argument("--profile-range", nargs="?", const="fp64", default=None, choices=["fp64", "df64", "mixed"],
                     help="batch512: make this form's timed region (default FP64) the CUDA profiler range "
@@ -945,6 +1011,8 @@ def main():
             main_serve(args, world, rank, local)
         elif args.workload == "skewed200":
             main_skewed(args, world, rank, local)
+        elif args.workload == "decomp":
+            main_decomp(args, world, rank, local)
         else:
             main_ours(args, world, rank, local)
     finally:

@@ -230,13 +230,49 @@ __global__ void __launch_bounds__(B, 1024 / B) dd_step_kernel(CaseDev cs, const 
     if (cs.min_iter > 0 || !conv) {
       for (;;) {
         if (iters > 0) {
-          for (int c = c0 + tid; c < c1; c += B) me.p[c] = fma(beta, me.p[c], me.w[c]);
+          int c = c0 + tid;
+          for (; c + B < c1; c += 2 * B) {  // two cells per trip, the next trip prefetched
+            pf_next<B>(me.p, c, c1);
+            pf_next<B>(me.w, c, c1);
+            const double pa = me.p[c], pb = me.p[c + B], wa = me.w[c], wb = me.w[c + B];
+            me.p[c] = fma(beta, pa, wa);
+            me.p[c + B] = fma(beta, pb, wb);
+          }
+          if (c < c1) me.p[c] = fma(beta, me.p[c], me.w[c]);
           dd_push(parts, me, e0, e1, false, B);
           if (!team_barrier(tm, sh)) return;
         }
-        // q = A p over the owned rows (ghost columns from the exchange), sigma = p.q
+        // q = A p over the owned rows (ghost columns from the exchange), sigma = p.q; with a
+        // fixed slot width two rows per trip, all their loads issued first, the matrix with
+        // streaming loads (the cells per thread and the order of the sum as one row per trip)
         double s1[1] = {0.0};
-        for (int c = c0 + tid; c < c1; c += B) {
+        int c = c0 + tid;
+        if constexpr (W > 0) {
+          for (; c + B < c1; c += 2 * B) {
+            const int c2 = c + B;
+            const double pc = me.p[c], pc2 = me.p[c2];
+            double acc = __ldcs(me.diag + c) * pc, acc2 = __ldcs(me.diag + c2) * pc2;
+            int o[W], o2[W];
+            double u[W], u2[W];
+#pragma unroll
+            for (int k = 0; k < W; ++k) {
+              o[k] = __ldcs(me.slot_local + (size_t)k * N + c);
+              o2[k] = __ldcs(me.slot_local + (size_t)k * N + c2);
+              u[k] = __ldcs(cs.slot_coef + (size_t)k * Ng + me.first + c);
+              u2[k] = __ldcs(cs.slot_coef + (size_t)k * Ng + me.first + c2);
+            }
+#pragma unroll
+            for (int k = 0; k < W; ++k) {
+              acc = fma(u[k], me.p[o[k]], acc);
+              acc2 = fma(u2[k], me.p[o2[k]], acc2);
+            }
+            me.q[c] = acc;
+            me.q[c2] = acc2;
+            s1[0] = fma(acc, pc, s1[0]);
+            s1[0] = fma(acc2, pc2, s1[0]);
+          }
+        }
+        for (; c < c1; c += B) {
           const double pc = me.p[c];
           double acc = me.diag[c] * pc;
           const int ns = W > 0 ? W : cs.W;
@@ -257,6 +293,13 @@ __global__ void __launch_bounds__(B, 1024 / B) dd_step_kernel(CaseDev cs, const 
         const double alpha = rho / sigma;
         double s2[2] = {0.0, 0.0};
         for (int c = c0 + tid; c < c1; c += B) {
+          if (c + B < c1) {  // the next trip's cell, into L2
+            prefetch_l2(me.q + c + B);
+            prefetch_l2(me.r + c + B);
+            prefetch_l2(me.p + c + B);
+            prefetch_l2(me.x + c + B);
+            prefetch_l2(me.rD + c + B);
+          }
           const double rn = fma(-alpha, me.q[c], me.r[c]);
           const double wn = me.rD[c] * rn;
           me.x[c] = fma(alpha, me.p[c], me.x[c]);
