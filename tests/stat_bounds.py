@@ -106,7 +106,9 @@ def step_bounds(case, om, T: np.ndarray, form: str, launch: Tuple[int, int],
     xb_exact = math.fsum(T) / N
     xb_serial = np.cumsum(T)[-1] / N  # the oracle's left-to-right sum
     ctas, threads = launch
-    depth = math.ceil(N / max(ctas * threads, 1)) + 10 + math.ceil(max(ctas, 1) / 32) + 5
+    # per thread; the block (up to 4 xor levels in a warp, up to 8 partials per lane of warp 0,
+    # a 5-level xor tree); the team (ranks per lane of the last arriver, a 5-level xor tree)
+    depth = math.ceil(N / max(ctas * threads, 1)) + 17 + math.ceil(max(ctas, 1) / 32) + 5
     dxb = abs(xb_serial - xb_exact) + gamma(depth + 2, u_sum) * float(np.mean(np.abs(T)))
     e_ax = (3 * nfaces + 4) * u_c * M
     e_b = 8.0 * (nfaces + 3) * u_c * C
