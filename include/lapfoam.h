@@ -359,6 +359,11 @@ int lfm_debug_skip_arrival(lfm_ctx *ctx, int32_t cta);
  * bounded). One-shot; no effect when the launch stages no rows. */
 int lfm_debug_skip_stage_copy(lfm_ctx *ctx, int32_t cta);
 
+/* Test evidence: the number of passes of the last advance (lfm_advance / lfm_advance_async
+ * and its finish) that ran with their matrix rows staged in shared memory, counted once per
+ * pass on the team's first CTA; 0 when the register form ran throughout. */
+int lfm_debug_staged_passes(lfm_ctx *ctx, int64_t *n);
+
 /* Test switch: on != 0 (the default) lets the passes that can stream their matrix rows into
  * shared memory with bulk copies do so (the FP32 A p of the mixed form in single-case
  * launches, on meshes of six slots per cell with N a multiple of 4); 0 makes them load the

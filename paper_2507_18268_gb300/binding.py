@@ -116,6 +116,7 @@ _SIGS = {
     "lfm_debug_skip_arrival": ([_ctx_p, c_int32], c_int),
     "lfm_debug_stage_rows": ([_ctx_p, c_int32], c_int),
     "lfm_debug_skip_stage_copy": ([_ctx_p, c_int32], c_int),
+    "lfm_debug_staged_passes": ([_ctx_p, POINTER(ctypes.c_int64)], c_int),
     "lfm_pcg_solve_static": ([c_int32, c_int32, c_void_p, c_void_p, c_void_p, c_void_p, c_void_p, c_void_p,
                               POINTER(lfm_solver_opts), POINTER(lfm_step_stats), c_void_p], c_int),
     "lfm_destroy": ([_ctx_p], c_int),
@@ -502,6 +503,12 @@ def lfm_debug_stage_rows(ctx, on: bool):
 
 def lfm_debug_skip_stage_copy(ctx, cta: int):
     _check(load().lfm_debug_skip_stage_copy(ctx, int(cta)), ctx)
+
+
+def lfm_debug_staged_passes(ctx) -> int:
+    n = ctypes.c_int64(0)
+    _check(load().lfm_debug_staged_passes(ctx, ctypes.byref(n)), ctx)
+    return n.value
 
 
 def lfm_checked_build() -> bool:

@@ -226,7 +226,8 @@ struct lfm_ctx {
   // async state
   lfm_step_stats* h_stats = nullptr;  // pinned, kStatsCap records
   int32_t* h_status = nullptr;        // pinned
-  unsigned long long* h_phase = nullptr;  // pinned, kPhases
+  unsigned long long* h_phase = nullptr;  // pinned, kPhases + 1 (the phase times, then the staged-pass count)
+  long long staged_passes = 0;        // passes of the last advance with staged rows (team rank 0)
   double phase_ms[kPhases] = {};      // per phase kind, summed over the last advance
   cudaEvent_t done = nullptr;
   int pending_steps = 0;
@@ -618,7 +619,7 @@ int enqueue_chunk(lfm_ctx* c, int steps, int mode) {
     CK(c, cudaMemcpyAsync(c->h_stats, c->cs.stats, sizeof(lfm_step_stats) * steps, cudaMemcpyDeviceToHost,
                           c->stream));
   CK(c, cudaMemcpyAsync(c->h_status, &c->cs.sync->status, sizeof(int32_t), cudaMemcpyDeviceToHost, c->stream));
-  CK(c, cudaMemcpyAsync(c->h_phase, c->cs.sync->phase_ns, sizeof(unsigned long long) * kPhases,
+  CK(c, cudaMemcpyAsync(c->h_phase, c->cs.sync->phase_ns, sizeof(unsigned long long) * (kPhases + 1),
                         cudaMemcpyDeviceToHost, c->stream));
   CK(c, cudaEventRecord(c->done, c->stream));
   return LFM_OK;
@@ -639,6 +640,7 @@ int collect_chunk(lfm_ctx* c, int steps) {
   CK(c, cudaEventSynchronize(c->done));
   for (int i = 0; i < steps; ++i) c->stats_acc.push_back(c->h_stats[i]);
   for (int k = 0; k < kPhases; ++k) c->phase_ms[k] += 1e-6 * (double)c->h_phase[k];
+  c->staged_passes += (long long)c->h_phase[kPhases];
   int32_t st = *c->h_status;
   if (st != 0) invalidate_seed(c);  // a launch that stopped early left no seed to trust
   if (st == LFM_ETIMEOUT) return fail(c, LFM_ETIMEOUT, "a device barrier wait ran out (kernel stopped)");
@@ -705,7 +707,7 @@ int lfm_create(lfm_ctx** out, int device, void* cuda_stream) {
   DeviceGuard g(device);
   if (cudaMallocHost(&c->h_stats, sizeof(lfm_step_stats) * kStatsCap) != cudaSuccess ||
       cudaMallocHost(&c->h_status, sizeof(int32_t)) != cudaSuccess ||
-      cudaMallocHost(&c->h_phase, sizeof(unsigned long long) * kPhases) != cudaSuccess ||
+      cudaMallocHost(&c->h_phase, sizeof(unsigned long long) * (kPhases + 1)) != cudaSuccess ||
       cudaEventCreateWithFlags(&c->done, cudaEventDisableTiming) != cudaSuccess) {
     lfm_destroy(c);
     return fail_free(LFM_ECUDA, "lfm_create: host staging or event allocation failed");
@@ -1291,6 +1293,7 @@ int lfm_advance_async(lfm_ctx* c, int32_t n_steps) {
   DeviceGuard g(c->device);
   c->stats_acc.clear();
   for (int k = 0; k < kPhases; ++k) c->phase_ms[k] = 0.0;
+  c->staged_passes = 0;
   const int first = n_steps < kStatsCap ? n_steps : kStatsCap;
   if ((rc = enqueue_chunk(c, first, kModeSteps))) return rc;
   c->pending_steps = first;
@@ -1457,6 +1460,13 @@ int lfm_debug_skip_arrival(lfm_ctx* c, int32_t cta) {
 int lfm_debug_skip_stage_copy(lfm_ctx* c, int32_t cta) {
   if (!c) return fail_free(LFM_EINVAL, "context is NULL");
   c->skip_copy_cta = cta >= 0 ? cta : -1;
+  return LFM_OK;
+}
+
+int lfm_debug_staged_passes(lfm_ctx* c, int64_t* n) {
+  if (!c) return fail_free(LFM_EINVAL, "context is NULL");
+  if (!n) return fail(c, LFM_EINVAL, "n is NULL");
+  *n = c->staged_passes;
   return LFM_OK;
 }
 

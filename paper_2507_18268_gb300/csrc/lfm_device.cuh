@@ -420,6 +420,7 @@ __device__ __forceinline__ bool staged_tiles(int c0, int c1, const Team& tm, Iss
       for (int u = t; u < ntiles && u < t + 2; ++u) mbar_drain(bar + (u & 1), (u >> 1) & 1, tm.timeout_ns);
     mbar_inval(bar);
     mbar_inval(bar + 1);
+    if (!failed && tm.rank == 0) ++tm.sw->staged;  // read back by the host (a test's evidence)
   }
   __syncthreads();
   return !failed;

@@ -31,7 +31,8 @@ struct alignas(128) SyncWords {
   int32_t status;                    // first error of the launch (0 = none)
   int32_t pad3[31];
   unsigned long long phase_ns[8];    // time per phase kind, accumulated by the team's rank 0
-  unsigned long long pad4[8];
+  unsigned long long staged;         // passes that ran with rows staged in shared memory (rank 0)
+  unsigned long long pad4[7];
 };
 
 // Phase kinds of the step (indices of SyncWords::phase_ns).

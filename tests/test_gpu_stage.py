@@ -20,13 +20,17 @@ pytestmark = pytest.mark.gpu
 STAT_KEYS = ("iters", "sweeps", "converged", "status", "init_res", "final_res", "norm_factor")
 
 
-def run(case, prec, stage: bool, ctas=0, threads=0, n_steps=None):
+def run(case, prec, stage: bool, ctas=0, threads=0, n_steps=None, staged=None):
+    """Field and statistics of a run; `staged` (a list) receives the number of passes that
+    ran with staged rows, as the device counted them."""
     with Solver.from_case(case) as s:
         s.set_solver(case.tol, case.rel_tol, case.max_iter, case.min_iter, prec)
         if ctas or threads:
             s.set_launch(ctas, threads)
         B.lfm_debug_stage_rows(s.ctx, stage)
         st = s.advance(case.n_steps if n_steps is None else n_steps)
+        if staged is not None:
+            staged.append(B.lfm_debug_staged_passes(s.ctx))
         return s.field().copy(), st
 
 
@@ -48,7 +52,14 @@ PRECS = [B.LFM_MIXED]
                                   "plain7", "ragged", "line"])
 def test_staged_rows_bitwise_equal_to_register_rows(name, prec):
     case = CASES[name]()
-    assert_same(run(case, prec, True), run(case, prec, False))
+    n_on, n_off = [], []
+    assert_same(run(case, prec, True, staged=n_on), run(case, prec, False, staged=n_off))
+    # the staged form really ran where it applies (six slots, N a multiple of 4), and only there
+    assert n_off == [0]
+    if case.n_cells % 4 == 0 and min(case.nx, case.ny, case.nz) > 1:
+        assert n_on[0] > 0
+    else:
+        assert n_on == [0]
 
 
 @pytest.mark.parametrize("prec", PRECS)
