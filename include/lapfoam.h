@@ -365,9 +365,9 @@ int lfm_debug_skip_stage_copy(lfm_ctx *ctx, int32_t cta);
 int lfm_debug_staged_passes(lfm_ctx *ctx, int64_t *n);
 
 /* Test switch: on != 0 (the default) lets the passes that can stream their matrix rows into
- * shared memory with bulk copies do so (the FP32 A p of the mixed form in single-case
- * launches, on meshes of six slots per cell with N a multiple of 4); 0 makes them load the
- * rows into registers. Both give the same results bit for bit; the switch exists to test
+ * shared memory with bulk copies do so (the FP32 A p of the mixed form on orthogonal meshes,
+ * in single-case launches, on meshes of six slots per cell with N a multiple of 4); 0 makes
+ * them load the rows into registers. Both give the same results bit for bit; the switch exists to test
  * that. */
 int lfm_debug_stage_rows(lfm_ctx *ctx, int32_t on);
 

@@ -324,9 +324,13 @@ void* step_fn_for(int precision, int threads, int W) {
 }
 
 // Dynamic shared memory of a step kernel: the two stages of the bulk-staged FP32 A p of the
-// mixed form (kernels specialised for six slots).
+// mixed form on orthogonal meshes (the kernel with df64 outer passes, specialised for six
+// slots). The mixed kernel for general meshes runs without them: the shared memory comes out
+// of the same on-chip array as L1, and its gradient and corrected-row passes, which gather
+// through L1, lost more (skewed200: 0.71 -> 0.86 and 1.97 -> 2.01 ms per step) than its A p
+// gained (0.655 -> 0.638).
 unsigned step_dyn_smem(int precision, int threads, int W) {
-  if ((precision == LFM_MIXED || precision == kMixedDf) && W == 6) {
+  if (precision == kMixedDf && W == 6) {
     switch (threads) {
       case 256: return stage_bytes_f32<256, 6>();
       case 512: return stage_bytes_f32<512, 6>();
