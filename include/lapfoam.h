@@ -409,7 +409,9 @@ int lfm_debug_check_inject(lfm_ctx *ctx, int32_t site);
  * allocating library routine. All calls share that array (each call re-initialises what it
  * needs), so calls whose kernels overlap on one GPU race: order them on one stream. The
  * first call on a device looks up the array's device address (cudaGetSymbolAddress) with
- * that device current; make that first call before any stream capture. */
+ * that device current. Because every call synchronises its stream, no call can be part of a
+ * stream capture: on a stream that is being captured the call returns LFM_ESTATE before any
+ * device work (and leaves the capture intact). */
 int lfm_pcg_solve_static(int32_t n_cells, int32_t n_faces, const int32_t *owner,
                          const int32_t *neighbour, const double *diag, const double *upper,
                          const double *source, double *x, const lfm_solver_opts *opts,

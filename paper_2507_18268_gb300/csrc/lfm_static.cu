@@ -361,6 +361,18 @@ extern "C" int lfm_pcg_solve_static(int32_t n_cells, int32_t n_faces, const int3
       overlaps(x, xb, owner, sizeof(int32_t) * (size_t)n_faces) ||
       overlaps(x, xb, neighbour, sizeof(int32_t) * (size_t)n_faces))
     return set_last_error(LFM_EINVAL, "%s: x overlaps an input array (the solve is not in place)", me);
+  {
+    // the call reads its record back and synchronises: it can never be part of a capture
+    cudaStreamCaptureStatus cap = cudaStreamCaptureStatusNone;
+    const cudaError_t ce = cudaStreamIsCapturing(static_cast<cudaStream_t>(cuda_stream), &cap);
+    if (ce != cudaSuccess) {
+      cudaGetLastError();
+      return set_last_error(LFM_ECUDA, "%s: querying the stream: %s", me, cudaGetErrorString(ce));
+    }
+    if (cap != cudaStreamCaptureStatusNone)
+      return set_last_error(LFM_ESTATE, "%s: the stream is being captured; this call synchronises and cannot be captured",
+                            me);
+  }
   unsigned char* scratch = nullptr;
   if (scratch_for_current_device(&scratch) != LFM_OK)
     return set_last_error(LFM_ECUDA, "%s: device address of the fixed working array not available", me);

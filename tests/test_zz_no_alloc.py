@@ -136,3 +136,32 @@ def test_static_solve_rejects_x_overlapping_an_input():
     assert rc == B.LFM_EINVAL and "overlaps" in B.lfm_last_error()
     rc, _ = _static(N, own, nbr, d, u, b, d)
     assert rc == B.LFM_EINVAL
+
+
+def test_static_solve_refuses_a_capturing_stream():
+    # the call synchronises its stream, so on a stream under capture it must refuse before
+    # any device work and leave the capture intact; the same call afterwards solves
+    import torch
+    N = 8
+    own = _dev(np.arange(N - 1, dtype=np.int32), torch.int32)
+    nbr = _dev(np.arange(1, N, dtype=np.int32), torch.int32)
+    d = _dev(np.full(N, 4.0), torch.float64)
+    u = _dev(np.full(N - 1, -1.0), torch.float64)
+    b = _dev(np.ones(N), torch.float64)
+    x = _dev(np.zeros(N), torch.float64)
+    side = torch.cuda.Stream()
+    graph = torch.cuda.CUDAGraph()
+    torch.cuda.synchronize()
+    with torch.cuda.stream(side):
+        graph.capture_begin(capture_error_mode="thread_local")
+        try:
+            rc, _ = B.lfm_pcg_solve_static(N, N - 1, own.data_ptr(), nbr.data_ptr(), d.data_ptr(), u.data_ptr(),
+                                           b.data_ptr(), x.data_ptr(), 1e-10, stream=side.cuda_stream)
+        finally:
+            graph.capture_end()
+    assert rc == B.LFM_ESTATE and "captured" in B.lfm_last_error()
+    rc, st = B.lfm_pcg_solve_static(N, N - 1, own.data_ptr(), nbr.data_ptr(), d.data_ptr(), u.data_ptr(),
+                                    b.data_ptr(), x.data_ptr(), 1e-10, stream=side.cuda_stream)
+    assert rc == B.LFM_OK and st.converged
+    A = np.diag(np.full(N, 4.0)) - np.diag(np.ones(N - 1), 1) - np.diag(np.ones(N - 1), -1)
+    assert np.allclose(x.cpu().numpy(), np.linalg.solve(A, np.ones(N)), rtol=1e-8)
