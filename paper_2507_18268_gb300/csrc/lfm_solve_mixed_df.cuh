@@ -12,7 +12,8 @@
 //   S   sum of x (xRef); x kept as the step's starting field x_old
 //   T0  rows of the matrix (FP32 copies of diag and 1/diag for the inner solve), the true
 //       residual r = b - A x, normFactor, and the seed of the inner solve
-//   sweep: inner CG (P, M, U on FP32 vectors) on A dx = r; C  x += dx, sum of x;
+//   sweep: inner CG (P, M, U on FP32 vectors; M with its matrix rows bulk-copied into shared
+//          memory where the launch provides it) on A dx = r; C  x += dx, sum of x;
 //          then the true residual after the correction: T1, or V (below); another sweep
 //          while it is not converged
 // V (steps without volumetric sources or non-orthogonal correctors): one pass over the rows
