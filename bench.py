@@ -646,6 +646,55 @@ def main_decomp(args, world, rank, local):
     print(json.dumps(line))
 
 
+def main_large(args, world, rank, local):
+    """Capacity: an n^3 box with graded200's total grading (ratio 1.02^(200/n) per cell),
+    built on the device, FP64 and mixed, with the device memory each case holds."""
+    import torch
+
+    from paper_2507_18268_gb300 import Solver
+    from paper_2507_18268_gb300 import binding as B
+
+    torch.cuda.set_device(local)
+    K = args.steps if args.steps_given else 20
+    W = args.warmup
+    n = args.large_n
+    stream = torch.cuda.Stream(device=local)
+    forms = {}
+    clocks = ClockSampler(local)
+    if rank == 0:
+        clocks.start()
+    for prec, name in ((B.LFM_FP64, "fp64"), (B.LFM_MIXED, "mixed")):
+        case = lapcase.graded_box(n, ratio=1.02 ** (200.0 / n), n_steps=K, precision=prec)
+        torch.cuda.synchronize()
+        free0, _ = torch.cuda.mem_get_info(local)
+        s = Solver.from_box_case(case, device=local, stream=stream, layout=prec)
+        free1, _ = torch.cuda.mem_get_info(local)
+        s.advance(W)
+        barrier(world)
+        secs, st = time_device_resident(s, B, torch, stream, K)
+        iters = sum(x["iters"] for x in st)
+        N = n ** 3
+        secs_max = reduce_max(secs, world)
+        forms[name] = {"value": reduce_sum(float(N) * iters, world) / secs_max, "unit": UNIT,
+                       "ms_per_step": 1e3 * secs_max / K, "iters_per_step": iters / K,
+                       "converged": all(x["converged"] for x in st), "device_GB": (free0 - free1) / 1e9,
+                       "bytes_per_cell": (free0 - free1) / N}
+        s.close()
+        del s
+        torch.cuda.synchronize()
+    clk = clocks.stop() if rank == 0 else None
+    if rank != 0:
+        return
+    line = {"metric": METRIC, "value": forms["fp64"]["value"], "unit": UNIT, "n_gpus": world, "steps": K,
+            "warmup": W, "ms_per_step": forms["fp64"]["ms_per_step"], "higher_is_better": True,
+            "scaling": "weak", "vs_baseline": None, "dtype": "f64", "data": "synthetic",
+            "config": {"workload": f"large{n}: {n}^3 box ({n ** 3} cells) graded {1.02 ** (200.0 / n):.6f}x per cell "
+                                   f"in x (graded200's total grading), graded200's BCs and controls, built on the "
+                                   f"device; value = FP64", "parallelism": "single GPU"},
+            "clocks": clk, "fp64": forms["fp64"], "mixed": forms["mixed"]}
+    print(json.dumps(line))
+
+
 def main_skewed(args, world, rank, local):
     """The non-orthogonal workload: device-resident FP64 and mixed, the oracle on a slab."""
     import torch
@@ -982,7 +1031,9 @@ def main():
     ap.add_argument("--no-cpu-baseline", action="store_true")
     ap.add_argument("--no-sub", action="store_true",
                     help="graded200: leave out the batch512 / serve1000 / serve100 records")
-    ap.add_argument("--workload", choices=["graded200", "batch512", "serve", "skewed200", "decomp"], default="graded200")
+    ap.add_argument("--workload", choices=["graded200", "batch512", "serve", "skewed200", "decomp", "large"],
+                    default="graded200")
+    ap.add_argument("--large-n", type=int, default=600, help="large: edge of the box")
     ap.add_argument("--decomp-n", type=int, default=200, help="decomp: edge of the graded box")
     ap.add_argument("--decomp-parts", type=int, nargs="+", default=[1, 2, 4, 8], help="decomp: part counts")
     ap.add_argument("--batch-cases", type=int, default=512)
@@ -1013,6 +1064,8 @@ def main():
             main_skewed(args, world, rank, local)
         elif args.workload == "decomp":
             main_decomp(args, world, rank, local)
+        elif args.workload == "large":
+            main_large(args, world, rank, local)
         else:
             main_ours(args, world, rank, local)
     finally:
