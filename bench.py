@@ -675,10 +675,16 @@ def main_large(args, world, rank, local):
         iters = sum(x["iters"] for x in st)
         N = n ** 3
         secs_max = reduce_max(secs, world)
+        F = 3 * n * n * (n - 1)
+        alg = algorithmic_bytes(N, F, iters, K, 0 if prec == B.LFM_FP64 else 1)
+        hbm_peak, peak_kind = load_peaks()
         forms[name] = {"value": reduce_sum(float(N) * iters, world) / secs_max, "unit": UNIT,
                        "ms_per_step": 1e3 * secs_max / K, "iters_per_step": iters / K,
                        "converged": all(x["converged"] for x in st), "device_GB": (free0 - free1) / 1e9,
-                       "bytes_per_cell": (free0 - free1) / N}
+                       "bytes_per_cell": (free0 - free1) / N,
+                       "roofline": {"bound": "hbm", "achieved": alg / secs_max / 1e9, "peak": hbm_peak, "unit": "GB/s",
+                                    "frac": alg / secs_max / 1e9 / hbm_peak, "peak_kind": peak_kind,
+                                    "traffic": None}}
         s.close()
         del s
         torch.cuda.synchronize()
