@@ -512,6 +512,7 @@ def main_ours(args, world, rank, local):
         subs["batch512"] = run_workload(["--workload", "batch512", "--warmup", str(args.warmup)])
         subs["serve1000"] = run_workload(["--workload", "serve", "--requests", "1000"])
         subs["serve100"] = run_workload(["--workload", "serve", "--requests", "100"])
+        subs["large600"] = run_workload(["--workload", "large", "--warmup", str(args.warmup)])
 
     if rank != 0:
         return
@@ -562,6 +563,10 @@ def main_ours(args, world, rank, local):
                        "max_rel_diff_batched_vs_alone":
                            v["plain_fp64_sequential"]["max_rel_diff_batched_vs_alone"],
                        "mixed_max_rel_diff_vs_fp64_batch": v["batched_mixed"]["max_rel_diff_vs_fp64_batch"]}
+        elif k == "large600":
+            line[k] = {"config": v["config"]["workload"], "clocks": v["clocks"], "unit": UNIT,
+                       **{f: {kk: v[f][kk] for kk in ("value", "ms_per_step", "iters_per_step", "device_GB",
+                                                      "roofline")} for f in ("fp64", "mixed")}}
         else:
             line[k] = {"config": v["config"]["workload"], "clocks": v["clocks"], "served": v["served"],
                        "serial_plain_fp64": v["serial_plain_fp64"],
@@ -1036,7 +1041,7 @@ def main():
     ap.add_argument("--no-e2e", action="store_true")
     ap.add_argument("--no-cpu-baseline", action="store_true")
     ap.add_argument("--no-sub", action="store_true",
-                    help="graded200: leave out the batch512 / serve1000 / serve100 records")
+                    help="graded200: leave out the batch512 / serve1000 / serve100 / large600 records")
     ap.add_argument("--workload", choices=["graded200", "batch512", "serve", "skewed200", "decomp", "large"],
                     default="graded200")
     ap.add_argument("--large-n", type=int, default=600, help="large: edge of the box")
