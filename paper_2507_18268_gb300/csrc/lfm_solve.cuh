@@ -624,8 +624,10 @@ __device__ __forceinline__ double2 pass_update_f64(int c0, int c1, double alpha,
 }
 
 // U (FP32 inner solve): dx += a p, r -= a q, w = rD r; returns sum|r| and w.r, each
-// accumulated exactly as FP32 pairs.
-template <int B>
+// accumulated exactly as FP32 pairs. kFirst (the solve's first iteration): dx = a p + 0,
+// the same value as dx += a p from the dx = 0 the solve starts from, without reading it (the
+// seed passes then need not write that zero).
+template <int B, bool kFirst = false>
 __device__ __forceinline__ double2 pass_update_f32(int c0, int c1, float a32, float* __restrict__ dx,
                                                 float* __restrict__ r, float* __restrict__ w,
                                                 const float* __restrict__ p, const float* __restrict__ q,
@@ -635,12 +637,13 @@ __device__ __forceinline__ double2 pass_update_f32(int c0, int c1, float a32, fl
   for (; c + B < c1; c += 2 * B) {
     pf_next<B>(p, c, c1);
     pf_next<B>(q, c, c1);
-    pf_next<B>(dx, c, c1);
+    if (!kFirst) pf_next<B>(dx, c, c1);
     pf_next<B>(r, c, c1);
     pf_next<B>(rD, c, c1);
     const int e = c + B;
     const float pa = p[c], pb = p[e], qa = q[c], qb = q[e];
-    const float xa = dx[c], xb = dx[e], ra = r[c], rb = r[e], da = rD[c], db = rD[e];
+    const float xa = kFirst ? 0.0f : dx[c], xb = kFirst ? 0.0f : dx[e], ra = r[c], rb = r[e], da = rD[c],
+                db = rD[e];
     const float rna = fmaf(-a32, qa, ra), rnb = fmaf(-a32, qb, rb);
     const float wa = da * rna, wb = db * rnb;
     dx[c] = fmaf(a32, pa, xa);
@@ -657,7 +660,7 @@ __device__ __forceinline__ double2 pass_update_f32(int c0, int c1, float a32, fl
   if (c < c1) {
     const float rn = fmaf(-a32, q[c], r[c]);
     const float wn = rD[c] * rn;
-    dx[c] = fmaf(a32, p[c], dx[c]);
+    dx[c] = fmaf(a32, p[c], kFirst ? 0.0f : dx[c]);
     r[c] = rn;
     w[c] = wn;
     rsum.add(fabsf(rn));
@@ -695,7 +698,8 @@ __device__ __noinline__ Sums3 pass_rows_init_f64(const CaseDev& cs, int c0, int 
 }
 
 // T (mixed step): the FP64 true residual r = b - A x, rounded to FP32 to seed the inner
-// solve (r, w = rD r, p = w, dx = 0). With kFirst it is computed together with the rows of
+// solve (r, w = rD r, p = w; dx starts at zero implicitly: the solve's first update writes it).
+// With kFirst it is computed together with the rows of
 // the matrix (A2) and the normFactor terms. Returns this thread's normFactor sum (kFirst),
 // sum|r| and rho (FP32 terms accumulated exactly as FP32 pairs).
 template <int B, int W, bool kFirst, bool kCorr>
@@ -703,7 +707,6 @@ __device__ __noinline__ Sums3 pass_true_residual(const CaseDev& cs, int c0, int 
   float* __restrict__ r = cs.r32;
   float* __restrict__ w = cs.w32;
   float* __restrict__ p = cs.p32;
-  float* __restrict__ dx = cs.dx32;
   const double* __restrict__ x = cs.x;
   double u0 = 0.0, u1 = 0.0;
   Acc2f rho_acc;
@@ -727,7 +730,6 @@ __device__ __noinline__ Sums3 pass_true_residual(const CaseDev& cs, int c0, int 
     r[c] = r32;
     w[c] = w32;
     p[c] = w32;
-    dx[c] = 0.0f;
   }
   return Sums3{u0, u1, rho_acc.value()};
 }
@@ -973,7 +975,8 @@ __device__ void run_steps_mixed(const CaseDev& cs, const CaseDev& cref, const Te
             status = LFM_ESINGULAR;
             break;
           }
-          const double2 su = pass_update_f32<B>(c0, c1, (float)(rho / sigma), dx, r, w, p, q, rD);
+          const double2 su = k == 0 ? pass_update_f32<B, true>(c0, c1, (float)(rho / sigma), dx, r, w, p, q, rD)
+                                    : pass_update_f32<B, false>(c0, c1, (float)(rho / sigma), dx, r, w, p, q, rD);
           double s2[2] = {su.x, su.y};
           if (!team_allreduce<2>(tm, s2, sh)) return;
           clk.lap(kPhU);

@@ -81,7 +81,8 @@ __device__ __forceinline__ void row_flux_df(const CaseDev& cs, int c, const tf& 
 
 // The rest of a step's first row pass once the row is assembled (diag d, source src, row sum
 // sa, residual rc; all scaled): A x = src - rc and the normFactor terms against xRef (xr),
-// sum|r|, and the inner solve's seed r32 = r / s, w32 = rD32 r32, p32 = w32, dx32 = 0,
+// sum|r|, and the inner solve's seed r32 = r / s, w32 = rD32 r32, p32 = w32 (dx32 starts at zero
+// implicitly: the solve's first update writes it),
 // rho = w32.r32 (FP32 pairs), with the FP32 copies of diag / s and s / diag.
 __device__ __forceinline__ void seed_row_df(const CaseDev& cs, int c, df d, df src, df sa, df rc, df xr, float s32,
                                             float inv_s32, DfAcc& a_nf, DfAcc& a_r, Acc2f& a_rho) {
@@ -100,7 +101,6 @@ __device__ __forceinline__ void seed_row_df(const CaseDev& cs, int c, df d, df s
   cs.r32[c] = r32;
   cs.w32[c] = w32;
   cs.p32[c] = w32;
-  cs.dx32[c] = 0.0f;
 }
 
 // T0: rows of the matrix, the true residual (flux form), normFactor terms, sum|r| (scaled;
@@ -167,7 +167,6 @@ __device__ __noinline__ double2 pass_true_residual_df(const CaseDev& cs, int c0,
     cs.r32[c] = r32;
     cs.w32[c] = w32;
     cs.p32[c] = w32;
-    cs.dx32[c] = 0.0f;
   }
   return make_double2(a_r.value(), a_rho.value());
 }
@@ -360,7 +359,8 @@ __device__ bool steps_mixed_df(const CaseDev& cs, const CaseDev& cref, const Tea
             status = LFM_ESINGULAR;
             break;
           }
-          const double2 su = pass_update_f32<B>(c0, c1, (float)(rho / sigma), dx, r, w, p, q, rD);
+          const double2 su = k == 0 ? pass_update_f32<B, true>(c0, c1, (float)(rho / sigma), dx, r, w, p, q, rD)
+                                    : pass_update_f32<B, false>(c0, c1, (float)(rho / sigma), dx, r, w, p, q, rD);
           double s2[2] = {su.x, su.y};
           if (!team_allreduce<2>(tm, s2, sh)) return false;
           clk.lap(kPhU);
